@@ -1,0 +1,192 @@
+/*
+ * xc.h -- C ABI of libxc, the GB300 (sm_103a) implementation of the
+ * execution stage of the extra-component method for fast matrix-vector
+ * products with special-function matrices (A. V. Terekhov, "An extra-component
+ * method for evaluating fast matrix-vector multiplication with special
+ * functions").
+ *
+ * The matrix is A[n, m] = phi_m(x_n), n = 0..N-1 (node), m = 0..N-1 (degree),
+ * eq. (cheb_matrix) for the Chebyshev family and eq. (Jac_matrix) for the
+ * orthogonal polynomials; Section 4 for the Laguerre functions.
+ *
+ *   xc_apply          y = A x      (Algorithm 1 for the two-sided Chebyshev
+ *                                    family, Algorithm 3 for the block method)
+ *   xc_apply_adjoint  x = A^T y    (Algorithm 2 / Algorithm 4)
+ *
+ * Conventions shared by every entry point
+ *   - Return value: XC_OK (0) or a negative XC_ERR_* code.  No C++ exception
+ *     crosses this boundary.  xc_strerror() names a code; xc_last_error_message()
+ *     gives the text of the most recent failure on the calling thread.
+ *   - Vectors are row-major [nrhs][ld] with ld >= N: right-hand side r occupies
+ *     elements r*ld .. r*ld+N-1.  Their element type is the plan's I/O type:
+ *     double for XC_FP64 plans, float for XC_FP32 and XC_FP32_COMPENSATED.
+ *   - Pointers named *_dev are device pointers owned by the caller; pointers
+ *     named *_host are host pointers owned by the caller.  The plan owns every
+ *     other buffer (compressed matrices, windows, twiddles, scratch).
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Apply
+ *     calls are asynchronous on that stream.  Calls on one plan must not
+ *     overlap on the GPU: the plan's scratch is shared by its calls.
+ *   - A plan is immutable after xc_plan_create, apart from the scratch growth
+ *     done by xc_plan_reserve / the first apply with a larger nrhs.
+ */
+#ifndef XC_H_
+#define XC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- error codes */
+#define XC_OK               0
+#define XC_ERR_ARG         -1   /* invalid argument (null pointer, N < 2, eps < 0, ...) */
+#define XC_ERR_ALLOC       -2   /* device or host allocation failed */
+#define XC_ERR_CUDA        -3   /* a CUDA runtime call or kernel launch failed */
+#define XC_ERR_TIMEOUT     -4   /* a bounded device-side wait gave up */
+#define XC_ERR_UNSUPPORTED -5   /* valid request outside what this build implements */
+
+/* ---------------------------------------------------------------- families */
+typedef enum {
+  XC_CHEBYSHEV_T = 0,  /* T_m(x) = cos(m arccos x); two-sided extension (Section 2) */
+  XC_LEGENDRE    = 1,  /* P_m(x); block method (Section 3, alpha = beta = 0) */
+  XC_JACOBI      = 2,  /* P_m^{(alpha,beta)}(x); block method (Section 3) */
+  XC_LAGUERRE_FN = 3,  /* l_m(x) = exp(-x/2) L_m(x) (Section 4); block method */
+  XC_HERMITE_FN  = 4   /* orthonormal Hermite functions psi_m(x); block method */
+} xc_family;
+
+/* node sets */
+#define XC_NODES_GAUSS 0   /* Gauss nodes of the family (Chebyshev: x_n = cos((2n+1)pi/(2N))) */
+#define XC_NODES_USER  1   /* caller-supplied nodes (user_nodes) */
+
+/* normalisation */
+#define XC_RAW         0   /* A[n,m] = phi_m(x_n) */
+#define XC_ORTHONORMAL 1   /* sqrt(lambda_n / chi_m) phi_m(x_n): orthogonal at Gauss nodes (Section 5.2) */
+
+/* apply precision */
+#define XC_FP64             0   /* FP64 FFT, FP64 sparse product */
+#define XC_FP32             1   /* FP32 FFT, FP32 sparse product */
+#define XC_FP32_COMPENSATED 2   /* FP32 FFT; sparse product and dense tail accumulated
+                                   with error-free transformations (TwoProduct/TwoSum) */
+
+/* extension scheme */
+#define XC_SCHEME_AUTO      0   /* two-sided for XC_CHEBYSHEV_T, block method otherwise */
+#define XC_SCHEME_TWO_SIDED 1   /* Algorithms 1-2; Chebyshev family only */
+#define XC_SCHEME_BLOCKS    2   /* Algorithms 3-4 */
+
+typedef struct {
+  double alpha, beta;        /* Jacobi parameters (> -1); ignored by the other families */
+  int nodes;                 /* XC_NODES_GAUSS | XC_NODES_USER */
+  const double* user_nodes;  /* host, N entries, copied at create; used when nodes == XC_NODES_USER */
+  int normalise;             /* XC_RAW | XC_ORTHONORMAL (orthonormal needs Gauss nodes) */
+  double eps2;               /* window floor of the first real component; 0 => 1e-3 (FP64) or 3e-2 (FP32) */
+  double eps_window;         /* eps that fixes zeta when eps == 0; 0 => 1e-14 */
+  int precision;             /* XC_FP64 | XC_FP32 | XC_FP32_COMPENSATED */
+  int scheme;                /* XC_SCHEME_* */
+  int tail_max;              /* blocks are added while m_i > tail_max; 0 => 20 */
+} xc_params;
+
+/* Fill *p with the defaults listed above (Gauss nodes, raw, FP64, auto scheme). */
+void xc_params_default(xc_params* p);
+
+typedef struct xc_plan* xc_plan_t;
+
+/*
+ * xc_plan_create -- precomputation stage of Algorithms 1-4 (step 1 of each).
+ *   family  an xc_family value
+ *   p       parameters (NULL => defaults); user_nodes is copied
+ *   N       matrix order, 2 <= N <= 2^20
+ *   eps     eps1 of the paper: elements of the compressed matrix with
+ *           |a| <= eps * max|A_e W F| (per block) are dropped, and the Kaiser
+ *           shape zeta solves 1/I0(zeta) = eps (Section 2.2).  eps == 0 keeps
+ *           every element and takes zeta from p->eps_window.
+ * Runs on the current CUDA device and synchronises it.  On success *out owns
+ * all device memory of the plan; on failure *out is NULL and nothing leaks.
+ */
+int xc_plan_create(xc_plan_t* out, int family, const xc_params* p, int64_t N, double eps);
+
+/* Release every resource of the plan (NULL is accepted).  Synchronises the device. */
+int xc_plan_destroy(xc_plan_t plan);
+
+/*
+ * xc_plan_reserve -- allocate the scratch needed by applies with up to nrhs
+ * right-hand sides, so that later applies allocate nothing.
+ */
+int xc_plan_reserve(xc_plan_t plan, int64_t nrhs);
+
+/*
+ * xc_apply -- y = A x (Algorithm 1 step 2 / Algorithm 3): per block, extend the
+ * input with zero extra components (eq. (Fe1) / (Fe3)), divide by the window,
+ * FFT, multiply by the compressed matrix; add the dense tail.
+ *   x_dev  device, [nrhs][ld] of the plan's I/O type (read only)
+ *   y_dev  device, [nrhs][ld] (written; must not alias x_dev)
+ *   nrhs   number of right-hand sides (0 is a no-op)
+ *   ld     leading dimension in elements, ld >= N
+ */
+int xc_apply(xc_plan_t plan, const void* x_dev, void* y_dev, int64_t nrhs, int64_t ld, void* stream);
+
+/*
+ * xc_apply_adjoint -- x = A^T y (Algorithm 2 step 2 / Algorithm 4): per block,
+ * multiply by the transposed compressed matrix, inverse FFT, divide by the
+ * window and discard the extra components (eq. (Fe2)); the dense tail writes
+ * the first m_tail entries.  Exactly the transpose of xc_apply's operator.
+ * Same argument conventions as xc_apply (y_dev is read, x_dev written).
+ */
+int xc_apply_adjoint(xc_plan_t plan, const void* y_dev, void* x_dev, int64_t nrhs, int64_t ld, void* stream);
+
+/*
+ * xc_apply_host -- end-to-end forward or adjoint apply on HOST buffers:
+ * copies the input to the device, applies, copies the result back and
+ * synchronises the stream.  adjoint = 0: out = A in; adjoint = 1: out = A^T in.
+ * in_host / out_host: [nrhs][ld] of the plan's I/O type (pinned memory gives
+ * full copy bandwidth).  Uses device staging owned by the plan.
+ */
+int xc_apply_host(xc_plan_t plan, int adjoint, const void* in_host, void* out_host,
+                  int64_t nrhs, int64_t ld, void* stream);
+
+/* Per-block statistics reported by xc_plan_info. */
+#define XC_MAX_BLOCKS 16
+typedef struct {
+  int64_t N;
+  int family, precision, scheme, normalise;
+  double eps, eps2, zeta;
+  int nblocks;
+  int64_t L[XC_MAX_BLOCKS];          /* FFT length of block i */
+  int64_t off[XC_MAX_BLOCKS];        /* extended column j holds matrix column j - off */
+  int64_t j_lo[XC_MAX_BLOCKS];       /* real input occupies extended columns [j_lo, j_hi) */
+  int64_t j_hi[XC_MAX_BLOCKS];
+  int64_t nnz[XC_MAX_BLOCKS];        /* kept elements in the half spectrum k = 0..L/2 */
+  int64_t stored[XC_MAX_BLOCKS];     /* stored band elements incl. explicit zeros (forward layout) */
+  double maxabs[XC_MAX_BLOCKS];      /* max |A_e W F| of the block */
+  int64_t m_tail;                    /* dense tail columns [0, m_tail) */
+  int64_t matrix_bytes;              /* device bytes of the compressed matrices + tail (forward) */
+  int64_t adjoint_bytes;             /* device bytes of the transposed copies */
+} xc_plan_stats;
+
+/* Copy the plan's parameters and per-block statistics into *out. */
+int xc_plan_info(xc_plan_t plan, xc_plan_stats* out);
+
+/* Copy the plan's N nodes (FP64, the order of the rows of A) into host_out. */
+int xc_get_nodes(xc_plan_t plan, double* host_out);
+
+/*
+ * xc_dense_matrix -- write the plain N x N matrix (with the plan's
+ * normalisation) to A_dev, row-major with leading dimension lda >= N, in the
+ * plan's I/O type.  Generated on the device by the same recurrences as the
+ * precompute; used by the dense-GEMM comparison.
+ */
+int xc_dense_matrix(xc_plan_t plan, void* A_dev, int64_t lda, void* stream);
+
+/*
+ * xc_sync_status -- synchronise the plan's last stream and report any error
+ * recorded by the device since the last call (XC_OK if none).
+ */
+int xc_sync_status(xc_plan_t plan);
+
+const char* xc_strerror(int code);
+const char* xc_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XC_H_ */
