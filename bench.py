@@ -1,0 +1,471 @@
+#!/usr/bin/env python3
+"""Throughput of the extra-component apply (forward + adjoint) on one node.
+
+One step = for every plan of the workload: y = A x (xc_apply) and x = A^T y
+(xc_apply_adjoint) over the workload's right-hand sides, inputs resident in
+HBM.  Default workload: Chebyshev T_k at 4096 Chebyshev-Gauss points and
+Laguerre functions at 4096 Gauss-Laguerre nodes, eps = 1e-12, FP64, 64
+standard-normal right-hand sides.
+
+Prints one JSON line (rank 0).  `value` counts vector applies (one right-hand
+side through one direction of one plan) per second over all ranks; ranks are
+independent replicas (weak scaling, no collective on the data path).
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import math
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2004_11610_gb300 import inputs  # noqa: E402
+
+METRIC = "vectors/s and HBM GB/s (fraction of peak) vs GPU direct dense GEMM at stated rel-l2 error"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flops x max SM clock
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("xc", "reference"), default="xc")
+    ap.add_argument("--workload", default="cheb_lag4096_fp64", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dense", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------- workload
+def plan_specs(wl):
+    out = []
+    for i, (fam, N, params) in enumerate(wl["plans"]):
+        out.append(dict(family=fam, N=N, params=params, index=i))
+    return out
+
+
+def workload_config(name, wl):
+    return {
+        "workload": name,
+        "plans": [f"{fam} N={N}" + (f" alpha={p['alpha']} beta={p['beta']}" if p else "")
+                  for fam, N, p in wl["plans"]],
+        "nodes": "Gauss nodes of each family (Chebyshev-Gauss for Chebyshev)",
+        "eps": wl["eps"], "precision": wl["precision"], "nrhs": wl["nrhs"], "input": wl["dist"],
+        "step": "forward + adjoint apply of every plan",
+        "l2": "flushed before every timed step (256 MiB write)",
+    }
+
+
+def algorithmic_work(info, nrhs, precision):
+    """Per kernel: algorithmic flops and bytes of one launch."""
+    eb = 8 if precision == "fp64" else 4
+    nnz = sum(info["nnz"])
+    N, mt = info["N"], info["m_tail"]
+    fft_flops = sum(2.5 * L * math.log2(L) for L in info["L"]) * nrhs
+    H = sum(L // 2 + 1 for L in info["L"])
+    return {
+        "fwd_fft": (fft_flops, nrhs * (N * eb + H * 2 * eb)),
+        "fwd_sparse": (nrhs * (4.0 * nnz + 2.0 * N * mt),
+                       nnz * 2 * eb + nrhs * (H * 2 * eb + N * eb + mt * eb)),
+        "adj_sparse": (nrhs * 4.0 * nnz, nnz * 2 * eb + nrhs * (N * eb + H * 2 * eb)),
+        "adj_fft": (fft_flops, nrhs * (H * 2 * eb + N * eb)),
+        "adj_tail": (nrhs * 2.0 * N * mt, N * mt * eb + nrhs * N * eb),
+    }
+
+
+def step_bytes(info, nrhs, precision):
+    """Algorithmic HBM bytes of one forward + adjoint apply of one plan."""
+    eb = 8 if precision == "fp64" else 4
+    H = sum(L // 2 + 1 for L in info["L"])
+    vec = 4 * nrhs * info["N"] * eb                    # x in, y out, y in, x out
+    spec = 2 * 2 * nrhs * H * 2 * eb                   # spectra written + read, both directions
+    return info["matrix_bytes"] + info["adjoint_bytes"] + vec + spec
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [c.strip() for c in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------- cpu oracle
+def time_oracle(wl, sample_rhs, min_seconds, max_reps=1000):
+    """The FP64 oracle (as it stands) on the host: forward + adjoint apply of
+    every plan on `sample_rhs` right-hand sides, repeated for >= min_seconds.
+    Plan construction (the precompute) is not timed."""
+    from oracle import families as F
+    from oracle import method as M
+    plans = []
+    for i, (fam, N, params) in enumerate(wl["plans"]):
+        sp = F.make_spec(fam, N, params.get("alpha", 0.0), params.get("beta", 0.0))
+        plans.append((M.build(sp, wl["eps"], precision=wl["precision"]),
+                      inputs.draw(wl["dist"], N, sample_rhs, 90, i)))
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        for P, X in plans:
+            Y = M.apply(P, X)
+            M.apply_adjoint(P, Y)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or reps >= max_reps:
+            break
+    vectors = reps * len(plans) * 2 * sample_rhs
+    return vectors / el, el, reps
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = inputs.WORKLOADS[args.workload]
+    from oracle import families as F
+    from oracle import method as M
+    plans = []
+    for i, (fam, N, params) in enumerate(wl["plans"]):
+        sp = F.make_spec(fam, N, params.get("alpha", 0.0), params.get("beta", 0.0))
+        plans.append((M.build(sp, wl["eps"], precision=wl["precision"]), inputs.draw(wl["dist"], N, 1, 91, i)))
+
+    def step():
+        for P, X in plans:
+            M.apply_adjoint(P, M.apply(P, X))
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    vectors = args.steps * len(plans) * 2
+    value = vectors / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.workload, wl) | {"sample": "1 right-hand side per plan and direction per step"},
+        "cpu_baseline": {"value": value, "unit": "vectors/s", "cores": 1, "kind": "oracle",
+                         "sample": "1 RHS per plan, forward + adjoint, numpy/scipy single-threaded"},
+        "e2e": {"value": value, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU path
+def traffic_from_profiles(kernel, workload):
+    """dram bytes per launch from the committed ncu summary of this kernel and
+    workload, if the kernel source has not changed since the capture."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}__{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"source_sha256:\s*([0-9a-f]{16,64})", text)
+    if not m or not h:
+        return None
+    src = open(os.path.join(ROOT, "paper_2004_11610_gb300", "csrc", "xc_apply.cu"), "rb").read()
+    if not hashlib.sha256(src).hexdigest().startswith(h.group(1)):
+        return None
+    return float(m.group(1))
+
+
+def run_xc(args, rank, world, local_rank):
+    import torch
+    from paper_2004_11610_gb300 import build
+    build.build()
+    from paper_2004_11610_gb300 import xc
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wl = inputs.WORKLOADS[args.workload]
+    prec = wl["precision"]
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    R = wl["nrhs"]
+    specs = plan_specs(wl)
+    plans, X, Y, XA = [], [], [], []
+    for s in specs:
+        p = xc.Plan(s["family"], s["N"], wl["eps"], precision=prec,
+                    alpha=s["params"].get("alpha", 0.0), beta=s["params"].get("beta", 0.0))
+        p.reserve(R)
+        plans.append(p)
+        x = torch.from_numpy(inputs.draw(wl["dist"], s["N"], R, 1, s["index"], rank)).to(dev, tdt)
+        X.append(x)
+        Y.append(torch.empty_like(x))
+        XA.append(torch.empty_like(x))
+    infos = [p.info() for p in plans]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    def step():
+        for p, x, y, xa in zip(plans, X, Y, XA):
+            p.apply(x, out=y, stream=stream)
+            p.apply_adjoint(y, out=xa, stream=stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = xc.xc_launch_count()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        stops[k].record(stream)
+    barrier()
+    launches = xc.xc_launch_count() - launches0
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
+
+    # per-kernel device time, same steps again with every launch bracketed by events
+    for p in plans:
+        p.timing_enable(True)
+        p.timing_read()
+    for k in range(args.steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    per_kernel = {}
+    for p, info in zip(plans, infos):
+        work = algorithmic_work(info, R, prec)
+        for name, (n, ms) in p.timing_read().items():
+            e = per_kernel.setdefault(name, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+            e["launches"] += n
+            e["ms"] += ms
+            e["flops"] += work[name][0] * n
+            e["bytes"] += work[name][1] * n
+        p.timing_enable(False)
+    clock_info = clocks.stop()
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    max_ms = float(t.item())
+    vectors_per_step = sum(2 * R for _ in plans)
+    value = world * vectors_per_step * args.steps / (max_ms / 1e3)
+    ms_per_step = max_ms / args.steps
+
+    # roofline of the dominant kernel (largest summed device time)
+    dom = max(per_kernel.items(), key=lambda kv: kv[1]["ms"])
+    name, e = dom
+    avg_ms = e["ms"] / e["launches"]
+    flops_per_launch = e["flops"] / e["launches"]
+    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
+    fp64 = prec == "fp64"
+    roofline = {
+        "kernel": name, "bound": "alu", "achieved": achieved, "unit": "TFLOP/s",
+        "peak": FP64_PEAK_TFLOPS if fp64 else 152 * 128 * 2 * 2.070e9 / 1e12,
+        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz" if fp64
+        else "derived: 152 SMs x 128 FP32 FMA/clk x 2 flops x 2070 MHz",
+    }
+    roofline["frac"] = achieved / roofline["peak"]
+    tb = traffic_from_profiles(name, args.workload)
+    roofline["traffic"] = tb
+    roofline["algorithmic_bytes_per_launch"] = e["bytes"] / e["launches"]
+    roofline["avg_launch_ms"] = avg_ms
+    kernel_table = {k: {"launches": v["launches"], "avg_ms": v["ms"] / v["launches"],
+                        "share": v["ms"] / sum(w["ms"] for w in per_kernel.values()),
+                        "tflops": v["flops"] / v["ms"] / 1e9 if v["ms"] > 0 else None}
+                    for k, v in per_kernel.items()}
+    hbm_peak, hbm_src = measured_peaks()
+    sb = sum(step_bytes(i, R, prec) for i in infos)
+    hbm_gbs = sb / (ms_per_step / 1e3) / 1e9
+
+    # end to end through the C ABI with pinned host buffers (copies timed)
+    e2e_steps = max(3, min(args.steps, 50))
+    hx = [torch.from_numpy(inputs.draw(wl["dist"], s["N"], R, 2, s["index"], rank)).to(tdt).pin_memory()
+          for s in specs]
+    hy = [torch.empty_like(h).pin_memory() for h in hx]
+    hz = [torch.empty_like(h).pin_memory() for h in hx]
+    import ctypes
+    st = ctypes.c_void_p(stream.cuda_stream)
+
+    def e2e_step():
+        for p, a, b, c in zip(plans, hx, hy, hz):
+            rc = xc._lib.xc_apply_host(p.handle, 0, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                       R, p.N, st)
+            xc._check(rc, "xc_apply_host")
+            rc = xc._lib.xc_apply_host(p.handle, 1, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                       R, p.N, st)
+            xc._check(rc, "xc_apply_host")
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    e2e_val = world * vectors_per_step * e2e_steps / float(t.item())
+    eb = 8 if prec == "fp64" else 4
+    io_bytes = sum(2 * R * s["N"] * eb for s in specs)
+
+    # dense GEMM comparison (cuBLAS through torch) at equal precision
+    dense = None
+    if not args.no_dense:
+        mats = [p.dense_matrix() for p in plans]
+        torch.cuda.synchronize(dev)
+        errs = []
+        for p, A, x in zip(plans, mats, X):
+            y_m = p.apply(x)
+            y_d = x @ A.T
+            errs.append(float(torch.linalg.norm(y_m - y_d) / torch.linalg.norm(y_d)))
+            xa_m = p.apply_adjoint(y_d)
+            xa_d = y_d @ A
+            errs.append(float(torch.linalg.norm(xa_m - xa_d) / torch.linalg.norm(xa_d)))
+
+        def dense_step():
+            for A, x, y, xa in zip(mats, X, Y, XA):
+                torch.matmul(x, A.T, out=y)
+                torch.matmul(y, A, out=xa)
+
+        for _ in range(3):
+            dense_step()
+        torch.cuda.synchronize(dev)
+        ds = max(3, min(args.steps, 20))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dms = 0.0
+        for _ in range(ds):
+            flush.zero_()
+            a.record(stream)
+            dense_step()
+            b.record(stream)
+            b.synchronize()
+            dms += a.elapsed_time(b)
+        dense = {"vectors_per_s": vectors_per_step * ds / (dms / 1e3), "ms_per_step": dms / ds,
+                 "library": "cuBLAS via torch.matmul", "dtype": "f64" if fp64 else "f32",
+                 "method_rel_l2_vs_dense": max(errs),
+                 "speedup_of_method": (vectors_per_step * ds / (dms / 1e3)) and value / world /
+                 (vectors_per_step * ds / (dms / 1e3))}
+        del mats
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, el, reps = time_oracle(wl, 2, 10.0)
+        cpu = {"value": v, "unit": "vectors/s", "cores": 1, "kind": "oracle",
+               "sample": f"2 RHS per plan, forward + adjoint, {reps} repetitions in {el:.1f} s "
+                         "(numpy/scipy, single-threaded)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if fp64 else ("f32" if prec == "fp32" else "f32-compensated"),
+            "data": "synthetic", "config": workload_config(args.workload, wl) | {"parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
+                    "peak_source": hbm_src, "note": "algorithmic bytes of the whole step / step time"},
+            "kernels": kernel_table,
+            "dense_gemm": dense,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "vectors/s", "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes},
+            "gpu_launches": int(launches),
+            "clocks": clock_info,
+            "plans": [{k: i[k] for k in ("L", "nnz", "stored", "m_tail", "zeta", "matrix_bytes")} for i in infos],
+        }
+        print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_xc(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -178,6 +178,25 @@ int xc_get_nodes(xc_plan_t plan, double* host_out);
 int xc_dense_matrix(xc_plan_t plan, void* A_dev, int64_t lda, void* stream);
 
 /*
+ * Per-kernel timing.  While enabled, every kernel the plan launches is
+ * bracketed by two CUDA events recorded on the launch stream; xc_timing_read
+ * synchronises those events and returns, per kernel name, the number of
+ * launches and their summed device time since the previous read (then resets).
+ * Timing adds two event records per launch; leave it off for throughput runs.
+ */
+typedef struct {
+  char name[32];      /* kernel name, e.g. "fwd_sparse" */
+  int64_t launches;
+  double total_ms;
+} xc_kernel_time;
+int xc_timing_enable(xc_plan_t plan, int enable);
+/* out: caller array of max entries; *count receives the number filled. */
+int xc_timing_read(xc_plan_t plan, xc_kernel_time* out, int max, int* count);
+
+/* Total number of kernels launched by this library in the process so far. */
+int64_t xc_launch_count(void);
+
+/*
  * xc_sync_status -- synchronise the plan's last stream and report any error
  * recorded by the device since the last call (XC_OK if none).
  */

@@ -1,0 +1,407 @@
+// Execution stage (the hot path) of Algorithms 1-4.
+//
+// Forward, y = A x (Algorithm 1 step 2 / Algorithm 3):
+//   fwd_fft_kernel     per (block, RHS): extend the input with zero extra
+//                      components (eqs. (Fe1), (Fe3)), multiply by W^{-1},
+//                      real FFT -> half spectrum F_k = sum_j u_j exp(-2 pi i jk/L)
+//   fwd_sparse_kernel  per (32-row slice, RHS group): y_n = sum over blocks of
+//                      sum_k Re(C_nk conj(F_k)) over the row's band, plus the
+//                      dense tail; C = g_k A_e W F / sqrt(L) is stored with the
+//                      unitary and half-spectrum factors folded in, so that
+//                      Re(C conj F) = Re C Re F + Im C Im F.
+// Adjoint, x = A^T y (Algorithm 2 step 2 / Algorithm 4):
+//   adj_sparse_kernel  per (32-bin slice, RHS group): z_k = sum_n CT_kn y_n
+//   adj_fft_kernel     per (block, RHS): real inverse FFT of z, W^{-1}, keep the
+//                      real components [j_lo, j_hi), discard the extra ones (eq. (Fe2))
+//   adj_tail_kernel    the first m_tail entries from the dense tail.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "xc_fft.cuh"
+#include "xc_internal.h"
+
+namespace xc {
+
+namespace {
+
+constexpr int kFftThreads = 256;
+constexpr int kSparseWarps = 4;
+
+// ------------------------------------------------------------- accumulation
+// Plain or compensated (TwoProduct + TwoSum) sum of products.
+template <typename T, bool COMP>
+struct Acc {
+  T s = 0, c = 0;
+  __device__ __forceinline__ void add(T a, T b) {
+    if constexpr (!COMP) {
+      s = fma(a, b, s);
+    } else {
+      const T p = a * b;
+      const T e = fma(a, b, -p);          // a*b = p + e exactly
+      const T t = s + p;                  // TwoSum(s, p)
+      const T bb = t - s;
+      const T err = (s - (t - bb)) + (p - bb);
+      s = t;
+      c += err + e;
+    }
+  }
+  __device__ __forceinline__ T value() const { return COMP ? s + c : s; }
+};
+
+// ------------------------------------------------------------ forward FFT
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads)
+    fwd_fft_kernel(const BlockDev* __restrict__ blocks, const T* __restrict__ x, int64_t ld,
+                   const T* __restrict__ colscale, cx<T>* __restrict__ spec, int64_t nrhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  const BlockDev& b = blocks[blockIdx.y];
+  const int64_t r = blockIdx.x;
+  const int n = b.n, j_lo = b.j_lo, j_hi = b.j_hi, off = b.off;
+  const T* __restrict__ invw = static_cast<const T*>(b.invw);
+  const int* __restrict__ perm = b.perm;
+  const cx<T>* __restrict__ tw = static_cast<const cx<T>*>(b.tw);
+  const T* __restrict__ xr = x + r * ld;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int j0 = 2 * j, j1 = 2 * j + 1;
+    T u0 = T(0), u1 = T(0);
+    if (j0 >= j_lo && j0 < j_hi) {
+      T v = xr[j0 - off];
+      if (colscale) v *= colscale[j0 - off];
+      u0 = v * invw[j0];
+    }
+    if (j1 >= j_lo && j1 < j_hi) {
+      T v = xr[j1 - off];
+      if (colscale) v *= colscale[j1 - off];
+      u1 = v * invw[j1];
+    }
+    s[perm[j]] = cx<T>{u0, u1};
+  }
+  __syncthreads();
+  fft_inplace<T>(s, n, b.p, b.radix, tw, threadIdx.x, blockDim.x);
+  cx<T>* out = spec + b.spec_off * nrhs + r * int64_t(n + 1);
+  for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
+    cx<T> Uk, Unk;
+    r2c_split(s, n, k, tw, &Uk, &Unk);
+    out[k] = Uk;
+    if (n - k != k) out[n - k] = Unk;
+  }
+}
+
+// ------------------------------------------------------- forward sparse
+// Warp w of the CTA owns the 32-row slice 4*blockIdx.x + w and the RHS group
+// [RPW*blockIdx.y, RPW*blockIdx.y + RPW).  Lane = row.  Each band value is
+// loaded once (coalesced across the slice) and used for the RPW right-hand
+// sides; the spectra are gathered through L1.
+template <typename T, int RPW, bool COMP>
+__global__ void __launch_bounds__(32 * kSparseWarps)
+    fwd_sparse_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N, const T* __restrict__ x,
+                      int64_t ld, T* __restrict__ y, const cx<T>* __restrict__ spec, int64_t nrhs,
+                      const T* __restrict__ rowscale, const T* __restrict__ colscale, const T* __restrict__ tail,
+                      int64_t m_tail) {
+  const int lane = threadIdx.x & 31;
+  const int64_t slice = int64_t(blockIdx.x) * kSparseWarps + (threadIdx.x >> 5);
+  const int64_t nslices = (N + 31) / 32;
+  if (slice >= nslices) return;
+  const int64_t n = slice * 32 + lane;
+  const int64_t r0 = int64_t(blockIdx.y) * RPW;
+  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
+  Acc<T, COMP> acc[RPW];
+  for (int i = 0; i < nblocks; ++i) {
+    const BlockDev& b = blocks[i];
+    const int W = b.f_width[slice];
+    const int k0 = b.f_k0[n];
+    const int H = b.H;
+    const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.f_val) + b.f_off[slice] + lane;
+    const cx<T>* __restrict__ F = spec + b.spec_off * nrhs + r0 * H + k0;
+    if (nq == RPW) {
+      for (int j = 0; j < W; ++j) {
+        const cx<T> c = val[j * 32];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          const cx<T> f = F[q * H + j];
+          acc[q].add(c.re, f.re);
+          acc[q].add(c.im, f.im);
+        }
+      }
+    } else {
+      for (int j = 0; j < W; ++j) {
+        const cx<T> c = val[j * 32];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          if (q < nq) {
+            const cx<T> f = F[q * H + j];
+            acc[q].add(c.re, f.re);
+            acc[q].add(c.im, f.im);
+          }
+        }
+      }
+    }
+  }
+  if (n >= N) return;
+  for (int64_t m = 0; m < m_tail; ++m) {
+    const T t = tail[m * N + n];
+    const T cs = colscale ? colscale[m] : T(1);
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+      if (q < nq) acc[q].add(t, x[(r0 + q) * ld + m] * cs);
+  }
+  const T rs = rowscale ? rowscale[n] : T(1);
+#pragma unroll
+  for (int q = 0; q < RPW; ++q)
+    if (q < nq) y[(r0 + q) * ld + n] = acc[q].value() * rs;
+}
+
+// ------------------------------------------------------- adjoint sparse
+// Warp = 32-bin slice of one block (slices of all blocks enumerated in
+// order); lane = bin k; z_k = sum_j CT[j][k] y[n0_k + j].
+template <typename T, int RPW, bool COMP>
+__global__ void __launch_bounds__(32 * kSparseWarps)
+    adj_sparse_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t total_tslices, int64_t N,
+                      const T* __restrict__ y, int64_t ld, cx<T>* __restrict__ spec, int64_t nrhs,
+                      const T* __restrict__ rowscale) {
+  const int lane = threadIdx.x & 31;
+  int64_t g = int64_t(blockIdx.x) * kSparseWarps + (threadIdx.x >> 5);
+  if (g >= total_tslices) return;
+  int i = 0;
+  while (i < nblocks - 1 && g >= blocks[i].tslices) {
+    g -= blocks[i].tslices;
+    ++i;
+  }
+  const BlockDev& b = blocks[i];
+  const int64_t k = g * 32 + lane;
+  const int H = b.H;
+  const int W = b.t_width[g];
+  const int n0 = b.t_n0[k];
+  const int64_t r0 = int64_t(blockIdx.y) * RPW;
+  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
+  const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.t_val) + b.t_off[g] + lane;
+  Acc<T, COMP> re[RPW], im[RPW];
+  for (int j = 0; j < W; ++j) {
+    const cx<T> c = val[j * 32];
+    const int64_t row = n0 + j;
+    const T rs = rowscale ? rowscale[row] : T(1);
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      if (q < nq) {
+        const T v = y[(r0 + q) * ld + row] * rs;
+        re[q].add(c.re, v);
+        im[q].add(c.im, v);
+      }
+    }
+  }
+  if (k >= H) return;
+  cx<T>* out = spec + b.spec_off * nrhs + r0 * H + k;
+#pragma unroll
+  for (int q = 0; q < RPW; ++q)
+    if (q < nq) out[q * H] = cx<T>{re[q].value(), im[q].value()};
+}
+
+// ------------------------------------------------------------ adjoint FFT
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads)
+    adj_fft_kernel(const BlockDev* __restrict__ blocks, const cx<T>* __restrict__ spec, int64_t nrhs,
+                   T* __restrict__ x, int64_t ld, const T* __restrict__ colscale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  const BlockDev& b = blocks[blockIdx.y];
+  const int64_t r = blockIdx.x;
+  const int n = b.n, j_lo = b.j_lo, j_hi = b.j_hi, off = b.off;
+  const int* __restrict__ perm = b.perm;
+  const cx<T>* __restrict__ tw = static_cast<const cx<T>*>(b.tw);
+  const T* __restrict__ invw = static_cast<const T*>(b.invw);
+  const cx<T>* __restrict__ U = spec + b.spec_off * nrhs + r * int64_t(n + 1);
+  for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
+    cx<T> Uk = U[k], Unk = U[n - k];
+    if (k == 0) {
+      Uk.im = T(0);    // U_0 and U_n enter as real numbers
+      Unk.im = T(0);
+    }
+    cx<T> Zk, Znk;
+    c2r_merge(Uk, Unk, k, tw, &Zk, &Znk);
+    // inverse FFT as conj(FFT(conj(Z)))
+    s[perm[k]] = conj(Zk);
+    if (k != 0 && n - k != k) s[perm[n - k]] = conj(Znk);
+  }
+  __syncthreads();
+  fft_inplace<T>(s, n, b.p, b.radix, tw, threadIdx.x, blockDim.x);
+  T* __restrict__ xr = x + r * ld;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const cx<T> v = s[j];
+    const int j0 = 2 * j, j1 = 2 * j + 1;
+    if (j0 >= j_lo && j0 < j_hi) {
+      T u = v.re * invw[j0];
+      if (colscale) u *= colscale[j0 - off];
+      xr[j0 - off] = u;
+    }
+    if (j1 >= j_lo && j1 < j_hi) {
+      T u = -v.im * invw[j1];
+      if (colscale) u *= colscale[j1 - off];
+      xr[j1 - off] = u;
+    }
+  }
+}
+
+// ------------------------------------------------------------ adjoint tail
+// Warp per (m, RHS): x_m = colscale_m sum_n tail[m][n] rowscale_n y_n.
+template <typename T, bool COMP>
+__global__ void adj_tail_kernel(int64_t N, int64_t m_tail, const T* __restrict__ tail, const T* __restrict__ y,
+                                int64_t ld, T* __restrict__ x, const T* __restrict__ rowscale,
+                                const T* __restrict__ colscale) {
+  const int lane = threadIdx.x & 31;
+  const int64_t m = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t r = blockIdx.y;
+  if (m >= m_tail) return;
+  Acc<T, COMP> acc;
+  for (int64_t n = lane; n < N; n += 32) acc.add(tail[m * N + n], y[r * ld + n] * (rowscale ? rowscale[n] : T(1)));
+  T v = acc.value();
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) x[r * ld + m] = v * (colscale ? colscale[m] : T(1));
+}
+
+// ------------------------------------------------------------------ launch
+template <typename T>
+int launch_fft(Plan* p, bool forward, const void* in, void* out, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  const size_t smem = size_t(p->max_n) * sizeof(cx<T>);
+  const void* fn = forward ? reinterpret_cast<const void*>(fwd_fft_kernel<T>)
+                           : reinterpret_cast<const void*>(adj_fft_kernel<T>);
+  static thread_local size_t configured[2] = {0, 0};   // per kernel, per host thread
+  size_t& done = configured[forward ? 0 : 1];
+  if (smem > 48 * 1024 && smem > done) {
+    XC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    done = smem;
+  }
+  dim3 grid(unsigned(nrhs), unsigned(p->blocks.size()));
+  const BlockDev* bd = static_cast<const BlockDev*>(p->scratch_desc);
+  const int kid = forward ? K_FWD_FFT : K_ADJ_FFT;
+  launch_begin(p, kid, st);
+  if (forward)
+    fwd_fft_kernel<T><<<grid, kFftThreads, smem, st>>>(bd, static_cast<const T*>(in), ld,
+                                                        static_cast<const T*>(p->colscale),
+                                                        static_cast<cx<T>*>(out), nrhs);
+  else
+    adj_fft_kernel<T><<<grid, kFftThreads, smem, st>>>(bd, static_cast<const cx<T>*>(in), nrhs,
+                                                        static_cast<T*>(out), ld, static_cast<const T*>(p->colscale));
+  launch_end(p, kid, st);
+  XC_CUDA(cudaGetLastError());
+  return XC_OK;
+}
+
+template <typename T, bool COMP, int RPW>
+int launch_sparse_fwd_rpw(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  const int64_t nslices = (p->N + 31) / 32;
+  dim3 grid(unsigned((nslices + kSparseWarps - 1) / kSparseWarps), unsigned((nrhs + RPW - 1) / RPW));
+  launch_begin(p, K_FWD_SPARSE, st);
+  fwd_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
+      static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->N, static_cast<const T*>(x), ld,
+      static_cast<T*>(y), static_cast<const cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale),
+      static_cast<const T*>(p->colscale), static_cast<const T*>(p->tail), p->m_tail);
+  launch_end(p, K_FWD_SPARSE, st);
+  XC_CUDA(cudaGetLastError());
+  return XC_OK;
+}
+
+template <typename T, bool COMP, int RPW>
+int launch_sparse_adj_rpw(Plan* p, const void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  int64_t total = 0;
+  for (const BlockDev& b : p->blocks) total += b.tslices;
+  if (total == 0) return XC_OK;
+  dim3 grid(unsigned((total + kSparseWarps - 1) / kSparseWarps), unsigned((nrhs + RPW - 1) / RPW));
+  launch_begin(p, K_ADJ_SPARSE, st);
+  adj_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
+      static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), total, p->N, static_cast<const T*>(y),
+      ld, static_cast<cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale));
+  launch_end(p, K_ADJ_SPARSE, st);
+  XC_CUDA(cudaGetLastError());
+  return XC_OK;
+}
+
+template <typename T, bool COMP>
+int launch_sparse_fwd(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  if (nrhs >= 8) return launch_sparse_fwd_rpw<T, COMP, 8>(p, x, y, nrhs, ld, st);
+  if (nrhs >= 4) return launch_sparse_fwd_rpw<T, COMP, 4>(p, x, y, nrhs, ld, st);
+  if (nrhs >= 2) return launch_sparse_fwd_rpw<T, COMP, 2>(p, x, y, nrhs, ld, st);
+  return launch_sparse_fwd_rpw<T, COMP, 1>(p, x, y, nrhs, ld, st);
+}
+
+template <typename T, bool COMP>
+int launch_sparse_adj(Plan* p, const void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  if (nrhs >= 8) return launch_sparse_adj_rpw<T, COMP, 8>(p, y, nrhs, ld, st);
+  if (nrhs >= 4) return launch_sparse_adj_rpw<T, COMP, 4>(p, y, nrhs, ld, st);
+  if (nrhs >= 2) return launch_sparse_adj_rpw<T, COMP, 2>(p, y, nrhs, ld, st);
+  return launch_sparse_adj_rpw<T, COMP, 1>(p, y, nrhs, ld, st);
+}
+
+template <typename T, bool COMP>
+int apply_impl(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  if (!p->blocks.empty()) XC_TRY(launch_fft<T>(p, true, x, p->scratch, nrhs, ld, st));
+  return launch_sparse_fwd<T, COMP>(p, x, y, nrhs, ld, st);
+}
+
+template <typename T, bool COMP>
+int adjoint_impl(Plan* p, const void* y, void* x, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  if (!p->blocks.empty()) {
+    XC_TRY(launch_sparse_adj<T, COMP>(p, y, nrhs, ld, st));
+    XC_TRY(launch_fft<T>(p, false, p->scratch, x, nrhs, ld, st));
+  }
+  if (p->m_tail > 0) {
+    dim3 grid(unsigned((p->m_tail + 7) / 8), unsigned(nrhs));
+    launch_begin(p, K_ADJ_TAIL, st);
+    adj_tail_kernel<T, COMP><<<grid, 256, 0, st>>>(p->N, p->m_tail, static_cast<const T*>(p->tail),
+                                                   static_cast<const T*>(y), ld, static_cast<T*>(x),
+                                                   static_cast<const T*>(p->rowscale),
+                                                   static_cast<const T*>(p->colscale));
+    launch_end(p, K_ADJ_TAIL, st);
+    XC_CUDA(cudaGetLastError());
+  }
+  return XC_OK;
+}
+
+}  // namespace
+
+int ensure_scratch(Plan* p, int64_t nrhs) {
+  if (p->scratch_desc == nullptr) {
+    void* d = nullptr;
+    XC_TRY(plan_alloc(p, &d, std::max<size_t>(1, p->blocks.size()) * sizeof(BlockDev)));
+    if (!p->blocks.empty())
+      XC_CUDA(cudaMemcpy(d, p->blocks.data(), p->blocks.size() * sizeof(BlockDev), cudaMemcpyHostToDevice));
+    p->scratch_desc = d;
+  }
+  if (nrhs <= p->scratch_nrhs) return XC_OK;
+  const size_t cbytes = 2 * p->elem_bytes();
+  const size_t bytes = size_t(std::max<int64_t>(1, p->spec_per_rhs)) * size_t(nrhs) * cbytes;
+  void* fresh = nullptr;
+  if (cudaMalloc(&fresh, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(XC_ERR_ALLOC, "scratch allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  if (p->scratch) {
+    // a previous apply may still use the old buffer on its stream
+    cudaDeviceSynchronize();
+    cudaFree(p->scratch);
+  }
+  p->scratch = fresh;
+  p->scratch_nrhs = nrhs;
+  return XC_OK;
+}
+
+int launch_apply(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  XC_TRY(ensure_scratch(p, nrhs));
+  switch (p->precision) {
+    case XC_FP64: return apply_impl<double, false>(p, x, y, nrhs, ld, st);
+    case XC_FP32: return apply_impl<float, false>(p, x, y, nrhs, ld, st);
+    default: return apply_impl<float, true>(p, x, y, nrhs, ld, st);
+  }
+}
+
+int launch_apply_adjoint(Plan* p, const void* y, void* x, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  XC_TRY(ensure_scratch(p, nrhs));
+  switch (p->precision) {
+    case XC_FP64: return adjoint_impl<double, false>(p, y, x, nrhs, ld, st);
+    case XC_FP32: return adjoint_impl<float, false>(p, y, x, nrhs, ld, st);
+    default: return adjoint_impl<float, true>(p, y, x, nrhs, ld, st);
+  }
+}
+
+}  // namespace xc

@@ -1,0 +1,140 @@
+// Internal declarations of libxc: the plan, per-block descriptors passed to
+// kernels, and the error plumbing shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "xc.h"
+
+namespace xc {
+
+constexpr int kMaxPasses = 24;   // radix passes of one FFT (n <= 2^24)
+constexpr int kSlice = 32;       // rows (forward) or spectrum bins (adjoint) per band slice
+
+// Set the thread's last error message and return `code`.
+int fail(int code, const std::string& msg);
+// Map a CUDA status to XC_ERR_CUDA with context; XC_OK if cudaSuccess.
+int cuda_check(cudaError_t e, const char* what);
+
+#define XC_CUDA(...)                                                  \
+  do {                                                                \
+    int _rc = ::xc::cuda_check((__VA_ARGS__), #__VA_ARGS__);          \
+    if (_rc != XC_OK) return _rc;                                     \
+  } while (0)
+
+#define XC_TRY(...)                   \
+  do {                                \
+    int _rc = (__VA_ARGS__);          \
+    if (_rc != XC_OK) return _rc;     \
+  } while (0)
+
+// ------------------------------------------------------------ host parameters
+// (xc_params.cpp) The host side of the precomputation stage, step 1.1 of
+// Algorithms 1-4: zeta, the extra-component counts and the block schedule.
+double bessel_i0_host(double z);
+double kaiser_value_host(double j, int64_t length, double zeta);
+double zeta_of_eps_host(double eps1);
+bool is_fft_friendly(int64_t length);
+int64_t fft_friendly_at_least(int64_t length);
+// Factor n into radices 8, 4, 2, 3, 5, 7 (product == n); returns pass count or -1.
+int fft_radices(int64_t n, int* radix);
+
+struct BlockShape {
+  int64_t L, off, j_lo, j_hi;
+};
+struct Schedule {
+  double zeta = 0, eps_window = 0;
+  std::vector<BlockShape> blocks;
+  int64_t m_tail = 0;
+};
+int make_schedule(int64_t N, double eps, double eps2, bool two_sided, double eps_window,
+                  int tail_max, Schedule* out);
+
+// ----------------------------------------------------------- device descriptor
+// One block of the compressed operator as the apply kernels see it.  Value
+// pointers are untyped; the kernels cast them to the plan's precision.
+struct BlockDev {
+  int L, n, H;               // FFT length, n = L/2 complex points, H = n + 1 bins
+  int off, j_lo, j_hi;       // extended column j <-> matrix column j - off; input in [j_lo, j_hi)
+  int p;                     // radix passes
+  int radix[kMaxPasses];
+  const int* perm;           // [n] digit-reversed position of input index j
+  const void* tw;            // [L] complex exp(-2 pi i k / L), plan precision
+  const void* invw;          // [L] 1 / w_j^{zeta, L-1}, plan precision
+  // forward band layout: slices of 32 rows; row n reads bins [k0[n], k0[n] + width[slice])
+  int nslices;
+  const int* f_k0;           // [N]
+  const int* f_width;        // [nslices]
+  const int64_t* f_off;      // [nslices] element offset of the slice's values
+  const void* f_val;         // complex values, value (slice, j, lane) at f_off[s] + j*32 + lane
+  // adjoint band layout: slices of 32 bins; bin k reads rows [n0[k], n0[k] + width[slice])
+  int tslices;
+  const int* t_n0;           // [H]
+  const int* t_width;        // [tslices]
+  const int64_t* t_off;      // [tslices]
+  const void* t_val;
+  int64_t spec_off;          // offset (complex elements) of this block's spectrum per unit nrhs
+};
+
+// ------------------------------------------------------------------- the plan
+struct Plan {
+  int64_t N = 0;
+  int family = 0, precision = 0, scheme = 0, normalise = 0;
+  xc_params params{};
+  double eps = 0, eps2 = 0, zeta = 0;
+  Schedule sch;
+  std::vector<BlockDev> blocks;        // device descriptors (pointers into plan memory)
+  std::vector<int64_t> nnz, stored;
+  std::vector<double> maxabs;
+  int64_t m_tail = 0;
+  void* tail = nullptr;                // [m_tail][N] plan precision
+  void* rowscale = nullptr;            // [N] or null (raw)
+  void* colscale = nullptr;            // [N] or null (raw)
+  double* nodes_dev = nullptr;         // [N] FP64
+  std::vector<double> nodes_host;
+  int64_t spec_per_rhs = 0;            // complex elements of all blocks' spectra per RHS
+  int64_t max_n = 0;                   // largest n over blocks (shared memory of the FFTs)
+  int64_t matrix_bytes = 0, adjoint_bytes = 0;
+  // device copy of `blocks` (read by the kernels), scratch spectra, host-path staging
+  void* scratch_desc = nullptr;
+  void* scratch = nullptr;
+  int64_t scratch_nrhs = 0;
+  void* stage = nullptr;
+  int64_t stage_elems = 0;
+  std::vector<void*> allocations;      // everything cudaMalloc'ed for the plan
+  cudaStream_t last_stream = nullptr;
+  // per-kernel timing (xc_timing_enable)
+  bool timing = false;
+  struct Pending { int kernel; cudaEvent_t start, stop; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<int64_t> t_launches;
+  std::vector<double> t_ms;
+  size_t elem_bytes() const { return precision == XC_FP64 ? 8 : 4; }
+};
+
+// Device allocation recorded in the plan (freed by xc_plan_destroy).
+int plan_alloc(Plan* p, void** ptr, size_t bytes);
+
+// Kernel identities for the launch counter and the per-kernel timing.
+enum KernelId { K_FWD_FFT = 0, K_FWD_SPARSE, K_ADJ_SPARSE, K_ADJ_FFT, K_ADJ_TAIL, K_COUNT };
+const char* kernel_name(int id);
+// Bracket one launch: begin() before it, end() after it (counts the launch and,
+// when timing is on, records events on the stream).
+void launch_begin(Plan* p, int kernel, cudaStream_t s);
+void launch_end(Plan* p, int kernel, cudaStream_t s);
+
+// ------------------------------------------------------------------- kernels
+// (xc_plan.cu) precomputation
+int build_plan_device(Plan* p);
+int dense_matrix_device(const Plan* p, void* A, int64_t lda, cudaStream_t s);
+// (xc_apply.cu) execution
+int ensure_scratch(Plan* p, int64_t nrhs);
+int launch_apply(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t s);
+int launch_apply_adjoint(Plan* p, const void* y, void* x, int64_t nrhs, int64_t ld, cudaStream_t s);
+
+}  // namespace xc

@@ -1,0 +1,826 @@
+// Precomputation stage of Algorithms 1-4 on the device, in FP64:
+//   nodes (closed form, or Sturm bisection + Newton on the three-term
+//   recurrence), the Kaiser window and its reciprocal, FFT twiddles, the rows of
+//   the extended matrix A_e by recurrence (step 1.2), their real FFTs giving the
+//   compressed matrix A_e W F (eq. (A_comp), step 1.3), the per-block maximum,
+//   the threshold |a| > eps1 * max|A_e W F|, and the banded storage of the kept
+//   elements for the forward and the transposed (adjoint) product.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "xc_fft.cuh"
+#include "xc_internal.h"
+
+namespace xc {
+
+namespace {
+
+// ------------------------------------------------------- family evaluation
+struct GenParams {
+  int family;
+  int64_t N;
+  double alpha, beta;
+  const double* x;      // nodes
+  int cheb_exact;       // Chebyshev at x_n = cos((2n+1) pi / (2N)): exact angles
+};
+
+// exp(-a) for a >= 0 as mant * 2^expo, with the argument split
+// a = q ln2 - r (q integer, ln2 = hi + lo, q * hi exact) so that the result
+// keeps full relative accuracy even when exp(-a) is far below the FP64 range.
+// a_lo carries a low-order part of the argument (exact products).
+__device__ void exp_neg_split(double a_hi, double a_lo, double* mant, int* expo) {
+  const double ln2_hi = 0.6931471803691238;          // ln 2 to 32 significant bits
+  const double ln2_lo = 1.9082149292705877e-10;      // ln 2 - ln2_hi
+  const double inv_ln2 = 1.4426950408889634;
+  const double q = rint(a_hi * inv_ln2);
+  // exp(-a) = 2^{-q} exp(q ln2 - a)
+  const double r = ((q * ln2_hi - a_hi) + q * ln2_lo) - a_lo;
+  double m = exp(r);
+  int e2 = 0;
+  m = frexp(m, &e2);
+  *mant = m;
+  *expo = e2 - int(q);
+}
+
+// Emit phi_m(x_n) for m in [m_lo, m_hi) to `emit(m, value)` in increasing m.
+template <class F>
+__device__ void gen_values(const GenParams& g, int64_t n, int64_t m_lo, int64_t m_hi, F emit) {
+  const double x = g.x[n];
+  if (g.family == XC_CHEBYSHEV_T) {
+    if (g.cheb_exact) {
+      // angle = pi m (2n+1) / (2N); period 4N in m (2n+1)
+      const int64_t num = 2 * n + 1, per = 4 * g.N;
+      for (int64_t m = m_lo; m < m_hi; ++m) {
+        int64_t k = (m % per) * num % per;
+        if (k < 0) k += per;
+        if (k > per / 2) k = per - k;                  // cos is even: k in [0, 2N]
+        emit(m, cospi(double(k) / double(2 * g.N)));
+      }
+    } else {
+      const double th = acos(fmin(1.0, fmax(-1.0, x)));
+      for (int64_t m = m_lo; m < m_hi; ++m) emit(m, cos(double(m) * th));
+    }
+    return;
+  }
+  // one-sided families start at m = 0
+  if (g.family == XC_LEGENDRE || g.family == XC_JACOBI) {
+    const double a = g.family == XC_JACOBI ? g.alpha : 0.0;
+    const double b = g.family == XC_JACOBI ? g.beta : 0.0;
+    double pm1 = 1.0;
+    double p = (a + 1.0) + (a + b + 2.0) * (x - 1.0) * 0.5;
+    if (m_lo <= 0 && 0 < m_hi) emit(0, pm1);
+    if (m_lo <= 1 && 1 < m_hi) emit(1, p);
+    for (int64_t m = 1; m + 1 < m_hi; ++m) {
+      const double c = 2.0 * m + a + b;
+      const double a1 = 2.0 * (m + 1) * (m + a + b + 1) * c;
+      const double a2 = (c + 1) * (a * a - b * b);
+      const double a3 = c * (c + 1) * (c + 2);
+      const double a4 = 2.0 * (m + a) * (m + b) * (c + 2);
+      const double pn = ((a2 + a3 * x) * p - a4 * pm1) / a1;
+      pm1 = p;
+      p = pn;
+      if (m + 1 >= m_lo) emit(m + 1, p);
+    }
+    return;
+  }
+  // Laguerre / Hermite functions: scaled recurrence with a power-of-two exponent
+  double mant;
+  int expo;
+  double pm1, p;
+  if (g.family == XC_LAGUERRE_FN) {
+    exp_neg_split(0.5 * x, 0.0, &mant, &expo);           // exp(-x/2)
+    pm1 = mant;
+    p = (1.0 - x) * mant;
+  } else {
+    const double xx = x * x;
+    const double xx_lo = fma(x, x, -xx);                 // x^2 = xx + xx_lo exactly
+    exp_neg_split(0.5 * xx, 0.5 * xx_lo, &mant, &expo);  // exp(-x^2/2)
+    mant *= 0.7511255444649425;                          // pi^(-1/4)
+    pm1 = mant;
+    p = 1.4142135623730951 * x * mant;
+  }
+  if (m_lo <= 0 && 0 < m_hi) emit(0, ldexp(pm1, expo));
+  if (m_lo <= 1 && 1 < m_hi) emit(1, ldexp(p, expo));
+  for (int64_t m = 1; m + 1 < m_hi; ++m) {
+    double pn;
+    if (g.family == XC_LAGUERRE_FN)
+      pn = ((2.0 * m + 1.0 - x) * p - double(m) * pm1) / double(m + 1);
+    else
+      pn = sqrt(2.0 / double(m + 1)) * x * p - sqrt(double(m) / double(m + 1)) * pm1;
+    pm1 = p;
+    p = pn;
+    const double big = fmax(fabs(p), fabs(pm1));
+    if (big > 0x1p+500) {
+      p *= 0x1p-500;
+      pm1 *= 0x1p-500;
+      expo += 500;
+    } else if (big < 0x1p-500 && big > 0.0) {
+      p *= 0x1p+500;
+      pm1 *= 0x1p+500;
+      expo -= 500;
+    }
+    if (m + 1 >= m_lo) emit(m + 1, ldexp(p, expo));
+  }
+}
+
+// ---------------------------------------------------------------- nodes
+// Number of eigenvalues of the symmetric tridiagonal matrix (d, e) below lam
+// (Sturm count through the LDL^T pivots).
+__device__ int sturm_count(const double* d, const double* e2, int64_t N, double lam) {
+  int cnt = 0;
+  double q = d[0] - lam;
+  if (q == 0.0) q = -1e-300;
+  cnt += q < 0.0;
+  for (int64_t i = 1; i < N; ++i) {
+    q = (d[i] - lam) - e2[i - 1] / q;
+    if (q == 0.0) q = -1e-300;
+    cnt += q < 0.0;
+  }
+  return cnt;
+}
+
+__global__ void bisect_kernel(const double* d, const double* e2, int64_t N, double lo, double hi,
+                              double* out) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  double a = lo, b = hi;
+  for (int it = 0; it < 64; ++it) {
+    const double mid = 0.5 * (a + b);
+    if (mid <= a || mid >= b) break;
+    if (sturm_count(d, e2, N, mid) > k) b = mid;
+    else a = mid;
+  }
+  out[k] = 0.5 * (a + b);
+}
+
+// (p_N, p_{N-1}) at x by the family's recurrence; a common scale factor may
+// remain (it cancels in the Newton ratio).
+__device__ void last_two(int family, int64_t N, double a, double b, double x, double* pN, double* pN1) {
+  double pm1 = 1.0, p;
+  if (family == XC_LEGENDRE || family == XC_JACOBI) {
+    p = (a + 1.0) + (a + b + 2.0) * (x - 1.0) * 0.5;
+    for (int64_t m = 1; m < N; ++m) {
+      const double c = 2.0 * m + a + b;
+      const double pn = ((c + 1) * ((c + 2) * c * x + a * a - b * b) * p - 2.0 * (m + a) * (m + b) * (c + 2) * pm1) /
+                        (2.0 * (m + 1) * (m + a + b + 1) * c);
+      pm1 = p;
+      p = pn;
+    }
+  } else if (family == XC_LAGUERRE_FN) {
+    p = 1.0 - x;
+    for (int64_t m = 1; m < N; ++m) {
+      const double pn = ((2.0 * m + 1.0 - x) * p - double(m) * pm1) / double(m + 1);
+      pm1 = p;
+      p = pn;
+      if (fabs(p) > 0x1p+500) { p *= 0x1p-500; pm1 *= 0x1p-500; }
+    }
+  } else {
+    p = 1.4142135623730951 * x;
+    for (int64_t m = 1; m < N; ++m) {
+      const double pn = sqrt(2.0 / double(m + 1)) * x * p - sqrt(double(m) / double(m + 1)) * pm1;
+      pm1 = p;
+      p = pn;
+      if (fabs(p) > 0x1p+500) { p *= 0x1p-500; pm1 *= 0x1p-500; }
+    }
+  }
+  *pN = p;
+  *pN1 = pm1;
+}
+
+// phi_N / phi_N' from the derivative identities of each family.
+__device__ double newton_ratio(int family, int64_t N, double a, double b, double x) {
+  double pN, pN1;
+  last_two(family, N, a, b, x, &pN, &pN1);
+  double d;
+  if (family == XC_LEGENDRE || family == XC_JACOBI) {
+    const double c = 2.0 * N + a + b;
+    d = (double(N) * ((a - b) - c * x) * pN + 2.0 * (N + a) * (N + b) * pN1) / (c * (1.0 - x * x));
+  } else if (family == XC_LAGUERRE_FN) {
+    d = double(N) * (pN - pN1) / x;
+  } else {
+    d = sqrt(2.0 * double(N)) * pN1 - x * pN;
+  }
+  return pN / d;
+}
+
+__global__ void newton_kernel(int family, int64_t N, double a, double b, double* x) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  double v = x[k];
+  for (int it = 0; it < 3; ++it) v -= newton_ratio(family, N, a, b, v);
+  x[k] = v;
+}
+
+__global__ void cheb_nodes_kernel(int64_t N, double* x) {
+  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n < N) x[n] = cospi(double(2 * n + 1) / double(2 * N));
+}
+
+// Christoffel numbers times exp(x) / exp(x^2) for the Laguerre / Hermite
+// functions (the discrete inner product of the functions themselves).
+__global__ void weights_kernel(GenParams g, double* lam) {
+  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n >= g.N) return;
+  const double x = g.x[n];
+  const int64_t N = g.N;
+  if (g.family == XC_CHEBYSHEV_T) {
+    lam[n] = 3.141592653589793 / double(N);
+    return;
+  }
+  if (g.family == XC_LEGENDRE || g.family == XC_JACOBI) {
+    const double a = g.family == XC_JACOBI ? g.alpha : 0.0, b = g.family == XC_JACOBI ? g.beta : 0.0;
+    double pN, pN1;
+    last_two(g.family, N, a, b, x, &pN, &pN1);
+    const double c = 2.0 * N + a + b;
+    const double d = (double(N) * ((a - b) - c * x) * pN + 2.0 * (N + a) * (N + b) * pN1) / (c * (1.0 - x * x));
+    const double lg = lgamma(N + a + 1.0) + lgamma(N + b + 1.0) - lgamma(N + a + b + 1.0) - lgamma(N + 1.0) +
+                      (a + b + 1.0) * 0.6931471805599453;
+    lam[n] = exp(lg) / ((1.0 - x * x) * d * d);
+    return;
+  }
+  // functions: the needed value phi_{N+1} (Laguerre) or phi_{N-1} (Hermite)
+  const int64_t want = g.family == XC_LAGUERRE_FN ? N + 1 : N - 1;
+  double v = 0.0;
+  gen_values(g, n, want, want + 1, [&](int64_t, double val) { v = val; });
+  lam[n] = g.family == XC_LAGUERRE_FN ? x / ((N + 1.0) * (N + 1.0) * v * v) : 1.0 / (double(N) * v * v);
+}
+
+// rowscale = sqrt(lambda_n); colscale = 1/sqrt(chi_m) for the polynomials
+__global__ void scales_kernel(GenParams g, const double* lam, void* rowscale, void* colscale, int fp64) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  const double rs = sqrt(lam[i]);
+  double chi = 1.0;
+  const double m = double(i);
+  if (g.family == XC_CHEBYSHEV_T) {
+    chi = i == 0 ? 3.141592653589793 : 1.5707963267948966;
+  } else if (g.family == XC_LEGENDRE) {
+    chi = 2.0 / (2.0 * m + 1.0);
+  } else if (g.family == XC_JACOBI) {
+    const double a = g.alpha, b = g.beta;
+    double lg;
+    if (i == 0)
+      lg = (a + b + 1.0) * 0.6931471805599453 + lgamma(a + 1.0) + lgamma(b + 1.0) - lgamma(a + b + 2.0);
+    else
+      lg = (a + b + 1.0) * 0.6931471805599453 - log(2.0 * m + a + b + 1.0) + lgamma(m + a + 1.0) +
+           lgamma(m + b + 1.0) - lgamma(m + a + b + 1.0) - lgamma(m + 1.0);
+    chi = exp(lg);
+  }
+  const double cs = 1.0 / sqrt(chi);
+  if (fp64) {
+    static_cast<double*>(rowscale)[i] = rs;
+    static_cast<double*>(colscale)[i] = cs;
+  } else {
+    static_cast<float*>(rowscale)[i] = float(rs);
+    static_cast<float*>(colscale)[i] = float(cs);
+  }
+}
+
+// -------------------------------------------------- window, twiddles, tables
+__device__ double bessel_i0_dev(double z) {
+  const double q = 0.25 * z * z;
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 4000; ++k) {
+    term *= q / (double(k) * double(k));
+    sum += term;
+    if (term <= 1e-18 * sum) break;
+  }
+  return sum;
+}
+
+// w_j^{zeta, L-1} (FP64) and 1/w_j in the plan precision.
+template <typename T>
+__global__ void window_kernel(int64_t L, double zeta, double* w, T* invw) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= L) return;
+  const double t = 2.0 * double(j) / double(L - 1) - 1.0;
+  const double a = sqrt(fmax(0.0, 1.0 - t * t));
+  const double v = bessel_i0_dev(zeta * a) / bessel_i0_dev(zeta);
+  w[j] = v;
+  invw[j] = T(1.0 / v);
+}
+
+// exp(-2 pi i k / L), k < L, reduced to the first octant for accuracy.
+template <typename T>
+__global__ void twiddle_kernel(int64_t L, cx<T>* tw) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= L) return;
+  double s, c;
+  sincospi(2.0 * double(k) / double(L), &s, &c);
+  tw[k] = cx<T>{T(c), T(-s)};
+}
+
+// ------------------------------------------------------------ row spectra
+// G[j * C + c] = phi_{j - off}(x_{row0 + c}) * w_j for j < L (column-major
+// chunk of C rows).
+__global__ void gen_rows_kernel(GenParams g, int64_t row0, int64_t C, int64_t L, int64_t off,
+                                const double* w, double* G) {
+  const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c >= C || row0 + c >= g.N) return;
+  gen_values(g, row0 + c, -off, L - off, [&](int64_t m, double v) {
+    const int64_t j = m + off;
+    G[j * C + c] = v * w[j];
+  });
+}
+
+// One CTA per row of the chunk: real FFT of length L = 2n of the windowed row,
+// S[row][k] = U_k / L for k = 0..n, and the block maximum of |S|^2.
+__global__ void __launch_bounds__(256) row_fft_kernel(const double* G, int64_t C, int64_t row0, int64_t N,
+                                                      BlockDev b, const cx<double>* tw, cx<double>* S,
+                                                      unsigned long long* maxsq_bits) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<double>* s = reinterpret_cast<cx<double>*>(smem_raw);
+  __shared__ double red[8];
+  const int64_t c = blockIdx.x;
+  const int64_t row = row0 + c;
+  if (row >= N) return;
+  const int n = b.n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    s[b.perm[j]] = cx<double>{G[int64_t(2 * j) * C + c], G[int64_t(2 * j + 1) * C + c]};
+  __syncthreads();
+  fft_inplace<double>(s, n, b.p, b.radix, tw, threadIdx.x, blockDim.x);
+  const double scale = 1.0 / double(b.L);
+  cx<double>* out = S + row * int64_t(n + 1);
+  double local = 0.0;
+  for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
+    cx<double> Uk, Unk;
+    r2c_split(s, n, k, tw, &Uk, &Unk);
+    Uk = scal(scale, Uk);
+    Unk = scal(scale, Unk);
+    out[k] = Uk;
+    out[n - k] = Unk;
+    local = fmax(local, fmax(Uk.re * Uk.re + Uk.im * Uk.im, Unk.re * Unk.re + Unk.im * Unk.im));
+  }
+  for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
+    // non-negative doubles order like their bit patterns
+    atomicMax(maxsq_bits, static_cast<unsigned long long>(__double_as_longlong(m)));
+  }
+}
+
+__device__ __forceinline__ bool kept(cx<double> v, double thr) { return v.re * v.re + v.im * v.im > thr; }
+
+// One warp per row: first/last kept bin and the number of kept bins.
+__global__ void extents_kernel(const cx<double>* S, int64_t N, int64_t H, double thr, int* kfirst, int* klast,
+                               int* count) {
+  const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= N) return;
+  int lo = INT_MAX, hi = -1, cnt = 0;
+  for (int64_t k = lane; k < H; k += 32) {
+    if (kept(S[row * H + k], thr)) {
+      lo = min(lo, int(k));
+      hi = max(hi, int(k));
+      ++cnt;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  if (lane == 0) {
+    kfirst[row] = hi >= 0 ? lo : 0;
+    klast[row] = hi;
+    count[row] = cnt;
+  }
+}
+
+// Forward band values: slice s, position j, lane -> row 32 s + lane, bin
+// k0[row] + j; kept elements times g_k (2 inside the half spectrum, 1 at k = 0
+// and k = n), everything else zero.
+template <typename T>
+__global__ void fill_forward_kernel(const cx<double>* S, int64_t N, int n, double thr, const int* k0,
+                                    const int* width, const int64_t* off, int nslices, cx<T>* val) {
+  const int s = blockIdx.y;
+  if (s >= nslices) return;
+  const int W = width[s];
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;   // j * 32 + lane
+  if (idx >= int64_t(W) * 32) return;
+  const int lane = int(idx & 31);
+  const int j = int(idx >> 5);
+  const int64_t row = int64_t(s) * 32 + lane;
+  cx<double> v{0.0, 0.0};
+  if (row < N) {
+    const int k = k0[row] + j;
+    const cx<double> a = S[row * int64_t(n + 1) + k];
+    if (kept(a, thr)) v = scal((k == 0 || k == n) ? 1.0 : 2.0, a);
+  }
+  val[off[s] + idx] = cx<T>{T(v.re), T(v.im)};
+}
+
+// Transposed band values: slice s of bins, lane -> bin 32 s + lane, row n0[bin] + j.
+template <typename T>
+__global__ void fill_adjoint_kernel(const cx<double>* S, int64_t N, int n, double thr, const int* n0,
+                                    const int* width, const int64_t* off, int tslices, cx<T>* val) {
+  const int s = blockIdx.y;
+  if (s >= tslices) return;
+  const int W = width[s];
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(W) * 32) return;
+  const int lane = int(idx & 31);
+  const int j = int(idx >> 5);
+  const int64_t k = int64_t(s) * 32 + lane;
+  cx<double> v{0.0, 0.0};
+  if (k <= n) {
+    const int64_t row = n0[k] + j;
+    const cx<double> a = S[row * int64_t(n + 1) + k];
+    if (kept(a, thr)) v = a;
+  }
+  val[off[s] + idx] = cx<T>{T(v.re), T(v.im)};
+}
+
+// Dense tail [m][N] and the plain matrix (comparison path).
+template <typename T>
+__global__ void tail_kernel(GenParams g, int64_t m_tail, T* tail) {
+  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n >= g.N) return;
+  gen_values(g, n, 0, m_tail, [&](int64_t m, double v) { tail[m * g.N + n] = T(v); });
+}
+
+// 32 rows per CTA (one warp); each lane walks its row's recurrence once and
+// the values are staged through shared memory 32 columns at a time so that
+// every row of A is written contiguously.  Lanes past the last row evaluate
+// row N-1 without writing, keeping the warp in lockstep.
+template <typename T>
+__global__ void dense_kernel(GenParams g, const T* rowscale, const T* colscale, T* A, int64_t lda) {
+  __shared__ T tile[32][33];
+  const int64_t n0 = int64_t(blockIdx.x) * 32;
+  const int lane = threadIdx.x;
+  const int64_t N = g.N;
+  const int64_t n = n0 + lane < N ? n0 + lane : N - 1;
+  gen_values(g, n, 0, N, [&](int64_t m, double v) {
+    tile[lane][m & 31] = T(v);
+    if ((m & 31) == 31 || m == N - 1) {
+      __syncwarp();
+      const int64_t mb = m & ~int64_t(31);
+      for (int r = 0; r < 32; ++r) {
+        const int64_t row = n0 + r;
+        const int64_t col = mb + lane;
+        if (row < N && col <= m) {
+          T val = tile[r][lane];
+          if (rowscale) val = val * rowscale[row] * colscale[col];
+          A[row * lda + col] = val;
+        }
+      }
+      __syncwarp();
+    }
+  });
+}
+
+}  // namespace
+
+// The plain N x N matrix with the plan's normalisation (comparison path).
+int dense_matrix_device(const Plan* p, void* A, int64_t lda, cudaStream_t s) {
+  GenParams g{p->family, p->N, p->params.alpha, p->params.beta, p->nodes_dev,
+              p->family == XC_CHEBYSHEV_T && p->params.nodes == XC_NODES_GAUSS};
+  const unsigned grid = unsigned((p->N + 31) / 32);
+  if (p->precision == XC_FP64)
+    dense_kernel<double><<<grid, 32, 0, s>>>(g, static_cast<const double*>(p->rowscale),
+                                              static_cast<const double*>(p->colscale), static_cast<double*>(A), lda);
+  else
+    dense_kernel<float><<<grid, 32, 0, s>>>(g, static_cast<const float*>(p->rowscale),
+                                             static_cast<const float*>(p->colscale), static_cast<float*>(A), lda);
+  XC_CUDA(cudaGetLastError());
+  return XC_OK;
+}
+
+namespace {
+
+// Host helpers ----------------------------------------------------------------
+
+// Jacobi matrix of the family's monic recurrence (Golub-Welsch) for the Sturm
+// bisection; e2 holds the squared off-diagonals.
+void jacobi_matrix(int family, int64_t N, double a, double b, std::vector<double>* d, std::vector<double>* e2) {
+  d->assign(N, 0.0);
+  e2->assign(N > 1 ? N - 1 : 1, 0.0);
+  for (int64_t k = 0; k < N; ++k) {
+    const double kk = double(k);
+    if (family == XC_LEGENDRE) {
+      (*d)[k] = 0.0;
+      if (k >= 1) (*e2)[k - 1] = kk * kk / (4.0 * kk * kk - 1.0);
+    } else if (family == XC_JACOBI) {
+      const double c = 2.0 * kk + a + b;
+      (*d)[k] = k == 0 ? (b - a) / (a + b + 2.0) : (b * b - a * a) / (c * (c + 2.0));
+      if (k >= 1) (*e2)[k - 1] = 4.0 * kk * (kk + a) * (kk + b) * (kk + a + b) / (c * c * (c + 1.0) * (c - 1.0));
+    } else if (family == XC_LAGUERRE_FN) {
+      (*d)[k] = 2.0 * kk + 1.0;
+      if (k >= 1) (*e2)[k - 1] = kk * kk;
+    } else {
+      (*d)[k] = 0.0;
+      if (k >= 1) (*e2)[k - 1] = kk / 2.0;
+    }
+  }
+}
+
+// Digit-reversed position of each input index (see xc_fft.cuh).
+std::vector<int> digit_reversal(int n, int p, const int* radix) {
+  std::vector<int> perm(n);
+  for (int j = 0; j < n; ++j) {
+    int rem = j, pos = 0, mult = 1;
+    // j = t_p + r_p (t_{p-1} + r_{p-1} (...)); position = t_1 + r_1 (t_2 + ...)
+    std::vector<int> t(p);
+    for (int q = p - 1; q >= 0; --q) {
+      t[q] = rem % radix[q];
+      rem /= radix[q];
+    }
+    for (int q = 0; q < p; ++q) {
+      pos += t[q] * mult;
+      mult *= radix[q];
+    }
+    perm[j] = pos;
+  }
+  return perm;
+}
+
+template <typename T>
+int upload(Plan* p, const std::vector<T>& v, T** out) {
+  void* d = nullptr;
+  XC_TRY(plan_alloc(p, &d, std::max<size_t>(1, v.size()) * sizeof(T)));
+  if (!v.empty()) XC_CUDA(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = static_cast<T*>(d);
+  return XC_OK;
+}
+
+struct DevBuf {  // scratch freed at scope exit
+  void* ptr = nullptr;
+  ~DevBuf() {
+    if (ptr) cudaFree(ptr);
+  }
+};
+
+int alloc_tmp(DevBuf* b, size_t bytes) {
+  if (cudaMalloc(&b->ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b->ptr = nullptr;
+    return fail(XC_ERR_ALLOC, "temporary device allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  return XC_OK;
+}
+
+int set_smem(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) XC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+  return XC_OK;
+}
+
+template <typename T>
+int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
+  BlockDev& b = p->blocks[bi];
+  std::memset(&b, 0, sizeof(b));
+  const int64_t N = p->N;
+  b.L = int(shp.L);
+  b.n = int(shp.L / 2);
+  b.H = b.n + 1;
+  b.off = int(shp.off);
+  b.j_lo = int(shp.j_lo);
+  b.j_hi = int(shp.j_hi);
+  b.p = fft_radices(b.n, b.radix);
+  if (b.p < 0) return fail(XC_ERR_UNSUPPORTED, "FFT length not 2^a 3^b 5^c 7^d");
+  const int n = b.n, H = b.H;
+  const size_t smem = size_t(n) * sizeof(cx<double>);
+  int dev = 0, optin = 0;
+  XC_CUDA(cudaGetDevice(&dev));
+  XC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem + 1024 > size_t(optin))   // the row FFT also holds a small static reduction buffer
+    return fail(XC_ERR_UNSUPPORTED, "block length L = " + std::to_string(b.L) +
+                                        " exceeds the single-CTA FP64 FFT of the precompute");
+
+  // permutation, window, twiddles
+  std::vector<int> perm = digit_reversal(n, b.p, b.radix);
+  int* perm_d = nullptr;
+  XC_TRY(upload(p, perm, &perm_d));
+  b.perm = perm_d;
+  DevBuf w64;
+  XC_TRY(alloc_tmp(&w64, size_t(b.L) * sizeof(double)));
+  void *invw = nullptr, *tw = nullptr;
+  XC_TRY(plan_alloc(p, &invw, size_t(b.L) * sizeof(T)));
+  XC_TRY(plan_alloc(p, &tw, size_t(b.L) * sizeof(cx<T>)));
+  const unsigned gL = unsigned((b.L + 255) / 256);
+  window_kernel<T><<<gL, 256>>>(b.L, p->zeta, static_cast<double*>(w64.ptr), static_cast<T*>(invw));
+  twiddle_kernel<T><<<gL, 256>>>(b.L, static_cast<cx<T>*>(tw));
+  XC_CUDA(cudaGetLastError());
+  b.invw = invw;
+  b.tw = tw;
+  // FP64 twiddles for the precompute FFT
+  DevBuf tw64;
+  XC_TRY(alloc_tmp(&tw64, size_t(b.L) * sizeof(cx<double>)));
+  twiddle_kernel<double><<<gL, 256>>>(b.L, static_cast<cx<double>*>(tw64.ptr));
+  XC_CUDA(cudaGetLastError());
+
+  // compressed rows: S[N][H] FP64 complex
+  DevBuf Sbuf, maxbuf;
+  const size_t s_bytes = size_t(N) * size_t(H) * sizeof(cx<double>);
+  if (s_bytes > (size_t(64) << 30)) return fail(XC_ERR_UNSUPPORTED, "compressed block exceeds 64 GiB during precompute");
+  XC_TRY(alloc_tmp(&Sbuf, s_bytes));
+  XC_TRY(alloc_tmp(&maxbuf, sizeof(unsigned long long)));
+  XC_CUDA(cudaMemset(maxbuf.ptr, 0, sizeof(unsigned long long)));
+  int64_t C = std::max<int64_t>(1, std::min<int64_t>(N, (int64_t(1) << 30) / (int64_t(b.L) * 8)));
+  DevBuf Gbuf;
+  XC_TRY(alloc_tmp(&Gbuf, size_t(C) * size_t(b.L) * sizeof(double)));
+  XC_TRY(set_smem(reinterpret_cast<const void*>(row_fft_kernel), smem));
+  for (int64_t row0 = 0; row0 < N; row0 += C) {
+    const int64_t rows = std::min<int64_t>(C, N - row0);
+    gen_rows_kernel<<<unsigned((rows + 127) / 128), 128>>>(g, row0, C, b.L, b.off, static_cast<double*>(w64.ptr),
+                                                           static_cast<double*>(Gbuf.ptr));
+    row_fft_kernel<<<unsigned(rows), 256, smem>>>(static_cast<double*>(Gbuf.ptr), C, row0, N, b,
+                                                   static_cast<cx<double>*>(tw64.ptr),
+                                                   static_cast<cx<double>*>(Sbuf.ptr),
+                                                   static_cast<unsigned long long*>(maxbuf.ptr));
+    XC_CUDA(cudaGetLastError());
+  }
+  unsigned long long bits = 0;
+  XC_CUDA(cudaMemcpy(&bits, maxbuf.ptr, sizeof(bits), cudaMemcpyDeviceToHost));
+  double maxsq;
+  std::memcpy(&maxsq, &bits, sizeof(maxsq));
+  const double thr = p->eps > 0 ? (p->eps * p->eps) * maxsq : -1.0;
+  p->maxabs[bi] = std::sqrt(maxsq);
+
+  // extents of the kept elements per row
+  DevBuf kf, kl, cnt;
+  XC_TRY(alloc_tmp(&kf, size_t(N) * sizeof(int)));
+  XC_TRY(alloc_tmp(&kl, size_t(N) * sizeof(int)));
+  XC_TRY(alloc_tmp(&cnt, size_t(N) * sizeof(int)));
+  extents_kernel<<<unsigned((N * 32 + 255) / 256), 256>>>(static_cast<cx<double>*>(Sbuf.ptr), N, H, thr,
+                                                          static_cast<int*>(kf.ptr), static_cast<int*>(kl.ptr),
+                                                          static_cast<int*>(cnt.ptr));
+  XC_CUDA(cudaGetLastError());
+  std::vector<int> kfirst(N), klast(N), count(N);
+  XC_CUDA(cudaMemcpy(kfirst.data(), kf.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
+  XC_CUDA(cudaMemcpy(klast.data(), kl.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
+  XC_CUDA(cudaMemcpy(count.data(), cnt.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
+  int64_t nnz = 0;
+  for (int64_t r = 0; r < N; ++r) nnz += count[r];
+  p->nnz[bi] = nnz;
+
+  // forward layout: slices of 32 rows, width = widest band in the slice; the
+  // band start is moved left where needed so that k0 + width <= H
+  const int nslices = int((N + kSlice - 1) / kSlice);
+  std::vector<int> fwidth(nslices, 0), fk0(size_t(nslices) * kSlice, 0);
+  std::vector<int64_t> foff(nslices, 0);
+  int64_t total = 0;
+  for (int s = 0; s < nslices; ++s) {
+    int W = 0;
+    for (int l = 0; l < kSlice; ++l) {
+      const int64_t r = int64_t(s) * kSlice + l;
+      if (r < N && klast[r] >= 0) W = std::max(W, klast[r] - kfirst[r] + 1);
+    }
+    fwidth[s] = W;
+    for (int l = 0; l < kSlice; ++l) {
+      const int64_t r = int64_t(s) * kSlice + l;
+      fk0[size_t(s) * kSlice + l] = (r < N && klast[r] >= 0) ? std::min(kfirst[r], H - W) : 0;
+    }
+    foff[s] = total;
+    total += int64_t(W) * kSlice;
+  }
+  p->stored[bi] = total;
+  // adjoint layout: slices of 32 bins; bin k covers the rows whose band holds it
+  const int tslices = int((H + kSlice - 1) / kSlice);
+  std::vector<int> nlo(H, INT_MAX), nhi(H, -1);
+  for (int64_t r = 0; r < N; ++r)
+    for (int k = kfirst[r]; k <= klast[r]; ++k) {
+      nlo[k] = std::min<int>(nlo[k], int(r));
+      nhi[k] = std::max<int>(nhi[k], int(r));
+    }
+  std::vector<int> twidth(tslices, 0), tn0(size_t(tslices) * kSlice, 0);
+  std::vector<int64_t> toff(tslices, 0);
+  int64_t ttotal = 0;
+  for (int s = 0; s < tslices; ++s) {
+    int W = 0;
+    for (int l = 0; l < kSlice; ++l) {
+      const int64_t k = int64_t(s) * kSlice + l;
+      if (k < H && nhi[k] >= 0) W = std::max(W, nhi[k] - nlo[k] + 1);
+    }
+    twidth[s] = W;
+    for (int l = 0; l < kSlice; ++l) {
+      const int64_t k = int64_t(s) * kSlice + l;
+      tn0[size_t(s) * kSlice + l] = (k < H && nhi[k] >= 0) ? int(std::min<int64_t>(nlo[k], N - W)) : 0;
+    }
+    toff[s] = ttotal;
+    ttotal += int64_t(W) * kSlice;
+  }
+
+  int *fk0_d, *fw_d, *tn0_d, *tw_d;
+  int64_t *foff_d, *toff_d;
+  XC_TRY(upload(p, fk0, &fk0_d));
+  XC_TRY(upload(p, fwidth, &fw_d));
+  XC_TRY(upload(p, foff, &foff_d));
+  XC_TRY(upload(p, tn0, &tn0_d));
+  XC_TRY(upload(p, twidth, &tw_d));
+  XC_TRY(upload(p, toff, &toff_d));
+  void *fval = nullptr, *tval = nullptr;
+  XC_TRY(plan_alloc(p, &fval, size_t(std::max<int64_t>(total, 1)) * sizeof(cx<T>)));
+  XC_TRY(plan_alloc(p, &tval, size_t(std::max<int64_t>(ttotal, 1)) * sizeof(cx<T>)));
+  int maxW = 0, maxTW = 0;
+  for (int v : fwidth) maxW = std::max(maxW, v);
+  for (int v : twidth) maxTW = std::max(maxTW, v);
+  if (maxW > 0) {
+    dim3 grid(unsigned((int64_t(maxW) * kSlice + 255) / 256), unsigned(nslices));
+    fill_forward_kernel<T><<<grid, 256>>>(static_cast<cx<double>*>(Sbuf.ptr), N, n, thr, fk0_d, fw_d, foff_d,
+                                          nslices, static_cast<cx<T>*>(fval));
+  }
+  if (maxTW > 0) {
+    dim3 grid(unsigned((int64_t(maxTW) * kSlice + 255) / 256), unsigned(tslices));
+    fill_adjoint_kernel<T><<<grid, 256>>>(static_cast<cx<double>*>(Sbuf.ptr), N, n, thr, tn0_d, tw_d, toff_d,
+                                          tslices, static_cast<cx<T>*>(tval));
+  }
+  XC_CUDA(cudaGetLastError());
+  XC_CUDA(cudaDeviceSynchronize());
+  b.nslices = nslices;
+  b.f_k0 = fk0_d;
+  b.f_width = fw_d;
+  b.f_off = foff_d;
+  b.f_val = fval;
+  b.tslices = tslices;
+  b.t_n0 = tn0_d;
+  b.t_width = tw_d;
+  b.t_off = toff_d;
+  b.t_val = tval;
+  p->matrix_bytes += total * int64_t(sizeof(cx<T>)) + int64_t(N) * 4;
+  p->adjoint_bytes += ttotal * int64_t(sizeof(cx<T>)) + int64_t(H) * 4;
+  return XC_OK;
+}
+
+}  // namespace
+
+int build_plan_device(Plan* p) {
+  const int64_t N = p->N;
+  const unsigned gN = unsigned((N + 127) / 128);
+  XC_TRY(plan_alloc(p, reinterpret_cast<void**>(&p->nodes_dev), size_t(N) * sizeof(double)));
+  const bool user = p->params.nodes == XC_NODES_USER;
+  if (user) {
+    XC_CUDA(cudaMemcpy(p->nodes_dev, p->nodes_host.data(), size_t(N) * sizeof(double), cudaMemcpyHostToDevice));
+  } else if (p->family == XC_CHEBYSHEV_T) {
+    cheb_nodes_kernel<<<gN, 128>>>(N, p->nodes_dev);
+  } else {
+    std::vector<double> d, e2;
+    jacobi_matrix(p->family, N, p->params.alpha, p->params.beta, &d, &e2);
+    double lo = 1e300, hi = -1e300;  // Gershgorin interval
+    for (int64_t k = 0; k < N; ++k) {
+      const double r = (k > 0 ? std::sqrt(e2[k - 1]) : 0.0) + (k + 1 < N ? std::sqrt(e2[k]) : 0.0);
+      lo = std::min(lo, d[k] - r);
+      hi = std::max(hi, d[k] + r);
+    }
+    DevBuf dd, de;
+    XC_TRY(alloc_tmp(&dd, d.size() * sizeof(double)));
+    XC_TRY(alloc_tmp(&de, e2.size() * sizeof(double)));
+    XC_CUDA(cudaMemcpy(dd.ptr, d.data(), d.size() * sizeof(double), cudaMemcpyHostToDevice));
+    XC_CUDA(cudaMemcpy(de.ptr, e2.data(), e2.size() * sizeof(double), cudaMemcpyHostToDevice));
+    bisect_kernel<<<gN, 128>>>(static_cast<double*>(dd.ptr), static_cast<double*>(de.ptr), N, lo, hi, p->nodes_dev);
+    newton_kernel<<<gN, 128>>>(p->family, N, p->params.alpha, p->params.beta, p->nodes_dev);
+    XC_CUDA(cudaGetLastError());
+    XC_CUDA(cudaDeviceSynchronize());
+  }
+  XC_CUDA(cudaGetLastError());
+  p->nodes_host.resize(N);
+  XC_CUDA(cudaMemcpy(p->nodes_host.data(), p->nodes_dev, size_t(N) * sizeof(double), cudaMemcpyDeviceToHost));
+
+  GenParams g{p->family, N, p->params.alpha, p->params.beta, p->nodes_dev,
+              p->family == XC_CHEBYSHEV_T && !user};
+  const bool fp64 = p->precision == XC_FP64;
+  if (p->normalise == XC_ORTHONORMAL) {
+    DevBuf lam;
+    XC_TRY(alloc_tmp(&lam, size_t(N) * sizeof(double)));
+    XC_TRY(plan_alloc(p, &p->rowscale, size_t(N) * p->elem_bytes()));
+    XC_TRY(plan_alloc(p, &p->colscale, size_t(N) * p->elem_bytes()));
+    weights_kernel<<<gN, 128>>>(g, static_cast<double*>(lam.ptr));
+    scales_kernel<<<gN, 128>>>(g, static_cast<double*>(lam.ptr), p->rowscale, p->colscale, fp64 ? 1 : 0);
+    XC_CUDA(cudaGetLastError());
+    XC_CUDA(cudaDeviceSynchronize());
+  }
+
+  const int nb = int(p->sch.blocks.size());
+  p->blocks.resize(nb);
+  p->nnz.assign(nb, 0);
+  p->stored.assign(nb, 0);
+  p->maxabs.assign(nb, 0.0);
+  p->spec_per_rhs = 0;
+  p->max_n = 0;
+  for (int i = 0; i < nb; ++i) {
+    if (fp64) XC_TRY(build_block<double>(p, i, g, p->sch.blocks[i]));
+    else XC_TRY(build_block<float>(p, i, g, p->sch.blocks[i]));
+    p->blocks[i].spec_off = p->spec_per_rhs;
+    p->spec_per_rhs += p->blocks[i].H;
+    p->max_n = std::max<int64_t>(p->max_n, p->blocks[i].n);
+  }
+  p->m_tail = p->sch.m_tail;
+  if (p->m_tail > 0) {
+    XC_TRY(plan_alloc(p, &p->tail, size_t(p->m_tail) * size_t(N) * p->elem_bytes()));
+    if (fp64) tail_kernel<double><<<gN, 128>>>(g, p->m_tail, static_cast<double*>(p->tail));
+    else tail_kernel<float><<<gN, 128>>>(g, p->m_tail, static_cast<float*>(p->tail));
+    XC_CUDA(cudaGetLastError());
+    p->matrix_bytes += p->m_tail * N * int64_t(p->elem_bytes());
+  }
+  XC_CUDA(cudaDeviceSynchronize());
+  return XC_OK;
+}
+
+}  // namespace xc

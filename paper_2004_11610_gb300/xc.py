@@ -1,0 +1,277 @@
+"""ctypes binding of libxc (C ABI in include/xc.h).
+
+Argument marshalling only: every step of the apply runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current stream; raw device
+pointers and the stream handle are what cross the boundary.  Importing this
+module fails loudly when libxc.so has not been built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libxc.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libxc.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+# ------------------------------------------------------------------ constants
+XC_OK, XC_ERR_ARG, XC_ERR_ALLOC, XC_ERR_CUDA, XC_ERR_TIMEOUT, XC_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+FAMILY = {"chebyshev": 0, "legendre": 1, "jacobi": 2, "laguerre": 3, "hermite": 4}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32c": 2}
+SCHEME = {"auto": 0, "two_sided": 1, "blocks": 2}
+XC_MAX_BLOCKS = 16
+
+
+class xc_params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("nodes", ctypes.c_int),
+                ("user_nodes", ctypes.POINTER(ctypes.c_double)), ("normalise", ctypes.c_int),
+                ("eps2", ctypes.c_double), ("eps_window", ctypes.c_double), ("precision", ctypes.c_int),
+                ("scheme", ctypes.c_int), ("tail_max", ctypes.c_int)]
+
+
+_I64x = ctypes.c_int64 * XC_MAX_BLOCKS
+
+
+class xc_plan_stats(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("family", ctypes.c_int), ("precision", ctypes.c_int),
+                ("scheme", ctypes.c_int), ("normalise", ctypes.c_int), ("eps", ctypes.c_double),
+                ("eps2", ctypes.c_double), ("zeta", ctypes.c_double), ("nblocks", ctypes.c_int),
+                ("L", _I64x), ("off", _I64x), ("j_lo", _I64x), ("j_hi", _I64x), ("nnz", _I64x),
+                ("stored", _I64x), ("maxabs", ctypes.c_double * XC_MAX_BLOCKS), ("m_tail", ctypes.c_int64),
+                ("matrix_bytes", ctypes.c_int64), ("adjoint_bytes", ctypes.c_int64)]
+
+
+class xc_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIGS = {
+    "xc_params_default": (None, [ctypes.POINTER(xc_params)]),
+    "xc_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(xc_params), _I64,
+                                      ctypes.c_double]),
+    "xc_plan_destroy": (ctypes.c_int, [_P]),
+    "xc_plan_reserve": (ctypes.c_int, [_P, _I64]),
+    "xc_apply": (ctypes.c_int, [_P, _P, _P, _I64, _I64, _P]),
+    "xc_apply_adjoint": (ctypes.c_int, [_P, _P, _P, _I64, _I64, _P]),
+    "xc_apply_host": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _I64, _I64, _P]),
+    "xc_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(xc_plan_stats)]),
+    "xc_get_nodes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "xc_dense_matrix": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "xc_sync_status": (ctypes.c_int, [_P]),
+    "xc_timing_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "xc_timing_read": (ctypes.c_int, [_P, ctypes.POINTER(xc_kernel_time), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "xc_launch_count": (ctypes.c_int64, []),
+    "xc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "xc_last_error_message": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class XcError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.xc_last_error_message().decode(errors="replace")
+        super().__init__(f"{where}: {_lib.xc_strerror(code).decode()} ({code}): {msg}")
+        self.code = code
+
+
+def _check(code: int, where: str) -> None:
+    if code != XC_OK:
+        raise XcError(code, where)
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------- plans
+
+class Plan:
+    """A compressed operator for A[n, m] = phi_m(x_n) (xc_plan_create).
+
+    family     'chebyshev' | 'legendre' | 'jacobi' | 'laguerre' | 'hermite'
+    N          order of the square matrix
+    eps        eps1: threshold and Kaiser shape (0 keeps every element)
+    precision  'fp64' | 'fp32' | 'fp32c' (FP32 with compensated accumulation)
+    nodes      optional host array of N nodes (default: the family's Gauss nodes)
+    """
+
+    def __init__(self, family: str, N: int, eps: float, precision: str = "fp64", alpha: float = 0.0,
+                 beta: float = 0.0, nodes=None, normalise: bool = False, eps2: float = 0.0,
+                 eps_window: float = 0.0, scheme: str = "auto", tail_max: int = 0):
+        p = xc_params()
+        _lib.xc_params_default(ctypes.byref(p))
+        p.alpha, p.beta = float(alpha), float(beta)
+        self._nodes_keep = None
+        if nodes is not None:
+            arr = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64))
+            if arr.shape != (N,):
+                raise ValueError("nodes must have shape (N,)")
+            self._nodes_keep = arr
+            p.nodes = 1
+            p.user_nodes = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.normalise = 1 if normalise else 0
+        p.eps2, p.eps_window = float(eps2), float(eps_window)
+        p.precision = PRECISION[precision]
+        p.scheme = SCHEME[scheme]
+        p.tail_max = int(tail_max)
+        h = _P()
+        _check(_lib.xc_plan_create(ctypes.byref(h), FAMILY[family], ctypes.byref(p), int(N), float(eps)),
+               "xc_plan_create")
+        self._h = h
+        self.family, self.N, self.eps, self.precision = family, int(N), float(eps), precision
+        self.np_dtype = np.float64 if precision == "fp64" else np.float32
+
+    # -- lifetime
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.xc_plan_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    # -- queries
+    def info(self) -> dict:
+        st = xc_plan_stats()
+        _check(_lib.xc_plan_info(self._h, ctypes.byref(st)), "xc_plan_info")
+        nb = st.nblocks
+        return {
+            "N": st.N, "family": st.family, "precision": st.precision, "scheme": st.scheme,
+            "normalise": st.normalise, "eps": st.eps, "eps2": st.eps2, "zeta": st.zeta, "nblocks": nb,
+            "L": list(st.L[:nb]), "off": list(st.off[:nb]), "j_lo": list(st.j_lo[:nb]),
+            "j_hi": list(st.j_hi[:nb]), "nnz": list(st.nnz[:nb]), "stored": list(st.stored[:nb]),
+            "maxabs": list(st.maxabs[:nb]), "m_tail": st.m_tail, "matrix_bytes": st.matrix_bytes,
+            "adjoint_bytes": st.adjoint_bytes,
+        }
+
+    def nodes(self) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.float64)
+        _check(_lib.xc_get_nodes(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "xc_get_nodes")
+        return out
+
+    def reserve(self, nrhs: int) -> None:
+        _check(_lib.xc_plan_reserve(self._h, int(nrhs)), "xc_plan_reserve")
+
+    # -- device applies (torch tensors)
+    def _check_tensor(self, t, name):
+        import torch
+        if not t.is_cuda or t.dtype != self.torch_dtype:
+            raise TypeError(f"{name} must be a CUDA tensor of dtype {self.torch_dtype}")
+        if t.dim() != 2 or t.shape[1] != self.N or t.stride(1) != 1:
+            raise ValueError(f"{name} must have shape (nrhs, N) with unit column stride")
+        return t
+
+    def apply(self, x, out=None, stream=None):
+        """y = A x for x of shape (nrhs, N) (xc_apply)."""
+        import torch
+        x = self._check_tensor(x if x.dim() == 2 else x[None, :], "x")
+        y = torch.empty_like(x) if out is None else self._check_tensor(out, "out")
+        _check(_lib.xc_apply(self._h, _P(x.data_ptr()), _P(y.data_ptr()), x.shape[0], x.stride(0),
+                             _stream_handle(stream)), "xc_apply")
+        return y
+
+    def apply_adjoint(self, y, out=None, stream=None):
+        """x = A^T y for y of shape (nrhs, N) (xc_apply_adjoint)."""
+        import torch
+        y = self._check_tensor(y if y.dim() == 2 else y[None, :], "y")
+        x = torch.empty_like(y) if out is None else self._check_tensor(out, "out")
+        _check(_lib.xc_apply_adjoint(self._h, _P(y.data_ptr()), _P(x.data_ptr()), y.shape[0], y.stride(0),
+                                     _stream_handle(stream)), "xc_apply_adjoint")
+        return x
+
+    # -- host path
+    def apply_host(self, v, adjoint: bool = False, out=None, stream=None):
+        """Forward or adjoint apply on host arrays (xc_apply_host): copies in,
+        applies, copies out and synchronises."""
+        v = np.ascontiguousarray(v, dtype=self.np_dtype)
+        if v.ndim == 1:
+            v = v[None, :]
+        res = np.empty_like(v) if out is None else out
+        s = ctypes.c_void_p(0) if stream is None else _stream_handle(stream)
+        _check(_lib.xc_apply_host(self._h, 1 if adjoint else 0, _P(v.ctypes.data), _P(res.ctypes.data),
+                                  v.shape[0], v.shape[1], s), "xc_apply_host")
+        return res
+
+    def dense_matrix(self, stream=None):
+        """The plain N x N matrix on the device (xc_dense_matrix)."""
+        import torch
+        A = torch.empty((self.N, self.N), dtype=self.torch_dtype, device="cuda")
+        _check(_lib.xc_dense_matrix(self._h, _P(A.data_ptr()), self.N, _stream_handle(stream)),
+               "xc_dense_matrix")
+        return A
+
+    def timing_enable(self, enable: bool = True) -> None:
+        """Bracket every launch of this plan with CUDA events (xc_timing_enable)."""
+        _check(_lib.xc_timing_enable(self._h, 1 if enable else 0), "xc_timing_enable")
+
+    def timing_read(self) -> dict:
+        """{kernel name: (launches, total device ms)} since the last read (xc_timing_read)."""
+        arr = (xc_kernel_time * 16)()
+        n = ctypes.c_int()
+        _check(_lib.xc_timing_read(self._h, arr, 16, ctypes.byref(n)), "xc_timing_read")
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(n.value)}
+
+    def sync_status(self) -> None:
+        _check(_lib.xc_sync_status(self._h), "xc_sync_status")
+
+
+# ------------------------------------------------------------------- autograd
+
+def _autograd():
+    import torch
+
+    class XcApply(torch.autograd.Function):
+        """y = A x with dy/dx^T g = A^T g (the hand-written adjoint apply)."""
+
+        @staticmethod
+        def forward(ctx, x, plan):
+            ctx.plan = plan
+            return plan.apply(x.contiguous())
+
+        @staticmethod
+        def backward(ctx, g):
+            return ctx.plan.apply_adjoint(g.contiguous()), None
+
+    return XcApply
+
+
+def xc_launch_count() -> int:
+    """Kernels launched by libxc in this process (xc_launch_count)."""
+    return int(_lib.xc_launch_count())
+
+
+def xc_apply_autograd(x, plan: Plan):
+    """Differentiable y = A x (torch.autograd.Function with the adjoint apply as backward)."""
+    return _autograd().apply(x, plan)

@@ -1,0 +1,74 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/xc.h declares, and rejects invalid arguments before
+touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "xc.h")
+
+
+@pytest.fixture(scope="module")
+def xc():
+    from paper_2004_11610_gb300 import build
+    build.build()
+    from paper_2004_11610_gb300 import xc as mod
+    return mod
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(xc_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("xc_plan_create", "xc_apply", "xc_apply_adjoint", "xc_plan_destroy", "xc_plan_info",
+                     "xc_get_nodes", "xc_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(xc):
+    lib = ctypes.CDLL(xc._LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(declared_functions()) == set(xc.EXPORTED)
+
+
+def test_invalid_arguments_are_rejected_on_the_host(xc):
+    h = ctypes.c_void_p()
+    p = xc.xc_params()
+    xc._lib.xc_params_default(ctypes.byref(p))
+    create = xc._lib.xc_plan_create
+    assert create(ctypes.byref(h), 99, ctypes.byref(p), 64, 1e-8) == xc.XC_ERR_ARG
+    assert create(ctypes.byref(h), 1, ctypes.byref(p), 1, 1e-8) == xc.XC_ERR_ARG
+    assert create(ctypes.byref(h), 1, ctypes.byref(p), 64, -1.0) == xc.XC_ERR_ARG
+    assert create(ctypes.byref(h), 1, ctypes.byref(p), 64, 1.5) == xc.XC_ERR_ARG
+    assert create(None, 1, ctypes.byref(p), 64, 1e-8) == xc.XC_ERR_ARG
+    p.precision = 7
+    assert create(ctypes.byref(h), 1, ctypes.byref(p), 64, 1e-8) == xc.XC_ERR_ARG
+    xc._lib.xc_params_default(ctypes.byref(p))
+    p.nodes = 1      # user nodes without a pointer
+    assert create(ctypes.byref(h), 1, ctypes.byref(p), 64, 1e-8) == xc.XC_ERR_ARG
+    xc._lib.xc_params_default(ctypes.byref(p))
+    p.alpha = -1.5
+    assert create(ctypes.byref(h), 2, ctypes.byref(p), 64, 1e-8) == xc.XC_ERR_ARG
+    xc._lib.xc_params_default(ctypes.byref(p))
+    p.scheme = 1     # two-sided needs the Chebyshev family
+    assert create(ctypes.byref(h), 1, ctypes.byref(p), 64, 1e-8) == xc.XC_ERR_ARG
+    assert not h.value
+    msg = xc._lib.xc_last_error_message().decode()
+    assert "two-sided" in msg
+    assert xc._lib.xc_apply(None, None, None, 1, 64, None) == xc.XC_ERR_ARG
+    assert xc._lib.xc_strerror(xc.XC_ERR_TIMEOUT) == b"device wait timed out"
+
+
+def test_structure_layouts_match_the_header(xc):
+    # offsets fixed by the C layout of include/xc.h (LP64)
+    assert ctypes.sizeof(xc.xc_params) == 72
+    assert xc.xc_plan_stats.L.offset == 56
+    assert ctypes.sizeof(xc.xc_plan_stats) == 56 + 7 * 8 * 16 + 24

@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Both sides build the plan independently from the same nodes: the Chebyshev
+family uses its exact Chebyshev-Gauss angles on both sides; the other families
+hand the oracle's Gauss nodes to the library as user nodes, so the matrices are
+defined at identical FP64 points (the library's own Gauss nodes are checked
+separately against the oracle's).
+
+Tolerances (relative to max |y|, elementwise):
+  FP64   the two sides round differently in the FFT (u log2 L relative to the
+         largest input, amplified by up to 1/eps2 through W^{-1}) and in the band
+         sums; elements within rounding of the threshold may be kept on one side
+         and dropped on the other, each such flip moving an output by about
+         eps1 max|A_e W F| |v| -- so tol = 64 u log2(L) / eps2 + 10 eps.
+  FP32   the FFT rounding of Section 2.2's W^{-1}-amplified input dominates:
+         relative l2 <= max(10 eps, 1e-5) against the FP64 oracle method.
+"""
+import functools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import families as F
+from oracle import method as M
+from paper_2004_11610_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def xc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2004_11610_gb300 import build
+    build.build()
+    from paper_2004_11610_gb300 import xc as mod
+    return mod
+
+
+def spec_for(fam, N, alpha=0.5, beta=-0.5):
+    return F.make_spec(fam, N, alpha, beta) if fam == "jacobi" else F.make_spec(fam, N)
+
+
+@functools.lru_cache(maxsize=32)
+def oracle_plan(fam, N, eps, eps2, normalise=False, scheme="auto", alpha=0.5, beta=-0.5):
+    sp = spec_for(fam, N, alpha, beta)
+    two = None if scheme == "auto" else scheme == "two_sided"
+    return M.build(sp, eps, eps2=eps2, normalise=normalise, two_sided=two)
+
+
+def gpu_plan(xc, fam, N, eps, precision, eps2, normalise=False, scheme="auto", alpha=0.5, beta=-0.5):
+    ora = oracle_plan(fam, N, eps, eps2, normalise, scheme, alpha, beta)
+    nodes = None if fam == "chebyshev" or normalise else ora.spec.x
+    return ora, xc.Plan(fam, N, eps, precision=precision, alpha=alpha, beta=beta, nodes=nodes,
+                        normalise=normalise, eps2=eps2, scheme=scheme)
+
+
+def fp64_tol(ora, eps):
+    Lmax = max([b.L for b in ora.blocks] + [8])
+    return 64 * U64 * math.log2(Lmax) / ora.schedule.eps2 + 10 * eps
+
+
+def check_schedule(ora, plan):
+    info = plan.info()
+    assert info["L"] == [b.L for b in ora.schedule.blocks]
+    assert info["j_lo"] == [b.j_lo for b in ora.schedule.blocks]
+    assert info["j_hi"] == [b.j_hi for b in ora.schedule.blocks]
+    assert info["off"] == [b.off for b in ora.schedule.blocks]
+    assert info["m_tail"] == ora.schedule.m_tail
+    assert info["zeta"] == pytest.approx(ora.schedule.zeta, rel=1e-13)
+    for nnz, b in zip(info["nnz"], ora.blocks):
+        total = int(b.nnz_half.sum())
+        assert abs(nnz - total) <= max(2, total // 1000)
+    return info
+
+
+def run_both(xc, plan, ora, X, adjoint=False):
+    dt = torch.float64 if plan.precision == "fp64" else torch.float32
+    Xd = torch.from_numpy(X).to("cuda", dt)
+    out = plan.apply_adjoint(Xd) if adjoint else plan.apply(Xd)
+    torch.cuda.synchronize()
+    plan.sync_status()
+    ref = M.apply_adjoint(ora, X) if adjoint else M.apply(ora, X)
+    return out.double().cpu().numpy(), ref
+
+
+def max_rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+CASES_FP64 = [
+    ("legendre", 512, 1e-14), ("legendre", 333, 1e-10), ("chebyshev", 256, 1e-12), ("chebyshev", 301, 1e-8),
+    ("jacobi", 400, 1e-10), ("laguerre", 256, 1e-10), ("hermite", 200, 1e-10), ("legendre", 97, 0.0),
+    ("chebyshev", 64, 0.0),
+]
+
+
+@pytest.mark.parametrize("fam,N,eps", CASES_FP64)
+@pytest.mark.parametrize("nrhs", [1, 3, 9])
+def test_fp64_forward_and_adjoint_match_oracle(xc, fam, N, eps, nrhs):
+    ora, plan = gpu_plan(xc, fam, N, eps, "fp64", 1e-3)
+    with plan:
+        check_schedule(ora, plan)
+        X = inputs.uniform_pm1(N, nrhs, 11)
+        y, y_ref = run_both(xc, plan, ora, X)
+        tol = fp64_tol(ora, eps)
+        assert max_rel(y, y_ref) <= tol
+        Y = inputs.normal(N, nrhs, 12)
+        xa, xa_ref = run_both(xc, plan, ora, Y, adjoint=True)
+        assert max_rel(xa, xa_ref) <= tol
+
+
+@pytest.mark.parametrize("fam,N,eps", [("legendre", 700, 1e-7), ("jacobi", 515, 1e-7), ("chebyshev", 640, 1e-7),
+                                       ("hermite", 300, 1e-7)])
+@pytest.mark.parametrize("precision", ["fp32", "fp32c"])
+def test_fp32_paths_match_oracle(xc, fam, N, eps, precision):
+    ora, plan = gpu_plan(xc, fam, N, eps, precision, 3e-2)
+    with plan:
+        check_schedule(ora, plan)
+        X = inputs.uniform_pm1(N, 17, 21)
+        y, y_ref = run_both(xc, plan, ora, X)
+        assert M.rel_l2(y, y_ref) <= max(10 * eps, 1e-5)
+        xa, xa_ref = run_both(xc, plan, ora, X, adjoint=True)
+        assert M.rel_l2(xa, xa_ref) <= max(10 * eps, 1e-5)
+
+
+def test_orthonormal_and_block_scheme_variants(xc):
+    ora, plan = gpu_plan(xc, "legendre", 256, 1e-12, "fp64", 1e-3, normalise=True)
+    with plan:
+        X = inputs.normal(256, 4, 31)
+        y, y_ref = run_both(xc, plan, ora, X)
+        assert max_rel(y, y_ref) <= fp64_tol(ora, 1e-12)
+        xa, xa_ref = run_both(xc, plan, ora, X, adjoint=True)
+        assert max_rel(xa, xa_ref) <= fp64_tol(ora, 1e-12)
+    ora, plan = gpu_plan(xc, "chebyshev", 200, 1e-10, "fp64", 1e-3, scheme="blocks")
+    with plan:
+        check_schedule(ora, plan)
+        X = inputs.normal(200, 2, 32)
+        y, y_ref = run_both(xc, plan, ora, X)
+        assert max_rel(y, y_ref) <= fp64_tol(ora, 1e-10)
+
+
+@pytest.mark.parametrize("N", [2, 3, 8, 20, 21, 33])
+def test_tiny_and_dense_only_plans(xc, N):
+    """N <= tail_max: no compressed block, the whole product is the dense tail."""
+    for fam in ("legendre", "chebyshev"):
+        ora, plan = gpu_plan(xc, fam, N, 1e-10, "fp64", 1e-3)
+        with plan:
+            check_schedule(ora, plan)
+            X = inputs.uniform_pm1(N, 2, 41)
+            y, y_ref = run_both(xc, plan, ora, X)
+            assert max_rel(y, y_ref) <= fp64_tol(ora, 1e-10)
+            xa, xa_ref = run_both(xc, plan, ora, X, adjoint=True)
+            assert max_rel(xa, xa_ref) <= fp64_tol(ora, 1e-10)
+
+
+def test_gauss_nodes_match_oracle(xc):
+    for fam, N in (("legendre", 1000), ("jacobi", 777), ("laguerre", 500), ("hermite", 600), ("chebyshev", 300)):
+        sp = spec_for(fam, N)
+        with xc.Plan(fam, N, 1e-8, alpha=0.5, beta=-0.5) as plan:
+            x = plan.nodes()
+        tol = 4 * N * U64 * (1 + np.abs(sp.x))
+        assert np.all(np.abs(x - sp.x) <= tol), fam
+
+
+def test_leading_dimension_and_host_path(xc):
+    ora, plan = gpu_plan(xc, "legendre", 300, 1e-10, "fp64", 1e-3)
+    with plan:
+        X = inputs.uniform_pm1(300, 5, 51)
+        big = torch.zeros((5, 320), dtype=torch.float64, device="cuda")
+        big[:, :300] = torch.from_numpy(X).cuda()
+        out = torch.full((5, 320), 7.0, dtype=torch.float64, device="cuda")
+        import ctypes
+        rc = xc._lib.xc_apply(plan.handle, ctypes.c_void_p(big.data_ptr()), ctypes.c_void_p(out.data_ptr()), 5, 320,
+                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 0
+        torch.cuda.synchronize()
+        y_ref = M.apply(ora, X)
+        o = out.cpu().numpy()
+        assert max_rel(o[:, :300], y_ref) <= fp64_tol(ora, 1e-10)
+        assert np.all(o[:, 300:] == 7.0)           # padding untouched
+        yh = plan.apply_host(X)
+        assert max_rel(yh, y_ref) <= fp64_tol(ora, 1e-10)
+        xh = plan.apply_host(X, adjoint=True)
+        assert max_rel(xh, M.apply_adjoint(ora, X)) <= fp64_tol(ora, 1e-10)
+
+
+def test_dense_matrix_matches_oracle(xc):
+    for fam, N, norm in (("legendre", 200, False), ("chebyshev", 150, False), ("laguerre", 180, False),
+                         ("hermite", 160, True), ("jacobi", 170, True)):
+        sp = spec_for(fam, N)
+        A_ref = F.dense_matrix(sp, normalise=norm)
+        nodes = None if (fam == "chebyshev" or norm) else sp.x
+        with xc.Plan(fam, N, 1e-8, alpha=0.5, beta=-0.5, nodes=nodes, normalise=norm) as plan:
+            A = plan.dense_matrix().cpu().numpy()
+        tol = 1e-12 if not norm else 1e-10
+        assert np.abs(A - A_ref).max() <= tol * np.abs(A_ref).max(), fam
+
+
+@pytest.mark.parametrize("fam", ["legendre", "chebyshev", "laguerre"])
+def test_adjoint_is_the_exact_transpose_on_gpu(xc, fam):
+    """<A x, y> = <x, A^T y> for the GPU operator itself (any size)."""
+    N = 1500
+    with xc.Plan(fam, N, 1e-9) as plan:
+        g = np.random.default_rng(7)
+        X = torch.from_numpy(g.standard_normal((4, N))).cuda()
+        Y = torch.from_numpy(g.standard_normal((4, N))).cuda()
+        Ax = plan.apply(X)
+        Aty = plan.apply_adjoint(Y)
+        lhs = (Ax * Y).sum(dim=1)
+        rhs = (X * Aty).sum(dim=1)
+        scale = (Ax * Y).abs().sum(dim=1)
+        assert torch.all((lhs - rhs).abs() <= 1e-12 * scale)
+
+
+def test_invalid_calls_return_errors(xc):
+    import ctypes
+    with xc.Plan("legendre", 64, 1e-8) as plan:
+        x = torch.zeros((2, 64), dtype=torch.float64, device="cuda")
+        st = ctypes.c_void_p(0)
+        assert xc._lib.xc_apply(plan.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), 2, 64,
+                                st) == xc.XC_ERR_ARG
+        y = torch.zeros_like(x)
+        assert xc._lib.xc_apply(plan.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), 2, 10,
+                                st) == xc.XC_ERR_ARG
+        assert xc._lib.xc_apply(plan.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), 0, 64,
+                                st) == xc.XC_OK
