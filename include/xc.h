@@ -135,6 +135,34 @@ int xc_apply(xc_plan_t plan, const void* x_dev, void* y_dev, int64_t nrhs, int64
 int xc_apply_adjoint(xc_plan_t plan, const void* y_dev, void* x_dev, int64_t nrhs, int64_t ld, void* stream);
 
 /*
+ * xc_apply_noalloc -- the same y = A x as xc_apply, for callers that must not
+ * allocate device memory: code running where cudaMalloc is forbidden or
+ * unsafe (inside a memory-pool-managed runtime that owns every allocation,
+ * real-time paths where an allocation could stall, or hosts that budget
+ * device memory up front).  The paper has no counterpart; this is an
+ * interface convenience of the library.
+ *
+ * The spectra that xc_apply keeps in the plan's scratch are placed instead in
+ * one fixed device array inside the library, XC_NOALLOC_SCRATCH_BYTES large,
+ * which every GPU that loads the library holds until the process exits.  The
+ * call allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ * routine.  It needs (sum over blocks of L_i/2 + 1) * nrhs complex elements
+ * of the plan's precision; larger requests return XC_ERR_UNSUPPORTED before
+ * anything is launched (split the right-hand sides into several calls).
+ *   - The first call on a device looks up that device's address of the array
+ *     (once per device, with the device current); make that first call before
+ *     any stream capture on the device.
+ *   - All calls share the one array and it keeps the last call's contents.
+ *     Every element a call reads was written earlier in the same call, so
+ *     nothing needs clearing, but calls that overlap on the GPU (different
+ *     streams, or different plans at the same time) race on the array: order
+ *     them, e.g. on one stream.
+ * Arguments as for xc_apply.
+ */
+#define XC_NOALLOC_SCRATCH_BYTES (16ll << 20)
+int xc_apply_noalloc(xc_plan_t plan, const void* x_dev, void* y_dev, int64_t nrhs, int64_t ld, void* stream);
+
+/*
  * xc_apply_host -- end-to-end forward or adjoint apply on HOST buffers:
  * copies the input to the device, applies, copies the result back and
  * synchronises the stream.  adjoint = 0: out = A in; adjoint = 1: out = A^T in.

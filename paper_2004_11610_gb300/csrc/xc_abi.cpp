@@ -49,6 +49,8 @@ const char* kernel_name(int id) {
   return (id >= 0 && id < K_COUNT) ? names[id] : "unknown";
 }
 
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 static cudaEvent_t take_event(Plan* p) {
   if (!p->event_pool.empty()) {
     cudaEvent_t e = p->event_pool.back();
@@ -201,6 +203,14 @@ int xc_apply_adjoint(xc_plan_t plan, const void* y_dev, void* x_dev, int64_t nrh
   if (nrhs == 0) return XC_OK;
   p->last_stream = static_cast<cudaStream_t>(stream);
   return xc::launch_apply_adjoint(p, y_dev, x_dev, nrhs, ld, static_cast<cudaStream_t>(stream));
+}
+
+int xc_apply_noalloc(xc_plan_t plan, const void* x_dev, void* y_dev, int64_t nrhs, int64_t ld, void* stream) {
+  auto* p = reinterpret_cast<xc::Plan*>(plan);
+  XC_TRY(xc::validate_vectors(p, x_dev, y_dev, nrhs, ld));
+  if (nrhs == 0) return XC_OK;
+  p->last_stream = static_cast<cudaStream_t>(stream);
+  return xc::launch_apply_noalloc(p, x_dev, y_dev, nrhs, ld, static_cast<cudaStream_t>(stream));
 }
 
 int xc_apply_host(xc_plan_t plan, int adjoint, const void* in_host, void* out_host, int64_t nrhs, int64_t ld,

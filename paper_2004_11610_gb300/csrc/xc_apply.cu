@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "xc_fft.cuh"
 #include "xc_internal.h"
@@ -359,6 +360,86 @@ int adjoint_impl(Plan* p, const void* y, void* x, int64_t nrhs, int64_t ld, cuda
 }
 
 }  // namespace
+
+// ------------------------------------------------------ allocation-free apply
+// Spectrum scratch for xc_apply_noalloc: one fixed array in device memory,
+// shared by every call on a device.  Host code must not use the symbol's
+// host-side name as a device address; the device address is looked up once
+// per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[XC_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (set up on the
+// first call per device).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  XC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(XC_ERR_UNSUPPORTED, "device index beyond 64");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || ptr == nullptr) {
+      cudaGetLastError();
+      return fail(XC_ERR_CUDA, std::string("cudaGetSymbolAddress of the no-alloc scratch failed: ") +
+                                   cudaGetErrorString(e));
+    }
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return XC_OK;
+}
+
+template <typename T, bool COMP>
+int apply_noalloc_impl(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st, void* spec) {
+  const BlockDev* bd = static_cast<const BlockDev*>(p->scratch_desc);
+  if (!p->blocks.empty()) {
+    const size_t smem = size_t(p->max_n) * sizeof(cx<T>);
+    if (smem > 48 * 1024)
+      XC_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(fwd_fft_kernel<T>),
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    dim3 grid(unsigned(nrhs), unsigned(p->blocks.size()));
+    count_launch();
+    fwd_fft_kernel<T><<<grid, kFftThreads, smem, st>>>(bd, static_cast<const T*>(x), ld,
+                                                        static_cast<const T*>(p->colscale),
+                                                        static_cast<cx<T>*>(spec), nrhs);
+    XC_CUDA(cudaGetLastError());
+  }
+  constexpr int RPW = 8;
+  const int64_t nslices = (p->N + 31) / 32;
+  dim3 grid(unsigned((nslices + kSparseWarps - 1) / kSparseWarps), unsigned((nrhs + RPW - 1) / RPW));
+  count_launch();
+  fwd_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
+      bd, int(p->blocks.size()), p->N, static_cast<const T*>(x), ld, static_cast<T*>(y),
+      static_cast<const cx<T>*>(spec), nrhs, static_cast<const T*>(p->rowscale),
+      static_cast<const T*>(p->colscale), static_cast<const T*>(p->tail), p->m_tail);
+  XC_CUDA(cudaGetLastError());
+  return XC_OK;
+}
+
+}  // namespace
+
+int launch_apply_noalloc(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  const double need = double(p->spec_per_rhs) * double(nrhs) * double(2 * p->elem_bytes());
+  if (need > double(XC_NOALLOC_SCRATCH_BYTES))
+    return fail(XC_ERR_UNSUPPORTED, "xc_apply_noalloc needs " + std::to_string(int64_t(need)) +
+                                        " bytes of spectrum scratch, above its fixed " +
+                                        std::to_string(int64_t(XC_NOALLOC_SCRATCH_BYTES)) +
+                                        "-byte array; split the right-hand sides");
+  if (p->scratch_desc == nullptr) return fail(XC_ERR_ARG, "plan has no device descriptors");
+  void* spec = nullptr;
+  XC_TRY(noalloc_scratch(&spec));
+  switch (p->precision) {
+    case XC_FP64: return apply_noalloc_impl<double, false>(p, x, y, nrhs, ld, st, spec);
+    case XC_FP32: return apply_noalloc_impl<float, false>(p, x, y, nrhs, ld, st, spec);
+    default: return apply_noalloc_impl<float, true>(p, x, y, nrhs, ld, st, spec);
+  }
+}
 
 int ensure_scratch(Plan* p, int64_t nrhs) {
   if (p->scratch_desc == nullptr) {

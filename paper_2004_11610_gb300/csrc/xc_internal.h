@@ -127,6 +127,10 @@ const char* kernel_name(int id);
 // when timing is on, records events on the stream).
 void launch_begin(Plan* p, int kernel, cudaStream_t s);
 void launch_end(Plan* p, int kernel, cudaStream_t s);
+// Count one launch without any event work (used by the allocation-free apply).
+void count_launch();
+// The allocation-free forward apply (xc_apply.cu).
+int launch_apply_noalloc(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t s);
 
 // ------------------------------------------------------------------- kernels
 // (xc_plan.cu) precomputation

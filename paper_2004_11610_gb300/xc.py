@@ -60,6 +60,7 @@ _SIGS = {
     "xc_apply": (ctypes.c_int, [_P, _P, _P, _I64, _I64, _P]),
     "xc_apply_adjoint": (ctypes.c_int, [_P, _P, _P, _I64, _I64, _P]),
     "xc_apply_host": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _I64, _I64, _P]),
+    "xc_apply_noalloc": (ctypes.c_int, [_P, _P, _P, _I64, _I64, _P]),
     "xc_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(xc_plan_stats)]),
     "xc_get_nodes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "xc_dense_matrix": (ctypes.c_int, [_P, _P, _I64, _P]),
@@ -210,6 +211,16 @@ class Plan:
         _check(_lib.xc_apply_adjoint(self._h, _P(y.data_ptr()), _P(x.data_ptr()), y.shape[0], y.stride(0),
                                      _stream_handle(stream)), "xc_apply_adjoint")
         return x
+
+    def apply_noalloc(self, x, out, stream=None):
+        """y = A x without any device allocation (xc_apply_noalloc): the
+        spectra go to the library's fixed device array instead of the plan's
+        scratch.  `out` must be supplied; calls must not overlap on the GPU."""
+        x = self._check_tensor(x, "x")
+        out = self._check_tensor(out, "out")
+        _check(_lib.xc_apply_noalloc(self._h, _P(x.data_ptr()), _P(out.data_ptr()), x.shape[0], x.stride(0),
+                                     _stream_handle(stream)), "xc_apply_noalloc")
+        return out
 
     # -- host path
     def apply_host(self, v, adjoint: bool = False, out=None, stream=None):
