@@ -90,9 +90,30 @@ __global__ void __launch_bounds__(kFftThreads)
   }
 }
 
+// ------------------------------------------------------- work distribution
+// The sparse kernels run a persistent grid (every CTA resident).  Each warp
+// takes items -- (slice, group of RPW right-hand sides) -- from a device
+// counter, longest slices first, until the list is exhausted; the last warp to
+// finish resets the counter pair for the next launch.  This keeps all SMs busy
+// to the end even though band widths differ from slice to slice.
+__device__ __forceinline__ int64_t take_item(unsigned* next, int lane) {
+  unsigned t = 0;
+  if (lane == 0) t = atomicAdd(next, 1u);
+  return int64_t(__shfl_sync(0xffffffffu, t, 0));
+}
+
+__device__ __forceinline__ void retire_warp(unsigned* next, unsigned* done, unsigned total_warps, int lane) {
+  if (lane == 0) {
+    __threadfence();                              // this warp's last take precedes its retirement
+    if (atomicAdd(done, 1u) == total_warps - 1) {
+      atomicExch(next, 0u);
+      atomicExch(done, 0u);
+    }
+  }
+}
+
 // ------------------------------------------------------- forward sparse
-// Warp w of the CTA owns the 32-row slice 4*blockIdx.x + w and the RHS group
-// [RPW*blockIdx.y, RPW*blockIdx.y + RPW).  Lane = row.  Each band value is
+// Item = (32-row slice, RPW right-hand sides); lane = row.  Each band value is
 // loaded once (coalesced across the slice) and used for the RPW right-hand
 // sides; the spectra are gathered through L1.
 template <typename T, int RPW, bool COMP>
@@ -100,103 +121,139 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
     fwd_sparse_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N, const T* __restrict__ x,
                       int64_t ld, T* __restrict__ y, const cx<T>* __restrict__ spec, int64_t nrhs,
                       const T* __restrict__ rowscale, const T* __restrict__ colscale, const T* __restrict__ tail,
-                      int64_t m_tail) {
+                      int64_t m_tail, const int* __restrict__ order, unsigned* counters) {
   const int lane = threadIdx.x & 31;
-  const int64_t slice = int64_t(blockIdx.x) * kSparseWarps + (threadIdx.x >> 5);
-  const int64_t nslices = (N + 31) / 32;
-  if (slice >= nslices) return;
-  const int64_t n = slice * 32 + lane;
-  const int64_t r0 = int64_t(blockIdx.y) * RPW;
-  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
-  Acc<T, COMP> acc[RPW];
-  for (int i = 0; i < nblocks; ++i) {
-    const BlockDev& b = blocks[i];
-    const int W = b.f_width[slice];
-    const int k0 = b.f_k0[n];
-    const int H = b.H;
-    const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.f_val) + b.f_off[slice] + lane;
-    const cx<T>* __restrict__ F = spec + b.spec_off * nrhs + r0 * H + k0;
-    if (nq == RPW) {
-      for (int j = 0; j < W; ++j) {
-        const cx<T> c = val[j * 32];
+  const int64_t ngroups = (nrhs + RPW - 1) / RPW;
+  const int64_t total = ((N + 31) / 32) * ngroups;
+  for (;;) {
+    const int64_t t = take_item(&counters[0], lane);
+    if (t >= total) break;
+    const int64_t slice = order[t / ngroups];
+    const int64_t r0 = (t % ngroups) * RPW;
+    const int64_t n = slice * 32 + lane;
+    const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
+    Acc<T, COMP> acc[RPW];
+    for (int i = 0; i < nblocks; ++i) {
+      const BlockDev& b = blocks[i];
+      const int W = b.f_width[slice];
+      const int k0 = b.f_k0[n];
+      const int H = b.H;
+      const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.f_val) + b.f_off[slice] + lane;
+      const cx<T>* __restrict__ F = spec + b.spec_off * nrhs + r0 * H + k0;
+      if (nq == RPW) {
+#pragma unroll 4
+        for (int j = 0; j < W; ++j) {
+          const cx<T> c = val[j * 32];
 #pragma unroll
-        for (int q = 0; q < RPW; ++q) {
-          const cx<T> f = F[q * H + j];
-          acc[q].add(c.re, f.re);
-          acc[q].add(c.im, f.im);
-        }
-      }
-    } else {
-      for (int j = 0; j < W; ++j) {
-        const cx<T> c = val[j * 32];
-#pragma unroll
-        for (int q = 0; q < RPW; ++q) {
-          if (q < nq) {
+          for (int q = 0; q < RPW; ++q) {
             const cx<T> f = F[q * H + j];
             acc[q].add(c.re, f.re);
             acc[q].add(c.im, f.im);
           }
         }
+      } else {
+        for (int j = 0; j < W; ++j) {
+          const cx<T> c = val[j * 32];
+#pragma unroll
+          for (int q = 0; q < RPW; ++q) {
+            if (q < nq) {
+              const cx<T> f = F[q * H + j];
+              acc[q].add(c.re, f.re);
+              acc[q].add(c.im, f.im);
+            }
+          }
+        }
       }
     }
-  }
-  if (n >= N) return;
-  for (int64_t m = 0; m < m_tail; ++m) {
-    const T t = tail[m * N + n];
-    const T cs = colscale ? colscale[m] : T(1);
+    if (n < N) {
+      for (int64_t m = 0; m < m_tail; ++m) {
+        const T tv = tail[m * N + n];
+        const T cs = colscale ? colscale[m] : T(1);
 #pragma unroll
-    for (int q = 0; q < RPW; ++q)
-      if (q < nq) acc[q].add(t, x[(r0 + q) * ld + m] * cs);
-  }
-  const T rs = rowscale ? rowscale[n] : T(1);
+        for (int q = 0; q < RPW; ++q)
+          if (q < nq) acc[q].add(tv, x[(r0 + q) * ld + m] * cs);
+      }
+      const T rs = rowscale ? rowscale[n] : T(1);
 #pragma unroll
-  for (int q = 0; q < RPW; ++q)
-    if (q < nq) y[(r0 + q) * ld + n] = acc[q].value() * rs;
+      for (int q = 0; q < RPW; ++q)
+        if (q < nq) y[(r0 + q) * ld + n] = acc[q].value() * rs;
+    }
+  }
+  retire_warp(&counters[0], &counters[1], gridDim.x * kSparseWarps, lane);
 }
 
 // ------------------------------------------------------- adjoint sparse
-// Warp = 32-bin slice of one block (slices of all blocks enumerated in
-// order); lane = bin k; z_k = sum_j CT[j][k] y[n0_k + j].
+// Item = (32-bin slice of one block -- slices of all blocks enumerated in
+// block order --, RPW right-hand sides); lane = bin k;
+// z_k = sum_j CT[j][k] y[n0_k + j].
 template <typename T, int RPW, bool COMP>
 __global__ void __launch_bounds__(32 * kSparseWarps)
     adj_sparse_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t total_tslices, int64_t N,
                       const T* __restrict__ y, int64_t ld, cx<T>* __restrict__ spec, int64_t nrhs,
-                      const T* __restrict__ rowscale) {
+                      const T* __restrict__ rowscale, const int* __restrict__ order, unsigned* counters) {
   const int lane = threadIdx.x & 31;
-  int64_t g = int64_t(blockIdx.x) * kSparseWarps + (threadIdx.x >> 5);
-  if (g >= total_tslices) return;
-  int i = 0;
-  while (i < nblocks - 1 && g >= blocks[i].tslices) {
-    g -= blocks[i].tslices;
-    ++i;
-  }
-  const BlockDev& b = blocks[i];
-  const int64_t k = g * 32 + lane;
-  const int H = b.H;
-  const int W = b.t_width[g];
-  const int n0 = b.t_n0[k];
-  const int64_t r0 = int64_t(blockIdx.y) * RPW;
-  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
-  const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.t_val) + b.t_off[g] + lane;
-  Acc<T, COMP> re[RPW], im[RPW];
-  for (int j = 0; j < W; ++j) {
-    const cx<T> c = val[j * 32];
-    const int64_t row = n0 + j;
-    const T rs = rowscale ? rowscale[row] : T(1);
+  const int64_t ngroups = (nrhs + RPW - 1) / RPW;
+  const int64_t total = total_tslices * ngroups;
+  for (;;) {
+    const int64_t t = take_item(&counters[2], lane);
+    if (t >= total) break;
+    int64_t g = order[t / ngroups];
+    const int64_t r0 = (t % ngroups) * RPW;
+    int i = 0;
+    while (i < nblocks - 1 && g >= blocks[i].tslices) {
+      g -= blocks[i].tslices;
+      ++i;
+    }
+    const BlockDev& b = blocks[i];
+    const int64_t k = g * 32 + lane;
+    const int H = b.H;
+    const int W = b.t_width[g];
+    const int n0 = b.t_n0[k];
+    const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
+    const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.t_val) + b.t_off[g] + lane;
+    Acc<T, COMP> re[RPW], im[RPW];
+#pragma unroll 4
+    for (int j = 0; j < W; ++j) {
+      const cx<T> c = val[j * 32];
+      const int64_t row = n0 + j;
+      const T rs = rowscale ? rowscale[row] : T(1);
 #pragma unroll
-    for (int q = 0; q < RPW; ++q) {
-      if (q < nq) {
-        const T v = y[(r0 + q) * ld + row] * rs;
-        re[q].add(c.re, v);
-        im[q].add(c.im, v);
+      for (int q = 0; q < RPW; ++q) {
+        if (q < nq) {
+          const T v = y[(r0 + q) * ld + row] * rs;
+          re[q].add(c.re, v);
+          im[q].add(c.im, v);
+        }
       }
     }
-  }
-  if (k >= H) return;
-  cx<T>* out = spec + b.spec_off * nrhs + r0 * H + k;
+    if (k < H) {
+      cx<T>* out = spec + b.spec_off * nrhs + r0 * H + k;
 #pragma unroll
-  for (int q = 0; q < RPW; ++q)
-    if (q < nq) out[q * H] = cx<T>{re[q].value(), im[q].value()};
+      for (int q = 0; q < RPW; ++q)
+        if (q < nq) out[q * H] = cx<T>{re[q].value(), im[q].value()};
+    }
+  }
+  retire_warp(&counters[2], &counters[3], gridDim.x * kSparseWarps, lane);
+}
+
+// Persistent grid: as many CTAs as can be resident, but no more than the
+// items need.
+int persistent_grid(const void* fn, int64_t items, unsigned* grid) {
+  static thread_local int cached_sms = 0;
+  if (cached_sms == 0) {
+    int dev = 0;
+    XC_CUDA(cudaGetDevice(&dev));
+    XC_CUDA(cudaDeviceGetAttribute(&cached_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  int per_sm = 0;
+  XC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * kSparseWarps, 0));
+  if (per_sm < 1) per_sm = 1;
+  // every resident warp takes part (warps that find the list empty retire at
+  // once); the dynamic schedule balances SMs and their schedulers
+  const int64_t need = (items + kSparseWarps - 1) / kSparseWarps;
+  const int64_t g = std::min<int64_t>(int64_t(cached_sms) * per_sm, std::max<int64_t>(1, need));
+  *grid = unsigned(g);
+  return XC_OK;
 }
 
 // ------------------------------------------------------------ adjoint FFT
@@ -291,13 +348,14 @@ int launch_fft(Plan* p, bool forward, const void* in, void* out, int64_t nrhs, i
 
 template <typename T, bool COMP, int RPW>
 int launch_sparse_fwd_rpw(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
-  const int64_t nslices = (p->N + 31) / 32;
-  dim3 grid(unsigned((nslices + kSparseWarps - 1) / kSparseWarps), unsigned((nrhs + RPW - 1) / RPW));
+  const void* fn = reinterpret_cast<const void*>(fwd_sparse_kernel<T, RPW, COMP>);
+  unsigned grid = 1;
+  XC_TRY(persistent_grid(fn, p->nslices * ((nrhs + RPW - 1) / RPW), &grid));
   launch_begin(p, K_FWD_SPARSE, st);
   fwd_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
       static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->N, static_cast<const T*>(x), ld,
       static_cast<T*>(y), static_cast<const cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale),
-      static_cast<const T*>(p->colscale), static_cast<const T*>(p->tail), p->m_tail);
+      static_cast<const T*>(p->colscale), static_cast<const T*>(p->tail), p->m_tail, p->f_order, p->counters);
   launch_end(p, K_FWD_SPARSE, st);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
@@ -305,21 +363,26 @@ int launch_sparse_fwd_rpw(Plan* p, const void* x, void* y, int64_t nrhs, int64_t
 
 template <typename T, bool COMP, int RPW>
 int launch_sparse_adj_rpw(Plan* p, const void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
-  int64_t total = 0;
-  for (const BlockDev& b : p->blocks) total += b.tslices;
-  if (total == 0) return XC_OK;
-  dim3 grid(unsigned((total + kSparseWarps - 1) / kSparseWarps), unsigned((nrhs + RPW - 1) / RPW));
+  if (p->total_tslices == 0) return XC_OK;
+  const void* fn = reinterpret_cast<const void*>(adj_sparse_kernel<T, RPW, COMP>);
+  unsigned grid = 1;
+  XC_TRY(persistent_grid(fn, p->total_tslices * ((nrhs + RPW - 1) / RPW), &grid));
   launch_begin(p, K_ADJ_SPARSE, st);
   adj_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
-      static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), total, p->N, static_cast<const T*>(y),
-      ld, static_cast<cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale));
+      static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->total_tslices, p->N,
+      static_cast<const T*>(y), ld, static_cast<cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale),
+      p->t_order, p->counters);
   launch_end(p, K_ADJ_SPARSE, st);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
 }
 
+// Right-hand sides per item: FP64 is bound by the FP64 pipe, where reusing a
+// band value over more right-hand sides buys nothing and finer items balance
+// better; FP32 needs the reuse.
 template <typename T, bool COMP>
 int launch_sparse_fwd(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  if (sizeof(T) == 8 && nrhs >= 2) return launch_sparse_fwd_rpw<T, COMP, 2>(p, x, y, nrhs, ld, st);
   if (nrhs >= 8) return launch_sparse_fwd_rpw<T, COMP, 8>(p, x, y, nrhs, ld, st);
   if (nrhs >= 4) return launch_sparse_fwd_rpw<T, COMP, 4>(p, x, y, nrhs, ld, st);
   if (nrhs >= 2) return launch_sparse_fwd_rpw<T, COMP, 2>(p, x, y, nrhs, ld, st);
@@ -328,6 +391,7 @@ int launch_sparse_fwd(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld,
 
 template <typename T, bool COMP>
 int launch_sparse_adj(Plan* p, const void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  if (sizeof(T) == 8 && nrhs >= 2) return launch_sparse_adj_rpw<T, COMP, 2>(p, y, nrhs, ld, st);
   if (nrhs >= 8) return launch_sparse_adj_rpw<T, COMP, 8>(p, y, nrhs, ld, st);
   if (nrhs >= 4) return launch_sparse_adj_rpw<T, COMP, 4>(p, y, nrhs, ld, st);
   if (nrhs >= 2) return launch_sparse_adj_rpw<T, COMP, 2>(p, y, nrhs, ld, st);
@@ -411,13 +475,14 @@ int apply_noalloc_impl(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld
     XC_CUDA(cudaGetLastError());
   }
   constexpr int RPW = 8;
-  const int64_t nslices = (p->N + 31) / 32;
-  dim3 grid(unsigned((nslices + kSparseWarps - 1) / kSparseWarps), unsigned((nrhs + RPW - 1) / RPW));
+  unsigned grid = 1;
+  XC_TRY(persistent_grid(reinterpret_cast<const void*>(fwd_sparse_kernel<T, RPW, COMP>),
+                         p->nslices * ((nrhs + RPW - 1) / RPW), &grid));
   count_launch();
   fwd_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
       bd, int(p->blocks.size()), p->N, static_cast<const T*>(x), ld, static_cast<T*>(y),
       static_cast<const cx<T>*>(spec), nrhs, static_cast<const T*>(p->rowscale),
-      static_cast<const T*>(p->colscale), static_cast<const T*>(p->tail), p->m_tail);
+      static_cast<const T*>(p->colscale), static_cast<const T*>(p->tail), p->m_tail, p->f_order, p->counters);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
 }

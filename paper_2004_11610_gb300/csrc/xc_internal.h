@@ -96,6 +96,12 @@ struct Plan {
   void* colscale = nullptr;            // [N] or null (raw)
   double* nodes_dev = nullptr;         // [N] FP64
   std::vector<double> nodes_host;
+  // work lists of the sparse kernels, longest item first: forward = row slices
+  // (cost = summed band widths over blocks), adjoint = bin slices of all blocks
+  int* f_order = nullptr;              // [nslices]
+  int* t_order = nullptr;              // [total tslices], global slice index
+  int64_t nslices = 0, total_tslices = 0;
+  unsigned* counters = nullptr;        // [4]: {next, done} for the forward and the adjoint sparse kernel
   int64_t spec_per_rhs = 0;            // complex elements of all blocks' spectra per RHS
   int64_t max_n = 0;                   // largest n over blocks (shared memory of the FFTs)
   int64_t matrix_bytes = 0, adjoint_bytes = 0;

@@ -811,6 +811,33 @@ int build_plan_device(Plan* p) {
     p->spec_per_rhs += p->blocks[i].H;
     p->max_n = std::max<int64_t>(p->max_n, p->blocks[i].n);
   }
+  // work lists for the sparse kernels (longest first); widths come back from the device
+  p->nslices = (N + kSlice - 1) / kSlice;
+  std::vector<int64_t> fcost(p->nslices, 0);
+  std::vector<std::pair<int64_t, int>> tcost;
+  int64_t gbase = 0;
+  for (int i = 0; i < nb; ++i) {
+    std::vector<int> w(p->blocks[i].nslices), tw(p->blocks[i].tslices);
+    XC_CUDA(cudaMemcpy(w.data(), p->blocks[i].f_width, w.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    XC_CUDA(cudaMemcpy(tw.data(), p->blocks[i].t_width, tw.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (size_t s2 = 0; s2 < w.size(); ++s2) fcost[s2] += w[s2];
+    for (size_t s2 = 0; s2 < tw.size(); ++s2) tcost.push_back({tw[s2], int(gbase + int64_t(s2))});
+    gbase += int64_t(tw.size());
+  }
+  p->total_tslices = gbase;
+  std::vector<int> forder(p->nslices);
+  for (int64_t s2 = 0; s2 < p->nslices; ++s2) forder[s2] = int(s2);
+  std::stable_sort(forder.begin(), forder.end(), [&](int a, int b) { return fcost[a] > fcost[b]; });
+  std::stable_sort(tcost.begin(), tcost.end(), [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) {
+    return a.first > b.first;
+  });
+  std::vector<int> torder(tcost.size());
+  for (size_t k = 0; k < tcost.size(); ++k) torder[k] = tcost[k].second;
+  XC_TRY(upload(p, forder, &p->f_order));
+  XC_TRY(upload(p, torder, &p->t_order));
+  XC_TRY(plan_alloc(p, reinterpret_cast<void**>(&p->counters), 4 * sizeof(unsigned)));
+  XC_CUDA(cudaMemset(p->counters, 0, 4 * sizeof(unsigned)));
+
   p->m_tail = p->sch.m_tail;
   if (p->m_tail > 0) {
     XC_TRY(plan_alloc(p, &p->tail, size_t(p->m_tail) * size_t(N) * p->elem_bytes()));
