@@ -183,37 +183,41 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
 }
 
 // ------------------------------------------------------- adjoint sparse
-// Item = (32-bin slice of one block -- slices of all blocks enumerated in
-// block order --, RPW right-hand sides); lane = bin k;
-// z_k = sum_j CT[j][k] y[n0_k + j].
+// Item = (chunk of up to kAdjChunk rows of a 32-bin slice of one block, RPW
+// right-hand sides); lane = bin k.  The chunk's partial sum
+// sum_j CT[j][k] y[n0_k + j] goes to part[chunk][rhs][lane]; the adjoint FFT
+// adds the chunks of each bin in chunk order (deterministic, no atomics).
+// Chunking keeps bins that are covered by thousands of rows (the small last
+// blocks, high frequencies of the Laguerre functions) from becoming one long
+// serial loop.
 template <typename T, int RPW, bool COMP>
 __global__ void __launch_bounds__(32 * kSparseWarps)
-    adj_sparse_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t total_tslices, int64_t N,
-                      const T* __restrict__ y, int64_t ld, cx<T>* __restrict__ spec, int64_t nrhs,
-                      const T* __restrict__ rowscale, const int* __restrict__ order, unsigned* counters) {
+    adj_sparse_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N, const T* __restrict__ y,
+                      int64_t ld, cx<T>* __restrict__ part, int64_t nrhs, const T* __restrict__ rowscale,
+                      const int2* __restrict__ items, const int* __restrict__ cbase, int64_t total_chunks,
+                      unsigned* counters) {
   const int lane = threadIdx.x & 31;
   const int64_t ngroups = (nrhs + RPW - 1) / RPW;
-  const int64_t total = total_tslices * ngroups;
+  const int64_t total = total_chunks * ngroups;
   for (;;) {
     const int64_t t = take_item(&counters[2], lane);
     if (t >= total) break;
-    int64_t g = order[t / ngroups];
+    const int2 it = items[t / ngroups];
     const int64_t r0 = (t % ngroups) * RPW;
     int i = 0;
-    while (i < nblocks - 1 && g >= blocks[i].tslices) {
-      g -= blocks[i].tslices;
-      ++i;
-    }
+    while (i < nblocks - 1 && it.x >= blocks[i].t_gbase + blocks[i].tslices) ++i;
     const BlockDev& b = blocks[i];
-    const int64_t k = g * 32 + lane;
-    const int H = b.H;
-    const int W = b.t_width[g];
+    const int gl = it.x - b.t_gbase;
+    const int64_t k = int64_t(gl) * 32 + lane;
+    const int W = b.t_width[gl];
+    const int j0 = it.y * kAdjChunk;
+    const int j1 = min(W, j0 + kAdjChunk);
     const int n0 = b.t_n0[k];
     const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
-    const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.t_val) + b.t_off[g] + lane;
+    const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.t_val) + b.t_off[gl] + lane;
     Acc<T, COMP> re[RPW], im[RPW];
 #pragma unroll 4
-    for (int j = 0; j < W; ++j) {
+    for (int j = j0; j < j1; ++j) {
       const cx<T> c = val[j * 32];
       const int64_t row = n0 + j;
       const T rs = rowscale ? rowscale[row] : T(1);
@@ -226,12 +230,10 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
         }
       }
     }
-    if (k < H) {
-      cx<T>* out = spec + b.spec_off * nrhs + r0 * H + k;
+    cx<T>* out = part + ((int64_t(cbase[it.x]) + it.y) * nrhs + r0) * 32 + lane;
 #pragma unroll
-      for (int q = 0; q < RPW; ++q)
-        if (q < nq) out[q * H] = cx<T>{re[q].value(), im[q].value()};
-    }
+    for (int q = 0; q < RPW; ++q)
+      if (q < nq) out[q * 32] = cx<T>{re[q].value(), im[q].value()};
   }
   retire_warp(&counters[2], &counters[3], gridDim.x * kSparseWarps, lane);
 }
@@ -257,10 +259,21 @@ int persistent_grid(const void* fn, int64_t items, unsigned* grid) {
 }
 
 // ------------------------------------------------------------ adjoint FFT
+// Sum of the chunk partials of bin k of this block for right-hand side r.
+template <typename T>
+__device__ __forceinline__ cx<T> gather_bin(const cx<T>* __restrict__ part, const int* __restrict__ cbase,
+                                            int gbase, int k, int64_t r, int64_t nrhs) {
+  const int g = gbase + (k >> 5);
+  const int c0 = cbase[g], c1 = cbase[g + 1];
+  cx<T> u{T(0), T(0)};
+  for (int c = c0; c < c1; ++c) u = u + part[(int64_t(c) * nrhs + r) * 32 + (k & 31)];
+  return u;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
-    adj_fft_kernel(const BlockDev* __restrict__ blocks, const cx<T>* __restrict__ spec, int64_t nrhs,
-                   T* __restrict__ x, int64_t ld, const T* __restrict__ colscale) {
+    adj_fft_kernel(const BlockDev* __restrict__ blocks, const cx<T>* __restrict__ part, const int* __restrict__ cbase,
+                   int64_t nrhs, T* __restrict__ x, int64_t ld, const T* __restrict__ colscale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   const BlockDev& b = blocks[blockIdx.y];
@@ -269,9 +282,9 @@ __global__ void __launch_bounds__(kFftThreads)
   const int* __restrict__ perm = b.perm;
   const cx<T>* __restrict__ tw = static_cast<const cx<T>*>(b.tw);
   const T* __restrict__ invw = static_cast<const T*>(b.invw);
-  const cx<T>* __restrict__ U = spec + b.spec_off * nrhs + r * int64_t(n + 1);
   for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
-    cx<T> Uk = U[k], Unk = U[n - k];
+    cx<T> Uk = gather_bin(part, cbase, b.t_gbase, k, r, nrhs);
+    cx<T> Unk = gather_bin(part, cbase, b.t_gbase, n - k, r, nrhs);
     if (k == 0) {
       Uk.im = T(0);    // U_0 and U_n enter as real numbers
       Unk.im = T(0);
@@ -339,7 +352,7 @@ int launch_fft(Plan* p, bool forward, const void* in, void* out, int64_t nrhs, i
                                                         static_cast<const T*>(p->colscale),
                                                         static_cast<cx<T>*>(out), nrhs);
   else
-    adj_fft_kernel<T><<<grid, kFftThreads, smem, st>>>(bd, static_cast<const cx<T>*>(in), nrhs,
+    adj_fft_kernel<T><<<grid, kFftThreads, smem, st>>>(bd, static_cast<const cx<T>*>(in), p->t_cbase, nrhs,
                                                         static_cast<T*>(out), ld, static_cast<const T*>(p->colscale));
   launch_end(p, kid, st);
   XC_CUDA(cudaGetLastError());
@@ -363,15 +376,15 @@ int launch_sparse_fwd_rpw(Plan* p, const void* x, void* y, int64_t nrhs, int64_t
 
 template <typename T, bool COMP, int RPW>
 int launch_sparse_adj_rpw(Plan* p, const void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
-  if (p->total_tslices == 0) return XC_OK;
+  if (p->total_chunks == 0) return XC_OK;
   const void* fn = reinterpret_cast<const void*>(adj_sparse_kernel<T, RPW, COMP>);
   unsigned grid = 1;
-  XC_TRY(persistent_grid(fn, p->total_tslices * ((nrhs + RPW - 1) / RPW), &grid));
+  XC_TRY(persistent_grid(fn, p->total_chunks * ((nrhs + RPW - 1) / RPW), &grid));
   launch_begin(p, K_ADJ_SPARSE, st);
   adj_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
-      static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->total_tslices, p->N,
-      static_cast<const T*>(y), ld, static_cast<cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale),
-      p->t_order, p->counters);
+      static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->N, static_cast<const T*>(y), ld,
+      static_cast<cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale), p->t_items, p->t_cbase,
+      p->total_chunks, p->counters);
   launch_end(p, K_ADJ_SPARSE, st);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
@@ -516,7 +529,9 @@ int ensure_scratch(Plan* p, int64_t nrhs) {
   }
   if (nrhs <= p->scratch_nrhs) return XC_OK;
   const size_t cbytes = 2 * p->elem_bytes();
-  const size_t bytes = size_t(std::max<int64_t>(1, p->spec_per_rhs)) * size_t(nrhs) * cbytes;
+  // forward spectra and adjoint chunk partials share the buffer (one direction at a time)
+  const int64_t per_rhs = std::max<int64_t>({1, p->spec_per_rhs, p->total_chunks * 32});
+  const size_t bytes = size_t(per_rhs) * size_t(nrhs) * cbytes;
   void* fresh = nullptr;
   if (cudaMalloc(&fresh, bytes) != cudaSuccess) {
     cudaGetLastError();

@@ -78,7 +78,12 @@ struct BlockDev {
   const int64_t* t_off;      // [tslices]
   const void* t_val;
   int64_t spec_off;          // offset (complex elements) of this block's spectrum per unit nrhs
+  int t_gbase;               // index of this block's first bin slice in the plan-wide slice list
 };
+
+// Rows per chunk of a transposed (bin) slice in the adjoint product: long
+// slices are cut into chunks whose partial sums the adjoint FFT adds up.
+constexpr int kAdjChunk = 256;
 
 // ------------------------------------------------------------------- the plan
 struct Plan {
@@ -99,7 +104,10 @@ struct Plan {
   // work lists of the sparse kernels, longest item first: forward = row slices
   // (cost = summed band widths over blocks), adjoint = bin slices of all blocks
   int* f_order = nullptr;              // [nslices]
-  int* t_order = nullptr;              // [total tslices], global slice index
+  int* t_order = nullptr;              // unused (kept zero)
+  int2* t_items = nullptr;             // [total_chunks]: (global bin slice, chunk), longest chunk first
+  int* t_cbase = nullptr;              // [total_tslices + 1]: first chunk of each bin slice
+  int64_t total_chunks = 0;
   int64_t nslices = 0, total_tslices = 0;
   unsigned* counters = nullptr;        // [4]: {next, done} for the forward and the adjoint sparse kernel
   int64_t spec_per_rhs = 0;            // complex elements of all blocks' spectra per RHS

@@ -825,16 +825,42 @@ int build_plan_device(Plan* p) {
     gbase += int64_t(tw.size());
   }
   p->total_tslices = gbase;
+  // adjoint items: every bin slice cut into chunks of kAdjChunk rows
+  std::vector<int> cbase(size_t(gbase) + 1, 0);
+  std::vector<std::pair<int, int2>> items;   // (length, (g, chunk))
+  {
+    std::vector<int64_t> widths(gbase, 0);
+    for (const auto& tc : tcost) widths[tc.second] = tc.first;
+    int64_t run = 0;
+    for (int64_t g = 0; g < gbase; ++g) {
+      const int64_t W = widths[g];
+      const int64_t nch = W > 0 ? (W + kAdjChunk - 1) / kAdjChunk : 1;
+      cbase[g] = int(run);
+      for (int64_t c = 0; c < nch; ++c)
+        items.push_back({int(std::min<int64_t>(kAdjChunk, std::max<int64_t>(0, W - c * kAdjChunk))),
+                         int2{int(g), int(c)}});
+      run += nch;
+    }
+    cbase[gbase] = int(run);
+    p->total_chunks = run;
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const std::pair<int, int2>& a, const std::pair<int, int2>& b) { return a.first > b.first; });
+  std::vector<int2> titems(items.size());
+  for (size_t k = 0; k < items.size(); ++k) titems[k] = items[k].second;
+  XC_TRY(upload(p, titems, &p->t_items));
+  XC_TRY(upload(p, cbase, &p->t_cbase));
+  {
+    int64_t gb = 0;
+    for (int i = 0; i < nb; ++i) {
+      p->blocks[i].t_gbase = int(gb);
+      gb += p->blocks[i].tslices;
+    }
+  }
   std::vector<int> forder(p->nslices);
   for (int64_t s2 = 0; s2 < p->nslices; ++s2) forder[s2] = int(s2);
   std::stable_sort(forder.begin(), forder.end(), [&](int a, int b) { return fcost[a] > fcost[b]; });
-  std::stable_sort(tcost.begin(), tcost.end(), [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) {
-    return a.first > b.first;
-  });
-  std::vector<int> torder(tcost.size());
-  for (size_t k = 0; k < tcost.size(); ++k) torder[k] = tcost[k].second;
   XC_TRY(upload(p, forder, &p->f_order));
-  XC_TRY(upload(p, torder, &p->t_order));
   XC_TRY(plan_alloc(p, reinterpret_cast<void**>(&p->counters), 4 * sizeof(unsigned)));
   XC_CUDA(cudaMemset(p->counters, 0, 4 * sizeof(unsigned)));
 
