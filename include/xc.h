@@ -79,7 +79,7 @@ typedef struct {
   int nodes;                 /* XC_NODES_GAUSS | XC_NODES_USER */
   const double* user_nodes;  /* host, N entries, copied at create; used when nodes == XC_NODES_USER */
   int normalise;             /* XC_RAW | XC_ORTHONORMAL (orthonormal needs Gauss nodes) */
-  double eps2;               /* window floor of the first real component; 0 => 1e-3 (FP64) or 3e-2 (FP32) */
+  double eps2;               /* window floor of the first real component; 0 => 1e-3 (FP64) or 1e-1 (FP32) */
   double eps_window;         /* eps that fixes zeta when eps == 0; 0 => 1e-14 */
   int precision;             /* XC_FP64 | XC_FP32 | XC_FP32_COMPENSATED */
   int scheme;                /* XC_SCHEME_* */

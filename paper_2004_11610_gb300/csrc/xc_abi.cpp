@@ -159,7 +159,7 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
   p->scheme = prm.scheme == XC_SCHEME_AUTO ? (family == XC_CHEBYSHEV_T ? XC_SCHEME_TWO_SIDED : XC_SCHEME_BLOCKS)
                                            : prm.scheme;
   p->eps = eps;
-  p->eps2 = prm.eps2 > 0 ? prm.eps2 : (prm.precision == XC_FP64 ? 1e-3 : 3e-2);
+  p->eps2 = prm.eps2 > 0 ? prm.eps2 : (prm.precision == XC_FP64 ? 1e-3 : 1e-1);
   if (prm.nodes == XC_NODES_USER) p->nodes_host.assign(prm.user_nodes, prm.user_nodes + N);
   int rc = xc::make_schedule(N, eps, p->eps2, p->scheme == XC_SCHEME_TWO_SIDED, prm.eps_window,
                              prm.tail_max > 0 ? prm.tail_max : 20, &p->sch);

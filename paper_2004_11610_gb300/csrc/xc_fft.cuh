@@ -155,12 +155,32 @@ __device__ __forceinline__ void dft_small(cx<T>* a) {
   else dft_odd<R, T>(a);
 }
 
-// One radix-R pass over the n-point array s (in place).  tw is the length-L
+// Element access for the FFT passes: the array lives either in this CTA's
+// shared memory, or spread over the shared memories of a thread-block cluster
+// (rank r holds elements [r*per, (r+1)*per)), reached through distributed
+// shared memory.
+template <typename T>
+struct LocalMem {
+  cx<T>* s;
+  __device__ __forceinline__ cx<T>& at(int e) const { return s[e]; }
+};
+
+template <typename T>
+struct ClusterMem {
+  cx<T>* base[8];
+  int per;
+  __device__ __forceinline__ cx<T>& at(int e) const {
+    const int r = e / per;
+    return base[r][e - r * per];
+  }
+};
+
+// One radix-R pass over the n-point array (in place).  tw is the length-L
 // table exp(-2 pi i k / L) with L = 2n; the twiddle exp(-2 pi i k t / m) of
 // sub-length m is tw[2 k t (n/m)].
-template <int R, typename T>
-__device__ __forceinline__ void fft_pass(cx<T>* s, int n, int m_prev, const cx<T>* __restrict__ tw,
-                                         int tid, int nthreads) {
+template <int R, typename T, class M>
+__device__ __forceinline__ void fft_pass(const M& mem, int n, int m_prev, const cx<T>* __restrict__ tw, int tid,
+                                         int nthreads) {
   const int m = m_prev * R;
   const int nbf = n / R;
   const int tw_step = 2 * (n / m);
@@ -169,52 +189,63 @@ __device__ __forceinline__ void fft_pass(cx<T>* s, int n, int m_prev, const cx<T
     const int base = (w / m_prev) * m + k;
     cx<T> a[R];
 #pragma unroll
-    for (int t = 0; t < R; ++t) a[t] = s[base + t * m_prev];
+    for (int t = 0; t < R; ++t) a[t] = mem.at(base + t * m_prev);
     if (m_prev > 1) {
 #pragma unroll
       for (int t = 1; t < R; ++t) a[t] = cmul(a[t], tw[k * t * tw_step]);
     }
     dft_small<R, T>(a);
 #pragma unroll
-    for (int t = 0; t < R; ++t) s[base + t * m_prev] = a[t];
+    for (int t = 0; t < R; ++t) mem.at(base + t * m_prev) = a[t];
   }
 }
 
-// Complete in-place forward FFT (exp(-2 pi i jk/n)) of the digit-reversed data
-// in shared memory.  Ends with a barrier.
-template <typename T>
-__device__ void fft_inplace(cx<T>* s, int n, int p, const int* radix, const cx<T>* __restrict__ tw,
-                            int tid, int nthreads) {
+// All passes of the in-place forward FFT (exp(-2 pi i jk/n)) of digit-reversed
+// data; `sync` is the barrier between passes (CTA or cluster) and ends the run.
+template <typename T, class M, class Sync>
+__device__ void fft_run(const M& mem, int n, int p, const int* radix, const cx<T>* __restrict__ tw, int tid,
+                        int nthreads, Sync sync) {
   int m_prev = 1;
   for (int q = 0; q < p; ++q) {
     const int r = radix[q];
     switch (r) {
-      case 2: fft_pass<2, T>(s, n, m_prev, tw, tid, nthreads); break;
-      case 3: fft_pass<3, T>(s, n, m_prev, tw, tid, nthreads); break;
-      case 4: fft_pass<4, T>(s, n, m_prev, tw, tid, nthreads); break;
-      case 5: fft_pass<5, T>(s, n, m_prev, tw, tid, nthreads); break;
-      case 7: fft_pass<7, T>(s, n, m_prev, tw, tid, nthreads); break;
-      default: fft_pass<8, T>(s, n, m_prev, tw, tid, nthreads); break;
+      case 2: fft_pass<2, T>(mem, n, m_prev, tw, tid, nthreads); break;
+      case 3: fft_pass<3, T>(mem, n, m_prev, tw, tid, nthreads); break;
+      case 4: fft_pass<4, T>(mem, n, m_prev, tw, tid, nthreads); break;
+      case 5: fft_pass<5, T>(mem, n, m_prev, tw, tid, nthreads); break;
+      case 7: fft_pass<7, T>(mem, n, m_prev, tw, tid, nthreads); break;
+      default: fft_pass<8, T>(mem, n, m_prev, tw, tid, nthreads); break;
     }
     m_prev *= r;
-    __syncthreads();
+    sync();
   }
+}
+
+// In-place FFT in this CTA's shared memory.  Ends with a barrier.
+template <typename T>
+__device__ void fft_inplace(cx<T>* s, int n, int p, const int* radix, const cx<T>* __restrict__ tw, int tid,
+                            int nthreads) {
+  fft_run<T>(LocalMem<T>{s}, n, p, radix, tw, tid, nthreads, [] { __syncthreads(); });
 }
 
 // Even/odd split after the packed FFT: from Z = FFT_n(u_even + i u_odd) give
 // the half spectrum U_k = sum_j u_j exp(-2 pi i jk / L), k = 0..n, as the pair
 // (U_k, U_{n-k}) for 0 <= k <= n/2.  For k = 0 the second value is U_n.
 template <typename T>
-__device__ __forceinline__ void r2c_split(const cx<T>* s, int n, int k, const cx<T>* __restrict__ tw,
-                                          cx<T>* Uk, cx<T>* Unk) {
-  const cx<T> Zk = s[k];
-  const cx<T> Znk = s[k == 0 ? 0 : n - k];
+__device__ __forceinline__ void r2c_split_vals(cx<T> Zk, cx<T> Znk, int k, const cx<T>* __restrict__ tw, cx<T>* Uk,
+                                               cx<T>* Unk) {
   const T half = T(0.5);
   const cx<T> E = scal(half, Zk + conj(Znk));
   const cx<T> O = scal(half, mul_mi(Zk - conj(Znk)));   // (Zk - conj Znk) / (2i)
   const cx<T> P = cmul(tw[k], O);
   *Uk = E + P;
   *Unk = conj(E - P);
+}
+
+template <typename T>
+__device__ __forceinline__ void r2c_split(const cx<T>* s, int n, int k, const cx<T>* __restrict__ tw, cx<T>* Uk,
+                                          cx<T>* Unk) {
+  r2c_split_vals(s[k], s[k == 0 ? 0 : n - k], k, tw, Uk, Unk);
 }
 
 // Inverse of r2c_split up to the packing: from a half spectrum U_0..U_n

@@ -5,6 +5,7 @@
 //   compressed matrix A_e W F (eq. (A_comp), step 1.3), the per-block maximum,
 //   the threshold |a| > eps1 * max|A_e W F|, and the banded storage of the kept
 //   elements for the forward and the transposed (adjoint) product.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -367,6 +368,60 @@ __global__ void __launch_bounds__(256) row_fft_kernel(const double* G, int64_t C
   }
 }
 
+// The same row transform for lengths whose FP64 array exceeds one CTA's shared
+// memory: a cluster of `csize` CTAs per row holds the n-point array split in
+// equal parts (rank r owns [r*per, (r+1)*per)); butterflies reach the other
+// parts through distributed shared memory, and a cluster barrier separates the
+// passes.  Launched with cluster dimension (csize, 1, 1), grid = rows * csize.
+__global__ void __launch_bounds__(256) row_fft_cluster_kernel(const double* G, int64_t C, int64_t row0, int64_t N,
+                                                              BlockDev b, const cx<double>* tw, cx<double>* S,
+                                                              unsigned long long* maxsq_bits, int csize) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<double>* s = reinterpret_cast<cx<double>*>(smem_raw);
+  __shared__ double red[8];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = int(cluster.block_rank());
+  const int64_t c = blockIdx.x / csize;
+  const int64_t row = row0 + c;
+  const int n = b.n;
+  ClusterMem<double> mem;
+  mem.per = n / csize;
+  for (int r = 0; r < 8; ++r) mem.base[r] = r < csize ? cluster.map_shared_rank(s, r) : s;
+  const int tid = rank * int(blockDim.x) + int(threadIdx.x);
+  const int nthreads = csize * int(blockDim.x);
+  const bool live = row < N;            // the whole cluster shares one row: uniform
+  cluster.sync();                       // every CTA of the cluster runs before any remote access
+  if (live)
+    for (int j = tid; j < n; j += nthreads)
+      mem.at(b.perm[j]) = cx<double>{G[int64_t(2 * j) * C + c], G[int64_t(2 * j + 1) * C + c]};
+  cluster.sync();
+  fft_run<double>(mem, n, b.p, b.radix, tw, tid, nthreads, [&] { cluster.sync(); });
+  const double scale = 1.0 / double(b.L);
+  double local = 0.0;
+  if (live) {
+    cx<double>* out = S + row * int64_t(n + 1);
+    for (int k = tid; k <= n / 2; k += nthreads) {
+      cx<double> Uk, Unk;
+      r2c_split_vals(mem.at(k), mem.at(k == 0 ? 0 : n - k), k, tw, &Uk, &Unk);
+      Uk = scal(scale, Uk);
+      Unk = scal(scale, Unk);
+      out[k] = Uk;
+      out[n - k] = Unk;
+      local = fmax(local, fmax(Uk.re * Uk.re + Uk.im * Uk.im, Unk.re * Unk.re + Unk.im * Unk.im));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x == 0 && live) {
+    double m = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
+    atomicMax(maxsq_bits, static_cast<unsigned long long>(__double_as_longlong(m)));
+  }
+  cluster.sync();   // no CTA leaves while another may still read its shared memory
+}
+
 __device__ __forceinline__ bool kept(cx<double> v, double thr) { return v.re * v.re + v.im * v.im > thr; }
 
 // One warp per row: first/last kept bin and the number of kept bins.
@@ -590,9 +645,23 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
   int dev = 0, optin = 0;
   XC_CUDA(cudaGetDevice(&dev));
   XC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (smem + 1024 > size_t(optin))   // the row FFT also holds a small static reduction buffer
+  // single CTA when the FP64 array fits its shared memory, else a cluster
+  int csize = 1;
+  if (smem + 1024 > size_t(optin)) {
+    csize = 0;
+    for (int cand = 2; cand <= 8; ++cand)
+      if (n % cand == 0 && size_t(n / cand) * sizeof(cx<double>) + 1024 <= size_t(optin)) {
+        csize = cand;
+        break;
+      }
+    if (csize == 0)
+      return fail(XC_ERR_UNSUPPORTED, "block length L = " + std::to_string(b.L) +
+                                          " exceeds an 8-CTA cluster FFT of the precompute");
+  }
+  // the apply FFT runs in one CTA in the plan precision
+  if (size_t(n) * sizeof(cx<T>) + 1024 > size_t(optin))
     return fail(XC_ERR_UNSUPPORTED, "block length L = " + std::to_string(b.L) +
-                                        " exceeds the single-CTA FP64 FFT of the precompute");
+                                        " exceeds the single-CTA FFT of the apply in this precision");
 
   // permutation, window, twiddles
   std::vector<int> perm = digit_reversal(n, b.p, b.radix);
@@ -626,15 +695,34 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
   int64_t C = std::max<int64_t>(1, std::min<int64_t>(N, (int64_t(1) << 30) / (int64_t(b.L) * 8)));
   DevBuf Gbuf;
   XC_TRY(alloc_tmp(&Gbuf, size_t(C) * size_t(b.L) * sizeof(double)));
-  XC_TRY(set_smem(reinterpret_cast<const void*>(row_fft_kernel), smem));
+  const size_t csmem = size_t(n / csize) * sizeof(cx<double>);
+  if (csize == 1) XC_TRY(set_smem(reinterpret_cast<const void*>(row_fft_kernel), smem));
+  else XC_TRY(set_smem(reinterpret_cast<const void*>(row_fft_cluster_kernel), csmem));
   for (int64_t row0 = 0; row0 < N; row0 += C) {
     const int64_t rows = std::min<int64_t>(C, N - row0);
     gen_rows_kernel<<<unsigned((rows + 127) / 128), 128>>>(g, row0, C, b.L, b.off, static_cast<double*>(w64.ptr),
                                                            static_cast<double*>(Gbuf.ptr));
-    row_fft_kernel<<<unsigned(rows), 256, smem>>>(static_cast<double*>(Gbuf.ptr), C, row0, N, b,
-                                                   static_cast<cx<double>*>(tw64.ptr),
-                                                   static_cast<cx<double>*>(Sbuf.ptr),
-                                                   static_cast<unsigned long long*>(maxbuf.ptr));
+    if (csize == 1) {
+      row_fft_kernel<<<unsigned(rows), 256, smem>>>(static_cast<double*>(Gbuf.ptr), C, row0, N, b,
+                                                     static_cast<cx<double>*>(tw64.ptr),
+                                                     static_cast<cx<double>*>(Sbuf.ptr),
+                                                     static_cast<unsigned long long*>(maxbuf.ptr));
+    } else {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(unsigned(rows * csize));
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = csmem;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = unsigned(csize);
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      XC_CUDA(cudaLaunchKernelEx(&cfg, row_fft_cluster_kernel, static_cast<const double*>(Gbuf.ptr), C, row0, N, b,
+                                 static_cast<const cx<double>*>(tw64.ptr), static_cast<cx<double>*>(Sbuf.ptr),
+                                 static_cast<unsigned long long*>(maxbuf.ptr), csize));
+    }
     XC_CUDA(cudaGetLastError());
   }
   unsigned long long bits = 0;
