@@ -205,6 +205,58 @@ int xc_get_nodes(xc_plan_t plan, double* host_out);
  */
 int xc_dense_matrix(xc_plan_t plan, void* A_dev, int64_t lda, void* stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many plans (uneven N, families, numbers of right-hand sides; one precision)
+ * applied by one persistent kernel launch per direction.  The launch works
+ * through a device task list over all plans: phase 1 (forward: the FFTs;
+ * adjoint: the transposed band products and dense tails), then phase 2
+ * (forward: the band products and tails; adjoint: the inverse FFTs).  A
+ * phase-2 task of a plan waits, with a bounded number of sleeps, until all
+ * phase-1 tasks of that plan have finished; a wait that runs out sets the
+ * batch's status to XC_ERR_TIMEOUT (read by xc_batch_status) instead of
+ * hanging.  This is the batched form of Algorithms 1-4; the paper itself
+ * applies one matrix at a time.
+ */
+typedef struct xc_batch* xc_batch_t;
+typedef struct {
+  int nplans;
+  int rhs_per_item;          /* right-hand sides per band-product task (tuned) */
+  int tuned;                 /* 1 after xc_batch_tune */
+  int64_t tasks_forward, tasks_adjoint;
+  int64_t shared_bytes;      /* dynamic shared memory of the persistent kernel */
+  int64_t matrix_bytes, adjoint_bytes;   /* summed over the plans */
+} xc_batch_stats;
+
+/* Group nplans plans (host array of handles; all of one precision).  The
+ * batch refers to the plans, which must outlive it. */
+int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans);
+/* Bind the I/O buffers: x_dev[i], y_dev[i] are device pointers to
+ * [nrhs[i]][ld[i]] arrays of plan i's type (ld[i] >= N_i; nrhs[i] = 0 skips the
+ * plan).  The forward apply reads x and writes y, the adjoint reads y and
+ * writes x.  Allocates the plans' scratch and builds the task lists
+ * (synchronous). */
+int xc_batch_bind(xc_batch_t b, const void* const* x_dev, void* const* y_dev, const int64_t* nrhs, const int64_t* ld);
+/* One persistent launch over all bound plans (adjoint = 0: y = A x for every
+ * plan; 1: x = A^T y).  Asynchronous on `stream`; allocates nothing and does
+ * not synchronise, so it can be captured in a CUDA graph and replayed.
+ * Launches of one batch, and of batches sharing a plan, must not overlap. */
+int xc_batch_apply(xc_batch_t b, int adjoint, void* stream);
+/* Autotuner: times the bound problem with 1, 2, 4 and 8 right-hand sides per
+ * band-product task (forward + adjoint, 3 repetitions each) and keeps the
+ * fastest; the choice is cached per batch shape for later binds in the
+ * process.  Synchronises `stream`; the bound buffers are restored afterwards. */
+int xc_batch_tune(xc_batch_t b, void* stream);
+int xc_batch_info(xc_batch_t b, xc_batch_stats* out);
+/* Synchronise `stream` and report XC_ERR_TIMEOUT if a phase wait of an
+ * earlier launch gave up (then clear it); XC_OK otherwise.  While the status
+ * is set, later launches skip their tasks. */
+int xc_batch_status(xc_batch_t b, void* stream);
+/* Fault injection for tests: plan `plan` needs `extra_need` more phase-1
+ * completions than exist (so its phase-2 waits run out), and every wait gives
+ * up after wait_limit sleeps of ~256 ns.  extra_need = 0 restores the plan. */
+int xc_batch_debug_set(xc_batch_t b, int plan, int extra_need, int64_t wait_limit);
+int xc_batch_destroy(xc_batch_t b);
+
 /*
  * Per-kernel timing.  While enabled, every kernel the plan launches is
  * bracketed by two CUDA events recorded on the launch stream; xc_timing_read

@@ -1,4 +1,5 @@
-// Execution stage (the hot path) of Algorithms 1-4.
+// Execution stage (the hot path) of Algorithms 1-4: the single-plan kernels
+// and their launches (device bodies in xc_items.cuh).
 //
 // Forward, y = A x (Algorithm 1 step 2 / Algorithm 3):
 //   fwd_fft_kernel     per (block, RHS): extend the input with zero extra
@@ -21,6 +22,7 @@
 
 #include "xc_fft.cuh"
 #include "xc_internal.h"
+#include "xc_items.cuh"
 
 namespace xc {
 
@@ -29,65 +31,14 @@ namespace {
 constexpr int kFftThreads = 256;
 constexpr int kSparseWarps = 4;
 
-// ------------------------------------------------------------- accumulation
-// Plain or compensated (TwoProduct + TwoSum) sum of products.
-template <typename T, bool COMP>
-struct Acc {
-  T s = 0, c = 0;
-  __device__ __forceinline__ void add(T a, T b) {
-    if constexpr (!COMP) {
-      s = fma(a, b, s);
-    } else {
-      const T p = a * b;
-      const T e = fma(a, b, -p);          // a*b = p + e exactly
-      const T t = s + p;                  // TwoSum(s, p)
-      const T bb = t - s;
-      const T err = (s - (t - bb)) + (p - bb);
-      s = t;
-      c += err + e;
-    }
-  }
-  __device__ __forceinline__ T value() const { return COMP ? s + c : s; }
-};
-
 // ------------------------------------------------------------ forward FFT
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
     fwd_fft_kernel(const BlockDev* __restrict__ blocks, const T* __restrict__ x, int64_t ld,
                    const T* __restrict__ colscale, cx<T>* __restrict__ spec, int64_t nrhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-  const BlockDev& b = blocks[blockIdx.y];
-  const int64_t r = blockIdx.x;
-  const int n = b.n, j_lo = b.j_lo, j_hi = b.j_hi, off = b.off;
-  const T* __restrict__ invw = static_cast<const T*>(b.invw);
-  const int* __restrict__ perm = b.perm;
-  const cx<T>* __restrict__ tw = static_cast<const cx<T>*>(b.tw);
-  const T* __restrict__ xr = x + r * ld;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const int j0 = 2 * j, j1 = 2 * j + 1;
-    T u0 = T(0), u1 = T(0);
-    if (j0 >= j_lo && j0 < j_hi) {
-      T v = xr[j0 - off];
-      if (colscale) v *= colscale[j0 - off];
-      u0 = v * invw[j0];
-    }
-    if (j1 >= j_lo && j1 < j_hi) {
-      T v = xr[j1 - off];
-      if (colscale) v *= colscale[j1 - off];
-      u1 = v * invw[j1];
-    }
-    s[perm[j]] = cx<T>{u0, u1};
-  }
-  __syncthreads();
-  fft_inplace<T>(s, n, b.p, b.radix, tw, threadIdx.x, blockDim.x);
-  cx<T>* out = spec + b.spec_off * nrhs + r * int64_t(n + 1);
-  for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
-    cx<T> Uk, Unk;
-    r2c_split(s, n, k, tw, &Uk, &Unk);
-    out[k] = Uk;
-    if (n - k != k) out[n - k] = Unk;
-  }
+  fwd_fft_body<T>(blocks[blockIdx.y], blockIdx.x, x, ld, colscale, spec, nrhs, reinterpret_cast<cx<T>*>(smem_raw),
+                  threadIdx.x, blockDim.x);
 }
 
 // ------------------------------------------------------- work distribution
@@ -113,9 +64,6 @@ __device__ __forceinline__ void retire_warp(unsigned* next, unsigned* done, unsi
 }
 
 // ------------------------------------------------------- forward sparse
-// Item = (32-row slice, RPW right-hand sides); lane = row.  Each band value is
-// loaded once (coalesced across the slice) and used for the RPW right-hand
-// sides; the spectra are gathered through L1.
 template <typename T, int RPW, bool COMP>
 __global__ void __launch_bounds__(32 * kSparseWarps)
     fwd_sparse_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N, const T* __restrict__ x,
@@ -128,112 +76,32 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
   for (;;) {
     const int64_t t = take_item(&counters[0], lane);
     if (t >= total) break;
-    const int64_t slice = order[t / ngroups];
-    const int64_t r0 = (t % ngroups) * RPW;
-    const int64_t n = slice * 32 + lane;
-    const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
-    Acc<T, COMP> acc[RPW];
-    for (int i = 0; i < nblocks; ++i) {
-      const BlockDev& b = blocks[i];
-      const int W = b.f_width[slice];
-      const int k0 = b.f_k0[n];
-      const int H = b.H;
-      const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.f_val) + b.f_off[slice] + lane;
-      const cx<T>* __restrict__ F = spec + b.spec_off * nrhs + r0 * H + k0;
-      if (nq == RPW) {
-#pragma unroll 4
-        for (int j = 0; j < W; ++j) {
-          const cx<T> c = val[j * 32];
-#pragma unroll
-          for (int q = 0; q < RPW; ++q) {
-            const cx<T> f = F[q * H + j];
-            acc[q].add(c.re, f.re);
-            acc[q].add(c.im, f.im);
-          }
-        }
-      } else {
-        for (int j = 0; j < W; ++j) {
-          const cx<T> c = val[j * 32];
-#pragma unroll
-          for (int q = 0; q < RPW; ++q) {
-            if (q < nq) {
-              const cx<T> f = F[q * H + j];
-              acc[q].add(c.re, f.re);
-              acc[q].add(c.im, f.im);
-            }
-          }
-        }
-      }
-    }
-    if (n < N) {
-      for (int64_t m = 0; m < m_tail; ++m) {
-        const T tv = tail[m * N + n];
-        const T cs = colscale ? colscale[m] : T(1);
-#pragma unroll
-        for (int q = 0; q < RPW; ++q)
-          if (q < nq) acc[q].add(tv, x[(r0 + q) * ld + m] * cs);
-      }
-      const T rs = rowscale ? rowscale[n] : T(1);
-#pragma unroll
-      for (int q = 0; q < RPW; ++q)
-        if (q < nq) y[(r0 + q) * ld + n] = acc[q].value() * rs;
-    }
+    fwd_sparse_item<T, RPW, COMP>(blocks, nblocks, N, x, ld, y, spec, nrhs, rowscale, colscale, tail, m_tail,
+                                  order[t / ngroups], (t % ngroups) * RPW, lane);
   }
   retire_warp(&counters[0], &counters[1], gridDim.x * kSparseWarps, lane);
 }
 
 // ------------------------------------------------------- adjoint sparse
-// Item = (chunk of up to kAdjChunk rows of a 32-bin slice of one block, RPW
-// right-hand sides); lane = bin k.  The chunk's partial sum
-// sum_j CT[j][k] y[n0_k + j] goes to part[chunk][rhs][lane]; the adjoint FFT
-// adds the chunks of each bin in chunk order (deterministic, no atomics).
 // Chunking keeps bins that are covered by thousands of rows (the small last
 // blocks, high frequencies of the Laguerre functions) from becoming one long
-// serial loop.
+// serial loop; the adjoint FFT adds the chunks of each bin in chunk order
+// (deterministic, no atomics).
 template <typename T, int RPW, bool COMP>
 __global__ void __launch_bounds__(32 * kSparseWarps)
     adj_sparse_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N, const T* __restrict__ y,
                       int64_t ld, cx<T>* __restrict__ part, int64_t nrhs, const T* __restrict__ rowscale,
                       const int2* __restrict__ items, const int* __restrict__ cbase, int64_t total_chunks,
                       unsigned* counters) {
+  (void)N;
   const int lane = threadIdx.x & 31;
   const int64_t ngroups = (nrhs + RPW - 1) / RPW;
   const int64_t total = total_chunks * ngroups;
   for (;;) {
     const int64_t t = take_item(&counters[2], lane);
     if (t >= total) break;
-    const int2 it = items[t / ngroups];
-    const int64_t r0 = (t % ngroups) * RPW;
-    int i = 0;
-    while (i < nblocks - 1 && it.x >= blocks[i].t_gbase + blocks[i].tslices) ++i;
-    const BlockDev& b = blocks[i];
-    const int gl = it.x - b.t_gbase;
-    const int64_t k = int64_t(gl) * 32 + lane;
-    const int W = b.t_width[gl];
-    const int j0 = it.y * kAdjChunk;
-    const int j1 = min(W, j0 + kAdjChunk);
-    const int n0 = b.t_n0[k];
-    const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
-    const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.t_val) + b.t_off[gl] + lane;
-    Acc<T, COMP> re[RPW], im[RPW];
-#pragma unroll 4
-    for (int j = j0; j < j1; ++j) {
-      const cx<T> c = val[j * 32];
-      const int64_t row = n0 + j;
-      const T rs = rowscale ? rowscale[row] : T(1);
-#pragma unroll
-      for (int q = 0; q < RPW; ++q) {
-        if (q < nq) {
-          const T v = y[(r0 + q) * ld + row] * rs;
-          re[q].add(c.re, v);
-          im[q].add(c.im, v);
-        }
-      }
-    }
-    cx<T>* out = part + ((int64_t(cbase[it.x]) + it.y) * nrhs + r0) * 32 + lane;
-#pragma unroll
-    for (int q = 0; q < RPW; ++q)
-      if (q < nq) out[q * 32] = cx<T>{re[q].value(), im[q].value()};
+    adj_sparse_item<T, RPW, COMP>(blocks, nblocks, y, ld, part, nrhs, rowscale, cbase, items[t / ngroups],
+                                  (t % ngroups) * RPW, lane);
   }
   retire_warp(&counters[2], &counters[3], gridDim.x * kSparseWarps, lane);
 }
@@ -259,76 +127,24 @@ int persistent_grid(const void* fn, int64_t items, unsigned* grid) {
 }
 
 // ------------------------------------------------------------ adjoint FFT
-// Sum of the chunk partials of bin k of this block for right-hand side r.
-template <typename T>
-__device__ __forceinline__ cx<T> gather_bin(const cx<T>* __restrict__ part, const int* __restrict__ cbase,
-                                            int gbase, int k, int64_t r, int64_t nrhs) {
-  const int g = gbase + (k >> 5);
-  const int c0 = cbase[g], c1 = cbase[g + 1];
-  cx<T> u{T(0), T(0)};
-  for (int c = c0; c < c1; ++c) u = u + part[(int64_t(c) * nrhs + r) * 32 + (k & 31)];
-  return u;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
     adj_fft_kernel(const BlockDev* __restrict__ blocks, const cx<T>* __restrict__ part, const int* __restrict__ cbase,
                    int64_t nrhs, T* __restrict__ x, int64_t ld, const T* __restrict__ colscale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-  const BlockDev& b = blocks[blockIdx.y];
-  const int64_t r = blockIdx.x;
-  const int n = b.n, j_lo = b.j_lo, j_hi = b.j_hi, off = b.off;
-  const int* __restrict__ perm = b.perm;
-  const cx<T>* __restrict__ tw = static_cast<const cx<T>*>(b.tw);
-  const T* __restrict__ invw = static_cast<const T*>(b.invw);
-  for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
-    cx<T> Uk = gather_bin(part, cbase, b.t_gbase, k, r, nrhs);
-    cx<T> Unk = gather_bin(part, cbase, b.t_gbase, n - k, r, nrhs);
-    if (k == 0) {
-      Uk.im = T(0);    // U_0 and U_n enter as real numbers
-      Unk.im = T(0);
-    }
-    cx<T> Zk, Znk;
-    c2r_merge(Uk, Unk, k, tw, &Zk, &Znk);
-    // inverse FFT as conj(FFT(conj(Z)))
-    s[perm[k]] = conj(Zk);
-    if (k != 0 && n - k != k) s[perm[n - k]] = conj(Znk);
-  }
-  __syncthreads();
-  fft_inplace<T>(s, n, b.p, b.radix, tw, threadIdx.x, blockDim.x);
-  T* __restrict__ xr = x + r * ld;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const cx<T> v = s[j];
-    const int j0 = 2 * j, j1 = 2 * j + 1;
-    if (j0 >= j_lo && j0 < j_hi) {
-      T u = v.re * invw[j0];
-      if (colscale) u *= colscale[j0 - off];
-      xr[j0 - off] = u;
-    }
-    if (j1 >= j_lo && j1 < j_hi) {
-      T u = -v.im * invw[j1];
-      if (colscale) u *= colscale[j1 - off];
-      xr[j1 - off] = u;
-    }
-  }
+  adj_fft_body<T>(blocks[blockIdx.y], blockIdx.x, part, cbase, nrhs, x, ld, colscale,
+                  reinterpret_cast<cx<T>*>(smem_raw), threadIdx.x, blockDim.x);
 }
 
 // ------------------------------------------------------------ adjoint tail
-// Warp per (m, RHS): x_m = colscale_m sum_n tail[m][n] rowscale_n y_n.
+// Warp per (m, RHS).
 template <typename T, bool COMP>
 __global__ void adj_tail_kernel(int64_t N, int64_t m_tail, const T* __restrict__ tail, const T* __restrict__ y,
                                 int64_t ld, T* __restrict__ x, const T* __restrict__ rowscale,
                                 const T* __restrict__ colscale) {
-  const int lane = threadIdx.x & 31;
   const int64_t m = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int64_t r = blockIdx.y;
   if (m >= m_tail) return;
-  Acc<T, COMP> acc;
-  for (int64_t n = lane; n < N; n += 32) acc.add(tail[m * N + n], y[r * ld + n] * (rowscale ? rowscale[n] : T(1)));
-  T v = acc.value();
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) x[r * ld + m] = v * (colscale ? colscale[m] : T(1));
+  adj_tail_warp<T, COMP>(N, m, blockIdx.y, tail, y, ld, x, rowscale, colscale, threadIdx.x & 31);
 }
 
 // ------------------------------------------------------------------ launch

@@ -108,6 +108,9 @@ struct Plan {
   int2* t_items = nullptr;             // [total_chunks]: (global bin slice, chunk), longest chunk first
   int* t_cbase = nullptr;              // [total_tslices + 1]: first chunk of each bin slice
   int64_t total_chunks = 0;
+  std::vector<int64_t> slice_cost;     // host: summed forward band width of each row slice
+  std::vector<int> item_len;           // host: rows of each adjoint chunk, in t_items order
+  std::vector<int2> item_host;         // host copy of t_items
   int64_t nslices = 0, total_tslices = 0;
   unsigned* counters = nullptr;        // [4]: {next, done} for the forward and the adjoint sparse kernel
   int64_t spec_per_rhs = 0;            // complex elements of all blocks' spectra per RHS

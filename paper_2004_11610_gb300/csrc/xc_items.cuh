@@ -1,0 +1,248 @@
+// Device bodies of the execution stage, shared by the single-plan kernels
+// (xc_apply.cu) and the many-plan persistent kernel (xc_batch.cu).
+//
+// Forward, y = A x (Algorithm 1 step 2 / Algorithm 3):
+//   fwd_fft_body      one (block, RHS): extend the input with zero extra
+//                     components (eqs. (Fe1), (Fe3)), multiply by W^{-1}, real
+//                     FFT -> half spectrum F_k = sum_j u_j exp(-2 pi i jk / L)
+//   fwd_sparse_item   one (32-row slice, RPW right-hand sides): y_n = sum over
+//                     blocks of sum_k Re(C_nk conj(F_k)) over the row's band,
+//                     plus the dense tail; C = g_k A_e W F / sqrt(L) carries the
+//                     unitary and half-spectrum factors, so
+//                     Re(C conj F) = Re C Re F + Im C Im F.
+// Adjoint, x = A^T y (Algorithm 2 step 2 / Algorithm 4):
+//   adj_sparse_item   one (chunk of rows of a 32-bin slice, RPW RHS): partial
+//                     sums of z_k = sum_n CT_kn y_n
+//   adj_fft_body      one (block, RHS): add the chunk partials, real inverse
+//                     FFT, W^{-1}, keep [j_lo, j_hi) and discard the extra
+//                     components (eq. (Fe2))
+//   adj_tail_warp     one (m, RHS): x_m from the dense tail.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "xc_fft.cuh"
+#include "xc_internal.h"
+
+namespace xc {
+
+// Plain or compensated (TwoProduct + TwoSum) sum of products.
+template <typename T, bool COMP>
+struct Acc {
+  T s = 0, c = 0;
+  __device__ __forceinline__ void add(T a, T b) {
+    if constexpr (!COMP) {
+      s = fma(a, b, s);
+    } else {
+      const T p = a * b;
+      const T e = fma(a, b, -p);          // a*b = p + e exactly
+      const T t = s + p;                  // TwoSum(s, p)
+      const T bb = t - s;
+      const T err = (s - (t - bb)) + (p - bb);
+      s = t;
+      c += err + e;
+    }
+  }
+  __device__ __forceinline__ T value() const { return COMP ? s + c : s; }
+};
+
+// ------------------------------------------------------------ forward FFT
+template <typename T>
+__device__ void fwd_fft_body(const BlockDev& b, int64_t r, const T* __restrict__ x, int64_t ld,
+                             const T* __restrict__ colscale, cx<T>* __restrict__ spec, int64_t nrhs, cx<T>* s,
+                             int tid, int nthreads) {
+  const int n = b.n, j_lo = b.j_lo, j_hi = b.j_hi, off = b.off;
+  const T* __restrict__ invw = static_cast<const T*>(b.invw);
+  const int* __restrict__ perm = b.perm;
+  const cx<T>* __restrict__ tw = static_cast<const cx<T>*>(b.tw);
+  const T* __restrict__ xr = x + r * ld;
+  for (int j = tid; j < n; j += nthreads) {
+    const int j0 = 2 * j, j1 = 2 * j + 1;
+    T u0 = T(0), u1 = T(0);
+    if (j0 >= j_lo && j0 < j_hi) {
+      T v = xr[j0 - off];
+      if (colscale) v *= colscale[j0 - off];
+      u0 = v * invw[j0];
+    }
+    if (j1 >= j_lo && j1 < j_hi) {
+      T v = xr[j1 - off];
+      if (colscale) v *= colscale[j1 - off];
+      u1 = v * invw[j1];
+    }
+    s[perm[j]] = cx<T>{u0, u1};
+  }
+  __syncthreads();
+  fft_inplace<T>(s, n, b.p, b.radix, tw, tid, nthreads);
+  cx<T>* out = spec + b.spec_off * nrhs + r * int64_t(n + 1);
+  for (int k = tid; k <= n / 2; k += nthreads) {
+    cx<T> Uk, Unk;
+    r2c_split(s, n, k, tw, &Uk, &Unk);
+    out[k] = Uk;
+    if (n - k != k) out[n - k] = Unk;
+  }
+}
+
+// ------------------------------------------------------- forward sparse
+// Lane = row.  Each band value is loaded once (coalesced across the slice)
+// and used for the RPW right-hand sides; the spectra are gathered through L1.
+template <typename T, int RPW, bool COMP>
+__device__ void fwd_sparse_item(const BlockDev* __restrict__ blocks, int nblocks, int64_t N,
+                                const T* __restrict__ x, int64_t ld, T* __restrict__ y,
+                                const cx<T>* __restrict__ spec, int64_t nrhs, const T* __restrict__ rowscale,
+                                const T* __restrict__ colscale, const T* __restrict__ tail, int64_t m_tail,
+                                int64_t slice, int64_t r0, int lane) {
+  const int64_t n = slice * 32 + lane;
+  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
+  Acc<T, COMP> acc[RPW];
+  for (int i = 0; i < nblocks; ++i) {
+    const BlockDev& b = blocks[i];
+    const int W = b.f_width[slice];
+    const int k0 = b.f_k0[n];
+    const int H = b.H;
+    const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.f_val) + b.f_off[slice] + lane;
+    const cx<T>* __restrict__ F = spec + b.spec_off * nrhs + r0 * H + k0;
+    if (nq == RPW) {
+#pragma unroll 4
+      for (int j = 0; j < W; ++j) {
+        const cx<T> c = val[j * 32];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          const cx<T> f = F[q * H + j];
+          acc[q].add(c.re, f.re);
+          acc[q].add(c.im, f.im);
+        }
+      }
+    } else {
+      for (int j = 0; j < W; ++j) {
+        const cx<T> c = val[j * 32];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          if (q < nq) {
+            const cx<T> f = F[q * H + j];
+            acc[q].add(c.re, f.re);
+            acc[q].add(c.im, f.im);
+          }
+        }
+      }
+    }
+  }
+  if (n < N) {
+    for (int64_t m = 0; m < m_tail; ++m) {
+      const T tv = tail[m * N + n];
+      const T cs = colscale ? colscale[m] : T(1);
+#pragma unroll
+      for (int q = 0; q < RPW; ++q)
+        if (q < nq) acc[q].add(tv, x[(r0 + q) * ld + m] * cs);
+    }
+    const T rs = rowscale ? rowscale[n] : T(1);
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+      if (q < nq) y[(r0 + q) * ld + n] = acc[q].value() * rs;
+  }
+}
+
+// ------------------------------------------------------- adjoint sparse
+// Item (global bin slice g, chunk c): lane = bin k; the partial sum over rows
+// [c*kAdjChunk, (c+1)*kAdjChunk) of the slice goes to part[chunk][rhs][lane].
+template <typename T, int RPW, bool COMP>
+__device__ void adj_sparse_item(const BlockDev* __restrict__ blocks, int nblocks, const T* __restrict__ y,
+                                int64_t ld, cx<T>* __restrict__ part, int64_t nrhs, const T* __restrict__ rowscale,
+                                const int* __restrict__ cbase, int2 it, int64_t r0, int lane) {
+  int i = 0;
+  while (i < nblocks - 1 && it.x >= blocks[i].t_gbase + blocks[i].tslices) ++i;
+  const BlockDev& b = blocks[i];
+  const int gl = it.x - b.t_gbase;
+  const int64_t k = int64_t(gl) * 32 + lane;
+  const int W = b.t_width[gl];
+  const int j0 = it.y * kAdjChunk;
+  const int j1 = min(W, j0 + kAdjChunk);
+  const int n0 = b.t_n0[k];
+  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
+  const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.t_val) + b.t_off[gl] + lane;
+  Acc<T, COMP> re[RPW], im[RPW];
+#pragma unroll 4
+  for (int j = j0; j < j1; ++j) {
+    const cx<T> c = val[j * 32];
+    const int64_t row = n0 + j;
+    const T rs = rowscale ? rowscale[row] : T(1);
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      if (q < nq) {
+        const T v = y[(r0 + q) * ld + row] * rs;
+        re[q].add(c.re, v);
+        im[q].add(c.im, v);
+      }
+    }
+  }
+  cx<T>* out = part + ((int64_t(cbase[it.x]) + it.y) * nrhs + r0) * 32 + lane;
+#pragma unroll
+  for (int q = 0; q < RPW; ++q)
+    if (q < nq) out[q * 32] = cx<T>{re[q].value(), im[q].value()};
+}
+
+// ------------------------------------------------------------ adjoint FFT
+// Sum of the chunk partials of bin k of a block for right-hand side r.
+template <typename T>
+__device__ __forceinline__ cx<T> gather_bin(const cx<T>* __restrict__ part, const int* __restrict__ cbase,
+                                            int gbase, int k, int64_t r, int64_t nrhs) {
+  const int g = gbase + (k >> 5);
+  const int c0 = cbase[g], c1 = cbase[g + 1];
+  cx<T> u{T(0), T(0)};
+  for (int c = c0; c < c1; ++c) u = u + part[(int64_t(c) * nrhs + r) * 32 + (k & 31)];
+  return u;
+}
+
+template <typename T>
+__device__ void adj_fft_body(const BlockDev& b, int64_t r, const cx<T>* __restrict__ part,
+                             const int* __restrict__ cbase, int64_t nrhs, T* __restrict__ x, int64_t ld,
+                             const T* __restrict__ colscale, cx<T>* s, int tid, int nthreads) {
+  const int n = b.n, j_lo = b.j_lo, j_hi = b.j_hi, off = b.off;
+  const int* __restrict__ perm = b.perm;
+  const cx<T>* __restrict__ tw = static_cast<const cx<T>*>(b.tw);
+  const T* __restrict__ invw = static_cast<const T*>(b.invw);
+  for (int k = tid; k <= n / 2; k += nthreads) {
+    cx<T> Uk = gather_bin(part, cbase, b.t_gbase, k, r, nrhs);
+    cx<T> Unk = gather_bin(part, cbase, b.t_gbase, n - k, r, nrhs);
+    if (k == 0) {
+      Uk.im = T(0);    // U_0 and U_n enter as real numbers
+      Unk.im = T(0);
+    }
+    cx<T> Zk, Znk;
+    c2r_merge(Uk, Unk, k, tw, &Zk, &Znk);
+    // inverse FFT as conj(FFT(conj(Z)))
+    s[perm[k]] = conj(Zk);
+    if (k != 0 && n - k != k) s[perm[n - k]] = conj(Znk);
+  }
+  __syncthreads();
+  fft_inplace<T>(s, n, b.p, b.radix, tw, tid, nthreads);
+  T* __restrict__ xr = x + r * ld;
+  for (int j = tid; j < n; j += nthreads) {
+    const cx<T> v = s[j];
+    const int j0 = 2 * j, j1 = 2 * j + 1;
+    if (j0 >= j_lo && j0 < j_hi) {
+      T u = v.re * invw[j0];
+      if (colscale) u *= colscale[j0 - off];
+      xr[j0 - off] = u;
+    }
+    if (j1 >= j_lo && j1 < j_hi) {
+      T u = -v.im * invw[j1];
+      if (colscale) u *= colscale[j1 - off];
+      xr[j1 - off] = u;
+    }
+  }
+}
+
+// ------------------------------------------------------------ adjoint tail
+// One warp: x_m = colscale_m sum_n tail[m][n] rowscale_n y_n for one RHS.
+template <typename T, bool COMP>
+__device__ void adj_tail_warp(int64_t N, int64_t m, int64_t r, const T* __restrict__ tail, const T* __restrict__ y,
+                              int64_t ld, T* __restrict__ x, const T* __restrict__ rowscale,
+                              const T* __restrict__ colscale, int lane) {
+  Acc<T, COMP> acc;
+  for (int64_t n = lane; n < N; n += 32) acc.add(tail[m * N + n], y[r * ld + n] * (rowscale ? rowscale[n] : T(1)));
+  T v = acc.value();
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) x[r * ld + m] = v * (colscale ? colscale[m] : T(1));
+}
+
+}  // namespace xc

@@ -935,7 +935,13 @@ int build_plan_device(Plan* p) {
   std::stable_sort(items.begin(), items.end(),
                    [](const std::pair<int, int2>& a, const std::pair<int, int2>& b) { return a.first > b.first; });
   std::vector<int2> titems(items.size());
-  for (size_t k = 0; k < items.size(); ++k) titems[k] = items[k].second;
+  p->item_len.resize(items.size());
+  for (size_t k = 0; k < items.size(); ++k) {
+    titems[k] = items[k].second;
+    p->item_len[k] = items[k].first;
+  }
+  p->item_host = titems;
+  p->slice_cost = fcost;
   XC_TRY(upload(p, titems, &p->t_items));
   XC_TRY(upload(p, cbase, &p->t_cbase));
   {

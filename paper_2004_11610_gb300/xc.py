@@ -49,6 +49,13 @@ class xc_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
+class xc_batch_stats(ctypes.Structure):
+    _fields_ = [("nplans", ctypes.c_int), ("rhs_per_item", ctypes.c_int), ("tuned", ctypes.c_int),
+                ("tasks_forward", ctypes.c_int64), ("tasks_adjoint", ctypes.c_int64),
+                ("shared_bytes", ctypes.c_int64), ("matrix_bytes", ctypes.c_int64),
+                ("adjoint_bytes", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _SIGS = {
@@ -69,6 +76,15 @@ _SIGS = {
     "xc_timing_read": (ctypes.c_int, [_P, ctypes.POINTER(xc_kernel_time), ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_int)]),
     "xc_launch_count": (ctypes.c_int64, []),
+    "xc_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
+    "xc_batch_bind": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I64),
+                                     ctypes.POINTER(_I64)]),
+    "xc_batch_apply": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "xc_batch_tune": (ctypes.c_int, [_P, _P]),
+    "xc_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(xc_batch_stats)]),
+    "xc_batch_status": (ctypes.c_int, [_P, _P]),
+    "xc_batch_debug_set": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _I64]),
+    "xc_batch_destroy": (ctypes.c_int, [_P]),
     "xc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "xc_last_error_message": (ctypes.c_char_p, []),
 }
@@ -256,6 +272,70 @@ class Plan:
 
     def sync_status(self) -> None:
         _check(_lib.xc_sync_status(self._h), "xc_sync_status")
+
+
+# -------------------------------------------------------------------- batches
+
+class Batch:
+    """Many plans of one precision applied by one persistent launch per
+    direction (xc_batch_*).  Bind device tensors once; `apply` then launches
+    without allocating or synchronising (CUDA-graph capturable)."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (_P * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = _P()
+        _check(_lib.xc_batch_create(ctypes.byref(h), arr, len(self.plans)), "xc_batch_create")
+        self._h = h
+        self._bound = None
+
+    def bind(self, xs, ys):
+        """xs[i], ys[i]: CUDA tensors (nrhs_i, N_i) of plan i's dtype."""
+        n = len(self.plans)
+        for p, a, b in zip(self.plans, xs, ys):
+            p._check_tensor(a, "x")
+            p._check_tensor(b, "y")
+        xp = (_P * n)(*[a.data_ptr() for a in xs])
+        yp = (_P * n)(*[b.data_ptr() for b in ys])
+        nr = (_I64 * n)(*[a.shape[0] for a in xs])
+        ld = (_I64 * n)(*[a.stride(0) for a in xs])
+        _check(_lib.xc_batch_bind(self._h, xp, yp, nr, ld), "xc_batch_bind")
+        self._bound = (list(xs), list(ys))
+
+    def apply(self, adjoint: bool = False, stream=None):
+        _check(_lib.xc_batch_apply(self._h, 1 if adjoint else 0, _stream_handle(stream)), "xc_batch_apply")
+
+    def tune(self, stream=None):
+        _check(_lib.xc_batch_tune(self._h, _stream_handle(stream)), "xc_batch_tune")
+
+    def info(self) -> dict:
+        st = xc_batch_stats()
+        _check(_lib.xc_batch_info(self._h, ctypes.byref(st)), "xc_batch_info")
+        return {k: getattr(st, k) for k, _ in xc_batch_stats._fields_}
+
+    def status(self, stream=None) -> int:
+        """XC_OK or XC_ERR_TIMEOUT (cleared on read)."""
+        return int(_lib.xc_batch_status(self._h, _stream_handle(stream)))
+
+    def debug_set(self, plan: int, extra_need: int, wait_limit: int) -> None:
+        _check(_lib.xc_batch_debug_set(self._h, plan, extra_need, wait_limit), "xc_batch_debug_set")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.xc_batch_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 # ------------------------------------------------------------------- autograd

@@ -72,3 +72,15 @@ def test_structure_layouts_match_the_header(xc):
     assert ctypes.sizeof(xc.xc_params) == 72
     assert xc.xc_plan_stats.L.offset == 56
     assert ctypes.sizeof(xc.xc_plan_stats) == 56 + 7 * 8 * 16 + 24
+
+
+def test_batch_arguments_are_checked_on_the_host(xc):
+    h = ctypes.c_void_p()
+    assert xc._lib.xc_batch_create(None, None, 1) == xc.XC_ERR_ARG
+    assert xc._lib.xc_batch_create(ctypes.byref(h), None, 1) == xc.XC_ERR_ARG
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert xc._lib.xc_batch_create(ctypes.byref(h), arr, 0) == xc.XC_ERR_ARG
+    assert xc._lib.xc_batch_create(ctypes.byref(h), arr, 2) == xc.XC_ERR_ARG
+    assert not h.value
+    assert xc._lib.xc_batch_apply(None, 0, None) == xc.XC_ERR_ARG
+    assert xc._lib.xc_batch_debug_set(None, 0, 0, 1) == xc.XC_ERR_ARG

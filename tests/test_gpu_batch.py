@@ -1,0 +1,143 @@
+"""The many-plan persistent launch (xc_batch_*): results equal the single-plan
+applies, the launch replays from a CUDA graph, the autotuner keeps results
+unchanged, and an injected missing dependency ends in XC_ERR_TIMEOUT (a
+bounded device wait) rather than a hang."""
+import numpy as np
+import pytest
+
+from paper_2004_11610_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2004_11610_gb300 import build
+    build.build()
+    from paper_2004_11610_gb300 import xc as mod
+    return mod
+
+
+def make_batch(xc, nplans, precision, seed, nmax=3000):
+    """Mixed families, log-uniform N, 1..32 right-hand sides (a small copy of
+    the 1000-plan workload)."""
+    g = np.random.default_rng(seed)
+    fams = ("chebyshev", "legendre", "jacobi", "hermite")
+    plans, xs, ys = [], [], []
+    for i in range(nplans):
+        N = int(round(np.exp(g.uniform(np.log(40), np.log(nmax)))))
+        fam = fams[i % 4]
+        R = int(g.integers(1, 33))
+        p = xc.Plan(fam, N, 1e-7, precision=precision, alpha=0.5, beta=-0.5)
+        plans.append(p)
+        x = torch.from_numpy(inputs.normal(N, R, 80, i)).to("cuda", p.torch_dtype)
+        xs.append(x)
+        ys.append(torch.empty_like(x))
+    return plans, xs, ys
+
+
+def close_all(plans):
+    for p in plans:
+        p.close()
+
+
+def rel(a, b):
+    return float((a.double() - b.double()).abs().max() / b.double().abs().max().clamp_min(1e-300))
+
+
+@pytest.mark.parametrize("precision,nplans", [("fp32", 24), ("fp64", 9), ("fp32c", 8)])
+def test_batch_matches_single_plan_applies(xc, precision, nplans):
+    plans, xs, ys = make_batch(xc, nplans, precision, 1)
+    try:
+        with xc.Batch(plans) as b:
+            b.bind(xs, ys)
+            b.apply(adjoint=False)
+            torch.cuda.synchronize()
+            assert b.status() == xc.XC_OK
+            for p, x, y in zip(plans, xs, ys):
+                assert rel(y, p.apply(x)) <= 1e-12
+            y_saved = [y.clone() for y in ys]
+            b.apply(adjoint=True)          # reads y, writes x
+            torch.cuda.synchronize()
+            assert b.status() == xc.XC_OK
+            for p, x, y in zip(plans, xs, y_saved):
+                assert rel(x, p.apply_adjoint(y)) <= 1e-12
+    finally:
+        close_all(plans)
+
+
+def test_batch_graph_capture_and_replay(xc):
+    plans, xs, ys = make_batch(xc, 16, "fp32", 2)
+    try:
+        with xc.Batch(plans) as b:
+            b.bind(xs, ys)
+            b.apply(False)                 # warm-up outside the capture
+            b.apply(True)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                with torch.cuda.graph(graph, stream=stream):
+                    b.apply(False, stream=stream)
+            for rep in range(2):
+                for i, (p, x) in enumerate(zip(plans, xs)):
+                    x.copy_(torch.from_numpy(inputs.normal(p.N, x.shape[0], 81 + rep, i)).to(x.dtype))
+                graph.replay()
+                torch.cuda.synchronize()
+                assert b.status() == xc.XC_OK
+                for p, x, y in zip(plans, xs, ys):
+                    assert rel(y, p.apply(x)) <= 1e-12
+    finally:
+        close_all(plans)
+
+
+def test_batch_autotune_keeps_results(xc):
+    plans, xs, ys = make_batch(xc, 12, "fp32", 3)
+    try:
+        with xc.Batch(plans) as b:
+            b.bind(xs, ys)
+            x0 = [x.clone() for x in xs]
+            b.tune()
+            assert all(torch.equal(a, c) for a, c in zip(xs, x0))   # inputs restored
+            info = b.info()
+            assert info["tuned"] == 1 and info["rhs_per_item"] in (1, 2, 4, 8)
+            b.apply(False)
+            torch.cuda.synchronize()
+            for p, x, y in zip(plans, xs, ys):
+                assert rel(y, p.apply(x)) <= 1e-12
+    finally:
+        close_all(plans)
+
+
+def test_batch_missing_dependency_times_out_without_hanging(xc):
+    plans, xs, ys = make_batch(xc, 6, "fp32", 4)
+    try:
+        with xc.Batch(plans) as b:
+            b.bind(xs, ys)
+            b.debug_set(3, 1, 2000)        # plan 3 waits for one FFT that never comes
+            b.apply(False)
+            torch.cuda.synchronize()
+            assert b.status() == xc.XC_ERR_TIMEOUT
+            assert b.status() == xc.XC_OK   # cleared on read
+            b.debug_set(3, 0, 1 << 22)
+            b.apply(False)
+            torch.cuda.synchronize()
+            assert b.status() == xc.XC_OK
+            for p, x, y in zip(plans, xs, ys):
+                assert rel(y, p.apply(x)) <= 1e-12
+    finally:
+        close_all(plans)
+
+
+def test_batch_rejects_mixed_precision(xc):
+    a = xc.Plan("legendre", 100, 1e-8, precision="fp64")
+    c = xc.Plan("legendre", 100, 1e-8, precision="fp32")
+    try:
+        with pytest.raises(xc.XcError):
+            xc.Batch([a, c])
+    finally:
+        a.close()
+        c.close()
