@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
 
 // Persistent grid: as many CTAs as can be resident, but no more than the
 // items need.
-int persistent_grid(const void* fn, int64_t items, unsigned* grid) {
+int persistent_grid(const void* fn, int64_t items, unsigned* grid, int items_per_warp = 1) {
   static thread_local int cached_sms = 0;
   if (cached_sms == 0) {
     int dev = 0;
@@ -120,7 +120,8 @@ int persistent_grid(const void* fn, int64_t items, unsigned* grid) {
   if (per_sm < 1) per_sm = 1;
   // every resident warp takes part (warps that find the list empty retire at
   // once); the dynamic schedule balances SMs and their schedulers
-  const int64_t need = (items + kSparseWarps - 1) / kSparseWarps;
+  const int64_t per_cta = int64_t(kSparseWarps) * items_per_warp;
+  const int64_t need = (items + per_cta - 1) / per_cta;
   const int64_t g = std::min<int64_t>(int64_t(cached_sms) * per_sm, std::max<int64_t>(1, need));
   *grid = unsigned(g);
   return XC_OK;
@@ -179,7 +180,9 @@ template <typename T, bool COMP, int RPW>
 int launch_sparse_fwd_rpw(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
   const void* fn = reinterpret_cast<const void*>(fwd_sparse_kernel<T, RPW, COMP>);
   unsigned grid = 1;
-  XC_TRY(persistent_grid(fn, p->nslices * ((nrhs + RPW - 1) / RPW), &grid));
+  // forward items cannot be split along the band, so each warp should see
+  // several of them for the dynamic schedule to balance the tail
+  XC_TRY(persistent_grid(fn, p->nslices * ((nrhs + RPW - 1) / RPW), &grid, 4));
   launch_begin(p, K_FWD_SPARSE, st);
   fwd_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
       static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->N, static_cast<const T*>(x), ld,
@@ -211,7 +214,7 @@ int launch_sparse_adj_rpw(Plan* p, const void* y, int64_t nrhs, int64_t ld, cuda
 // better; FP32 needs the reuse.
 template <typename T, bool COMP>
 int launch_sparse_fwd(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
-  if (sizeof(T) == 8 && nrhs >= 2) return launch_sparse_fwd_rpw<T, COMP, 2>(p, x, y, nrhs, ld, st);
+  if (sizeof(T) == 8) return launch_sparse_fwd_rpw<T, COMP, 1>(p, x, y, nrhs, ld, st);
   if (nrhs >= 8) return launch_sparse_fwd_rpw<T, COMP, 8>(p, x, y, nrhs, ld, st);
   if (nrhs >= 4) return launch_sparse_fwd_rpw<T, COMP, 4>(p, x, y, nrhs, ld, st);
   if (nrhs >= 2) return launch_sparse_fwd_rpw<T, COMP, 2>(p, x, y, nrhs, ld, st);
