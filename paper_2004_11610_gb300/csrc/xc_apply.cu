@@ -69,15 +69,16 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
     fwd_sparse_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N, const T* __restrict__ x,
                       int64_t ld, T* __restrict__ y, const cx<T>* __restrict__ spec, int64_t nrhs,
                       const T* __restrict__ rowscale, const T* __restrict__ colscale, const T* __restrict__ tail,
-                      int64_t m_tail, const int* __restrict__ order, unsigned* counters) {
+                      int64_t m_tail, const int* __restrict__ order, unsigned* counters, int sg) {
+  // item = (slice, supergroup of sg groups of RPW right-hand sides)
   const int lane = threadIdx.x & 31;
-  const int64_t ngroups = (nrhs + RPW - 1) / RPW;
-  const int64_t total = ((N + 31) / 32) * ngroups;
+  const int64_t nsup = ((nrhs + RPW - 1) / RPW + sg - 1) / sg;
+  const int64_t total = ((N + 31) / 32) * nsup;
   for (;;) {
     const int64_t t = take_item(&counters[0], lane);
     if (t >= total) break;
     fwd_sparse_item<T, RPW, COMP>(blocks, nblocks, N, x, ld, y, spec, nrhs, rowscale, colscale, tail, m_tail,
-                                  order[t / ngroups], (t % ngroups) * RPW, lane);
+                                  order[t / nsup], (t % nsup) * int64_t(sg) * RPW, lane, sg);
   }
   retire_warp(&counters[0], &counters[1], gridDim.x * kSparseWarps, lane);
 }
@@ -92,16 +93,16 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
     adj_sparse_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N, const T* __restrict__ y,
                       int64_t ld, cx<T>* __restrict__ part, int64_t nrhs, const T* __restrict__ rowscale,
                       const int2* __restrict__ items, const int* __restrict__ cbase, int64_t total_chunks,
-                      unsigned* counters) {
+                      unsigned* counters, int sg) {
   (void)N;
   const int lane = threadIdx.x & 31;
-  const int64_t ngroups = (nrhs + RPW - 1) / RPW;
-  const int64_t total = total_chunks * ngroups;
+  const int64_t nsup = ((nrhs + RPW - 1) / RPW + sg - 1) / sg;
+  const int64_t total = total_chunks * nsup;
   for (;;) {
     const int64_t t = take_item(&counters[2], lane);
     if (t >= total) break;
-    adj_sparse_item<T, RPW, COMP>(blocks, nblocks, y, ld, part, nrhs, rowscale, cbase, items[t / ngroups],
-                                  (t % ngroups) * RPW, lane);
+    adj_sparse_item<T, RPW, COMP>(blocks, nblocks, y, ld, part, nrhs, rowscale, cbase, items[t / nsup],
+                                  (t % nsup) * int64_t(sg) * RPW, lane, sg);
   }
   retire_warp(&counters[2], &counters[3], gridDim.x * kSparseWarps, lane);
 }
@@ -148,6 +149,23 @@ __global__ void adj_tail_kernel(int64_t N, int64_t m_tail, const T* __restrict__
   adj_tail_warp<T, COMP>(N, m, blockIdx.y, tail, y, ld, x, rowscale, colscale, threadIdx.x & 31);
 }
 
+// Right-hand-side groups per item: enough items for ~4 per resident warp,
+// and no more groups per item than that, so that short bands (FP32 plans,
+// small blocks) amortise each item's bookkeeping over several groups.
+int supergroup(const void* fn, int64_t units, int64_t ngroups) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * kSparseWarps, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  const int64_t warps = int64_t(sms) * std::max(1, per_sm) * kSparseWarps;
+  const int64_t want_items = 4 * warps;
+  const int64_t have = std::max<int64_t>(1, units * ngroups);
+  if (have <= want_items) return 1;
+  return int(std::min<int64_t>(ngroups, (have + want_items - 1) / want_items));
+}
+
 // ------------------------------------------------------------------ launch
 template <typename T>
 int launch_fft(Plan* p, bool forward, const void* in, void* out, int64_t nrhs, int64_t ld, cudaStream_t st) {
@@ -182,12 +200,14 @@ int launch_sparse_fwd_rpw(Plan* p, const void* x, void* y, int64_t nrhs, int64_t
   unsigned grid = 1;
   // forward items cannot be split along the band, so each warp should see
   // several of them for the dynamic schedule to balance the tail
-  XC_TRY(persistent_grid(fn, p->nslices * ((nrhs + RPW - 1) / RPW), &grid, 4));
+  const int64_t ngroups = (nrhs + RPW - 1) / RPW;
+  const int sg = supergroup(fn, p->nslices, ngroups);
+  XC_TRY(persistent_grid(fn, p->nslices * ((ngroups + sg - 1) / sg), &grid, 4));
   launch_begin(p, K_FWD_SPARSE, st);
   fwd_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
       static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->N, static_cast<const T*>(x), ld,
       static_cast<T*>(y), static_cast<const cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale),
-      static_cast<const T*>(p->colscale), static_cast<const T*>(p->tail), p->m_tail, p->f_order, p->counters);
+      static_cast<const T*>(p->colscale), static_cast<const T*>(p->tail), p->m_tail, p->f_order, p->counters, sg);
   launch_end(p, K_FWD_SPARSE, st);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
@@ -198,12 +218,14 @@ int launch_sparse_adj_rpw(Plan* p, const void* y, int64_t nrhs, int64_t ld, cuda
   if (p->total_chunks == 0) return XC_OK;
   const void* fn = reinterpret_cast<const void*>(adj_sparse_kernel<T, RPW, COMP>);
   unsigned grid = 1;
-  XC_TRY(persistent_grid(fn, p->total_chunks * ((nrhs + RPW - 1) / RPW), &grid));
+  const int64_t ngroups = (nrhs + RPW - 1) / RPW;
+  const int sg = supergroup(fn, p->total_chunks, ngroups);
+  XC_TRY(persistent_grid(fn, p->total_chunks * ((ngroups + sg - 1) / sg), &grid));
   launch_begin(p, K_ADJ_SPARSE, st);
   adj_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
       static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->N, static_cast<const T*>(y), ld,
       static_cast<cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale), p->t_items, p->t_cbase,
-      p->total_chunks, p->counters);
+      p->total_chunks, p->counters, sg);
   launch_end(p, K_ADJ_SPARSE, st);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
@@ -314,7 +336,7 @@ int apply_noalloc_impl(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld
   fwd_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
       bd, int(p->blocks.size()), p->N, static_cast<const T*>(x), ld, static_cast<T*>(y),
       static_cast<const cx<T>*>(spec), nrhs, static_cast<const T*>(p->rowscale),
-      static_cast<const T*>(p->colscale), static_cast<const T*>(p->tail), p->m_tail, p->f_order, p->counters);
+      static_cast<const T*>(p->colscale), static_cast<const T*>(p->tail), p->m_tail, p->f_order, p->counters, 1);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
 }

@@ -85,13 +85,18 @@ __device__ void fwd_fft_body(const BlockDev& b, int64_t r, const T* __restrict__
 // ------------------------------------------------------- forward sparse
 // Lane = row.  Each band value is loaded once (coalesced across the slice)
 // and used for the RPW right-hand sides; the spectra are gathered through L1.
+// `groups` consecutive groups of RPW right-hand sides starting at r_begin are
+// processed one after the other (the slice's band layout is read once).
 template <typename T, int RPW, bool COMP>
 __device__ void fwd_sparse_item(const BlockDev* __restrict__ blocks, int nblocks, int64_t N,
                                 const T* __restrict__ x, int64_t ld, T* __restrict__ y,
                                 const cx<T>* __restrict__ spec, int64_t nrhs, const T* __restrict__ rowscale,
                                 const T* __restrict__ colscale, const T* __restrict__ tail, int64_t m_tail,
-                                int64_t slice, int64_t r0, int lane) {
+                                int64_t slice, int64_t r_begin, int lane, int groups = 1) {
   const int64_t n = slice * 32 + lane;
+  for (int grp = 0; grp < groups; ++grp) {
+  const int64_t r0 = r_begin + int64_t(grp) * RPW;
+  if (r0 >= nrhs) break;
   const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
   Acc<T, COMP> acc[RPW];
   for (int i = 0; i < nblocks; ++i) {
@@ -139,6 +144,7 @@ __device__ void fwd_sparse_item(const BlockDev* __restrict__ blocks, int nblocks
     for (int q = 0; q < RPW; ++q)
       if (q < nq) y[(r0 + q) * ld + n] = acc[q].value() * rs;
   }
+  }
 }
 
 // ------------------------------------------------------- adjoint sparse
@@ -147,7 +153,7 @@ __device__ void fwd_sparse_item(const BlockDev* __restrict__ blocks, int nblocks
 template <typename T, int RPW, bool COMP>
 __device__ void adj_sparse_item(const BlockDev* __restrict__ blocks, int nblocks, const T* __restrict__ y,
                                 int64_t ld, cx<T>* __restrict__ part, int64_t nrhs, const T* __restrict__ rowscale,
-                                const int* __restrict__ cbase, int2 it, int64_t r0, int lane) {
+                                const int* __restrict__ cbase, int2 it, int64_t r_begin, int lane, int groups = 1) {
   int i = 0;
   while (i < nblocks - 1 && it.x >= blocks[i].t_gbase + blocks[i].tslices) ++i;
   const BlockDev& b = blocks[i];
@@ -157,8 +163,12 @@ __device__ void adj_sparse_item(const BlockDev* __restrict__ blocks, int nblocks
   const int j0 = it.y * kAdjChunk;
   const int j1 = min(W, j0 + kAdjChunk);
   const int n0 = b.t_n0[k];
-  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
   const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.t_val) + b.t_off[gl] + lane;
+  const int64_t cb = cbase[it.x];
+  for (int grp = 0; grp < groups; ++grp) {
+  const int64_t r0 = r_begin + int64_t(grp) * RPW;
+  if (r0 >= nrhs) break;
+  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
   Acc<T, COMP> re[RPW], im[RPW];
 #pragma unroll 4
   for (int j = j0; j < j1; ++j) {
@@ -174,10 +184,11 @@ __device__ void adj_sparse_item(const BlockDev* __restrict__ blocks, int nblocks
       }
     }
   }
-  cx<T>* out = part + ((int64_t(cbase[it.x]) + it.y) * nrhs + r0) * 32 + lane;
+  cx<T>* out = part + ((cb + it.y) * nrhs + r0) * 32 + lane;
 #pragma unroll
   for (int q = 0; q < RPW; ++q)
     if (q < nq) out[q * 32] = cx<T>{re[q].value(), im[q].value()};
+  }
 }
 
 // ------------------------------------------------------------ adjoint FFT
