@@ -111,6 +111,24 @@ def step_bytes(info, nrhs, precision):
     return info["matrix_bytes"] + info["adjoint_bytes"] + vec + spec
 
 
+# ------------------------------------------------------------------ ranks
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank number over all ranks (the slowest replica sets
+    the job's time).  Works with any torch.distributed backend."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_per_step: float, steps: int, max_ms: float, world: int) -> float:
+    """Whole-job units per second: every rank processes its own units
+    (replicas, weak scaling), the job takes the slowest rank's time."""
+    return world * units_per_rank_per_step * steps / (max_ms / 1e3)
+
+
 # ------------------------------------------------------------------- clocks
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -188,9 +206,15 @@ def time_oracle(wl, sample_rhs, min_seconds, max_reps=1000):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = inputs.WORKLOADS[args.workload]
     from oracle import families as F
     from oracle import method as M
+    if args.workload == "batch1000":
+        # bounded sample: the first plans of the batch with N <= 1024
+        sample = [w for w in inputs.batch_workload(args.nplans) if w[1] <= 1024][:4]
+        wl = {"plans": [(f, N, p) for f, N, p, _ in sample], "eps": 1e-7, "precision": "fp32", "nrhs": 1,
+              "dist": "normal"}
+    else:
+        wl = inputs.WORKLOADS[args.workload]
     plans = []
     for i, (fam, N, params) in enumerate(wl["plans"]):
         sp = F.make_spec(fam, N, params.get("alpha", 0.0), params.get("beta", 0.0))
@@ -212,7 +236,9 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.workload, wl) | {"sample": "1 right-hand side per plan and direction per step"},
+        "config": (workload_config(args.workload, wl) if args.workload != "batch1000" else {"workload": "batch1000"})
+        | {"sample": "1 right-hand side per plan and direction per step"
+           + ("" if args.workload != "batch1000" else "; 4 plans of the batch with N <= 1024")},
         "cpu_baseline": {"value": value, "unit": "vectors/s", "cores": 1, "kind": "oracle",
                          "sample": "1 RHS per plan, forward + adjoint, numpy/scipy single-threaded"},
         "e2e": {"value": value, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -221,21 +247,30 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU path
-def traffic_from_profiles(kernel, workload):
-    """dram bytes per launch from the committed ncu summary of this kernel and
-    workload, if the kernel source has not changed since the capture."""
+def kernel_source_hash():
+    """sha256 over the sources of the execution kernels (changes whenever a
+    kernel does)."""
+    h = hashlib.sha256()
+    for f in ("xc_items.cuh", "xc_apply.cu", "xc_batch.cu", "xc_fft.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2004_11610_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def traffic_from_profiles(kernel, workload, plan=None):
+    """dram bytes of one launch from the committed ncu summary of this kernel
+    and workload (line `traffic: <kernel> plan=<i> dram_bytes=<B>`), provided
+    the kernel sources have not changed since the capture (`source_sha256:`)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}__{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     h = re.search(r"source_sha256:\s*([0-9a-f]{16,64})", text)
-    if not m or not h:
+    if not h or not kernel_source_hash().startswith(h.group(1)):
         return None
-    src = open(os.path.join(ROOT, "paper_2004_11610_gb300", "csrc", "xc_apply.cu"), "rb").read()
-    if not hashlib.sha256(src).hexdigest().startswith(h.group(1)):
-        return None
-    return float(m.group(1))
+    for m in re.finditer(r"traffic:\s*(\S+)\s+plan=(\S+)\s+dram_bytes=([0-9.eE+]+)", text):
+        if m.group(1) == kernel and (plan is None or m.group(2) == str(plan)):
+            return float(m.group(3))
+    return None
 
 
 def run_xc(args, rank, world, local_rank):
@@ -300,41 +335,40 @@ def run_xc(args, rank, world, local_rank):
         flush.zero_()
         step()
     torch.cuda.synchronize(dev)
-    per_kernel = {}
-    for p, info in zip(plans, infos):
+    per_kernel, per_pair = {}, {}
+    for pi, (p, info) in enumerate(zip(plans, infos)):
         work = algorithmic_work(info, R, prec)
         for name, (n, ms) in p.timing_read().items():
-            e = per_kernel.setdefault(name, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
-            e["launches"] += n
-            e["ms"] += ms
-            e["flops"] += work[name][0] * n
-            e["bytes"] += work[name][1] * n
+            for key, table in ((name, per_kernel), ((pi, name), per_pair)):
+                e = table.setdefault(key, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+                e["launches"] += n
+                e["ms"] += ms
+                e["flops"] += work[name][0] * n
+                e["bytes"] += work[name][1] * n
         p.timing_enable(False)
     clock_info = clocks.stop()
 
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms = reduce_max(total_ms, world, dev)
     vectors_per_step = sum(2 * R for _ in plans)
-    value = world * vectors_per_step * args.steps / (max_ms / 1e3)
+    value = job_throughput(vectors_per_step, args.steps, max_ms, world)
     ms_per_step = max_ms / args.steps
 
-    # roofline of the dominant kernel (largest summed device time)
-    dom = max(per_kernel.items(), key=lambda kv: kv[1]["ms"])
-    name, e = dom
+    # roofline of the dominant kernel: the (plan, kernel) pair with the largest
+    # summed device time
+    (dom_plan, name), e = max(per_pair.items(), key=lambda kv: kv[1]["ms"])
     avg_ms = e["ms"] / e["launches"]
     flops_per_launch = e["flops"] / e["launches"]
     achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
     fp64 = prec == "fp64"
     roofline = {
-        "kernel": name, "bound": "alu", "achieved": achieved, "unit": "TFLOP/s",
+        "kernel": name, "plan": f"{specs[dom_plan]['family']} N={specs[dom_plan]['N']}",
+        "bound": "alu", "achieved": achieved, "unit": "TFLOP/s",
         "peak": FP64_PEAK_TFLOPS if fp64 else 152 * 128 * 2 * 2.070e9 / 1e12,
         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz" if fp64
         else "derived: 152 SMs x 128 FP32 FMA/clk x 2 flops x 2070 MHz",
     }
     roofline["frac"] = achieved / roofline["peak"]
-    tb = traffic_from_profiles(name, args.workload)
+    tb = traffic_from_profiles(name, args.workload, dom_plan)
     roofline["traffic"] = tb
     roofline["algorithmic_bytes_per_launch"] = e["bytes"] / e["launches"]
     roofline["avg_launch_ms"] = avg_ms
@@ -371,11 +405,8 @@ def run_xc(args, rank, world, local_rank):
     for _ in range(e2e_steps):
         e2e_step()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    e2e_val = world * vectors_per_step * e2e_steps / float(t.item())
+    e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
+    e2e_val = job_throughput(vectors_per_step, e2e_steps, 1e3 * e2e_s, world)
     eb = 8 if prec == "fp64" else 4
     io_bytes = sum(2 * R * s["N"] * eb for s in specs)
 
@@ -539,11 +570,8 @@ def run_batch(args, rank, world, local_rank):
         dir_ms[1] += ev[2].elapsed_time(ev[3])
     clock_info = clocks.stop()
     dir_ms = [d / nrep for d in dir_ms]
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * vectors_per_step * args.steps / (max_ms / 1e3)
+    max_ms = reduce_max(total_ms, world, dev)
+    value = job_throughput(vectors_per_step, args.steps, max_ms, world)
     ms_per_step = max_ms / args.steps
 
     # algorithmic bytes of one launch per direction (matrices once, vectors, spectra)
@@ -560,7 +588,8 @@ def run_batch(args, rank, world, local_rank):
     achieved = (fwd_bytes, adj_bytes)[dom] / (dir_ms[dom] / 1e3) / 1e9
     roofline = {"kernel": ("batch_kernel (forward)", "batch_kernel (adjoint)")[dom], "bound": "hbm",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_source": hbm_src, "traffic": traffic_from_profiles("batch_kernel", "batch1000"),
+                "peak_source": hbm_src,
+                "traffic": traffic_from_profiles("batch_kernel", "batch1000", ("forward", "adjoint")[dom]),
                 "algorithmic_bytes_per_launch": (fwd_bytes, adj_bytes)[dom], "avg_launch_ms": dir_ms[dom]}
 
     # end to end: pinned host inputs copied in, both launches, results copied out

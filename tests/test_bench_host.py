@@ -1,0 +1,66 @@
+"""Host-side logic of bench.py: the cross-rank reduction under a real
+two-rank torch.distributed group (gloo on CPU), the replica throughput
+formula, and the reference arm's rank handling."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        local_ms = 10.0 + 5.0 * rank            # rank 1 is the slow replica
+        m = bench.reduce_max(local_ms, world)
+        v = bench.job_throughput(100, 4, m, world)
+        out.put((rank, m, v))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_reduce_max_and_throughput_over_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, m, v in res:
+        assert m == 15.0                       # every rank sees the slowest time
+        assert v == pytest.approx(2 * 100 * 4 / 0.015)
+
+
+def test_job_throughput_single_rank():
+    import bench
+    assert bench.job_throughput(64, 10, 5.0, 1) == pytest.approx(64 * 10 / 0.005)
+    assert bench.reduce_max(3.5, 1) == 3.5
+
+
+def test_reference_arm_non_zero_rank_exits_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
