@@ -231,25 +231,44 @@ int launch_sparse_adj_rpw(Plan* p, const void* y, int64_t nrhs, int64_t ld, cuda
   return XC_OK;
 }
 
-// Right-hand sides per item: FP64 is bound by the FP64 pipe, where reusing a
+// Right-hand sides per item.  FP64 is bound by the FP64 pipe, where reusing a
 // band value over more right-hand sides buys nothing and finer items balance
-// better; FP32 needs the reuse.
+// better.  FP32 gains from the reuse, but only while the items still outnumber
+// the resident warps about twice: plans with few slices and long bands
+// (Hermite and Laguerre functions) otherwise leave most of the GPU idle.
+int choose_rpw(int preferred, int64_t units, int64_t nrhs) {
+  static thread_local int64_t warps = 0;
+  if (warps == 0) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    warps = int64_t(sms) * 32;   // a typical resident count for these kernels
+  }
+  int r = preferred;
+  while (r > 1 && (r > nrhs || units * ((nrhs + r - 1) / r) < 2 * warps)) r /= 2;
+  return r;
+}
+
 template <typename T, bool COMP>
 int launch_sparse_fwd(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
-  if (sizeof(T) == 8) return launch_sparse_fwd_rpw<T, COMP, 1>(p, x, y, nrhs, ld, st);
-  if (nrhs >= 8) return launch_sparse_fwd_rpw<T, COMP, 8>(p, x, y, nrhs, ld, st);
-  if (nrhs >= 4) return launch_sparse_fwd_rpw<T, COMP, 4>(p, x, y, nrhs, ld, st);
-  if (nrhs >= 2) return launch_sparse_fwd_rpw<T, COMP, 2>(p, x, y, nrhs, ld, st);
-  return launch_sparse_fwd_rpw<T, COMP, 1>(p, x, y, nrhs, ld, st);
+  switch (choose_rpw(sizeof(T) == 8 ? 1 : 8, p->nslices, nrhs)) {
+    case 8: return launch_sparse_fwd_rpw<T, COMP, 8>(p, x, y, nrhs, ld, st);
+    case 4: return launch_sparse_fwd_rpw<T, COMP, 4>(p, x, y, nrhs, ld, st);
+    case 2: return launch_sparse_fwd_rpw<T, COMP, 2>(p, x, y, nrhs, ld, st);
+    default: return launch_sparse_fwd_rpw<T, COMP, 1>(p, x, y, nrhs, ld, st);
+  }
 }
 
 template <typename T, bool COMP>
 int launch_sparse_adj(Plan* p, const void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
-  if (sizeof(T) == 8 && nrhs >= 2) return launch_sparse_adj_rpw<T, COMP, 2>(p, y, nrhs, ld, st);
-  if (nrhs >= 8) return launch_sparse_adj_rpw<T, COMP, 8>(p, y, nrhs, ld, st);
-  if (nrhs >= 4) return launch_sparse_adj_rpw<T, COMP, 4>(p, y, nrhs, ld, st);
-  if (nrhs >= 2) return launch_sparse_adj_rpw<T, COMP, 2>(p, y, nrhs, ld, st);
-  return launch_sparse_adj_rpw<T, COMP, 1>(p, y, nrhs, ld, st);
+  switch (choose_rpw(sizeof(T) == 8 ? 2 : 8, p->total_chunks, nrhs)) {
+    case 8: return launch_sparse_adj_rpw<T, COMP, 8>(p, y, nrhs, ld, st);
+    case 4: return launch_sparse_adj_rpw<T, COMP, 4>(p, y, nrhs, ld, st);
+    case 2: return launch_sparse_adj_rpw<T, COMP, 2>(p, y, nrhs, ld, st);
+    default: return launch_sparse_adj_rpw<T, COMP, 1>(p, y, nrhs, ld, st);
+  }
 }
 
 template <typename T, bool COMP>
