@@ -117,7 +117,11 @@ int xc_plan_reserve(xc_plan_t plan, int64_t nrhs);
 /*
  * xc_apply -- y = A x (Algorithm 1 step 2 / Algorithm 3): per block, extend the
  * input with zero extra components (eq. (Fe1) / (Fe3)), divide by the window,
- * FFT, multiply by the compressed matrix; add the dense tail.
+ * FFT, multiply by the compressed matrix; add the dense tail.  Plans whose
+ * bands (summed over blocks) exceed 512 bins in some 32-row slice sum each
+ * row's band in chunks of 256 bins and add the chunks in a fixed order; the
+ * summation order is a property of the plan, so a column's result does not
+ * depend on nrhs, on the stream or on batching.
  *   x_dev  device, [nrhs][ld] of the plan's I/O type (read only)
  *   y_dev  device, [nrhs][ld] (written; must not alias x_dev)
  *   nrhs   number of right-hand sides (0 is a no-op)
@@ -210,9 +214,11 @@ int xc_dense_matrix(xc_plan_t plan, void* A_dev, int64_t lda, void* stream);
  * applied by one persistent kernel launch per direction.  The launch works
  * through a device task list over all plans: phase 1 (forward: the FFTs;
  * adjoint: the transposed band products and dense tails), then phase 2
- * (forward: the band products and tails; adjoint: the inverse FFTs).  A
- * phase-2 task of a plan waits, with a bounded number of sleeps, until all
- * phase-1 tasks of that plan have finished; a wait that runs out sets the
+ * (forward: the band products and tails; adjoint: the inverse FFTs), then,
+ * for the forward products of long-band plans, phase 3 (the sums of their
+ * chunk partials, as in xc_apply).  A task of a phase waits, with a bounded
+ * number of sleeps, until all tasks of the plan's previous phase have
+ * finished; a wait that runs out sets the
  * batch's status to XC_ERR_TIMEOUT (read by xc_batch_status) instead of
  * hanging.  This is the batched form of Algorithms 1-4; the paper itself
  * applies one matrix at a time.
@@ -220,8 +226,9 @@ int xc_dense_matrix(xc_plan_t plan, void* A_dev, int64_t lda, void* stream);
 typedef struct xc_batch* xc_batch_t;
 typedef struct {
   int nplans;
-  int rhs_per_item;          /* right-hand sides per band-product task (tuned) */
+  int rhs_per_item;          /* right-hand sides per forward band-product task (tuned) */
   int tuned;                 /* 1 after xc_batch_tune */
+  int rhs_per_item_adjoint;  /* right-hand sides per adjoint band-product task (tuned) */
   int64_t tasks_forward, tasks_adjoint;
   int64_t shared_bytes;      /* dynamic shared memory of the persistent kernel */
   int64_t matrix_bytes, adjoint_bytes;   /* summed over the plans */

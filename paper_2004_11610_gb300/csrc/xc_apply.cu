@@ -83,6 +83,36 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
   retire_warp(&counters[0], &counters[1], gridDim.x * kSparseWarps, lane);
 }
 
+// Chunked forward (plans with long bands): item = (unit, supergroup).
+template <typename T, int RPW, bool COMP>
+__global__ void __launch_bounds__(32 * kSparseWarps)
+    fwd_unit_kernel(const BlockDev* __restrict__ blocks, const cx<T>* __restrict__ spec, int64_t nrhs,
+                    cx<T>* __restrict__ part, const int4* __restrict__ units, const int* __restrict__ order,
+                    int64_t total_units, unsigned* counters, int sg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nsup = ((nrhs + RPW - 1) / RPW + sg - 1) / sg;
+  const int64_t total = total_units * nsup;
+  for (;;) {
+    const int64_t t = take_item(&counters[0], lane);
+    if (t >= total) break;
+    const int u = order[t / nsup];
+    fwd_unit_item<T, RPW, COMP>(blocks, spec, nrhs, part, units[u], u, (t % nsup) * int64_t(sg) * RPW, lane, sg);
+  }
+  retire_warp(&counters[0], &counters[1], gridDim.x * kSparseWarps, lane);
+}
+
+// Thread per (row, RHS); grid.y strides over the right-hand sides.
+template <typename T, bool COMP>
+__global__ void fwd_reduce_kernel(int64_t N, const T* __restrict__ x, int64_t ld, T* __restrict__ y,
+                                  const cx<T>* __restrict__ part, int64_t nrhs, const int* __restrict__ ubase,
+                                  const T* __restrict__ rowscale, const T* __restrict__ colscale,
+                                  const T* __restrict__ tail, int64_t m_tail) {
+  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  for (int64_t r = blockIdx.y; r < nrhs; r += gridDim.y)
+    fwd_reduce_row<T, COMP>(N, x, ld, y, part, nrhs, ubase, rowscale, colscale, tail, m_tail, n, r);
+}
+
 // ------------------------------------------------------- adjoint sparse
 // Chunking keeps bins that are covered by thousands of rows (the small last
 // blocks, high frequencies of the Laguerre functions) from becoming one long
@@ -214,6 +244,32 @@ int launch_sparse_fwd_rpw(Plan* p, const void* x, void* y, int64_t nrhs, int64_t
 }
 
 template <typename T, bool COMP, int RPW>
+int launch_unit_fwd_rpw(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  const void* fn = reinterpret_cast<const void*>(fwd_unit_kernel<T, RPW, COMP>);
+  unsigned grid = 1;
+  const int64_t ngroups = (nrhs + RPW - 1) / RPW;
+  const int sg = supergroup(fn, p->total_units, ngroups);
+  XC_TRY(persistent_grid(fn, p->total_units * ((ngroups + sg - 1) / sg), &grid, 4));
+  cx<T>* spec = static_cast<cx<T>*>(p->scratch);
+  cx<T>* part = spec + p->spec_per_rhs * nrhs;
+  launch_begin(p, K_FWD_SPARSE, st);
+  fwd_unit_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
+      static_cast<const BlockDev*>(p->scratch_desc), spec, nrhs, part, p->fu_units, p->fu_order, p->total_units,
+      p->counters, sg);
+  launch_end(p, K_FWD_SPARSE, st);
+  XC_CUDA(cudaGetLastError());
+  dim3 rgrid(unsigned((p->N + 255) / 256), unsigned(std::min<int64_t>(nrhs, 65535)));
+  launch_begin(p, K_FWD_REDUCE, st);
+  fwd_reduce_kernel<T, COMP><<<rgrid, 256, 0, st>>>(p->N, static_cast<const T*>(x), ld, static_cast<T*>(y), part,
+                                                    nrhs, p->fu_ubase, static_cast<const T*>(p->rowscale),
+                                                    static_cast<const T*>(p->colscale),
+                                                    static_cast<const T*>(p->tail), p->m_tail);
+  launch_end(p, K_FWD_REDUCE, st);
+  XC_CUDA(cudaGetLastError());
+  return XC_OK;
+}
+
+template <typename T, bool COMP, int RPW>
 int launch_sparse_adj_rpw(Plan* p, const void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
   if (p->total_chunks == 0) return XC_OK;
   const void* fn = reinterpret_cast<const void*>(adj_sparse_kernel<T, RPW, COMP>);
@@ -253,7 +309,16 @@ int choose_rpw(int preferred, int64_t units, int64_t nrhs) {
 
 template <typename T, bool COMP>
 int launch_sparse_fwd(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
-  switch (choose_rpw(sizeof(T) == 8 ? 1 : 8, p->nslices, nrhs)) {
+  const int pref = sizeof(T) == 8 ? 1 : 8;
+  if (p->fwd_chunked) {
+    switch (choose_rpw(pref, p->total_units, nrhs)) {
+      case 8: return launch_unit_fwd_rpw<T, COMP, 8>(p, x, y, nrhs, ld, st);
+      case 4: return launch_unit_fwd_rpw<T, COMP, 4>(p, x, y, nrhs, ld, st);
+      case 2: return launch_unit_fwd_rpw<T, COMP, 2>(p, x, y, nrhs, ld, st);
+      default: return launch_unit_fwd_rpw<T, COMP, 1>(p, x, y, nrhs, ld, st);
+    }
+  }
+  switch (choose_rpw(pref, p->nslices, nrhs)) {
     case 8: return launch_sparse_fwd_rpw<T, COMP, 8>(p, x, y, nrhs, ld, st);
     case 4: return launch_sparse_fwd_rpw<T, COMP, 4>(p, x, y, nrhs, ld, st);
     case 2: return launch_sparse_fwd_rpw<T, COMP, 2>(p, x, y, nrhs, ld, st);
@@ -389,8 +454,10 @@ int ensure_scratch(Plan* p, int64_t nrhs) {
   }
   if (nrhs <= p->scratch_nrhs) return XC_OK;
   const size_t cbytes = 2 * p->elem_bytes();
-  // forward spectra and adjoint chunk partials share the buffer (one direction at a time)
-  const int64_t per_rhs = std::max<int64_t>({1, p->spec_per_rhs, p->total_chunks * 32});
+  // forward spectra (+ forward unit partials) and adjoint chunk partials share
+  // the buffer (one direction at a time)
+  const int64_t fwd = p->spec_per_rhs + (p->fwd_chunked ? p->total_units * 32 : 0);
+  const int64_t per_rhs = std::max<int64_t>({1, fwd, p->total_chunks * 32});
   const size_t bytes = size_t(per_rhs) * size_t(nrhs) * cbytes;
   void* fresh = nullptr;
   if (cudaMalloc(&fresh, bytes) != cudaSuccess) {

@@ -4,17 +4,23 @@
 // right-hand sides).  Binding I/O buffers builds, per direction, one device
 // task list over all plans:
 //   forward   phase 1: FFT of (plan, block, RHS)              [fwd_fft_body]
-//             phase 2: band product of (plan, 8 row slices, RPW RHS) + tail
+//             phase 2: band product of (plan, 8 row slices, RPW RHS) + tail;
+//                      for plans with long bands, of (plan, 8 band chunks,
+//                      RPW RHS) into partial sums               [fwd_unit_item]
+//             phase 3: (long-band plans) partials + tail of (plan, 256 rows,
+//                      32 RHS)                                  [fwd_reduce_row]
 //   adjoint   phase 1: transposed band product of (plan, 8 chunks, RPW RHS),
 //                      and the dense tail of (plan, RHS)
 //             phase 2: inverse FFT of (plan, block, RHS)
 // Every CTA of a persistent grid takes tasks from a device counter in list
-// order; all phase-1 tasks precede all phase-2 tasks, and within a phase the
-// costliest tasks come first.  A phase-2 task of plan p waits until every
-// phase-1 task of p has finished: phase-1 tasks increment done[p] when they
-// end; a phase-2 task reads done[p] with acquire semantics and waits, for a
-// bounded number of sleeps, until it reaches need[p].  Because every phase-1
-// task has been taken (and so is running) before any phase-2 task starts, the
+// order; all phase-1 tasks precede all phase-2 tasks (and those all phase-3
+// tasks), and within a phase the costliest tasks come first.  A phase-2 task
+// of plan p waits until every phase-1 task of p has finished: phase-1 tasks
+// increment done[p] when they end; a phase-2 task reads done[p] with acquire
+// semantics and waits, for a bounded number of sleeps, until it reaches
+// need[p].  Phase-3 tasks wait in the same way on done[nplans + p], which the
+// chunked phase-2 tasks increment.  Because every task of a phase has been
+// taken (and so is running) before any task of the next phase starts, the
 // waits end; if one does not end within the limit, the status word records a
 // timeout, the remaining tasks are skipped and the host reads XC_ERR_TIMEOUT.
 // The last CTA to finish resets the counters, so a launch needs no memset and
@@ -40,7 +46,10 @@ namespace {
 
 constexpr int kBatchThreads = 256;
 constexpr int kBatchWarps = kBatchThreads / 32;
-enum TaskKind { T_FWD_FFT = 0, T_FWD_SPARSE = 1, T_ADJ_SPARSE = 2, T_ADJ_FFT = 3, T_ADJ_TAIL = 4 };
+enum TaskKind {
+  T_FWD_FFT = 0, T_FWD_SPARSE = 1, T_ADJ_SPARSE = 2, T_ADJ_FFT = 3, T_ADJ_TAIL = 4, T_FWD_UNIT = 5, T_FWD_REDUCE = 6
+};
+constexpr int kReduceRhs = 32;   // right-hand sides per phase-3 task
 
 struct BatchPlanDev {
   const BlockDev* blocks;
@@ -52,6 +61,11 @@ struct BatchPlanDev {
   const void* colscale;
   const int2* t_items;
   const int* t_cbase;
+  const int4* fu_units;      // chunked forward (nullptr: direct band product)
+  const int* fu_order;
+  const int* fu_ubase;
+  int64_t total_units;
+  int64_t spec_per_rhs;      // the unit partials follow the spectra in scratch
   void* scratch;
   const void* x;
   void* y;
@@ -100,8 +114,10 @@ __global__ void __launch_bounds__(kBatchThreads)
     const BatchPlanDev& P = plans[tk.y];
     const BlockDev* blocks = P.blocks;
     if (tid == 0) {
-      if (tk.x == T_FWD_SPARSE || tk.x == T_ADJ_FFT)
+      if (tk.x == T_FWD_SPARSE || tk.x == T_FWD_UNIT || tk.x == T_ADJ_FFT)
         s_ok = wait_for(&done[tk.y], need[tk.y], wait_limit, status);
+      else if (tk.x == T_FWD_REDUCE)
+        s_ok = wait_for(&done[nplans + tk.y], need[nplans + tk.y], wait_limit, status);
       else
         s_ok = *(volatile unsigned*)status == 0u;
     }
@@ -120,6 +136,27 @@ __global__ void __launch_bounds__(kBatchThreads)
             fwd_sparse_item<T, RPW, COMP>(blocks, P.nblocks, P.N, static_cast<const T*>(P.x), P.ld,
                                           static_cast<T*>(P.y), static_cast<const cx<T>*>(P.scratch), P.nrhs, rs, cs,
                                           static_cast<const T*>(P.tail), P.m_tail, slice, int64_t(tk.w) * RPW, lane);
+          break;
+        }
+        case T_FWD_UNIT: {
+          const int64_t k = int64_t(tk.z) + warp;
+          if (k < P.total_units) {
+            const int u = P.fu_order[k];
+            fwd_unit_item<T, RPW, COMP>(blocks, static_cast<const cx<T>*>(P.scratch), P.nrhs,
+                                        static_cast<cx<T>*>(P.scratch) + P.spec_per_rhs * P.nrhs, P.fu_units[u], u,
+                                        int64_t(tk.w) * RPW, lane);
+          }
+          break;
+        }
+        case T_FWD_REDUCE: {
+          const int64_t n = int64_t(tk.z) * kBatchThreads + tid;
+          if (n < P.N) {
+            const int64_t r1 = min(P.nrhs, int64_t(tk.w) + kReduceRhs);
+            for (int64_t r = tk.w; r < r1; ++r)
+              fwd_reduce_row<T, COMP>(P.N, static_cast<const T*>(P.x), P.ld, static_cast<T*>(P.y),
+                                      static_cast<const cx<T>*>(P.scratch) + P.spec_per_rhs * P.nrhs, P.nrhs,
+                                      P.fu_ubase, rs, cs, static_cast<const T*>(P.tail), P.m_tail, n, r);
+          }
           break;
         }
         case T_ADJ_SPARSE: {
@@ -141,11 +178,11 @@ __global__ void __launch_bounds__(kBatchThreads)
           break;
       }
     }
-    if (tk.x == T_FWD_FFT || tk.x == T_ADJ_SPARSE) {
+    if (tk.x == T_FWD_FFT || tk.x == T_ADJ_SPARSE || tk.x == T_FWD_UNIT) {
       __syncthreads();                        // every thread's results are written
       if (tid == 0) {
         __threadfence();
-        atomicAdd(&done[tk.y], 1u);
+        atomicAdd(&done[tk.x == T_FWD_UNIT ? nplans + tk.y : tk.y], 1u);
       }
     }
     __syncthreads();                          // s_task / s_ok are reused
@@ -156,7 +193,7 @@ __global__ void __launch_bounds__(kBatchThreads)
   }
   __syncthreads();
   if (s_last) {
-    for (int p = tid; p < nplans; p += kBatchThreads) done[p] = 0u;
+    for (int p = tid; p < 2 * nplans; p += kBatchThreads) done[p] = 0u;
     __syncthreads();
     if (tid == 0) {
       *next = 0u;
@@ -175,10 +212,10 @@ struct Batch {
   int64_t ntasks[2] = {0, 0};
   unsigned* need[2] = {nullptr, nullptr};
   unsigned* ctrl = nullptr;      // [0] next task, [1] finished CTAs, [2] status
-  unsigned* done = nullptr;      // [nplans]
+  unsigned* done = nullptr;      // [2 * nplans]: phase-1, phase-2 completions per plan
   std::vector<int> extra_need;   // fault injection (tests)
   long long wait_limit = 1LL << 22;   // sleeps of ~256 ns: about a second
-  int rpw = 0;                   // right-hand sides per band item (0 = not bound)
+  int rpw[2] = {0, 0};           // right-hand sides per band item, per direction (0 = not bound)
   bool tuned = false;
   size_t smem = 0;
   int64_t max_n = 0;
@@ -202,11 +239,12 @@ struct Batch {
 
 namespace {
 
-// Task lists of both directions for the bound right-hand sides and `rpw`.
-int build_tasks(Batch* b, int rpw) {
+// Task lists of both directions for the bound right-hand sides, with rpw_f
+// (forward) and rpw_a (adjoint) right-hand sides per band item.
+int build_tasks(Batch* b, int rpw_f, int rpw_a) {
   const int np = int(b->plans.size());
-  std::vector<std::pair<double, int4>> ph1, ph2;
-  std::vector<unsigned> need_f(np, 0), need_a(np, 0);
+  std::vector<std::pair<double, int4>> ph1, ph2, ph3;
+  std::vector<unsigned> need_f(2 * size_t(np), 0), need_a(2 * size_t(np), 0);
   // forward
   for (int p = 0; p < np; ++p) {
     const Plan* P = b->plans[p];
@@ -219,7 +257,21 @@ int build_tasks(Batch* b, int rpw) {
         ++need_f[p];
       }
     }
+    const int rpw = rpw_f;
     const int64_t groups = (R + rpw - 1) / rpw;
+    if (P->fwd_chunked) {
+      for (int64_t k0 = 0; k0 < P->total_units; k0 += kBatchWarps) {
+        const double c = double(P->unit_len[k0]);   // longest first
+        for (int64_t g = 0; g < groups; ++g) {
+          ph2.push_back({c * rpw, int4{T_FWD_UNIT, p, int(k0), int(g)}});
+          ++need_f[np + p];
+        }
+      }
+      for (int64_t n0 = 0; n0 < P->N; n0 += kBatchThreads)
+        for (int64_t r0 = 0; r0 < R; r0 += kReduceRhs)
+          ph3.push_back({0.0, int4{T_FWD_REDUCE, p, int(n0 / kBatchThreads), int(r0)}});
+      continue;
+    }
     for (int64_t s0 = 0; s0 < P->nslices; s0 += kBatchWarps) {
       double c = 0;
       for (int64_t s = s0; s < std::min<int64_t>(P->nslices, s0 + kBatchWarps); ++s)
@@ -235,6 +287,7 @@ int build_tasks(Batch* b, int rpw) {
   std::vector<int4> fwd;
   for (auto& e : ph1) fwd.push_back(e.second);
   for (auto& e : ph2) fwd.push_back(e.second);
+  for (auto& e : ph3) fwd.push_back(e.second);
   // adjoint
   ph1.clear();
   ph2.clear();
@@ -242,6 +295,7 @@ int build_tasks(Batch* b, int rpw) {
     const Plan* P = b->plans[p];
     const int64_t R = b->nrhs[p];
     if (R == 0) continue;
+    const int rpw = rpw_a;
     const int64_t groups = (R + rpw - 1) / rpw;
     for (int64_t i0 = 0; i0 < P->total_chunks; i0 += kBatchWarps) {
       double c = 0;
@@ -280,9 +334,10 @@ int build_tasks(Batch* b, int rpw) {
     b->ntasks[d] = int64_t(lists2[d]->size());
     if (!lists2[d]->empty())
       XC_CUDA(cudaMemcpy(b->tasks[d], lists2[d]->data(), lists2[d]->size() * sizeof(int4), cudaMemcpyHostToDevice));
-    XC_CUDA(cudaMemcpy(b->need[d], needs[d]->data(), size_t(np) * sizeof(unsigned), cudaMemcpyHostToDevice));
+    XC_CUDA(cudaMemcpy(b->need[d], needs[d]->data(), 2 * size_t(np) * sizeof(unsigned), cudaMemcpyHostToDevice));
   }
-  b->rpw = rpw;
+  b->rpw[0] = rpw_f;
+  b->rpw[1] = rpw_a;
   return XC_OK;
 }
 
@@ -308,7 +363,7 @@ int launch_batch_rpw(Batch* b, int dir, cudaStream_t st) {
 
 template <typename T, bool COMP>
 int launch_batch_t(Batch* b, int dir, cudaStream_t st) {
-  switch (b->rpw) {
+  switch (b->rpw[dir]) {
     case 1: return launch_batch_rpw<T, COMP, 1>(b, dir, st);
     case 2: return launch_batch_rpw<T, COMP, 2>(b, dir, st);
     case 4: return launch_batch_rpw<T, COMP, 4>(b, dir, st);
@@ -325,9 +380,9 @@ int launch_batch(Batch* b, int dir, cudaStream_t st) {
   }
 }
 
-// Tuning cache: batch signature -> chosen right-hand sides per item.
+// Tuning cache: batch signature -> chosen right-hand sides per item (forward, adjoint).
 std::mutex g_tune_mutex;
-std::map<std::string, int> g_tune_cache;
+std::map<std::string, std::pair<int, int>> g_tune_cache;
 
 std::string signature(const Batch* b) {
   std::string sig = std::to_string(b->precision) + ":" + std::to_string(b->plans.size());
@@ -374,15 +429,15 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans) {
   int rc = b->alloc(&ptr, 4 * sizeof(unsigned));
   if (rc == XC_OK) {
     b->ctrl = static_cast<unsigned*>(ptr);
-    rc = b->alloc(&ptr, size_t(nplans) * sizeof(unsigned));
+    rc = b->alloc(&ptr, 2 * size_t(nplans) * sizeof(unsigned));
   }
   if (rc == XC_OK) {
     b->done = static_cast<unsigned*>(ptr);
-    rc = b->alloc(&ptr, size_t(nplans) * sizeof(unsigned));
+    rc = b->alloc(&ptr, 2 * size_t(nplans) * sizeof(unsigned));
   }
   if (rc == XC_OK) {
     b->need[0] = static_cast<unsigned*>(ptr);
-    rc = b->alloc(&ptr, size_t(nplans) * sizeof(unsigned));
+    rc = b->alloc(&ptr, 2 * size_t(nplans) * sizeof(unsigned));
   }
   if (rc == XC_OK) {
     b->need[1] = static_cast<unsigned*>(ptr);
@@ -391,7 +446,7 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans) {
   if (rc == XC_OK) {
     b->dplans = static_cast<xc::BatchPlanDev*>(ptr);
     if (cudaMemset(b->ctrl, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(b->done, 0, size_t(nplans) * sizeof(unsigned)) != cudaSuccess)
+        cudaMemset(b->done, 0, 2 * size_t(nplans) * sizeof(unsigned)) != cudaSuccess)
       rc = xc::cuda_check(cudaGetLastError(), "cudaMemset");
   }
   if (rc != XC_OK) {
@@ -432,6 +487,13 @@ int xc_batch_bind(xc_batch_t batch, const void* const* x_dev, void* const* y_dev
     d.colscale = p->colscale;
     d.t_items = p->t_items;
     d.t_cbase = p->t_cbase;
+    if (p->fwd_chunked) {
+      d.fu_units = p->fu_units;
+      d.fu_order = p->fu_order;
+      d.fu_ubase = p->fu_ubase;
+      d.total_units = p->total_units;
+    }
+    d.spec_per_rhs = p->spec_per_rhs;
     d.scratch = p->scratch;
     d.x = x_dev[i];
     d.y = y_dev[i];
@@ -439,26 +501,27 @@ int xc_batch_bind(xc_batch_t batch, const void* const* x_dev, void* const* y_dev
     d.ld = ld[i];
   }
   XC_CUDA(cudaMemcpy(b->dplans, host.data(), size_t(np) * sizeof(xc::BatchPlanDev), cudaMemcpyHostToDevice));
-  int rpw = b->rpw > 0 ? b->rpw : (b->precision == XC_FP64 ? 2 : 8);
+  const int dflt = b->precision == XC_FP64 ? 2 : 8;
+  std::pair<int, int> rpw{b->rpw[0] > 0 ? b->rpw[0] : dflt, b->rpw[1] > 0 ? b->rpw[1] : dflt};
   {
     std::lock_guard<std::mutex> lock(xc::g_tune_mutex);
     auto it = xc::g_tune_cache.find(xc::signature(b));
     if (it != xc::g_tune_cache.end()) rpw = it->second;
   }
-  return xc::build_tasks(b, rpw);
+  return xc::build_tasks(b, rpw.first, rpw.second);
 }
 
 int xc_batch_apply(xc_batch_t batch, int adjoint, void* stream) {
   auto* b = reinterpret_cast<xc::Batch*>(batch);
   if (!b) return fail(XC_ERR_ARG, "batch is NULL");
-  if (b->rpw == 0) return fail(XC_ERR_ARG, "bind the batch's buffers first");
+  if (b->rpw[0] == 0) return fail(XC_ERR_ARG, "bind the batch's buffers first");
   return xc::launch_batch(b, adjoint ? 1 : 0, static_cast<cudaStream_t>(stream));
 }
 
 int xc_batch_tune(xc_batch_t batch, void* stream) {
   auto* b = reinterpret_cast<xc::Batch*>(batch);
   if (!b) return fail(XC_ERR_ARG, "batch is NULL");
-  if (b->rpw == 0) return fail(XC_ERR_ARG, "bind the batch's buffers first");
+  if (b->rpw[0] == 0) return fail(XC_ERR_ARG, "bind the batch's buffers first");
   auto st = static_cast<cudaStream_t>(stream);
   // the trial launches overwrite x (adjoint) and y (forward): keep copies
   const size_t eb = b->precision == XC_FP64 ? 8 : 4;
@@ -485,31 +548,37 @@ int xc_batch_tune(xc_batch_t batch, void* stream) {
       }
     }
   }
-  cudaEvent_t e0, e1;
-  XC_CUDA(cudaEventCreate(&e0));
-  XC_CUDA(cudaEventCreate(&e1));
-  int best = b->rpw;
-  float best_ms = 1e30f;
+  // each direction is timed on its own: the forward and adjoint band
+  // products favour different numbers of right-hand sides per item
+  cudaEvent_t ev[3];
+  for (auto& e : ev) XC_CUDA(cudaEventCreate(&e));
+  int best[2] = {b->rpw[0], b->rpw[1]};
+  float best_ms[2] = {1e30f, 1e30f};
   for (int cand : {1, 2, 4, 8}) {
-    XC_TRY(xc::build_tasks(b, cand));
+    XC_TRY(xc::build_tasks(b, cand, cand));
     XC_TRY(xc::launch_batch(b, 0, st));   // warm
     XC_TRY(xc::launch_batch(b, 1, st));
-    XC_CUDA(cudaEventRecord(e0, st));
+    float ms[2] = {0, 0};
     for (int rep = 0; rep < 3; ++rep) {
+      XC_CUDA(cudaEventRecord(ev[0], st));
       XC_TRY(xc::launch_batch(b, 0, st));
+      XC_CUDA(cudaEventRecord(ev[1], st));
       XC_TRY(xc::launch_batch(b, 1, st));
+      XC_CUDA(cudaEventRecord(ev[2], st));
+      XC_CUDA(cudaEventSynchronize(ev[2]));
+      float f = 0, a = 0;
+      XC_CUDA(cudaEventElapsedTime(&f, ev[0], ev[1]));
+      XC_CUDA(cudaEventElapsedTime(&a, ev[1], ev[2]));
+      ms[0] += f;
+      ms[1] += a;
     }
-    XC_CUDA(cudaEventRecord(e1, st));
-    XC_CUDA(cudaEventSynchronize(e1));
-    float ms = 0;
-    XC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = cand;
-    }
+    for (int d = 0; d < 2; ++d)
+      if (ms[d] < best_ms[d]) {
+        best_ms[d] = ms[d];
+        best[d] = cand;
+      }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (auto& e : ev) cudaEventDestroy(e);
   for (size_t i = 0; i < b->plans.size(); ++i) {
     const size_t bytes = size_t(b->nrhs[i]) * size_t(b->ld[i]) * eb;
     if (bytes == 0) continue;
@@ -517,10 +586,10 @@ int xc_batch_tune(xc_batch_t batch, void* stream) {
     XC_CUDA(cudaMemcpyAsync(b->y[i], saved[2 * i + 1], bytes, cudaMemcpyDeviceToDevice, st));
   }
   XC_CUDA(cudaStreamSynchronize(st));
-  XC_TRY(xc::build_tasks(b, best));
+  XC_TRY(xc::build_tasks(b, best[0], best[1]));
   b->tuned = true;
   std::lock_guard<std::mutex> lock(xc::g_tune_mutex);
-  xc::g_tune_cache[xc::signature(b)] = best;
+  xc::g_tune_cache[xc::signature(b)] = {best[0], best[1]};
   return XC_OK;
 }
 
@@ -529,7 +598,8 @@ int xc_batch_info(xc_batch_t batch, xc_batch_stats* out) {
   if (!b || !out) return fail(XC_ERR_ARG, "NULL argument");
   std::memset(out, 0, sizeof(*out));
   out->nplans = int(b->plans.size());
-  out->rhs_per_item = b->rpw;
+  out->rhs_per_item = b->rpw[0];
+  out->rhs_per_item_adjoint = b->rpw[1];
   out->tuned = b->tuned ? 1 : 0;
   out->tasks_forward = b->ntasks[0];
   out->tasks_adjoint = b->ntasks[1];
@@ -563,7 +633,7 @@ int xc_batch_debug_set(xc_batch_t batch, int plan, int extra_need, int64_t wait_
     return fail(XC_ERR_ARG, "bad debug setting");
   b->extra_need[plan] = extra_need;
   b->wait_limit = wait_limit;
-  if (b->rpw > 0) return xc::build_tasks(b, b->rpw);
+  if (b->rpw[0] > 0) return xc::build_tasks(b, b->rpw[0], b->rpw[1]);
   return XC_OK;
 }
 

@@ -85,6 +85,10 @@ struct BlockDev {
 // slices are cut into chunks whose partial sums the adjoint FFT adds up.
 constexpr int kAdjChunk = 256;
 
+// Band rows per chunk of a row slice in the forward product of plans with long
+// bands; a reduction kernel adds the chunks of each slice.
+constexpr int kFwdChunk = 256;
+
 // ------------------------------------------------------------------- the plan
 struct Plan {
   int64_t N = 0;
@@ -109,6 +113,13 @@ struct Plan {
   int* t_cbase = nullptr;              // [total_tslices + 1]: first chunk of each bin slice
   int64_t total_chunks = 0;
   std::vector<int64_t> slice_cost;     // host: summed forward band width of each row slice
+  // forward chunking (plans with long bands): units (block, slice, chunk, rows)
+  bool fwd_chunked = false;
+  int4* fu_units = nullptr;            // [total_units]
+  int* fu_order = nullptr;             // [total_units], longest first
+  int* fu_ubase = nullptr;             // [nslices + 1]: first unit of each slice (units of a slice are consecutive)
+  int64_t total_units = 0;
+  std::vector<int> unit_len;           // host: rows of each unit (in fu_order order)
   std::vector<int> item_len;           // host: rows of each adjoint chunk, in t_items order
   std::vector<int2> item_host;         // host copy of t_items
   int64_t nslices = 0, total_tslices = 0;
@@ -138,7 +149,7 @@ struct Plan {
 int plan_alloc(Plan* p, void** ptr, size_t bytes);
 
 // Kernel identities for the launch counter and the per-kernel timing.
-enum KernelId { K_FWD_FFT = 0, K_FWD_SPARSE, K_ADJ_SPARSE, K_ADJ_FFT, K_ADJ_TAIL, K_COUNT };
+enum KernelId { K_FWD_FFT = 0, K_FWD_SPARSE, K_ADJ_SPARSE, K_ADJ_FFT, K_ADJ_TAIL, K_FWD_REDUCE, K_COUNT };
 const char* kernel_name(int id);
 // Bracket one launch: begin() before it, end() after it (counts the launch and,
 // when timing is on, records events on the stream).

@@ -10,6 +10,10 @@
 //                     plus the dense tail; C = g_k A_e W F / sqrt(L) carries the
 //                     unitary and half-spectrum factors, so
 //                     Re(C conj F) = Re C Re F + Im C Im F.
+//   fwd_unit_item     the same over one chunk of a slice's band (plans with
+//                     long bands), partial sums out
+//   fwd_reduce_row    one (row, RHS): adds a chunked slice's partials and the
+//                     dense tail.
 // Adjoint, x = A^T y (Algorithm 2 step 2 / Algorithm 4):
 //   adj_sparse_item   one (chunk of rows of a 32-bin slice, RPW RHS): partial
 //                     sums of z_k = sum_n CT_kn y_n
@@ -41,6 +45,18 @@ struct Acc {
       const T err = (s - (t - bb)) + (p - bb);
       s = t;
       c += err + e;
+    }
+  }
+  // adds a partial sum given as a (sum, compensation) pair
+  __device__ __forceinline__ void add_pair(T ps, T pc) {
+    if constexpr (!COMP) {
+      s += ps;
+    } else {
+      const T t = s + ps;
+      const T bb = t - s;
+      const T err = (s - (t - bb)) + (ps - bb);
+      s = t;
+      c += err + pc;
     }
   }
   __device__ __forceinline__ T value() const { return COMP ? s + c : s; }
@@ -145,6 +161,80 @@ __device__ void fwd_sparse_item(const BlockDev* __restrict__ blocks, int nblocks
       if (q < nq) y[(r0 + q) * ld + n] = acc[q].value() * rs;
   }
   }
+}
+
+// ------------------------------------------- forward sparse, chunked bands
+// Plans whose bands run to thousands of bins (Hermite and Laguerre functions)
+// have few row slices with long serial loops; their bands are cut into units
+// (block, slice, chunk of kFwdChunk band rows).  A unit writes the partial
+// sums of its rows as (sum, compensation) pairs to part[u][rhs][lane];
+// fwd_reduce_row adds the units of a slice in unit order (deterministic).
+template <typename T, int RPW, bool COMP>
+__device__ void fwd_unit_item(const BlockDev* __restrict__ blocks, const cx<T>* __restrict__ spec, int64_t nrhs,
+                              cx<T>* __restrict__ part, int4 unit, int64_t u, int64_t r_begin, int lane,
+                              int groups = 1) {
+  const BlockDev& b = blocks[unit.x];
+  const int64_t slice = unit.y;
+  const int64_t n = slice * 32 + lane;
+  const int j0 = unit.z * kFwdChunk, j1 = j0 + unit.w;
+  const int k0 = b.f_k0[n];
+  const int H = b.H;
+  const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.f_val) + b.f_off[slice] + lane;
+  for (int grp = 0; grp < groups; ++grp) {
+    const int64_t r0 = r_begin + int64_t(grp) * RPW;
+    if (r0 >= nrhs) break;
+    const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
+    const cx<T>* __restrict__ F = spec + b.spec_off * nrhs + r0 * H + k0;
+    Acc<T, COMP> acc[RPW];
+    if (nq == RPW) {
+#pragma unroll 4
+      for (int j = j0; j < j1; ++j) {
+        const cx<T> c = val[j * 32];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          const cx<T> f = F[q * H + j];
+          acc[q].add(c.re, f.re);
+          acc[q].add(c.im, f.im);
+        }
+      }
+    } else {
+      for (int j = j0; j < j1; ++j) {
+        const cx<T> c = val[j * 32];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          if (q < nq) {
+            const cx<T> f = F[q * H + j];
+            acc[q].add(c.re, f.re);
+            acc[q].add(c.im, f.im);
+          }
+        }
+      }
+    }
+    cx<T>* out = part + (u * nrhs + r0) * 32 + lane;
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+      if (q < nq) out[q * 32] = cx<T>{acc[q].s, acc[q].c};
+  }
+}
+
+// y_n for one (row n < N, RHS r) of a chunked plan: the unit partials of the
+// row's slice in unit order, plus the dense tail, times the row scaling.
+template <typename T, bool COMP>
+__device__ __forceinline__ void fwd_reduce_row(int64_t N, const T* __restrict__ x, int64_t ld, T* __restrict__ y,
+                                               const cx<T>* __restrict__ part, int64_t nrhs,
+                                               const int* __restrict__ ubase, const T* __restrict__ rowscale,
+                                               const T* __restrict__ colscale, const T* __restrict__ tail,
+                                               int64_t m_tail, int64_t n, int64_t r) {
+  const int64_t slice = n >> 5;
+  const int lane = int(n & 31);
+  Acc<T, COMP> acc;
+  for (int64_t u = ubase[slice], u1 = ubase[slice + 1]; u < u1; ++u) {
+    const cx<T> v = part[(u * nrhs + r) * 32 + lane];
+    acc.add_pair(v.re, v.im);
+  }
+  for (int64_t m = 0; m < m_tail; ++m)
+    acc.add(tail[m * N + n], x[r * ld + m] * (colscale ? colscale[m] : T(1)));
+  y[r * ld + n] = acc.value() * (rowscale ? rowscale[n] : T(1));
 }
 
 // ------------------------------------------------------- adjoint sparse

@@ -904,10 +904,12 @@ int build_plan_device(Plan* p) {
   std::vector<int64_t> fcost(p->nslices, 0);
   std::vector<std::pair<int64_t, int>> tcost;
   int64_t gbase = 0;
+  std::vector<std::vector<int>> fwidths(nb);
   for (int i = 0; i < nb; ++i) {
     std::vector<int> w(p->blocks[i].nslices), tw(p->blocks[i].tslices);
     XC_CUDA(cudaMemcpy(w.data(), p->blocks[i].f_width, w.size() * sizeof(int), cudaMemcpyDeviceToHost));
     XC_CUDA(cudaMemcpy(tw.data(), p->blocks[i].t_width, tw.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    fwidths[i] = w;
     for (size_t s2 = 0; s2 < w.size(); ++s2) fcost[s2] += w[s2];
     for (size_t s2 = 0; s2 < tw.size(); ++s2) tcost.push_back({tw[s2], int(gbase + int64_t(s2))});
     gbase += int64_t(tw.size());
@@ -949,6 +951,35 @@ int build_plan_device(Plan* p) {
     for (int i = 0; i < nb; ++i) {
       p->blocks[i].t_gbase = int(gb);
       gb += p->blocks[i].tslices;
+    }
+  }
+  // forward chunking when some slice's bands (summed over blocks) are long:
+  // units (block, slice, chunk) of up to kFwdChunk rows, slice-major
+  {
+    int64_t longest = 0;
+    for (int64_t c : fcost) longest = std::max(longest, c);
+    p->fwd_chunked = longest > 2 * kFwdChunk;
+    if (p->fwd_chunked) {
+      std::vector<int4> units;
+      std::vector<int> ubase(size_t(p->nslices) + 1, 0);
+      for (int64_t s2 = 0; s2 < p->nslices; ++s2) {
+        ubase[s2] = int(units.size());
+        for (int i = 0; i < nb; ++i) {
+          const int W = fwidths[i][s2];
+          for (int c = 0; c * kFwdChunk < W; ++c)
+            units.push_back(int4{i, int(s2), c, std::min(kFwdChunk, W - c * kFwdChunk)});
+        }
+      }
+      ubase[p->nslices] = int(units.size());
+      std::vector<int> uorder(units.size());
+      for (size_t u = 0; u < units.size(); ++u) uorder[u] = int(u);
+      std::stable_sort(uorder.begin(), uorder.end(), [&](int a, int b2) { return units[a].w > units[b2].w; });
+      p->unit_len.resize(units.size());
+      for (size_t u = 0; u < units.size(); ++u) p->unit_len[u] = units[uorder[u]].w;
+      p->total_units = int64_t(units.size());
+      XC_TRY(upload(p, units, &p->fu_units));
+      XC_TRY(upload(p, uorder, &p->fu_order));
+      XC_TRY(upload(p, ubase, &p->fu_ubase));
     }
   }
   std::vector<int> forder(p->nslices);

@@ -51,7 +51,7 @@ class xc_kernel_time(ctypes.Structure):
 
 class xc_batch_stats(ctypes.Structure):
     _fields_ = [("nplans", ctypes.c_int), ("rhs_per_item", ctypes.c_int), ("tuned", ctypes.c_int),
-                ("tasks_forward", ctypes.c_int64), ("tasks_adjoint", ctypes.c_int64),
+                ("rhs_per_item_adjoint", ctypes.c_int), ("tasks_forward", ctypes.c_int64), ("tasks_adjoint", ctypes.c_int64),
                 ("shared_bytes", ctypes.c_int64), ("matrix_bytes", ctypes.c_int64),
                 ("adjoint_bytes", ctypes.c_int64)]
 

@@ -74,6 +74,34 @@ def test_structure_layouts_match_the_header(xc):
     assert ctypes.sizeof(xc.xc_plan_stats) == 56 + 7 * 8 * 16 + 24
 
 
+def test_ctypes_mirrors_match_a_c_compiler(xc, tmp_path):
+    """Every field offset and struct size of the Python mirrors equals what a
+    C compiler makes of include/xc.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [xc.xc_params, xc.xc_plan_stats, xc.xc_kernel_time, xc.xc_batch_stats]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "xc.h"', "int main(void) {"]
+    expect = []
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        expect.append(ctypes.sizeof(st))
+        for field in st._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {field[0]}));')
+            expect.append(getattr(st, field[0]).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
+
+
 def test_batch_arguments_are_checked_on_the_host(xc):
     h = ctypes.c_void_p()
     assert xc._lib.xc_batch_create(None, None, 1) == xc.XC_ERR_ARG

@@ -104,6 +104,7 @@ def test_batch_autotune_keeps_results(xc):
             assert all(torch.equal(a, c) for a, c in zip(xs, x0))   # inputs restored
             info = b.info()
             assert info["tuned"] == 1 and info["rhs_per_item"] in (1, 2, 4, 8)
+            assert info["rhs_per_item_adjoint"] in (1, 2, 4, 8)
             b.apply(False)
             torch.cuda.synchronize()
             for p, x, y in zip(plans, xs, ys):
