@@ -106,6 +106,8 @@ def algorithmic_work(info, nrhs, precision, chunked=False):
         "adj_sparse": (nrhs * 4.0 * nnz, nnz * 2 * eb + nrhs * (N * eb + H * 2 * eb)),
         "adj_fft": (fft_flops, nrhs * (H * 2 * eb + N * eb)),
         "adj_tail": (nrhs * 2.0 * N * mt, N * mt * eb + nrhs * N * eb),
+        # layout change only (y -> its transpose, RHS padded to 8): no flops
+        "adj_transpose": (0.0, N * eb * (nrhs + (nrhs + 7) // 8 * 8)),
     }
 
 

@@ -45,7 +45,7 @@ int plan_alloc(Plan* p, void** ptr, size_t bytes) {
 static std::atomic<int64_t> g_launches{0};
 
 const char* kernel_name(int id) {
-  static const char* names[K_COUNT] = {"fwd_fft", "fwd_sparse", "adj_sparse", "adj_fft", "adj_tail", "fwd_reduce"};
+  static const char* names[K_COUNT] = {"fwd_fft", "fwd_sparse", "adj_sparse", "adj_fft", "adj_tail", "fwd_reduce", "adj_transpose"};
   return (id >= 0 && id < K_COUNT) ? names[id] : "unknown";
 }
 

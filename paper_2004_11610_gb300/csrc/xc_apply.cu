@@ -118,10 +118,10 @@ __global__ void fwd_reduce_kernel(int64_t N, const T* __restrict__ x, int64_t ld
 // blocks, high frequencies of the Laguerre functions) from becoming one long
 // serial loop; the adjoint FFT adds the chunks of each bin in chunk order
 // (deterministic, no atomics).
-template <typename T, int RPW, bool COMP>
+template <typename T, int RPW, bool COMP, bool YT>
 __global__ void __launch_bounds__(32 * kSparseWarps)
     adj_sparse_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N, const T* __restrict__ y,
-                      int64_t ld, cx<T>* __restrict__ part, int64_t nrhs, const T* __restrict__ rowscale,
+                      int64_t ld, const T* __restrict__ yt, int64_t ldt, cx<T>* __restrict__ part, int64_t nrhs, const T* __restrict__ rowscale,
                       const int2* __restrict__ items, const int* __restrict__ cbase, int64_t total_chunks,
                       unsigned* counters, int sg) {
   (void)N;
@@ -131,10 +131,21 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
   for (;;) {
     const int64_t t = take_item(&counters[2], lane);
     if (t >= total) break;
-    adj_sparse_item<T, RPW, COMP>(blocks, nblocks, y, ld, part, nrhs, rowscale, cbase, items[t / nsup],
-                                  (t % nsup) * int64_t(sg) * RPW, lane, sg);
+    adj_sparse_item<T, RPW, COMP, YT>(blocks, nblocks, y, ld, yt, ldt, part, nrhs, rowscale, cbase,
+                                      items[t / nsup], (t % nsup) * int64_t(sg) * RPW, lane, sg);
   }
   retire_warp(&counters[2], &counters[3], gridDim.x * kSparseWarps, lane);
+}
+
+// y [nrhs][ld] -> yt [N][ldt] (zero columns beyond nrhs).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    transpose_kernel(const T* __restrict__ y, int64_t ld, int64_t N, int64_t nrhs, T* __restrict__ yt, int64_t ldt) {
+  __shared__ T tile[32][33];
+  for (int64_t rb = blockIdx.y; rb * 32 < ldt; rb += gridDim.y) {
+    transpose_tile<T>(y, ld, N, nrhs, yt, ldt, int64_t(blockIdx.x) * 32, rb * 32, tile, threadIdx.x, threadIdx.y);
+    __syncthreads();                       // the tile is refilled next
+  }
 }
 
 // Persistent grid: as many CTAs as can be resident, but no more than the
@@ -272,15 +283,31 @@ int launch_unit_fwd_rpw(Plan* p, const void* x, void* y, int64_t nrhs, int64_t l
 template <typename T, bool COMP, int RPW>
 int launch_sparse_adj_rpw(Plan* p, const void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
   if (p->total_chunks == 0) return XC_OK;
-  const void* fn = reinterpret_cast<const void*>(adj_sparse_kernel<T, RPW, COMP>);
+  // blocks whose bins start far apart read a transposed copy of y (columns
+  // beyond nrhs zero), where a step reads each lane's RPW values of one row
+  // as one vector; with fewer than 4 right-hand sides per item the vector
+  // is too short to pay for the transposition and for the shorter reuse of
+  // each cache line (4 rows per 128-byte line instead of 32)
+  const int64_t ldt = yt_ld(nrhs);
+  T* yt = nullptr;
+  if (p->any_yt && RPW >= 4) {
+    yt = reinterpret_cast<T*>(static_cast<cx<T>*>(p->scratch) + p->total_chunks * 32 * nrhs);
+    launch_begin(p, K_ADJ_TRANSPOSE, st);
+    const int64_t rtiles = (ldt + 31) / 32;
+    transpose_kernel<T><<<dim3(unsigned((p->N + 31) / 32), unsigned(std::min<int64_t>(rtiles, 65535))), dim3(32, 8),
+                          0, st>>>(static_cast<const T*>(y), ld, p->N, nrhs, yt, ldt);
+    launch_end(p, K_ADJ_TRANSPOSE, st);
+    XC_CUDA(cudaGetLastError());
+  }
+  const void* fn = reinterpret_cast<const void*>(adj_sparse_kernel<T, RPW, COMP, true>);
   unsigned grid = 1;
   const int64_t ngroups = (nrhs + RPW - 1) / RPW;
   const int sg = supergroup(fn, p->total_chunks, ngroups);
   XC_TRY(persistent_grid(fn, p->total_chunks * ((ngroups + sg - 1) / sg), &grid));
   launch_begin(p, K_ADJ_SPARSE, st);
-  adj_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
-      static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->N, static_cast<const T*>(y), ld,
-      static_cast<cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale), p->t_items, p->t_cbase,
+  adj_sparse_kernel<T, RPW, COMP, true><<<grid, 32 * kSparseWarps, 0, st>>>(
+      static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->N, static_cast<const T*>(y), ld, yt,
+      ldt, static_cast<cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale), p->t_items, p->t_cbase,
       p->total_chunks, p->counters, sg);
   launch_end(p, K_ADJ_SPARSE, st);
   XC_CUDA(cudaGetLastError());
@@ -454,11 +481,13 @@ int ensure_scratch(Plan* p, int64_t nrhs) {
   }
   if (nrhs <= p->scratch_nrhs) return XC_OK;
   const size_t cbytes = 2 * p->elem_bytes();
-  // forward spectra (+ forward unit partials) and adjoint chunk partials share
-  // the buffer (one direction at a time)
+  // forward: spectra (+ unit partials); adjoint: chunk partials + transposed
+  // y.  The directions share the buffer (one at a time).
   const int64_t fwd = p->spec_per_rhs + (p->fwd_chunked ? p->total_units * 32 : 0);
-  const int64_t per_rhs = std::max<int64_t>({1, fwd, p->total_chunks * 32});
-  const size_t bytes = size_t(per_rhs) * size_t(nrhs) * cbytes;
+  const size_t fwd_bytes = size_t(fwd) * size_t(nrhs) * cbytes;
+  const size_t adj_bytes = size_t(p->total_chunks) * 32 * size_t(nrhs) * cbytes +
+                           (p->any_yt ? size_t(p->N) * size_t(yt_ld(nrhs)) * p->elem_bytes() : 0);
+  const size_t bytes = std::max<size_t>({cbytes, fwd_bytes, adj_bytes});
   void* fresh = nullptr;
   if (cudaMalloc(&fresh, bytes) != cudaSuccess) {
     cudaGetLastError();

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kBatchThreads)
         case T_ADJ_SPARSE: {
           const int64_t item = int64_t(tk.z) + warp;
           if (item < P.total_chunks)
-            adj_sparse_item<T, RPW, COMP>(blocks, P.nblocks, static_cast<const T*>(P.y), P.ld,
+            adj_sparse_item<T, RPW, COMP>(blocks, P.nblocks, static_cast<const T*>(P.y), P.ld, nullptr, 0,
                                           static_cast<cx<T>*>(P.scratch), P.nrhs, rs, P.t_cbase, P.t_items[item],
                                           int64_t(tk.w) * RPW, lane);
           break;

@@ -77,6 +77,7 @@ struct BlockDev {
   const int* t_width;        // [tslices]
   const int64_t* t_off;      // [tslices]
   const void* t_val;
+  int t_yt;                  // 1: the adjoint product reads the transposed right-hand sides
   int64_t spec_off;          // offset (complex elements) of this block's spectrum per unit nrhs
   int t_gbase;               // index of this block's first bin slice in the plan-wide slice list
 };
@@ -119,6 +120,7 @@ struct Plan {
   int* fu_order = nullptr;             // [total_units], longest first
   int* fu_ubase = nullptr;             // [nslices + 1]: first unit of each slice (units of a slice are consecutive)
   int64_t total_units = 0;
+  bool any_yt = false;                 // some block reads the transposed right-hand sides
   std::vector<int> unit_len;           // host: rows of each unit (in fu_order order)
   std::vector<int> item_len;           // host: rows of each adjoint chunk, in t_items order
   std::vector<int2> item_host;         // host copy of t_items
@@ -149,7 +151,10 @@ struct Plan {
 int plan_alloc(Plan* p, void** ptr, size_t bytes);
 
 // Kernel identities for the launch counter and the per-kernel timing.
-enum KernelId { K_FWD_FFT = 0, K_FWD_SPARSE, K_ADJ_SPARSE, K_ADJ_FFT, K_ADJ_TAIL, K_FWD_REDUCE, K_COUNT };
+enum KernelId { K_FWD_FFT = 0, K_FWD_SPARSE, K_ADJ_SPARSE, K_ADJ_FFT, K_ADJ_TAIL, K_FWD_REDUCE, K_ADJ_TRANSPOSE, K_COUNT };
+
+// Row stride of the transposed adjoint input: nrhs rounded up to 8.
+inline int64_t yt_ld(int64_t nrhs) { return (nrhs + 7) / 8 * 8; }
 const char* kernel_name(int id);
 // Bracket one launch: begin() before it, end() after it (counts the launch and,
 // when timing is on, records events on the stream).

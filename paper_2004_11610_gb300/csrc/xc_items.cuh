@@ -15,6 +15,7 @@
 //   fwd_reduce_row    one (row, RHS): adds a chunked slice's partials and the
 //                     dense tail.
 // Adjoint, x = A^T y (Algorithm 2 step 2 / Algorithm 4):
+//   transpose_tile    y [rhs][row] -> yt [row][rhs] for the adjoint products
 //   adj_sparse_item   one (chunk of rows of a 32-bin slice, RPW RHS): partial
 //                     sums of z_k = sum_n CT_kn y_n
 //   adj_fft_body      one (block, RHS): add the chunk partials, real inverse
@@ -238,12 +239,79 @@ __device__ __forceinline__ void fwd_reduce_row(int64_t N, const T* __restrict__ 
 }
 
 // ------------------------------------------------------- adjoint sparse
+// RPW consecutive values from p, which is aligned to RPW * sizeof(T) bytes
+// (vector loads of up to 16 bytes).
+template <typename T, int RPW>
+__device__ __forceinline__ void load_rhs(const T* __restrict__ p, T (&v)[RPW]) {
+  constexpr int bytes = RPW * int(sizeof(T));
+  if constexpr (bytes >= 16) {
+    constexpr int per = 16 / int(sizeof(T));
+#pragma unroll
+    for (int q = 0; q < RPW; q += per) {
+      if constexpr (sizeof(T) == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p + q));
+        v[q] = t.x; v[q + 1] = t.y; v[q + 2] = t.z; v[q + 3] = t.w;
+      } else {
+        const double2 t = __ldg(reinterpret_cast<const double2*>(p + q));
+        v[q] = t.x; v[q + 1] = t.y;
+      }
+    }
+  } else if constexpr (bytes == 8 && sizeof(T) == 4) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = t.x; v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) v[q] = __ldg(p + q);
+  }
+}
+
+// Rows [j0, j1) of one bin-slice chunk for RPW right-hand sides from r0.
+// y is read row-major by right-hand side ([rhs][ld]) or, with YT, from its
+// transpose yt[row][ldt] (ldt a multiple of 8, columns beyond nrhs zero),
+// where one lane's RPW values of a row are adjacent and a step reads one
+// vector per lane.
+template <typename T, int RPW, bool COMP, bool YT>
+__device__ __forceinline__ void adj_chunk_rows(const cx<T>* __restrict__ val, int64_t n0, int j0, int j1,
+                                               const T* __restrict__ y, int64_t ld, int64_t r0, int nq,
+                                               const T* __restrict__ rowscale, Acc<T, COMP> (&re)[RPW],
+                                               Acc<T, COMP> (&im)[RPW]) {
+#pragma unroll 4
+  for (int j = j0; j < j1; ++j) {
+    const cx<T> c = val[j * 32];
+    const int64_t row = n0 + j;
+    const T rs = rowscale ? rowscale[row] : T(1);
+    if constexpr (YT) {
+      T v[RPW];
+      load_rhs<T, RPW>(y + row * ld + r0, v);
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        re[q].add(c.re, v[q] * rs);
+        im[q].add(c.im, v[q] * rs);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        if (q < nq) {
+          const T v = y[(r0 + q) * ld + row] * rs;
+          re[q].add(c.re, v);
+          im[q].add(c.im, v);
+        }
+      }
+    }
+  }
+}
+
 // Item (global bin slice g, chunk c): lane = bin k; the partial sum over rows
 // [c*kAdjChunk, (c+1)*kAdjChunk) of the slice goes to part[chunk][rhs][lane].
-template <typename T, int RPW, bool COMP>
+// Blocks marked t_yt (their bins start at rows far apart, so that a step of
+// scalar loads touches up to 32 sectors per right-hand side) read the
+// transposed copy yt when USE_YT and yt is given; the others read y, where
+// neighbouring bins share cache lines over many steps.
+template <typename T, int RPW, bool COMP, bool USE_YT = false>
 __device__ void adj_sparse_item(const BlockDev* __restrict__ blocks, int nblocks, const T* __restrict__ y,
-                                int64_t ld, cx<T>* __restrict__ part, int64_t nrhs, const T* __restrict__ rowscale,
-                                const int* __restrict__ cbase, int2 it, int64_t r_begin, int lane, int groups = 1) {
+                                int64_t ld, const T* __restrict__ yt, int64_t ldt, cx<T>* __restrict__ part,
+                                int64_t nrhs, const T* __restrict__ rowscale, const int* __restrict__ cbase, int2 it,
+                                int64_t r_begin, int lane, int groups = 1) {
   int i = 0;
   while (i < nblocks - 1 && it.x >= blocks[i].t_gbase + blocks[i].tslices) ++i;
   const BlockDev& b = blocks[i];
@@ -255,29 +323,41 @@ __device__ void adj_sparse_item(const BlockDev* __restrict__ blocks, int nblocks
   const int n0 = b.t_n0[k];
   const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.t_val) + b.t_off[gl] + lane;
   const int64_t cb = cbase[it.x];
+  const bool from_yt = USE_YT && b.t_yt && yt != nullptr;
   for (int grp = 0; grp < groups; ++grp) {
-  const int64_t r0 = r_begin + int64_t(grp) * RPW;
-  if (r0 >= nrhs) break;
-  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
-  Acc<T, COMP> re[RPW], im[RPW];
-#pragma unroll 4
-  for (int j = j0; j < j1; ++j) {
-    const cx<T> c = val[j * 32];
-    const int64_t row = n0 + j;
-    const T rs = rowscale ? rowscale[row] : T(1);
-#pragma unroll
-    for (int q = 0; q < RPW; ++q) {
-      if (q < nq) {
-        const T v = y[(r0 + q) * ld + row] * rs;
-        re[q].add(c.re, v);
-        im[q].add(c.im, v);
-      }
+    const int64_t r0 = r_begin + int64_t(grp) * RPW;
+    if (r0 >= nrhs) break;
+    const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
+    Acc<T, COMP> re[RPW], im[RPW];
+    if constexpr (USE_YT) {
+      if (from_yt)
+        adj_chunk_rows<T, RPW, COMP, true>(val, n0, j0, j1, yt, ldt, r0, nq, rowscale, re, im);
+      else
+        adj_chunk_rows<T, RPW, COMP, false>(val, n0, j0, j1, y, ld, r0, nq, rowscale, re, im);
+    } else {
+      adj_chunk_rows<T, RPW, COMP, false>(val, n0, j0, j1, y, ld, r0, nq, rowscale, re, im);
     }
-  }
-  cx<T>* out = part + ((cb + it.y) * nrhs + r0) * 32 + lane;
+    cx<T>* out = part + ((cb + it.y) * nrhs + r0) * 32 + lane;
 #pragma unroll
-  for (int q = 0; q < RPW; ++q)
-    if (q < nq) out[q * 32] = cx<T>{re[q].value(), im[q].value()};
+    for (int q = 0; q < RPW; ++q)
+      if (q < nq) out[q * 32] = cx<T>{re[q].value(), im[q].value()};
+  }
+}
+
+// yt[n][ldt] = y[r][n] for r < nrhs, 0 for nrhs <= r < ldt: a 32 x 32 tile per
+// CTA of 32 x 8 threads through shared memory (coalesced on both sides).
+template <typename T>
+__device__ __forceinline__ void transpose_tile(const T* __restrict__ y, int64_t ld, int64_t N, int64_t nrhs,
+                                               T* __restrict__ yt, int64_t ldt, int64_t n_base, int64_t r_base,
+                                               T (*tile)[33], int tx, int ty) {
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = r_base + i, n = n_base + tx;
+    tile[i][tx] = (r < nrhs && n < N) ? y[r * ld + n] : T(0);
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t n = n_base + i, r = r_base + tx;
+    if (n < N && r < ldt) yt[n * ldt + r] = tile[tx][i];
   }
 }
 

@@ -795,6 +795,29 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
     toff[s] = ttotal;
     ttotal += int64_t(W) * kSlice;
   }
+  // Transposed right-hand sides for the adjoint product of FP32 plans where
+  // the 32 bins of a slice start at rows far apart: the width-weighted mean
+  // number of distinct 32-byte sectors among their first rows is 8 or more,
+  // so that a step of scalar loads would gather from as many sectors per
+  // right-hand side and the row-major y lines would not survive in L1.  (The
+  // FP64 product is bound by the FP64 pipe, not by these loads.)
+  int use_yt = 0;
+  if (sizeof(T) == 4) {
+    const int rows_per_sector = 32 / int(sizeof(T));
+    double wsum = 0, swsum = 0;
+    for (int s = 0; s < tslices; ++s) {
+      int sec[kSlice], ns = 0;
+      for (int l = 0; l < kSlice && int64_t(s) * kSlice + l < H; ++l) {
+        const int sid = tn0[size_t(s) * kSlice + l] / rows_per_sector;
+        bool seen = false;
+        for (int q = 0; q < ns; ++q) seen = seen || sec[q] == sid;
+        if (!seen) sec[ns++] = sid;
+      }
+      wsum += twidth[s];
+      swsum += double(twidth[s]) * ns;
+    }
+    use_yt = wsum > 0 && swsum / wsum >= 8.0;
+  }
 
   int *fk0_d, *fw_d, *tn0_d, *tw_d;
   int64_t *foff_d, *toff_d;
@@ -832,6 +855,8 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
   b.t_width = tw_d;
   b.t_off = toff_d;
   b.t_val = tval;
+  b.t_yt = use_yt;
+  p->any_yt = p->any_yt || use_yt;
   p->matrix_bytes += total * int64_t(sizeof(cx<T>)) + int64_t(N) * 4;
   p->adjoint_bytes += ttotal * int64_t(sizeof(cx<T>)) + int64_t(H) * 4;
   return XC_OK;

@@ -64,3 +64,20 @@ def test_reference_arm_non_zero_rank_exits_without_work():
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_work_model_covers_every_kernel_the_library_times():
+    """Every kernel name the library reports in its timings has an entry in
+    bench.py's algorithmic work model (otherwise the bench stops at a KeyError)."""
+    import pathlib
+    import re
+    root = pathlib.Path(__file__).resolve().parents[1]
+    src = (root / "paper_2004_11610_gb300" / "csrc" / "xc_abi.cpp").read_text()
+    m = re.search(r"names\[K_COUNT\]\s*=\s*\{([^}]*)\}", src)
+    assert m
+    names = re.findall(r'"([a-z_]+)"', m.group(1))
+    import bench
+    info = {"nnz": [100, 50], "N": 64, "m_tail": 3, "L": [80, 24]}
+    for chunked in (False, True):
+        work = bench.algorithmic_work(info, 4, "fp32", chunked)
+        assert set(names) <= set(work), set(names) - set(work)

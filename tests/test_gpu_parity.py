@@ -129,6 +129,37 @@ def test_fp32_paths_match_oracle(xc, fam, N, eps, precision):
         assert M.rel_l2(xa, xa_ref) <= max(10 * eps, 1e-5)
 
 
+@pytest.mark.parametrize("fam,N,precision,nrhs,kernel", [
+    ("legendre", 4096, "fp32c", 512, "adj_transpose"),   # bins far apart: transposed right-hand sides
+    ("legendre", 4096, "fp32", 512, "adj_transpose"),
+    ("hermite", 1500, "fp32", 48, "fwd_reduce"),         # long bands: chunked forward product
+    ("laguerre", 1200, "fp64", 5, "fwd_reduce"),
+])
+def test_wide_and_long_band_paths_match_oracle(xc, fam, N, precision, nrhs, kernel):
+    """Many right-hand sides (the adjoint reads a transposed copy of y for
+    blocks whose bins start far apart) and long bands (the forward product is
+    summed in chunks and reduced): the kernel that marks the path runs, and the
+    results match the oracle."""
+    eps = 1e-7 if precision != "fp64" else 1e-10
+    ora, plan = gpu_plan(xc, fam, N, eps, precision, 1e-3 if precision == "fp64" else 3e-2)
+    with plan:
+        plan.timing_enable(True)
+        plan.timing_read()
+        X = inputs.uniform_pm1(N, nrhs, 23)
+        y, y_ref = run_both(xc, plan, ora, X)
+        Y = inputs.normal(N, nrhs, 24)
+        xa, xa_ref = run_both(xc, plan, ora, Y, adjoint=True)
+        ran = plan.timing_read()
+        plan.timing_enable(False)
+        assert kernel in ran
+        if precision == "fp64":
+            tol = fp64_tol(ora, eps)
+            assert max_rel(y, y_ref) <= tol and max_rel(xa, xa_ref) <= tol
+        else:
+            assert M.rel_l2(y, y_ref) <= max(10 * eps, 1e-5)
+            assert M.rel_l2(xa, xa_ref) <= max(10 * eps, 1e-5)
+
+
 def test_orthonormal_and_block_scheme_variants(xc):
     ora, plan = gpu_plan(xc, "legendre", 256, 1e-12, "fp64", 1e-3, normalise=True)
     with plan:
