@@ -1,30 +1,33 @@
 // Many plans in one persistent launch per direction.
 //
 // A batch groups plans of one precision (uneven N, families and numbers of
-// right-hand sides).  Binding I/O buffers builds, per direction, one device
-// task list over all plans:
-//   forward   phase 1: FFT of (plan, block, RHS)              [fwd_fft_body]
-//             phase 2: band product of (plan, 8 row slices, RPW RHS) + tail;
-//                      for plans with long bands, of (plan, 8 band chunks,
-//                      RPW RHS) into partial sums               [fwd_unit_item]
-//             phase 3: (long-band plans) partials + tail of (plan, 256 rows,
-//                      32 RHS)                                  [fwd_reduce_row]
-//   adjoint   phase 1: transposed band product of (plan, 8 chunks, RPW RHS),
-//                      and the dense tail of (plan, RHS)
-//             phase 2: inverse FFT of (plan, block, RHS)
-// Every CTA of a persistent grid takes tasks from a device counter in list
-// order; all phase-1 tasks precede all phase-2 tasks (and those all phase-3
-// tasks), and within a phase the costliest tasks come first.  A phase-2 task
-// of plan p waits until every phase-1 task of p has finished: phase-1 tasks
-// increment done[p] when they end; a phase-2 task reads done[p] with acquire
-// semantics and waits, for a bounded number of sleeps, until it reaches
-// need[p].  Phase-3 tasks wait in the same way on done[nplans + p], which the
-// chunked phase-2 tasks increment.  Because every task of a phase has been
-// taken (and so is running) before any task of the next phase starts, the
-// waits end; if one does not end within the limit, the status word records a
-// timeout, the remaining tasks are skipped and the host reads XC_ERR_TIMEOUT.
-// The last CTA to finish resets the counters, so a launch needs no memset and
-// can be captured in a CUDA graph and replayed.
+// right-hand sides).  Binding I/O buffers builds, per direction, three device
+// work lists over all plans:
+//   forward   A: FFT of (plan, block, RHS), one CTA each        [fwd_fft_body]
+//             B: band product of (plan, row slice, RPW RHS) + tail, or for
+//                plans with long bands of (plan, band chunk, RPW RHS) into
+//                partial sums; one warp each         [fwd_sparse_item / fwd_unit_item]
+//             C: (long-band plans) partials + tail of (plan, 32 rows), one
+//                warp each                                      [fwd_reduce_row]
+//   adjoint   B: transposed band product of (plan, chunk, RPW RHS) and the
+//                dense tail of (plan, column, RHS), one warp each
+//             C: inverse FFT of (plan, block, RHS), one CTA each
+// Every CTA of a persistent grid works through A (CTA tasks from a device
+// counter), then its warps take B items one by one from a second counter,
+// then -- after a CTA barrier -- it works through C (CTA tasks or warp items).
+// Warps thus never wait for the slowest warp of their CTA inside B, where the
+// items are of very uneven length.  Within each list the costliest entries
+// come first.  An entry of plan p in B waits until all A tasks of p have
+// finished (done[p] reaches need[p]); an entry in C waits for all B items of
+// p (done[nplans + p] reaches need[nplans + p]).  The finishing task or item
+// increments the counter after a fence; the waiter reads it with acquire
+// semantics, sleeping between reads, for a bounded number of reads.  Because
+// a CTA enters B only when A is exhausted -- every A task has been taken by a
+// running CTA -- and C only when B is exhausted, the waits end; if one does
+// not end within the limit, the status word records a timeout, the remaining
+// work of the launch is skipped and the host reads XC_ERR_TIMEOUT.  The last
+// CTA to finish resets the counters, so a launch needs no memset and can be
+// captured in a CUDA graph and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,7 +52,8 @@ constexpr int kBatchWarps = kBatchThreads / 32;
 enum TaskKind {
   T_FWD_FFT = 0, T_FWD_SPARSE = 1, T_ADJ_SPARSE = 2, T_ADJ_FFT = 3, T_ADJ_TAIL = 4, T_FWD_UNIT = 5, T_FWD_REDUCE = 6
 };
-constexpr int kReduceRhs = 32;   // right-hand sides per phase-3 task
+// control words: next entry of lists A, B, C; finished CTAs; status
+enum { C_NEXT_A = 0, C_NEXT_B = 1, C_NEXT_C = 2, C_FINISHED = 3, C_STATUS = 4, C_WORDS = 8 };
 
 struct BatchPlanDev {
   const BlockDev* blocks;
@@ -92,112 +96,167 @@ __device__ int wait_for(const unsigned* done, unsigned need, long long limit, un
   }
 }
 
+// One CTA task (an FFT of one block and RHS).
+template <typename T>
+__device__ __forceinline__ void run_cta_task(const BatchPlanDev& P, int4 tk, cx<T>* s, int tid) {
+  const T* cs = static_cast<const T*>(P.colscale);
+  if (tk.x == T_FWD_FFT)
+    fwd_fft_body<T>(P.blocks[tk.z], tk.w, static_cast<const T*>(P.x), P.ld, cs, static_cast<cx<T>*>(P.scratch),
+                    P.nrhs, s, tid, kBatchThreads);
+  else  // T_ADJ_FFT
+    adj_fft_body<T>(P.blocks[tk.z], tk.w, static_cast<const cx<T>*>(P.scratch), P.t_cbase, P.nrhs,
+                    static_cast<T*>(const_cast<void*>(P.x)), P.ld, cs, s, tid, kBatchThreads);
+}
+
+// One warp item.
 template <typename T, int RPW, bool COMP>
-__global__ void __launch_bounds__(kBatchThreads)
-    batch_kernel(const BatchPlanDev* __restrict__ plans, const int4* __restrict__ tasks, int64_t ntasks,
-                 unsigned* ctrl, const unsigned* __restrict__ need, unsigned* done, int nplans, long long wait_limit) {
+__device__ __forceinline__ void run_warp_item(const BatchPlanDev& P, int4 tk, int lane) {
+  const T* rs = static_cast<const T*>(P.rowscale);
+  const T* cs = static_cast<const T*>(P.colscale);
+  switch (tk.x) {
+    case T_FWD_SPARSE:
+      fwd_sparse_item<T, RPW, COMP>(P.blocks, P.nblocks, P.N, static_cast<const T*>(P.x), P.ld, static_cast<T*>(P.y),
+                                    static_cast<const cx<T>*>(P.scratch), P.nrhs, rs, cs,
+                                    static_cast<const T*>(P.tail), P.m_tail, tk.z, int64_t(tk.w) * RPW, lane);
+      break;
+    case T_FWD_UNIT: {
+      const int u = P.fu_order[tk.z];
+      fwd_unit_item<T, RPW, COMP>(P.blocks, static_cast<const cx<T>*>(P.scratch), P.nrhs,
+                                  static_cast<cx<T>*>(P.scratch) + P.spec_per_rhs * P.nrhs, P.fu_units[u], u,
+                                  int64_t(tk.w) * RPW, lane);
+      break;
+    }
+    case T_FWD_REDUCE: {
+      const int64_t n = int64_t(tk.z) * 32 + lane;
+      if (n < P.N)
+        for (int64_t r = 0; r < P.nrhs; ++r)
+          fwd_reduce_row<T, COMP>(P.N, static_cast<const T*>(P.x), P.ld, static_cast<T*>(P.y),
+                                  static_cast<const cx<T>*>(P.scratch) + P.spec_per_rhs * P.nrhs, P.nrhs, P.fu_ubase,
+                                  rs, cs, static_cast<const T*>(P.tail), P.m_tail, n, r);
+      break;
+    }
+    case T_ADJ_SPARSE:
+      adj_sparse_item<T, RPW, COMP>(P.blocks, P.nblocks, static_cast<const T*>(P.y), P.ld, nullptr, 0,
+                                    static_cast<cx<T>*>(P.scratch), P.nrhs, rs, P.t_cbase, P.t_items[tk.z],
+                                    int64_t(tk.w) * RPW, lane);
+      break;
+    default:  // T_ADJ_TAIL: column tk.z, RHS tk.w
+      adj_tail_warp<T, COMP>(P.N, tk.z, tk.w, static_cast<const T*>(P.tail), static_cast<const T*>(P.y), P.ld,
+                             static_cast<T*>(const_cast<void*>(P.x)), rs, cs, lane);
+      break;
+  }
+}
+
+// Which completion counter an entry waits for (-1: none) and which one it
+// increments (-1: none): index p (after the A tasks of plan p) or nplans + p
+// (after its B items).
+__device__ __forceinline__ int waits_on(int kind, int plan, int nplans) {
+  if (kind == T_FWD_SPARSE || kind == T_FWD_UNIT) return plan;
+  if (kind == T_FWD_REDUCE || kind == T_ADJ_FFT) return nplans + plan;
+  return -1;
+}
+__device__ __forceinline__ int counts_in(int kind, int plan, int nplans) {
+  if (kind == T_FWD_FFT) return plan;
+  if (kind == T_FWD_SPARSE || kind == T_FWD_UNIT || kind == T_ADJ_SPARSE || kind == T_ADJ_TAIL) return nplans + plan;
+  return -1;
+}
+
+// A list worked through by whole CTAs.
+template <typename T>
+__device__ void cta_list(const BatchPlanDev* __restrict__ plans, const int4* __restrict__ list, int64_t n,
+                         unsigned* next, const unsigned* __restrict__ need, unsigned* done, int nplans,
+                         long long wait_limit, unsigned* status, cx<T>* s, unsigned* s_task, int* s_ok) {
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) *s_task = atomicAdd(next, 1u);
+    __syncthreads();
+    const int64_t t = *s_task;
+    if (t >= n) break;
+    const int4 tk = list[t];
+    if (tid == 0) {
+      const int w = waits_on(tk.x, tk.y, nplans);
+      *s_ok = w >= 0 ? wait_for(&done[w], need[w], wait_limit, status) : (*(volatile unsigned*)status == 0u);
+    }
+    __syncthreads();
+    if (*s_ok) run_cta_task<T>(plans[tk.y], tk, s, tid);
+    const int c = counts_in(tk.x, tk.y, nplans);
+    if (c >= 0) {
+      __syncthreads();                        // every thread's results are written
+      if (tid == 0) {
+        __threadfence();
+        atomicAdd(&done[c], 1u);
+      }
+    }
+    __syncthreads();                          // s_task / s_ok are reused
+  }
+}
+
+// A list worked through by single warps.
+template <typename T, int RPW, bool COMP>
+__device__ void warp_list(const BatchPlanDev* __restrict__ plans, const int4* __restrict__ list, int64_t n,
+                          unsigned* next, const unsigned* __restrict__ need, unsigned* done, int nplans,
+                          long long wait_limit, unsigned* status) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(next, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (int64_t(t) >= n) break;
+    const int4 tk = list[t];
+    int ok = 0;
+    if (lane == 0) {
+      const int w = waits_on(tk.x, tk.y, nplans);
+      ok = w >= 0 ? wait_for(&done[w], need[w], wait_limit, status) : (*(volatile unsigned*)status == 0u);
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) run_warp_item<T, RPW, COMP>(plans[tk.y], tk, lane);
+    const int c = counts_in(tk.x, tk.y, nplans);
+    if (c >= 0) {
+      __syncwarp();                           // every lane's results are written
+      if (lane == 0) {
+        __threadfence();
+        atomicAdd(&done[c], 1u);
+      }
+    }
+  }
+}
+
+// Three CTAs per SM where the accumulators fit in 80 registers (the shared
+// FFT buffer of the largest plans allows about three as well), two otherwise.
+template <typename T, int RPW, bool COMP>
+__global__ void __launch_bounds__(kBatchThreads, RPW * sizeof(T) >= 32 ? 2 : 3)
+    batch_kernel(const BatchPlanDev* __restrict__ plans, const int4* __restrict__ listA, int64_t nA,
+                 const int4* __restrict__ listB, int64_t nB, const int4* __restrict__ listC, int64_t nC,
+                 int c_by_warps, unsigned* ctrl, const unsigned* __restrict__ need, unsigned* done, int nplans,
+                 long long wait_limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   __shared__ unsigned s_task;
   __shared__ int s_ok;
   __shared__ int s_last;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  unsigned* next = &ctrl[0];
-  unsigned* finished = &ctrl[1];
-  unsigned* status = &ctrl[2];
-  for (;;) {
-    if (tid == 0) s_task = atomicAdd(next, 1u);
-    __syncthreads();
-    const int64_t t = s_task;
-    if (t >= ntasks) break;
-    const int4 tk = tasks[t];
-    const BatchPlanDev& P = plans[tk.y];
-    const BlockDev* blocks = P.blocks;
-    if (tid == 0) {
-      if (tk.x == T_FWD_SPARSE || tk.x == T_FWD_UNIT || tk.x == T_ADJ_FFT)
-        s_ok = wait_for(&done[tk.y], need[tk.y], wait_limit, status);
-      else if (tk.x == T_FWD_REDUCE)
-        s_ok = wait_for(&done[nplans + tk.y], need[nplans + tk.y], wait_limit, status);
-      else
-        s_ok = *(volatile unsigned*)status == 0u;
-    }
-    __syncthreads();
-    if (s_ok) {
-      const T* rs = static_cast<const T*>(P.rowscale);
-      const T* cs = static_cast<const T*>(P.colscale);
-      switch (tk.x) {
-        case T_FWD_FFT:
-          fwd_fft_body<T>(blocks[tk.z], tk.w, static_cast<const T*>(P.x), P.ld, cs,
-                          static_cast<cx<T>*>(P.scratch), P.nrhs, s, tid, kBatchThreads);
-          break;
-        case T_FWD_SPARSE: {
-          const int64_t slice = int64_t(tk.z) + warp;
-          if (slice < P.nslices)
-            fwd_sparse_item<T, RPW, COMP>(blocks, P.nblocks, P.N, static_cast<const T*>(P.x), P.ld,
-                                          static_cast<T*>(P.y), static_cast<const cx<T>*>(P.scratch), P.nrhs, rs, cs,
-                                          static_cast<const T*>(P.tail), P.m_tail, slice, int64_t(tk.w) * RPW, lane);
-          break;
-        }
-        case T_FWD_UNIT: {
-          const int64_t k = int64_t(tk.z) + warp;
-          if (k < P.total_units) {
-            const int u = P.fu_order[k];
-            fwd_unit_item<T, RPW, COMP>(blocks, static_cast<const cx<T>*>(P.scratch), P.nrhs,
-                                        static_cast<cx<T>*>(P.scratch) + P.spec_per_rhs * P.nrhs, P.fu_units[u], u,
-                                        int64_t(tk.w) * RPW, lane);
-          }
-          break;
-        }
-        case T_FWD_REDUCE: {
-          const int64_t n = int64_t(tk.z) * kBatchThreads + tid;
-          if (n < P.N) {
-            const int64_t r1 = min(P.nrhs, int64_t(tk.w) + kReduceRhs);
-            for (int64_t r = tk.w; r < r1; ++r)
-              fwd_reduce_row<T, COMP>(P.N, static_cast<const T*>(P.x), P.ld, static_cast<T*>(P.y),
-                                      static_cast<const cx<T>*>(P.scratch) + P.spec_per_rhs * P.nrhs, P.nrhs,
-                                      P.fu_ubase, rs, cs, static_cast<const T*>(P.tail), P.m_tail, n, r);
-          }
-          break;
-        }
-        case T_ADJ_SPARSE: {
-          const int64_t item = int64_t(tk.z) + warp;
-          if (item < P.total_chunks)
-            adj_sparse_item<T, RPW, COMP>(blocks, P.nblocks, static_cast<const T*>(P.y), P.ld, nullptr, 0,
-                                          static_cast<cx<T>*>(P.scratch), P.nrhs, rs, P.t_cbase, P.t_items[item],
-                                          int64_t(tk.w) * RPW, lane);
-          break;
-        }
-        case T_ADJ_FFT:
-          adj_fft_body<T>(blocks[tk.z], tk.w, static_cast<const cx<T>*>(P.scratch), P.t_cbase, P.nrhs,
-                          static_cast<T*>(const_cast<void*>(P.x)), P.ld, cs, s, tid, kBatchThreads);
-          break;
-        default:  // T_ADJ_TAIL
-          for (int64_t m = warp; m < P.m_tail; m += kBatchWarps)
-            adj_tail_warp<T, COMP>(P.N, m, tk.w, static_cast<const T*>(P.tail), static_cast<const T*>(P.y), P.ld,
-                                   static_cast<T*>(const_cast<void*>(P.x)), rs, cs, lane);
-          break;
-      }
-    }
-    if (tk.x == T_FWD_FFT || tk.x == T_ADJ_SPARSE || tk.x == T_FWD_UNIT) {
-      __syncthreads();                        // every thread's results are written
-      if (tid == 0) {
-        __threadfence();
-        atomicAdd(&done[tk.x == T_FWD_UNIT ? nplans + tk.y : tk.y], 1u);
-      }
-    }
-    __syncthreads();                          // s_task / s_ok are reused
-  }
+  const int tid = threadIdx.x;
+  unsigned* status = &ctrl[C_STATUS];
+  cta_list<T>(plans, listA, nA, &ctrl[C_NEXT_A], need, done, nplans, wait_limit, status, s, &s_task, &s_ok);
+  warp_list<T, RPW, COMP>(plans, listB, nB, &ctrl[C_NEXT_B], need, done, nplans, wait_limit, status);
+  __syncthreads();
+  if (c_by_warps)
+    warp_list<T, RPW, COMP>(plans, listC, nC, &ctrl[C_NEXT_C], need, done, nplans, wait_limit, status);
+  else
+    cta_list<T>(plans, listC, nC, &ctrl[C_NEXT_C], need, done, nplans, wait_limit, status, s, &s_task, &s_ok);
+  __syncthreads();
   if (tid == 0) {
     __threadfence();
-    s_last = atomicAdd(finished, 1u) == gridDim.x - 1;
+    s_last = atomicAdd(&ctrl[C_FINISHED], 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (s_last) {
     for (int p = tid; p < 2 * nplans; p += kBatchThreads) done[p] = 0u;
     __syncthreads();
     if (tid == 0) {
-      *next = 0u;
-      *finished = 0u;
+      ctrl[C_NEXT_A] = 0u;
+      ctrl[C_NEXT_B] = 0u;
+      ctrl[C_NEXT_C] = 0u;
+      ctrl[C_FINISHED] = 0u;
     }
   }
 }
@@ -208,11 +267,13 @@ struct Batch {
   std::vector<Plan*> plans;
   int precision = XC_FP64;
   BatchPlanDev* dplans = nullptr;
-  int4* tasks[2] = {nullptr, nullptr};
-  int64_t ntasks[2] = {0, 0};
-  unsigned* need[2] = {nullptr, nullptr};
-  unsigned* ctrl = nullptr;      // [0] next task, [1] finished CTAs, [2] status
-  unsigned* done = nullptr;      // [2 * nplans]: phase-1, phase-2 completions per plan
+  // per direction (0 forward, 1 adjoint): work lists A, B, C
+  int4* list[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  int64_t nlist[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  int64_t cap[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  unsigned* need[2] = {nullptr, nullptr};   // [2 * nplans]: A tasks, B items per plan
+  unsigned* ctrl = nullptr;      // C_WORDS control words
+  unsigned* done = nullptr;      // [2 * nplans]: finished A tasks, B items per plan
   std::vector<int> extra_need;   // fault injection (tests)
   long long wait_limit = 1LL << 22;   // sleeps of ~256 ns: about a second
   int rpw[2] = {0, 0};           // right-hand sides per band item, per direction (0 = not bound)
@@ -235,106 +296,85 @@ struct Batch {
     allocs.push_back(*ptr);
     return XC_OK;
   }
+  int64_t entries(int dir) const { return nlist[dir][0] + nlist[dir][1] + nlist[dir][2]; }
 };
 
 namespace {
 
-// Task lists of both directions for the bound right-hand sides, with rpw_f
+using Entry = std::pair<double, int4>;   // (cost estimate, entry)
+
+// Work lists of both directions for the bound right-hand sides, with rpw_f
 // (forward) and rpw_a (adjoint) right-hand sides per band item.
 int build_tasks(Batch* b, int rpw_f, int rpw_a) {
   const int np = int(b->plans.size());
-  std::vector<std::pair<double, int4>> ph1, ph2, ph3;
-  std::vector<unsigned> need_f(2 * size_t(np), 0), need_a(2 * size_t(np), 0);
-  // forward
+  std::vector<Entry> L[2][3];
+  std::vector<unsigned> need[2] = {std::vector<unsigned>(2 * size_t(np), 0), std::vector<unsigned>(2 * size_t(np), 0)};
   for (int p = 0; p < np; ++p) {
     const Plan* P = b->plans[p];
     const int64_t R = b->nrhs[p];
     if (R == 0) continue;
+    // forward
     for (size_t i = 0; i < P->blocks.size(); ++i) {
       const double c = double(P->blocks[i].n) * std::log2(double(P->blocks[i].n) + 1.0);
       for (int64_t r = 0; r < R; ++r) {
-        ph1.push_back({c, int4{T_FWD_FFT, p, int(i), int(r)}});
-        ++need_f[p];
+        L[0][0].push_back({c, int4{T_FWD_FFT, p, int(i), int(r)}});
+        ++need[0][p];
       }
     }
-    const int rpw = rpw_f;
-    const int64_t groups = (R + rpw - 1) / rpw;
+    const int64_t gf = (R + rpw_f - 1) / rpw_f;
     if (P->fwd_chunked) {
-      for (int64_t k0 = 0; k0 < P->total_units; k0 += kBatchWarps) {
-        const double c = double(P->unit_len[k0]);   // longest first
-        for (int64_t g = 0; g < groups; ++g) {
-          ph2.push_back({c * rpw, int4{T_FWD_UNIT, p, int(k0), int(g)}});
-          ++need_f[np + p];
+      for (int64_t k = 0; k < P->total_units; ++k)
+        for (int64_t g = 0; g < gf; ++g) {
+          L[0][1].push_back({double(P->unit_len[k]) * rpw_f, int4{T_FWD_UNIT, p, int(k), int(g)}});
+          ++need[0][np + p];
         }
+      for (int64_t s0 = 0; s0 < P->nslices; ++s0)
+        L[0][2].push_back({double(R) * double(P->m_tail + 4), int4{T_FWD_REDUCE, p, int(s0), 0}});
+    } else {
+      for (int64_t s0 = 0; s0 < P->nslices; ++s0)
+        for (int64_t g = 0; g < gf; ++g) {
+          L[0][1].push_back({double(P->slice_cost[s0] + P->m_tail) * rpw_f, int4{T_FWD_SPARSE, p, int(s0), int(g)}});
+          ++need[0][np + p];
+        }
+    }
+    // adjoint
+    const int64_t ga = (R + rpw_a - 1) / rpw_a;
+    for (int64_t i = 0; i < P->total_chunks; ++i)
+      for (int64_t g = 0; g < ga; ++g) {
+        L[1][1].push_back({double(P->item_len[i]) * rpw_a, int4{T_ADJ_SPARSE, p, int(i), int(g)}});
+        ++need[1][np + p];
       }
-      for (int64_t n0 = 0; n0 < P->N; n0 += kBatchThreads)
-        for (int64_t r0 = 0; r0 < R; r0 += kReduceRhs)
-          ph3.push_back({0.0, int4{T_FWD_REDUCE, p, int(n0 / kBatchThreads), int(r0)}});
-      continue;
-    }
-    for (int64_t s0 = 0; s0 < P->nslices; s0 += kBatchWarps) {
-      double c = 0;
-      for (int64_t s = s0; s < std::min<int64_t>(P->nslices, s0 + kBatchWarps); ++s)
-        c = std::max(c, double(P->slice_cost[s] + P->m_tail));
-      for (int64_t g = 0; g < groups; ++g) ph2.push_back({c * rpw, int4{T_FWD_SPARSE, p, int(s0), int(g)}});
-    }
-  }
-  auto order = [](std::vector<std::pair<double, int4>>& v) {
-    std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b2) { return a.first > b2.first; });
-  };
-  order(ph1);
-  order(ph2);
-  std::vector<int4> fwd;
-  for (auto& e : ph1) fwd.push_back(e.second);
-  for (auto& e : ph2) fwd.push_back(e.second);
-  for (auto& e : ph3) fwd.push_back(e.second);
-  // adjoint
-  ph1.clear();
-  ph2.clear();
-  for (int p = 0; p < np; ++p) {
-    const Plan* P = b->plans[p];
-    const int64_t R = b->nrhs[p];
-    if (R == 0) continue;
-    const int rpw = rpw_a;
-    const int64_t groups = (R + rpw - 1) / rpw;
-    for (int64_t i0 = 0; i0 < P->total_chunks; i0 += kBatchWarps) {
-      double c = 0;
-      for (int64_t i = i0; i < std::min<int64_t>(P->total_chunks, i0 + kBatchWarps); ++i)
-        c = std::max(c, double(P->item_len[i]));
-      for (int64_t g = 0; g < groups; ++g) {
-        ph1.push_back({c * rpw, int4{T_ADJ_SPARSE, p, int(i0), int(g)}});
-        ++need_a[p];
+    for (int64_t m = 0; m < P->m_tail; ++m)
+      for (int64_t r = 0; r < R; ++r) {
+        L[1][1].push_back({double(P->N) / 32.0, int4{T_ADJ_TAIL, p, int(m), int(r)}});
+        ++need[1][np + p];
       }
-    }
-    if (P->m_tail > 0)
-      for (int64_t r = 0; r < R; ++r) ph1.push_back({double(P->N * P->m_tail) / 32.0, int4{T_ADJ_TAIL, p, 0, int(r)}});
     for (size_t i = 0; i < P->blocks.size(); ++i) {
       const double c = double(P->blocks[i].n) * std::log2(double(P->blocks[i].n) + 1.0);
-      for (int64_t r = 0; r < R; ++r) ph2.push_back({c, int4{T_ADJ_FFT, p, int(i), int(r)}});
+      for (int64_t r = 0; r < R; ++r) L[1][2].push_back({c, int4{T_ADJ_FFT, p, int(i), int(r)}});
     }
   }
-  order(ph1);
-  order(ph2);
-  std::vector<int4> adj;
-  for (auto& e : ph1) adj.push_back(e.second);
-  for (auto& e : ph2) adj.push_back(e.second);
-
   for (int p = 0; p < np; ++p) {
-    need_f[p] += unsigned(b->extra_need[p]);
-    need_a[p] += unsigned(b->extra_need[p]);
+    need[0][p] += unsigned(b->extra_need[p]);       // forward B items wait for A
+    need[1][np + p] += unsigned(b->extra_need[p]);  // adjoint C tasks wait for B
   }
-  const std::vector<int4>* lists2[2] = {&fwd, &adj};
-  const std::vector<unsigned>* needs[2] = {&need_f, &need_a};
   for (int d = 0; d < 2; ++d) {
-    if (int64_t(lists2[d]->size()) > b->ntasks[d] || b->tasks[d] == nullptr) {
-      void* ptr = nullptr;
-      XC_TRY(b->alloc(&ptr, std::max<size_t>(1, lists2[d]->size()) * sizeof(int4)));
-      b->tasks[d] = static_cast<int4*>(ptr);
+    for (int l = 0; l < 3; ++l) {
+      auto& v = L[d][l];
+      std::stable_sort(v.begin(), v.end(), [](const Entry& a, const Entry& c) { return a.first > c.first; });
+      std::vector<int4> flat(v.size());
+      for (size_t k = 0; k < v.size(); ++k) flat[k] = v[k].second;
+      if (int64_t(flat.size()) > b->cap[d][l] || b->list[d][l] == nullptr) {
+        void* ptr = nullptr;
+        XC_TRY(b->alloc(&ptr, std::max<size_t>(1, flat.size()) * sizeof(int4)));
+        b->list[d][l] = static_cast<int4*>(ptr);
+        b->cap[d][l] = int64_t(std::max<size_t>(1, flat.size()));
+      }
+      b->nlist[d][l] = int64_t(flat.size());
+      if (!flat.empty())
+        XC_CUDA(cudaMemcpy(b->list[d][l], flat.data(), flat.size() * sizeof(int4), cudaMemcpyHostToDevice));
     }
-    b->ntasks[d] = int64_t(lists2[d]->size());
-    if (!lists2[d]->empty())
-      XC_CUDA(cudaMemcpy(b->tasks[d], lists2[d]->data(), lists2[d]->size() * sizeof(int4), cudaMemcpyHostToDevice));
-    XC_CUDA(cudaMemcpy(b->need[d], needs[d]->data(), 2 * size_t(np) * sizeof(unsigned), cudaMemcpyHostToDevice));
+    XC_CUDA(cudaMemcpy(b->need[d], need[d].data(), 2 * size_t(np) * sizeof(unsigned), cudaMemcpyHostToDevice));
   }
   b->rpw[0] = rpw_f;
   b->rpw[1] = rpw_a;
@@ -353,10 +393,15 @@ int launch_batch_rpw(Batch* b, int dir, cudaStream_t st) {
   XC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(fn), kBatchThreads,
                                                         b->smem));
   if (per_sm < 1) return fail(XC_ERR_UNSUPPORTED, "batch kernel does not fit on an SM");
-  const int64_t grid = std::min<int64_t>(int64_t(sms) * per_sm, std::max<int64_t>(1, b->ntasks[dir]));
+  // every CTA is resident (the waits rely on it); no more CTAs than the work needs
+  const int64_t work = std::max<int64_t>({b->nlist[dir][0], (b->nlist[dir][1] + kBatchWarps - 1) / kBatchWarps,
+                                          b->nlist[dir][2], int64_t(1)});
+  const int64_t grid = std::min<int64_t>(int64_t(sms) * per_sm, work);
   count_launch();
-  fn<<<unsigned(grid), kBatchThreads, b->smem, st>>>(b->dplans, b->tasks[dir], b->ntasks[dir], b->ctrl, b->need[dir],
-                                                      b->done, int(b->plans.size()), b->wait_limit);
+  fn<<<unsigned(grid), kBatchThreads, b->smem, st>>>(b->dplans, b->list[dir][0], b->nlist[dir][0], b->list[dir][1],
+                                                      b->nlist[dir][1], b->list[dir][2], b->nlist[dir][2],
+                                                      dir == 0 ? 1 : 0, b->ctrl, b->need[dir], b->done,
+                                                      int(b->plans.size()), b->wait_limit);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
 }
@@ -372,7 +417,7 @@ int launch_batch_t(Batch* b, int dir, cudaStream_t st) {
 }
 
 int launch_batch(Batch* b, int dir, cudaStream_t st) {
-  if (b->ntasks[dir] == 0) return XC_OK;
+  if (b->entries(dir) == 0) return XC_OK;
   switch (b->precision) {
     case XC_FP64: return launch_batch_t<double, false>(b, dir, st);
     case XC_FP32: return launch_batch_t<float, false>(b, dir, st);
@@ -426,7 +471,7 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans) {
   b->smem = size_t(b->max_n) * 2 * (b->precision == XC_FP64 ? 8 : 4);
   b->extra_need.assign(nplans, 0);
   void* ptr = nullptr;
-  int rc = b->alloc(&ptr, 4 * sizeof(unsigned));
+  int rc = b->alloc(&ptr, xc::C_WORDS * sizeof(unsigned));
   if (rc == XC_OK) {
     b->ctrl = static_cast<unsigned*>(ptr);
     rc = b->alloc(&ptr, 2 * size_t(nplans) * sizeof(unsigned));
@@ -445,7 +490,7 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans) {
   }
   if (rc == XC_OK) {
     b->dplans = static_cast<xc::BatchPlanDev*>(ptr);
-    if (cudaMemset(b->ctrl, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
+    if (cudaMemset(b->ctrl, 0, xc::C_WORDS * sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(b->done, 0, 2 * size_t(nplans) * sizeof(unsigned)) != cudaSuccess)
       rc = xc::cuda_check(cudaGetLastError(), "cudaMemset");
   }
@@ -601,8 +646,8 @@ int xc_batch_info(xc_batch_t batch, xc_batch_stats* out) {
   out->rhs_per_item = b->rpw[0];
   out->rhs_per_item_adjoint = b->rpw[1];
   out->tuned = b->tuned ? 1 : 0;
-  out->tasks_forward = b->ntasks[0];
-  out->tasks_adjoint = b->ntasks[1];
+  out->tasks_forward = b->entries(0);
+  out->tasks_adjoint = b->entries(1);
   out->shared_bytes = int64_t(b->smem);
   for (const xc::Plan* p : b->plans) {
     out->matrix_bytes += p->matrix_bytes;
@@ -616,10 +661,10 @@ int xc_batch_status(xc_batch_t batch, void* stream) {
   if (!b) return fail(XC_ERR_ARG, "batch is NULL");
   auto st = static_cast<cudaStream_t>(stream);
   unsigned status = 0;
-  XC_CUDA(cudaMemcpyAsync(&status, &b->ctrl[2], sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  XC_CUDA(cudaMemcpyAsync(&status, &b->ctrl[xc::C_STATUS], sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   XC_CUDA(cudaStreamSynchronize(st));
   if (status != 0) {
-    XC_CUDA(cudaMemsetAsync(&b->ctrl[2], 0, sizeof(unsigned), st));
+    XC_CUDA(cudaMemsetAsync(&b->ctrl[xc::C_STATUS], 0, sizeof(unsigned), st));
     XC_CUDA(cudaStreamSynchronize(st));
     return fail(XC_ERR_TIMEOUT, "a phase wait of the batch kernel gave up; results of that launch are incomplete");
   }
