@@ -74,6 +74,12 @@ typedef enum {
 #define XC_SCHEME_TWO_SIDED 1   /* Algorithms 1-2; Chebyshev family only */
 #define XC_SCHEME_BLOCKS    2   /* Algorithms 3-4 */
 
+/* precomputation of the compressed rows */
+#define XC_PRECOMPUTE_AUTO 0   /* Appendix A closed form for XC_CHEBYSHEV_T at its Gauss nodes with
+                                  eps > 0 (blocks of a few hundred columns and more), FFT of the
+                                  generated rows otherwise */
+#define XC_PRECOMPUTE_FFT  1   /* always the FFT of the generated rows (Algorithm 1 step 1.3 as written) */
+
 typedef struct {
   double alpha, beta;        /* Jacobi parameters (> -1); ignored by the other families */
   int nodes;                 /* XC_NODES_GAUSS | XC_NODES_USER */
@@ -84,6 +90,7 @@ typedef struct {
   int precision;             /* XC_FP64 | XC_FP32 | XC_FP32_COMPENSATED */
   int scheme;                /* XC_SCHEME_* */
   int tail_max;              /* blocks are added while m_i > tail_max; 0 => 20 */
+  int precompute;            /* XC_PRECOMPUTE_* */
 } xc_params;
 
 /* Fill *p with the defaults listed above (Gauss nodes, raw, FP64, auto scheme). */
@@ -193,6 +200,8 @@ typedef struct {
   int64_t m_tail;                    /* dense tail columns [0, m_tail) */
   int64_t matrix_bytes;              /* device bytes of the compressed matrices + tail (forward) */
   int64_t adjoint_bytes;             /* device bytes of the transposed copies */
+  int closed_form_blocks;            /* blocks whose rows the Appendix A closed form built
+                                        (the others: FFT of the generated rows) */
 } xc_plan_stats;
 
 /* Copy the plan's parameters and per-block statistics into *out. */

@@ -76,6 +76,80 @@ def compress_rows(spec, blk: special.Block, zeta: float, rows) -> np.ndarray:
     return np.fft.fft(A_e * w[None, :], axis=1) / np.sqrt(blk.L)
 
 
+def _sinpi_ratio(num, den: int):
+    """sin(pi * num / den) for integer arrays num, with num reduced exactly
+    modulo 2 den and reflected into [-den/2, den/2] (sin(pi - x) = sin x)
+    first, so that the only rounding is in the final quotient and sine and the
+    result keeps its relative accuracy next to every zero."""
+    r = np.mod(np.asarray(num, dtype=object), 2 * den).astype(np.int64)
+    r = np.where(r >= den, r - 2 * den, r)                 # [-den, den)
+    r = np.where(2 * r > den, den - r, r)
+    r = np.where(2 * r < -den, -den - r, r)
+    return np.sin(np.pi * r.astype(np.float64) / den)
+
+
+def _cospi_ratio(num, den: int):
+    r = np.mod(np.asarray(num, dtype=object), 2 * den).astype(np.int64)
+    return np.cos(np.pi * r.astype(np.float64) / den)
+
+
+def chebyshev_row_dft(n: int, N: int, L: int, off: int, q) -> np.ndarray:
+    """Appendix A, eqs. (y1)/(y3): the DFT sum_{j<L} cos((j - off) theta_n)
+    exp(-2 pi i j q / L) of an extended Chebyshev row in closed form, theta_n =
+    (2n+1) pi / (2N).  Writing cos as two exponentials, each part is a
+    geometric series sum_j exp(i j phi) = exp(i (L-1) phi / 2) sin(L phi / 2) /
+    sin(phi / 2) with phi = +-theta - 2 pi q / L.  Every angle is a rational
+    multiple of pi; numerators are reduced exactly before the sines are taken,
+    and the series is L where phi is a multiple of 2 pi."""
+    q = np.asarray(q, dtype=np.int64)
+    P = 4 * N * L                                   # phi / 2 = pi a / P
+    t = (2 * n + 1) * L                             # L theta / 2 = pi t / (4N)
+    sin_lt = float(_sinpi_ratio(np.array([t]), 4 * N)[0])
+    sign_q = np.where(q % 2 == 0, 1.0, -1.0)
+
+    def dirichlet_ratio(a):
+        """sin(L phi/2) / sin(phi/2) for phi/2 = pi a / P, sin(L phi/2) = (-1)^q sin(L theta/2)."""
+        den = _sinpi_ratio(a, P)
+        res = np.mod(a.astype(object), P) == 0
+        p = (a.astype(object) // P)
+        lim = np.array([L * (1.0 if (int(pp) * (L - 1)) % 2 == 0 else -1.0) for pp in p])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            val = sign_q * sin_lt / den
+        return np.where(res.astype(bool), lim, val)
+
+    s_plus = dirichlet_ratio(t - 4 * N * q)         # phi = theta - 2 pi q / L
+    s_minus = dirichlet_ratio(t + 4 * N * q)        # -phi for phi = -theta - 2 pi q / L (the ratio is even)
+    c2 = (2 * n + 1) * (L - 1 - 2 * off)            # theta (L - 1 - 2 off) / 2 = pi c2 / (4N)
+    e_c = complex(float(_cospi_ratio(np.array([c2]), 4 * N)[0]), float(_sinpi_ratio(np.array([c2]), 4 * N)[0]))
+    ph = -(q * (L - 1))                             # -pi q (L - 1) / L
+    e_q = _cospi_ratio(ph, L) + 1j * _sinpi_ratio(ph, L)
+    return e_q * 0.5 * (e_c * s_plus + np.conj(e_c) * s_minus)
+
+
+def compress_rows_appendix_a(spec, blk: special.Block, zeta: float, rows, M: int) -> np.ndarray:
+    """Rows of the compressed Chebyshev block by Appendix A: the DFT of the
+    windowed row is the circular convolution (eq. (conv_appendix)) of the
+    window's DFT with the row's closed-form DFT; only the window components
+    |m| <= M enter (the Kaiser spectrum is concentrated there).  Same
+    normalisation as compress_rows: fft(A_e w) / sqrt(L)."""
+    assert spec.family == "chebyshev"
+    N, L, off = spec.N, blk.L, blk.off
+    w = special.kaiser_window(L, zeta)
+    j = np.arange(L, dtype=np.int64)
+    ms = np.arange(-M, M + 1)
+    xw = np.array([np.sum(w * np.exp(-2j * np.pi * ((j * m) % L) / L)) for m in ms])
+    k = np.arange(L)
+    q = np.arange(-M, L + M)
+    out = np.empty((len(rows), L), dtype=complex)
+    for r, n in enumerate(rows):
+        a_hat = chebyshev_row_dft(int(n), N, L, off, q)
+        u = np.zeros(L, dtype=complex)
+        for i, m in enumerate(ms):
+            u += xw[i] * a_hat[k - m + M]
+        out[r] = u / L / np.sqrt(L)
+    return out
+
+
 def build(spec, eps: float, eps2: float | None = None, precision: str = "fp64",
           normalise: bool = False, eps_window: float = 0.0, tail_max: int = 20,
           two_sided: bool | None = None, rows=None, chunk: int = 256) -> OraclePlan:

@@ -146,6 +146,8 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
     return fail(XC_ERR_ARG, "the two-sided extension needs the Chebyshev family");
   if (prm.eps2 < 0.0 || prm.eps2 >= 1.0 || prm.eps_window < 0.0 || prm.eps_window >= 1.0 || prm.tail_max < 0)
     return fail(XC_ERR_ARG, "eps2 / eps_window / tail_max out of range");
+  if (prm.precompute != XC_PRECOMPUTE_AUTO && prm.precompute != XC_PRECOMPUTE_FFT)
+    return fail(XC_ERR_ARG, "unknown precompute mode");
 
   xc::Plan* p = new (std::nothrow) xc::Plan();
   if (!p) return fail(XC_ERR_ALLOC, "host allocation failed");
@@ -272,6 +274,7 @@ int xc_plan_info(xc_plan_t plan, xc_plan_stats* out) {
   out->m_tail = p->m_tail;
   out->matrix_bytes = p->matrix_bytes;
   out->adjoint_bytes = p->adjoint_bytes;
+  out->closed_form_blocks = p->closed_form_blocks;
   return XC_OK;
 }
 

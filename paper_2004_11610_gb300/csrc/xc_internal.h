@@ -101,6 +101,7 @@ struct Plan {
   std::vector<int64_t> nnz, stored;
   std::vector<double> maxabs;
   int64_t m_tail = 0;
+  int closed_form_blocks = 0;          // blocks whose rows came from the Appendix A closed form
   void* tail = nullptr;                // [m_tail][N] plan precision
   void* rowscale = nullptr;            // [N] or null (raw)
   void* colscale = nullptr;            // [N] or null (raw)

@@ -422,6 +422,145 @@ __global__ void __launch_bounds__(256) row_fft_cluster_kernel(const double* G, i
   cluster.sync();   // no CTA leaves while another may still read its shared memory
 }
 
+// ------------------------------------------- Appendix A (Chebyshev rows)
+// sin(pi a / d) and cos(pi a / d) for integers a and d > 0: a is reduced
+// exactly modulo 2d and reflected into [-d/2, d/2] (sin(pi - x) = sin x,
+// cos(pi - x) = -cos x) first, so the only rounding is in the final quotient
+// and sincospi, and the sine keeps its relative accuracy next to every zero.
+__device__ __forceinline__ void sincospi_ratio(int64_t a, int64_t d, double* s, double* c) {
+  int64_t r = a % (2 * d);
+  if (r < 0) r += 2 * d;
+  if (r >= d) r -= 2 * d;
+  double sign_c = 1.0;
+  if (2 * r > d) {
+    r = d - r;
+    sign_c = -1.0;
+  } else if (2 * r < -d) {
+    r = -d - r;
+    sign_c = -1.0;
+  }
+  sincospi(double(r) / double(d), s, c);
+  *c *= sign_c;
+}
+
+// xw[m + M] = sum_{j<L} w_j exp(-2 pi i j m / L) for |m| <= M: the few DFT
+// components of the Kaiser window that carry it (one CTA per m).
+__global__ void __launch_bounds__(256) window_dft_kernel(const double* w, int64_t L, int M, cx<double>* xw) {
+  __shared__ double red[2][8];
+  const int64_t m = int64_t(blockIdx.x) - M;
+  double re = 0.0, im = 0.0;
+  for (int64_t j = threadIdx.x; j < L; j += blockDim.x) {
+    double sn, cs;
+    sincospi_ratio(2 * ((j * m) % L), L, &sn, &cs);
+    re += w[j] * cs;
+    im -= w[j] * sn;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = re;
+    red[1][threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) {
+      a += red[0][i];
+      b += red[1][i];
+    }
+    xw[blockIdx.x] = cx<double>{a, b};
+  }
+}
+
+constexpr int kCfMaxM = 32;   // window components |m| <= M
+constexpr int kCfMaxB = 64;   // bins |k - k_c| <= B computed per row
+
+// The candidate bins of row `row` of a Chebyshev block: within B of the
+// row's peak k_c = round(theta L / (2 pi)), clipped to [0, n].
+__host__ __device__ __forceinline__ void cf_window(int64_t row, int64_t N, int64_t L, int n, int B, int64_t* klo,
+                                                   int64_t* khi) {
+  const int64_t t = (2 * row + 1) * L;   // theta L / (2 pi) = t / (4N)
+  const int64_t kc = (t + 2 * N) / (4 * N);
+  *klo = kc - B < 0 ? 0 : kc - B;
+  *khi = kc + B > n ? int64_t(n) : kc + B;
+}
+
+// Appendix A: S[row][k] = U_k / L for the extended Chebyshev row
+// a_j = cos((j - off) theta), theta = (2 row + 1) pi / (2N), j < L, where
+// U = DFT(a . w).  By the convolution theorem (eq. (conv_appendix)),
+// U_k = L^{-1} sum_m xw_m Ahat_{k-m} with Ahat the row's own DFT, which has a
+// closed form (eqs. (y1), (y3)): writing cos as two exponentials,
+//   Ahat_q = e^{-i pi q (L-1)/L} [e^{i theta c} D_+ + e^{-i theta c} D_-] / 2,
+//   c = (L - 1 - 2 off) / 2,  D_+- = (-1)^q sin(L theta/2) / sin(theta/2 -+ pi q/L),
+// and D_+- = L (-1)^{p (L-1)} where the sine below vanishes (theta/2 -+ pi q/L = pi p).
+// Only |m| <= M enter (the window's spectrum is concentrated there) and only
+// the candidate bins are computed; S is zero elsewhere.  One CTA per row.
+__global__ void __launch_bounds__(128) cheb_rows_closed_kernel(int64_t N, int64_t L, int64_t off, int n, int M,
+                                                               int B, const cx<double>* xw, cx<double>* S,
+                                                               unsigned long long* maxsq_bits) {
+  __shared__ cx<double> ah[2 * kCfMaxB + 2 * kCfMaxM + 1];
+  __shared__ cx<double> xs[2 * kCfMaxM + 1];
+  __shared__ double red[4];
+  const int64_t row = blockIdx.x;
+  int64_t klo, khi;
+  cf_window(row, N, L, n, B, &klo, &khi);
+  const int64_t q0 = klo - M;
+  const int Q = int(khi - klo) + 2 * M + 1;
+  for (int i = threadIdx.x; i <= 2 * M; i += blockDim.x) xs[i] = xw[i];
+  const int64_t t = (2 * row + 1) * L;
+  double sin_lt, cos_lt;
+  sincospi_ratio(t, 4 * N, &sin_lt, &cos_lt);            // L theta / 2 = pi t / (4N)
+  double sc, cc;
+  sincospi_ratio((2 * row + 1) * (L - 1 - 2 * off), 4 * N, &sc, &cc);   // theta c
+  const int64_t P = 4 * N * L;                           // theta/2 -+ pi q/L = pi (t -+ 4Nq) / P
+  for (int i = threadIdx.x; i < Q; i += blockDim.x) {
+    const int64_t q = q0 + i;
+    const double sg = (q & 1) ? -1.0 : 1.0;
+    double d[2];
+    for (int h = 0; h < 2; ++h) {
+      const int64_t a = h == 0 ? t - 4 * N * q : t + 4 * N * q;
+      if (a % P == 0) {
+        const int64_t p = a / P;
+        d[h] = ((p & 1) && ((L - 1) & 1)) ? -double(L) : double(L);
+      } else {
+        double sn, cs;
+        sincospi_ratio(a, P, &sn, &cs);
+        d[h] = sg * sin_lt / sn;
+      }
+    }
+    double sq, cq;
+    sincospi_ratio(-(q * (L - 1)), L, &sq, &cq);
+    // e^{i theta c} D_+ + e^{-i theta c} D_-
+    const cx<double> v{0.5 * cc * (d[0] + d[1]), 0.5 * sc * (d[0] - d[1])};
+    ah[i] = cx<double>{cq * v.re - sq * v.im, cq * v.im + sq * v.re};
+  }
+  __syncthreads();
+  const double scale = 1.0 / (double(L) * double(L));
+  double local = 0.0;
+  for (int64_t k = klo + threadIdx.x; k <= khi; k += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int i = 0; i <= 2 * M; ++i) {
+      const cx<double> a = xs[i], b = ah[k - (i - M) - q0];
+      re += a.re * b.re - a.im * b.im;
+      im += a.re * b.im + a.im * b.re;
+    }
+    re *= scale;
+    im *= scale;
+    S[row * int64_t(n + 1) + k] = cx<double>{re, im};
+    local = fmax(local, re * re + im * im);
+  }
+  for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
+    atomicMax(maxsq_bits, static_cast<unsigned long long>(__double_as_longlong(m)));
+  }
+}
+
 __device__ __forceinline__ bool kept(cx<double> v, double thr) { return v.re * v.re + v.im * v.im > thr; }
 
 // One warp per row: first/last kept bin and the number of kept bins.
@@ -692,44 +831,79 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
   XC_TRY(alloc_tmp(&Sbuf, s_bytes));
   XC_TRY(alloc_tmp(&maxbuf, sizeof(unsigned long long)));
   XC_CUDA(cudaMemset(maxbuf.ptr, 0, sizeof(unsigned long long)));
-  int64_t C = std::max<int64_t>(1, std::min<int64_t>(N, (int64_t(1) << 30) / (int64_t(b.L) * 8)));
-  DevBuf Gbuf;
-  XC_TRY(alloc_tmp(&Gbuf, size_t(C) * size_t(b.L) * sizeof(double)));
-  const size_t csmem = size_t(n / csize) * sizeof(cx<double>);
-  if (csize == 1) XC_TRY(set_smem(reinterpret_cast<const void*>(row_fft_kernel), smem));
-  else XC_TRY(set_smem(reinterpret_cast<const void*>(row_fft_cluster_kernel), csmem));
-  for (int64_t row0 = 0; row0 < N; row0 += C) {
-    const int64_t rows = std::min<int64_t>(C, N - row0);
-    gen_rows_kernel<<<unsigned((rows + 127) / 128), 128>>>(g, row0, C, b.L, b.off, static_cast<double*>(w64.ptr),
-                                                           static_cast<double*>(Gbuf.ptr));
-    if (csize == 1) {
-      row_fft_kernel<<<unsigned(rows), 256, smem>>>(static_cast<double*>(Gbuf.ptr), C, row0, N, b,
-                                                     static_cast<cx<double>*>(tw64.ptr),
-                                                     static_cast<cx<double>*>(Sbuf.ptr),
-                                                     static_cast<unsigned long long*>(maxbuf.ptr));
-    } else {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(unsigned(rows * csize));
-      cfg.blockDim = dim3(256);
-      cfg.dynamicSmemBytes = csmem;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = unsigned(csize);
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      XC_CUDA(cudaLaunchKernelEx(&cfg, row_fft_cluster_kernel, static_cast<const double*>(Gbuf.ptr), C, row0, N, b,
-                                 static_cast<const cx<double>*>(tw64.ptr), static_cast<cx<double>*>(Sbuf.ptr),
-                                 static_cast<unsigned long long*>(maxbuf.ptr), csize));
+  // Rows by the FFT of the generated, windowed rows (Algorithm 1 step 1.3).
+  auto fft_rows = [&]() -> int {
+    int64_t C = std::max<int64_t>(1, std::min<int64_t>(N, (int64_t(1) << 30) / (int64_t(b.L) * 8)));
+    DevBuf Gbuf;
+    XC_TRY(alloc_tmp(&Gbuf, size_t(C) * size_t(b.L) * sizeof(double)));
+    const size_t csmem = size_t(n / csize) * sizeof(cx<double>);
+    if (csize == 1) XC_TRY(set_smem(reinterpret_cast<const void*>(row_fft_kernel), smem));
+    else XC_TRY(set_smem(reinterpret_cast<const void*>(row_fft_cluster_kernel), csmem));
+    for (int64_t row0 = 0; row0 < N; row0 += C) {
+      const int64_t rows = std::min<int64_t>(C, N - row0);
+      gen_rows_kernel<<<unsigned((rows + 127) / 128), 128>>>(g, row0, C, b.L, b.off, static_cast<double*>(w64.ptr),
+                                                             static_cast<double*>(Gbuf.ptr));
+      if (csize == 1) {
+        row_fft_kernel<<<unsigned(rows), 256, smem>>>(static_cast<double*>(Gbuf.ptr), C, row0, N, b,
+                                                       static_cast<cx<double>*>(tw64.ptr),
+                                                       static_cast<cx<double>*>(Sbuf.ptr),
+                                                       static_cast<unsigned long long*>(maxbuf.ptr));
+      } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(rows * csize));
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = csmem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = unsigned(csize);
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        XC_CUDA(cudaLaunchKernelEx(&cfg, row_fft_cluster_kernel, static_cast<const double*>(Gbuf.ptr), C, row0, N,
+                                   b, static_cast<const cx<double>*>(tw64.ptr), static_cast<cx<double>*>(Sbuf.ptr),
+                                   static_cast<unsigned long long*>(maxbuf.ptr), csize));
+      }
+      XC_CUDA(cudaGetLastError());
     }
+    XC_CUDA(cudaDeviceSynchronize());
+    return XC_OK;
+  };
+  // Chebyshev rows at Chebyshev-Gauss angles by the Appendix A closed form:
+  // the window's DFT components |m| <= cf_M (main lobe plus a margin; the
+  // truncation error is under a tenth of eps1 * max|A_e W F|), the bins within
+  // cf_B of each row's peak.  eps == 0 keeps every element, and short blocks
+  // (where |m| <= cf_M would reach around the circle) are cheap to transform:
+  // FFT rows then.
+  const int cf_M = std::min(kCfMaxM, int(std::ceil(p->zeta / 3.141592653589793)) + 10);
+  const int cf_B = std::min(kCfMaxB, cf_M + 24);
+  const bool closed_ok = g.family == XC_CHEBYSHEV_T && g.cheb_exact && p->eps > 0 &&
+                         p->params.precompute == XC_PRECOMPUTE_AUTO && b.L >= 8 * (2 * cf_M + 1);
+  auto closed_rows = [&]() -> int {
+    DevBuf xw;
+    XC_TRY(alloc_tmp(&xw, size_t(2 * cf_M + 1) * sizeof(cx<double>)));
+    window_dft_kernel<<<unsigned(2 * cf_M + 1), 256>>>(static_cast<double*>(w64.ptr), b.L, cf_M,
+                                                       static_cast<cx<double>*>(xw.ptr));
+    XC_CUDA(cudaMemset(Sbuf.ptr, 0, s_bytes));
+    cheb_rows_closed_kernel<<<unsigned(N), 128>>>(N, b.L, b.off, n, cf_M, cf_B, static_cast<cx<double>*>(xw.ptr),
+                                                  static_cast<cx<double>*>(Sbuf.ptr),
+                                                  static_cast<unsigned long long*>(maxbuf.ptr));
     XC_CUDA(cudaGetLastError());
-  }
+    XC_CUDA(cudaDeviceSynchronize());
+    return XC_OK;
+  };
+  bool closed = closed_ok;
+  if (closed) XC_TRY(closed_rows());
+  else XC_TRY(fft_rows());
   unsigned long long bits = 0;
-  XC_CUDA(cudaMemcpy(&bits, maxbuf.ptr, sizeof(bits), cudaMemcpyDeviceToHost));
-  double maxsq;
-  std::memcpy(&maxsq, &bits, sizeof(maxsq));
-  const double thr = p->eps > 0 ? (p->eps * p->eps) * maxsq : -1.0;
+  double maxsq = 0.0, thr = -1.0;
+  auto read_threshold = [&]() -> int {
+    XC_CUDA(cudaMemcpy(&bits, maxbuf.ptr, sizeof(bits), cudaMemcpyDeviceToHost));
+    std::memcpy(&maxsq, &bits, sizeof(maxsq));
+    thr = p->eps > 0 ? (p->eps * p->eps) * maxsq : -1.0;
+    return XC_OK;
+  };
+  XC_TRY(read_threshold());
   p->maxabs[bi] = std::sqrt(maxsq);
 
   // extents of the kept elements per row
@@ -737,14 +911,38 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
   XC_TRY(alloc_tmp(&kf, size_t(N) * sizeof(int)));
   XC_TRY(alloc_tmp(&kl, size_t(N) * sizeof(int)));
   XC_TRY(alloc_tmp(&cnt, size_t(N) * sizeof(int)));
-  extents_kernel<<<unsigned((N * 32 + 255) / 256), 256>>>(static_cast<cx<double>*>(Sbuf.ptr), N, H, thr,
-                                                          static_cast<int*>(kf.ptr), static_cast<int*>(kl.ptr),
-                                                          static_cast<int*>(cnt.ptr));
-  XC_CUDA(cudaGetLastError());
   std::vector<int> kfirst(N), klast(N), count(N);
-  XC_CUDA(cudaMemcpy(kfirst.data(), kf.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
-  XC_CUDA(cudaMemcpy(klast.data(), kl.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
-  XC_CUDA(cudaMemcpy(count.data(), cnt.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
+  auto extents = [&]() -> int {
+    extents_kernel<<<unsigned((N * 32 + 255) / 256), 256>>>(static_cast<cx<double>*>(Sbuf.ptr), N, H, thr,
+                                                            static_cast<int*>(kf.ptr), static_cast<int*>(kl.ptr),
+                                                            static_cast<int*>(cnt.ptr));
+    XC_CUDA(cudaGetLastError());
+    XC_CUDA(cudaMemcpy(kfirst.data(), kf.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
+    XC_CUDA(cudaMemcpy(klast.data(), kl.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
+    XC_CUDA(cudaMemcpy(count.data(), cnt.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
+    return XC_OK;
+  };
+  XC_TRY(extents());
+  if (closed) {
+    // a kept element on the edge of a row's candidate bins means its band may
+    // reach beyond them: build the block from the FFT rows instead
+    bool edge = false;
+    for (int64_t r = 0; r < N && !edge; ++r) {
+      if (klast[r] < 0) continue;
+      int64_t klo, khi;
+      cf_window(r, N, b.L, n, cf_B, &klo, &khi);
+      edge = (klo > 0 && kfirst[r] <= klo) || (khi < n && klast[r] >= khi);
+    }
+    if (edge) {
+      closed = false;
+      XC_CUDA(cudaMemset(maxbuf.ptr, 0, sizeof(unsigned long long)));
+      XC_TRY(fft_rows());
+      XC_TRY(read_threshold());
+      p->maxabs[bi] = std::sqrt(maxsq);
+      XC_TRY(extents());
+    }
+  }
+  if (closed) ++p->closed_form_blocks;
   int64_t nnz = 0;
   for (int64_t r = 0; r < N; ++r) nnz += count[r];
   p->nnz[bi] = nnz;

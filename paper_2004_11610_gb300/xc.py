@@ -30,7 +30,7 @@ class xc_params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("nodes", ctypes.c_int),
                 ("user_nodes", ctypes.POINTER(ctypes.c_double)), ("normalise", ctypes.c_int),
                 ("eps2", ctypes.c_double), ("eps_window", ctypes.c_double), ("precision", ctypes.c_int),
-                ("scheme", ctypes.c_int), ("tail_max", ctypes.c_int)]
+                ("scheme", ctypes.c_int), ("tail_max", ctypes.c_int), ("precompute", ctypes.c_int)]
 
 
 _I64x = ctypes.c_int64 * XC_MAX_BLOCKS
@@ -42,7 +42,7 @@ class xc_plan_stats(ctypes.Structure):
                 ("eps2", ctypes.c_double), ("zeta", ctypes.c_double), ("nblocks", ctypes.c_int),
                 ("L", _I64x), ("off", _I64x), ("j_lo", _I64x), ("j_hi", _I64x), ("nnz", _I64x),
                 ("stored", _I64x), ("maxabs", ctypes.c_double * XC_MAX_BLOCKS), ("m_tail", ctypes.c_int64),
-                ("matrix_bytes", ctypes.c_int64), ("adjoint_bytes", ctypes.c_int64)]
+                ("matrix_bytes", ctypes.c_int64), ("adjoint_bytes", ctypes.c_int64), ("closed_form_blocks", ctypes.c_int)]
 
 
 class xc_kernel_time(ctypes.Structure):
@@ -128,7 +128,7 @@ class Plan:
 
     def __init__(self, family: str, N: int, eps: float, precision: str = "fp64", alpha: float = 0.0,
                  beta: float = 0.0, nodes=None, normalise: bool = False, eps2: float = 0.0,
-                 eps_window: float = 0.0, scheme: str = "auto", tail_max: int = 0):
+                 eps_window: float = 0.0, scheme: str = "auto", tail_max: int = 0, precompute: str = "auto"):
         p = xc_params()
         _lib.xc_params_default(ctypes.byref(p))
         p.alpha, p.beta = float(alpha), float(beta)
@@ -145,6 +145,7 @@ class Plan:
         p.precision = PRECISION[precision]
         p.scheme = SCHEME[scheme]
         p.tail_max = int(tail_max)
+        p.precompute = {"auto": 0, "fft": 1}[precompute]
         h = _P()
         _check(_lib.xc_plan_create(ctypes.byref(h), FAMILY[family], ctypes.byref(p), int(N), float(eps)),
                "xc_plan_create")
@@ -190,7 +191,7 @@ class Plan:
             "L": list(st.L[:nb]), "off": list(st.off[:nb]), "j_lo": list(st.j_lo[:nb]),
             "j_hi": list(st.j_hi[:nb]), "nnz": list(st.nnz[:nb]), "stored": list(st.stored[:nb]),
             "maxabs": list(st.maxabs[:nb]), "m_tail": st.m_tail, "matrix_bytes": st.matrix_bytes,
-            "adjoint_bytes": st.adjoint_bytes,
+            "adjoint_bytes": st.adjoint_bytes, "closed_form_blocks": st.closed_form_blocks,
         }
 
     def nodes(self) -> np.ndarray:

@@ -194,6 +194,37 @@ def test_compressed_chebyshev_rows_match_appendix_a_convolution():
         assert np.abs(conv - comp[r]).max() < 1e-11 * np.abs(comp[r]).max()
 
 
+def test_chebyshev_row_dft_closed_form_against_sums():
+    """The closed-form DFT of an extended Chebyshev row (two geometric series
+    with exactly reduced angles) equals the direct sum, including a row and a
+    length where one of the series is resonant (theta/2 = pi q / L)."""
+    for N, L, off, n in ((64, 80, 8, 5), (64, 81, 8, 63), (100, 160, 30, 0), (8, 16, 0, 1), (4, 8, 2, 0),
+                         (6, 12, 3, 1)):
+        q = np.arange(-5, L + 5)
+        j = np.arange(L)
+        th = (2 * n + 1) * math.pi / (2 * N)
+        direct = np.array([np.sum(np.cos((j - off) * th) * np.exp(-2j * np.pi * j * qq / L)) for qq in q])
+        cf = M.chebyshev_row_dft(n, N, L, off, q)
+        assert np.abs(cf - direct).max() <= 1e-13 * np.abs(direct).max(), (N, L, off, n)
+
+
+@pytest.mark.parametrize("N,eps,two_sided", [(512, 1e-14, True), (300, 1e-10, True), (1000, 1e-8, True),
+                                             (4096, 1e-12, True), (700, 1e-10, False)])
+def test_appendix_a_truncated_rows_match_fft_rows(N, eps, two_sided):
+    """Appendix A with only the window components |m| <= ceil(zeta/pi) + 10:
+    the rows agree with the FFT of the windowed rows to under a tenth of
+    eps1 * max|Ä| (the Kaiser spectrum outside its main lobe sits at about
+    eps1), i.e. below the threshold that decides which elements are kept."""
+    sp = _spec("chebyshev", N)
+    sch = S.schedule(N, eps, 1e-3, two_sided)
+    blk = sch.blocks[0]
+    rows = [0, 1, N // 3, N // 2, N - 2, N - 1]
+    comp = M.compress_rows(sp, blk, sch.zeta, rows)
+    Mw = int(math.ceil(sch.zeta / math.pi)) + 10
+    cf = M.compress_rows_appendix_a(sp, blk, sch.zeta, rows, Mw)
+    assert np.abs(cf - comp).max() <= max(0.1 * eps, 4e-15) * np.abs(comp).max()
+
+
 # ------------------------------------------------------------- planted mistakes
 
 def test_planted_mistakes_are_caught(monkeypatch):
