@@ -115,7 +115,7 @@ def test_legendre_jacobi16384_fp32c_full(xc):
 
 
 def test_legendre32768_fp32_full_uses_cluster_precompute(xc):
-    """The first block (L_1 = 44800) is too long for one CTA's FP64 FFT: the
+    """The first block (L_1 = 44100) is too long for one CTA's FP64 FFT: the
     precompute runs it on a thread-block cluster (distributed shared memory)."""
     for res in run_workload(xc, "legendre32768_fp32", nrhs_cap=16):
         check(res)
