@@ -39,6 +39,8 @@ from paper_2004_11610_gb300 import inputs  # noqa: E402
 
 METRIC = "vectors/s and HBM GB/s (fraction of peak) vs GPU direct dense GEMM at stated rel-l2 error"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flops x max SM clock
+# band products of XC_FP64_PAIR plans: 12 FP32 instructions per pair multiply-add (2 algorithmic flops)
+PAIR_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 6 / 1e12
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -52,6 +54,7 @@ def parse_args():
     ap.add_argument("--nplans", type=int, default=1000, help="plans of the batch workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--no-variant", action="store_true", help="skip the XC_FP64_PAIR line of FP64 workloads")
     return ap.parse_args()
 
 
@@ -90,7 +93,7 @@ def algorithmic_work(info, nrhs, precision, chunked=False):
     A chunked forward product (plans with long bands) leaves the dense tail
     and the output to the reduction kernel; its partial sums are scratch, not
     algorithmic traffic."""
-    eb = 8 if precision == "fp64" else 4
+    eb = 8 if precision in ("fp64", "fp64pair") else 4
     nnz = sum(info["nnz"])
     N, mt = info["N"], info["m_tail"]
     fft_flops = sum(2.5 * L * math.log2(L) for L in info["L"]) * nrhs
@@ -108,12 +111,14 @@ def algorithmic_work(info, nrhs, precision, chunked=False):
         "adj_tail": (nrhs * 2.0 * N * mt, N * mt * eb + nrhs * N * eb),
         # layout change only (y -> its transpose, RHS padded to 8): no flops
         "adj_transpose": (0.0, N * eb * (nrhs + (nrhs + 7) // 8 * 8)),
+        # per-RHS scaling of FP64 pair plans: read the vector (adjoint: write its pairs)
+        "pair_scale": (0.0, 2.0 * N * eb * nrhs),
     }
 
 
 def step_bytes(info, nrhs, precision):
     """Algorithmic HBM bytes of one forward + adjoint apply of one plan."""
-    eb = 8 if precision == "fp64" else 4
+    eb = 8 if precision in ("fp64", "fp64pair") else 4
     H = sum(L // 2 + 1 for L in info["L"])
     vec = 4 * nrhs * info["N"] * eb                    # x in, y out, y in, x out
     spec = 2 * 2 * nrhs * H * 2 * eb                   # spectra written + read, both directions
@@ -197,7 +202,8 @@ def time_oracle(wl, sample_rhs, min_seconds, max_reps=1000):
     plans = []
     for i, (fam, N, params) in enumerate(wl["plans"]):
         sp = F.make_spec(fam, N, params.get("alpha", 0.0), params.get("beta", 0.0))
-        plans.append((M.build(sp, wl["eps"], precision=wl["precision"]),
+        prec = "fp64" if wl["precision"] == "fp64pair" else wl["precision"]   # same schedule (eps2) as the library
+        plans.append((M.build(sp, wl["eps"], precision=prec),
                       inputs.draw(wl["dist"], N, sample_rhs, 90, i)))
     reps, t0 = 0, time.perf_counter()
     while True:
@@ -227,7 +233,8 @@ def run_reference(args, rank, world):
     plans = []
     for i, (fam, N, params) in enumerate(wl["plans"]):
         sp = F.make_spec(fam, N, params.get("alpha", 0.0), params.get("beta", 0.0))
-        plans.append((M.build(sp, wl["eps"], precision=wl["precision"]), inputs.draw(wl["dist"], N, 1, 91, i)))
+        prec = "fp64" if wl["precision"] == "fp64pair" else wl["precision"]   # same schedule (eps2) as the library
+        plans.append((M.build(sp, wl["eps"], precision=prec), inputs.draw(wl["dist"], N, 1, 91, i)))
 
     def step():
         for P, X in plans:
@@ -282,6 +289,59 @@ def traffic_from_profiles(kernel, workload, plan=None):
     return None
 
 
+def measure_pair_variant(xc, torch, wl, specs, dev, steps, warmup, world, mats=None):
+    """The same FP64 workload with XC_FP64_PAIR plans (FP64 vectors and FFTs,
+    band products in FP32 pairs): vector applies per second over `steps`
+    flushed steps, and the relative l2 error against the dense product."""
+    R = wl["nrhs"]
+    plans, X, Y, XA = [], [], [], []
+    for s in specs:
+        p = xc.Plan(s["family"], s["N"], wl["eps"], precision="fp64pair",
+                    alpha=s["params"].get("alpha", 0.0), beta=s["params"].get("beta", 0.0))
+        p.reserve(R)
+        plans.append(p)
+        x = torch.from_numpy(inputs.draw(wl["dist"], s["N"], R, 1, s["index"], 0)).to(dev, torch.float64)
+        X.append(x)
+        Y.append(torch.empty_like(x))
+        XA.append(torch.empty_like(x))
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def step():
+        for p, x, y, xa in zip(plans, X, Y, XA):
+            p.apply(x, out=y, stream=stream)
+            p.apply_adjoint(y, out=xa, stream=stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    total = reduce_max(total, world, dev)
+    out = {"precision": "fp64pair (FP64 vectors, FFTs and tail; band values, spectra and band products in FP32 "
+                        "pairs with TwoProduct/TwoSum accumulation)",
+           "value": job_throughput(2 * R * len(plans), steps, total, world), "unit": "vectors/s",
+           "ms_per_step": total / steps}
+    if mats is not None:
+        errs = []
+        for p, A, x in zip(plans, mats, X):
+            y_d = x @ A.T
+            errs.append(float(torch.linalg.norm(p.apply(x) - y_d) / torch.linalg.norm(y_d)))
+            xa_d = y_d @ A
+            errs.append(float(torch.linalg.norm(p.apply_adjoint(y_d) - xa_d) / torch.linalg.norm(xa_d)))
+        out["method_rel_l2_vs_dense"] = max(errs)
+    for p in plans:
+        p.close()
+    return out
+
+
 def run_xc(args, rank, world, local_rank):
     import torch
     from paper_2004_11610_gb300 import build
@@ -292,7 +352,7 @@ def run_xc(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     wl = inputs.WORKLOADS[args.workload]
     prec = wl["precision"]
-    tdt = torch.float64 if prec == "fp64" else torch.float32
+    tdt = torch.float64 if prec in ("fp64", "fp64pair") else torch.float32
     R = wl["nrhs"]
     specs = plan_specs(wl)
     plans, X, Y, XA = [], [], [], []
@@ -369,13 +429,18 @@ def run_xc(args, rank, world, local_rank):
     avg_ms = e["ms"] / e["launches"]
     flops_per_launch = e["flops"] / e["launches"]
     achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
-    fp64 = prec == "fp64"
+    fp64 = prec in ("fp64", "fp64pair")   # FP64 vectors (the dense comparison runs DGEMM)
+    if prec == "fp64" or name not in ("fwd_sparse", "adj_sparse") and prec == "fp64pair":
+        peak, src = FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz"
+    elif prec == "fp64pair":
+        peak = PAIR_PEAK_TFLOPS
+        src = ("derived: 152 SMs x 128 FP32 instr/clk x 2070 MHz / 6 FP32 instructions per algorithmic "
+               "flop (one pair multiply-add = 2 flops = 12 instructions)")
+    else:
+        peak, src = 152 * 128 * 2 * 2.070e9 / 1e12, "derived: 152 SMs x 128 FP32 FMA/clk x 2 flops x 2070 MHz"
     roofline = {
         "kernel": name, "plan": f"{specs[dom_plan]['family']} N={specs[dom_plan]['N']}",
-        "bound": "alu", "achieved": achieved, "unit": "TFLOP/s",
-        "peak": FP64_PEAK_TFLOPS if fp64 else 152 * 128 * 2 * 2.070e9 / 1e12,
-        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz" if fp64
-        else "derived: 152 SMs x 128 FP32 FMA/clk x 2 flops x 2070 MHz",
+        "bound": "alu", "achieved": achieved, "unit": "TFLOP/s", "peak": peak, "peak_source": src,
     }
     roofline["frac"] = achieved / roofline["peak"]
     tb = traffic_from_profiles(name, args.workload, dom_plan)
@@ -417,11 +482,12 @@ def run_xc(args, rank, world, local_rank):
     barrier()
     e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
     e2e_val = job_throughput(vectors_per_step, e2e_steps, 1e3 * e2e_s, world)
-    eb = 8 if prec == "fp64" else 4
+    eb = 8 if prec in ("fp64", "fp64pair") else 4
     io_bytes = sum(2 * R * s["N"] * eb for s in specs)
 
     # dense GEMM comparison (cuBLAS through torch) at equal precision
     dense = None
+    variant = None
     if not args.no_dense:
         mats = [p.dense_matrix() for p in plans]
         torch.cuda.synchronize(dev)
@@ -452,6 +518,8 @@ def run_xc(args, rank, world, local_rank):
             b.record(stream)
             b.synchronize()
             dms += a.elapsed_time(b)
+        if prec == "fp64" and not args.no_variant:
+            variant = measure_pair_variant(xc, torch, wl, specs, dev, max(3, min(args.steps, 50)), 3, world, mats)
         dense = {"vectors_per_s": vectors_per_step * ds / (dms / 1e3), "ms_per_step": dms / ds,
                  "library": "cuBLAS via torch.matmul", "dtype": "f64" if fp64 else "f32",
                  "method_rel_l2_vs_dense": max(errs),
@@ -470,13 +538,16 @@ def run_xc(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if fp64 else ("f32" if prec == "fp32" else "f32-compensated"),
+            "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp64pair": "f64 (band products in f32 pairs)", "fp32": "f32"}.get(
+                prec, "f32-compensated"),
             "data": "synthetic", "config": workload_config(args.workload, wl) | {"parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
                     "peak_source": hbm_src, "note": "algorithmic bytes of the whole step / step time"},
             "kernels": kernel_table,
             "dense_gemm": dense,
+            "fp64_pair_variant": variant,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "vectors/s", "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},

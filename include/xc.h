@@ -68,6 +68,10 @@ typedef enum {
 #define XC_FP32             1   /* FP32 FFT, FP32 sparse product */
 #define XC_FP32_COMPENSATED 2   /* FP32 FFT; sparse product and dense tail accumulated
                                    with error-free transformations (TwoProduct/TwoSum) */
+#define XC_FP64_PAIR        3   /* FP64 vectors, FFTs and dense tail; band values and spectra as
+                                   pairs of FP32 (hi + lo, 48-bit significands), band products on the
+                                   FP32 pipes accumulated with TwoProduct/TwoSum.  I/O type double.
+                                   Single-plan applies only (not xc_batch_*, not xc_apply_noalloc). */
 
 /* extension scheme */
 #define XC_SCHEME_AUTO      0   /* two-sided for XC_CHEBYSHEV_T, block method otherwise */
@@ -87,7 +91,7 @@ typedef struct {
   int normalise;             /* XC_RAW | XC_ORTHONORMAL (orthonormal needs Gauss nodes) */
   double eps2;               /* window floor of the first real component; 0 => 1e-3 (FP64) or 1e-1 (FP32) */
   double eps_window;         /* eps that fixes zeta when eps == 0; 0 => 1e-14 */
-  int precision;             /* XC_FP64 | XC_FP32 | XC_FP32_COMPENSATED */
+  int precision;             /* XC_FP64 | XC_FP32 | XC_FP32_COMPENSATED | XC_FP64_PAIR */
   int scheme;                /* XC_SCHEME_* */
   int tail_max;              /* blocks are added while m_i > tail_max; 0 => 20 */
   int precompute;            /* XC_PRECOMPUTE_* */

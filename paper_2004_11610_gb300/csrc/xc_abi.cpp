@@ -45,7 +45,7 @@ int plan_alloc(Plan* p, void** ptr, size_t bytes) {
 static std::atomic<int64_t> g_launches{0};
 
 const char* kernel_name(int id) {
-  static const char* names[K_COUNT] = {"fwd_fft", "fwd_sparse", "adj_sparse", "adj_fft", "adj_tail", "fwd_reduce", "adj_transpose"};
+  static const char* names[K_COUNT] = {"fwd_fft", "fwd_sparse", "adj_sparse", "adj_fft", "adj_tail", "fwd_reduce", "adj_transpose", "pair_scale"};
   return (id >= 0 && id < K_COUNT) ? names[id] : "unknown";
 }
 
@@ -134,7 +134,7 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
   if (family < XC_CHEBYSHEV_T || family > XC_HERMITE_FN) return fail(XC_ERR_ARG, "unknown family");
   if (N < 2 || N > (int64_t(1) << 20)) return fail(XC_ERR_ARG, "N must lie in [2, 2^20]");
   if (!(eps >= 0.0) || !(eps < 1.0)) return fail(XC_ERR_ARG, "eps must lie in [0, 1)");
-  if (prm.precision < XC_FP64 || prm.precision > XC_FP32_COMPENSATED) return fail(XC_ERR_ARG, "unknown precision");
+  if (prm.precision < XC_FP64 || prm.precision > XC_FP64_PAIR) return fail(XC_ERR_ARG, "unknown precision");
   if (prm.nodes != XC_NODES_GAUSS && prm.nodes != XC_NODES_USER) return fail(XC_ERR_ARG, "unknown node set");
   if (prm.nodes == XC_NODES_USER && !prm.user_nodes) return fail(XC_ERR_ARG, "user_nodes is NULL");
   if (prm.normalise != XC_RAW && prm.normalise != XC_ORTHONORMAL) return fail(XC_ERR_ARG, "unknown normalisation");
@@ -161,7 +161,7 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
   p->scheme = prm.scheme == XC_SCHEME_AUTO ? (family == XC_CHEBYSHEV_T ? XC_SCHEME_TWO_SIDED : XC_SCHEME_BLOCKS)
                                            : prm.scheme;
   p->eps = eps;
-  p->eps2 = prm.eps2 > 0 ? prm.eps2 : (prm.precision == XC_FP64 ? 1e-3 : 1e-1);
+  p->eps2 = prm.eps2 > 0 ? prm.eps2 : (p->io64() ? 1e-3 : 1e-1);
   if (prm.nodes == XC_NODES_USER) p->nodes_host.assign(prm.user_nodes, prm.user_nodes + N);
   int rc = xc::make_schedule(N, eps, p->eps2, p->scheme == XC_SCHEME_TWO_SIDED, prm.eps_window,
                              prm.tail_max > 0 ? prm.tail_max : 20, &p->sch);

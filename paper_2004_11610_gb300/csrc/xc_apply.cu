@@ -137,6 +137,101 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
   retire_warp(&counters[2], &counters[3], gridDim.x * kSparseWarps, lane);
 }
 
+// ------------------------------------------------ FP64 plans in FP32 pairs
+// Per right-hand side r: e[r] = the binary exponent of max_n |v[r][n] rs[n]|
+// (0 for a zero vector), so that v 2^-e[r] lies below 1 in magnitude; with
+// `out`, also out[r][n] = pair(v[r][n] rs[n] 2^-e[r]).  One CTA per RHS.
+__global__ void __launch_bounds__(256)
+    pair_scale_kernel(const double* __restrict__ v, int64_t ld, int64_t N, const double* __restrict__ rs,
+                      int* __restrict__ e, float2* __restrict__ out) {
+  __shared__ double red[8];
+  __shared__ int s_e;
+  const int64_t r = blockIdx.x;
+  const double* __restrict__ vr = v + r * ld;
+  double m = 0.0;
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) m = fmax(m, fabs(vr[n] * (rs ? rs[n] : 1.0)));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) mm = fmax(mm, red[i]);
+    int ex = 0;
+    if (mm > 0.0) frexp(mm, &ex);
+    s_e = ex;
+    e[r] = ex;
+  }
+  __syncthreads();
+  if (out) {
+    const int ex = -s_e;
+    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) out[r * N + n] = to_pair(ldexp(vr[n] * (rs ? rs[n] : 1.0), ex));
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads)
+    fwd_fft_pair_kernel(const BlockDev* __restrict__ blocks, const double* __restrict__ x, int64_t ld,
+                        const double* __restrict__ colscale, cx<double>* __restrict__ spec, int64_t nrhs,
+                        const int* __restrict__ pexp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fwd_fft_body<double>(blocks[blockIdx.y], blockIdx.x, x, ld, colscale, spec, nrhs,
+                       reinterpret_cast<cx<double>*>(smem_raw), threadIdx.x, blockDim.x, pexp);
+}
+
+template <int RPW>
+__global__ void __launch_bounds__(32 * kSparseWarps)
+    fwd_sparse_pair_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N, const double* __restrict__ x,
+                           int64_t ld, double* __restrict__ y, const PairCx* __restrict__ spec, int64_t nrhs,
+                           const int* __restrict__ pexp, const double* __restrict__ rowscale,
+                           const double* __restrict__ colscale, const double* __restrict__ tail, int64_t m_tail,
+                           const int* __restrict__ order, unsigned* counters, int sg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nsup = ((nrhs + RPW - 1) / RPW + sg - 1) / sg;
+  const int64_t total = ((N + 31) / 32) * nsup;
+  for (;;) {
+    const int64_t t = take_item(&counters[0], lane);
+    if (t >= total) break;
+    fwd_sparse_item_pair<RPW>(blocks, nblocks, N, x, ld, y, spec, nrhs, pexp, rowscale, colscale, tail, m_tail,
+                              order[t / nsup], (t % nsup) * int64_t(sg) * RPW, lane, sg);
+  }
+  retire_warp(&counters[0], &counters[1], gridDim.x * kSparseWarps, lane);
+}
+
+template <int RPW>
+__global__ void __launch_bounds__(32 * kSparseWarps)
+    fwd_unit_pair_kernel(const BlockDev* __restrict__ blocks, const PairCx* __restrict__ spec, int64_t nrhs,
+                         const int* __restrict__ pexp, cx<double>* __restrict__ part, const int4* __restrict__ units,
+                         const int* __restrict__ order, int64_t total_units, unsigned* counters, int sg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nsup = ((nrhs + RPW - 1) / RPW + sg - 1) / sg;
+  const int64_t total = total_units * nsup;
+  for (;;) {
+    const int64_t t = take_item(&counters[0], lane);
+    if (t >= total) break;
+    const int u = order[t / nsup];
+    fwd_unit_item_pair<RPW>(blocks, spec, nrhs, pexp, part, units[u], u, (t % nsup) * int64_t(sg) * RPW, lane, sg);
+  }
+  retire_warp(&counters[0], &counters[1], gridDim.x * kSparseWarps, lane);
+}
+
+template <int RPW>
+__global__ void __launch_bounds__(32 * kSparseWarps)
+    adj_sparse_pair_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N,
+                           const float2* __restrict__ yp, const int* __restrict__ pexp, cx<double>* __restrict__ part,
+                           int64_t nrhs, const int2* __restrict__ items, const int* __restrict__ cbase,
+                           int64_t total_chunks, unsigned* counters, int sg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nsup = ((nrhs + RPW - 1) / RPW + sg - 1) / sg;
+  const int64_t total = total_chunks * nsup;
+  for (;;) {
+    const int64_t t = take_item(&counters[2], lane);
+    if (t >= total) break;
+    adj_sparse_item_pair<RPW>(blocks, nblocks, yp, N, pexp, part, nrhs, cbase, items[t / nsup],
+                              (t % nsup) * int64_t(sg) * RPW, lane, sg);
+  }
+  retire_warp(&counters[2], &counters[3], gridDim.x * kSparseWarps, lane);
+}
+
 // y [nrhs][ld] -> yt [N][ldt] (zero columns beyond nrhs).
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -388,6 +483,128 @@ int adjoint_impl(Plan* p, const void* y, void* x, int64_t nrhs, int64_t ld, cuda
   return XC_OK;
 }
 
+// ------------------------------------------------ FP64 plans in FP32 pairs
+int* pair_exponents(Plan* p) { return reinterpret_cast<int*>(static_cast<char*>(p->scratch) + p->pexp_off); }
+
+template <int RPW>
+int launch_pair_fwd_rpw(Plan* p, const double* x, double* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  const BlockDev* bd = static_cast<const BlockDev*>(p->scratch_desc);
+  const PairCx* spec = static_cast<const PairCx*>(p->scratch);
+  int* pexp = pair_exponents(p);
+  const int64_t ngroups = (nrhs + RPW - 1) / RPW;
+  unsigned grid = 1;
+  if (p->fwd_chunked) {
+    const void* fn = reinterpret_cast<const void*>(fwd_unit_pair_kernel<RPW>);
+    const int sg = supergroup(fn, p->total_units, ngroups);
+    XC_TRY(persistent_grid(fn, p->total_units * ((ngroups + sg - 1) / sg), &grid, 4));
+    cx<double>* part = static_cast<cx<double>*>(p->scratch) + p->spec_per_rhs * nrhs;
+    launch_begin(p, K_FWD_SPARSE, st);
+    fwd_unit_pair_kernel<RPW><<<grid, 32 * kSparseWarps, 0, st>>>(bd, spec, nrhs, pexp, part, p->fu_units,
+                                                                   p->fu_order, p->total_units, p->counters, sg);
+    launch_end(p, K_FWD_SPARSE, st);
+    XC_CUDA(cudaGetLastError());
+    dim3 rgrid(unsigned((p->N + 255) / 256), unsigned(std::min<int64_t>(nrhs, 65535)));
+    launch_begin(p, K_FWD_REDUCE, st);
+    fwd_reduce_kernel<double, false><<<rgrid, 256, 0, st>>>(p->N, x, ld, y, part, nrhs, p->fu_ubase,
+                                                            static_cast<const double*>(p->rowscale),
+                                                            static_cast<const double*>(p->colscale),
+                                                            static_cast<const double*>(p->tail), p->m_tail);
+    launch_end(p, K_FWD_REDUCE, st);
+    XC_CUDA(cudaGetLastError());
+    return XC_OK;
+  }
+  const void* fn = reinterpret_cast<const void*>(fwd_sparse_pair_kernel<RPW>);
+  const int sg = supergroup(fn, p->nslices, ngroups);
+  XC_TRY(persistent_grid(fn, p->nslices * ((ngroups + sg - 1) / sg), &grid, 4));
+  launch_begin(p, K_FWD_SPARSE, st);
+  fwd_sparse_pair_kernel<RPW><<<grid, 32 * kSparseWarps, 0, st>>>(
+      bd, int(p->blocks.size()), p->N, x, ld, y, spec, nrhs, pexp, static_cast<const double*>(p->rowscale),
+      static_cast<const double*>(p->colscale), static_cast<const double*>(p->tail), p->m_tail, p->f_order,
+      p->counters, sg);
+  launch_end(p, K_FWD_SPARSE, st);
+  XC_CUDA(cudaGetLastError());
+  return XC_OK;
+}
+
+int apply_pair(Plan* p, const void* xv, void* yv, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  const double* x = static_cast<const double*>(xv);
+  double* y = static_cast<double*>(yv);
+  int* pexp = pair_exponents(p);
+  launch_begin(p, K_PAIR_SCALE, st);
+  pair_scale_kernel<<<unsigned(nrhs), 256, 0, st>>>(x, ld, p->N, nullptr, pexp, nullptr);
+  launch_end(p, K_PAIR_SCALE, st);
+  XC_CUDA(cudaGetLastError());
+  if (!p->blocks.empty()) {
+    const size_t smem = size_t(p->max_n) * sizeof(cx<double>);
+    static thread_local size_t configured = 0;
+    if (smem > 48 * 1024 && smem > configured) {
+      XC_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(fwd_fft_pair_kernel<double>),
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+      configured = smem;
+    }
+    dim3 grid(unsigned(nrhs), unsigned(p->blocks.size()));
+    launch_begin(p, K_FWD_FFT, st);
+    fwd_fft_pair_kernel<double><<<grid, kFftThreads, smem, st>>>(static_cast<const BlockDev*>(p->scratch_desc), x, ld,
+                                                                 static_cast<const double*>(p->colscale),
+                                                                 static_cast<cx<double>*>(p->scratch), nrhs, pexp);
+    launch_end(p, K_FWD_FFT, st);
+    XC_CUDA(cudaGetLastError());
+  }
+  switch (choose_rpw(8, p->fwd_chunked ? p->total_units : p->nslices, nrhs)) {
+    case 8: return launch_pair_fwd_rpw<8>(p, x, y, nrhs, ld, st);
+    case 4: return launch_pair_fwd_rpw<4>(p, x, y, nrhs, ld, st);
+    case 2: return launch_pair_fwd_rpw<2>(p, x, y, nrhs, ld, st);
+    default: return launch_pair_fwd_rpw<1>(p, x, y, nrhs, ld, st);
+  }
+}
+
+template <int RPW>
+int launch_pair_adj_rpw(Plan* p, const float2* yp, int64_t nrhs, cudaStream_t st) {
+  if (p->total_chunks == 0) return XC_OK;
+  const void* fn = reinterpret_cast<const void*>(adj_sparse_pair_kernel<RPW>);
+  unsigned grid = 1;
+  const int64_t ngroups = (nrhs + RPW - 1) / RPW;
+  const int sg = supergroup(fn, p->total_chunks, ngroups);
+  XC_TRY(persistent_grid(fn, p->total_chunks * ((ngroups + sg - 1) / sg), &grid));
+  launch_begin(p, K_ADJ_SPARSE, st);
+  adj_sparse_pair_kernel<RPW><<<grid, 32 * kSparseWarps, 0, st>>>(
+      static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->N, yp, pair_exponents(p),
+      static_cast<cx<double>*>(p->scratch), nrhs, p->t_items, p->t_cbase, p->total_chunks, p->counters, sg);
+  launch_end(p, K_ADJ_SPARSE, st);
+  XC_CUDA(cudaGetLastError());
+  return XC_OK;
+}
+
+int adjoint_pair(Plan* p, const void* yv, void* xv, int64_t nrhs, int64_t ld, cudaStream_t st) {
+  const double* y = static_cast<const double*>(yv);
+  if (!p->blocks.empty()) {
+    float2* yp = reinterpret_cast<float2*>(static_cast<cx<double>*>(p->scratch) + p->total_chunks * 32 * nrhs);
+    launch_begin(p, K_PAIR_SCALE, st);
+    pair_scale_kernel<<<unsigned(nrhs), 256, 0, st>>>(y, ld, p->N, static_cast<const double*>(p->rowscale),
+                                                      pair_exponents(p), yp);
+    launch_end(p, K_PAIR_SCALE, st);
+    XC_CUDA(cudaGetLastError());
+    switch (choose_rpw(8, p->total_chunks, nrhs)) {
+      case 8: XC_TRY(launch_pair_adj_rpw<8>(p, yp, nrhs, st)); break;
+      case 4: XC_TRY(launch_pair_adj_rpw<4>(p, yp, nrhs, st)); break;
+      case 2: XC_TRY(launch_pair_adj_rpw<2>(p, yp, nrhs, st)); break;
+      default: XC_TRY(launch_pair_adj_rpw<1>(p, yp, nrhs, st)); break;
+    }
+    XC_TRY(launch_fft<double>(p, false, p->scratch, xv, nrhs, ld, st));
+  }
+  if (p->m_tail > 0) {
+    dim3 grid(unsigned((p->m_tail + 7) / 8), unsigned(nrhs));
+    launch_begin(p, K_ADJ_TAIL, st);
+    adj_tail_kernel<double, false><<<grid, 256, 0, st>>>(p->N, p->m_tail, static_cast<const double*>(p->tail), y,
+                                                         ld, static_cast<double*>(xv),
+                                                         static_cast<const double*>(p->rowscale),
+                                                         static_cast<const double*>(p->colscale));
+    launch_end(p, K_ADJ_TAIL, st);
+    XC_CUDA(cudaGetLastError());
+  }
+  return XC_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------ allocation-free apply
@@ -462,6 +679,7 @@ int launch_apply_noalloc(Plan* p, const void* x, void* y, int64_t nrhs, int64_t 
                                         std::to_string(int64_t(XC_NOALLOC_SCRATCH_BYTES)) +
                                         "-byte array; split the right-hand sides");
   if (p->scratch_desc == nullptr) return fail(XC_ERR_ARG, "plan has no device descriptors");
+  if (p->precision == XC_FP64_PAIR) return fail(XC_ERR_UNSUPPORTED, "xc_apply_noalloc does not take XC_FP64_PAIR plans");
   void* spec = nullptr;
   XC_TRY(noalloc_scratch(&spec));
   switch (p->precision) {
@@ -487,7 +705,14 @@ int ensure_scratch(Plan* p, int64_t nrhs) {
   const size_t fwd_bytes = size_t(fwd) * size_t(nrhs) * cbytes;
   const size_t adj_bytes = size_t(p->total_chunks) * 32 * size_t(nrhs) * cbytes +
                            (p->any_yt ? size_t(p->N) * size_t(yt_ld(nrhs)) * p->elem_bytes() : 0);
-  const size_t bytes = std::max<size_t>({cbytes, fwd_bytes, adj_bytes});
+  size_t bytes = std::max<size_t>({cbytes, fwd_bytes, adj_bytes});
+  if (p->precision == XC_FP64_PAIR) {
+    // adjoint input pairs after the chunk partials, then the per-RHS exponents
+    const size_t adj_pair = size_t(p->total_chunks) * 32 * size_t(nrhs) * cbytes + size_t(p->N) * size_t(nrhs) * 8;
+    bytes = (std::max(bytes, adj_pair) + 255) / 256 * 256;
+    p->pexp_off = bytes;
+    bytes += size_t(nrhs) * sizeof(int);
+  }
   void* fresh = nullptr;
   if (cudaMalloc(&fresh, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -507,6 +732,7 @@ int launch_apply(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cuda
   XC_TRY(ensure_scratch(p, nrhs));
   switch (p->precision) {
     case XC_FP64: return apply_impl<double, false>(p, x, y, nrhs, ld, st);
+    case XC_FP64_PAIR: return apply_pair(p, x, y, nrhs, ld, st);
     case XC_FP32: return apply_impl<float, false>(p, x, y, nrhs, ld, st);
     default: return apply_impl<float, true>(p, x, y, nrhs, ld, st);
   }
@@ -516,6 +742,7 @@ int launch_apply_adjoint(Plan* p, const void* y, void* x, int64_t nrhs, int64_t 
   XC_TRY(ensure_scratch(p, nrhs));
   switch (p->precision) {
     case XC_FP64: return adjoint_impl<double, false>(p, y, x, nrhs, ld, st);
+    case XC_FP64_PAIR: return adjoint_pair(p, y, x, nrhs, ld, st);
     case XC_FP32: return adjoint_impl<float, false>(p, y, x, nrhs, ld, st);
     default: return adjoint_impl<float, true>(p, y, x, nrhs, ld, st);
   }

@@ -134,6 +134,7 @@ struct Plan {
   void* scratch_desc = nullptr;
   void* scratch = nullptr;
   int64_t scratch_nrhs = 0;
+  size_t pexp_off = 0;                 // XC_FP64_PAIR: byte offset of the per-RHS exponents in scratch
   void* stage = nullptr;
   int64_t stage_elems = 0;
   std::vector<void*> allocations;      // everything cudaMalloc'ed for the plan
@@ -145,14 +146,17 @@ struct Plan {
   std::vector<cudaEvent_t> event_pool;
   std::vector<int64_t> t_launches;
   std::vector<double> t_ms;
-  size_t elem_bytes() const { return precision == XC_FP64 ? 8 : 4; }
+  bool io64() const { return precision == XC_FP64 || precision == XC_FP64_PAIR; }   // FP64 vectors, FFTs, tail
+  size_t elem_bytes() const { return io64() ? 8 : 4; }
 };
 
 // Device allocation recorded in the plan (freed by xc_plan_destroy).
 int plan_alloc(Plan* p, void** ptr, size_t bytes);
 
 // Kernel identities for the launch counter and the per-kernel timing.
-enum KernelId { K_FWD_FFT = 0, K_FWD_SPARSE, K_ADJ_SPARSE, K_ADJ_FFT, K_ADJ_TAIL, K_FWD_REDUCE, K_ADJ_TRANSPOSE, K_COUNT };
+enum KernelId {
+  K_FWD_FFT = 0, K_FWD_SPARSE, K_ADJ_SPARSE, K_ADJ_FFT, K_ADJ_TAIL, K_FWD_REDUCE, K_ADJ_TRANSPOSE, K_PAIR_SCALE, K_COUNT
+};
 
 // Row stride of the transposed adjoint input: nrhs rounded up to 8.
 inline int64_t yt_ld(int64_t nrhs) { return (nrhs + 7) / 8 * 8; }

@@ -63,6 +63,44 @@ struct Acc {
   __device__ __forceinline__ T value() const { return COMP ? s + c : s; }
 };
 
+// ------------------------------------------------------ FP32 pairs
+// XC_FP64_PAIR plans keep FP64 vectors and FFTs but store band values and
+// spectra as pairs of FP32 numbers, v = hi + lo with |lo| <= ulp(hi)/2
+// (48-bit significands), and run the band products on the FP32 pipes: a
+// product a*b of pairs is hi*hi exactly (TwoProduct by FMA) plus the cross
+// terms hi*lo + lo*hi, and the sum is accumulated with TwoSum, its errors
+// collected in a second FP32 word.  The result matches FP64 accumulation to a
+// few units of 2^-48 of the summed magnitudes, independently of the band
+// length, while the FP32 pipes run 64 times the FP64 rate on this GPU.
+struct __align__(16) PairCx {
+  float re_hi, re_lo, im_hi, im_lo;
+};
+
+__device__ __forceinline__ float2 to_pair(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - double(hi)));
+}
+__device__ __forceinline__ PairCx to_pair(double re, double im) {
+  const float2 a = to_pair(re), b = to_pair(im);
+  return PairCx{a.x, a.y, b.x, b.y};
+}
+
+struct AccPair {
+  float s = 0.f, c = 0.f;
+  // += (ah + al) (bh + bl)
+  __device__ __forceinline__ void add(float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    const float e = fmaf(ah, bh, -p);               // ah*bh = p + e exactly
+    const float x = fmaf(ah, bl, al * bh);          // cross terms
+    const float t = s + p;                           // TwoSum(s, p)
+    const float bb = t - s;
+    const float err = (s - (t - bb)) + (p - bb);
+    s = t;
+    c += err + (e + x);
+  }
+  __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
 // ------------------------------------------------------ band streaming
 // Band rows [j0, j1) of a slice whose value (j, lane) sits at base[j*32 + lane]:
 // step(j) is called for every row in order, four rows per unrolled iteration
@@ -108,10 +146,12 @@ __device__ __forceinline__ void fwd_band(const cx<T>* __restrict__ base, int lan
 }
 
 // ------------------------------------------------------------ forward FFT
+// With `pair_exp` (FP64 plans whose band products run in FP32 pairs), the
+// spectrum is written as pairs (see PairCx) scaled by 2^-pair_exp[r].
 template <typename T>
 __device__ void fwd_fft_body(const BlockDev& b, int64_t r, const T* __restrict__ x, int64_t ld,
                              const T* __restrict__ colscale, cx<T>* __restrict__ spec, int64_t nrhs, cx<T>* s,
-                             int tid, int nthreads) {
+                             int tid, int nthreads, const int* __restrict__ pair_exp = nullptr) {
   const int n = b.n, j_lo = b.j_lo, j_hi = b.j_hi, off = b.off;
   const T* __restrict__ invw = static_cast<const T*>(b.invw);
   const int* __restrict__ perm = b.perm;
@@ -135,6 +175,19 @@ __device__ void fwd_fft_body(const BlockDev& b, int64_t r, const T* __restrict__
   __syncthreads();
   fft_inplace<T>(s, n, b.p, b.radix, tw, tid, nthreads);
   cx<T>* out = spec + b.spec_off * nrhs + r * int64_t(n + 1);
+  if constexpr (sizeof(T) == 8) {
+    if (pair_exp) {
+      const int e = -pair_exp[r];
+      PairCx* po = reinterpret_cast<PairCx*>(out);
+      for (int k = tid; k <= n / 2; k += nthreads) {
+        cx<T> Uk, Unk;
+        r2c_split(s, n, k, tw, &Uk, &Unk);
+        po[k] = to_pair(ldexp(Uk.re, e), ldexp(Uk.im, e));
+        if (n - k != k) po[n - k] = to_pair(ldexp(Unk.re, e), ldexp(Unk.im, e));
+      }
+      return;
+    }
+  }
   for (int k = tid; k <= n / 2; k += nthreads) {
     cx<T> Uk, Unk;
     r2c_split(s, n, k, tw, &Uk, &Unk);
@@ -354,6 +407,135 @@ __device__ __forceinline__ void transpose_tile(const T* __restrict__ y, int64_t 
   for (int i = ty; i < 32; i += 8) {
     const int64_t n = n_base + i, r = r_base + tx;
     if (n < N && r < ldt) yt[n * ldt + r] = tile[tx][i];
+  }
+}
+
+// ------------------------------------------- band products in FP32 pairs
+// Forward band rows [j0, j1) for RPW right-hand sides, pairs (values, spectra).
+template <int RPW>
+__device__ __forceinline__ void fwd_band_pair(const PairCx* __restrict__ base, int lane,
+                                              const PairCx* __restrict__ F, int H, int j0, int j1, int nq,
+                                              AccPair (&acc)[RPW]) {
+  const PairCx* __restrict__ val = base + lane;
+  band_rows<double>(j0, j1, [&](int j) {
+    const PairCx c = val[j * 32];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      if (q < nq) {
+        const PairCx f = F[q * H + j];
+        acc[q].add(c.re_hi, c.re_lo, f.re_hi, f.re_lo);
+        acc[q].add(c.im_hi, c.im_lo, f.im_hi, f.im_lo);
+      }
+    }
+  });
+}
+
+// fwd_sparse_item for pair plans: the band sums scaled back by 2^e[r] (the
+// spectra were scaled by 2^-e[r]), the dense tail and the output in FP64.
+template <int RPW>
+__device__ void fwd_sparse_item_pair(const BlockDev* __restrict__ blocks, int nblocks, int64_t N,
+                                     const double* __restrict__ x, int64_t ld, double* __restrict__ y,
+                                     const PairCx* __restrict__ spec, int64_t nrhs, const int* __restrict__ pexp,
+                                     const double* __restrict__ rowscale, const double* __restrict__ colscale,
+                                     const double* __restrict__ tail, int64_t m_tail, int64_t slice, int64_t r_begin,
+                                     int lane, int groups = 1) {
+  const int64_t n = slice * 32 + lane;
+  for (int grp = 0; grp < groups; ++grp) {
+    const int64_t r0 = r_begin + int64_t(grp) * RPW;
+    if (r0 >= nrhs) break;
+    const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
+    AccPair acc[RPW];
+    for (int i = 0; i < nblocks; ++i) {
+      const BlockDev& b = blocks[i];
+      const int W = b.f_width[slice];
+      const int k0 = b.f_k0[n];
+      const int H = b.H;
+      fwd_band_pair<RPW>(static_cast<const PairCx*>(b.f_val) + b.f_off[slice], lane,
+                         spec + b.spec_off * nrhs + r0 * H + k0, H, 0, W, nq, acc);
+    }
+    if (n < N) {
+      const double rs = rowscale ? rowscale[n] : 1.0;
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        if (q < nq) {
+          double t = ldexp(acc[q].value(), pexp[r0 + q]);
+          for (int64_t m = 0; m < m_tail; ++m)
+            t = fma(tail[m * N + n], x[(r0 + q) * ld + m] * (colscale ? colscale[m] : 1.0), t);
+          y[(r0 + q) * ld + n] = t * rs;
+        }
+      }
+    }
+  }
+}
+
+// fwd_unit_item for pair plans: the partial goes out as one FP64 value (in
+// the `re` word of the plan's partial array), already scaled back.
+template <int RPW>
+__device__ void fwd_unit_item_pair(const BlockDev* __restrict__ blocks, const PairCx* __restrict__ spec,
+                                   int64_t nrhs, const int* __restrict__ pexp, cx<double>* __restrict__ part,
+                                   int4 unit, int64_t u, int64_t r_begin, int lane, int groups = 1) {
+  const BlockDev& b = blocks[unit.x];
+  const int64_t slice = unit.y;
+  const int64_t n = slice * 32 + lane;
+  const int j0 = unit.z * kFwdChunk, j1 = j0 + unit.w;
+  const int k0 = b.f_k0[n];
+  const int H = b.H;
+  const PairCx* __restrict__ base = static_cast<const PairCx*>(b.f_val) + b.f_off[slice];
+  for (int grp = 0; grp < groups; ++grp) {
+    const int64_t r0 = r_begin + int64_t(grp) * RPW;
+    if (r0 >= nrhs) break;
+    const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
+    AccPair acc[RPW];
+    fwd_band_pair<RPW>(base, lane, spec + b.spec_off * nrhs + r0 * H + k0, H, j0, j1, nq, acc);
+    cx<double>* out = part + (u * nrhs + r0) * 32 + lane;
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+      if (q < nq) out[q * 32] = cx<double>{ldexp(acc[q].value(), pexp[r0 + q]), 0.0};
+  }
+}
+
+// adj_sparse_item for pair plans: y arrives as pairs yp[r][n] scaled by
+// 2^-e[r]; the chunk partials go out in FP64, scaled back.
+template <int RPW>
+__device__ void adj_sparse_item_pair(const BlockDev* __restrict__ blocks, int nblocks,
+                                     const float2* __restrict__ yp, int64_t N, const int* __restrict__ pexp,
+                                     cx<double>* __restrict__ part, int64_t nrhs, const int* __restrict__ cbase,
+                                     int2 it, int64_t r_begin, int lane, int groups = 1) {
+  int i = 0;
+  while (i < nblocks - 1 && it.x >= blocks[i].t_gbase + blocks[i].tslices) ++i;
+  const BlockDev& b = blocks[i];
+  const int gl = it.x - b.t_gbase;
+  const int64_t k = int64_t(gl) * 32 + lane;
+  const int W = b.t_width[gl];
+  const int j0 = it.y * kAdjChunk;
+  const int j1 = min(W, j0 + kAdjChunk);
+  const int64_t n0 = b.t_n0[k];
+  const PairCx* __restrict__ val = static_cast<const PairCx*>(b.t_val) + b.t_off[gl] + lane;
+  const int64_t cb = cbase[it.x];
+  for (int grp = 0; grp < groups; ++grp) {
+    const int64_t r0 = r_begin + int64_t(grp) * RPW;
+    if (r0 >= nrhs) break;
+    const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
+    AccPair re[RPW], im[RPW];
+    band_rows<double>(j0, j1, [&](int j) {
+      const PairCx c = val[j * 32];
+      const int64_t row = n0 + j;
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        if (q < nq) {
+          const float2 v = yp[(r0 + q) * N + row];
+          re[q].add(c.re_hi, c.re_lo, v.x, v.y);
+          im[q].add(c.im_hi, c.im_lo, v.x, v.y);
+        }
+      }
+    });
+    cx<double>* out = part + ((cb + it.y) * nrhs + r0) * 32 + lane;
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+      if (q < nq) {
+        const int e = pexp[r0 + q];
+        out[q * 32] = cx<double>{ldexp(re[q].value(), e), ldexp(im[q].value(), e)};
+      }
   }
 }
 

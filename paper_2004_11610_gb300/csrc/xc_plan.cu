@@ -16,6 +16,7 @@
 
 #include "xc_fft.cuh"
 #include "xc_internal.h"
+#include "xc_items.cuh"
 
 namespace xc {
 
@@ -589,12 +590,25 @@ __global__ void extents_kernel(const cx<double>* S, int64_t N, int64_t H, double
   }
 }
 
+// A stored band value in the plan's format: cx<T>, or (pair, T = double) the
+// FP32 pair split of each part in the same 16 bytes.
+template <typename T>
+__device__ __forceinline__ void store_value(cx<T>* dst, cx<double> v, int pair) {
+  if constexpr (sizeof(T) == 8) {
+    if (pair) {
+      *reinterpret_cast<PairCx*>(dst) = to_pair(v.re, v.im);
+      return;
+    }
+  }
+  *dst = cx<T>{T(v.re), T(v.im)};
+}
+
 // Forward band values: slice s, position j, lane -> row 32 s + lane, bin
 // k0[row] + j; kept elements times g_k (2 inside the half spectrum, 1 at k = 0
 // and k = n), everything else zero.
 template <typename T>
 __global__ void fill_forward_kernel(const cx<double>* S, int64_t N, int n, double thr, const int* k0,
-                                    const int* width, const int64_t* off, int nslices, cx<T>* val) {
+                                    const int* width, const int64_t* off, int nslices, cx<T>* val, int pair) {
   const int s = blockIdx.y;
   if (s >= nslices) return;
   const int W = width[s];
@@ -609,13 +623,13 @@ __global__ void fill_forward_kernel(const cx<double>* S, int64_t N, int n, doubl
     const cx<double> a = S[row * int64_t(n + 1) + k];
     if (kept(a, thr)) v = scal((k == 0 || k == n) ? 1.0 : 2.0, a);
   }
-  val[off[s] + idx] = cx<T>{T(v.re), T(v.im)};
+  store_value(val + off[s] + idx, v, pair);
 }
 
 // Transposed band values: slice s of bins, lane -> bin 32 s + lane, row n0[bin] + j.
 template <typename T>
 __global__ void fill_adjoint_kernel(const cx<double>* S, int64_t N, int n, double thr, const int* n0,
-                                    const int* width, const int64_t* off, int tslices, cx<T>* val) {
+                                    const int* width, const int64_t* off, int tslices, cx<T>* val, int pair) {
   const int s = blockIdx.y;
   if (s >= tslices) return;
   const int W = width[s];
@@ -630,7 +644,7 @@ __global__ void fill_adjoint_kernel(const cx<double>* S, int64_t N, int n, doubl
     const cx<double> a = S[row * int64_t(n + 1) + k];
     if (kept(a, thr)) v = a;
   }
-  val[off[s] + idx] = cx<T>{T(v.re), T(v.im)};
+  store_value(val + off[s] + idx, v, pair);
 }
 
 // Dense tail [m][N] and the plain matrix (comparison path).
@@ -678,7 +692,7 @@ int dense_matrix_device(const Plan* p, void* A, int64_t lda, cudaStream_t s) {
   GenParams g{p->family, p->N, p->params.alpha, p->params.beta, p->nodes_dev,
               p->family == XC_CHEBYSHEV_T && p->params.nodes == XC_NODES_GAUSS};
   const unsigned grid = unsigned((p->N + 31) / 32);
-  if (p->precision == XC_FP64)
+  if (p->io64())
     dense_kernel<double><<<grid, 32, 0, s>>>(g, static_cast<const double*>(p->rowscale),
                                               static_cast<const double*>(p->colscale), static_cast<double*>(A), lda);
   else
@@ -905,6 +919,11 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
   };
   XC_TRY(read_threshold());
   p->maxabs[bi] = std::sqrt(maxsq);
+  const int pair = p->precision == XC_FP64_PAIR ? 1 : 0;
+  // stored values reach 2 max|S| (the half-spectrum factor): keep them well
+  // inside the FP32 range
+  if (pair && !(2.0 * std::sqrt(maxsq) < 1e30))
+    return fail(XC_ERR_UNSUPPORTED, "band values exceed the FP32 range of XC_FP64_PAIR; use XC_FP64");
 
   // extents of the kept elements per row
   DevBuf kf, kl, cnt;
@@ -1034,12 +1053,12 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
   if (maxW > 0) {
     dim3 grid(unsigned((int64_t(maxW) * kSlice + 255) / 256), unsigned(nslices));
     fill_forward_kernel<T><<<grid, 256>>>(static_cast<cx<double>*>(Sbuf.ptr), N, n, thr, fk0_d, fw_d, foff_d,
-                                          nslices, static_cast<cx<T>*>(fval));
+                                          nslices, static_cast<cx<T>*>(fval), pair);
   }
   if (maxTW > 0) {
     dim3 grid(unsigned((int64_t(maxTW) * kSlice + 255) / 256), unsigned(tslices));
     fill_adjoint_kernel<T><<<grid, 256>>>(static_cast<cx<double>*>(Sbuf.ptr), N, n, thr, tn0_d, tw_d, toff_d,
-                                          tslices, static_cast<cx<T>*>(tval));
+                                          tslices, static_cast<cx<T>*>(tval), pair);
   }
   XC_CUDA(cudaGetLastError());
   XC_CUDA(cudaDeviceSynchronize());
@@ -1096,7 +1115,7 @@ int build_plan_device(Plan* p) {
 
   GenParams g{p->family, N, p->params.alpha, p->params.beta, p->nodes_dev,
               p->family == XC_CHEBYSHEV_T && !user};
-  const bool fp64 = p->precision == XC_FP64;
+  const bool fp64 = p->io64();
   if (p->normalise == XC_ORTHONORMAL) {
     DevBuf lam;
     XC_TRY(alloc_tmp(&lam, size_t(N) * sizeof(double)));

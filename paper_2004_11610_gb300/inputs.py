@@ -52,6 +52,11 @@ WORKLOADS = {
     "cheb_lag4096_fp64": dict(
         plans=[("chebyshev", 4096, {}), ("laguerre", 4096, {})], eps=1e-12, precision="fp64",
         nrhs=64, dist="normal"),
+    # The same workload with FP64 vectors and FFTs but the band products in
+    # FP32 pairs (XC_FP64_PAIR).
+    "cheb_lag4096_fp64pair": dict(
+        plans=[("chebyshev", 4096, {}), ("laguerre", 4096, {})], eps=1e-12, precision="fp64pair",
+        nrhs=64, dist="normal"),
     # Legendre and Jacobi(1/2,-1/2) at N=16384, FP32 compensated apply,
     # eps=1e-7, 256 uniform[-1,1] RHS.
     "leg_jac16384_fp32c": dict(

@@ -21,7 +21,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 # ------------------------------------------------------------------ constants
 XC_OK, XC_ERR_ARG, XC_ERR_ALLOC, XC_ERR_CUDA, XC_ERR_TIMEOUT, XC_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 FAMILY = {"chebyshev": 0, "legendre": 1, "jacobi": 2, "laguerre": 3, "hermite": 4}
-PRECISION = {"fp64": 0, "fp32": 1, "fp32c": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32c": 2, "fp64pair": 3}
 SCHEME = {"auto": 0, "two_sided": 1, "blocks": 2}
 XC_MAX_BLOCKS = 16
 
@@ -151,7 +151,7 @@ class Plan:
                "xc_plan_create")
         self._h = h
         self.family, self.N, self.eps, self.precision = family, int(N), float(eps), precision
-        self.np_dtype = np.float64 if precision == "fp64" else np.float32
+        self.np_dtype = np.float64 if precision in ("fp64", "fp64pair") else np.float32
 
     # -- lifetime
     def close(self) -> None:
@@ -178,7 +178,7 @@ class Plan:
     @property
     def torch_dtype(self):
         import torch
-        return torch.float64 if self.precision == "fp64" else torch.float32
+        return torch.float64 if self.precision in ("fp64", "fp64pair") else torch.float32
 
     # -- queries
     def info(self) -> dict:

@@ -80,7 +80,7 @@ def check_schedule(ora, plan):
 
 
 def run_both(xc, plan, ora, X, adjoint=False):
-    dt = torch.float64 if plan.precision == "fp64" else torch.float32
+    dt = torch.float64 if plan.precision in ("fp64", "fp64pair") else torch.float32
     Xd = torch.from_numpy(X).to("cuda", dt)
     out = plan.apply_adjoint(Xd) if adjoint else plan.apply(Xd)
     torch.cuda.synchronize()
@@ -113,6 +113,29 @@ def test_fp64_forward_and_adjoint_match_oracle(xc, fam, N, eps, nrhs):
         Y = inputs.normal(N, nrhs, 12)
         xa, xa_ref = run_both(xc, plan, ora, Y, adjoint=True)
         assert max_rel(xa, xa_ref) <= tol
+
+
+@pytest.mark.parametrize("fam,N,eps", [("legendre", 512, 1e-14), ("chebyshev", 1000, 1e-12), ("laguerre", 700, 1e-12),
+                                       ("hermite", 400, 1e-10), ("jacobi", 333, 1e-10), ("legendre", 64, 0.0)])
+@pytest.mark.parametrize("nrhs", [1, 9])
+def test_fp64_pair_matches_oracle(xc, fam, N, eps, nrhs):
+    """XC_FP64_PAIR (FP64 vectors and FFTs, band products in FP32 pairs with
+    error-free accumulation) meets the FP64 tolerances."""
+    ora, plan = gpu_plan(xc, fam, N, eps, "fp64pair", 1e-3)
+    with plan:
+        check_schedule(ora, plan)
+        tol = fp64_tol(ora, eps)
+        X = inputs.uniform_pm1(N, nrhs, 13)
+        y, y_ref = run_both(xc, plan, ora, X)
+        assert max_rel(y, y_ref) <= tol
+        Y = inputs.normal(N, nrhs, 14)
+        xa, xa_ref = run_both(xc, plan, ora, Y, adjoint=True)
+        assert max_rel(xa, xa_ref) <= tol
+        # far from unit scale: the per-RHS power-of-two scaling keeps the pairs in range
+        y2, y2_ref = run_both(xc, plan, ora, X * 1e200)
+        assert max_rel(y2, y2_ref) <= tol
+        xa2, xa2_ref = run_both(xc, plan, ora, Y * 1e-200, adjoint=True)
+        assert max_rel(xa2, xa2_ref) <= tol
 
 
 @pytest.mark.parametrize("fam,N,eps", [("legendre", 700, 1e-7), ("jacobi", 515, 1e-7), ("chebyshev", 640, 1e-7),
