@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <unordered_map>
 
 #include "xc_fft.cuh"
 #include "xc_internal.h"
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
     adj_sparse_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N, const T* __restrict__ y,
                       int64_t ld, const T* __restrict__ yt, int64_t ldt, cx<T>* __restrict__ part, int64_t nrhs, const T* __restrict__ rowscale,
                       const int2* __restrict__ items, const int* __restrict__ cbase, int64_t total_chunks,
-                      unsigned* counters, int sg) {
+                      int chunk, unsigned* counters, int sg) {
   (void)N;
   const int lane = threadIdx.x & 31;
   const int64_t nsup = ((nrhs + RPW - 1) / RPW + sg - 1) / sg;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
     const int64_t t = take_item(&counters[2], lane);
     if (t >= total) break;
     adj_sparse_item<T, RPW, COMP, YT>(blocks, nblocks, y, ld, yt, ldt, part, nrhs, rowscale, cbase,
-                                      items[t / nsup], (t % nsup) * int64_t(sg) * RPW, lane, sg);
+                                      items[t / nsup], chunk, (t % nsup) * int64_t(sg) * RPW, lane, sg);
   }
   retire_warp(&counters[2], &counters[3], gridDim.x * kSparseWarps, lane);
 }
@@ -219,14 +220,14 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
     adj_sparse_pair_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N,
                            const float2* __restrict__ yp, const int* __restrict__ pexp, cx<double>* __restrict__ part,
                            int64_t nrhs, const int2* __restrict__ items, const int* __restrict__ cbase,
-                           int64_t total_chunks, unsigned* counters, int sg) {
+                           int64_t total_chunks, int chunk, unsigned* counters, int sg) {
   const int lane = threadIdx.x & 31;
   const int64_t nsup = ((nrhs + RPW - 1) / RPW + sg - 1) / sg;
   const int64_t total = total_chunks * nsup;
   for (;;) {
     const int64_t t = take_item(&counters[2], lane);
     if (t >= total) break;
-    adj_sparse_item_pair<RPW>(blocks, nblocks, yp, N, pexp, part, nrhs, cbase, items[t / nsup],
+    adj_sparse_item_pair<RPW>(blocks, nblocks, yp, N, pexp, part, nrhs, cbase, items[t / nsup], chunk,
                               (t % nsup) * int64_t(sg) * RPW, lane, sg);
   }
   retire_warp(&counters[2], &counters[3], gridDim.x * kSparseWarps, lane);
@@ -243,24 +244,41 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Persistent grid: as many CTAs as can be resident, but no more than the
-// items need.
-int persistent_grid(const void* fn, int64_t items, unsigned* grid, int items_per_warp = 1) {
+// Resident CTAs of kSparseWarps warps per SM for a kernel, and the SM count:
+// queried once per kernel and host thread (the queries cost microseconds,
+// which small applies would otherwise pay at every launch).
+int resident_ctas(const void* fn, int* per_sm, int* sms) {
   static thread_local int cached_sms = 0;
+  static thread_local std::unordered_map<const void*, int> cache;
   if (cached_sms == 0) {
     int dev = 0;
     XC_CUDA(cudaGetDevice(&dev));
     XC_CUDA(cudaDeviceGetAttribute(&cached_sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  int per_sm = 0;
-  XC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * kSparseWarps, 0));
-  if (per_sm < 1) per_sm = 1;
-  // every resident warp takes part (warps that find the list empty retire at
-  // once); the dynamic schedule balances SMs and their schedulers
+  auto it = cache.find(fn);
+  if (it == cache.end()) {
+    int n = 0;
+    XC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * kSparseWarps, 0));
+    it = cache.emplace(fn, n < 1 ? 1 : n).first;
+  }
+  *per_sm = it->second;
+  *sms = cached_sms;
+  return XC_OK;
+}
+
+// Persistent grid: as many CTAs as can be resident, but no more than the
+// items need.  Every resident warp takes part (warps that find the list empty
+// retire at once); the dynamic schedule balances SMs and their schedulers.
+// With many items a warp is meant to take about items_per_warp of them; with
+// few, every item gets a warp of its own.
+int persistent_grid(const void* fn, int64_t items, unsigned* grid, int items_per_warp = 1) {
+  int per_sm = 1, sms = 1;
+  XC_TRY(resident_ctas(fn, &per_sm, &sms));
+  const int64_t resident = int64_t(sms) * per_sm;
+  if (items < resident * kSparseWarps * items_per_warp) items_per_warp = 1;
   const int64_t per_cta = int64_t(kSparseWarps) * items_per_warp;
   const int64_t need = (items + per_cta - 1) / per_cta;
-  const int64_t g = std::min<int64_t>(int64_t(cached_sms) * per_sm, std::max<int64_t>(1, need));
-  *grid = unsigned(g);
+  *grid = unsigned(std::min<int64_t>(resident, std::max<int64_t>(1, need)));
   return XC_OK;
 }
 
@@ -289,13 +307,12 @@ __global__ void adj_tail_kernel(int64_t N, int64_t m_tail, const T* __restrict__
 // and no more groups per item than that, so that short bands (FP32 plans,
 // small blocks) amortise each item's bookkeeping over several groups.
 int supergroup(const void* fn, int64_t units, int64_t ngroups) {
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * kSparseWarps, 0) != cudaSuccess) {
+  int per_sm = 1, sms = 1;
+  if (resident_ctas(fn, &per_sm, &sms) != XC_OK) {
     cudaGetLastError();
     return 1;
   }
-  const int64_t warps = int64_t(sms) * std::max(1, per_sm) * kSparseWarps;
+  const int64_t warps = int64_t(sms) * per_sm * kSparseWarps;
   const int64_t want_items = 4 * warps;
   const int64_t have = std::max<int64_t>(1, units * ngroups);
   if (have <= want_items) return 1;
@@ -323,7 +340,7 @@ int launch_fft(Plan* p, bool forward, const void* in, void* out, int64_t nrhs, i
                                                         static_cast<const T*>(p->colscale),
                                                         static_cast<cx<T>*>(out), nrhs);
   else
-    adj_fft_kernel<T><<<grid, kFftThreads, smem, st>>>(bd, static_cast<const cx<T>*>(in), p->t_cbase, nrhs,
+    adj_fft_kernel<T><<<grid, kFftThreads, smem, st>>>(bd, static_cast<const cx<T>*>(in), p->s_cbase, nrhs,
                                                         static_cast<T*>(out), ld, static_cast<const T*>(p->colscale));
   launch_end(p, kid, st);
   XC_CUDA(cudaGetLastError());
@@ -377,7 +394,7 @@ int launch_unit_fwd_rpw(Plan* p, const void* x, void* y, int64_t nrhs, int64_t l
 
 template <typename T, bool COMP, int RPW>
 int launch_sparse_adj_rpw(Plan* p, const void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
-  if (p->total_chunks == 0) return XC_OK;
+  if (p->s_total_chunks == 0) return XC_OK;
   // blocks whose bins start far apart read a transposed copy of y (columns
   // beyond nrhs zero), where a step reads each lane's RPW values of one row
   // as one vector; with fewer than 4 right-hand sides per item the vector
@@ -386,7 +403,7 @@ int launch_sparse_adj_rpw(Plan* p, const void* y, int64_t nrhs, int64_t ld, cuda
   const int64_t ldt = yt_ld(nrhs);
   T* yt = nullptr;
   if (p->any_yt && RPW >= 4) {
-    yt = reinterpret_cast<T*>(static_cast<cx<T>*>(p->scratch) + p->total_chunks * 32 * nrhs);
+    yt = reinterpret_cast<T*>(static_cast<cx<T>*>(p->scratch) + p->s_total_chunks * 32 * nrhs);
     launch_begin(p, K_ADJ_TRANSPOSE, st);
     const int64_t rtiles = (ldt + 31) / 32;
     transpose_kernel<T><<<dim3(unsigned((p->N + 31) / 32), unsigned(std::min<int64_t>(rtiles, 65535))), dim3(32, 8),
@@ -397,13 +414,13 @@ int launch_sparse_adj_rpw(Plan* p, const void* y, int64_t nrhs, int64_t ld, cuda
   const void* fn = reinterpret_cast<const void*>(adj_sparse_kernel<T, RPW, COMP, true>);
   unsigned grid = 1;
   const int64_t ngroups = (nrhs + RPW - 1) / RPW;
-  const int sg = supergroup(fn, p->total_chunks, ngroups);
-  XC_TRY(persistent_grid(fn, p->total_chunks * ((ngroups + sg - 1) / sg), &grid));
+  const int sg = supergroup(fn, p->s_total_chunks, ngroups);
+  XC_TRY(persistent_grid(fn, p->s_total_chunks * ((ngroups + sg - 1) / sg), &grid));
   launch_begin(p, K_ADJ_SPARSE, st);
   adj_sparse_kernel<T, RPW, COMP, true><<<grid, 32 * kSparseWarps, 0, st>>>(
       static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->N, static_cast<const T*>(y), ld, yt,
-      ldt, static_cast<cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale), p->t_items, p->t_cbase,
-      p->total_chunks, p->counters, sg);
+      ldt, static_cast<cx<T>*>(p->scratch), nrhs, static_cast<const T*>(p->rowscale), p->s_items, p->s_cbase,
+      p->s_total_chunks, p->s_chunk, p->counters, sg);
   launch_end(p, K_ADJ_SPARSE, st);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
@@ -450,7 +467,7 @@ int launch_sparse_fwd(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld,
 
 template <typename T, bool COMP>
 int launch_sparse_adj(Plan* p, const void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
-  switch (choose_rpw(sizeof(T) == 8 ? 2 : 8, p->total_chunks, nrhs)) {
+  switch (choose_rpw(sizeof(T) == 8 ? 2 : 8, p->s_total_chunks, nrhs)) {
     case 8: return launch_sparse_adj_rpw<T, COMP, 8>(p, y, nrhs, ld, st);
     case 4: return launch_sparse_adj_rpw<T, COMP, 4>(p, y, nrhs, ld, st);
     case 2: return launch_sparse_adj_rpw<T, COMP, 2>(p, y, nrhs, ld, st);
@@ -560,16 +577,17 @@ int apply_pair(Plan* p, const void* xv, void* yv, int64_t nrhs, int64_t ld, cuda
 
 template <int RPW>
 int launch_pair_adj_rpw(Plan* p, const float2* yp, int64_t nrhs, cudaStream_t st) {
-  if (p->total_chunks == 0) return XC_OK;
+  if (p->s_total_chunks == 0) return XC_OK;
   const void* fn = reinterpret_cast<const void*>(adj_sparse_pair_kernel<RPW>);
   unsigned grid = 1;
   const int64_t ngroups = (nrhs + RPW - 1) / RPW;
-  const int sg = supergroup(fn, p->total_chunks, ngroups);
-  XC_TRY(persistent_grid(fn, p->total_chunks * ((ngroups + sg - 1) / sg), &grid));
+  const int sg = supergroup(fn, p->s_total_chunks, ngroups);
+  XC_TRY(persistent_grid(fn, p->s_total_chunks * ((ngroups + sg - 1) / sg), &grid));
   launch_begin(p, K_ADJ_SPARSE, st);
   adj_sparse_pair_kernel<RPW><<<grid, 32 * kSparseWarps, 0, st>>>(
       static_cast<const BlockDev*>(p->scratch_desc), int(p->blocks.size()), p->N, yp, pair_exponents(p),
-      static_cast<cx<double>*>(p->scratch), nrhs, p->t_items, p->t_cbase, p->total_chunks, p->counters, sg);
+      static_cast<cx<double>*>(p->scratch), nrhs, p->s_items, p->s_cbase, p->s_total_chunks, p->s_chunk,
+      p->counters, sg);
   launch_end(p, K_ADJ_SPARSE, st);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
@@ -578,13 +596,13 @@ int launch_pair_adj_rpw(Plan* p, const float2* yp, int64_t nrhs, cudaStream_t st
 int adjoint_pair(Plan* p, const void* yv, void* xv, int64_t nrhs, int64_t ld, cudaStream_t st) {
   const double* y = static_cast<const double*>(yv);
   if (!p->blocks.empty()) {
-    float2* yp = reinterpret_cast<float2*>(static_cast<cx<double>*>(p->scratch) + p->total_chunks * 32 * nrhs);
+    float2* yp = reinterpret_cast<float2*>(static_cast<cx<double>*>(p->scratch) + p->s_total_chunks * 32 * nrhs);
     launch_begin(p, K_PAIR_SCALE, st);
     pair_scale_kernel<<<unsigned(nrhs), 256, 0, st>>>(y, ld, p->N, static_cast<const double*>(p->rowscale),
                                                       pair_exponents(p), yp);
     launch_end(p, K_PAIR_SCALE, st);
     XC_CUDA(cudaGetLastError());
-    switch (choose_rpw(8, p->total_chunks, nrhs)) {
+    switch (choose_rpw(8, p->s_total_chunks, nrhs)) {
       case 8: XC_TRY(launch_pair_adj_rpw<8>(p, yp, nrhs, st)); break;
       case 4: XC_TRY(launch_pair_adj_rpw<4>(p, yp, nrhs, st)); break;
       case 2: XC_TRY(launch_pair_adj_rpw<2>(p, yp, nrhs, st)); break;
@@ -703,12 +721,13 @@ int ensure_scratch(Plan* p, int64_t nrhs) {
   // y.  The directions share the buffer (one at a time).
   const int64_t fwd = p->spec_per_rhs + (p->fwd_chunked ? p->total_units * 32 : 0);
   const size_t fwd_bytes = size_t(fwd) * size_t(nrhs) * cbytes;
-  const size_t adj_bytes = size_t(p->total_chunks) * 32 * size_t(nrhs) * cbytes +
+  const int64_t chunks = std::max(p->total_chunks, p->s_total_chunks);
+  const size_t adj_bytes = size_t(chunks) * 32 * size_t(nrhs) * cbytes +
                            (p->any_yt ? size_t(p->N) * size_t(yt_ld(nrhs)) * p->elem_bytes() : 0);
   size_t bytes = std::max<size_t>({cbytes, fwd_bytes, adj_bytes});
   if (p->precision == XC_FP64_PAIR) {
     // adjoint input pairs after the chunk partials, then the per-RHS exponents
-    const size_t adj_pair = size_t(p->total_chunks) * 32 * size_t(nrhs) * cbytes + size_t(p->N) * size_t(nrhs) * 8;
+    const size_t adj_pair = size_t(chunks) * 32 * size_t(nrhs) * cbytes + size_t(p->N) * size_t(nrhs) * 8;
     bytes = (std::max(bytes, adj_pair) + 255) / 256 * 256;
     p->pexp_off = bytes;
     bytes += size_t(nrhs) * sizeof(int);

@@ -137,7 +137,7 @@ __device__ __forceinline__ void run_warp_item(const BatchPlanDev& P, int4 tk, in
     }
     case T_ADJ_SPARSE:
       adj_sparse_item<T, RPW, COMP>(P.blocks, P.nblocks, static_cast<const T*>(P.y), P.ld, nullptr, 0,
-                                    static_cast<cx<T>*>(P.scratch), P.nrhs, rs, P.t_cbase, P.t_items[tk.z],
+                                    static_cast<cx<T>*>(P.scratch), P.nrhs, rs, P.t_cbase, P.t_items[tk.z], kAdjChunk,
                                     int64_t(tk.w) * RPW, lane);
       break;
     default:  // T_ADJ_TAIL: column tk.z, RHS tk.w

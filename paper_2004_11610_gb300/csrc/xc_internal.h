@@ -84,7 +84,11 @@ struct BlockDev {
 
 // Rows per chunk of a transposed (bin) slice in the adjoint product: long
 // slices are cut into chunks whose partial sums the adjoint FFT adds up.
+// Plans with few rows in all take shorter chunks (down to kAdjChunkMin), so
+// that even one right-hand side spreads over enough warps.
 constexpr int kAdjChunk = 256;
+constexpr int kAdjChunkMin = 32;
+constexpr int64_t kAdjTargetChunks = 512;
 
 // Band rows per chunk of a row slice in the forward product of plans with long
 // bands; a reduction kernel adds the chunks of each slice.
@@ -112,6 +116,12 @@ struct Plan {
   int* f_order = nullptr;              // [nslices]
   int* t_order = nullptr;              // unused (kept zero)
   int2* t_items = nullptr;             // [total_chunks]: (global bin slice, chunk), longest chunk first
+  // the adjoint items of single-plan applies: the same as t_items / t_cbase,
+  // or (small plans) a cut into shorter chunks of s_chunk rows
+  int s_chunk = kAdjChunk;
+  int64_t s_total_chunks = 0;
+  int2* s_items = nullptr;
+  int* s_cbase = nullptr;
   int* t_cbase = nullptr;              // [total_tslices + 1]: first chunk of each bin slice
   int64_t total_chunks = 0;
   std::vector<int64_t> slice_cost;     // host: summed forward band width of each row slice

@@ -351,7 +351,7 @@ __device__ __forceinline__ void adj_chunk_rows(const cx<T>* __restrict__ base, i
 }
 
 // Item (global bin slice g, chunk c): lane = bin k; the partial sum over rows
-// [c*kAdjChunk, (c+1)*kAdjChunk) of the slice goes to part[chunk][rhs][lane].
+// [c*chunk, (c+1)*chunk) of the slice goes to part[chunk][rhs][lane].
 // Blocks marked t_yt (their bins start at rows far apart, so that a step of
 // scalar loads touches up to 32 sectors per right-hand side) read the
 // transposed copy yt when USE_YT and yt is given; the others read y, where
@@ -360,15 +360,15 @@ template <typename T, int RPW, bool COMP, bool USE_YT = false>
 __device__ void adj_sparse_item(const BlockDev* __restrict__ blocks, int nblocks, const T* __restrict__ y,
                                 int64_t ld, const T* __restrict__ yt, int64_t ldt, cx<T>* __restrict__ part,
                                 int64_t nrhs, const T* __restrict__ rowscale, const int* __restrict__ cbase, int2 it,
-                                int64_t r_begin, int lane, int groups = 1) {
+                                int chunk, int64_t r_begin, int lane, int groups = 1) {
   int i = 0;
   while (i < nblocks - 1 && it.x >= blocks[i].t_gbase + blocks[i].tslices) ++i;
   const BlockDev& b = blocks[i];
   const int gl = it.x - b.t_gbase;
   const int64_t k = int64_t(gl) * 32 + lane;
   const int W = b.t_width[gl];
-  const int j0 = it.y * kAdjChunk;
-  const int j1 = min(W, j0 + kAdjChunk);
+  const int j0 = it.y * chunk;
+  const int j1 = min(W, j0 + chunk);
   const int n0 = b.t_n0[k];
   const cx<T>* __restrict__ base = static_cast<const cx<T>*>(b.t_val) + b.t_off[gl];
   const int64_t cb = cbase[it.x];
@@ -500,15 +500,15 @@ template <int RPW>
 __device__ void adj_sparse_item_pair(const BlockDev* __restrict__ blocks, int nblocks,
                                      const float2* __restrict__ yp, int64_t N, const int* __restrict__ pexp,
                                      cx<double>* __restrict__ part, int64_t nrhs, const int* __restrict__ cbase,
-                                     int2 it, int64_t r_begin, int lane, int groups = 1) {
+                                     int2 it, int chunk, int64_t r_begin, int lane, int groups = 1) {
   int i = 0;
   while (i < nblocks - 1 && it.x >= blocks[i].t_gbase + blocks[i].tslices) ++i;
   const BlockDev& b = blocks[i];
   const int gl = it.x - b.t_gbase;
   const int64_t k = int64_t(gl) * 32 + lane;
   const int W = b.t_width[gl];
-  const int j0 = it.y * kAdjChunk;
-  const int j1 = min(W, j0 + kAdjChunk);
+  const int j0 = it.y * chunk;
+  const int j1 = min(W, j0 + chunk);
   const int64_t n0 = b.t_n0[k];
   const PairCx* __restrict__ val = static_cast<const PairCx*>(b.t_val) + b.t_off[gl] + lane;
   const int64_t cb = cbase[it.x];

@@ -1157,37 +1157,63 @@ int build_plan_device(Plan* p) {
     gbase += int64_t(tw.size());
   }
   p->total_tslices = gbase;
-  // adjoint items: every bin slice cut into chunks of kAdjChunk rows
-  std::vector<int> cbase(size_t(gbase) + 1, 0);
-  std::vector<std::pair<int, int2>> items;   // (length, (g, chunk))
-  {
-    std::vector<int64_t> widths(gbase, 0);
-    for (const auto& tc : tcost) widths[tc.second] = tc.first;
+  // adjoint items: every bin slice cut into chunks of kAdjChunk rows (the
+  // batch's items and, for plans with enough of them, the single-plan ones);
+  // a plan that would give fewer than kAdjTargetChunks such chunks also gets
+  // a second cut with shorter chunks (a power of two, at least kAdjChunkMin)
+  // for single-plan applies, so that even one right-hand side spreads over
+  // enough warps
+  std::vector<int64_t> twidths(gbase, 0);
+  for (const auto& tc : tcost) twidths[tc.second] = tc.first;
+  auto make_chunks = [&](int chunk, std::vector<int2>* titems, std::vector<int>* cbase,
+                         std::vector<int>* lens) -> int64_t {
+    std::vector<std::pair<int, int2>> items;   // (rows, (g, chunk))
+    cbase->assign(size_t(gbase) + 1, 0);
     int64_t run = 0;
     for (int64_t g = 0; g < gbase; ++g) {
-      const int64_t W = widths[g];
-      const int64_t nch = W > 0 ? (W + kAdjChunk - 1) / kAdjChunk : 1;
-      cbase[g] = int(run);
+      const int64_t W = twidths[g];
+      const int64_t nch = W > 0 ? (W + chunk - 1) / chunk : 1;
+      (*cbase)[g] = int(run);
       for (int64_t c = 0; c < nch; ++c)
-        items.push_back({int(std::min<int64_t>(kAdjChunk, std::max<int64_t>(0, W - c * kAdjChunk))),
-                         int2{int(g), int(c)}});
+        items.push_back({int(std::min<int64_t>(chunk, std::max<int64_t>(0, W - c * chunk))), int2{int(g), int(c)}});
       run += nch;
     }
-    cbase[gbase] = int(run);
-    p->total_chunks = run;
-  }
-  std::stable_sort(items.begin(), items.end(),
-                   [](const std::pair<int, int2>& a, const std::pair<int, int2>& b) { return a.first > b.first; });
-  std::vector<int2> titems(items.size());
-  p->item_len.resize(items.size());
-  for (size_t k = 0; k < items.size(); ++k) {
-    titems[k] = items[k].second;
-    p->item_len[k] = items[k].first;
-  }
+    (*cbase)[gbase] = int(run);
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<int, int2>& a, const std::pair<int, int2>& b) { return a.first > b.first; });
+    titems->resize(items.size());
+    lens->resize(items.size());
+    for (size_t k = 0; k < items.size(); ++k) {
+      (*titems)[k] = items[k].second;
+      (*lens)[k] = items[k].first;
+    }
+    return run;
+  };
+  std::vector<int2> titems;
+  std::vector<int> cbase;
+  p->total_chunks = make_chunks(kAdjChunk, &titems, &cbase, &p->item_len);
   p->item_host = titems;
   p->slice_cost = fcost;
   XC_TRY(upload(p, titems, &p->t_items));
   XC_TRY(upload(p, cbase, &p->t_cbase));
+  {
+    int64_t rows = 0;
+    for (int64_t W : twidths) rows += W;
+    int chunk = kAdjChunk;
+    while (chunk > kAdjChunkMin && rows / chunk < kAdjTargetChunks) chunk /= 2;
+    p->s_chunk = chunk;
+    if (chunk == kAdjChunk) {
+      p->s_items = p->t_items;
+      p->s_cbase = p->t_cbase;
+      p->s_total_chunks = p->total_chunks;
+    } else {
+      std::vector<int2> si;
+      std::vector<int> sc, sl;
+      p->s_total_chunks = make_chunks(chunk, &si, &sc, &sl);
+      XC_TRY(upload(p, si, &p->s_items));
+      XC_TRY(upload(p, sc, &p->s_cbase));
+    }
+  }
   {
     int64_t gb = 0;
     for (int i = 0; i < nb; ++i) {

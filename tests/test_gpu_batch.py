@@ -63,8 +63,12 @@ def test_batch_matches_single_plan_applies(xc, precision, nplans):
             b.apply(adjoint=True)          # reads y, writes x
             torch.cuda.synchronize()
             assert b.status() == xc.XC_OK
+            # single-plan adjoints of small plans cut their bands into shorter
+            # chunks than the batch (more warps per right-hand side), which
+            # changes the summation order: equal to rounding, not bit for bit
+            tol = 1e-12 if precision == "fp64" else 2e-6
             for p, x, y in zip(plans, xs, y_saved):
-                assert rel(x, p.apply_adjoint(y)) <= 1e-12
+                assert rel(x, p.apply_adjoint(y)) <= tol
     finally:
         close_all(plans)
 
