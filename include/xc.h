@@ -52,11 +52,14 @@ typedef enum {
   XC_LEGENDRE    = 1,  /* P_m(x); block method (Section 3, alpha = beta = 0) */
   XC_JACOBI      = 2,  /* P_m^{(alpha,beta)}(x); block method (Section 3) */
   XC_LAGUERRE_FN = 3,  /* l_m(x) = exp(-x/2) L_m(x) (Section 4); block method */
-  XC_HERMITE_FN  = 4   /* orthonormal Hermite functions psi_m(x); block method */
+  XC_HERMITE_FN  = 4,  /* orthonormal Hermite functions psi_m(x); block method */
+  XC_SINE        = 5,  /* sin(m theta_n), theta_n = arccos x_n (Section 2.2 names the sin and exp
+                          matrices beside eq. (cheb_matrix)); two-sided extension */
+  XC_COS_POWER   = 6   /* cos^s(m theta_n), s = xc_params.power (eq. (cosd2)); two-sided extension */
 } xc_family;
 
 /* node sets */
-#define XC_NODES_GAUSS 0   /* Gauss nodes of the family (Chebyshev: x_n = cos((2n+1)pi/(2N))) */
+#define XC_NODES_GAUSS 0   /* Gauss nodes of the family (Chebyshev, sine, cos^s: x_n = cos((2n+1)pi/(2N))) */
 #define XC_NODES_USER  1   /* caller-supplied nodes (user_nodes) */
 
 /* normalisation */
@@ -74,8 +77,8 @@ typedef enum {
                                    Single-plan applies only (not xc_batch_*, not xc_apply_noalloc). */
 
 /* extension scheme */
-#define XC_SCHEME_AUTO      0   /* two-sided for XC_CHEBYSHEV_T, block method otherwise */
-#define XC_SCHEME_TWO_SIDED 1   /* Algorithms 1-2; Chebyshev family only */
+#define XC_SCHEME_AUTO      0   /* two-sided for the trigonometric families, block method otherwise */
+#define XC_SCHEME_TWO_SIDED 1   /* Algorithms 1-2; trigonometric families (Chebyshev, sine, cos^s) only */
 #define XC_SCHEME_BLOCKS    2   /* Algorithms 3-4 */
 
 /* precomputation of the compressed rows */
@@ -88,13 +91,15 @@ typedef struct {
   double alpha, beta;        /* Jacobi parameters (> -1); ignored by the other families */
   int nodes;                 /* XC_NODES_GAUSS | XC_NODES_USER */
   const double* user_nodes;  /* host, N entries, copied at create; used when nodes == XC_NODES_USER */
-  int normalise;             /* XC_RAW | XC_ORTHONORMAL (orthonormal needs Gauss nodes) */
+  int normalise;             /* XC_RAW | XC_ORTHONORMAL (orthonormal needs Gauss nodes and a
+                                polynomial family: not XC_SINE / XC_COS_POWER) */
   double eps2;               /* window floor of the first real component; 0 => 1e-3 (FP64) or 1e-1 (FP32) */
   double eps_window;         /* eps that fixes zeta when eps == 0; 0 => 1e-14 */
   int precision;             /* XC_FP64 | XC_FP32 | XC_FP32_COMPENSATED | XC_FP64_PAIR */
   int scheme;                /* XC_SCHEME_* */
   int tail_max;              /* blocks are added while m_i > tail_max; 0 => 20 */
   int precompute;            /* XC_PRECOMPUTE_* */
+  int power;                 /* s of XC_COS_POWER, 1..16; 0 => 2 */
 } xc_params;
 
 /* Fill *p with the defaults listed above (Gauss nodes, raw, FP64, auto scheme). */

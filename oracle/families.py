@@ -19,8 +19,13 @@ import numpy as np
 import scipy.linalg
 from scipy.special import gammaln
 
-FAMILIES = ("chebyshev", "legendre", "jacobi", "laguerre", "hermite")
+FAMILIES = ("chebyshev", "legendre", "jacobi", "laguerre", "hermite", "sine", "cospow")
 ONE_SIDED = ("legendre", "jacobi", "laguerre", "hermite")
+# trigonometric families, all at the angles theta_n of the Chebyshev-Gauss
+# points: cos(m theta_n) (Chebyshev T), sin(m theta_n) (Section 2.2 names the
+# sin and exp matrices beside eq. (cheb_matrix)) and cos^s(m theta_n)
+# (eq. (cosd2)); all are defined for negative m and take the two-sided extension
+TRIG = ("chebyshev", "sine", "cospow")
 
 
 @dataclass
@@ -36,6 +41,7 @@ class Spec:
     beta: float = 0.0
     cheb_num: np.ndarray | None = None
     cheb_den: int = 0
+    power: int = 2            # s of the cos^s family
 
 
 # ------------------------------------------------------------------ recurrences
@@ -176,17 +182,21 @@ def values(spec: Spec, m_lo: int, m_hi: int, rows=None) -> np.ndarray:
     """
     x = spec.x if rows is None else spec.x[np.asarray(rows)]
     fam = spec.family
-    if fam == "chebyshev":
+    if fam in TRIG:
         m = np.arange(m_lo, m_hi, dtype=np.int64)
         if spec.cheb_num is not None:
             num = spec.cheb_num if rows is None else spec.cheb_num[np.asarray(rows)]
             period = 2 * spec.cheb_den  # angle = pi * num * m / den, period 2*den in num*m
             k = np.mod(np.outer(num.astype(np.int64), m), period)
-            return np.cos(np.pi * k / spec.cheb_den)
-        theta = np.arccos(np.clip(x, -1.0, 1.0))
-        return np.cos(np.outer(theta, m.astype(np.float64)))
+            ang = np.pi * k / spec.cheb_den
+        else:
+            ang = np.outer(np.arccos(np.clip(x, -1.0, 1.0)), m.astype(np.float64))
+        if fam == "sine":
+            return np.sin(ang)
+        c = np.cos(ang)
+        return c ** spec.power if fam == "cospow" else c
     if m_lo < 0:
-        raise ValueError("only the Chebyshev family extends to negative degrees")
+        raise ValueError("only the trigonometric families extend to negative degrees")
     if fam == "legendre":
         full = _legendre_rows(x, m_hi)
     elif fam == "jacobi":
@@ -298,7 +308,7 @@ def gauss_nodes(family: str, N: int, alpha: float = 0.0, beta: float = 0.0) -> n
     recurrence value (Section 5.2 uses Gauss-Jacobi quadrature nodes; Laguerre
     and Hermite function nodes are the Gauss-Laguerre / Gauss-Hermite nodes).
     """
-    if family == "chebyshev":
+    if family in TRIG:
         n = np.arange(N)
         return np.cos((2 * n + 1) * np.pi / (2 * N))
     diag, off = _jacobi_matrix(family, N, alpha, beta)
@@ -308,14 +318,15 @@ def gauss_nodes(family: str, N: int, alpha: float = 0.0, beta: float = 0.0) -> n
     return np.sort(x)
 
 
-def make_spec(family: str, N: int, alpha: float = 0.0, beta: float = 0.0, x=None) -> Spec:
-    """A family at its Gauss nodes (or at user nodes x)."""
+def make_spec(family: str, N: int, alpha: float = 0.0, beta: float = 0.0, x=None, power: int = 2) -> Spec:
+    """A family at its Gauss nodes (or at user nodes x); `power` is the s of
+    the cos^s family."""
     if x is not None:
-        return Spec(family, N, np.asarray(x, dtype=np.float64), alpha, beta)
-    if family == "chebyshev":
+        return Spec(family, N, np.asarray(x, dtype=np.float64), alpha, beta, power=power)
+    if family in TRIG:
         n = np.arange(N, dtype=np.int64)
         return Spec(family, N, gauss_nodes(family, N), alpha, beta,
-                    cheb_num=2 * n + 1, cheb_den=2 * N)
+                    cheb_num=2 * n + 1, cheb_den=2 * N, power=power)
     return Spec(family, N, gauss_nodes(family, N, alpha, beta), alpha, beta)
 
 
@@ -381,6 +392,8 @@ def scalings(spec: Spec, normalise: bool):
     N = spec.N
     if not normalise:
         return np.ones(N), np.ones(N)
+    if spec.family in ("sine", "cospow"):
+        raise ValueError("the orthonormal variant is defined for the orthogonal polynomial families")
     return np.sqrt(quadrature_weights(spec)), 1.0 / np.sqrt(column_norms_sq(spec, N))
 
 

@@ -167,7 +167,7 @@ def build(spec, eps: float, eps2: float | None = None, precision: str = "fp64",
     if eps2 is None:
         eps2 = default_eps2(precision)
     if two_sided is None:
-        two_sided = spec.family == "chebyshev"
+        two_sided = spec.family in fam_mod.TRIG
     N = spec.N
     sch = special.schedule(N, eps, eps2, two_sided, eps_window, tail_max)
     rows = np.arange(N) if rows is None else np.asarray(rows)

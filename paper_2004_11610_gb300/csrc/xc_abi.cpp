@@ -131,7 +131,8 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
   xc_params prm;
   if (params) prm = *params;
   else xc_params_default(&prm);
-  if (family < XC_CHEBYSHEV_T || family > XC_HERMITE_FN) return fail(XC_ERR_ARG, "unknown family");
+  if (family < XC_CHEBYSHEV_T || family > XC_COS_POWER) return fail(XC_ERR_ARG, "unknown family");
+  const bool trig = family == XC_CHEBYSHEV_T || family == XC_SINE || family == XC_COS_POWER;
   if (N < 2 || N > (int64_t(1) << 20)) return fail(XC_ERR_ARG, "N must lie in [2, 2^20]");
   if (!(eps >= 0.0) || !(eps < 1.0)) return fail(XC_ERR_ARG, "eps must lie in [0, 1)");
   if (prm.precision < XC_FP64 || prm.precision > XC_FP64_PAIR) return fail(XC_ERR_ARG, "unknown precision");
@@ -142,8 +143,11 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
     return fail(XC_ERR_ARG, "the orthonormal variant needs Gauss nodes");
   if (family == XC_JACOBI && !(prm.alpha > -1.0 && prm.beta > -1.0)) return fail(XC_ERR_ARG, "Jacobi needs alpha, beta > -1");
   if (prm.scheme < XC_SCHEME_AUTO || prm.scheme > XC_SCHEME_BLOCKS) return fail(XC_ERR_ARG, "unknown scheme");
-  if (prm.scheme == XC_SCHEME_TWO_SIDED && family != XC_CHEBYSHEV_T)
-    return fail(XC_ERR_ARG, "the two-sided extension needs the Chebyshev family");
+  if (prm.scheme == XC_SCHEME_TWO_SIDED && !trig)
+    return fail(XC_ERR_ARG, "the two-sided extension needs a trigonometric family");
+  if (prm.normalise == XC_ORTHONORMAL && (family == XC_SINE || family == XC_COS_POWER))
+    return fail(XC_ERR_UNSUPPORTED, "the orthonormal variant is defined for the polynomial families");
+  if (prm.power < 0 || prm.power > 16) return fail(XC_ERR_ARG, "power must lie in [0, 16]");
   if (prm.eps2 < 0.0 || prm.eps2 >= 1.0 || prm.eps_window < 0.0 || prm.eps_window >= 1.0 || prm.tail_max < 0)
     return fail(XC_ERR_ARG, "eps2 / eps_window / tail_max out of range");
   if (prm.precompute != XC_PRECOMPUTE_AUTO && prm.precompute != XC_PRECOMPUTE_FFT)
@@ -158,8 +162,8 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
   if (family != XC_JACOBI) p->params.alpha = p->params.beta = 0.0;   // only the Jacobi family has (alpha, beta)
   p->precision = prm.precision;
   p->normalise = prm.normalise;
-  p->scheme = prm.scheme == XC_SCHEME_AUTO ? (family == XC_CHEBYSHEV_T ? XC_SCHEME_TWO_SIDED : XC_SCHEME_BLOCKS)
-                                           : prm.scheme;
+  p->scheme = prm.scheme == XC_SCHEME_AUTO ? (trig ? XC_SCHEME_TWO_SIDED : XC_SCHEME_BLOCKS) : prm.scheme;
+  if (family == XC_COS_POWER && p->params.power == 0) p->params.power = 2;
   p->eps = eps;
   p->eps2 = prm.eps2 > 0 ? prm.eps2 : (p->io64() ? 1e-3 : 1e-1);
   if (prm.nodes == XC_NODES_USER) p->nodes_host.assign(prm.user_nodes, prm.user_nodes + N);

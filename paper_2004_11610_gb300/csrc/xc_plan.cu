@@ -28,8 +28,13 @@ struct GenParams {
   int64_t N;
   double alpha, beta;
   const double* x;      // nodes
-  int cheb_exact;       // Chebyshev at x_n = cos((2n+1) pi / (2N)): exact angles
+  int cheb_exact;       // trigonometric family at x_n = cos((2n+1) pi / (2N)): exact angles
+  int power;            // s of the cos^s family
 };
+
+__host__ __device__ __forceinline__ bool is_trig(int family) {
+  return family == XC_CHEBYSHEV_T || family == XC_SINE || family == XC_COS_POWER;
+}
 
 // exp(-a) for a >= 0 as mant * 2^expo, with the argument split
 // a = q ln2 - r (q integer, ln2 = hi + lo, q * hi exact) so that the result
@@ -53,19 +58,38 @@ __device__ void exp_neg_split(double a_hi, double a_lo, double* mant, int* expo)
 template <class F>
 __device__ void gen_values(const GenParams& g, int64_t n, int64_t m_lo, int64_t m_hi, F emit) {
   const double x = g.x[n];
-  if (g.family == XC_CHEBYSHEV_T) {
+  if (is_trig(g.family)) {
+    // cos(m theta), sin(m theta) or cos^s(m theta) of the row's angle
+    auto finish = [&](double c, double sn) {
+      if (g.family == XC_SINE) return sn;
+      if (g.family == XC_COS_POWER) {
+        double v = c;
+        for (int i = 1; i < g.power; ++i) v *= c;
+        return v;
+      }
+      return c;
+    };
     if (g.cheb_exact) {
       // angle = pi m (2n+1) / (2N); period 4N in m (2n+1)
       const int64_t num = 2 * n + 1, per = 4 * g.N;
       for (int64_t m = m_lo; m < m_hi; ++m) {
         int64_t k = (m % per) * num % per;
         if (k < 0) k += per;
-        if (k > per / 2) k = per - k;                  // cos is even: k in [0, 2N]
-        emit(m, cospi(double(k) / double(2 * g.N)));
+        double sign = 1.0;
+        if (k > per / 2) {                             // angle in (pi, 2 pi): cos even, sin odd
+          k = per - k;
+          sign = -1.0;
+        }
+        const double a = double(k) / double(2 * g.N);  // in [0, 1]
+        emit(m, finish(cospi(a), g.family == XC_SINE ? sign * sinpi(a) : 0.0));
       }
     } else {
       const double th = acos(fmin(1.0, fmax(-1.0, x)));
-      for (int64_t m = m_lo; m < m_hi; ++m) emit(m, cos(double(m) * th));
+      for (int64_t m = m_lo; m < m_hi; ++m) {
+        double sn, c;
+        sincos(double(m) * th, &sn, &c);
+        emit(m, finish(c, sn));
+      }
     }
     return;
   }
@@ -690,7 +714,7 @@ __global__ void dense_kernel(GenParams g, const T* rowscale, const T* colscale, 
 // The plain N x N matrix with the plan's normalisation (comparison path).
 int dense_matrix_device(const Plan* p, void* A, int64_t lda, cudaStream_t s) {
   GenParams g{p->family, p->N, p->params.alpha, p->params.beta, p->nodes_dev,
-              p->family == XC_CHEBYSHEV_T && p->params.nodes == XC_NODES_GAUSS};
+              is_trig(p->family) && p->params.nodes == XC_NODES_GAUSS, p->params.power};
   const unsigned grid = unsigned((p->N + 31) / 32);
   if (p->io64())
     dense_kernel<double><<<grid, 32, 0, s>>>(g, static_cast<const double*>(p->rowscale),
@@ -1088,7 +1112,7 @@ int build_plan_device(Plan* p) {
   const bool user = p->params.nodes == XC_NODES_USER;
   if (user) {
     XC_CUDA(cudaMemcpy(p->nodes_dev, p->nodes_host.data(), size_t(N) * sizeof(double), cudaMemcpyHostToDevice));
-  } else if (p->family == XC_CHEBYSHEV_T) {
+  } else if (is_trig(p->family)) {
     cheb_nodes_kernel<<<gN, 128>>>(N, p->nodes_dev);
   } else {
     std::vector<double> d, e2;
@@ -1113,8 +1137,8 @@ int build_plan_device(Plan* p) {
   p->nodes_host.resize(N);
   XC_CUDA(cudaMemcpy(p->nodes_host.data(), p->nodes_dev, size_t(N) * sizeof(double), cudaMemcpyDeviceToHost));
 
-  GenParams g{p->family, N, p->params.alpha, p->params.beta, p->nodes_dev,
-              p->family == XC_CHEBYSHEV_T && !user};
+  GenParams g{p->family, N, p->params.alpha, p->params.beta, p->nodes_dev, is_trig(p->family) && !user,
+              p->params.power};
   const bool fp64 = p->io64();
   if (p->normalise == XC_ORTHONORMAL) {
     DevBuf lam;

@@ -20,7 +20,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 # ------------------------------------------------------------------ constants
 XC_OK, XC_ERR_ARG, XC_ERR_ALLOC, XC_ERR_CUDA, XC_ERR_TIMEOUT, XC_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
-FAMILY = {"chebyshev": 0, "legendre": 1, "jacobi": 2, "laguerre": 3, "hermite": 4}
+FAMILY = {"chebyshev": 0, "legendre": 1, "jacobi": 2, "laguerre": 3, "hermite": 4, "sine": 5, "cospow": 6}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32c": 2, "fp64pair": 3}
 SCHEME = {"auto": 0, "two_sided": 1, "blocks": 2}
 XC_MAX_BLOCKS = 16
@@ -30,7 +30,8 @@ class xc_params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("nodes", ctypes.c_int),
                 ("user_nodes", ctypes.POINTER(ctypes.c_double)), ("normalise", ctypes.c_int),
                 ("eps2", ctypes.c_double), ("eps_window", ctypes.c_double), ("precision", ctypes.c_int),
-                ("scheme", ctypes.c_int), ("tail_max", ctypes.c_int), ("precompute", ctypes.c_int)]
+                ("scheme", ctypes.c_int), ("tail_max", ctypes.c_int), ("precompute", ctypes.c_int),
+                ("power", ctypes.c_int)]
 
 
 _I64x = ctypes.c_int64 * XC_MAX_BLOCKS
@@ -128,7 +129,8 @@ class Plan:
 
     def __init__(self, family: str, N: int, eps: float, precision: str = "fp64", alpha: float = 0.0,
                  beta: float = 0.0, nodes=None, normalise: bool = False, eps2: float = 0.0,
-                 eps_window: float = 0.0, scheme: str = "auto", tail_max: int = 0, precompute: str = "auto"):
+                 eps_window: float = 0.0, scheme: str = "auto", tail_max: int = 0, precompute: str = "auto",
+                 power: int = 0):
         p = xc_params()
         _lib.xc_params_default(ctypes.byref(p))
         p.alpha, p.beta = float(alpha), float(beta)
@@ -146,6 +148,7 @@ class Plan:
         p.scheme = SCHEME[scheme]
         p.tail_max = int(tail_max)
         p.precompute = {"auto": 0, "fft": 1}[precompute]
+        p.power = int(power)
         h = _P()
         _check(_lib.xc_plan_create(ctypes.byref(h), FAMILY[family], ctypes.byref(p), int(N), float(eps)),
                "xc_plan_create")

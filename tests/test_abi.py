@@ -69,7 +69,7 @@ def test_invalid_arguments_are_rejected_on_the_host(xc):
 
 def test_structure_layouts_match_the_header(xc):
     # offsets fixed by the C layout of include/xc.h (LP64)
-    assert ctypes.sizeof(xc.xc_params) == 72   # the precompute int fills the former tail padding
+    assert ctypes.sizeof(xc.xc_params) == 80
     assert xc.xc_plan_stats.L.offset == 56
     assert ctypes.sizeof(xc.xc_plan_stats) == 56 + 7 * 8 * 16 + 24 + 8
 

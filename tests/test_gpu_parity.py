@@ -284,3 +284,29 @@ def test_invalid_calls_return_errors(xc):
                                 st) == xc.XC_ERR_ARG
         assert xc._lib.xc_apply(plan.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), 0, 64,
                                 st) == xc.XC_OK
+
+
+@pytest.mark.parametrize("fam,N,eps,power,precision", [
+    ("sine", 512, 1e-12, 0, "fp64"), ("sine", 1001, 1e-8, 0, "fp64"), ("cospow", 600, 1e-10, 2, "fp64"),
+    ("cospow", 400, 1e-10, 3, "fp64"), ("sine", 700, 1e-7, 0, "fp32"), ("cospow", 500, 1e-7, 4, "fp32c"),
+    ("sine", 2048, 1e-12, 0, "fp64pair"),
+])
+def test_sine_and_cos_power_families_match_oracle(xc, fam, N, eps, power, precision):
+    """The sin(m theta_n) and cos^s(m theta_n) matrices (Section 2.2, eq.
+    (cosd2)) through the same two-sided method as the Chebyshev family."""
+    eps2 = 1e-3 if precision in ("fp64", "fp64pair") else 3e-2
+    ora = M.build(F.make_spec(fam, N, power=power or 2), eps, eps2=eps2)
+    with xc.Plan(fam, N, eps, precision=precision, eps2=eps2, power=power) as plan:
+        check_schedule(ora, plan)
+        X = inputs.uniform_pm1(N, 3, 51)
+        y, y_ref = run_both(xc, plan, ora, X)
+        xa, xa_ref = run_both(xc, plan, ora, X, adjoint=True)
+        if precision in ("fp64", "fp64pair"):
+            tol = fp64_tol(ora, eps)
+            assert max_rel(y, y_ref) <= tol and max_rel(xa, xa_ref) <= tol
+        else:
+            assert M.rel_l2(y, y_ref) <= max(10 * eps, 1e-5)
+            assert M.rel_l2(xa, xa_ref) <= max(10 * eps, 1e-5)
+        # the method approximates the plain product to about eps1 / eps2
+        y_d = M.dense_apply(ora.spec, X)
+        assert M.rel_l2(y, y_d) <= max(10 * eps / eps2, 1e-5)

@@ -177,3 +177,37 @@ def test_orthonormal_matrix_is_orthogonal(fam, N):
     Q = F.dense_matrix(sp, normalise=True)
     err = np.abs(Q.T @ Q - np.eye(N)).max()
     assert err < (5e-11 if fam == "laguerre" else 2e-12)
+
+
+# ------------------------------------------------- sine and cos^s families
+
+@pytest.mark.parametrize("N", [8, 63, 256])
+def test_sine_matvec_is_a_dst(N):
+    """sum_m x_m sin(m theta_n), theta_n = (2n+1) pi / (2N), m < N, is half of
+    scipy's DST-III of (x_1, ..., x_{N-1}, 0)."""
+    sp = F.make_spec("sine", N)
+    x = np.random.default_rng(N).standard_normal(N)
+    y = F.dense_matrix(sp) @ x
+    xs = np.concatenate([x[1:], [0.0]])
+    assert np.allclose(y, scipy.fft.dst(xs, type=3) / 2, rtol=0, atol=1e-12 * np.abs(x).sum())
+
+
+@pytest.mark.parametrize("N", [16, 100])
+def test_sine_discrete_orthogonality(N):
+    """sum_n sin(m theta_n) sin(k theta_n) = (N/2) delta_mk for 1 <= m, k < N."""
+    S = F.dense_matrix(F.make_spec("sine", N))[:, 1:]
+    assert np.abs(S.T @ S - (N / 2) * np.eye(N - 1)).max() < 1e-11 * N
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 5])
+def test_cospow_is_a_sum_of_chebyshev_matrices(s):
+    """cos^s(m theta) = 2^-s sum_k C(s, k) cos((s - 2k) m theta): the cos^s
+    matrix equals the binomial combination of Chebyshev matrices at the nodes
+    cos((s - 2k) theta_n) (generated through arccos, not the exact angles)."""
+    N = 97
+    sp = F.make_spec("cospow", N, power=s)
+    th = (2 * np.arange(N) + 1) * np.pi / (2 * N)
+    acc = np.zeros((N, N))
+    for k in range(s + 1):
+        acc += math.comb(s, k) * F.dense_matrix(F.make_spec("chebyshev", N, x=np.cos((s - 2 * k) * th)))
+    assert np.abs(F.dense_matrix(sp) - acc / 2 ** s).max() < 1e-12
