@@ -15,6 +15,7 @@
 //   adj_fft_kernel     per (block, RHS): real inverse FFT of z, W^{-1}, keep the
 //                      real components [j_lo, j_hi), discard the extra ones (eq. (Fe2))
 //   adj_tail_kernel    the first m_tail entries from the dense tail.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,13 +34,40 @@ constexpr int kFftThreads = 256;
 constexpr int kSparseWarps = 4;
 
 // ------------------------------------------------------------ forward FFT
+// (pexp: per-RHS exponents of FP32-pair plans, whose spectra go out as pairs)
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
     fwd_fft_kernel(const BlockDev* __restrict__ blocks, const T* __restrict__ x, int64_t ld,
-                   const T* __restrict__ colscale, cx<T>* __restrict__ spec, int64_t nrhs) {
+                   const T* __restrict__ colscale, cx<T>* __restrict__ spec, int64_t nrhs,
+                   const int* __restrict__ pexp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fwd_fft_body<T>(blocks[blockIdx.y], blockIdx.x, x, ld, colscale, spec, nrhs, reinterpret_cast<cx<T>*>(smem_raw),
-                  threadIdx.x, blockDim.x);
+                  threadIdx.x, blockDim.x, pexp);
+}
+
+// The same for one block whose n-point array is split over a cluster of
+// csize CTAs (rank q holds [q n/csize, (q+1) n/csize)); butterflies reach the
+// other parts through distributed shared memory, a cluster barrier separates
+// the passes.  Grid: nrhs * csize CTAs, cluster dimension (csize, 1, 1).
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads)
+    fwd_fft_cluster_kernel(const BlockDev* __restrict__ block, const T* __restrict__ x, int64_t ld,
+                           const T* __restrict__ colscale, cx<T>* __restrict__ spec, int64_t nrhs,
+                           const int* __restrict__ pexp) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int csize = int(cluster.num_blocks());
+  const int rank = int(cluster.block_rank());
+  const BlockDev& b = *block;
+  ClusterMem<T> mem;
+  mem.per = b.n / csize;
+  for (int q = 0; q < 8; ++q) mem.base[q] = q < csize ? cluster.map_shared_rank(s, q) : s;
+  cluster.sync();   // every CTA of the cluster runs before any remote access
+  fwd_fft_run<T>(b, blockIdx.x / csize, x, ld, colscale, spec, nrhs, mem, rank * int(blockDim.x) + int(threadIdx.x),
+                 csize * int(blockDim.x), [&] { cluster.sync(); }, pexp);
+  cluster.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 // ------------------------------------------------------- work distribution
@@ -169,16 +197,6 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads)
-    fwd_fft_pair_kernel(const BlockDev* __restrict__ blocks, const double* __restrict__ x, int64_t ld,
-                        const double* __restrict__ colscale, cx<double>* __restrict__ spec, int64_t nrhs,
-                        const int* __restrict__ pexp) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  fwd_fft_body<double>(blocks[blockIdx.y], blockIdx.x, x, ld, colscale, spec, nrhs,
-                       reinterpret_cast<cx<double>*>(smem_raw), threadIdx.x, blockDim.x, pexp);
-}
-
 template <int RPW>
 __global__ void __launch_bounds__(32 * kSparseWarps)
     fwd_sparse_pair_kernel(const BlockDev* __restrict__ blocks, int nblocks, int64_t N, const double* __restrict__ x,
@@ -292,6 +310,27 @@ __global__ void __launch_bounds__(kFftThreads)
                   reinterpret_cast<cx<T>*>(smem_raw), threadIdx.x, blockDim.x);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads)
+    adj_fft_cluster_kernel(const BlockDev* __restrict__ block, const cx<T>* __restrict__ part,
+                           const int* __restrict__ cbase, int64_t nrhs, T* __restrict__ x, int64_t ld,
+                           const T* __restrict__ colscale) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int csize = int(cluster.num_blocks());
+  const int rank = int(cluster.block_rank());
+  const BlockDev& b = *block;
+  ClusterMem<T> mem;
+  mem.per = b.n / csize;
+  for (int q = 0; q < 8; ++q) mem.base[q] = q < csize ? cluster.map_shared_rank(s, q) : s;
+  cluster.sync();
+  adj_fft_run<T>(b, blockIdx.x / csize, part, cbase, nrhs, x, ld, colscale, mem,
+                 rank * int(blockDim.x) + int(threadIdx.x), csize * int(blockDim.x), [&] { cluster.sync(); });
+  cluster.sync();
+}
+
 // ------------------------------------------------------------ adjoint tail
 // Warp per (m, RHS).
 template <typename T, bool COMP>
@@ -321,29 +360,74 @@ int supergroup(const void* fn, int64_t units, int64_t ngroups) {
 
 // ------------------------------------------------------------------ launch
 template <typename T>
-int launch_fft(Plan* p, bool forward, const void* in, void* out, int64_t nrhs, int64_t ld, cudaStream_t st) {
-  const size_t smem = size_t(p->max_n) * sizeof(cx<T>);
-  const void* fn = forward ? reinterpret_cast<const void*>(fwd_fft_kernel<T>)
-                           : reinterpret_cast<const void*>(adj_fft_kernel<T>);
-  static thread_local size_t configured[2] = {0, 0};   // per kernel, per host thread
-  size_t& done = configured[forward ? 0 : 1];
+int set_dynamic_smem(const void* fn, size_t smem) {
+  static thread_local std::unordered_map<const void*, size_t> configured;
+  size_t& done = configured[fn];
   if (smem > 48 * 1024 && smem > done) {
     XC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     done = smem;
   }
-  dim3 grid(unsigned(nrhs), unsigned(p->blocks.size()));
+  return XC_OK;
+}
+
+// The FFTs of all blocks (forward: input -> spectra; adjoint: chunk partials
+// -> output).  One launch over (RHS, block) when every block fits one CTA;
+// otherwise one launch per block, clusters for the long ones.
+template <typename T>
+int launch_fft(Plan* p, bool forward, const void* in, void* out, int64_t nrhs, int64_t ld, cudaStream_t st,
+               const int* pexp = nullptr) {
   const BlockDev* bd = static_cast<const BlockDev*>(p->scratch_desc);
   const int kid = forward ? K_FWD_FFT : K_ADJ_FFT;
+  const T* cs = static_cast<const T*>(p->colscale);
+  auto one_cta = [&](const BlockDev* d, unsigned nb, size_t smem) -> int {
+    dim3 grid(unsigned(nrhs), nb);
+    if (forward) {
+      XC_TRY(set_dynamic_smem<T>(reinterpret_cast<const void*>(fwd_fft_kernel<T>), smem));
+      fwd_fft_kernel<T><<<grid, kFftThreads, smem, st>>>(d, static_cast<const T*>(in), ld, cs,
+                                                          static_cast<cx<T>*>(out), nrhs, pexp);
+    } else {
+      XC_TRY(set_dynamic_smem<T>(reinterpret_cast<const void*>(adj_fft_kernel<T>), smem));
+      adj_fft_kernel<T><<<grid, kFftThreads, smem, st>>>(d, static_cast<const cx<T>*>(in), p->s_cbase, nrhs,
+                                                          static_cast<T*>(out), ld, cs);
+    }
+    XC_CUDA(cudaGetLastError());
+    return XC_OK;
+  };
   launch_begin(p, kid, st);
-  if (forward)
-    fwd_fft_kernel<T><<<grid, kFftThreads, smem, st>>>(bd, static_cast<const T*>(in), ld,
-                                                        static_cast<const T*>(p->colscale),
-                                                        static_cast<cx<T>*>(out), nrhs);
-  else
-    adj_fft_kernel<T><<<grid, kFftThreads, smem, st>>>(bd, static_cast<const cx<T>*>(in), p->s_cbase, nrhs,
-                                                        static_cast<T*>(out), ld, static_cast<const T*>(p->colscale));
+  if (p->max_csize == 1) {
+    XC_TRY(one_cta(bd, unsigned(p->blocks.size()), size_t(p->max_n) * sizeof(cx<T>)));
+  } else {
+    for (size_t i = 0; i < p->blocks.size(); ++i) {
+      const BlockDev& b = p->blocks[i];
+      if (b.a_csize == 1) {
+        XC_TRY(one_cta(bd + i, 1u, size_t(b.n) * sizeof(cx<T>)));
+        continue;
+      }
+      const size_t smem = size_t(b.n / b.a_csize) * sizeof(cx<T>);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(unsigned(nrhs * b.a_csize));
+      cfg.blockDim = dim3(kFftThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = unsigned(b.a_csize);
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (forward) {
+        XC_TRY(set_dynamic_smem<T>(reinterpret_cast<const void*>(fwd_fft_cluster_kernel<T>), smem));
+        XC_CUDA(cudaLaunchKernelEx(&cfg, fwd_fft_cluster_kernel<T>, bd + i, static_cast<const T*>(in), ld, cs,
+                                   static_cast<cx<T>*>(out), nrhs, pexp));
+      } else {
+        XC_TRY(set_dynamic_smem<T>(reinterpret_cast<const void*>(adj_fft_cluster_kernel<T>), smem));
+        XC_CUDA(cudaLaunchKernelEx(&cfg, adj_fft_cluster_kernel<T>, bd + i, static_cast<const cx<T>*>(in),
+                                   static_cast<const int*>(p->s_cbase), nrhs, static_cast<T*>(out), ld, cs));
+      }
+    }
+  }
   launch_end(p, kid, st);
-  XC_CUDA(cudaGetLastError());
   return XC_OK;
 }
 
@@ -551,22 +635,7 @@ int apply_pair(Plan* p, const void* xv, void* yv, int64_t nrhs, int64_t ld, cuda
   pair_scale_kernel<<<unsigned(nrhs), 256, 0, st>>>(x, ld, p->N, nullptr, pexp, nullptr);
   launch_end(p, K_PAIR_SCALE, st);
   XC_CUDA(cudaGetLastError());
-  if (!p->blocks.empty()) {
-    const size_t smem = size_t(p->max_n) * sizeof(cx<double>);
-    static thread_local size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-      XC_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(fwd_fft_pair_kernel<double>),
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-      configured = smem;
-    }
-    dim3 grid(unsigned(nrhs), unsigned(p->blocks.size()));
-    launch_begin(p, K_FWD_FFT, st);
-    fwd_fft_pair_kernel<double><<<grid, kFftThreads, smem, st>>>(static_cast<const BlockDev*>(p->scratch_desc), x, ld,
-                                                                 static_cast<const double*>(p->colscale),
-                                                                 static_cast<cx<double>*>(p->scratch), nrhs, pexp);
-    launch_end(p, K_FWD_FFT, st);
-    XC_CUDA(cudaGetLastError());
-  }
+  if (!p->blocks.empty()) XC_TRY(launch_fft<double>(p, true, x, p->scratch, nrhs, ld, st, pexp));
   switch (choose_rpw(8, p->fwd_chunked ? p->total_units : p->nslices, nrhs)) {
     case 8: return launch_pair_fwd_rpw<8>(p, x, y, nrhs, ld, st);
     case 4: return launch_pair_fwd_rpw<4>(p, x, y, nrhs, ld, st);
@@ -671,7 +740,7 @@ int apply_noalloc_impl(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld
     count_launch();
     fwd_fft_kernel<T><<<grid, kFftThreads, smem, st>>>(bd, static_cast<const T*>(x), ld,
                                                         static_cast<const T*>(p->colscale),
-                                                        static_cast<cx<T>*>(spec), nrhs);
+                                                        static_cast<cx<T>*>(spec), nrhs, nullptr);
     XC_CUDA(cudaGetLastError());
   }
   constexpr int RPW = 8;
@@ -698,6 +767,7 @@ int launch_apply_noalloc(Plan* p, const void* x, void* y, int64_t nrhs, int64_t 
                                         "-byte array; split the right-hand sides");
   if (p->scratch_desc == nullptr) return fail(XC_ERR_ARG, "plan has no device descriptors");
   if (p->precision == XC_FP64_PAIR) return fail(XC_ERR_UNSUPPORTED, "xc_apply_noalloc does not take XC_FP64_PAIR plans");
+  if (p->max_csize > 1) return fail(XC_ERR_UNSUPPORTED, "xc_apply_noalloc does not take plans with cluster FFTs");
   void* spec = nullptr;
   XC_TRY(noalloc_scratch(&spec));
   switch (p->precision) {

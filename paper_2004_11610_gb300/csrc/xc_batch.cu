@@ -460,6 +460,10 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans) {
       delete b;
       return fail(XC_ERR_ARG, "plan " + std::to_string(i) + " is NULL");
     }
+    if (p->max_csize > 1) {
+      delete b;
+      return fail(XC_ERR_UNSUPPORTED, "plan " + std::to_string(i) + " has blocks whose FFT needs a CTA cluster");
+    }
     if (p->precision == XC_FP64_PAIR) {
       delete b;
       return fail(XC_ERR_UNSUPPORTED, "batches take XC_FP64, XC_FP32 or XC_FP32_COMPENSATED plans");

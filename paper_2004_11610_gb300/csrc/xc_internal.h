@@ -59,6 +59,7 @@ int make_schedule(int64_t N, double eps, double eps2, bool two_sided, double eps
 // pointers are untyped; the kernels cast them to the plan's precision.
 struct BlockDev {
   int L, n, H;               // FFT length, n = L/2 complex points, H = n + 1 bins
+  int a_csize;               // CTAs sharing the apply FFT (1, or a cluster of 2..8 for long blocks)
   int off, j_lo, j_hi;       // extended column j <-> matrix column j - off; input in [j_lo, j_hi)
   int p;                     // radix passes
   int radix[kMaxPasses];
@@ -138,7 +139,8 @@ struct Plan {
   int64_t nslices = 0, total_tslices = 0;
   unsigned* counters = nullptr;        // [4]: {next, done} for the forward and the adjoint sparse kernel
   int64_t spec_per_rhs = 0;            // complex elements of all blocks' spectra per RHS
-  int64_t max_n = 0;                   // largest n over blocks (shared memory of the FFTs)
+  int64_t max_n = 0;                   // largest n of a block whose apply FFT runs in one CTA
+  int max_csize = 1;                   // largest apply cluster of any block                   // largest n over blocks (shared memory of the FFTs)
   int64_t matrix_bytes = 0, adjoint_bytes = 0;
   // device copy of `blocks` (read by the kernels), scratch spectra, host-path staging
   void* scratch_desc = nullptr;

@@ -148,10 +148,13 @@ __device__ __forceinline__ void fwd_band(const cx<T>* __restrict__ base, int lan
 // ------------------------------------------------------------ forward FFT
 // With `pair_exp` (FP64 plans whose band products run in FP32 pairs), the
 // spectrum is written as pairs (see PairCx) scaled by 2^-pair_exp[r].
-template <typename T>
-__device__ void fwd_fft_body(const BlockDev& b, int64_t r, const T* __restrict__ x, int64_t ld,
-                             const T* __restrict__ colscale, cx<T>* __restrict__ spec, int64_t nrhs, cx<T>* s,
-                             int tid, int nthreads, const int* __restrict__ pair_exp = nullptr) {
+// `mem` is this CTA's shared memory (LocalMem) or a cluster's distributed
+// shared memory (ClusterMem) for blocks too long for one CTA; `sync` is the
+// matching barrier; tid / nthreads count over all CTAs that share the array.
+template <typename T, class M, class Sync>
+__device__ void fwd_fft_run(const BlockDev& b, int64_t r, const T* __restrict__ x, int64_t ld,
+                            const T* __restrict__ colscale, cx<T>* __restrict__ spec, int64_t nrhs, const M& mem,
+                            int tid, int nthreads, Sync sync, const int* __restrict__ pair_exp) {
   const int n = b.n, j_lo = b.j_lo, j_hi = b.j_hi, off = b.off;
   const T* __restrict__ invw = static_cast<const T*>(b.invw);
   const int* __restrict__ perm = b.perm;
@@ -170,10 +173,10 @@ __device__ void fwd_fft_body(const BlockDev& b, int64_t r, const T* __restrict__
       if (colscale) v *= colscale[j1 - off];
       u1 = v * invw[j1];
     }
-    s[perm[j]] = cx<T>{u0, u1};
+    mem.at(perm[j]) = cx<T>{u0, u1};
   }
-  __syncthreads();
-  fft_inplace<T>(s, n, b.p, b.radix, tw, tid, nthreads);
+  sync();
+  fft_run<T>(mem, n, b.p, b.radix, tw, tid, nthreads, sync);
   cx<T>* out = spec + b.spec_off * nrhs + r * int64_t(n + 1);
   if constexpr (sizeof(T) == 8) {
     if (pair_exp) {
@@ -181,7 +184,7 @@ __device__ void fwd_fft_body(const BlockDev& b, int64_t r, const T* __restrict__
       PairCx* po = reinterpret_cast<PairCx*>(out);
       for (int k = tid; k <= n / 2; k += nthreads) {
         cx<T> Uk, Unk;
-        r2c_split(s, n, k, tw, &Uk, &Unk);
+        r2c_split_vals(mem.at(k), mem.at(k == 0 ? 0 : n - k), k, tw, &Uk, &Unk);
         po[k] = to_pair(ldexp(Uk.re, e), ldexp(Uk.im, e));
         if (n - k != k) po[n - k] = to_pair(ldexp(Unk.re, e), ldexp(Unk.im, e));
       }
@@ -190,10 +193,18 @@ __device__ void fwd_fft_body(const BlockDev& b, int64_t r, const T* __restrict__
   }
   for (int k = tid; k <= n / 2; k += nthreads) {
     cx<T> Uk, Unk;
-    r2c_split(s, n, k, tw, &Uk, &Unk);
+    r2c_split_vals(mem.at(k), mem.at(k == 0 ? 0 : n - k), k, tw, &Uk, &Unk);
     out[k] = Uk;
     if (n - k != k) out[n - k] = Unk;
   }
+}
+
+template <typename T>
+__device__ void fwd_fft_body(const BlockDev& b, int64_t r, const T* __restrict__ x, int64_t ld,
+                             const T* __restrict__ colscale, cx<T>* __restrict__ spec, int64_t nrhs, cx<T>* s,
+                             int tid, int nthreads, const int* __restrict__ pair_exp = nullptr) {
+  fwd_fft_run<T>(b, r, x, ld, colscale, spec, nrhs, LocalMem<T>{s}, tid, nthreads, [] { __syncthreads(); },
+                 pair_exp);
 }
 
 // ------------------------------------------------------- forward sparse
@@ -551,10 +562,10 @@ __device__ __forceinline__ cx<T> gather_bin(const cx<T>* __restrict__ part, cons
   return u;
 }
 
-template <typename T>
-__device__ void adj_fft_body(const BlockDev& b, int64_t r, const cx<T>* __restrict__ part,
-                             const int* __restrict__ cbase, int64_t nrhs, T* __restrict__ x, int64_t ld,
-                             const T* __restrict__ colscale, cx<T>* s, int tid, int nthreads) {
+template <typename T, class M, class Sync>
+__device__ void adj_fft_run(const BlockDev& b, int64_t r, const cx<T>* __restrict__ part,
+                            const int* __restrict__ cbase, int64_t nrhs, T* __restrict__ x, int64_t ld,
+                            const T* __restrict__ colscale, const M& mem, int tid, int nthreads, Sync sync) {
   const int n = b.n, j_lo = b.j_lo, j_hi = b.j_hi, off = b.off;
   const int* __restrict__ perm = b.perm;
   const cx<T>* __restrict__ tw = static_cast<const cx<T>*>(b.tw);
@@ -569,14 +580,14 @@ __device__ void adj_fft_body(const BlockDev& b, int64_t r, const cx<T>* __restri
     cx<T> Zk, Znk;
     c2r_merge(Uk, Unk, k, tw, &Zk, &Znk);
     // inverse FFT as conj(FFT(conj(Z)))
-    s[perm[k]] = conj(Zk);
-    if (k != 0 && n - k != k) s[perm[n - k]] = conj(Znk);
+    mem.at(perm[k]) = conj(Zk);
+    if (k != 0 && n - k != k) mem.at(perm[n - k]) = conj(Znk);
   }
-  __syncthreads();
-  fft_inplace<T>(s, n, b.p, b.radix, tw, tid, nthreads);
+  sync();
+  fft_run<T>(mem, n, b.p, b.radix, tw, tid, nthreads, sync);
   T* __restrict__ xr = x + r * ld;
   for (int j = tid; j < n; j += nthreads) {
-    const cx<T> v = s[j];
+    const cx<T> v = mem.at(j);
     const int j0 = 2 * j, j1 = 2 * j + 1;
     if (j0 >= j_lo && j0 < j_hi) {
       T u = v.re * invw[j0];
@@ -589,6 +600,13 @@ __device__ void adj_fft_body(const BlockDev& b, int64_t r, const cx<T>* __restri
       xr[j1 - off] = u;
     }
   }
+}
+
+template <typename T>
+__device__ void adj_fft_body(const BlockDev& b, int64_t r, const cx<T>* __restrict__ part,
+                             const int* __restrict__ cbase, int64_t nrhs, T* __restrict__ x, int64_t ld,
+                             const T* __restrict__ colscale, cx<T>* s, int tid, int nthreads) {
+  adj_fft_run<T>(b, r, part, cbase, nrhs, x, ld, colscale, LocalMem<T>{s}, tid, nthreads, [] { __syncthreads(); });
 }
 
 // ------------------------------------------------------------ adjoint tail

@@ -835,10 +835,15 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
       return fail(XC_ERR_UNSUPPORTED, "block length L = " + std::to_string(b.L) +
                                           " exceeds an 8-CTA cluster FFT of the precompute");
   }
-  // the apply FFT runs in one CTA in the plan precision
-  if (size_t(n) * sizeof(cx<T>) + 1024 > size_t(optin))
+  // the apply FFT runs in one CTA in the plan precision, or for long blocks
+  // on a cluster of up to 8 CTAs that split the array (distributed shared
+  // memory)
+  b.a_csize = 0;
+  for (int cand = 1; cand <= 8 && b.a_csize == 0; ++cand)
+    if (n % cand == 0 && size_t(n / cand) * sizeof(cx<T>) + 1024 <= size_t(optin)) b.a_csize = cand;
+  if (b.a_csize == 0)
     return fail(XC_ERR_UNSUPPORTED, "block length L = " + std::to_string(b.L) +
-                                        " exceeds the single-CTA FFT of the apply in this precision");
+                                        " exceeds an 8-CTA cluster FFT of the apply in this precision");
 
   // permutation, window, twiddles
   std::vector<int> perm = digit_reversal(n, b.p, b.radix);
@@ -1163,7 +1168,8 @@ int build_plan_device(Plan* p) {
     else XC_TRY(build_block<float>(p, i, g, p->sch.blocks[i]));
     p->blocks[i].spec_off = p->spec_per_rhs;
     p->spec_per_rhs += p->blocks[i].H;
-    p->max_n = std::max<int64_t>(p->max_n, p->blocks[i].n);
+    if (p->blocks[i].a_csize == 1) p->max_n = std::max<int64_t>(p->max_n, p->blocks[i].n);
+    p->max_csize = std::max(p->max_csize, p->blocks[i].a_csize);
   }
   // work lists for the sparse kernels (longest first); widths come back from the device
   p->nslices = (N + kSlice - 1) / kSlice;

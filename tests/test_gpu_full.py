@@ -160,3 +160,36 @@ def test_autograd_legendre32768_fp32_against_dense_transpose(xc):
         grad = x.grad.double().cpu().numpy()
     ref = M.dense_apply_adjoint(sp, gout.double().cpu().numpy())
     assert M.rel_l2(grad, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("N,eps,precision", [(30000, 1e-10, "fp64"), (30000, 1e-10, "fp64pair"),
+                                             (60000, 1e-7, "fp32")])
+def test_long_blocks_run_the_apply_fft_on_a_cluster(xc, N, eps, precision):
+    """Chebyshev blocks too long for one CTA's shared memory in the plan
+    precision (n = L/2 complex points above ~14.5 k in FP64, ~29 k in FP32):
+    the apply FFTs split the array over a thread-block cluster.  Checked
+    against the plain dense product (the method's own accuracy, eps1/eps2) and
+    the exact-transpose property of the adjoint."""
+    eps2 = 1e-3 if precision != "fp32" else 1e-1
+    with xc.Plan("chebyshev", N, eps, precision=precision, eps2=eps2) as plan:
+        info = plan.info()
+        dt = torch.float64 if precision != "fp32" else torch.float32
+        esize = 16 if precision != "fp32" else 8
+        assert info["L"][0] // 2 * esize > 227 * 1024          # one CTA could not hold it
+        A = plan.dense_matrix()
+        X = torch.from_numpy(inputs.normal(N, 4, 61)).to("cuda", dt)
+        y = plan.apply(X)
+        y_d = X @ A.T
+        bound = max(10 * eps / eps2, 1e-5) if precision == "fp32" else 10 * eps / eps2
+        assert float(torch.linalg.norm(y.double() - y_d.double()) / torch.linalg.norm(y_d.double())) <= bound
+        Y = torch.from_numpy(inputs.normal(N, 4, 62)).to("cuda", dt)
+        xa = plan.apply_adjoint(Y)
+        xa_d = Y @ A
+        assert float(torch.linalg.norm(xa.double() - xa_d.double()) / torch.linalg.norm(xa_d.double())) <= bound
+        # <A x, y> = <x, A^T y> for the method's own operators
+        lhs = (y.double() * Y.double()).sum(dim=1)
+        rhs = (X.double() * xa.double()).sum(dim=1)
+        scale = (y.double() * Y.double()).abs().sum(dim=1)
+        tol = 1e-12 if precision != "fp32" else 1e-5
+        assert bool(((lhs - rhs).abs() <= tol * scale).all())
+        del A
