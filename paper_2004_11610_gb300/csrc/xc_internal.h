@@ -115,7 +115,6 @@ struct Plan {
   // work lists of the sparse kernels, longest item first: forward = row slices
   // (cost = summed band widths over blocks), adjoint = bin slices of all blocks
   int* f_order = nullptr;              // [nslices]
-  int* t_order = nullptr;              // unused (kept zero)
   int2* t_items = nullptr;             // [total_chunks]: (global bin slice, chunk), longest chunk first
   // the adjoint items of single-plan applies: the same as t_items / t_cbase,
   // or (small plans) a cut into shorter chunks of s_chunk rows
@@ -135,7 +134,6 @@ struct Plan {
   bool any_yt = false;                 // some block reads the transposed right-hand sides
   std::vector<int> unit_len;           // host: rows of each unit (in fu_order order)
   std::vector<int> item_len;           // host: rows of each adjoint chunk, in t_items order
-  std::vector<int2> item_host;         // host copy of t_items
   int64_t nslices = 0, total_tslices = 0;
   unsigned* counters = nullptr;        // [4]: {next, done} for the forward and the adjoint sparse kernel
   int64_t spec_per_rhs = 0;            // complex elements of all blocks' spectra per RHS

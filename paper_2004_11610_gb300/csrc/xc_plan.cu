@@ -1222,7 +1222,6 @@ int build_plan_device(Plan* p) {
   std::vector<int2> titems;
   std::vector<int> cbase;
   p->total_chunks = make_chunks(kAdjChunk, &titems, &cbase, &p->item_len);
-  p->item_host = titems;
   p->slice_cost = fcost;
   XC_TRY(upload(p, titems, &p->t_items));
   XC_TRY(upload(p, cbase, &p->t_cbase));
