@@ -19,13 +19,22 @@ import numpy as np
 import scipy.linalg
 from scipy.special import gammaln
 
-FAMILIES = ("chebyshev", "legendre", "jacobi", "laguerre", "hermite", "sine", "cospow")
+FAMILIES = ("chebyshev", "legendre", "jacobi", "laguerre", "hermite", "sine", "cospow", "exp", "lagspec")
 ONE_SIDED = ("legendre", "jacobi", "laguerre", "hermite")
 # trigonometric families, all at the angles theta_n of the Chebyshev-Gauss
 # points: cos(m theta_n) (Chebyshev T), sin(m theta_n) (Section 2.2 names the
 # sin and exp matrices beside eq. (cheb_matrix)) and cos^s(m theta_n)
 # (eq. (cosd2)); all are defined for negative m and take the two-sided extension
 TRIG = ("chebyshev", "sine", "cospow")
+# complex families (complex matrix, complex vectors): exp(i m theta_n) at
+# angles theta_n (the nodes are the angles themselves), and the spectral
+# Laguerre matrix C of eq. (lag_matrix), C[j, m] = exp(i m psi_j) / (eta/2 -
+# i k_j), k_j = 2 pi j / T, whose exp part is an exp matrix at the angles psi_j
+# and whose 1 / (eta/2 - i k_j) is a row factor outside the compression
+# (Section 4: Algorithms 1 and 2 apply to the exp elements unchanged).  Both
+# are defined for negative m: two-sided extension.
+COMPLEX = ("exp", "lagspec")
+TWO_SIDED = TRIG + COMPLEX
 
 
 @dataclass
@@ -42,6 +51,10 @@ class Spec:
     cheb_num: np.ndarray | None = None
     cheb_den: int = 0
     power: int = 2            # s of the cos^s family
+
+    @property
+    def is_complex(self) -> bool:
+        return self.family in COMPLEX
 
 
 # ------------------------------------------------------------------ recurrences
@@ -182,6 +195,16 @@ def values(spec: Spec, m_lo: int, m_hi: int, rows=None) -> np.ndarray:
     """
     x = spec.x if rows is None else spec.x[np.asarray(rows)]
     fam = spec.family
+    if fam in COMPLEX:
+        # exp(i m theta_n); exact angle reduction when theta_n = pi num_n / den
+        m = np.arange(m_lo, m_hi, dtype=np.int64)
+        if spec.cheb_num is not None:
+            num = spec.cheb_num if rows is None else spec.cheb_num[np.asarray(rows)]
+            k = np.mod(np.outer(num.astype(np.int64), m), 2 * spec.cheb_den)
+            ang = np.pi * k / spec.cheb_den
+        else:
+            ang = np.outer(x, m.astype(np.float64))
+        return np.exp(1j * ang)
     if fam in TRIG:
         m = np.arange(m_lo, m_hi, dtype=np.int64)
         if spec.cheb_num is not None:
@@ -231,8 +254,11 @@ def _jacobi_matrix(family, N, a=0.0, b=0.0):
         diag[0] = (b - a) / (a + b + 2)
         kk = k[1:]
         c1 = 2 * kk + a + b
-        off = np.sqrt(4 * kk * (kk + a) * (kk + b) * (kk + a + b)
-                      / (c1 * c1 * (c1 + 1) * (c1 - 1)))
+        with np.errstate(invalid="ignore", divide="ignore"):
+            off = np.sqrt(4 * kk * (kk + a) * (kk + b) * (kk + a + b)
+                          / (c1 * c1 * (c1 + 1) * (c1 - 1)))
+        if N > 1:   # k = 1 with the factor 1 + a + b cancelled (0/0 when a + b = -1)
+            off[0] = np.sqrt(4 * (1 + a) * (1 + b) / ((2 + a + b) ** 2 * (3 + a + b)))
     elif family == "laguerre":
         diag = 2 * k + 1
         off = k[1:]
@@ -318,11 +344,42 @@ def gauss_nodes(family: str, N: int, alpha: float = 0.0, beta: float = 0.0) -> n
     return np.sort(x)
 
 
+def exp_default_angles(N: int):
+    """Default angles of the exp family: the midpoints theta_n = (2n + 1 - N)
+    pi / N of N equal arcs of (-pi, pi), at which the exp functions of degrees
+    0..N-1 are discretely orthogonal; returned as (numerator, denominator) of
+    theta_n / pi."""
+    return 2 * np.arange(N, dtype=np.int64) + 1 - N, N
+
+
+def lagspec_angles(N: int, eta: float, period: float) -> np.ndarray:
+    """psi_j of the spectral Laguerre matrix: exp(i psi_j) = (-eta/2 - i k_j) /
+    (eta/2 - i k_j), k_j = 2 pi j / T, j = 0..N-1.  The quotient is
+    -(eta/2 + i k)^2 / |eta/2 + i k|^2, so psi_j = 2 arctan(2 k_j / eta) - pi,
+    in [-pi, 0) and increasing with j."""
+    k = 2.0 * np.pi * np.arange(N) / period
+    return 2.0 * np.arctan(2.0 * k / eta) - np.pi
+
+
+def lagspec_row_factor(N: int, eta: float, period: float) -> np.ndarray:
+    """1 / (eta/2 - i k_j), the row factor of the spectral Laguerre matrix."""
+    k = 2.0 * np.pi * np.arange(N) / period
+    return 1.0 / (eta / 2.0 - 1j * k)
+
+
 def make_spec(family: str, N: int, alpha: float = 0.0, beta: float = 0.0, x=None, power: int = 2) -> Spec:
     """A family at its Gauss nodes (or at user nodes x); `power` is the s of
-    the cos^s family."""
+    the cos^s family.  exp: x are angles (default `exp_default_angles`);
+    lagspec: alpha = eta, beta = T (the angles follow from them)."""
+    if family == "lagspec":
+        if not (alpha > 0 and beta > 0):
+            raise ValueError("the spectral Laguerre matrix needs eta > 0 and T > 0")
+        return Spec(family, N, lagspec_angles(N, alpha, beta), alpha, beta)
     if x is not None:
         return Spec(family, N, np.asarray(x, dtype=np.float64), alpha, beta, power=power)
+    if family == "exp":
+        num, den = exp_default_angles(N)
+        return Spec(family, N, np.pi * num / den, alpha, beta, cheb_num=num, cheb_den=den)
     if family in TRIG:
         n = np.arange(N, dtype=np.int64)
         return Spec(family, N, gauss_nodes(family, N), alpha, beta,
@@ -390,9 +447,11 @@ def scalings(spec: Spec, normalise: bool):
     colscale = 1/sqrt(chi_m), which makes Q orthogonal at Gauss nodes.
     """
     N = spec.N
+    if spec.family == "lagspec" and not normalise:
+        return lagspec_row_factor(N, spec.alpha, spec.beta), np.ones(N)
     if not normalise:
         return np.ones(N), np.ones(N)
-    if spec.family in ("sine", "cospow"):
+    if spec.family in ("sine", "cospow") + COMPLEX:
         raise ValueError("the orthonormal variant is defined for the orthogonal polynomial families")
     return np.sqrt(quadrature_weights(spec)), 1.0 / np.sqrt(column_norms_sq(spec, N))
 
@@ -400,6 +459,9 @@ def scalings(spec: Spec, normalise: bool):
 def dense_matrix(spec: Spec, normalise: bool = False, rows=None) -> np.ndarray:
     """The plain N x N matrix (or the selected rows) that defines the result."""
     A = values(spec, 0, spec.N, rows)
+    if spec.family == "lagspec":
+        r = lagspec_row_factor(spec.N, spec.alpha, spec.beta)
+        A = (r if rows is None else r[np.asarray(rows)])[:, None] * A
     if normalise:
         r, c = scalings(spec, True)
         if rows is not None:

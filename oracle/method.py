@@ -167,7 +167,7 @@ def build(spec, eps: float, eps2: float | None = None, precision: str = "fp64",
     if eps2 is None:
         eps2 = default_eps2(precision)
     if two_sided is None:
-        two_sided = spec.family in fam_mod.TRIG
+        two_sided = spec.family in fam_mod.TWO_SIDED
     N = spec.N
     sch = special.schedule(N, eps, eps2, two_sided, eps_window, tail_max)
     rows = np.arange(N) if rows is None else np.asarray(rows)
@@ -197,8 +197,8 @@ def build(spec, eps: float, eps2: float | None = None, precision: str = "fp64",
     return plan
 
 
-def _as_2d(v):
-    v = np.asarray(v, dtype=np.float64)
+def _as_2d(v, complex_=False):
+    v = np.asarray(v, dtype=np.complex128 if complex_ or np.iscomplexobj(v) else np.float64)
     return (v[None, :], True) if v.ndim == 1 else (v, False)
 
 
@@ -208,17 +208,20 @@ def apply(plan: OraclePlan, x) -> np.ndarray:
 
     Per block: x^{[1]} of eq. (Fe1)/(Fe3) (zeros outside [j_lo, j_hi)), then
     Ä_e F* W^{-1} x^{[1]} (step 2.2), real part, summed over the blocks.
+    Complex families: complex x and y, no real part taken.
     """
-    X, flat = _as_2d(x)
+    cplx = plan.spec.is_complex
+    X, flat = _as_2d(x, cplx)
     Xs = X * plan.colscale[None, :]
     R = X.shape[0]
-    Y = np.zeros((R, plan.rows.size))
+    Y = np.zeros((R, plan.rows.size), dtype=np.complex128 if cplx else np.float64)
     for b in plan.blocks:
-        x1 = np.zeros((R, b.L))
+        x1 = np.zeros((R, b.L), dtype=Xs.dtype)
         x1[:, b.j_lo:b.j_hi] = Xs[:, b.j_lo - b.off:b.j_hi - b.off]
         u = x1 / b.window[None, :]
         v = np.fft.ifft(u, axis=1) * np.sqrt(b.L)          # F* W^{-1} x^{[1]}
-        Y += np.real((b.kept @ v.T).T)                     # Ä_e (F* W^{-1} x^{[1]})
+        prod = (b.kept @ v.T).T                            # Ä_e (F* W^{-1} x^{[1]})
+        Y += prod if cplx else np.real(prod)
     if plan.tail is not None:
         Y += Xs[:, : plan.tail.shape[1]] @ plan.tail.T     # direct product, last block
     Y *= plan.rowscale[plan.rows][None, :]
@@ -231,18 +234,21 @@ def apply_adjoint(plan: OraclePlan, y) -> np.ndarray:
     Per block: x^{[2]} = W^{-1} F* Ä_e^T y (step 2.1, plain transpose), real
     part, then the extra components outside [j_lo, j_hi) are discarded
     (step 2.2, eq. (Fe2)); each block writes its own slice of x.
-    Requires a plan built over all rows.
+    Requires a plan built over all rows.  Complex families: the plain
+    transpose (not the conjugate transpose), no real part taken.
     """
     if plan.rows.size != plan.spec.N:
         raise ValueError("the adjoint needs every row of the compressed matrix")
-    Y, flat = _as_2d(y)
+    cplx = plan.spec.is_complex
+    Y, flat = _as_2d(y, cplx)
     Ys = Y * plan.rowscale[None, :]
     R = Y.shape[0]
-    Xh = np.zeros((R, plan.spec.N))
+    Xh = np.zeros((R, plan.spec.N), dtype=np.complex128 if cplx else np.float64)
     for b in plan.blocks:
         z = (b.kept.T @ Ys.T).T                            # Ä_e^T y
         x2 = np.fft.ifft(z, axis=1) * np.sqrt(b.L) / b.window[None, :]   # W^{-1} F* (.)
-        Xh[:, b.j_lo - b.off:b.j_hi - b.off] = np.real(x2[:, b.j_lo:b.j_hi])
+        part = x2[:, b.j_lo:b.j_hi]
+        Xh[:, b.j_lo - b.off:b.j_hi - b.off] = part if cplx else np.real(part)
     if plan.tail is not None:
         Xh[:, : plan.tail.shape[1]] = Ys @ plan.tail
     Xh *= plan.colscale[None, :]
@@ -252,9 +258,9 @@ def apply_adjoint(plan: OraclePlan, y) -> np.ndarray:
 def dense_apply(spec, x, normalise: bool = False, rows=None, chunk: int = 1024) -> np.ndarray:
     """The definition y = A x (A of eq. (cheb_matrix) / (Jac_matrix)), rows of A
     generated in chunks by the recurrences; x has shape (N,) or (R, N)."""
-    X, flat = _as_2d(x)
+    X, flat = _as_2d(x, spec.is_complex)
     rows = np.arange(spec.N) if rows is None else np.asarray(rows)
-    Y = np.empty((X.shape[0], rows.size))
+    Y = np.empty((X.shape[0], rows.size), dtype=np.complex128 if spec.is_complex else np.float64)
     for lo in range(0, rows.size, chunk):
         sel = rows[lo:lo + chunk]
         A = fam_mod.dense_matrix(spec, normalise, sel)
@@ -264,8 +270,8 @@ def dense_apply(spec, x, normalise: bool = False, rows=None, chunk: int = 1024) 
 
 def dense_apply_adjoint(spec, y, normalise: bool = False, chunk: int = 1024) -> np.ndarray:
     """The definition x = A^T y, accumulated over chunks of rows of A."""
-    Y, flat = _as_2d(y)
-    Xh = np.zeros((Y.shape[0], spec.N))
+    Y, flat = _as_2d(y, spec.is_complex)
+    Xh = np.zeros((Y.shape[0], spec.N), dtype=np.complex128 if spec.is_complex else np.float64)
     for lo in range(0, spec.N, chunk):
         sel = np.arange(lo, min(spec.N, lo + chunk))
         A = fam_mod.dense_matrix(spec, normalise, sel)
@@ -275,6 +281,8 @@ def dense_apply_adjoint(spec, y, normalise: bool = False, chunk: int = 1024) -> 
 
 def rel_l2(a, b) -> float:
     """||a - b||_2 / ||b||_2 over all entries."""
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
+    a = np.asarray(a)
+    b = np.asarray(b)
+    a = a.astype(np.complex128 if np.iscomplexobj(a) else np.float64)
+    b = b.astype(np.complex128 if np.iscomplexobj(b) else np.float64)
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))

@@ -42,7 +42,7 @@ def test_laguerre_hermite_extreme_nodes_against_mpmath():
             assert abs(x[i] - float(r)) <= tol(float(r))
 
 
-@pytest.mark.parametrize("ab", [(0.5, -0.5), (1.0, 1.0), (-0.3, 2.5), (0.0, 0.0)])
+@pytest.mark.parametrize("ab", [(0.5, -0.5), (1.0, 1.0), (-0.3, 2.5), (0.0, 0.0), (-0.5, -0.5), (-0.3, -0.7)])
 def test_jacobi_nodes_match_scipy_roots(ab):
     a, b = ab
     for N in (7, 60):
@@ -56,6 +56,19 @@ def test_jacobi_half_minus_half_nodes_closed_form():
         k = np.arange(1, N + 1)
         ref = np.sort(np.cos(2 * k * np.pi / (2 * N + 1)))
         assert np.allclose(F.gauss_nodes("jacobi", N, 0.5, -0.5), ref, rtol=0, atol=2e-15)
+
+
+def test_jacobi_nodes_of_the_chebyshev_kinds_closed_form():
+    """alpha = beta = -1/2 and 1/2 are the Chebyshev polynomials of the first and
+    second kind, alpha = -1/2, beta = 1/2 the third kind: zeros cos((2k-1) pi /
+    (2N)), cos(k pi / (N+1)) and cos((2k-1) pi / (2N+1)).  alpha + beta = -1
+    makes the k = 1 entry of the Jacobi matrix a removable 0/0."""
+    for N in (2, 31, 1000):
+        k = np.arange(1, N + 1)
+        for (a, b), t in (((-0.5, -0.5), (2 * k - 1) / (2 * N)), ((0.5, 0.5), k / (N + 1)),
+                          ((-0.5, 0.5), (2 * k - 1) / (2 * N + 1))):
+            ref = np.sort(np.cos(t * np.pi))
+            assert np.allclose(F.gauss_nodes("jacobi", N, a, b), ref, rtol=0, atol=2e-15), (a, b, N)
 
 
 def test_chebyshev_gauss_points():
