@@ -88,6 +88,9 @@ def workload_config(name, wl):
     }
 
 
+COMPLEX_FAMILY_IDS = (7, 8)   # exp, spectral Laguerre
+
+
 def algorithmic_work(info, nrhs, precision, chunked=False):
     """Per kernel: algorithmic flops and bytes of one launch.
     A chunked forward product (plans with long bands) leaves the dense tail
@@ -96,6 +99,18 @@ def algorithmic_work(info, nrhs, precision, chunked=False):
     eb = 8 if precision in ("fp64", "fp64pair") else 4
     nnz = sum(info["nnz"])
     N, mt = info["N"], info["m_tail"]
+    if info.get("family") in COMPLEX_FAMILY_IDS:
+        # complex vectors and values (2 eb per element), full spectrum of L
+        # bins, 8 real flops per complex multiply-add, 5 L log2 L per FFT
+        ce, L = 2 * eb, info["L"][0]
+        cfft = 5.0 * L * math.log2(L) * nrhs
+        return {
+            "fwd_fft": (cfft, nrhs * (N + L) * ce),
+            "fwd_sparse": (8.0 * nnz * nrhs, nnz * ce + nrhs * (L + N) * ce),
+            "row_scale": (6.0 * N * nrhs, N * ce + 2 * nrhs * N * ce),
+            "adj_sparse": (8.0 * nnz * nrhs, nnz * ce + nrhs * (N + L) * ce),
+            "adj_fft": (cfft, nrhs * (L + N) * ce),
+        }
     fft_flops = sum(2.5 * L * math.log2(L) for L in info["L"]) * nrhs
     H = sum(L // 2 + 1 for L in info["L"])
     if chunked:
@@ -113,6 +128,8 @@ def algorithmic_work(info, nrhs, precision, chunked=False):
         "adj_transpose": (0.0, N * eb * (nrhs + (nrhs + 7) // 8 * 8)),
         # per-RHS scaling of FP64 pair plans: read the vector (adjoint: write its pairs)
         "pair_scale": (0.0, 2.0 * N * eb * nrhs),
+        # row factors of the complex spectral Laguerre matrix (not run by real plans)
+        "row_scale": (0.0, 0.0),
     }
 
 

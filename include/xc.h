@@ -20,6 +20,9 @@
  *   - Vectors are row-major [nrhs][ld] with ld >= N: right-hand side r occupies
  *     elements r*ld .. r*ld+N-1.  Their element type is the plan's I/O type:
  *     double for XC_FP64 plans, float for XC_FP32 and XC_FP32_COMPENSATED.
+ *     The complex families (XC_EXP, XC_LAGUERRE_SPECTRAL) take complex
+ *     vectors: an element is two consecutive values (re, im) of the I/O type,
+ *     and ld, N and every element count are in complex elements.
  *   - Pointers named *_dev are device pointers owned by the caller; pointers
  *     named *_host are host pointers owned by the caller.  The plan owns every
  *     other buffer (compressed matrices, windows, twiddles, scratch).
@@ -55,7 +58,20 @@ typedef enum {
   XC_HERMITE_FN  = 4,  /* orthonormal Hermite functions psi_m(x); block method */
   XC_SINE        = 5,  /* sin(m theta_n), theta_n = arccos x_n (Section 2.2 names the sin and exp
                           matrices beside eq. (cheb_matrix)); two-sided extension */
-  XC_COS_POWER   = 6   /* cos^s(m theta_n), s = xc_params.power (eq. (cosd2)); two-sided extension */
+  XC_COS_POWER   = 6,  /* cos^s(m theta_n), s = xc_params.power (eq. (cosd2)); two-sided extension */
+  XC_EXP         = 7,  /* exp(i m theta_n), complex matrix and vectors (Section 2.2 names the exp
+                          matrix beside eq. (cheb_matrix)).  The nodes are the angles theta_n
+                          themselves: Gauss nodes = the midpoints (2n + 1 - N) pi / N of N equal
+                          arcs (discretely orthogonal), user nodes = any real angles.  Two-sided
+                          extension, one block. */
+  XC_LAGUERRE_SPECTRAL = 8  /* the spectral Laguerre matrix C of eq. (lag_matrix) (Section 4),
+                          read as C[j, m] = (-eta/2 - i k_j)^m / (eta/2 - i k_j)^(m+1)
+                          = exp(i m psi_j) / (eta/2 - i k_j), k_j = 2 pi j / T,
+                          psi_j = 2 arctan(2 k_j / eta) - pi; eta = alpha > 0, T = beta > 0.
+                          The exp part is compressed (an XC_EXP plan at the angles psi_j, which
+                          xc_get_nodes returns), the factor 1/(eta/2 - i k_j) is applied to the
+                          rows outside it.  xc_apply_adjoint gives C^T F (Fourier coefficients
+                          to Laguerre coefficients).  Complex vectors. */
 } xc_family;
 
 /* node sets */
@@ -88,7 +104,8 @@ typedef enum {
 #define XC_PRECOMPUTE_FFT  1   /* always the FFT of the generated rows (Algorithm 1 step 1.3 as written) */
 
 typedef struct {
-  double alpha, beta;        /* Jacobi parameters (> -1); ignored by the other families */
+  double alpha, beta;        /* Jacobi parameters (> -1); eta and T (> 0) of XC_LAGUERRE_SPECTRAL;
+                                ignored by the other families */
   int nodes;                 /* XC_NODES_GAUSS | XC_NODES_USER */
   const double* user_nodes;  /* host, N entries, copied at create; used when nodes == XC_NODES_USER */
   int normalise;             /* XC_RAW | XC_ORTHONORMAL (orthonormal needs Gauss nodes and a
@@ -118,6 +135,13 @@ typedef struct xc_plan* xc_plan_t;
  *           every element and takes zeta from p->eps_window.
  * Runs on the current CUDA device and synchronises it.  On success *out owns
  * all device memory of the plan; on failure *out is NULL and nothing leaks.
+ * Complex families: precision XC_FP64 or XC_FP32, the two-sided scheme, raw
+ * normalisation, and a block length L whose L complex values fit one CTA's
+ * shared memory (L <= 14464 in FP64, 28928 in FP32; L / N is about 1.46 at
+ * eps1 = 1e-10, eps2 = 1e-3 and 1.9 at eps1 = 1e-6, eps2 = 0.1, so N up to
+ * about 9800 and 15000); otherwise XC_ERR_UNSUPPORTED.  Such plans are applied by
+ * xc_apply / xc_apply_adjoint / xc_apply_host only (xc_apply_noalloc and
+ * the batches return XC_ERR_UNSUPPORTED).
  */
 int xc_plan_create(xc_plan_t* out, int family, const xc_params* p, int64_t N, double eps);
 
@@ -149,7 +173,8 @@ int xc_apply(xc_plan_t plan, const void* x_dev, void* y_dev, int64_t nrhs, int64
  * xc_apply_adjoint -- x = A^T y (Algorithm 2 step 2 / Algorithm 4): per block,
  * multiply by the transposed compressed matrix, inverse FFT, divide by the
  * window and discard the extra components (eq. (Fe2)); the dense tail writes
- * the first m_tail entries.  Exactly the transpose of xc_apply's operator.
+ * the first m_tail entries.  Exactly the transpose of xc_apply's operator
+ * (for the complex families the plain transpose, not the conjugate one).
  * Same argument conventions as xc_apply (y_dev is read, x_dev written).
  */
 int xc_apply_adjoint(xc_plan_t plan, const void* y_dev, void* x_dev, int64_t nrhs, int64_t ld, void* stream);
@@ -203,7 +228,8 @@ typedef struct {
   int64_t off[XC_MAX_BLOCKS];        /* extended column j holds matrix column j - off */
   int64_t j_lo[XC_MAX_BLOCKS];       /* real input occupies extended columns [j_lo, j_hi) */
   int64_t j_hi[XC_MAX_BLOCKS];
-  int64_t nnz[XC_MAX_BLOCKS];        /* kept elements in the half spectrum k = 0..L/2 */
+  int64_t nnz[XC_MAX_BLOCKS];        /* kept elements in the half spectrum k = 0..L/2 (complex
+                                        families: in the full spectrum) */
   int64_t stored[XC_MAX_BLOCKS];     /* stored band elements incl. explicit zeros (forward layout) */
   double maxabs[XC_MAX_BLOCKS];      /* max |A_e W F| of the block */
   int64_t m_tail;                    /* dense tail columns [0, m_tail) */

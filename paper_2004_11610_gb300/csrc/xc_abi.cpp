@@ -45,7 +45,8 @@ int plan_alloc(Plan* p, void** ptr, size_t bytes) {
 static std::atomic<int64_t> g_launches{0};
 
 const char* kernel_name(int id) {
-  static const char* names[K_COUNT] = {"fwd_fft", "fwd_sparse", "adj_sparse", "adj_fft", "adj_tail", "fwd_reduce", "adj_transpose", "pair_scale"};
+  static const char* names[K_COUNT] = {"fwd_fft",       "fwd_sparse", "adj_sparse", "adj_fft",  "adj_tail",
+                                       "fwd_reduce",    "adj_transpose", "pair_scale", "row_scale"};
   return (id >= 0 && id < K_COUNT) ? names[id] : "unknown";
 }
 
@@ -131,8 +132,9 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
   xc_params prm;
   if (params) prm = *params;
   else xc_params_default(&prm);
-  if (family < XC_CHEBYSHEV_T || family > XC_COS_POWER) return fail(XC_ERR_ARG, "unknown family");
-  const bool trig = family == XC_CHEBYSHEV_T || family == XC_SINE || family == XC_COS_POWER;
+  if (family < XC_CHEBYSHEV_T || family > XC_LAGUERRE_SPECTRAL) return fail(XC_ERR_ARG, "unknown family");
+  const bool cplx = family == XC_EXP || family == XC_LAGUERRE_SPECTRAL;
+  const bool trig = family == XC_CHEBYSHEV_T || family == XC_SINE || family == XC_COS_POWER || cplx;
   if (N < 2 || N > (int64_t(1) << 20)) return fail(XC_ERR_ARG, "N must lie in [2, 2^20]");
   if (!(eps >= 0.0) || !(eps < 1.0)) return fail(XC_ERR_ARG, "eps must lie in [0, 1)");
   if (prm.precision < XC_FP64 || prm.precision > XC_FP64_PAIR) return fail(XC_ERR_ARG, "unknown precision");
@@ -152,6 +154,16 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
     return fail(XC_ERR_ARG, "eps2 / eps_window / tail_max out of range");
   if (prm.precompute != XC_PRECOMPUTE_AUTO && prm.precompute != XC_PRECOMPUTE_FFT)
     return fail(XC_ERR_ARG, "unknown precompute mode");
+  if (family == XC_LAGUERRE_SPECTRAL && !(prm.alpha > 0.0 && prm.beta > 0.0))
+    return fail(XC_ERR_ARG, "the spectral Laguerre matrix needs eta = alpha > 0 and T = beta > 0");
+  if (family == XC_LAGUERRE_SPECTRAL && prm.nodes == XC_NODES_USER)
+    return fail(XC_ERR_ARG, "the spectral Laguerre matrix has its own angles (no user nodes)");
+  if (cplx && prm.precision != XC_FP64 && prm.precision != XC_FP32)
+    return fail(XC_ERR_UNSUPPORTED, "complex families run in XC_FP64 or XC_FP32");
+  if (cplx && prm.scheme == XC_SCHEME_BLOCKS)
+    return fail(XC_ERR_UNSUPPORTED, "complex families take the two-sided extension");
+  if (cplx && prm.normalise == XC_ORTHONORMAL)
+    return fail(XC_ERR_UNSUPPORTED, "the orthonormal variant is defined for the polynomial families");
 
   xc::Plan* p = new (std::nothrow) xc::Plan();
   if (!p) return fail(XC_ERR_ALLOC, "host allocation failed");
@@ -159,7 +171,9 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
   p->family = family;
   p->params = prm;
   p->params.user_nodes = nullptr;
-  if (family != XC_JACOBI) p->params.alpha = p->params.beta = 0.0;   // only the Jacobi family has (alpha, beta)
+  // only the Jacobi family (alpha, beta) and the spectral Laguerre matrix (eta, T) have parameters
+  if (family != XC_JACOBI && family != XC_LAGUERRE_SPECTRAL) p->params.alpha = p->params.beta = 0.0;
+  p->cplx = cplx;
   p->precision = prm.precision;
   p->normalise = prm.normalise;
   p->scheme = prm.scheme == XC_SCHEME_AUTO ? (trig ? XC_SCHEME_TWO_SIDED : XC_SCHEME_BLOCKS) : prm.scheme;
@@ -215,6 +229,7 @@ int xc_apply_noalloc(xc_plan_t plan, const void* x_dev, void* y_dev, int64_t nrh
   auto* p = reinterpret_cast<xc::Plan*>(plan);
   XC_TRY(xc::validate_vectors(p, x_dev, y_dev, nrhs, ld));
   if (nrhs == 0) return XC_OK;
+  if (p->cplx) return fail(XC_ERR_UNSUPPORTED, "xc_apply_noalloc does not take complex plans");
   p->last_stream = static_cast<cudaStream_t>(stream);
   return xc::launch_apply_noalloc(p, x_dev, y_dev, nrhs, ld, static_cast<cudaStream_t>(stream));
 }
@@ -233,7 +248,7 @@ int xc_apply_host(xc_plan_t plan, int adjoint, const void* in_host, void* out_ho
       p->stage_elems = 0;
     }
     void* d = nullptr;
-    if (cudaMalloc(&d, size_t(2 * elems) * p->elem_bytes()) != cudaSuccess) {
+    if (cudaMalloc(&d, size_t(2 * elems) * p->io_bytes()) != cudaSuccess) {
       cudaGetLastError();
       return fail(XC_ERR_ALLOC, "staging allocation failed");
     }
@@ -243,8 +258,8 @@ int xc_apply_host(xc_plan_t plan, int adjoint, const void* in_host, void* out_ho
   auto st = static_cast<cudaStream_t>(stream);
   p->last_stream = st;
   char* din = static_cast<char*>(p->stage);
-  char* dout = din + size_t(p->stage_elems) * p->elem_bytes();
-  const size_t bytes = size_t(elems) * p->elem_bytes();
+  char* dout = din + size_t(p->stage_elems) * p->io_bytes();
+  const size_t bytes = size_t(elems) * p->io_bytes();
   XC_CUDA(cudaMemcpyAsync(din, in_host, bytes, cudaMemcpyHostToDevice, st));
   if (adjoint) XC_TRY(xc::launch_apply_adjoint(p, din, dout, nrhs, ld, st));
   else XC_TRY(xc::launch_apply(p, din, dout, nrhs, ld, st));

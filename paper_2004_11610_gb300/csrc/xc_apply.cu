@@ -777,31 +777,9 @@ int launch_apply_noalloc(Plan* p, const void* x, void* y, int64_t nrhs, int64_t 
   }
 }
 
-int ensure_scratch(Plan* p, int64_t nrhs) {
-  if (p->scratch_desc == nullptr) {
-    void* d = nullptr;
-    XC_TRY(plan_alloc(p, &d, std::max<size_t>(1, p->blocks.size()) * sizeof(BlockDev)));
-    if (!p->blocks.empty())
-      XC_CUDA(cudaMemcpy(d, p->blocks.data(), p->blocks.size() * sizeof(BlockDev), cudaMemcpyHostToDevice));
-    p->scratch_desc = d;
-  }
-  if (nrhs <= p->scratch_nrhs) return XC_OK;
-  const size_t cbytes = 2 * p->elem_bytes();
-  // forward: spectra (+ unit partials); adjoint: chunk partials + transposed
-  // y.  The directions share the buffer (one at a time).
-  const int64_t fwd = p->spec_per_rhs + (p->fwd_chunked ? p->total_units * 32 : 0);
-  const size_t fwd_bytes = size_t(fwd) * size_t(nrhs) * cbytes;
-  const int64_t chunks = std::max(p->total_chunks, p->s_total_chunks);
-  const size_t adj_bytes = size_t(chunks) * 32 * size_t(nrhs) * cbytes +
-                           (p->any_yt ? size_t(p->N) * size_t(yt_ld(nrhs)) * p->elem_bytes() : 0);
-  size_t bytes = std::max<size_t>({cbytes, fwd_bytes, adj_bytes});
-  if (p->precision == XC_FP64_PAIR) {
-    // adjoint input pairs after the chunk partials, then the per-RHS exponents
-    const size_t adj_pair = size_t(chunks) * 32 * size_t(nrhs) * cbytes + size_t(p->N) * size_t(nrhs) * 8;
-    bytes = (std::max(bytes, adj_pair) + 255) / 256 * 256;
-    p->pexp_off = bytes;
-    bytes += size_t(nrhs) * sizeof(int);
-  }
+namespace {
+
+int grow_scratch(Plan* p, int64_t nrhs, size_t bytes) {
   void* fresh = nullptr;
   if (cudaMalloc(&fresh, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -817,8 +795,40 @@ int ensure_scratch(Plan* p, int64_t nrhs) {
   return XC_OK;
 }
 
+}  // namespace
+
+int ensure_scratch(Plan* p, int64_t nrhs) {
+  if (p->scratch_desc == nullptr) {
+    void* d = nullptr;
+    XC_TRY(plan_alloc(p, &d, std::max<size_t>(1, p->blocks.size()) * sizeof(BlockDev)));
+    if (!p->blocks.empty())
+      XC_CUDA(cudaMemcpy(d, p->blocks.data(), p->blocks.size() * sizeof(BlockDev), cudaMemcpyHostToDevice));
+    p->scratch_desc = d;
+  }
+  if (nrhs <= p->scratch_nrhs) return XC_OK;
+  const size_t cbytes = 2 * p->elem_bytes();
+  if (p->cplx) return grow_scratch(p, nrhs, complex_scratch_bytes(p, nrhs));
+  // forward: spectra (+ unit partials); adjoint: chunk partials + transposed
+  // y.  The directions share the buffer (one at a time).
+  const int64_t fwd = p->spec_per_rhs + (p->fwd_chunked ? p->total_units * 32 : 0);
+  const size_t fwd_bytes = size_t(fwd) * size_t(nrhs) * cbytes;
+  const int64_t chunks = std::max(p->total_chunks, p->s_total_chunks);
+  const size_t adj_bytes = size_t(chunks) * 32 * size_t(nrhs) * cbytes +
+                           (p->any_yt ? size_t(p->N) * size_t(yt_ld(nrhs)) * p->elem_bytes() : 0);
+  size_t bytes = std::max<size_t>({cbytes, fwd_bytes, adj_bytes});
+  if (p->precision == XC_FP64_PAIR) {
+    // adjoint input pairs after the chunk partials, then the per-RHS exponents
+    const size_t adj_pair = size_t(chunks) * 32 * size_t(nrhs) * cbytes + size_t(p->N) * size_t(nrhs) * 8;
+    bytes = (std::max(bytes, adj_pair) + 255) / 256 * 256;
+    p->pexp_off = bytes;
+    bytes += size_t(nrhs) * sizeof(int);
+  }
+  return grow_scratch(p, nrhs, bytes);
+}
+
 int launch_apply(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
   XC_TRY(ensure_scratch(p, nrhs));
+  if (p->cplx) return launch_apply_complex(p, x, y, nrhs, ld, st);
   switch (p->precision) {
     case XC_FP64: return apply_impl<double, false>(p, x, y, nrhs, ld, st);
     case XC_FP64_PAIR: return apply_pair(p, x, y, nrhs, ld, st);
@@ -829,6 +839,7 @@ int launch_apply(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cuda
 
 int launch_apply_adjoint(Plan* p, const void* y, void* x, int64_t nrhs, int64_t ld, cudaStream_t st) {
   XC_TRY(ensure_scratch(p, nrhs));
+  if (p->cplx) return launch_adjoint_complex(p, y, x, nrhs, ld, st);
   switch (p->precision) {
     case XC_FP64: return adjoint_impl<double, false>(p, y, x, nrhs, ld, st);
     case XC_FP64_PAIR: return adjoint_pair(p, y, x, nrhs, ld, st);

@@ -468,6 +468,10 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans) {
       delete b;
       return fail(XC_ERR_UNSUPPORTED, "batches take XC_FP64, XC_FP32 or XC_FP32_COMPENSATED plans");
     }
+    if (p->cplx) {
+      delete b;
+      return fail(XC_ERR_UNSUPPORTED, "plan " + std::to_string(i) + " is complex: batches take real families");
+    }
     if (i > 0 && p->precision != b->precision) {
       delete b;
       return fail(XC_ERR_ARG, "all plans of a batch need the same precision");

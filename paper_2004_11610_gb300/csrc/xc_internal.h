@@ -111,6 +111,8 @@ struct Plan {
   void* rowscale = nullptr;            // [N] or null (raw)
   void* colscale = nullptr;            // [N] or null (raw)
   double* nodes_dev = nullptr;         // [N] FP64
+  double* rc_dev = nullptr;            // [3 nrc] recurrence coefficients (one-sided families)
+  int64_t nrc = 0;
   std::vector<double> nodes_host;
   // work lists of the sparse kernels, longest item first: forward = row slices
   // (cost = summed band widths over blocks), adjoint = bin slices of all blocks
@@ -138,7 +140,12 @@ struct Plan {
   unsigned* counters = nullptr;        // [4]: {next, done} for the forward and the adjoint sparse kernel
   int64_t spec_per_rhs = 0;            // complex elements of all blocks' spectra per RHS
   int64_t max_n = 0;                   // largest n of a block whose apply FFT runs in one CTA
-  int max_csize = 1;                   // largest apply cluster of any block                   // largest n over blocks (shared memory of the FFTs)
+  int max_csize = 1;                   // largest apply cluster of any block
+  // complex families: one two-sided block over the full spectrum, circular
+  // bands (xc_complex.cu); the forward spectra carry a periodic copy of their
+  // first c_vpad bins after bin L-1 so that no band read wraps
+  bool cplx = false;
+  int c_vpad = 0;
   int64_t matrix_bytes = 0, adjoint_bytes = 0;
   // device copy of `blocks` (read by the kernels), scratch spectra, host-path staging
   void* scratch_desc = nullptr;
@@ -157,7 +164,8 @@ struct Plan {
   std::vector<int64_t> t_launches;
   std::vector<double> t_ms;
   bool io64() const { return precision == XC_FP64 || precision == XC_FP64_PAIR; }   // FP64 vectors, FFTs, tail
-  size_t elem_bytes() const { return io64() ? 8 : 4; }
+  size_t elem_bytes() const { return io64() ? 8 : 4; }   // one real value
+  size_t io_bytes() const { return (cplx ? 2 : 1) * elem_bytes(); }   // one vector element
 };
 
 // Device allocation recorded in the plan (freed by xc_plan_destroy).
@@ -165,7 +173,8 @@ int plan_alloc(Plan* p, void** ptr, size_t bytes);
 
 // Kernel identities for the launch counter and the per-kernel timing.
 enum KernelId {
-  K_FWD_FFT = 0, K_FWD_SPARSE, K_ADJ_SPARSE, K_ADJ_FFT, K_ADJ_TAIL, K_FWD_REDUCE, K_ADJ_TRANSPOSE, K_PAIR_SCALE, K_COUNT
+  K_FWD_FFT = 0, K_FWD_SPARSE, K_ADJ_SPARSE, K_ADJ_FFT, K_ADJ_TAIL, K_FWD_REDUCE, K_ADJ_TRANSPOSE, K_PAIR_SCALE,
+  K_ROW_SCALE, K_COUNT
 };
 
 // Row stride of the transposed adjoint input: nrhs rounded up to 8.
@@ -188,5 +197,9 @@ int dense_matrix_device(const Plan* p, void* A, int64_t lda, cudaStream_t s);
 int ensure_scratch(Plan* p, int64_t nrhs);
 int launch_apply(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t s);
 int launch_apply_adjoint(Plan* p, const void* y, void* x, int64_t nrhs, int64_t ld, cudaStream_t s);
+// (xc_complex.cu) execution of the complex families
+size_t complex_scratch_bytes(const Plan* p, int64_t nrhs);
+int launch_apply_complex(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t s);
+int launch_adjoint_complex(Plan* p, const void* y, void* x, int64_t nrhs, int64_t ld, cudaStream_t s);
 
 }  // namespace xc

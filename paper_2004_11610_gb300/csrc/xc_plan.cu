@@ -30,10 +30,20 @@ struct GenParams {
   const double* x;      // nodes
   int cheb_exact;       // trigonometric family at x_n = cos((2n+1) pi / (2N)): exact angles
   int power;            // s of the cos^s family
+  // three-term recurrence phi_{m+1} = (rc[3m] + rc[3m+1] x) phi_m - rc[3m+2] phi_{m-1}
+  // for m < nrc (null for the trigonometric families)
+  const double* rc = nullptr;
+  int64_t nrc = 0;
+  int cpart = 0;        // complex families: 0 = real part cos(m theta), 1 = imaginary part sin(m theta)
 };
 
+__host__ __device__ __forceinline__ bool is_complex_family(int family) {
+  return family == XC_EXP || family == XC_LAGUERRE_SPECTRAL;
+}
+
 __host__ __device__ __forceinline__ bool is_trig(int family) {
-  return family == XC_CHEBYSHEV_T || family == XC_SINE || family == XC_COS_POWER;
+  return family == XC_CHEBYSHEV_T || family == XC_SINE || family == XC_COS_POWER || family == XC_EXP ||
+         family == XC_LAGUERRE_SPECTRAL;
 }
 
 // exp(-a) for a >= 0 as mant * 2^expo, with the argument split
@@ -58,6 +68,34 @@ __device__ void exp_neg_split(double a_hi, double a_lo, double* mant, int* expo)
 template <class F>
 __device__ void gen_values(const GenParams& g, int64_t n, int64_t m_lo, int64_t m_hi, F emit) {
   const double x = g.x[n];
+  if (is_complex_family(g.family)) {
+    // exp(i m theta_n), one part at a time; the node is the angle itself
+    if (g.cheb_exact) {
+      // theta_n = pi (2n + 1 - N) / N: angle pi k / N with k = m (2n + 1 - N) mod 2N
+      const int64_t per = 2 * g.N;
+      int64_t num = (2 * n + 1 - g.N) % per;
+      if (num < 0) num += per;
+      for (int64_t m = m_lo; m < m_hi; ++m) {
+        int64_t mm = m % per;
+        if (mm < 0) mm += per;
+        int64_t k = mm * num % per;
+        double sign = 1.0;
+        if (k > g.N) {                                 // angle in (pi, 2 pi): sin odd
+          k = per - k;
+          sign = -1.0;
+        }
+        const double a = double(k) / double(g.N);      // in [0, 1]
+        emit(m, g.cpart ? sign * sinpi(a) : cospi(a));
+      }
+    } else {
+      for (int64_t m = m_lo; m < m_hi; ++m) {
+        double sn, c;
+        sincos(double(m) * x, &sn, &c);
+        emit(m, g.cpart ? sn : c);
+      }
+    }
+    return;
+  }
   if (is_trig(g.family)) {
     // cos(m theta), sin(m theta) or cos^s(m theta) of the row's angle
     auto finish = [&](double c, double sn) {
@@ -102,12 +140,17 @@ __device__ void gen_values(const GenParams& g, int64_t n, int64_t m_lo, int64_t 
     if (m_lo <= 0 && 0 < m_hi) emit(0, pm1);
     if (m_lo <= 1 && 1 < m_hi) emit(1, p);
     for (int64_t m = 1; m + 1 < m_hi; ++m) {
-      const double c = 2.0 * m + a + b;
-      const double a1 = 2.0 * (m + 1) * (m + a + b + 1) * c;
-      const double a2 = (c + 1) * (a * a - b * b);
-      const double a3 = c * (c + 1) * (c + 2);
-      const double a4 = 2.0 * (m + a) * (m + b) * (c + 2);
-      const double pn = ((a2 + a3 * x) * p - a4 * pm1) / a1;
+      double pn;
+      if (m < g.nrc) {
+        pn = (g.rc[3 * m] + g.rc[3 * m + 1] * x) * p - g.rc[3 * m + 2] * pm1;
+      } else {
+        const double c = 2.0 * m + a + b;
+        const double a1 = 2.0 * (m + 1) * (m + a + b + 1) * c;
+        const double a2 = (c + 1) * (a * a - b * b);
+        const double a3 = c * (c + 1) * (c + 2);
+        const double a4 = 2.0 * (m + a) * (m + b) * (c + 2);
+        pn = ((a2 + a3 * x) * p - a4 * pm1) / a1;
+      }
       pm1 = p;
       p = pn;
       if (m + 1 >= m_lo) emit(m + 1, p);
@@ -130,11 +173,17 @@ __device__ void gen_values(const GenParams& g, int64_t n, int64_t m_lo, int64_t 
     pm1 = mant;
     p = 1.4142135623730951 * x * mant;
   }
-  if (m_lo <= 0 && 0 < m_hi) emit(0, ldexp(pm1, expo));
-  if (m_lo <= 1 && 1 < m_hi) emit(1, ldexp(p, expo));
+  // values times 2^expo: one multiply while 2^expo is a normal number
+  double sc = ldexp(1.0, expo);
+  bool sc_ok = expo >= -1000 && expo <= 1000;
+  auto scaled = [&](double v) { return sc_ok ? v * sc : ldexp(v, expo); };
+  if (m_lo <= 0 && 0 < m_hi) emit(0, scaled(pm1));
+  if (m_lo <= 1 && 1 < m_hi) emit(1, scaled(p));
   for (int64_t m = 1; m + 1 < m_hi; ++m) {
     double pn;
-    if (g.family == XC_LAGUERRE_FN)
+    if (m < g.nrc)
+      pn = (g.rc[3 * m] + g.rc[3 * m + 1] * x) * p - g.rc[3 * m + 2] * pm1;
+    else if (g.family == XC_LAGUERRE_FN)
       pn = ((2.0 * m + 1.0 - x) * p - double(m) * pm1) / double(m + 1);
     else
       pn = sqrt(2.0 / double(m + 1)) * x * p - sqrt(double(m) / double(m + 1)) * pm1;
@@ -145,12 +194,16 @@ __device__ void gen_values(const GenParams& g, int64_t n, int64_t m_lo, int64_t 
       p *= 0x1p-500;
       pm1 *= 0x1p-500;
       expo += 500;
+      sc = ldexp(1.0, expo);
+      sc_ok = expo >= -1000 && expo <= 1000;
     } else if (big < 0x1p-500 && big > 0.0) {
       p *= 0x1p+500;
       pm1 *= 0x1p+500;
       expo -= 500;
+      sc = ldexp(1.0, expo);
+      sc_ok = expo >= -1000 && expo <= 1000;
     }
-    if (m + 1 >= m_lo) emit(m + 1, ldexp(p, expo));
+    if (m + 1 >= m_lo) emit(m + 1, scaled(p));
   }
 }
 
@@ -170,20 +223,20 @@ __device__ int sturm_count(const double* d, const double* e2, int64_t N, double 
   return cnt;
 }
 
-__global__ void bisect_kernel(const double* d, const double* e2, int64_t N, double lo, double hi,
-                              double* out) {
-  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  double a = lo, b = hi;
-  for (int it = 0; it < 64; ++it) {
-    const double mid = 0.5 * (a + b);
-    if (mid <= a || mid >= b) break;
-    if (sturm_count(d, e2, N, mid) > k) b = mid;
-    else a = mid;
-  }
-  out[k] = 0.5 * (a + b);
+// Sturm counts at G+1 points of [lo, hi], spaced like the zeros: uniform in
+// theta for lo + h (1 - cos(pi u)) (polynomials on [-1, 1], Hermite
+// functions), uniform in sqrt(x - lo) for the Laguerre functions, whose zeros
+// crowd near 0.  The ends are set to 0 and N: [lo, hi] strictly contains the
+// spectrum.
+__global__ void grid_count_kernel(const double* d, const double* e2, int64_t N, double lo, double hi,
+                                  int square, int64_t G, double* grid, int* counts) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i > G) return;
+  const double u = double(i) / double(G);
+  const double x = square ? lo + (hi - lo) * u * u : lo + 0.5 * (hi - lo) * (1.0 - cospi(u));
+  grid[i] = x;
+  counts[i] = i == 0 ? 0 : i == G ? int(N) : sturm_count(d, e2, N, x);
 }
-
 // (p_N, p_{N-1}) at x by the family's recurrence; a common scale factor may
 // remain (it cancels in the Newton ratio).
 __device__ void last_two(int family, int64_t N, double a, double b, double x, double* pN, double* pN1) {
@@ -234,11 +287,103 @@ __device__ double newton_ratio(int family, int64_t N, double a, double b, double
   return pN / d;
 }
 
-__global__ void newton_kernel(int family, int64_t N, double a, double b, double* x) {
+// p_N(x) / p_N'(x) for the monic polynomials of the Jacobi matrix (d, e2):
+// p_{m+1} = (x - d_m) p_m - e2_{m-1} p_{m-1}, differentiated alongside; *f
+// gets p_N up to a positive factor (both are rescaled by powers of two).
+__device__ double monic_ratio(const double* d, const double* e2, int64_t N, double x, double* f) {
+  double p0 = 0.0, p1 = 1.0, q0 = 0.0, q1 = 0.0;
+  for (int64_t m = 0; m < N; ++m) {
+    const double t = x - d[m];
+    const double e = m > 0 ? e2[m - 1] : 0.0;
+    const double p2 = t * p1 - e * p0;
+    const double q2 = p1 + t * q1 - e * q0;
+    p0 = p1; p1 = p2; q0 = q1; q1 = q2;
+    const double big = fmax(fabs(p1), fabs(q1));
+    if (big > 0x1p+500) {
+      p0 *= 0x1p-500; p1 *= 0x1p-500; q0 *= 0x1p-500; q1 *= 0x1p-500;
+    } else if (big < 0x1p-500 && big > 0.0) {
+      p0 *= 0x1p+500; p1 *= 0x1p+500; q0 *= 0x1p+500; q1 *= 0x1p+500;
+    }
+  }
+  *f = p1;
+  return p1 / q1;
+}
+
+// The k-th smallest zero: bracket it between the grid points where the Sturm
+// count passes k, bisect (Sturm counts) until the bracket holds this zero
+// alone, then Newton on the recurrence, kept inside the bracket (a step that
+// leaves it bisects instead; every iterate shrinks the bracket by the sign of
+// phi_N).  Both loops are bounded.
+__global__ void isolate_newton_kernel(const double* d, const double* e2, int64_t N, const double* grid,
+                                      const int* counts, int64_t G, double* out) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  int64_t lo = 0, hi = G;  // counts[lo] <= k < counts[hi]
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) / 2;
+    if (counts[mid] > k) hi = mid;
+    else lo = mid;
+  }
+  double a = grid[lo], b = grid[hi];
+  int ca = counts[lo], cb = counts[hi];
+  for (int it = 0; it < 64 && !(ca == k && cb == k + 1); ++it) {
+    const double mid = 0.5 * (a + b);
+    if (mid <= a || mid >= b) break;
+    const int cm = sturm_count(d, e2, N, mid);
+    if (cm > k) { b = mid; cb = cm; }
+    else { a = mid; ca = cm; }
+  }
+  double fa;
+  monic_ratio(d, e2, N, a, &fa);
+  const double tiny = 1e-6 * (b - a);  // absolute scale for a zero at x = 0
+  double x = 0.5 * (a + b);
+  bool clipped = false;
+  for (int it = 0; it < 40; ++it) {
+    double f;
+    const double r = monic_ratio(d, e2, N, x, &f);
+    if (f == 0.0) break;
+    if (fabs(r) <= 1e-10 * fmax(fabs(x), tiny)) {  // quadratic: the error is now far below rounding
+      x -= r;
+      break;
+    }
+    if ((f < 0.0) == (fa < 0.0)) a = x;
+    else b = x;
+    double xn = x - r;
+    if (!(xn > a && xn < b)) {
+      // Overshoot: try the bracket end it passed (a zero right at an end
+      // otherwise costs one bisection per bit), then bisect.
+      const double end = xn <= a ? a : b;
+      xn = (!clipped && x != end) ? end : 0.5 * (a + b);
+      clipped = !clipped && xn == end;
+    } else {
+      clipped = false;
+    }
+    x = xn;
+    if (b - a <= 4e-16 * fmax(fabs(a), fabs(b))) break;
+  }
+  out[k] = x;
+}
+
+// Zeros of the Jacobi polynomials with |alpha| = |beta| = 1/2 in closed form
+// (Chebyshev polynomials of the four kinds), ascending.
+__global__ void jacobi_half_nodes_kernel(int64_t N, double al, double be, double* x) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const double j = double(N - k);  // theta_j descending in k
+  double t;
+  if (al < 0 && be < 0) t = (2.0 * j - 1.0) / (2.0 * double(N));         // first kind
+  else if (al > 0 && be > 0) t = j / double(N + 1);                      // second kind
+  else if (al > 0) t = 2.0 * j / (2.0 * double(N) + 1.0);                // fourth kind
+  else t = (2.0 * j - 1.0) / (2.0 * double(N) + 1.0);                    // third kind
+  x[k] = cospi(t);
+}
+
+// Final Newton step(s) on the family's own recurrence.
+__global__ void newton_kernel(int family, int64_t N, double a, double b, int steps, double* x) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= N) return;
   double v = x[k];
-  for (int it = 0; it < 3; ++it) v -= newton_ratio(family, N, a, b, v);
+  for (int it = 0; it < steps; ++it) v -= newton_ratio(family, N, a, b, v);
   x[k] = v;
 }
 
@@ -671,6 +816,179 @@ __global__ void fill_adjoint_kernel(const cx<double>* S, int64_t N, int n, doubl
   store_value(val + off[s] + idx, v, pair);
 }
 
+// ---------------------------------------------------- complex families
+// Full spectrum of the complex row exp(i (j - off) theta) w_j from the half
+// spectra of its real part (Sc) and imaginary part (Ss), each the DFT of a
+// real row and so Hermitian: S_k = Sc_k + i Ss_k with Sc_{L-k} = conj(Sc_k).
+__device__ __forceinline__ cx<double> full_bin(const cx<double>* __restrict__ Sc, const cx<double>* __restrict__ Ss,
+                                               int64_t row, int n, int k) {
+  const int64_t H = n + 1;
+  cx<double> a, b;
+  if (k <= n) {
+    a = Sc[row * H + k];
+    b = Ss[row * H + k];
+  } else {
+    a = conj(Sc[row * H + (2 * n - k)]);
+    b = conj(Ss[row * H + (2 * n - k)]);
+  }
+  return cx<double>{a.re - b.im, a.im + b.re};
+}
+
+__device__ __forceinline__ double sq(cx<double> v) { return v.re * v.re + v.im * v.im; }
+
+// max |S|^2 over the block (non-negative doubles order like their bits)
+__global__ void c_max_kernel(const cx<double>* Sc, const cx<double>* Ss, int64_t N, int n,
+                             unsigned long long* maxsq_bits) {
+  const int64_t L = 2 * int64_t(n);
+  double local = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N * L; i += int64_t(gridDim.x) * blockDim.x)
+    local = fmax(local, sq(full_bin(Sc, Ss, i / L, n, int(i % L))));
+  for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxsq_bits, static_cast<unsigned long long>(__double_as_longlong(local)));
+}
+
+// Smallest circular interval [start, start + width) of 0..len-1 around the
+// reference `ref` that holds every index whose offset from ref lies in
+// [dmin, dmax] (offsets taken in [-len/2, len/2)).
+__device__ __forceinline__ int circ_offset(int64_t i, int64_t ref, int64_t len) {
+  int64_t d = (i - ref) % len;
+  if (d < 0) d += len;
+  if (d >= (len + 1) / 2) d -= len;
+  return int(d);
+}
+
+// One warp per row: the row's peak bin, then the circular band of its kept
+// bins around the peak (start k0 in [0, L), width), and the kept count.
+__global__ void c_extents_kernel(const cx<double>* Sc, const cx<double>* Ss, int64_t N, int n, double thr,
+                                 int* k0, int* width, int* count) {
+  const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= N) return;
+  const int L = 2 * n;
+  double best = -1.0;
+  int bk = 0;
+  for (int k = lane; k < L; k += 32) {
+    const double m = sq(full_bin(Sc, Ss, row, n, k));
+    if (m > best) { best = m; bk = k; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+    if (ob > best || (ob == best && ok < bk)) { best = ob; bk = ok; }
+  }
+  int dmin = INT_MAX, dmax = INT_MIN, cnt = 0;
+  for (int k = lane; k < L; k += 32) {
+    if (sq(full_bin(Sc, Ss, row, n, k)) > thr) {
+      const int d = circ_offset(k, bk, L);
+      dmin = min(dmin, d);
+      dmax = max(dmax, d);
+      ++cnt;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+    dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  if (lane == 0) {
+    k0[row] = cnt > 0 ? int(((bk + dmin) % L + L) % L) : 0;
+    width[row] = cnt > 0 ? dmax - dmin + 1 : 0;
+    count[row] = cnt;
+  }
+}
+
+// One thread per bin (consecutive bins in a warp read consecutive values):
+// the bin's peak row, then the circular run of rows around it that holds its
+// kept elements (start n0 in [0, N), width).
+__global__ void c_col_extents_kernel(const cx<double>* Sc, const cx<double>* Ss, int64_t N, int n, double thr,
+                                     int* n0, int* width) {
+  const int k = int(int64_t(blockIdx.x) * blockDim.x + threadIdx.x);
+  if (k >= 2 * n) return;
+  double best = -1.0;
+  int64_t br = 0;
+  for (int64_t r = 0; r < N; ++r) {
+    const double m = sq(full_bin(Sc, Ss, r, n, k));
+    if (m > best) { best = m; br = r; }
+  }
+  int dmin = INT_MAX, dmax = INT_MIN;
+  for (int64_t r = 0; r < N; ++r) {
+    if (sq(full_bin(Sc, Ss, r, n, k)) > thr) {
+      const int d = circ_offset(r, br, N);
+      dmin = min(dmin, d);
+      dmax = max(dmax, d);
+    }
+  }
+  const bool any = dmax >= dmin;
+  n0[k] = any ? int(((br + dmin) % N + N) % N) : 0;
+  width[k] = any ? dmax - dmin + 1 : 0;
+}
+
+// Band values of the complex block, forward layout: slice s, band position j,
+// lane -> row 32 s + lane, bin (k0 + j) mod L; zero outside the row's band or
+// where the element is dropped.
+template <typename T>
+__global__ void c_fill_forward_kernel(const cx<double>* Sc, const cx<double>* Ss, int64_t N, int n, double thr,
+                                      const int* k0, const int* rwidth, const int* width, const int64_t* off,
+                                      int nslices, cx<T>* val) {
+  const int s = blockIdx.y;
+  if (s >= nslices) return;
+  const int W = width[s];
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;   // j * 32 + lane
+  if (idx >= int64_t(W) * 32) return;
+  const int lane = int(idx & 31);
+  const int j = int(idx >> 5);
+  const int64_t row = int64_t(s) * 32 + lane;
+  cx<double> v{0.0, 0.0};
+  if (row < N && j < rwidth[row]) {
+    const int L = 2 * n;
+    const int k = (k0[row] + j) % L;
+    const cx<double> a = full_bin(Sc, Ss, row, n, k);
+    if (sq(a) > thr) v = a;
+  }
+  val[off[s] + idx] = cx<T>{T(v.re), T(v.im)};
+}
+
+// Transposed band values: slice s of bins, lane -> bin 32 s + lane, row
+// (n0 + i) mod N.
+template <typename T>
+__global__ void c_fill_adjoint_kernel(const cx<double>* Sc, const cx<double>* Ss, int64_t N, int n, double thr,
+                                      const int* n0, const int* bwidth, const int* width, const int64_t* off,
+                                      int tslices, cx<T>* val) {
+  const int s = blockIdx.y;
+  if (s >= tslices) return;
+  const int W = width[s];
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;   // i * 32 + lane
+  if (idx >= int64_t(W) * 32) return;
+  const int lane = int(idx & 31);
+  const int i = int(idx >> 5);
+  const int k = s * 32 + lane;
+  cx<double> v{0.0, 0.0};
+  if (k < 2 * n && i < bwidth[k]) {
+    const int64_t row = (int64_t(n0[k]) + i) % N;
+    const cx<double> a = full_bin(Sc, Ss, row, n, k);
+    if (sq(a) > thr) v = a;
+  }
+  val[off[s] + idx] = cx<T>{T(v.re), T(v.im)};
+}
+
+// The plain complex matrix (comparison path): one thread per element, the
+// row factor of the spectral Laguerre matrix included.
+template <typename T>
+__global__ void c_dense_kernel(GenParams g, const cx<T>* rowscale, cx<T>* A, int64_t lda) {
+  const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t n = blockIdx.y;
+  if (m >= g.N || n >= g.N) return;
+  double re = 0.0, im = 0.0;
+  GenParams gc = g;
+  gc.cpart = 0;
+  gen_values(gc, n, m, m + 1, [&](int64_t, double v) { re = v; });
+  gc.cpart = 1;
+  gen_values(gc, n, m, m + 1, [&](int64_t, double v) { im = v; });
+  cx<T> a{T(re), T(im)};
+  if (rowscale) a = cmul(rowscale[n], a);
+  A[n * lda + m] = a;
+}
+
 // Dense tail [m][N] and the plain matrix (comparison path).
 template <typename T>
 __global__ void tail_kernel(GenParams g, int64_t m_tail, T* tail) {
@@ -714,7 +1032,19 @@ __global__ void dense_kernel(GenParams g, const T* rowscale, const T* colscale, 
 // The plain N x N matrix with the plan's normalisation (comparison path).
 int dense_matrix_device(const Plan* p, void* A, int64_t lda, cudaStream_t s) {
   GenParams g{p->family, p->N, p->params.alpha, p->params.beta, p->nodes_dev,
-              is_trig(p->family) && p->params.nodes == XC_NODES_GAUSS, p->params.power};
+              is_trig(p->family) && p->family != XC_LAGUERRE_SPECTRAL && p->params.nodes == XC_NODES_GAUSS,
+              p->params.power, p->rc_dev, p->nrc};
+  if (p->cplx) {
+    const dim3 grid(unsigned((p->N + 127) / 128), unsigned(p->N));
+    if (p->io64())
+      c_dense_kernel<double><<<grid, 128, 0, s>>>(g, static_cast<const cx<double>*>(p->rowscale),
+                                                   static_cast<cx<double>*>(A), lda);
+    else
+      c_dense_kernel<float><<<grid, 128, 0, s>>>(g, static_cast<const cx<float>*>(p->rowscale),
+                                                  static_cast<cx<float>*>(A), lda);
+    XC_CUDA(cudaGetLastError());
+    return XC_OK;
+  }
   const unsigned grid = unsigned((p->N + 31) / 32);
   if (p->io64())
     dense_kernel<double><<<grid, 32, 0, s>>>(g, static_cast<const double*>(p->rowscale),
@@ -743,7 +1073,10 @@ void jacobi_matrix(int family, int64_t N, double a, double b, std::vector<double
     } else if (family == XC_JACOBI) {
       const double c = 2.0 * kk + a + b;
       (*d)[k] = k == 0 ? (b - a) / (a + b + 2.0) : (b * b - a * a) / (c * (c + 2.0));
-      if (k >= 1) (*e2)[k - 1] = 4.0 * kk * (kk + a) * (kk + b) * (kk + a + b) / (c * c * (c + 1.0) * (c - 1.0));
+      if (k == 1)  // the factor 1 + a + b cancelled (0/0 when a + b = -1)
+        (*e2)[0] = 4.0 * (1.0 + a) * (1.0 + b) / ((2.0 + a + b) * (2.0 + a + b) * (3.0 + a + b));
+      else if (k > 1)
+        (*e2)[k - 1] = 4.0 * kk * (kk + a) * (kk + b) * (kk + a + b) / (c * c * (c + 1.0) * (c - 1.0));
     } else if (family == XC_LAGUERRE_FN) {
       (*d)[k] = 2.0 * kk + 1.0;
       if (k >= 1) (*e2)[k - 1] = kk * kk;
@@ -752,6 +1085,37 @@ void jacobi_matrix(int family, int64_t N, double a, double b, std::vector<double
       if (k >= 1) (*e2)[k - 1] = kk / 2.0;
     }
   }
+}
+
+// Coefficients (alpha_m, beta_m, gamma_m) of phi_{m+1} = (alpha_m + beta_m x)
+// phi_m - gamma_m phi_{m-1}, m = 1..M-1, of the one-sided families: the
+// three-term recurrences of the Jacobi polynomials, the Laguerre polynomials
+// and the normalised Hermite functions with their divisions done once.
+std::vector<double> recurrence_table(int family, double a, double b, int64_t M) {
+  std::vector<double> t(size_t(3 * M), 0.0);
+  for (int64_t m = 1; m < M; ++m) {
+    const double mm = double(m);
+    double al, be, ga;
+    if (family == XC_LEGENDRE || family == XC_JACOBI) {
+      const double c = 2.0 * mm + a + b;
+      const double a1 = 2.0 * (mm + 1) * (mm + a + b + 1) * c;
+      al = (c + 1) * (a * a - b * b) / a1;
+      be = c * (c + 1) * (c + 2) / a1;
+      ga = 2.0 * (mm + a) * (mm + b) * (c + 2) / a1;
+    } else if (family == XC_LAGUERRE_FN) {
+      al = (2.0 * mm + 1.0) / (mm + 1.0);
+      be = -1.0 / (mm + 1.0);
+      ga = mm / (mm + 1.0);
+    } else {
+      al = 0.0;
+      be = std::sqrt(2.0 / (mm + 1.0));
+      ga = std::sqrt(mm / (mm + 1.0));
+    }
+    t[size_t(3 * m)] = al;
+    t[size_t(3 * m + 1)] = be;
+    t[size_t(3 * m + 2)] = ga;
+  }
+  return t;
 }
 
 // Digit-reversed position of each input index (see xc_fft.cuh).
@@ -884,8 +1248,9 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
     else XC_TRY(set_smem(reinterpret_cast<const void*>(row_fft_cluster_kernel), csmem));
     for (int64_t row0 = 0; row0 < N; row0 += C) {
       const int64_t rows = std::min<int64_t>(C, N - row0);
-      gen_rows_kernel<<<unsigned((rows + 127) / 128), 128>>>(g, row0, C, b.L, b.off, static_cast<double*>(w64.ptr),
-                                                             static_cast<double*>(Gbuf.ptr));
+      // one thread per row, 32 per CTA so that the rows spread over every SM
+      gen_rows_kernel<<<unsigned((rows + 31) / 32), 32>>>(g, row0, C, b.L, b.off, static_cast<double*>(w64.ptr),
+                                                          static_cast<double*>(Gbuf.ptr));
       if (csize == 1) {
         row_fft_kernel<<<unsigned(rows), 256, smem>>>(static_cast<double*>(Gbuf.ptr), C, row0, N, b,
                                                        static_cast<cx<double>*>(tw64.ptr),
@@ -1108,6 +1473,187 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
   return XC_OK;
 }
 
+// The single two-sided block of a complex family (Section 2.2 with a complex
+// matrix): the extended rows exp(i (j - off) theta_n) w_j are transformed as
+// their real and imaginary parts (two real row FFTs), which give the full
+// spectrum S = A_e W F / sqrt(L) (up to the 1/sqrt(L) the apply folds in);
+// each row keeps one circular band around its peak bin theta_n L / (2 pi),
+// each bin one circular run of rows.
+template <typename T>
+int build_block_complex(Plan* p, const GenParams& g, const BlockShape& shp) {
+  BlockDev& b = p->blocks[0];
+  std::memset(&b, 0, sizeof(b));
+  const int64_t N = p->N;
+  b.L = int(shp.L);
+  b.n = int(shp.L / 2);
+  b.H = b.n + 1;
+  b.off = int(shp.off);
+  b.j_lo = int(shp.j_lo);
+  b.j_hi = int(shp.j_hi);
+  b.a_csize = 1;
+  b.p = fft_radices(b.n, b.radix);
+  if (b.p < 0) return fail(XC_ERR_UNSUPPORTED, "FFT length not 2^a 3^b 5^c 7^d");
+  const int n = b.n, H = b.H, L = b.L;
+  int dev = 0, optin = 0;
+  XC_CUDA(cudaGetDevice(&dev));
+  XC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t smem = size_t(n) * sizeof(cx<double>);
+  if (smem + 1024 > size_t(optin) || size_t(L) * sizeof(cx<T>) + 1024 > size_t(optin))
+    return fail(XC_ERR_UNSUPPORTED, "complex block length L = " + std::to_string(L) +
+                                        " exceeds one CTA's shared memory");
+  std::vector<int> perm = digit_reversal(n, b.p, b.radix);
+  int* perm_d = nullptr;
+  XC_TRY(upload(p, perm, &perm_d));
+  b.perm = perm_d;
+  DevBuf w64;
+  XC_TRY(alloc_tmp(&w64, size_t(L) * sizeof(double)));
+  void *invw = nullptr, *tw = nullptr;
+  XC_TRY(plan_alloc(p, &invw, size_t(L) * sizeof(T)));
+  XC_TRY(plan_alloc(p, &tw, size_t(L) * sizeof(cx<T>)));
+  const unsigned gL = unsigned((L + 255) / 256);
+  window_kernel<T><<<gL, 256>>>(L, p->zeta, static_cast<double*>(w64.ptr), static_cast<T*>(invw));
+  twiddle_kernel<T><<<gL, 256>>>(L, static_cast<cx<T>*>(tw));
+  b.invw = invw;
+  b.tw = tw;
+  DevBuf tw64;
+  XC_TRY(alloc_tmp(&tw64, size_t(L) * sizeof(cx<double>)));
+  twiddle_kernel<double><<<gL, 256>>>(L, static_cast<cx<double>*>(tw64.ptr));
+  XC_CUDA(cudaGetLastError());
+
+  // half spectra of the real and imaginary parts of every row
+  const size_t s_bytes = size_t(N) * size_t(H) * sizeof(cx<double>);
+  if (2 * s_bytes > (size_t(64) << 30)) return fail(XC_ERR_UNSUPPORTED, "compressed block exceeds 64 GiB during precompute");
+  DevBuf Sc, Ss, maxbuf;
+  XC_TRY(alloc_tmp(&Sc, s_bytes));
+  XC_TRY(alloc_tmp(&Ss, s_bytes));
+  XC_TRY(alloc_tmp(&maxbuf, sizeof(unsigned long long)));
+  XC_TRY(set_smem(reinterpret_cast<const void*>(row_fft_kernel), smem));
+  {
+    const int64_t C = std::max<int64_t>(1, std::min<int64_t>(N, (int64_t(1) << 30) / (int64_t(L) * 8)));
+    DevBuf Gbuf;
+    XC_TRY(alloc_tmp(&Gbuf, size_t(C) * size_t(L) * sizeof(double)));
+    for (int part = 0; part < 2; ++part) {
+      GenParams gp = g;
+      gp.cpart = part;
+      cx<double>* S = static_cast<cx<double>*>(part == 0 ? Sc.ptr : Ss.ptr);
+      for (int64_t row0 = 0; row0 < N; row0 += C) {
+        const int64_t rows = std::min<int64_t>(C, N - row0);
+        gen_rows_kernel<<<unsigned((rows + 31) / 32), 32>>>(gp, row0, C, L, b.off, static_cast<double*>(w64.ptr),
+                                                            static_cast<double*>(Gbuf.ptr));
+        row_fft_kernel<<<unsigned(rows), 256, smem>>>(static_cast<double*>(Gbuf.ptr), C, row0, N, b,
+                                                       static_cast<cx<double>*>(tw64.ptr), S,
+                                                       static_cast<unsigned long long*>(maxbuf.ptr));
+        XC_CUDA(cudaGetLastError());
+      }
+    }
+  }
+  const cx<double>* scp = static_cast<const cx<double>*>(Sc.ptr);
+  const cx<double>* ssp = static_cast<const cx<double>*>(Ss.ptr);
+  XC_CUDA(cudaMemset(maxbuf.ptr, 0, sizeof(unsigned long long)));
+  c_max_kernel<<<unsigned(std::min<int64_t>(152 * 16, (N * L + 255) / 256)), 256>>>(
+      scp, ssp, N, n, static_cast<unsigned long long*>(maxbuf.ptr));
+  XC_CUDA(cudaGetLastError());
+  unsigned long long bits = 0;
+  double maxsq = 0.0;
+  XC_CUDA(cudaMemcpy(&bits, maxbuf.ptr, sizeof(bits), cudaMemcpyDeviceToHost));
+  std::memcpy(&maxsq, &bits, sizeof(maxsq));
+  const double thr = p->eps > 0 ? (p->eps * p->eps) * maxsq : -1.0;
+  p->maxabs[0] = std::sqrt(maxsq);
+
+  // circular row bands and bin runs
+  DevBuf k0d, rwd, cntd, n0d, bwd;
+  XC_TRY(alloc_tmp(&k0d, size_t(N) * sizeof(int)));
+  XC_TRY(alloc_tmp(&rwd, size_t(N) * sizeof(int)));
+  XC_TRY(alloc_tmp(&cntd, size_t(N) * sizeof(int)));
+  XC_TRY(alloc_tmp(&n0d, size_t(L) * sizeof(int)));
+  XC_TRY(alloc_tmp(&bwd, size_t(L) * sizeof(int)));
+  c_extents_kernel<<<unsigned((N * 32 + 255) / 256), 256>>>(scp, ssp, N, n, thr, static_cast<int*>(k0d.ptr),
+                                                            static_cast<int*>(rwd.ptr), static_cast<int*>(cntd.ptr));
+  c_col_extents_kernel<<<unsigned((L + 127) / 128), 128>>>(scp, ssp, N, n, thr, static_cast<int*>(n0d.ptr),
+                                                           static_cast<int*>(bwd.ptr));
+  XC_CUDA(cudaGetLastError());
+  std::vector<int> k0(N), rw(N), cnt(N), bw(L), n0(L);
+  XC_CUDA(cudaMemcpy(k0.data(), k0d.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
+  XC_CUDA(cudaMemcpy(rw.data(), rwd.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
+  XC_CUDA(cudaMemcpy(cnt.data(), cntd.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
+  XC_CUDA(cudaMemcpy(n0.data(), n0d.ptr, size_t(L) * sizeof(int), cudaMemcpyDeviceToHost));
+  XC_CUDA(cudaMemcpy(bw.data(), bwd.ptr, size_t(L) * sizeof(int), cudaMemcpyDeviceToHost));
+  int64_t nnz = 0;
+  for (int64_t r = 0; r < N; ++r) nnz += cnt[r];
+  p->nnz[0] = nnz;
+
+  // forward: slices of 32 rows, width = widest band of the slice
+  const int nslices = int((N + kSlice - 1) / kSlice);
+  std::vector<int> fwidth(nslices, 0);
+  std::vector<int64_t> foff(nslices, 0);
+  int64_t total = 0;
+  int vpad = 0;
+  for (int sl = 0; sl < nslices; ++sl) {
+    int W = 0;
+    for (int l = 0; l < kSlice; ++l) {
+      const int64_t r = int64_t(sl) * kSlice + l;
+      if (r < N) W = std::max(W, rw[r]);
+    }
+    fwidth[sl] = W;
+    foff[sl] = total;
+    total += int64_t(W) * kSlice;
+    vpad = std::max(vpad, W);
+  }
+  p->stored[0] = total;
+  p->c_vpad = vpad;
+  // adjoint: slices of 32 bins, width = longest run of the slice
+  const int tslices = (L + kSlice - 1) / kSlice;
+  std::vector<int> twidth(tslices, 0);
+  std::vector<int64_t> toff(tslices, 0);
+  int64_t ttotal = 0;
+  for (int sl = 0; sl < tslices; ++sl) {
+    int W = 0;
+    for (int l = 0; l < kSlice; ++l) {
+      const int k = sl * kSlice + l;
+      if (k < L) W = std::max(W, bw[k]);
+    }
+    twidth[sl] = W;
+    toff[sl] = ttotal;
+    ttotal += int64_t(W) * kSlice;
+  }
+  int *fk0_d, *fw_d, *tn0_d, *tw_d;
+  int64_t *foff_d, *toff_d;
+  XC_TRY(upload(p, k0, &fk0_d));
+  XC_TRY(upload(p, fwidth, &fw_d));
+  XC_TRY(upload(p, foff, &foff_d));
+  XC_TRY(upload(p, n0, &tn0_d));
+  XC_TRY(upload(p, twidth, &tw_d));
+  XC_TRY(upload(p, toff, &toff_d));
+  void *fval = nullptr, *tval = nullptr;
+  XC_TRY(plan_alloc(p, &fval, size_t(std::max<int64_t>(1, total)) * sizeof(cx<T>)));
+  XC_TRY(plan_alloc(p, &tval, size_t(std::max<int64_t>(1, ttotal)) * sizeof(cx<T>)));
+  int maxW = 0, maxTW = 0;
+  for (int w : fwidth) maxW = std::max(maxW, w);
+  for (int w : twidth) maxTW = std::max(maxTW, w);
+  if (maxW > 0)
+    c_fill_forward_kernel<T><<<dim3(unsigned((int64_t(maxW) * 32 + 255) / 256), unsigned(nslices)), 256>>>(
+        scp, ssp, N, n, thr, fk0_d, static_cast<int*>(rwd.ptr), fw_d, foff_d, nslices, static_cast<cx<T>*>(fval));
+  if (maxTW > 0)
+    c_fill_adjoint_kernel<T><<<dim3(unsigned((int64_t(maxTW) * 32 + 255) / 256), unsigned(tslices)), 256>>>(
+        scp, ssp, N, n, thr, tn0_d, static_cast<int*>(bwd.ptr), tw_d, toff_d, tslices, static_cast<cx<T>*>(tval));
+  XC_CUDA(cudaGetLastError());
+  XC_CUDA(cudaDeviceSynchronize());
+  b.nslices = nslices;
+  b.f_k0 = fk0_d;
+  b.f_width = fw_d;
+  b.f_off = foff_d;
+  b.f_val = fval;
+  b.tslices = tslices;
+  b.t_n0 = tn0_d;
+  b.t_width = tw_d;
+  b.t_off = toff_d;
+  b.t_val = tval;
+  b.spec_off = 0;
+  p->matrix_bytes += total * int64_t(sizeof(cx<T>)) + int64_t(N) * 4;
+  p->adjoint_bytes += ttotal * int64_t(sizeof(cx<T>)) + int64_t(L) * 4;
+  return XC_OK;
+}
+
 }  // namespace
 
 int build_plan_device(Plan* p) {
@@ -1115,7 +1661,22 @@ int build_plan_device(Plan* p) {
   const unsigned gN = unsigned((N + 127) / 128);
   XC_TRY(plan_alloc(p, reinterpret_cast<void**>(&p->nodes_dev), size_t(N) * sizeof(double)));
   const bool user = p->params.nodes == XC_NODES_USER;
-  if (user) {
+  if (p->cplx) {
+    // the nodes of the complex families are angles: the arc midpoints
+    // (2n + 1 - N) pi / N, the caller's angles, or the psi_j of the spectral
+    // Laguerre matrix, 2 arctan(2 k_j / eta) - pi with k_j = 2 pi j / T
+    if (p->family == XC_LAGUERRE_SPECTRAL) {
+      p->nodes_host.resize(N);
+      for (int64_t j = 0; j < N; ++j) {
+        const double k = 2.0 * 3.141592653589793 * double(j) / p->params.beta;
+        p->nodes_host[j] = 2.0 * std::atan(2.0 * k / p->params.alpha) - 3.141592653589793;
+      }
+    } else if (!user) {
+      p->nodes_host.resize(N);
+      for (int64_t j = 0; j < N; ++j) p->nodes_host[j] = 3.141592653589793 * double(2 * j + 1 - N) / double(N);
+    }
+    XC_CUDA(cudaMemcpy(p->nodes_dev, p->nodes_host.data(), size_t(N) * sizeof(double), cudaMemcpyHostToDevice));
+  } else if (user) {
     XC_CUDA(cudaMemcpy(p->nodes_dev, p->nodes_host.data(), size_t(N) * sizeof(double), cudaMemcpyHostToDevice));
   } else if (is_trig(p->family)) {
     cheb_nodes_kernel<<<gN, 128>>>(N, p->nodes_dev);
@@ -1128,13 +1689,32 @@ int build_plan_device(Plan* p) {
       lo = std::min(lo, d[k] - r);
       hi = std::max(hi, d[k] + r);
     }
-    DevBuf dd, de;
-    XC_TRY(alloc_tmp(&dd, d.size() * sizeof(double)));
-    XC_TRY(alloc_tmp(&de, e2.size() * sizeof(double)));
-    XC_CUDA(cudaMemcpy(dd.ptr, d.data(), d.size() * sizeof(double), cudaMemcpyHostToDevice));
-    XC_CUDA(cudaMemcpy(de.ptr, e2.data(), e2.size() * sizeof(double), cudaMemcpyHostToDevice));
-    bisect_kernel<<<gN, 128>>>(static_cast<double*>(dd.ptr), static_cast<double*>(de.ptr), N, lo, hi, p->nodes_dev);
-    newton_kernel<<<gN, 128>>>(p->family, N, p->params.alpha, p->params.beta, p->nodes_dev);
+    const double al = p->params.alpha, be = p->params.beta;
+    if (p->family == XC_JACOBI && std::fabs(al) == 0.5 && std::fabs(be) == 0.5) {
+      jacobi_half_nodes_kernel<<<gN, 128>>>(N, al, be, p->nodes_dev);
+    } else {
+      const double pad = 1e-3 * (hi - lo) + 1e-300;
+      lo -= pad;
+      hi += pad;
+      const int64_t G = 4 * N;
+      DevBuf dd, de, grid, counts;
+      XC_TRY(alloc_tmp(&dd, d.size() * sizeof(double)));
+      XC_TRY(alloc_tmp(&de, e2.size() * sizeof(double)));
+      XC_TRY(alloc_tmp(&grid, size_t(G + 1) * sizeof(double)));
+      XC_TRY(alloc_tmp(&counts, size_t(G + 1) * sizeof(int)));
+      XC_CUDA(cudaMemcpy(dd.ptr, d.data(), d.size() * sizeof(double), cudaMemcpyHostToDevice));
+      XC_CUDA(cudaMemcpy(de.ptr, e2.data(), e2.size() * sizeof(double), cudaMemcpyHostToDevice));
+      const double* dp = static_cast<double*>(dd.ptr);
+      const double* ep = static_cast<double*>(de.ptr);
+      double* gp = static_cast<double*>(grid.ptr);
+      int* cp = static_cast<int*>(counts.ptr);
+      grid_count_kernel<<<unsigned((G + 128) / 128), 128>>>(dp, ep, N, lo, hi, p->family == XC_LAGUERRE_FN, G, gp,
+                                                            cp);
+      isolate_newton_kernel<<<gN, 128>>>(dp, ep, N, gp, cp, G, p->nodes_dev);
+      XC_CUDA(cudaGetLastError());
+      XC_CUDA(cudaDeviceSynchronize());
+    }
+    newton_kernel<<<gN, 128>>>(p->family, N, al, be, 1, p->nodes_dev);
     XC_CUDA(cudaGetLastError());
     XC_CUDA(cudaDeviceSynchronize());
   }
@@ -1142,8 +1722,51 @@ int build_plan_device(Plan* p) {
   p->nodes_host.resize(N);
   XC_CUDA(cudaMemcpy(p->nodes_host.data(), p->nodes_dev, size_t(N) * sizeof(double), cudaMemcpyDeviceToHost));
 
-  GenParams g{p->family, N, p->params.alpha, p->params.beta, p->nodes_dev, is_trig(p->family) && !user,
-              p->params.power};
+  GenParams g{p->family, N, p->params.alpha, p->params.beta, p->nodes_dev,
+              is_trig(p->family) && p->family != XC_LAGUERRE_SPECTRAL && !user, p->params.power};
+  if (p->cplx) {
+    const bool fp64c = p->io64();
+    if (p->family == XC_LAGUERRE_SPECTRAL) {
+      // row factor 1 / (eta/2 - i k_j) = (eta/2 + i k_j) / ((eta/2)^2 + k_j^2)
+      std::vector<double> rf(size_t(2 * N));
+      const double h = 0.5 * p->params.alpha;
+      for (int64_t j = 0; j < N; ++j) {
+        const double k = 2.0 * 3.141592653589793 * double(j) / p->params.beta;
+        const double d = h * h + k * k;
+        rf[size_t(2 * j)] = h / d;
+        rf[size_t(2 * j + 1)] = k / d;
+      }
+      XC_TRY(plan_alloc(p, &p->rowscale, size_t(N) * 2 * p->elem_bytes()));
+      if (fp64c) {
+        XC_CUDA(cudaMemcpy(p->rowscale, rf.data(), rf.size() * sizeof(double), cudaMemcpyHostToDevice));
+      } else {
+        std::vector<float> rff(rf.begin(), rf.end());
+        XC_CUDA(cudaMemcpy(p->rowscale, rff.data(), rff.size() * sizeof(float), cudaMemcpyHostToDevice));
+      }
+    }
+    p->blocks.resize(1);
+    p->nnz.assign(1, 0);
+    p->stored.assign(1, 0);
+    p->maxabs.assign(1, 0.0);
+    if (fp64c) XC_TRY(build_block_complex<double>(p, g, p->sch.blocks[0]));
+    else XC_TRY(build_block_complex<float>(p, g, p->sch.blocks[0]));
+    p->spec_per_rhs = p->blocks[0].L + p->c_vpad;
+    p->max_n = p->blocks[0].n;
+    p->m_tail = 0;
+    return XC_OK;
+  }
+  if (!is_trig(p->family)) {
+    // recurrence coefficients for every degree the rows, weights and dense
+    // comparison reach
+    int64_t M = N + 2;
+    for (const auto& shp : p->sch.blocks) M = std::max<int64_t>(M, int64_t(shp.L) - int64_t(shp.off));
+    const std::vector<double> rc = recurrence_table(p->family, p->params.alpha, p->params.beta, M + 1);
+    XC_TRY(plan_alloc(p, reinterpret_cast<void**>(&p->rc_dev), rc.size() * sizeof(double)));
+    XC_CUDA(cudaMemcpy(p->rc_dev, rc.data(), rc.size() * sizeof(double), cudaMemcpyHostToDevice));
+    p->nrc = M + 1;
+    g.rc = p->rc_dev;
+    g.nrc = p->nrc;
+  }
   const bool fp64 = p->io64();
   if (p->normalise == XC_ORTHONORMAL) {
     DevBuf lam;

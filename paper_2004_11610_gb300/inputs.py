@@ -40,6 +40,12 @@ def normal(n: int, nrhs: int, *offsets: int) -> np.ndarray:
     return rng(*offsets).standard_normal(size=(nrhs, n))
 
 
+def complex_normal(n: int, nrhs: int, *offsets: int) -> np.ndarray:
+    """nrhs complex vectors whose real and imaginary parts are i.i.d. standard
+    normal (the imaginary parts from the stream offset by 1000)."""
+    return normal(n, nrhs, *offsets) + 1j * normal(n, nrhs, *(tuple(offsets) + (1000,)))
+
+
 # Named workloads.  Each entry gives the plans (family, N, parameters), the
 # tolerance threshold eps, the precision of the apply, the number of
 # right-hand sides and the input distribution.

@@ -20,7 +20,9 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 # ------------------------------------------------------------------ constants
 XC_OK, XC_ERR_ARG, XC_ERR_ALLOC, XC_ERR_CUDA, XC_ERR_TIMEOUT, XC_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
-FAMILY = {"chebyshev": 0, "legendre": 1, "jacobi": 2, "laguerre": 3, "hermite": 4, "sine": 5, "cospow": 6}
+FAMILY = {"chebyshev": 0, "legendre": 1, "jacobi": 2, "laguerre": 3, "hermite": 4, "sine": 5, "cospow": 6,
+          "exp": 7, "lagspec": 8}
+COMPLEX_FAMILIES = ("exp", "lagspec")
 PRECISION = {"fp64": 0, "fp32": 1, "fp32c": 2, "fp64pair": 3}
 SCHEME = {"auto": 0, "two_sided": 1, "blocks": 2}
 XC_MAX_BLOCKS = 16
@@ -120,19 +122,26 @@ def _stream_handle(stream=None):
 class Plan:
     """A compressed operator for A[n, m] = phi_m(x_n) (xc_plan_create).
 
-    family     'chebyshev' | 'legendre' | 'jacobi' | 'laguerre' | 'hermite'
+    family     'chebyshev' | 'legendre' | 'jacobi' | 'laguerre' | 'hermite' | 'sine' | 'cospow'
+               | 'exp' | 'lagspec' (the last two complex: complex128 / complex64 tensors)
     N          order of the square matrix
     eps        eps1: threshold and Kaiser shape (0 keeps every element)
-    precision  'fp64' | 'fp32' | 'fp32c' (FP32 with compensated accumulation)
-    nodes      optional host array of N nodes (default: the family's Gauss nodes)
+    precision  'fp64' | 'fp32' | 'fp32c' (FP32 with compensated accumulation) | 'fp64pair'
+    nodes      optional host array of N nodes (default: the family's Gauss nodes;
+               'exp': angles)
+    eta, period  the spectral Laguerre matrix's eta and T (stored as alpha, beta)
     """
 
     def __init__(self, family: str, N: int, eps: float, precision: str = "fp64", alpha: float = 0.0,
                  beta: float = 0.0, nodes=None, normalise: bool = False, eps2: float = 0.0,
                  eps_window: float = 0.0, scheme: str = "auto", tail_max: int = 0, precompute: str = "auto",
-                 power: int = 0):
+                 power: int = 0, eta: float | None = None, period: float | None = None):
         p = xc_params()
         _lib.xc_params_default(ctypes.byref(p))
+        if eta is not None:
+            alpha = eta
+        if period is not None:
+            beta = period
         p.alpha, p.beta = float(alpha), float(beta)
         self._nodes_keep = None
         if nodes is not None:
@@ -154,7 +163,12 @@ class Plan:
                "xc_plan_create")
         self._h = h
         self.family, self.N, self.eps, self.precision = family, int(N), float(eps), precision
-        self.np_dtype = np.float64 if precision in ("fp64", "fp64pair") else np.float32
+        self.is_complex = family in COMPLEX_FAMILIES
+        wide = precision in ("fp64", "fp64pair")
+        if self.is_complex:
+            self.np_dtype = np.complex128 if wide else np.complex64
+        else:
+            self.np_dtype = np.float64 if wide else np.float32
 
     # -- lifetime
     def close(self) -> None:
@@ -181,7 +195,10 @@ class Plan:
     @property
     def torch_dtype(self):
         import torch
-        return torch.float64 if self.precision in ("fp64", "fp64pair") else torch.float32
+        wide = self.precision in ("fp64", "fp64pair")
+        if self.is_complex:
+            return torch.complex128 if wide else torch.complex64
+        return torch.float64 if wide else torch.float32
 
     # -- queries
     def info(self) -> dict:
@@ -210,6 +227,8 @@ class Plan:
         import torch
         if not t.is_cuda or t.dtype != self.torch_dtype:
             raise TypeError(f"{name} must be a CUDA tensor of dtype {self.torch_dtype}")
+        if t.is_complex() and t.is_conj():
+            raise ValueError(f"{name} has PyTorch's lazy conjugate bit set: pass t.resolve_conj()")
         if t.dim() != 2 or t.shape[1] != self.N or t.stride(1) != 1:
             raise ValueError(f"{name} must have shape (nrhs, N) with unit column stride")
         return t
@@ -224,7 +243,8 @@ class Plan:
         return y
 
     def apply_adjoint(self, y, out=None, stream=None):
-        """x = A^T y for y of shape (nrhs, N) (xc_apply_adjoint)."""
+        """x = A^T y for y of shape (nrhs, N) (xc_apply_adjoint; the plain
+        transpose for the complex families)."""
         import torch
         y = self._check_tensor(y if y.dim() == 2 else y[None, :], "y")
         x = torch.empty_like(y) if out is None else self._check_tensor(out, "out")
@@ -348,7 +368,9 @@ def _autograd():
     import torch
 
     class XcApply(torch.autograd.Function):
-        """y = A x with dy/dx^T g = A^T g (the hand-written adjoint apply)."""
+        """y = A x with the gradient A^T g (the hand-written adjoint apply);
+        complex plans: A^H g = conj(A^T conj(g)), PyTorch's convention for the
+        gradient of a complex linear map."""
 
         @staticmethod
         def forward(ctx, x, plan):
@@ -357,6 +379,8 @@ def _autograd():
 
         @staticmethod
         def backward(ctx, g):
+            if ctx.plan.is_complex:   # conj_physical: the kernels read memory, not the conj bit
+                return torch.conj_physical(ctx.plan.apply_adjoint(torch.conj_physical(g).contiguous())), None
             return ctx.plan.apply_adjoint(g.contiguous()), None
 
     return XcApply

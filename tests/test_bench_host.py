@@ -81,3 +81,8 @@ def test_work_model_covers_every_kernel_the_library_times():
     for chunked in (False, True):
         work = bench.algorithmic_work(info, 4, "fp32", chunked)
         assert set(names) <= set(work), set(names) - set(work)
+    # complex families run the FFT, band and row-scale kernels
+    cinfo = {"nnz": [900], "N": 64, "m_tail": 0, "L": [80], "family": 8}
+    work = bench.algorithmic_work(cinfo, 4, "fp64")
+    assert {"fwd_fft", "fwd_sparse", "adj_sparse", "adj_fft", "row_scale"} <= set(work)
+    assert work["fwd_sparse"][0] == 8.0 * 900 * 4

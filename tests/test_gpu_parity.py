@@ -222,6 +222,23 @@ def test_gauss_nodes_match_oracle(xc):
         assert np.all(np.abs(x - sp.x) <= tol), fam
 
 
+@pytest.mark.parametrize("fam,N,alpha,beta", [
+    ("legendre", 4096, 0.0, 0.0), ("legendre", 4097, 0.0, 0.0), ("jacobi", 3000, 0.3, -0.7),
+    ("jacobi", 2000, 2.5, 1.0), ("jacobi", 1500, -0.5, 0.5), ("jacobi", 1500, 0.5, 0.5),
+    ("jacobi", 1500, -0.5, -0.5), ("jacobi", 1200, -0.3, -0.7), ("laguerre", 4096, 0.0, 0.0), ("hermite", 4096, 0.0, 0.0),
+    ("hermite", 4095, 0.0, 0.0), ("legendre", 2, 0.0, 0.0), ("laguerre", 2, 0.0, 0.0), ("hermite", 3, 0.0, 0.0)])
+def test_gauss_nodes_of_every_kind_match_oracle(xc, fam, N, alpha, beta):
+    """Nodes from the Sturm-count grid and bracketed Newton (and the closed
+    forms of the Jacobi polynomials with |alpha| = |beta| = 1/2) against the
+    oracle's Golub-Welsch eigenvalues: every node, including the ones at the
+    ends of the spectrum and at x = 0."""
+    sp = F.make_spec(fam, N, alpha=alpha, beta=beta)
+    with xc.Plan(fam, N, 1e-8, alpha=alpha, beta=beta, precision="fp32") as plan:
+        x = plan.nodes()
+    assert np.all(np.diff(x) > 0)
+    assert np.all(np.abs(x - sp.x) <= 4 * N * U64 * (1 + np.abs(sp.x))), fam
+
+
 def test_leading_dimension_and_host_path(xc):
     ora, plan = gpu_plan(xc, "legendre", 300, 1e-10, "fp64", 1e-3)
     with plan:

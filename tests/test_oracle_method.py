@@ -18,7 +18,11 @@ CLAIMS = json.load(open(os.path.join(GOLDEN, "paper_claims.json")))
 
 
 def _spec(fam, N):
-    return F.make_spec(fam, N, 0.5, -0.5) if fam == "jacobi" else F.make_spec(fam, N)
+    if fam == "jacobi":
+        return F.make_spec(fam, N, 0.5, -0.5)
+    if fam == "lagspec":
+        return F.make_spec(fam, N, 50.0, 2.0)     # eta, T
+    return F.make_spec(fam, N)
 
 
 def identity_error(fam, N, two_sided=None, normalise=False, seed=0):
