@@ -136,10 +136,10 @@ typedef struct xc_plan* xc_plan_t;
  * Runs on the current CUDA device and synchronises it.  On success *out owns
  * all device memory of the plan; on failure *out is NULL and nothing leaks.
  * Complex families: precision XC_FP64 or XC_FP32, the two-sided scheme, raw
- * normalisation, and a block length L whose L complex values fit one CTA's
- * shared memory (L <= 14464 in FP64, 28928 in FP32; L / N is about 1.46 at
- * eps1 = 1e-10, eps2 = 1e-3 and 1.9 at eps1 = 1e-6, eps2 = 0.1, so N up to
- * about 9800 and 15000); otherwise XC_ERR_UNSUPPORTED.  Such plans are applied by
+ * normalisation, and a block length L whose L/2 complex FP64 values fit one
+ * CTA's shared memory (L <= 28928; L / N is about 1.46 at eps1 = 1e-10,
+ * eps2 = 1e-3 and 1.9 at eps1 = 1e-6, eps2 = 0.1, so N up to about 19800 and
+ * 15000); otherwise XC_ERR_UNSUPPORTED.  Such plans are applied by
  * xc_apply / xc_apply_adjoint / xc_apply_host only (xc_apply_noalloc and
  * the batches return XC_ERR_UNSUPPORTED).
  */

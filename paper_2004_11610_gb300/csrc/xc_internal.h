@@ -146,6 +146,11 @@ struct Plan {
   // first c_vpad bins after bin L-1 so that no band read wraps
   bool cplx = false;
   int c_vpad = 0;
+  // adjoint items of the complex block: (bin slice, chunk of 64 rows), item
+  // g = c_cbase[slice] + chunk
+  int2* c_items = nullptr;
+  int* c_cbase = nullptr;              // [tslices + 1]
+  int64_t c_nchunks = 0;
   int64_t matrix_bytes = 0, adjoint_bytes = 0;
   // device copy of `blocks` (read by the kernels), scratch spectra, host-path staging
   void* scratch_desc = nullptr;

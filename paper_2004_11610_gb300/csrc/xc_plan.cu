@@ -1430,6 +1430,18 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
     use_yt = wsum > 0 && swsum / wsum >= 8.0;
   }
 
+  // adjoint items: each slice's run cut into chunks of 64 rows
+  constexpr int kChunk = 64;
+  std::vector<int2> citems;
+  std::vector<int> cbase(tslices + 1, 0);
+  for (int sl = 0; sl < tslices; ++sl) {
+    cbase[sl] = int(citems.size());
+    for (int c = 0; c * kChunk < twidth[sl]; ++c) citems.push_back(int2{sl, c});
+  }
+  cbase[tslices] = int(citems.size());
+  p->c_nchunks = int64_t(citems.size());
+  XC_TRY(upload(p, citems, &p->c_items));
+  XC_TRY(upload(p, cbase, &p->c_cbase));
   int *fk0_d, *fw_d, *tn0_d, *tw_d;
   int64_t *foff_d, *toff_d;
   XC_TRY(upload(p, fk0, &fk0_d));
@@ -1498,9 +1510,11 @@ int build_block_complex(Plan* p, const GenParams& g, const BlockShape& shp) {
   XC_CUDA(cudaGetDevice(&dev));
   XC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const size_t smem = size_t(n) * sizeof(cx<double>);
-  if (smem + 1024 > size_t(optin) || size_t(L) * sizeof(cx<T>) + 1024 > size_t(optin))
+  // the FP64 row FFT of the precompute and each CTA of the apply's two-CTA
+  // transforms hold n = L/2 complex values
+  if (smem + 1024 > size_t(optin) || size_t(n) * sizeof(cx<T>) + 1024 > size_t(optin))
     return fail(XC_ERR_UNSUPPORTED, "complex block length L = " + std::to_string(L) +
-                                        " exceeds one CTA's shared memory");
+                                        " exceeds one CTA's shared memory for L/2 values");
   std::vector<int> perm = digit_reversal(n, b.p, b.radix);
   int* perm_d = nullptr;
   XC_TRY(upload(p, perm, &perm_d));
@@ -1616,6 +1630,18 @@ int build_block_complex(Plan* p, const GenParams& g, const BlockShape& shp) {
     toff[sl] = ttotal;
     ttotal += int64_t(W) * kSlice;
   }
+  // adjoint items: each slice's run cut into chunks of 64 rows
+  constexpr int kChunk = 64;
+  std::vector<int2> citems;
+  std::vector<int> cbase(tslices + 1, 0);
+  for (int sl = 0; sl < tslices; ++sl) {
+    cbase[sl] = int(citems.size());
+    for (int c = 0; c * kChunk < twidth[sl]; ++c) citems.push_back(int2{sl, c});
+  }
+  cbase[tslices] = int(citems.size());
+  p->c_nchunks = int64_t(citems.size());
+  XC_TRY(upload(p, citems, &p->c_items));
+  XC_TRY(upload(p, cbase, &p->c_cbase));
   int *fk0_d, *fw_d, *tn0_d, *tw_d;
   int64_t *foff_d, *toff_d;
   XC_TRY(upload(p, k0, &fk0_d));

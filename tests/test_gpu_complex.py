@@ -78,7 +78,7 @@ CASES = [  # family, N, eps, nodes kind, eta, T
     ("exp", 777, 1e-12, "sorted", 0, 0), ("exp", 500, 1e-10, "unsorted", 0, 0), ("exp", 400, 1e-10, "wide", 0, 0),
     ("exp", 256, 1e-12, "dft", 0, 0), ("exp", 200, 0.0, None, 0, 0), ("exp", 2, 1e-10, None, 0, 0),
     ("lagspec", 649, 1e-10, None, 2500.0, 4.0), ("lagspec", 1000, 1e-12, None, 50.0, 2.0),
-    ("lagspec", 97, 1e-8, None, 3.0, 10.0),
+    ("lagspec", 97, 1e-8, None, 3.0, 10.0), ("lagspec", 3000, 1e-10, None, 50.0, 0.5),
 ]
 
 
@@ -114,10 +114,11 @@ def test_fp32_matches_oracle(xc, fam, N, eps, eta, T):
 
 
 def test_full_size_sampled_rows_and_transpose_identity(xc):
-    """N = 9000 exp plan at FP64 (L = 13122, near the single-CTA limit of
-    14464): sampled rows of the forward product against the oracle built on
-    those rows, and the bilinear identity y . (A x) = (A^T y) . x on all of it."""
-    N, eps, R = 9000, 1e-10, 8
+    """N = 19000 exp plan at FP64 (L = 27648, near the limit of 28928 set by
+    L/2 FP64 values per CTA): sampled rows of the forward product against the
+    oracle built on those rows, and the bilinear identity
+    y . (A x) = (A^T y) . x on all of it."""
+    N, eps, R = 19000, 1e-10, 8
     with xc.Plan("exp", N, eps, precision="fp64") as plan:
         spec = F.make_spec("exp", N)
         rows = np.sort(np.random.default_rng(4).choice(N, 48, replace=False))
@@ -192,6 +193,6 @@ def test_complex_plans_refuse_what_they_do_not_support(xc):
     with pytest.raises(xc.XcError) as e:
         xc.Plan("lagspec", 100, 1e-8, eta=0.0, period=2.0)
     assert e.value.code == xc.XC_ERR_ARG
-    with pytest.raises(xc.XcError) as e:   # L above one CTA's shared memory in FP64
-        xc.Plan("exp", 20000, 1e-8)
+    with pytest.raises(xc.XcError) as e:   # L/2 FP64 values above one CTA's shared memory
+        xc.Plan("exp", 30000, 1e-8)
     assert e.value.code == xc.XC_ERR_UNSUPPORTED
