@@ -81,7 +81,9 @@ def workload_config(name, wl):
         "workload": name,
         "plans": [f"{fam} N={N}" + (f" alpha={p['alpha']} beta={p['beta']}" if p else "")
                   for fam, N, p in wl["plans"]],
-        "nodes": "Gauss nodes of each family (Chebyshev-Gauss for Chebyshev)",
+        "nodes": ("angles: arc midpoints (2n+1-N) pi/N (exp), psi_j = 2 arctan(2 k_j/eta) - pi "
+                  "(spectral Laguerre)" if any(f in ("exp", "lagspec") for f, _, _ in wl["plans"])
+                  else "Gauss nodes of each family (Chebyshev-Gauss for Chebyshev)"),
         "eps": wl["eps"], "precision": wl["precision"], "nrhs": wl["nrhs"], "input": wl["dist"],
         "step": "forward + adjoint apply of every plan",
         "l2": "flushed before every timed step (256 MiB write)",
@@ -136,6 +138,9 @@ def algorithmic_work(info, nrhs, precision, chunked=False):
 def step_bytes(info, nrhs, precision):
     """Algorithmic HBM bytes of one forward + adjoint apply of one plan."""
     eb = 8 if precision in ("fp64", "fp64pair") else 4
+    if info.get("family") in COMPLEX_FAMILY_IDS:   # complex vectors, full spectrum
+        ce, L = 2 * eb, info["L"][0]
+        return info["matrix_bytes"] + info["adjoint_bytes"] + 4 * nrhs * info["N"] * ce + 2 * 2 * nrhs * L * ce
     H = sum(L // 2 + 1 for L in info["L"])
     vec = 4 * nrhs * info["N"] * eb                    # x in, y out, y in, x out
     spec = 2 * 2 * nrhs * H * 2 * eb                   # spectra written + read, both directions
@@ -284,7 +289,7 @@ def kernel_source_hash():
     """sha256 over the sources of the execution kernels (changes whenever a
     kernel does)."""
     h = hashlib.sha256()
-    for f in ("xc_items.cuh", "xc_apply.cu", "xc_batch.cu", "xc_fft.cuh"):
+    for f in ("xc_items.cuh", "xc_apply.cu", "xc_batch.cu", "xc_fft.cuh", "xc_complex.cu"):
         h.update(open(os.path.join(ROOT, "paper_2004_11610_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -369,7 +374,6 @@ def run_xc(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     wl = inputs.WORKLOADS[args.workload]
     prec = wl["precision"]
-    tdt = torch.float64 if prec in ("fp64", "fp64pair") else torch.float32
     R = wl["nrhs"]
     specs = plan_specs(wl)
     plans, X, Y, XA = [], [], [], []
@@ -378,7 +382,7 @@ def run_xc(args, rank, world, local_rank):
                     alpha=s["params"].get("alpha", 0.0), beta=s["params"].get("beta", 0.0))
         p.reserve(R)
         plans.append(p)
-        x = torch.from_numpy(inputs.draw(wl["dist"], s["N"], R, 1, s["index"], rank)).to(dev, tdt)
+        x = torch.from_numpy(inputs.draw(wl["dist"], s["N"], R, 1, s["index"], rank)).to(dev, p.torch_dtype)
         X.append(x)
         Y.append(torch.empty_like(x))
         XA.append(torch.empty_like(x))
@@ -474,8 +478,8 @@ def run_xc(args, rank, world, local_rank):
 
     # end to end through the C ABI with pinned host buffers (copies timed)
     e2e_steps = max(3, min(args.steps, 50))
-    hx = [torch.from_numpy(inputs.draw(wl["dist"], s["N"], R, 2, s["index"], rank)).to(tdt).pin_memory()
-          for s in specs]
+    hx = [torch.from_numpy(inputs.draw(wl["dist"], s["N"], R, 2, s["index"], rank)).to(p.torch_dtype).pin_memory()
+          for s, p in zip(specs, plans)]
     hy = [torch.empty_like(h).pin_memory() for h in hx]
     hz = [torch.empty_like(h).pin_memory() for h in hx]
     import ctypes
@@ -500,7 +504,8 @@ def run_xc(args, rank, world, local_rank):
     e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
     e2e_val = job_throughput(vectors_per_step, e2e_steps, 1e3 * e2e_s, world)
     eb = 8 if prec in ("fp64", "fp64pair") else 4
-    io_bytes = sum(2 * R * s["N"] * eb for s in specs)
+    io_bytes = sum(2 * R * s["N"] * eb * (2 if p.is_complex else 1) for s, p in zip(specs, plans))
+    cplx = any(p.is_complex for p in plans)
 
     # dense GEMM comparison (cuBLAS through torch) at equal precision
     dense = None
@@ -535,10 +540,11 @@ def run_xc(args, rank, world, local_rank):
             b.record(stream)
             b.synchronize()
             dms += a.elapsed_time(b)
-        if prec == "fp64" and not args.no_variant:
+        if prec == "fp64" and not args.no_variant and not cplx:
             variant = measure_pair_variant(xc, torch, wl, specs, dev, max(3, min(args.steps, 50)), 3, world, mats)
         dense = {"vectors_per_s": vectors_per_step * ds / (dms / 1e3), "ms_per_step": dms / ds,
-                 "library": "cuBLAS via torch.matmul", "dtype": "f64" if fp64 else "f32",
+                 "library": "cuBLAS via torch.matmul",
+                 "dtype": ("c128" if fp64 else "c64") if cplx else ("f64" if fp64 else "f32"),
                  "method_rel_l2_vs_dense": max(errs),
                  "speedup_of_method": (vectors_per_step * ds / (dms / 1e3)) and value / world /
                  (vectors_per_step * ds / (dms / 1e3))}
@@ -557,7 +563,7 @@ def run_xc(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp64pair": "f64 (band products in f32 pairs)", "fp32": "f32"}.get(
-                prec, "f32-compensated"),
+                prec, "f32-compensated") + (" complex" if cplx else ""),
             "data": "synthetic", "config": workload_config(args.workload, wl) | {"parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,

@@ -36,7 +36,7 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-constexpr int kCfftThreads = 256;   // per CTA; two CTAs (a cluster) per transform
+constexpr int kCfftThreads = 512;   // per CTA; two CTAs (a cluster) per transform
 constexpr int kCsparseThreads = 128;
 constexpr int kCAdjChunk = 64;      // rows per adjoint item (long bin runs are cut)
 
@@ -192,7 +192,7 @@ __device__ __forceinline__ cx<T> gather_z(const cx<T>* __restrict__ part, const 
   return z;
 }
 
-// Cluster of two CTAs per RHS: rank 0 takes P_k = (z_k + conj z_{L-k}) / 2,
+// Cluster of two CTAs per RHS: rank 0 transforms P_k = (z_k + conj z_{L-k}) / 2,
 // rank 1 Q_k = (z_k - conj z_{L-k}) / (2i), both Hermitian, so that
 // sum_k z_k exp(+2 pi i jk / L) = p_j + i q_j with p, q the real inverse
 // transforms of P and Q (packed as in the real adjoint); each rank then writes
@@ -210,23 +210,33 @@ __global__ void __launch_bounds__(kCfftThreads) c_adj_fft_kernel(BlockDev b, con
   const T* __restrict__ invw = static_cast<const T*>(b.invw);
   const cx<T>* __restrict__ tw = static_cast<const cx<T>*>(b.tw);
   const T h = T(0.5);
-  auto PQ = [&](int k) {
-    const cx<T> a = gather_z(part, cbase, k, r, nrhs);
-    const cx<T> c = conj(gather_z(part, cbase, k == 0 ? 0 : L - k, r, nrhs));
-    return rank == 0 ? scal(h, a + c) : scal(h, mul_mi(a - c));
-  };
-  for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
-    cx<T> Uk = PQ(k), Unk = PQ(n - k);
-    if (k == 0) {   // U_0 and U_n enter as real numbers
-      Uk.im = T(0);
-      Unk.im = T(0);
+  // each bin pair (k, n - k) once: this CTA takes every other pair, forms
+  // both P and Q, and stores them packed into rank 0's (P) and rank 1's (Q)
+  // shared memory
+  cx<T>* dp = cluster.map_shared_rank(s, 0);
+  cx<T>* dq = cluster.map_shared_rank(s, 1);
+  cluster.sync();   // the partner runs before its shared memory is written
+  for (int k = rank * int(blockDim.x) + int(threadIdx.x); k <= n / 2; k += 2 * int(blockDim.x)) {
+    const cx<T> zk = gather_z(part, cbase, k, r, nrhs);
+    const cx<T> zLk = conj(gather_z(part, cbase, k == 0 ? 0 : L - k, r, nrhs));
+    const cx<T> znk = gather_z(part, cbase, n - k, r, nrhs);
+    const cx<T> zLnk = conj(gather_z(part, cbase, L - (n - k), r, nrhs));
+    cx<T> Pk = scal(h, zk + zLk), Qk = scal(h, mul_mi(zk - zLk));
+    cx<T> Pnk = scal(h, znk + zLnk), Qnk = scal(h, mul_mi(znk - zLnk));
+    if (k == 0) {   // P_0, P_n, Q_0, Q_n enter as real numbers
+      Pk.im = Pnk.im = Qk.im = Qnk.im = T(0);
     }
+    const int pk = b.perm[k], pnk = b.perm[n - k];
+    const bool two = k != 0 && n - k != k;
     cx<T> Zk, Znk;
-    c2r_merge(Uk, Unk, k, tw, &Zk, &Znk);
-    s[b.perm[k]] = conj(Zk);   // inverse FFT as conj(FFT(conj(Z)))
-    if (k != 0 && n - k != k) s[b.perm[n - k]] = conj(Znk);
+    c2r_merge(Pk, Pnk, k, tw, &Zk, &Znk);
+    dp[pk] = conj(Zk);   // inverse FFT as conj(FFT(conj(Z)))
+    if (two) dp[pnk] = conj(Znk);
+    c2r_merge(Qk, Qnk, k, tw, &Zk, &Znk);
+    dq[pk] = conj(Zk);
+    if (two) dq[pnk] = conj(Znk);
   }
-  __syncthreads();
+  cluster.sync();   // both packed spectra are in place
   fft_inplace<T>(s, n, b.p, b.radix, tw, threadIdx.x, blockDim.x);
   cluster.sync();   // p and q are complete
   const cx<T>* sp = cluster.map_shared_rank(s, 0);

@@ -71,6 +71,15 @@ WORKLOADS = {
     # Legendre at N=32768, FP32 forward and adjoint, 128 standard-normal RHS.
     "legendre32768_fp32": dict(
         plans=[("legendre", 32768, {})], eps=1e-7, precision="fp32", nrhs=128, dist="normal"),
+    # Complex families: exp(i m theta_n) at the 8192 arc-midpoint angles, and
+    # the spectral Laguerre matrix with the shape parameters of the paper's
+    # Section 4 figure (eta = 2500, T = 4 s) at N = 8192; FP64, eps=1e-12, 64
+    # complex standard-normal RHS.
+    "exp8192_fp64": dict(
+        plans=[("exp", 8192, {})], eps=1e-12, precision="fp64", nrhs=64, dist="complex_normal"),
+    "lagspec8192_fp64": dict(
+        plans=[("lagspec", 8192, {"alpha": 2500.0, "beta": 4.0})], eps=1e-12, precision="fp64", nrhs=64,
+        dist="complex_normal"),
 }
 
 
@@ -97,4 +106,6 @@ def draw(dist: str, n: int, nrhs: int, *offsets: int) -> np.ndarray:
         return uniform_01(n, nrhs, *offsets)
     if dist == "normal":
         return normal(n, nrhs, *offsets)
+    if dist == "complex_normal":
+        return complex_normal(n, nrhs, *offsets)
     raise ValueError(f"unknown distribution {dist!r}")
