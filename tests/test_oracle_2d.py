@@ -1,0 +1,158 @@
+"""Pins of the oracle's 2-D compression (eq. (comp_2d)) and its block scheme
+(Sections 4.2, 5.3): what fixes them independently of the oracle's formulas.
+
+- the decomposition covers every (row, column) of the matrix exactly once;
+- eps1 = 0 keeps every element: the product equals the dense product up to
+  rounding amplified by 1/eps2 (the identity behind eq. (comp_2d));
+- eps1 > 0: error within the eps1/eps2 bound of Section 2.2;
+- the adjoint is the exact transpose of the forward operator;
+- tiny matrices are rebuilt entrywise;
+- the matrix entries: Laguerre / Hermite functions vs scipy at equispaced
+  nodes, Lambda(z) = Gamma(z+1/2)/Gamma(z+1) vs mpmath, A^[2] at a few entries
+  by hand;
+- the paper's numbers: the Laguerre transform matrix at t_i = 12 i/(N-1)
+  compresses "up to 3-4 %" in its main block (Section 5.3, eta = 100, 1e-10),
+  where the 1-D compression keeps no fewer elements than the matrix has;
+  A^[2]'s compression factors N^2/nnz of the wavelet table (Section 5.3) are
+  met within a factor of two.
+"""
+import math
+
+import mpmath
+import numpy as np
+import pytest
+import scipy.special
+
+from oracle import families as F
+from oracle import method as M
+from oracle import method2d as M2
+
+
+def laguerre_transform(N, eta):
+    """D[i, m] = l_m(eta t_i), t_i = 12 (i + 1) / (N - 1) (the points of
+    Section 5.3, i = 1..N, shifted to a 0-based index)."""
+    h = 12.0 * eta / (N - 1)
+    return M2.Spec2D("laguerre", N, h, h)
+
+
+SPECS = [
+    ("laguerre eta=20", laguerre_transform(300, 20.0)),
+    ("hermite equispaced", M2.Spec2D("hermite", 260, -12.0, 0.09)),
+    ("a1", M2.Spec2D("a1", 240)),
+    ("a2", M2.Spec2D("a2", 250)),
+]
+
+
+@pytest.mark.parametrize("N", [21, 64, 300, 1000, 1024])
+def test_decomposition_covers_every_entry_once(N):
+    from oracle import special as S
+    zeta = S.zeta_of_eps(1e-8)
+    blocks, dense = M2.decompose(N, zeta, 1e-3)
+    cover = np.zeros((N, N), dtype=np.int32)
+    for (r0, Lr, vr0, r1, c0, Lc, vc0, c1) in blocks:
+        assert r0 <= vr0 < r1 <= r0 + Lr and c0 <= vc0 < c1 <= c0 + Lc
+        w_r = S.kaiser_window(Lr, zeta)
+        w_c = S.kaiser_window(Lc, zeta)
+        # every valid row / column keeps a window value of at least eps2
+        assert w_r[vr0 - r0:r1 - r0].min() >= 1e-3 and w_c[vc0 - c0:c1 - c0].min() >= 1e-3
+        cover[vr0:r1, vc0:c1] += 1
+    for (r0, r1, c0, c1) in dense:
+        cover[r0:r1, c0:c1] += 1
+    assert np.all(cover == 1)
+
+
+@pytest.mark.parametrize("name,spec", SPECS)
+def test_without_threshold_the_product_is_dense(name, spec):
+    P = M2.build(spec, 0.0, eps2=1e-3)
+    D = M2.dense_matrix(spec)
+    X = np.random.default_rng(1).standard_normal((3, spec.N))
+    assert M.rel_l2(M2.apply(P, X), X @ D.T) <= 1e-11
+    assert M.rel_l2(M2.apply_adjoint(P, X), X @ D) <= 1e-11
+
+
+@pytest.mark.parametrize("name,spec", SPECS)
+@pytest.mark.parametrize("eps,eps2", [(1e-10, 1e-3), (1e-6, 1e-2)])
+def test_error_within_the_eps1_over_eps2_bound(name, spec, eps, eps2):
+    P = M2.build(spec, eps, eps2=eps2)
+    D = M2.dense_matrix(spec)
+    X = np.random.default_rng(2).standard_normal((4, spec.N))
+    # A^[1] jumps across its diagonal: the bound holds with a larger constant
+    c = 100.0 if spec.family == "a1" else 10.0
+    assert M.rel_l2(M2.apply(P, X), X @ D.T) <= c * eps / eps2
+    assert M.rel_l2(M2.apply_adjoint(P, X), X @ D) <= c * eps / eps2
+
+
+@pytest.mark.parametrize("name,spec", SPECS)
+def test_adjoint_is_the_exact_transpose(name, spec):
+    P = M2.build(spec, 1e-8, eps2=1e-3)
+    rng = np.random.default_rng(3)
+    x, y = rng.standard_normal(spec.N), rng.standard_normal(spec.N)
+    fx = M2.apply(P, x)
+    assert abs(y @ fx - M2.apply_adjoint(P, y) @ x) <= 1e-12 * np.abs(y).sum() * np.abs(fx).max()
+
+
+@pytest.mark.parametrize("fam", ["laguerre", "a2"])
+def test_tiny_matrices_rebuilt_entrywise(fam):
+    for N in (5, 21, 48):
+        spec = M2.Spec2D(fam, N, 0.3, 0.7) if fam == "laguerre" else M2.Spec2D(fam, N)
+        P = M2.build(spec, 0.0, eps2=1e-3)
+        A = M2.apply(P, np.eye(N)).T
+        ref = M2.dense_matrix(spec)
+        assert np.abs(A - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_entries_against_independent_evaluations():
+    # Laguerre and Hermite functions at equispaced nodes vs scipy
+    sp = M2.Spec2D("laguerre", 50, 0.5, 0.25)
+    V = sp.values(3, 9, 0, 40)
+    x = sp.nodes(3, 9)
+    for m in (0, 7, 39):
+        ref = np.exp(-x / 2) * scipy.special.eval_laguerre(m, x)
+        assert np.allclose(V[:, m], ref, rtol=1e-12, atol=1e-300)
+    sp = M2.Spec2D("hermite", 50, -3.0, 0.2)
+    V = sp.values(0, 30, 0, 20)
+    x = sp.nodes(0, 30)
+    for m in (0, 5, 19):
+        ref = scipy.special.eval_hermite(m, x) * np.exp(-x * x / 2) / math.sqrt(2.0 ** m * math.factorial(m) *
+                                                                               math.sqrt(math.pi))
+        assert np.allclose(V[:, m], ref, rtol=1e-11, atol=1e-14)
+    # Lambda against mpmath, A^[1] and A^[2] entries by hand
+    for z in (0, 1, 7, 500):
+        assert M2.lam(z) == pytest.approx(float(mpmath.gamma(z + 0.5) / mpmath.gamma(z + 1)), rel=1e-13)
+    A1 = M2.Spec2D("a1", 10).values(0, 10, 0, 10)
+    assert A1[0, 4] == pytest.approx(float(mpmath.gamma(4.5) / mpmath.gamma(5)) / math.pi, rel=1e-13)
+    assert A1[2, 5] == pytest.approx(2 / math.pi * float(mpmath.gamma(3.5) / mpmath.gamma(4) *
+                                                          mpmath.gamma(7.5) / mpmath.gamma(8)), rel=1e-13)
+    assert A1[5, 2] == 0.0
+    A2 = M2.Spec2D("a2", 10).values(0, 10, 0, 10)
+    assert A2[3, 7] == pytest.approx((3 * math.cos(math.log(9)) - 7 * math.cos(math.log(49))) / 16, rel=1e-13)
+    assert A2[0, 2] == pytest.approx(-2 * math.cos(math.log(4)) / 4, rel=1e-13)
+    assert A2[4, 4] == 0.0
+
+
+def test_laguerre_transform_main_block_compresses_to_a_few_percent():
+    """Section 5.3: eta = 100, accuracy 1e-10, N = 1000 -- the compressed
+    matrix keeps "up to 3-4 %" of the elements; the 1-D compressions of
+    Section 4.2 do not reduce them."""
+    spec = laguerre_transform(1000, 100.0)
+    P = M2.build(spec, 1e-10, eps2=1e-3)
+    main = max(P.blocks, key=lambda b: b.Lr * b.Lc)
+    assert main.kept.nnz <= 0.04 * main.Lr * main.Lc
+    one_d = M.build(F.make_spec("laguerre", 1000, x=spec.nodes(0, 1000)), 1e-10, eps2=1e-3)
+    assert sum(b.kept.nnz for b in one_d.blocks) >= 0.9 * 1000 ** 2
+
+
+@pytest.mark.parametrize("N,eps,eps2,paper_factor", [(512, 1e-3, 1e-1, 10.3), (1024, 1e-3, 1e-1, 23.0),
+                                                     (1024, 1e-7, 1e-2, 6.5)])
+def test_a2_compression_factor_near_the_wavelet_table(N, eps, eps2, paper_factor):
+    """Section 5.3's table: N^2 / nnz of A^[2] at accuracy 1e-2 (10.3 at
+    N = 512, 23 at 1024) and 1e-6 (6.5 at 1024); eps1/eps2 chosen to reach
+    that accuracy.  Met within a factor of two (the paper's decomposition is
+    only drawn)."""
+    spec = M2.Spec2D("a2", N)
+    P = M2.build(spec, eps, eps2=eps2)
+    X = np.random.default_rng(4).standard_normal((3, N))
+    err = M.rel_l2(M2.apply(P, X), X @ M2.dense_matrix(spec).T)
+    assert err <= (1e-2 if eps > 1e-5 else 2e-6)
+    factor = 1.0 / M2.stored_fraction(P)
+    assert paper_factor / 2 <= factor <= paper_factor * 2
