@@ -91,6 +91,7 @@ def workload_config(name, wl):
 
 
 COMPLEX_FAMILY_IDS = (7, 8)   # exp, spectral Laguerre
+SCHEME_2D = 3
 
 
 def algorithmic_work(info, nrhs, precision, chunked=False):
@@ -101,6 +102,17 @@ def algorithmic_work(info, nrhs, precision, chunked=False):
     eb = 8 if precision in ("fp64", "fp64pair") else 4
     nnz = sum(info["nnz"])
     N, mt = info["N"], info["m_tail"]
+    if info.get("scheme") == SCHEME_2D:
+        # per direction: input transforms, CSR product (2 complex values and an
+        # index per entry, 8 real flops per entry and RHS), output transforms,
+        # combine (dense rectangles: 2 flops per element and RHS)
+        nnz2, de = info["nnz2d"], info["dense_elems2d"]
+        return {
+            "fft_in_2d": (0.0, nrhs * N * eb),
+            "sparse_2d": (8.0 * nnz2 * nrhs, nnz2 * (4 * eb + 4)),
+            "fft_out_2d": (0.0, nrhs * N * eb),
+            "combine_2d": (2.0 * de * nrhs, de * eb + 2 * nrhs * N * eb),
+        }
     if info.get("family") in COMPLEX_FAMILY_IDS:
         # complex vectors and values (2 eb per element), full spectrum of L
         # bins, 8 real flops per complex multiply-add, 5 L log2 L per FFT
@@ -132,6 +144,8 @@ def algorithmic_work(info, nrhs, precision, chunked=False):
         "pair_scale": (0.0, 2.0 * N * eb * nrhs),
         # row factors of the complex spectral Laguerre matrix (not run by real plans)
         "row_scale": (0.0, 0.0),
+        # kernels of the 2-D block scheme (not run by 1-D plans)
+        "fft_in_2d": (0.0, 0.0), "sparse_2d": (0.0, 0.0), "fft_out_2d": (0.0, 0.0), "combine_2d": (0.0, 0.0),
     }
 
 

@@ -64,7 +64,7 @@ typedef enum {
                           themselves: Gauss nodes = the midpoints (2n + 1 - N) pi / N of N equal
                           arcs (discretely orthogonal), user nodes = any real angles.  Two-sided
                           extension, one block. */
-  XC_LAGUERRE_SPECTRAL = 8  /* the spectral Laguerre matrix C of eq. (lag_matrix) (Section 4),
+  XC_LAGUERRE_SPECTRAL = 8,  /* the spectral Laguerre matrix C of eq. (lag_matrix) (Section 4),
                           read as C[j, m] = (-eta/2 - i k_j)^m / (eta/2 - i k_j)^(m+1)
                           = exp(i m psi_j) / (eta/2 - i k_j), k_j = 2 pi j / T,
                           psi_j = 2 arctan(2 k_j / eta) - pi; eta = alpha > 0, T = beta > 0.
@@ -72,6 +72,12 @@ typedef enum {
                           xc_get_nodes returns), the factor 1/(eta/2 - i k_j) is applied to the
                           rows outside it.  xc_apply_adjoint gives C^T F (Fourier coefficients
                           to Laguerre coefficients).  Complex vectors. */
+  XC_KERNEL_A1   = 9,  /* A^[1] of Section 5.3 (entries of the row and column indices):
+                          Lambda(j)/pi on row 0, (2/pi) Lambda(j-i) Lambda(j+i) for 0 < i <= j,
+                          0 below the diagonal, Lambda(z) = Gamma(z+1/2)/Gamma(z+1);
+                          XC_SCHEME_2D only */
+  XC_KERNEL_A2   = 10  /* A^[2] of Section 5.3: (i cos(log i^2) - j cos(log j^2)) / (i - j)^2,
+                          0 on the diagonal (k cos(log k^2) read as 0 at k = 0); XC_SCHEME_2D only */
 } xc_family;
 
 /* node sets */
@@ -96,6 +102,15 @@ typedef enum {
 #define XC_SCHEME_AUTO      0   /* two-sided for the trigonometric families, block method otherwise */
 #define XC_SCHEME_TWO_SIDED 1   /* Algorithms 1-2; trigonometric families (Chebyshev, sine, cos^s) only */
 #define XC_SCHEME_BLOCKS    2   /* Algorithms 3-4 */
+#define XC_SCHEME_2D        3   /* the 2-D compression F W D W F (eq. (comp_2d)) in its block
+                                   scheme (Sections 4.2, 5.3): rectangles of the matrix, each
+                                   extended below and to the right, compressed along both
+                                   dimensions; the rows and columns whose window is below eps2
+                                   form further rectangles, thin ones (a side <= tail_max) are
+                                   dense.  XC_LAGUERRE_FN / XC_HERMITE_FN at equispaced user nodes
+                                   (x_i = x_0 + i h, extended with the same step) and
+                                   XC_KERNEL_A1 / XC_KERNEL_A2; XC_FP64 or XC_FP32; real vectors.
+                                   Blocks up to L <= 28928 along each side (N up to about 19000). */
 
 /* precomputation of the compressed rows */
 #define XC_PRECOMPUTE_AUTO 0   /* Appendix A closed form for XC_CHEBYSHEV_T at its Gauss nodes with
@@ -237,6 +252,11 @@ typedef struct {
   int64_t adjoint_bytes;             /* device bytes of the transposed copies */
   int closed_form_blocks;            /* blocks whose rows the Appendix A closed form built
                                         (the others: FFT of the generated rows) */
+  /* XC_SCHEME_2D plans (the per-block arrays above then stay empty, nblocks = 0): */
+  int blocks2d;                      /* compressed 2-D blocks */
+  int dense2d;                       /* dense rectangles */
+  int64_t nnz2d;                     /* kept elements of the compressed blocks (full spectra) */
+  int64_t dense_elems2d;             /* elements of the dense rectangles */
 } xc_plan_stats;
 
 /* Copy the plan's parameters and per-block statistics into *out. */

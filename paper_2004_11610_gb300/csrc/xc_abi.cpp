@@ -46,7 +46,8 @@ static std::atomic<int64_t> g_launches{0};
 
 const char* kernel_name(int id) {
   static const char* names[K_COUNT] = {"fwd_fft",       "fwd_sparse", "adj_sparse", "adj_fft",  "adj_tail",
-                                       "fwd_reduce",    "adj_transpose", "pair_scale", "row_scale"};
+                                       "fwd_reduce",    "adj_transpose", "pair_scale", "row_scale",
+                                       "fft_in_2d",     "sparse_2d",  "fft_out_2d", "combine_2d"};
   return (id >= 0 && id < K_COUNT) ? names[id] : "unknown";
 }
 
@@ -95,6 +96,7 @@ static void free_plan(Plan* p) {
   cudaDeviceSynchronize();
   release_events(p);
   for (void* d : p->allocations) cudaFree(d);
+  delete p->d2;
   if (p->scratch) cudaFree(p->scratch);
   if (p->stage) cudaFree(p->stage);
   delete p;
@@ -132,7 +134,10 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
   xc_params prm;
   if (params) prm = *params;
   else xc_params_default(&prm);
-  if (family < XC_CHEBYSHEV_T || family > XC_LAGUERRE_SPECTRAL) return fail(XC_ERR_ARG, "unknown family");
+  if (family < XC_CHEBYSHEV_T || family > XC_KERNEL_A2) return fail(XC_ERR_ARG, "unknown family");
+  const bool index_kernel = family == XC_KERNEL_A1 || family == XC_KERNEL_A2;
+  if (index_kernel && prm.scheme == XC_SCHEME_AUTO) prm.scheme = XC_SCHEME_2D;
+  const bool two_d = prm.scheme == XC_SCHEME_2D;
   const bool cplx = family == XC_EXP || family == XC_LAGUERRE_SPECTRAL;
   const bool trig = family == XC_CHEBYSHEV_T || family == XC_SINE || family == XC_COS_POWER || cplx;
   if (N < 2 || N > (int64_t(1) << 20)) return fail(XC_ERR_ARG, "N must lie in [2, 2^20]");
@@ -144,7 +149,30 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
   if (prm.normalise == XC_ORTHONORMAL && prm.nodes == XC_NODES_USER)
     return fail(XC_ERR_ARG, "the orthonormal variant needs Gauss nodes");
   if (family == XC_JACOBI && !(prm.alpha > -1.0 && prm.beta > -1.0)) return fail(XC_ERR_ARG, "Jacobi needs alpha, beta > -1");
-  if (prm.scheme < XC_SCHEME_AUTO || prm.scheme > XC_SCHEME_BLOCKS) return fail(XC_ERR_ARG, "unknown scheme");
+  if (prm.scheme < XC_SCHEME_AUTO || prm.scheme > XC_SCHEME_2D) return fail(XC_ERR_ARG, "unknown scheme");
+  double x0 = 0.0, h = 1.0;
+  if (two_d) {
+    if (!(index_kernel || family == XC_LAGUERRE_FN || family == XC_HERMITE_FN))
+      return fail(XC_ERR_UNSUPPORTED, "the 2-D scheme takes Laguerre / Hermite functions or the index kernels");
+    if (prm.precision != XC_FP64 && prm.precision != XC_FP32)
+      return fail(XC_ERR_UNSUPPORTED, "the 2-D scheme runs in XC_FP64 or XC_FP32");
+    if (prm.normalise != XC_RAW) return fail(XC_ERR_UNSUPPORTED, "the 2-D scheme takes the raw matrix");
+    if (!index_kernel) {
+      // equispaced nodes x_i = x0 + i h, h > 0: the rows extend with the same step
+      if (prm.nodes != XC_NODES_USER || !prm.user_nodes)
+        return fail(XC_ERR_ARG, "the 2-D scheme needs equispaced user nodes");
+      x0 = prm.user_nodes[0];
+      h = (prm.user_nodes[N - 1] - x0) / double(N - 1);
+      if (!(h > 0.0)) return fail(XC_ERR_ARG, "the 2-D scheme needs increasing equispaced nodes");
+      for (int64_t i = 0; i < N; ++i) {
+        const double want = x0 + h * double(i);
+        if (std::fabs(prm.user_nodes[i] - want) > 1e-12 * std::fmax(std::fabs(want), h * double(N)))
+          return fail(XC_ERR_ARG, "the 2-D scheme needs equispaced user nodes");
+      }
+    }
+  } else if (index_kernel) {
+    return fail(XC_ERR_ARG, "the index kernels take XC_SCHEME_2D");
+  }
   if (prm.scheme == XC_SCHEME_TWO_SIDED && !trig)
     return fail(XC_ERR_ARG, "the two-sided extension needs a trigonometric family");
   if (prm.normalise == XC_ORTHONORMAL && (family == XC_SINE || family == XC_COS_POWER))
@@ -174,6 +202,8 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
   // only the Jacobi family (alpha, beta) and the spectral Laguerre matrix (eta, T) have parameters
   if (family != XC_JACOBI && family != XC_LAGUERRE_SPECTRAL) p->params.alpha = p->params.beta = 0.0;
   p->cplx = cplx;
+  p->x0 = x0;
+  p->h = h;
   p->precision = prm.precision;
   p->normalise = prm.normalise;
   p->scheme = prm.scheme == XC_SCHEME_AUTO ? (trig ? XC_SCHEME_TWO_SIDED : XC_SCHEME_BLOCKS) : prm.scheme;
@@ -181,8 +211,16 @@ int xc_plan_create(xc_plan_t* out, int family, const xc_params* params, int64_t 
   p->eps = eps;
   p->eps2 = prm.eps2 > 0 ? prm.eps2 : (p->io64() ? 1e-3 : 1e-1);
   if (prm.nodes == XC_NODES_USER) p->nodes_host.assign(prm.user_nodes, prm.user_nodes + N);
-  int rc = xc::make_schedule(N, eps, p->eps2, p->scheme == XC_SCHEME_TWO_SIDED, prm.eps_window,
-                             prm.tail_max > 0 ? prm.tail_max : 20, &p->sch);
+  int rc = XC_OK;
+  if (two_d) {
+    // zeta as for any block; the 2-D decomposition is made on the device side
+    const double ew = eps > 0 ? eps : (prm.eps_window > 0 ? prm.eps_window : 1e-14);
+    p->sch.eps_window = ew;
+    p->sch.zeta = xc::zeta_of_eps_host(ew);
+  } else {
+    rc = xc::make_schedule(N, eps, p->eps2, p->scheme == XC_SCHEME_TWO_SIDED, prm.eps_window,
+                           prm.tail_max > 0 ? prm.tail_max : 20, &p->sch);
+  }
   if (rc == XC_OK) {
     p->zeta = p->sch.zeta;
     rc = xc::build_plan_device(p);
@@ -229,7 +267,7 @@ int xc_apply_noalloc(xc_plan_t plan, const void* x_dev, void* y_dev, int64_t nrh
   auto* p = reinterpret_cast<xc::Plan*>(plan);
   XC_TRY(xc::validate_vectors(p, x_dev, y_dev, nrhs, ld));
   if (nrhs == 0) return XC_OK;
-  if (p->cplx) return fail(XC_ERR_UNSUPPORTED, "xc_apply_noalloc does not take complex plans");
+  if (p->cplx || p->d2) return fail(XC_ERR_UNSUPPORTED, "xc_apply_noalloc takes 1-D real plans only");
   p->last_stream = static_cast<cudaStream_t>(stream);
   return xc::launch_apply_noalloc(p, x_dev, y_dev, nrhs, ld, static_cast<cudaStream_t>(stream));
 }
@@ -294,6 +332,13 @@ int xc_plan_info(xc_plan_t plan, xc_plan_stats* out) {
   out->matrix_bytes = p->matrix_bytes;
   out->adjoint_bytes = p->adjoint_bytes;
   out->closed_form_blocks = p->closed_form_blocks;
+  if (p->d2) {
+    out->nblocks = 0;
+    out->blocks2d = p->d2->nb;
+    out->dense2d = int(p->d2->rects_host.size());
+    out->nnz2d = p->d2->kept;
+    out->dense_elems2d = p->d2->dense_elems;
+  }
   return XC_OK;
 }
 

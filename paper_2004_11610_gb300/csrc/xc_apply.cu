@@ -808,6 +808,7 @@ int ensure_scratch(Plan* p, int64_t nrhs) {
   if (nrhs <= p->scratch_nrhs) return XC_OK;
   const size_t cbytes = 2 * p->elem_bytes();
   if (p->cplx) return grow_scratch(p, nrhs, complex_scratch_bytes(p, nrhs));
+  if (p->d2) return grow_scratch(p, nrhs, d2_scratch_bytes(p, nrhs));
   // forward: spectra (+ unit partials); adjoint: chunk partials + transposed
   // y.  The directions share the buffer (one at a time).
   const int64_t fwd = p->spec_per_rhs + (p->fwd_chunked ? p->total_units * 32 : 0);
@@ -829,6 +830,7 @@ int ensure_scratch(Plan* p, int64_t nrhs) {
 int launch_apply(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st) {
   XC_TRY(ensure_scratch(p, nrhs));
   if (p->cplx) return launch_apply_complex(p, x, y, nrhs, ld, st);
+  if (p->d2) return launch_apply_2d(p, x, y, nrhs, ld, st, false);
   switch (p->precision) {
     case XC_FP64: return apply_impl<double, false>(p, x, y, nrhs, ld, st);
     case XC_FP64_PAIR: return apply_pair(p, x, y, nrhs, ld, st);
@@ -840,6 +842,7 @@ int launch_apply(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cuda
 int launch_apply_adjoint(Plan* p, const void* y, void* x, int64_t nrhs, int64_t ld, cudaStream_t st) {
   XC_TRY(ensure_scratch(p, nrhs));
   if (p->cplx) return launch_adjoint_complex(p, y, x, nrhs, ld, st);
+  if (p->d2) return launch_apply_2d(p, y, x, nrhs, ld, st, true);
   switch (p->precision) {
     case XC_FP64: return adjoint_impl<double, false>(p, y, x, nrhs, ld, st);
     case XC_FP64_PAIR: return adjoint_pair(p, y, x, nrhs, ld, st);

@@ -468,9 +468,9 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans) {
       delete b;
       return fail(XC_ERR_UNSUPPORTED, "batches take XC_FP64, XC_FP32 or XC_FP32_COMPENSATED plans");
     }
-    if (p->cplx) {
+    if (p->cplx || p->d2) {
       delete b;
-      return fail(XC_ERR_UNSUPPORTED, "plan " + std::to_string(i) + " is complex: batches take real families");
+      return fail(XC_ERR_UNSUPPORTED, "plan " + std::to_string(i) + ": batches take real 1-D plans");
     }
     if (i > 0 && p->precision != b->precision) {
       delete b;

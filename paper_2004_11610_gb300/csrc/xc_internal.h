@@ -40,6 +40,8 @@ double kaiser_value_host(double j, int64_t length, double zeta);
 double zeta_of_eps_host(double eps1);
 bool is_fft_friendly(int64_t length);
 int64_t fft_friendly_at_least(int64_t length);
+// Smallest s >= 1 with w_s^{zeta, L-1} >= eps2 (Section 2.2), or -1.
+int64_t extra_count(int64_t m, double zeta, double eps2, bool two_sided);
 // Factor n into radices 8, 4, 2, 3, 5, 7 (product == n); returns pass count or -1.
 int fft_radices(int64_t n, int* radix);
 
@@ -95,6 +97,47 @@ constexpr int64_t kAdjTargetChunks = 512;
 // bands; a reduction kernel adds the chunks of each slice.
 constexpr int kFwdChunk = 256;
 
+// ---------------------------------------------------------- 2-D block scheme
+// One direction of the 2-D scheme (forward: input side = columns, output side
+// = rows; adjoint: the other way round).  Block b's input transform is
+// described by in_host[b] (a BlockDev whose j_lo/j_hi/off select the valid
+// inputs), its output transform by out_host[b]; the compressed product of all
+// blocks is one CSR over the output half-spectrum bins, each entry (k, a, c)
+// adding a conj(U_k) + c U_k (U: the input half spectrum, DFT with exp(-...)).
+struct D2Dir {
+  std::vector<BlockDev> in_host, out_host;
+  void* in_dev = nullptr;              // BlockDev[nb]
+  void* out_dev = nullptr;             // BlockDev[nb]
+  int64_t spec_in = 0, spec_out = 0;   // complex elements per RHS over all blocks
+  int64_t parts = 0;                   // real elements per RHS: every block's valid outputs
+  int64_t rows = 0, nnz = 0;           // CSR rows (output bins of all blocks) and entries
+  int64_t* ptr = nullptr;              // [rows + 1]
+  int* idx = nullptr;                  // [nnz] input bin
+  void* a = nullptr;                   // [nnz] complex, plan precision
+  void* c = nullptr;                   // [nnz]
+  int* row_blk = nullptr;              // [rows] block of the row
+  int* row_loc = nullptr;              // [rows] output bin within the block
+  int64_t* part_off = nullptr;         // [nb] per-RHS offset of the block's valid outputs
+  int max_n_in = 0, max_n_out = 0;
+  // combine: output index o gets entries comb_ent[comb_ptr[o] .. comb_ptr[o+1]):
+  // b >= 0 a block's partial, ~d a dense rectangle
+  int* comb_ptr = nullptr;             // [N + 1]
+  int* comb_ent = nullptr;
+};
+struct D2Rect {
+  int r0, r1, c0, c1;
+  int64_t off;                         // row-major values [r1 - r0][c1 - c0] at dense + off
+};
+struct D2Plan {
+  int nb = 0;
+  D2Dir fwd, adj;
+  std::vector<D2Rect> rects_host;
+  D2Rect* rects = nullptr;
+  void* dense = nullptr;               // plan precision
+  double* lam = nullptr;               // Lambda table of A^[1]
+  int64_t dense_elems = 0, kept = 0;
+};
+
 // ------------------------------------------------------------------- the plan
 struct Plan {
   int64_t N = 0;
@@ -146,6 +189,9 @@ struct Plan {
   // first c_vpad bins after bin L-1 so that no band read wraps
   bool cplx = false;
   int c_vpad = 0;
+  // XC_SCHEME_2D (xc_2d.cu); node spacing of the equispaced nodes
+  D2Plan* d2 = nullptr;
+  double x0 = 0, h = 0;
   // adjoint items of the complex block: (bin slice, chunk of 64 rows), item
   // g = c_cbase[slice] + chunk
   int2* c_items = nullptr;
@@ -179,7 +225,7 @@ int plan_alloc(Plan* p, void** ptr, size_t bytes);
 // Kernel identities for the launch counter and the per-kernel timing.
 enum KernelId {
   K_FWD_FFT = 0, K_FWD_SPARSE, K_ADJ_SPARSE, K_ADJ_FFT, K_ADJ_TAIL, K_FWD_REDUCE, K_ADJ_TRANSPOSE, K_PAIR_SCALE,
-  K_ROW_SCALE, K_COUNT
+  K_ROW_SCALE, K_2D_FFT_IN, K_2D_SPARSE, K_2D_FFT_OUT, K_2D_COMBINE, K_COUNT
 };
 
 // Row stride of the transposed adjoint input: nrhs rounded up to 8.
@@ -202,6 +248,9 @@ int dense_matrix_device(const Plan* p, void* A, int64_t lda, cudaStream_t s);
 int ensure_scratch(Plan* p, int64_t nrhs);
 int launch_apply(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t s);
 int launch_apply_adjoint(Plan* p, const void* y, void* x, int64_t nrhs, int64_t ld, cudaStream_t s);
+// (xc_2d.cu) execution of the 2-D block scheme
+size_t d2_scratch_bytes(const Plan* p, int64_t nrhs);
+int launch_apply_2d(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t s, bool adjoint);
 // (xc_complex.cu) execution of the complex families
 size_t complex_scratch_bytes(const Plan* p, int64_t nrhs);
 int launch_apply_complex(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t s);

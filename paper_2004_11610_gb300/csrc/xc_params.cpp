@@ -94,7 +94,7 @@ int fft_radices(int64_t n, int* radix) {
 // Smallest s >= 1 with w_s^{zeta, L-1} >= eps2, L = m + 2s (two-sided) or m + s
 // (one-sided): the extra components keep the window of every real component
 // at eps2 or above (Section 2.2, sequential search over s).
-static int64_t extra_count(int64_t m, double zeta, double eps2, bool two_sided) {
+int64_t extra_count(int64_t m, double zeta, double eps2, bool two_sided) {
   for (int64_t s = 1; s <= 50 * m + 100; ++s) {
     const int64_t length = two_sided ? m + 2 * s : m + s;
     if (kaiser_value_host(double(s), length, zeta) >= eps2) return s;

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -989,6 +990,68 @@ __global__ void c_dense_kernel(GenParams g, const cx<T>* rowscale, cx<T>* A, int
   A[n * lda + m] = a;
 }
 
+// ------------------------------------------------------- 2-D block scheme
+// Lambda(z) = Gamma(z + 1/2) / Gamma(z + 1) from a table (built on the host by
+// the recurrence Lambda(z) = Lambda(z - 1) (2z - 1) / (2z) in long double).
+__device__ __forceinline__ double kernel_a1(int64_t i, int64_t j, const double* lam) {
+  if (i > j) return 0.0;
+  if (i == 0) return lam[j] * 0.3183098861837907;          // 1/pi
+  return 0.6366197723675814 * lam[j - i] * lam[j + i];      // 2/pi
+}
+
+__device__ __forceinline__ double kernel_a2(int64_t i, int64_t j) {
+  if (i == j) return 0.0;
+  auto g = [](int64_t k) { return k > 0 ? double(k) * cos(2.0 * log(double(k))) : 0.0; };
+  const double d = double(i - j);
+  return (g(i) - g(j)) / (d * d);
+}
+
+// W_r D_e W_c of a 2-D block, column-major for the row FFT: G[j * C + i] =
+// D(r0 + i, c0 + j) wr[i] wc[j], i < Lr (= C), j < Lc.  Functions at nodes:
+// one thread per row i (recurrence over the degrees; g.x holds the block's
+// row nodes); index kernels: one thread per element.
+__global__ void gen2d_rows_kernel(GenParams g, int64_t Lr, int64_t c0, int64_t Lc, const double* wr,
+                                  const double* wc, double* G) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= Lr) return;
+  const double a = wr[i];
+  gen_values(g, i, c0, c0 + Lc, [&](int64_t m, double v) { G[(m - c0) * Lr + i] = v * a * wc[m - c0]; });
+}
+
+__global__ void gen2d_kernel_elems(int kind, int64_t r0, int64_t Lr, int64_t c0, int64_t Lc, const double* wr,
+                                   const double* wc, const double* lam, double* G) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i >= Lr || j >= Lc) return;
+  const double v = kind == XC_KERNEL_A1 ? kernel_a1(r0 + i, c0 + j, lam) : kernel_a2(r0 + i, c0 + j);
+  G[j * Lr + i] = v * wr[i] * wc[j];
+}
+
+// S[i][q] (Lr x Hc complex) -> the real and imaginary parts as rows q of
+// length Lr for the second row FFT: Re[i * Hc + q], Im[i * Hc + q].
+__global__ void split2d_kernel(const cx<double>* S, int64_t Lr, int64_t Hc, double* Re, double* Im) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= Lr * Hc) return;
+  Re[e] = S[e].re;
+  Im[e] = S[e].im;
+}
+
+// Entries of a rectangle [r0, r1) x [c0, c1), row i at out + i * ldo, in the
+// plan precision (g.x holds the rectangle's row nodes).
+template <typename T>
+__global__ void rect2d_kernel(GenParams g, int kind, int64_t r0, int64_t r1, int64_t c0, int64_t c1,
+                              const double* lam, T* out, int64_t ldo) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= r1 - r0) return;
+  const int64_t w = c1 - c0;
+  if (kind == XC_KERNEL_A1 || kind == XC_KERNEL_A2) {
+    for (int64_t j = 0; j < w; ++j)
+      out[i * ldo + j] = T(kind == XC_KERNEL_A1 ? kernel_a1(r0 + i, c0 + j, lam) : kernel_a2(r0 + i, c0 + j));
+  } else {
+    gen_values(g, i, c0, c1, [&](int64_t m, double v) { out[i * ldo + (m - c0)] = T(v); });
+  }
+}
+
 // Dense tail [m][N] and the plain matrix (comparison path).
 template <typename T>
 __global__ void tail_kernel(GenParams g, int64_t m_tail, T* tail) {
@@ -1034,6 +1097,17 @@ int dense_matrix_device(const Plan* p, void* A, int64_t lda, cudaStream_t s) {
   GenParams g{p->family, p->N, p->params.alpha, p->params.beta, p->nodes_dev,
               is_trig(p->family) && p->family != XC_LAGUERRE_SPECTRAL && p->params.nodes == XC_NODES_GAUSS,
               p->params.power, p->rc_dev, p->nrc};
+  if (p->d2) {
+    // the whole index square as one rectangle
+    g.x = p->nodes_dev;
+    const unsigned gr = unsigned((p->N + 31) / 32);
+    if (p->io64())
+      rect2d_kernel<double><<<gr, 32, 0, s>>>(g, p->family, 0, p->N, 0, p->N, p->d2->lam, static_cast<double*>(A), lda);
+    else
+      rect2d_kernel<float><<<gr, 32, 0, s>>>(g, p->family, 0, p->N, 0, p->N, p->d2->lam, static_cast<float*>(A), lda);
+    XC_CUDA(cudaGetLastError());
+    return XC_OK;
+  }
   if (p->cplx) {
     const dim3 grid(unsigned((p->N + 127) / 128), unsigned(p->N));
     if (p->io64())
@@ -1680,11 +1754,400 @@ int build_block_complex(Plan* p, const GenParams& g, const BlockShape& shp) {
   return XC_OK;
 }
 
+// One transform side (length L) of a 2-D block: the apply's descriptor in the
+// plan precision (permutation, twiddles, 1/w) and the FP64 window and
+// twiddles of the precompute.
+template <typename T>
+int make_side(Plan* p, int64_t L, BlockDev* d, DevBuf* w64, DevBuf* tw64) {
+  std::memset(d, 0, sizeof(*d));
+  d->L = int(L);
+  d->n = int(L / 2);
+  d->H = d->n + 1;
+  d->a_csize = 1;
+  d->p = fft_radices(d->n, d->radix);
+  if (d->p < 0) return fail(XC_ERR_UNSUPPORTED, "FFT length not 2^a 3^b 5^c 7^d");
+  std::vector<int> perm = digit_reversal(d->n, d->p, d->radix);
+  int* perm_d = nullptr;
+  XC_TRY(upload(p, perm, &perm_d));
+  d->perm = perm_d;
+  void *invw = nullptr, *tw = nullptr;
+  XC_TRY(plan_alloc(p, &invw, size_t(L) * sizeof(T)));
+  XC_TRY(plan_alloc(p, &tw, size_t(L) * sizeof(cx<T>)));
+  XC_TRY(alloc_tmp(w64, size_t(L) * sizeof(double)));
+  XC_TRY(alloc_tmp(tw64, size_t(L) * sizeof(cx<double>)));
+  const unsigned gL = unsigned((L + 255) / 256);
+  window_kernel<T><<<gL, 256>>>(L, p->zeta, static_cast<double*>(w64->ptr), static_cast<T*>(invw));
+  twiddle_kernel<T><<<gL, 256>>>(L, static_cast<cx<T>*>(tw));
+  twiddle_kernel<double><<<gL, 256>>>(L, static_cast<cx<double>*>(tw64->ptr));
+  XC_CUDA(cudaGetLastError());
+  d->invw = invw;
+  d->tw = tw;
+  return XC_OK;
+}
+
+struct Blk2 {
+  int64_t r0, Lr, vr0, r1, c0, Lc, vc0, c1;
+};
+
+// Cover the N x N index square by the valid rectangles of 2-D blocks and
+// dense rectangles: a rectangle takes a block whose first sr rows and sc
+// columns (window below eps2) are left to two further rectangles; a side of
+// at most `tail` makes it dense.
+void decompose_2d(int64_t N, double zeta, double eps2, int64_t tail, std::vector<Blk2>* blocks,
+                  std::vector<D2Rect>* rects) {
+  std::vector<std::array<int64_t, 4>> todo{{0, N, 0, N}};
+  while (!todo.empty()) {
+    const std::array<int64_t, 4> t = todo.back();
+    todo.pop_back();
+    const int64_t r0 = t[0], r1 = t[1], c0 = t[2], c1 = t[3];
+    const int64_t mr = r1 - r0, mc = c1 - c0;
+    if (mr <= 0 || mc <= 0) continue;
+    const D2Rect whole{int(r0), int(r1), int(c0), int(c1), 0};
+    if (mr <= tail || mc <= tail) {
+      rects->push_back(whole);
+      continue;
+    }
+    int64_t sr = extra_count(mr, zeta, eps2, false), sc = extra_count(mc, zeta, eps2, false);
+    if (sr < 0 || sc < 0) {
+      rects->push_back(whole);
+      continue;
+    }
+    const int64_t Lr = fft_friendly_at_least(mr + sr), Lc = fft_friendly_at_least(mc + sc);
+    sr = Lr - mr;
+    sc = Lc - mc;
+    if (sr >= mr || sc >= mc) {
+      rects->push_back(whole);
+      continue;
+    }
+    blocks->push_back(Blk2{r0, Lr, r0 + sr, r1, c0, Lc, c0 + sc, c1});
+    todo.push_back({r0, r0 + sr, c0, c1});
+    todo.push_back({r0 + sr, r1, c0, c0 + sc});
+  }
+}
+
+// Combine lists of the 2-D scheme: output index o (a row for the forward
+// product, a column for the adjoint) takes the partials of the blocks whose
+// valid outputs hold it (entry b), then the dense rectangles that cover it
+// (entry ~d).
+void combine_lists_2d(int64_t N, const std::vector<Blk2>& blks, const std::vector<D2Rect>& rects, bool rows,
+                      std::vector<int>* ptr, std::vector<int>* flat) {
+  std::vector<std::vector<int>> ent(static_cast<size_t>(N));
+  for (size_t bi = 0; bi < blks.size(); ++bi) {
+    const Blk2& b = blks[bi];
+    const int64_t lo = rows ? b.vr0 : b.vc0;
+    const int64_t hi = rows ? b.r1 : b.c1;
+    for (int64_t o = lo; o < hi; ++o) ent[static_cast<size_t>(o)].push_back(static_cast<int>(bi));
+  }
+  for (size_t d = 0; d < rects.size(); ++d) {
+    const int lo = rows ? rects[d].r0 : rects[d].c0;
+    const int hi = rows ? rects[d].r1 : rects[d].c1;
+    for (int o = lo; o < hi; ++o) ent[static_cast<size_t>(o)].push_back(~static_cast<int>(d));
+  }
+  ptr->assign(static_cast<size_t>(N) + 1, 0);
+  flat->clear();
+  for (int64_t o = 0; o < N; ++o) {
+    (*ptr)[static_cast<size_t>(o)] = static_cast<int>(flat->size());
+    flat->insert(flat->end(), ent[static_cast<size_t>(o)].begin(), ent[static_cast<size_t>(o)].end());
+  }
+  (*ptr)[static_cast<size_t>(N)] = static_cast<int>(flat->size());
+}
+
+// The 2-D block scheme's precompute.  Per block: W_r D_e W_c generated on the
+// device, FFT of every row along the columns (row_fft_kernel), then of every
+// column along the rows (its real and imaginary parts as two real row
+// transforms), giving S = DFT2(W_r D_e W_c) / (Lr Lc) = D̈ / sqrt(Lr Lc) for
+// row bins p < Lr and column bins q <= Lc/2; the other columns follow from
+// S[p][Lc - q] = conj(S[(Lr - p) % Lr][q]) (real D_e).  Elements with
+// |S|^2 <= eps1^2 max|S|^2 are dropped and each direction's product is stored
+// as a CSR over its output half-spectrum bins.
+template <typename T>
+int build_plan_2d(Plan* p) {
+  const int64_t N = p->N;
+  const bool kernel = p->family == XC_KERNEL_A1 || p->family == XC_KERNEL_A2;
+  auto* d2 = new (std::nothrow) D2Plan();
+  if (!d2) return fail(XC_ERR_ALLOC, "host allocation failed");
+  p->d2 = d2;
+  std::vector<Blk2> blks;
+  const int64_t tail = p->params.tail_max > 0 ? p->params.tail_max : 20;
+  decompose_2d(N, p->zeta, p->eps2, tail, &blks, &d2->rects_host);
+  const int nb = int(blks.size());
+  d2->nb = nb;
+  int64_t mmax = N + 2, rmax = N;
+  for (const auto& b : blks) {
+    mmax = std::max(mmax, b.c0 + b.Lc + 2);
+    rmax = std::max(rmax, b.r0 + b.Lr);
+  }
+  int dev = 0, optin = 0;
+  XC_CUDA(cudaGetDevice(&dev));
+  XC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  for (const auto& b : blks)
+    if (size_t(std::max(b.Lr, b.Lc) / 2) * sizeof(cx<double>) + 1024 > size_t(optin))
+      return fail(XC_ERR_UNSUPPORTED, "2-D block side above one CTA's shared memory for L/2 FP64 values");
+  // generation helpers: recurrence coefficients (functions) or the Lambda
+  // table (A^[1]), node arrays per block
+  GenParams g{p->family, N, 0.0, 0.0, nullptr, 0, 0};
+  XC_TRY(plan_alloc(p, reinterpret_cast<void**>(&p->nodes_dev), size_t(N) * sizeof(double)));
+  XC_CUDA(cudaMemcpy(p->nodes_dev, p->nodes_host.data(), size_t(N) * sizeof(double), cudaMemcpyHostToDevice));
+  const double* lamp = nullptr;
+  if (kernel) {
+    const int64_t K = 2 * std::max(mmax, rmax) + 4;
+    std::vector<double> lam(K);
+    long double v = 1.7724538509055160272981674833411452L;   // sqrt(pi) = Lambda(0)
+    for (int64_t z = 0; z < K; ++z) {
+      if (z > 0) v = v * (2.0L * z - 1.0L) / (2.0L * z);
+      lam[z] = double(v);
+    }
+    double* lamd = nullptr;
+    XC_TRY(upload(p, lam, &lamd));
+    d2->lam = lamd;
+    lamp = lamd;
+  } else {
+    const std::vector<double> rc = recurrence_table(p->family, 0.0, 0.0, mmax + 1);
+    XC_TRY(plan_alloc(p, reinterpret_cast<void**>(&p->rc_dev), rc.size() * sizeof(double)));
+    XC_CUDA(cudaMemcpy(p->rc_dev, rc.data(), rc.size() * sizeof(double), cudaMemcpyHostToDevice));
+    p->nrc = mmax + 1;
+    g.rc = p->rc_dev;
+    g.nrc = p->nrc;
+  }
+  auto node_array = [&](int64_t r0, int64_t rows, DevBuf* buf) -> int {
+    std::vector<double> x(rows);
+    for (int64_t i = 0; i < rows; ++i) x[i] = p->x0 + p->h * double(r0 + i);
+    XC_TRY(alloc_tmp(buf, size_t(rows) * sizeof(double)));
+    XC_CUDA(cudaMemcpy(buf->ptr, x.data(), size_t(rows) * sizeof(double), cudaMemcpyHostToDevice));
+    return XC_OK;
+  };
+
+  d2->fwd.in_host.resize(nb);
+  d2->fwd.out_host.resize(nb);
+  d2->adj.in_host.resize(nb);
+  d2->adj.out_host.resize(nb);
+  struct Csr {
+    std::vector<int64_t> ptr{0};
+    std::vector<int> idx, blk, loc;
+    std::vector<cx<T>> a, c;
+  } fcsr, acsr;
+  int64_t kept_total = 0;
+  int64_t fspec_in = 0, fspec_out = 0, aspec_in = 0, aspec_out = 0, fparts = 0, aparts = 0;
+  std::vector<int64_t> fpart_off(nb), apart_off(nb);
+  for (int bi = 0; bi < nb; ++bi) {
+    const Blk2& B = blks[bi];
+    BlockDev col, row;
+    DevBuf wc64, twc64, wr64, twr64;
+    XC_TRY(make_side<T>(p, B.Lc, &col, &wc64, &twc64));
+    XC_TRY(make_side<T>(p, B.Lr, &row, &wr64, &twr64));
+    const int64_t Lr = B.Lr, Lc = B.Lc, Hr = row.H, Hc = col.H;
+    // W_r D_e W_c, column-major [Lc][Lr]
+    DevBuf G;
+    XC_TRY(alloc_tmp(&G, size_t(Lr) * size_t(Lc) * sizeof(double)));
+    if (kernel) {
+      gen2d_kernel_elems<<<dim3(unsigned((Lr + 127) / 128), unsigned(Lc)), 128>>>(
+          p->family, B.r0, Lr, B.c0, Lc, static_cast<double*>(wr64.ptr), static_cast<double*>(wc64.ptr), lamp,
+          static_cast<double*>(G.ptr));
+    } else {
+      DevBuf xn;
+      XC_TRY(node_array(B.r0, Lr, &xn));
+      GenParams gb = g;
+      gb.x = static_cast<double*>(xn.ptr);
+      gen2d_rows_kernel<<<unsigned((Lr + 31) / 32), 32>>>(gb, Lr, B.c0, Lc, static_cast<double*>(wr64.ptr),
+                                                          static_cast<double*>(wc64.ptr),
+                                                          static_cast<double*>(G.ptr));
+      XC_CUDA(cudaDeviceSynchronize());
+    }
+    XC_CUDA(cudaGetLastError());
+    // along the columns: S1[i][q], q <= Lc/2 (scaled 1/Lc)
+    DevBuf S1, dummy;
+    XC_TRY(alloc_tmp(&S1, size_t(Lr) * size_t(Hc) * sizeof(cx<double>)));
+    XC_TRY(alloc_tmp(&dummy, sizeof(unsigned long long)));
+    XC_TRY(set_smem(reinterpret_cast<const void*>(row_fft_kernel),
+                    size_t(std::max(col.n, row.n)) * sizeof(cx<double>)));
+    row_fft_kernel<<<unsigned(Lr), 256, size_t(col.n) * sizeof(cx<double>)>>>(
+        static_cast<double*>(G.ptr), Lr, 0, Lr, col, static_cast<cx<double>*>(twc64.ptr),
+        static_cast<cx<double>*>(S1.ptr), static_cast<unsigned long long*>(dummy.ptr));
+    XC_CUDA(cudaGetLastError());
+    // along the rows: real and imaginary parts of every column bin q
+    DevBuf Re, Im, A, Bm;
+    XC_TRY(alloc_tmp(&Re, size_t(Lr) * size_t(Hc) * sizeof(double)));
+    XC_TRY(alloc_tmp(&Im, size_t(Lr) * size_t(Hc) * sizeof(double)));
+    split2d_kernel<<<unsigned((Lr * Hc + 255) / 256), 256>>>(static_cast<cx<double>*>(S1.ptr), Lr, Hc,
+                                                              static_cast<double*>(Re.ptr),
+                                                              static_cast<double*>(Im.ptr));
+    XC_TRY(alloc_tmp(&A, size_t(Hc) * size_t(Hr) * sizeof(cx<double>)));
+    XC_TRY(alloc_tmp(&Bm, size_t(Hc) * size_t(Hr) * sizeof(cx<double>)));
+    const size_t rsm = size_t(row.n) * sizeof(cx<double>);
+    row_fft_kernel<<<unsigned(Hc), 256, rsm>>>(static_cast<double*>(Re.ptr), Hc, 0, Hc, row,
+                                                static_cast<cx<double>*>(twr64.ptr), static_cast<cx<double>*>(A.ptr),
+                                                static_cast<unsigned long long*>(dummy.ptr));
+    row_fft_kernel<<<unsigned(Hc), 256, rsm>>>(static_cast<double*>(Im.ptr), Hc, 0, Hc, row,
+                                                static_cast<cx<double>*>(twr64.ptr), static_cast<cx<double>*>(Bm.ptr),
+                                                static_cast<unsigned long long*>(dummy.ptr));
+    XC_CUDA(cudaGetLastError());
+    std::vector<cx<double>> Ah(size_t(Hc) * size_t(Hr)), Bh(size_t(Hc) * size_t(Hr));
+    XC_CUDA(cudaMemcpy(Ah.data(), A.ptr, Ah.size() * sizeof(cx<double>), cudaMemcpyDeviceToHost));
+    XC_CUDA(cudaMemcpy(Bh.data(), Bm.ptr, Bh.size() * sizeof(cx<double>), cudaMemcpyDeviceToHost));
+    // S(p, q) for p < Lr, q <= Lc/2: A_full + i B_full along p
+    auto S = [&](int64_t pp, int64_t q) {
+      cx<double> a, b;
+      if (pp <= Lr / 2) {
+        a = Ah[size_t(q) * Hr + pp];
+        b = Bh[size_t(q) * Hr + pp];
+      } else {
+        a = Ah[size_t(q) * Hr + (Lr - pp)];
+        b = Bh[size_t(q) * Hr + (Lr - pp)];
+        a.im = -a.im;
+        b.im = -b.im;
+      }
+      return cx<double>{a.re - b.im, a.im + b.re};
+    };
+    auto sq = [](cx<double> v) { return v.re * v.re + v.im * v.im; };
+    double maxsq = 0.0;
+    for (int64_t pp = 0; pp < Lr; ++pp)
+      for (int64_t q = 0; q < Hc; ++q) maxsq = std::max(maxsq, sq(S(pp, q)));
+    const double thr = p->eps > 0 ? (p->eps * p->eps) * maxsq : -1.0;
+    for (int64_t pp = 0; pp < Lr; ++pp)
+      for (int64_t q = 0; q < Hc; ++q)
+        if (sq(S(pp, q)) > thr) kept_total += (q > 0 && q < Lc / 2) ? 2 : 1;
+    auto cvt = [](cx<double> v) { return cx<T>{T(v.re), T(v.im)}; };
+    // forward: z_p = sum_q a conj(U_q) + c U_q, a = S(p, q), c = conj(S(-p, q)) (0 < q < Lc/2)
+    for (int64_t pp = 0; pp < Hr; ++pp) {
+      for (int64_t q = 0; q < Hc; ++q) {
+        const cx<double> a = S(pp, q);
+        const bool ka = sq(a) > thr;
+        cx<double> c{0.0, 0.0};
+        bool kc = false;
+        if (q > 0 && q < Lc / 2) {
+          const cx<double> m = S((Lr - pp) % Lr, q);
+          kc = sq(m) > thr;
+          c = cx<double>{m.re, -m.im};
+        }
+        if (!ka && !kc) continue;
+        fcsr.idx.push_back(int(q));
+        fcsr.a.push_back(ka ? cvt(a) : cx<T>{T(0), T(0)});
+        fcsr.c.push_back(kc ? cvt(c) : cx<T>{T(0), T(0)});
+      }
+      fcsr.ptr.push_back(int64_t(fcsr.idx.size()));
+      fcsr.blk.push_back(bi);
+      fcsr.loc.push_back(int(pp));
+    }
+    // adjoint: z_q = sum_p a conj(U_p) + c U_p, a = S(p, q), c = S(Lr - p, q) (0 < p < Lr/2)
+    for (int64_t q = 0; q < Hc; ++q) {
+      for (int64_t pp = 0; pp < Hr; ++pp) {
+        const cx<double> a = S(pp, q);
+        const bool ka = sq(a) > thr;
+        cx<double> c{0.0, 0.0};
+        bool kc = false;
+        if (pp > 0 && pp < Lr / 2) {
+          c = S(Lr - pp, q);
+          kc = sq(c) > thr;
+        }
+        if (!ka && !kc) continue;
+        acsr.idx.push_back(int(pp));
+        acsr.a.push_back(ka ? cvt(a) : cx<T>{T(0), T(0)});
+        acsr.c.push_back(kc ? cvt(c) : cx<T>{T(0), T(0)});
+      }
+      acsr.ptr.push_back(int64_t(acsr.idx.size()));
+      acsr.blk.push_back(bi);
+      acsr.loc.push_back(int(q));
+    }
+    // descriptors: the column side takes the forward inputs and the adjoint
+    // outputs, the row side the forward outputs and the adjoint inputs
+    col.off = -int(B.c0);
+    col.j_lo = int(B.vc0 - B.c0);
+    col.j_hi = int(B.c1 - B.c0);
+    row.off = -int(B.r0);
+    row.j_lo = int(B.vr0 - B.r0);
+    row.j_hi = int(B.r1 - B.r0);
+    d2->fwd.in_host[bi] = col;
+    d2->fwd.in_host[bi].spec_off = fspec_in;
+    d2->fwd.out_host[bi] = row;
+    d2->fwd.out_host[bi].spec_off = fspec_out;
+    d2->adj.in_host[bi] = row;
+    d2->adj.in_host[bi].spec_off = aspec_in;
+    d2->adj.out_host[bi] = col;
+    d2->adj.out_host[bi].spec_off = aspec_out;
+    fspec_in += Hc;
+    fspec_out += Hr;
+    aspec_in += Hr;
+    aspec_out += Hc;
+    fpart_off[bi] = fparts;
+    fparts += B.r1 - B.vr0;
+    apart_off[bi] = aparts;
+    aparts += B.c1 - B.vc0;
+    d2->fwd.max_n_in = std::max(d2->fwd.max_n_in, col.n);
+    d2->fwd.max_n_out = std::max(d2->fwd.max_n_out, row.n);
+    d2->adj.max_n_in = std::max(d2->adj.max_n_in, row.n);
+    d2->adj.max_n_out = std::max(d2->adj.max_n_out, col.n);
+  }
+  d2->kept = kept_total;
+  // device copies
+  auto put_dir = [&](D2Dir& D, Csr& C, int64_t spec_in, int64_t spec_out, int64_t parts,
+                     const std::vector<int64_t>& part_off) -> int {
+    D.spec_in = spec_in;
+    D.spec_out = spec_out;
+    D.parts = parts;
+    D.rows = int64_t(C.blk.size());
+    D.nnz = int64_t(C.idx.size());
+    XC_TRY(upload(p, D.in_host, reinterpret_cast<BlockDev**>(&D.in_dev)));
+    XC_TRY(upload(p, D.out_host, reinterpret_cast<BlockDev**>(&D.out_dev)));
+    XC_TRY(upload(p, C.ptr, &D.ptr));
+    XC_TRY(upload(p, C.idx, &D.idx));
+    XC_TRY(upload(p, C.blk, &D.row_blk));
+    XC_TRY(upload(p, C.loc, &D.row_loc));
+    cx<T>* a = nullptr;
+    cx<T>* c = nullptr;
+    XC_TRY(upload(p, C.a, &a));
+    XC_TRY(upload(p, C.c, &c));
+    D.a = a;
+    D.c = c;
+    XC_TRY(upload(p, part_off, &D.part_off));
+    return XC_OK;
+  };
+  XC_TRY(put_dir(d2->fwd, fcsr, fspec_in, fspec_out, fparts, fpart_off));
+  XC_TRY(put_dir(d2->adj, acsr, aspec_in, aspec_out, aparts, apart_off));
+  // dense rectangles
+  int64_t dense_elems = 0;
+  for (auto& r : d2->rects_host) {
+    r.off = dense_elems;
+    dense_elems += int64_t(r.r1 - r.r0) * (r.c1 - r.c0);
+  }
+  d2->dense_elems = dense_elems;
+  XC_TRY(plan_alloc(p, &d2->dense, size_t(std::max<int64_t>(1, dense_elems)) * sizeof(T)));
+  for (const auto& r : d2->rects_host) {
+    DevBuf xn;
+    GenParams gr = g;
+    if (!kernel) {
+      XC_TRY(node_array(r.r0, r.r1 - r.r0, &xn));
+      gr.x = static_cast<double*>(xn.ptr);
+    }
+    rect2d_kernel<T><<<unsigned((r.r1 - r.r0 + 31) / 32), 32>>>(gr, p->family, r.r0, r.r1, r.c0, r.c1, lamp,
+                                                                 static_cast<T*>(d2->dense) + r.off, r.c1 - r.c0);
+    XC_CUDA(cudaGetLastError());
+    XC_CUDA(cudaDeviceSynchronize());
+  }
+  XC_TRY(upload(p, d2->rects_host, &d2->rects));
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<int> ptr, flat;
+    combine_lists_2d(N, blks, d2->rects_host, dir == 0, &ptr, &flat);
+    D2Dir& D = dir == 0 ? d2->fwd : d2->adj;
+    XC_TRY(upload(p, ptr, &D.comb_ptr));
+    XC_TRY(upload(p, flat, &D.comb_ent));
+  }
+  p->matrix_bytes = d2->fwd.nnz * int64_t(2 * sizeof(cx<T>) + sizeof(int)) + dense_elems * int64_t(sizeof(T));
+  p->adjoint_bytes = d2->adj.nnz * int64_t(2 * sizeof(cx<T>) + sizeof(int));
+  return XC_OK;
+}
+
 }  // namespace
 
 int build_plan_device(Plan* p) {
   const int64_t N = p->N;
   const unsigned gN = unsigned((N + 127) / 128);
+  if (p->scheme == XC_SCHEME_2D) {
+    // nodes: the equispaced nodes (functions) or the row indices (index kernels)
+    p->nodes_host.resize(N);
+    for (int64_t i = 0; i < N; ++i) p->nodes_host[i] = p->x0 + p->h * double(i);
+    if (p->io64()) return build_plan_2d<double>(p);
+    return build_plan_2d<float>(p);
+  }
   XC_TRY(plan_alloc(p, reinterpret_cast<void**>(&p->nodes_dev), size_t(N) * sizeof(double)));
   const bool user = p->params.nodes == XC_NODES_USER;
   if (p->cplx) {

@@ -21,10 +21,10 @@ _lib = ctypes.CDLL(_LIB_PATH)
 # ------------------------------------------------------------------ constants
 XC_OK, XC_ERR_ARG, XC_ERR_ALLOC, XC_ERR_CUDA, XC_ERR_TIMEOUT, XC_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 FAMILY = {"chebyshev": 0, "legendre": 1, "jacobi": 2, "laguerre": 3, "hermite": 4, "sine": 5, "cospow": 6,
-          "exp": 7, "lagspec": 8}
+          "exp": 7, "lagspec": 8, "a1": 9, "a2": 10}
 COMPLEX_FAMILIES = ("exp", "lagspec")
 PRECISION = {"fp64": 0, "fp32": 1, "fp32c": 2, "fp64pair": 3}
-SCHEME = {"auto": 0, "two_sided": 1, "blocks": 2}
+SCHEME = {"auto": 0, "two_sided": 1, "blocks": 2, "2d": 3}
 XC_MAX_BLOCKS = 16
 
 
@@ -45,7 +45,9 @@ class xc_plan_stats(ctypes.Structure):
                 ("eps2", ctypes.c_double), ("zeta", ctypes.c_double), ("nblocks", ctypes.c_int),
                 ("L", _I64x), ("off", _I64x), ("j_lo", _I64x), ("j_hi", _I64x), ("nnz", _I64x),
                 ("stored", _I64x), ("maxabs", ctypes.c_double * XC_MAX_BLOCKS), ("m_tail", ctypes.c_int64),
-                ("matrix_bytes", ctypes.c_int64), ("adjoint_bytes", ctypes.c_int64), ("closed_form_blocks", ctypes.c_int)]
+                ("matrix_bytes", ctypes.c_int64), ("adjoint_bytes", ctypes.c_int64), ("closed_form_blocks", ctypes.c_int),
+                ("blocks2d", ctypes.c_int), ("dense2d", ctypes.c_int), ("nnz2d", ctypes.c_int64),
+                ("dense_elems2d", ctypes.c_int64)]
 
 
 class xc_kernel_time(ctypes.Structure):
@@ -123,7 +125,10 @@ class Plan:
     """A compressed operator for A[n, m] = phi_m(x_n) (xc_plan_create).
 
     family     'chebyshev' | 'legendre' | 'jacobi' | 'laguerre' | 'hermite' | 'sine' | 'cospow'
-               | 'exp' | 'lagspec' (the last two complex: complex128 / complex64 tensors)
+               | 'exp' | 'lagspec' (complex: complex128 / complex64 tensors) | 'a1' | 'a2'
+               (index kernels of Section 5.3, scheme '2d')
+    scheme     'auto' | 'two_sided' | 'blocks' | '2d' (2-D compression; Laguerre / Hermite
+               functions at equispaced `nodes`, or 'a1' / 'a2')
     N          order of the square matrix
     eps        eps1: threshold and Kaiser shape (0 keeps every element)
     precision  'fp64' | 'fp32' | 'fp32c' (FP32 with compensated accumulation) | 'fp64pair'
@@ -212,6 +217,7 @@ class Plan:
             "j_hi": list(st.j_hi[:nb]), "nnz": list(st.nnz[:nb]), "stored": list(st.stored[:nb]),
             "maxabs": list(st.maxabs[:nb]), "m_tail": st.m_tail, "matrix_bytes": st.matrix_bytes,
             "adjoint_bytes": st.adjoint_bytes, "closed_form_blocks": st.closed_form_blocks,
+            "blocks2d": st.blocks2d, "dense2d": st.dense2d, "nnz2d": st.nnz2d, "dense_elems2d": st.dense_elems2d,
         }
 
     def nodes(self) -> np.ndarray:

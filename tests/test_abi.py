@@ -71,7 +71,7 @@ def test_structure_layouts_match_the_header(xc):
     # offsets fixed by the C layout of include/xc.h (LP64)
     assert ctypes.sizeof(xc.xc_params) == 80
     assert xc.xc_plan_stats.L.offset == 56
-    assert ctypes.sizeof(xc.xc_plan_stats) == 56 + 7 * 8 * 16 + 24 + 8
+    assert ctypes.sizeof(xc.xc_plan_stats) == 56 + 7 * 8 * 16 + 24 + 32
 
 
 def test_ctypes_mirrors_match_a_c_compiler(xc, tmp_path):
