@@ -76,11 +76,44 @@ def plan_specs(wl):
     return out
 
 
+def plan_label(fam, N, params):
+    return f"{fam} N={N}" + "".join(f" {k}={v}" for k, v in sorted(params.items()))
+
+
+def laguerre_transform_nodes(N, eta):
+    """The Laguerre transform's points x_i = eta t_i, t_i = 12 (i + 1) / (N - 1)
+    (Section 5.3's t_i = 12 i / (N - 1), i = 1..N)."""
+    h = 12.0 * eta / (N - 1)
+    return h * (1.0 + np.arange(N))
+
+
+def make_xc_plan(xc, fam, N, params, eps, precision):
+    if params.get("scheme") == "2d":
+        nodes = laguerre_transform_nodes(N, params["eta"]) if fam in ("laguerre", "hermite") else None
+        return xc.Plan(fam, N, eps, precision=precision, nodes=nodes, scheme="2d")
+    return xc.Plan(fam, N, eps, precision=precision, alpha=params.get("alpha", 0.0), beta=params.get("beta", 0.0))
+
+
+def oracle_apply_pair(fam, N, params, eps, precision):
+    """(forward, adjoint) of the oracle's plan for one plan of a workload, with
+    the library's schedule (eps2 default of the precision)."""
+    from oracle import families as F
+    from oracle import method as M
+    prec = "fp64" if precision == "fp64pair" else precision
+    if params.get("scheme") == "2d":
+        from oracle import method2d as M2
+        h = 12.0 * params["eta"] / (N - 1)
+        P = M2.build(M2.Spec2D(fam, N, h, h), eps, eps2=M.default_eps2(prec))
+        return (lambda X: M2.apply(P, X)), (lambda Y: M2.apply_adjoint(P, Y))
+    sp = F.make_spec(fam, N, params.get("alpha", 0.0), params.get("beta", 0.0))
+    P = M.build(sp, eps, precision=prec)
+    return (lambda X: M.apply(P, X)), (lambda Y: M.apply_adjoint(P, Y))
+
+
 def workload_config(name, wl):
     return {
         "workload": name,
-        "plans": [f"{fam} N={N}" + (f" alpha={p['alpha']} beta={p['beta']}" if p else "")
-                  for fam, N, p in wl["plans"]],
+        "plans": [plan_label(fam, N, p) for fam, N, p in wl["plans"]],
         "nodes": ("angles: arc midpoints (2n+1-N) pi/N (exp), psi_j = 2 arctan(2 k_j/eta) - pi "
                   "(spectral Laguerre)" if any(f in ("exp", "lagspec") for f, _, _ in wl["plans"])
                   else "Gauss nodes of each family (Chebyshev-Gauss for Chebyshev)"),
@@ -233,19 +266,14 @@ def time_oracle(wl, sample_rhs, min_seconds, max_reps=1000):
     """The FP64 oracle (as it stands) on the host: forward + adjoint apply of
     every plan on `sample_rhs` right-hand sides, repeated for >= min_seconds.
     Plan construction (the precompute) is not timed."""
-    from oracle import families as F
-    from oracle import method as M
     plans = []
     for i, (fam, N, params) in enumerate(wl["plans"]):
-        sp = F.make_spec(fam, N, params.get("alpha", 0.0), params.get("beta", 0.0))
-        prec = "fp64" if wl["precision"] == "fp64pair" else wl["precision"]   # same schedule (eps2) as the library
-        plans.append((M.build(sp, wl["eps"], precision=prec),
-                      inputs.draw(wl["dist"], N, sample_rhs, 90, i)))
+        fwd, adj = oracle_apply_pair(fam, N, params, wl["eps"], wl["precision"])
+        plans.append((fwd, adj, inputs.draw(wl["dist"], N, sample_rhs, 90, i)))
     reps, t0 = 0, time.perf_counter()
     while True:
-        for P, X in plans:
-            Y = M.apply(P, X)
-            M.apply_adjoint(P, Y)
+        for fwd, adj, X in plans:
+            adj(fwd(X))
         reps += 1
         el = time.perf_counter() - t0
         if el >= min_seconds or reps >= max_reps:
@@ -257,8 +285,6 @@ def time_oracle(wl, sample_rhs, min_seconds, max_reps=1000):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    from oracle import families as F
-    from oracle import method as M
     if args.workload == "batch1000":
         # bounded sample: the first plans of the batch with N <= 1024
         sample = [w for w in inputs.batch_workload(args.nplans) if w[1] <= 1024][:4]
@@ -268,13 +294,12 @@ def run_reference(args, rank, world):
         wl = inputs.WORKLOADS[args.workload]
     plans = []
     for i, (fam, N, params) in enumerate(wl["plans"]):
-        sp = F.make_spec(fam, N, params.get("alpha", 0.0), params.get("beta", 0.0))
-        prec = "fp64" if wl["precision"] == "fp64pair" else wl["precision"]   # same schedule (eps2) as the library
-        plans.append((M.build(sp, wl["eps"], precision=prec), inputs.draw(wl["dist"], N, 1, 91, i)))
+        fwd, adj = oracle_apply_pair(fam, N, params, wl["eps"], wl["precision"])
+        plans.append((fwd, adj, inputs.draw(wl["dist"], N, 1, 91, i)))
 
     def step():
-        for P, X in plans:
-            M.apply_adjoint(P, M.apply(P, X))
+        for fwd, adj, X in plans:
+            adj(fwd(X))
 
     for _ in range(args.warmup):
         step()
@@ -392,8 +417,7 @@ def run_xc(args, rank, world, local_rank):
     specs = plan_specs(wl)
     plans, X, Y, XA = [], [], [], []
     for s in specs:
-        p = xc.Plan(s["family"], s["N"], wl["eps"], precision=prec,
-                    alpha=s["params"].get("alpha", 0.0), beta=s["params"].get("beta", 0.0))
+        p = make_xc_plan(xc, s["family"], s["N"], s["params"], wl["eps"], prec)
         p.reserve(R)
         plans.append(p)
         x = torch.from_numpy(inputs.draw(wl["dist"], s["N"], R, 1, s["index"], rank)).to(dev, p.torch_dtype)

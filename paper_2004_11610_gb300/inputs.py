@@ -80,6 +80,12 @@ WORKLOADS = {
     "lagspec8192_fp64": dict(
         plans=[("lagspec", 8192, {"alpha": 2500.0, "beta": 4.0})], eps=1e-12, precision="fp64", nrhs=64,
         dist="complex_normal"),
+    # The Laguerre transform matrix of Section 5.3 (Laguerre functions at the
+    # equispaced points eta t_i, t_i = 12 (i+1)/(N-1), eta = 100) under the
+    # 2-D block scheme, N = 4096, eps=1e-10, FP64, 64 standard-normal RHS.
+    "lagtransform4096_2d_fp64": dict(
+        plans=[("laguerre", 4096, {"scheme": "2d", "eta": 100.0})], eps=1e-10, precision="fp64", nrhs=64,
+        dist="normal"),
 }
 
 
