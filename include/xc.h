@@ -262,7 +262,9 @@ typedef struct {
 /* Copy the plan's parameters and per-block statistics into *out. */
 int xc_plan_info(xc_plan_t plan, xc_plan_stats* out);
 
-/* Copy the plan's N nodes (FP64, the order of the rows of A) into host_out. */
+/* Copy the plan's N nodes (FP64, the order of the rows of A) into host_out
+ * (the angles for XC_EXP / XC_LAGUERRE_SPECTRAL, the row indices for the index
+ * kernels). */
 int xc_get_nodes(xc_plan_t plan, double* host_out);
 
 /*
