@@ -3,8 +3,8 @@
 // valid rows, plus the dense rectangles.  The adjoint is the transpose,
 // x_e = W_c^{-1} F* D̈^T F* W_r^{-1} y^{[1]}.  One direction is four launches:
 //   d2_in_kernel       per (RHS, block): the input side's extension, W^{-1} and
-//                      real FFT (the 1-D forward transform body) -> half
-//                      spectrum U (DFT with exp(-2 pi i jk / L))
+//                      real FFT -> half spectrum U (DFT with exp(-2 pi i jk / L)),
+//                      stored bin-major ([bin][RHS]) like the product's output
 //   d2_sparse_kernel   per (output bin of a block, RHS), one warp (lanes over
 //                      the row's entries; with 16 or more RHS d2_sparse_rhs_kernel,
 //                      lanes over 32 RHS): z = sum a conj(U_k) + c U_k over the
@@ -29,13 +29,35 @@ namespace {
 
 constexpr int kD2FftThreads = 256;
 
+// Spectra are stored bin-major, [spec_off + k][nrhs]: the 32 lanes of a CSR
+// warp (32 consecutive RHS) read one contiguous line per entry.
 template <typename T>
 __global__ void __launch_bounds__(kD2FftThreads)
     d2_in_kernel(const BlockDev* __restrict__ devs, const T* __restrict__ x, int64_t ld, cx<T>* __restrict__ spec,
                  int64_t nrhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fwd_fft_body<T>(devs[blockIdx.y], blockIdx.x, x, ld, nullptr, spec, nrhs, reinterpret_cast<cx<T>*>(smem_raw),
-                  threadIdx.x, blockDim.x, nullptr);
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  const BlockDev& b = devs[blockIdx.y];
+  const int64_t r = blockIdx.x;
+  const int n = b.n;
+  const T* __restrict__ invw = static_cast<const T*>(b.invw);
+  const cx<T>* __restrict__ tw = static_cast<const cx<T>*>(b.tw);
+  const T* __restrict__ xr = x + r * ld;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int j0 = 2 * j, j1 = 2 * j + 1;
+    const T u0 = (j0 >= b.j_lo && j0 < b.j_hi) ? xr[j0 - b.off] * invw[j0] : T(0);
+    const T u1 = (j1 >= b.j_lo && j1 < b.j_hi) ? xr[j1 - b.off] * invw[j1] : T(0);
+    s[b.perm[j]] = cx<T>{u0, u1};
+  }
+  __syncthreads();
+  fft_inplace<T>(s, n, b.p, b.radix, tw, threadIdx.x, blockDim.x);
+  cx<T>* __restrict__ out = spec + b.spec_off * nrhs + r;
+  for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
+    cx<T> Uk, Unk;
+    r2c_split_vals(s[k], s[k == 0 ? 0 : n - k], k, tw, &Uk, &Unk);
+    out[int64_t(k) * nrhs] = Uk;
+    if (n - k != k) out[int64_t(n - k) * nrhs] = Unk;
+  }
 }
 
 template <typename T>
@@ -50,10 +72,10 @@ __global__ void d2_sparse_kernel(const BlockDev* __restrict__ in, const BlockDev
   const int64_t row = item / nrhs, r = item % nrhs;
   const int b = row_blk[row];
   const BlockDev& bi = in[b];
-  const cx<T>* __restrict__ U = spec + bi.spec_off * nrhs + r * int64_t(bi.n + 1);
+  const cx<T>* __restrict__ U = spec + bi.spec_off * nrhs + r;
   T re = T(0), im = T(0);
   for (int64_t e = ptr[row] + lane; e < ptr[row + 1]; e += 32) {
-    const cx<T> u = U[idx[e]];
+    const cx<T> u = U[int64_t(idx[e]) * nrhs];
     const cx<T> ae = a[e], ce = c[e];
     // a conj(u) + c u
     re += ae.re * u.re + ae.im * u.im + ce.re * u.re - ce.im * u.im;
@@ -65,7 +87,7 @@ __global__ void d2_sparse_kernel(const BlockDev* __restrict__ in, const BlockDev
   }
   if (lane == 0) {
     const BlockDev& bo = out[b];
-    z[bo.spec_off * nrhs + r * int64_t(bo.n + 1) + row_loc[row]] = cx<T>{re, im};
+    z[(bo.spec_off + row_loc[row]) * nrhs + r] = cx<T>{re, im};
   }
 }
 
@@ -86,17 +108,17 @@ __global__ void d2_sparse_rhs_kernel(const BlockDev* __restrict__ in, const Bloc
   const int64_t rr = r < nrhs ? r : nrhs - 1;
   const int b = row_blk[row];
   const BlockDev& bi = in[b];
-  const cx<T>* __restrict__ U = spec + bi.spec_off * nrhs + rr * int64_t(bi.n + 1);
+  const cx<T>* __restrict__ U = spec + bi.spec_off * nrhs + rr;
   T re = T(0), im = T(0);
   for (int64_t e = ptr[row]; e < ptr[row + 1]; ++e) {
-    const cx<T> u = U[idx[e]];
+    const cx<T> u = U[int64_t(idx[e]) * nrhs];
     const cx<T> ae = a[e], ce = c[e];
     re += ae.re * u.re + ae.im * u.im + ce.re * u.re - ce.im * u.im;
     im += ae.im * u.re - ae.re * u.im + ce.re * u.im + ce.im * u.re;
   }
   if (r < nrhs) {
     const BlockDev& bo = out[b];
-    z[bo.spec_off * nrhs + r * int64_t(bo.n + 1) + row_loc[row]] = cx<T>{re, im};
+    z[(bo.spec_off + row_loc[row]) * nrhs + r] = cx<T>{re, im};
   }
 }
 
@@ -112,9 +134,9 @@ __global__ void __launch_bounds__(kD2FftThreads)
   const int* __restrict__ perm = b.perm;
   const cx<T>* __restrict__ tw = static_cast<const cx<T>*>(b.tw);
   const T* __restrict__ invw = static_cast<const T*>(b.invw);
-  const cx<T>* __restrict__ zr = z + b.spec_off * nrhs + r * int64_t(n + 1);
+  const cx<T>* __restrict__ zr = z + b.spec_off * nrhs + r;
   for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
-    cx<T> Uk = zr[k], Unk = zr[n - k];
+    cx<T> Uk = zr[int64_t(k) * nrhs], Unk = zr[int64_t(n - k) * nrhs];
     if (k == 0) {   // U_0 and U_n enter as real numbers
       Uk.im = T(0);
       Unk.im = T(0);
