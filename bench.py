@@ -578,7 +578,8 @@ def run_xc(args, rank, world, local_rank):
             b.record(stream)
             b.synchronize()
             dms += a.elapsed_time(b)
-        if prec == "fp64" and not args.no_variant and not cplx:
+        two_d = any(sp["params"].get("scheme") == "2d" for sp in specs)
+        if prec == "fp64" and not args.no_variant and not cplx and not two_d:
             variant = measure_pair_variant(xc, torch, wl, specs, dev, max(3, min(args.steps, 50)), 3, world, mats)
         dense = {"vectors_per_s": vectors_per_step * ds / (dms / 1e3), "ms_per_step": dms / ds,
                  "library": "cuBLAS via torch.matmul",

@@ -7,9 +7,10 @@
 //                      stored bin-major ([bin][RHS]) like the product's output
 //   d2_sparse_kernel   per (output bin of a block, RHS), one warp (lanes over
 //                      the row's entries; with 16 or more RHS d2_sparse_rhs_kernel,
-//                      lanes over 32 RHS): z = sum a conj(U_k) + c U_k over the
-//                      bin's CSR row (F* x = conj(U) for real x; c carries the
-//                      other half of the spectrum through the Hermitian symmetries)
+//                      lanes over 32 RHS): z = sum a conj(U_k) + sum c U_k over the
+//                      bin's two CSR segments (F* x = conj(U) for real x; the c
+//                      terms carry the other half of the spectrum through the
+//                      Hermitian symmetries)
 //   d2_out_kernel      per (RHS, block): real inverse FFT of z, W^{-1}, the
 //                      block's valid outputs into its partial buffer
 //   d2_combine_kernel  per (output index, RHS), one warp: the partials of the blocks
@@ -63,8 +64,7 @@ __global__ void __launch_bounds__(kD2FftThreads)
 template <typename T>
 __global__ void d2_sparse_kernel(const BlockDev* __restrict__ in, const BlockDev* __restrict__ out,
                                  const int64_t* __restrict__ ptr, const int* __restrict__ idx,
-                                 const cx<T>* __restrict__ a, const cx<T>* __restrict__ c,
-                                 const int* __restrict__ row_blk, const int* __restrict__ row_loc, int64_t rows,
+                                 const cx<T>* __restrict__ a, const int* __restrict__ row_blk, const int* __restrict__ row_loc, int64_t rows,
                                  const cx<T>* __restrict__ spec, cx<T>* __restrict__ z, int64_t nrhs) {
   const int64_t item = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -74,12 +74,17 @@ __global__ void d2_sparse_kernel(const BlockDev* __restrict__ in, const BlockDev
   const BlockDev& bi = in[b];
   const cx<T>* __restrict__ U = spec + bi.spec_off * nrhs + r;
   T re = T(0), im = T(0);
-  for (int64_t e = ptr[row] + lane; e < ptr[row + 1]; e += 32) {
+  for (int64_t e = ptr[2 * row] + lane; e < ptr[2 * row + 1]; e += 32) {   // a conj(u)
     const cx<T> u = U[int64_t(idx[e]) * nrhs];
-    const cx<T> ae = a[e], ce = c[e];
-    // a conj(u) + c u
-    re += ae.re * u.re + ae.im * u.im + ce.re * u.re - ce.im * u.im;
-    im += ae.im * u.re - ae.re * u.im + ce.re * u.im + ce.im * u.re;
+    const cx<T> ae = a[e];
+    re += ae.re * u.re + ae.im * u.im;
+    im += ae.im * u.re - ae.re * u.im;
+  }
+  for (int64_t e = ptr[2 * row + 1] + lane; e < ptr[2 * row + 2]; e += 32) {   // c u
+    const cx<T> u = U[int64_t(idx[e]) * nrhs];
+    const cx<T> ce = a[e];
+    re += ce.re * u.re - ce.im * u.im;
+    im += ce.re * u.im + ce.im * u.re;
   }
   for (int o = 16; o > 0; o >>= 1) {
     re += __shfl_xor_sync(0xffffffffu, re, o);
@@ -96,8 +101,7 @@ __global__ void d2_sparse_kernel(const BlockDev* __restrict__ in, const BlockDev
 template <typename T>
 __global__ void d2_sparse_rhs_kernel(const BlockDev* __restrict__ in, const BlockDev* __restrict__ out,
                                      const int64_t* __restrict__ ptr, const int* __restrict__ idx,
-                                     const cx<T>* __restrict__ a, const cx<T>* __restrict__ c,
-                                     const int* __restrict__ row_blk, const int* __restrict__ row_loc, int64_t rows,
+                                     const cx<T>* __restrict__ a, const int* __restrict__ row_blk, const int* __restrict__ row_loc, int64_t rows,
                                      const cx<T>* __restrict__ spec, cx<T>* __restrict__ z, int64_t nrhs) {
   const int64_t groups = (nrhs + 31) / 32;
   const int64_t item = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -110,11 +114,17 @@ __global__ void d2_sparse_rhs_kernel(const BlockDev* __restrict__ in, const Bloc
   const BlockDev& bi = in[b];
   const cx<T>* __restrict__ U = spec + bi.spec_off * nrhs + rr;
   T re = T(0), im = T(0);
-  for (int64_t e = ptr[row]; e < ptr[row + 1]; ++e) {
+  for (int64_t e = ptr[2 * row]; e < ptr[2 * row + 1]; ++e) {   // a conj(u)
     const cx<T> u = U[int64_t(idx[e]) * nrhs];
-    const cx<T> ae = a[e], ce = c[e];
-    re += ae.re * u.re + ae.im * u.im + ce.re * u.re - ce.im * u.im;
-    im += ae.im * u.re - ae.re * u.im + ce.re * u.im + ce.im * u.re;
+    const cx<T> ae = a[e];
+    re += ae.re * u.re + ae.im * u.im;
+    im += ae.im * u.re - ae.re * u.im;
+  }
+  for (int64_t e = ptr[2 * row + 1]; e < ptr[2 * row + 2]; ++e) {   // c u
+    const cx<T> u = U[int64_t(idx[e]) * nrhs];
+    const cx<T> ce = a[e];
+    re += ce.re * u.re - ce.im * u.im;
+    im += ce.re * u.im + ce.im * u.re;
   }
   if (r < nrhs) {
     const BlockDev& bo = out[b];
@@ -224,12 +234,12 @@ int run_dir(Plan* p, const D2Dir& D, bool rows, const T* x, T* y, int64_t nrhs, 
     if (nrhs >= 16) {
       const int64_t warps = D.rows * ((nrhs + 31) / 32);
       d2_sparse_rhs_kernel<T><<<unsigned((warps * 32 + 255) / 256), 256, 0, st>>>(
-          in, out, D.ptr, D.idx, static_cast<const cx<T>*>(D.a), static_cast<const cx<T>*>(D.c), D.row_blk,
+          in, out, D.ptr, D.idx, static_cast<const cx<T>*>(D.a), D.row_blk,
           D.row_loc, D.rows, spec, z, nrhs);
     } else {
       const int64_t warps = D.rows * nrhs;
       d2_sparse_kernel<T><<<unsigned((warps * 32 + 255) / 256), 256, 0, st>>>(
-          in, out, D.ptr, D.idx, static_cast<const cx<T>*>(D.a), static_cast<const cx<T>*>(D.c), D.row_blk,
+          in, out, D.ptr, D.idx, static_cast<const cx<T>*>(D.a), D.row_blk,
           D.row_loc, D.rows, spec, z, nrhs);
     }
     launch_end(p, K_2D_SPARSE, st);

@@ -102,8 +102,9 @@ constexpr int kFwdChunk = 256;
 // = rows; adjoint: the other way round).  Block b's input transform is
 // described by in_host[b] (a BlockDev whose j_lo/j_hi/off select the valid
 // inputs), its output transform by out_host[b]; the compressed product of all
-// blocks is one CSR over the output half-spectrum bins, each entry (k, a, c)
-// adding a conj(U_k) + c U_k (U: the input half spectrum, DFT with exp(-...)).
+// blocks is one CSR over the output half-spectrum bins with two segments per
+// bin, entries (k, a) adding a conj(U_k), then entries (k, c) adding c U_k
+// (U: the input half spectrum, DFT with exp(-...)).
 struct D2Dir {
   std::vector<BlockDev> in_host, out_host;
   void* in_dev = nullptr;              // BlockDev[nb]
@@ -111,10 +112,9 @@ struct D2Dir {
   int64_t spec_in = 0, spec_out = 0;   // complex elements per RHS over all blocks
   int64_t parts = 0;                   // real elements per RHS: every block's valid outputs
   int64_t rows = 0, nnz = 0;           // CSR rows (output bins of all blocks) and entries
-  int64_t* ptr = nullptr;              // [rows + 1]
+  int64_t* ptr = nullptr;              // [2 rows + 1]: bin r's a terms [ptr[2r], ptr[2r+1]), c terms to ptr[2r+2]
   int* idx = nullptr;                  // [nnz] input bin
-  void* a = nullptr;                   // [nnz] complex, plan precision
-  void* c = nullptr;                   // [nnz]
+  void* a = nullptr;                   // [nnz] complex values, plan precision
   int* row_blk = nullptr;              // [rows] block of the row
   int* row_loc = nullptr;              // [rows] output bin within the block
   int64_t* part_off = nullptr;         // [nb] per-RHS offset of the block's valid outputs

@@ -1921,10 +1921,11 @@ int build_plan_2d(Plan* p) {
   d2->fwd.out_host.resize(nb);
   d2->adj.in_host.resize(nb);
   d2->adj.out_host.resize(nb);
+  // per output bin two segments: the a terms (with conj(U)), then the c terms
   struct Csr {
     std::vector<int64_t> ptr{0};
     std::vector<int> idx, blk, loc;
-    std::vector<cx<T>> a, c;
+    std::vector<cx<T>> val;
   } fcsr, acsr;
   int64_t kept_total = 0;
   int64_t fspec_in = 0, fspec_out = 0, aspec_in = 0, aspec_out = 0, fparts = 0, aparts = 0;
@@ -2011,18 +2012,18 @@ int build_plan_2d(Plan* p) {
     for (int64_t pp = 0; pp < Hr; ++pp) {
       for (int64_t q = 0; q < Hc; ++q) {
         const cx<double> a = S(pp, q);
-        const bool ka = sq(a) > thr;
-        cx<double> c{0.0, 0.0};
-        bool kc = false;
-        if (q > 0 && q < Lc / 2) {
-          const cx<double> m = S((Lr - pp) % Lr, q);
-          kc = sq(m) > thr;
-          c = cx<double>{m.re, -m.im};
+        if (sq(a) > thr) {
+          fcsr.idx.push_back(int(q));
+          fcsr.val.push_back(cvt(a));
         }
-        if (!ka && !kc) continue;
-        fcsr.idx.push_back(int(q));
-        fcsr.a.push_back(ka ? cvt(a) : cx<T>{T(0), T(0)});
-        fcsr.c.push_back(kc ? cvt(c) : cx<T>{T(0), T(0)});
+      }
+      fcsr.ptr.push_back(int64_t(fcsr.idx.size()));
+      for (int64_t q = 1; q < (Lc + 1) / 2; ++q) {
+        const cx<double> m = S((Lr - pp) % Lr, q);
+        if (sq(m) > thr) {
+          fcsr.idx.push_back(int(q));
+          fcsr.val.push_back(cvt(cx<double>{m.re, -m.im}));
+        }
       }
       fcsr.ptr.push_back(int64_t(fcsr.idx.size()));
       fcsr.blk.push_back(bi);
@@ -2032,17 +2033,18 @@ int build_plan_2d(Plan* p) {
     for (int64_t q = 0; q < Hc; ++q) {
       for (int64_t pp = 0; pp < Hr; ++pp) {
         const cx<double> a = S(pp, q);
-        const bool ka = sq(a) > thr;
-        cx<double> c{0.0, 0.0};
-        bool kc = false;
-        if (pp > 0 && pp < Lr / 2) {
-          c = S(Lr - pp, q);
-          kc = sq(c) > thr;
+        if (sq(a) > thr) {
+          acsr.idx.push_back(int(pp));
+          acsr.val.push_back(cvt(a));
         }
-        if (!ka && !kc) continue;
-        acsr.idx.push_back(int(pp));
-        acsr.a.push_back(ka ? cvt(a) : cx<T>{T(0), T(0)});
-        acsr.c.push_back(kc ? cvt(c) : cx<T>{T(0), T(0)});
+      }
+      acsr.ptr.push_back(int64_t(acsr.idx.size()));
+      for (int64_t pp = 1; pp < (Lr + 1) / 2; ++pp) {
+        const cx<double> c = S(Lr - pp, q);
+        if (sq(c) > thr) {
+          acsr.idx.push_back(int(pp));
+          acsr.val.push_back(cvt(c));
+        }
       }
       acsr.ptr.push_back(int64_t(acsr.idx.size()));
       acsr.blk.push_back(bi);
@@ -2092,12 +2094,9 @@ int build_plan_2d(Plan* p) {
     XC_TRY(upload(p, C.idx, &D.idx));
     XC_TRY(upload(p, C.blk, &D.row_blk));
     XC_TRY(upload(p, C.loc, &D.row_loc));
-    cx<T>* a = nullptr;
-    cx<T>* c = nullptr;
-    XC_TRY(upload(p, C.a, &a));
-    XC_TRY(upload(p, C.c, &c));
-    D.a = a;
-    D.c = c;
+    cx<T>* v = nullptr;
+    XC_TRY(upload(p, C.val, &v));
+    D.a = v;
     XC_TRY(upload(p, part_off, &D.part_off));
     return XC_OK;
   };
@@ -2131,8 +2130,8 @@ int build_plan_2d(Plan* p) {
     XC_TRY(upload(p, ptr, &D.comb_ptr));
     XC_TRY(upload(p, flat, &D.comb_ent));
   }
-  p->matrix_bytes = d2->fwd.nnz * int64_t(2 * sizeof(cx<T>) + sizeof(int)) + dense_elems * int64_t(sizeof(T));
-  p->adjoint_bytes = d2->adj.nnz * int64_t(2 * sizeof(cx<T>) + sizeof(int));
+  p->matrix_bytes = d2->fwd.nnz * int64_t(sizeof(cx<T>) + sizeof(int)) + dense_elems * int64_t(sizeof(T));
+  p->adjoint_bytes = d2->adj.nnz * int64_t(sizeof(cx<T>) + sizeof(int));
   return XC_OK;
 }
 
