@@ -328,7 +328,7 @@ def kernel_source_hash():
     """sha256 over the sources of the execution kernels (changes whenever a
     kernel does)."""
     h = hashlib.sha256()
-    for f in ("xc_items.cuh", "xc_apply.cu", "xc_batch.cu", "xc_fft.cuh", "xc_complex.cu"):
+    for f in ("xc_items.cuh", "xc_apply.cu", "xc_batch.cu", "xc_fft.cuh", "xc_complex.cu", "xc_2d.cu"):
         h.update(open(os.path.join(ROOT, "paper_2004_11610_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
