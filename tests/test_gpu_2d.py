@@ -133,3 +133,16 @@ def test_2d_plans_refuse_what_they_do_not_support(xc):
     with pytest.raises(xc.XcError) as e:
         xc.Plan("legendre", 100, 1e-8, nodes=np.linspace(-0.9, 0.9, 100), scheme="2d")
     assert e.value.code == xc.XC_ERR_UNSUPPORTED
+
+
+def test_bench_size_laguerre_transform(xc):
+    """The bench's 2-D workload (eta = 100, N = 4096, eps1 = 1e-10, FP64): the
+    whole forward and transposed products of 4 right-hand sides against the
+    oracle."""
+    spec = spec_of("laguerre", 4096, eta=100.0)
+    with make(xc, spec, 1e-10, eps2=1e-3) as plan:
+        ora = M2.build(spec, 1e-10, eps2=1e-3)
+        assert plan.info()["blocks2d"] == len(ora.blocks)
+        X = inputs.normal(4096, 4, 65)
+        assert max_rel(run(plan, X), M2.apply(ora, X)) <= 1e-10 + 10 * 1e-10
+        assert max_rel(run(plan, X, True), M2.apply_adjoint(ora, X)) <= 1e-10 + 10 * 1e-10

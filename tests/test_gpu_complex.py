@@ -196,3 +196,17 @@ def test_complex_plans_refuse_what_they_do_not_support(xc):
     with pytest.raises(xc.XcError) as e:   # L/2 FP64 values above one CTA's shared memory
         xc.Plan("exp", 30000, 1e-8)
     assert e.value.code == xc.XC_ERR_UNSUPPORTED
+
+
+def test_bench_size_spectral_laguerre(xc):
+    """The bench's spectral Laguerre workload (eta = 2500, T = 4, N = 8192,
+    eps1 = 1e-12, FP64): forward and transpose of 3 right-hand sides against
+    the oracle at the plan's angles."""
+    N, eps, eta, T = 8192, 1e-12, 2500.0, 4.0
+    with xc.Plan("lagspec", N, eps, precision="fp64", eta=eta, period=T) as plan:
+        spec = oracle_spec(plan, "lagspec", N, None, eta, T)
+        ora = M.build(spec, eps, eps2=1e-3)
+        X = cinput(N, 3, 71)
+        tol = 64 * U64 * math.log2(ora.blocks[0].L) / 1e-3 + 10 * eps
+        assert max_rel(run(plan, X), M.apply(ora, X)) <= tol
+        assert max_rel(run(plan, X, True), M.apply_adjoint(ora, X)) <= tol
