@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(32 * kSparseWarps)
   for (;;) {
     const int64_t t = take_item(&counters[2], lane);
     if (t >= total) break;
-    adj_sparse_item<T, RPW, COMP, YT>(blocks, nblocks, y, ld, yt, ldt, part, nrhs, rowscale, cbase,
+    adj_sparse_item<T, RPW, COMP, YT, true>(blocks, nblocks, y, ld, yt, ldt, part, nrhs, rowscale, cbase,
                                       items[t / nsup], chunk, (t % nsup) * int64_t(sg) * RPW, lane, sg);
   }
   retire_warp(&counters[2], &counters[3], gridDim.x * kSparseWarps, lane);

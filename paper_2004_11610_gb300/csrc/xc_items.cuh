@@ -102,6 +102,24 @@ struct AccPair {
 };
 
 // ------------------------------------------------------ band streaming
+// A band value is read once per item: in the single-plan FP32 adjoint
+// product (STREAM) it is loaded evict-first, so that it does not displace the
+// right-hand-side lines that the slice's other rows re-read from L1 (Legendre
+// N = 32768, 128 RHS: adjoint 0.43 -> 0.33 ms).  Elsewhere the normal load is
+// kept: FP64 items of other right-hand-side groups re-read the same values
+// from L1 (evict-first cost the FP64 adjoint 58 %), and the batch kernel's
+// adjoint ran 2 % slower with it.
+template <typename T>
+__device__ __forceinline__ cx<T> load_band(const cx<T>* p) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 t = __ldcs(reinterpret_cast<const float2*>(p));
+    return cx<T>{t.x, t.y};
+  } else {
+    const double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+    return cx<T>{t.x, t.y};
+  }
+}
+
 // Band rows [j0, j1) of a slice whose value (j, lane) sits at base[j*32 + lane]:
 // step(j) is called for every row in order, four rows per unrolled iteration
 // so that their loads are in flight together.  (An L2 bulk prefetch of the
@@ -330,14 +348,14 @@ __device__ __forceinline__ void load_rhs(const T* __restrict__ p, T (&v)[RPW]) {
 // transpose yt[row][ldt] (ldt a multiple of 8, columns beyond nrhs zero),
 // where one lane's RPW values of a row are adjacent and a step reads one
 // vector per lane.
-template <typename T, int RPW, bool COMP, bool YT>
+template <typename T, int RPW, bool COMP, bool YT, bool STREAM>
 __device__ __forceinline__ void adj_chunk_rows(const cx<T>* __restrict__ base, int lane, int64_t n0, int j0, int j1,
                                                const T* __restrict__ y, int64_t ld, int64_t r0, int nq,
                                                const T* __restrict__ rowscale, Acc<T, COMP> (&re)[RPW],
                                                Acc<T, COMP> (&im)[RPW]) {
   const cx<T>* __restrict__ val = base + lane;
   band_rows<T>(j0, j1, [&](int j) {
-    const cx<T> c = val[j * 32];
+    const cx<T> c = (STREAM && sizeof(T) == 4) ? load_band(val + j * 32) : val[j * 32];
     const int64_t row = n0 + j;
     const T rs = rowscale ? rowscale[row] : T(1);
     if constexpr (YT) {
@@ -367,7 +385,7 @@ __device__ __forceinline__ void adj_chunk_rows(const cx<T>* __restrict__ base, i
 // scalar loads touches up to 32 sectors per right-hand side) read the
 // transposed copy yt when USE_YT and yt is given; the others read y, where
 // neighbouring bins share cache lines over many steps.
-template <typename T, int RPW, bool COMP, bool USE_YT = false>
+template <typename T, int RPW, bool COMP, bool USE_YT = false, bool STREAM = false>
 __device__ void adj_sparse_item(const BlockDev* __restrict__ blocks, int nblocks, const T* __restrict__ y,
                                 int64_t ld, const T* __restrict__ yt, int64_t ldt, cx<T>* __restrict__ part,
                                 int64_t nrhs, const T* __restrict__ rowscale, const int* __restrict__ cbase, int2 it,
@@ -391,11 +409,11 @@ __device__ void adj_sparse_item(const BlockDev* __restrict__ blocks, int nblocks
     Acc<T, COMP> re[RPW], im[RPW];
     if constexpr (USE_YT) {
       if (from_yt)
-        adj_chunk_rows<T, RPW, COMP, true>(base, lane, n0, j0, j1, yt, ldt, r0, nq, rowscale, re, im);
+        adj_chunk_rows<T, RPW, COMP, true, STREAM>(base, lane, n0, j0, j1, yt, ldt, r0, nq, rowscale, re, im);
       else
-        adj_chunk_rows<T, RPW, COMP, false>(base, lane, n0, j0, j1, y, ld, r0, nq, rowscale, re, im);
+        adj_chunk_rows<T, RPW, COMP, false, STREAM>(base, lane, n0, j0, j1, y, ld, r0, nq, rowscale, re, im);
     } else {
-      adj_chunk_rows<T, RPW, COMP, false>(base, lane, n0, j0, j1, y, ld, r0, nq, rowscale, re, im);
+      adj_chunk_rows<T, RPW, COMP, false, STREAM>(base, lane, n0, j0, j1, y, ld, r0, nq, rowscale, re, im);
     }
     cx<T>* out = part + ((cb + it.y) * nrhs + r0) * 32 + lane;
 #pragma unroll
