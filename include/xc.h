@@ -110,7 +110,10 @@ typedef enum {
                                    dense.  XC_LAGUERRE_FN / XC_HERMITE_FN at equispaced user nodes
                                    (x_i = x_0 + i h, extended with the same step) and
                                    XC_KERNEL_A1 / XC_KERNEL_A2; XC_FP64 or XC_FP32; real vectors.
-                                   Blocks up to L <= 28928 along each side (N up to about 19000). */
+                                   Blocks up to L <= 28928 along each side (N up to about 19000);
+                                   at most 65535 right-hand sides per apply (else
+                                   XC_ERR_UNSUPPORTED).  The error bound is eps1 / eps2^2 (two
+                                   window divisions): take eps2 larger than for 1-D plans. */
 
 /* precomputation of the compressed rows */
 #define XC_PRECOMPUTE_AUTO 0   /* Appendix A closed form for XC_CHEBYSHEV_T at its Gauss nodes with
