@@ -325,11 +325,16 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- GPU path
 def kernel_source_hash():
-    """sha256 over the sources of the execution kernels (changes whenever a
-    kernel does)."""
+    """sha256 over the code of the execution kernels' sources (changes whenever
+    a kernel does; '//' comments and blank lines are left out, so a comment
+    edit does not orphan the profiles)."""
     h = hashlib.sha256()
     for f in ("xc_items.cuh", "xc_apply.cu", "xc_batch.cu", "xc_fft.cuh", "xc_complex.cu", "xc_2d.cu"):
-        h.update(open(os.path.join(ROOT, "paper_2004_11610_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_2004_11610_gb300", "csrc", f), encoding="utf-8").read()
+        for line in text.splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()
 
 

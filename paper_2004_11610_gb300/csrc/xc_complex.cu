@@ -20,8 +20,9 @@
 //
 // The L-point complex transforms reuse the n = L/2 point packed real FFT of
 // the real families twice: a complex sequence is the pair of its real and
-// imaginary parts, two real sequences, and the two halves of the CTA
-// transform one each at the same time.
+// imaginary parts, two real sequences, which the two CTAs of a cluster
+// transform one each, exchanging the results through distributed shared
+// memory.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
