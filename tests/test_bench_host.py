@@ -86,3 +86,33 @@ def test_work_model_covers_every_kernel_the_library_times():
     work = bench.algorithmic_work(cinfo, 4, "fp64")
     assert {"fwd_fft", "fwd_sparse", "adj_sparse", "adj_fft", "row_scale"} <= set(work)
     assert work["fwd_sparse"][0] == 8.0 * 900 * 4
+
+
+def test_workload_plumbing_for_the_complex_and_2d_workloads():
+    """Every named workload has a label and a config; the 2-D workload's nodes
+    are the Laguerre transform's points; the oracle arms build the right kind
+    of plan (1-D, complex, 2-D) and give outputs of the input's shape."""
+    import numpy as np
+    import bench
+    from paper_2004_11610_gb300 import inputs
+    for name, wl in inputs.WORKLOADS.items():
+        cfg = bench.workload_config(name, wl)
+        assert cfg["workload"] == name and len(cfg["plans"]) == len(wl["plans"])
+    x = bench.laguerre_transform_nodes(4096, 100.0)
+    assert np.allclose(np.diff(x), 12.0 * 100.0 / 4095) and x[0] == pytest.approx(12.0 * 100.0 / 4095)
+    for fam, N, params, dist in (("laguerre", 60, {"scheme": "2d", "eta": 10.0}, "normal"),
+                                 ("lagspec", 40, {"alpha": 30.0, "beta": 2.0}, "complex_normal"),
+                                 ("legendre", 50, {}, "uniform_pm1")):
+        fwd, adj = bench.oracle_apply_pair(fam, N, params, 1e-8, "fp64")
+        X = inputs.draw(dist, N, 2, 5)
+        assert fwd(X).shape == X.shape and adj(X).shape == X.shape
+        assert np.iscomplexobj(fwd(X)) == (fam == "lagspec")
+
+
+def test_work_model_of_2d_plans():
+    import bench
+    info = {"nnz": [], "N": 100, "m_tail": 0, "L": [], "scheme": 3, "nnz2d": 5000, "dense_elems2d": 700}
+    work = bench.algorithmic_work(info, 8, "fp64")
+    assert work["sparse_2d"][0] == 8.0 * 5000 * 8
+    assert work["combine_2d"][0] == 2.0 * 700 * 8
+    assert bench.step_bytes(dict(info, matrix_bytes=10, adjoint_bytes=20), 8, "fp64") > 30
