@@ -324,12 +324,15 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU path
-def kernel_source_hash():
-    """sha256 over the code of the execution kernels' sources (changes whenever
-    a kernel does; '//' comments and blank lines are left out, so a comment
-    edit does not orphan the profiles)."""
+KERNEL_SOURCES = ("xc_items.cuh", "xc_apply.cu", "xc_batch.cu", "xc_fft.cuh", "xc_complex.cu", "xc_2d.cu")
+
+
+def kernel_source_hash(files=KERNEL_SOURCES):
+    """sha256 over the code of the given kernel sources (changes whenever a
+    kernel in them does; '//' comments and blank lines are left out, so a
+    comment edit does not orphan the profiles)."""
     h = hashlib.sha256()
-    for f in ("xc_items.cuh", "xc_apply.cu", "xc_batch.cu", "xc_fft.cuh", "xc_complex.cu", "xc_2d.cu"):
+    for f in files:
         text = open(os.path.join(ROOT, "paper_2004_11610_gb300", "csrc", f), encoding="utf-8").read()
         for line in text.splitlines():
             code = line.split("//", 1)[0].rstrip()
@@ -341,13 +344,16 @@ def kernel_source_hash():
 def traffic_from_profiles(kernel, workload, plan=None):
     """dram bytes of one launch from the committed ncu summary of this kernel
     and workload (line `traffic: <kernel> plan=<i> dram_bytes=<B>`), provided
-    the kernel sources have not changed since the capture (`source_sha256:`)."""
+    the sources its kernels are compiled from (line `sources:`, else all
+    kernel sources) have not changed since the capture (`source_sha256:`)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}__{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     h = re.search(r"source_sha256:\s*([0-9a-f]{16,64})", text)
-    if not h or not kernel_source_hash().startswith(h.group(1)):
+    src = re.search(r"^sources:\s*(.+)$", text, re.M)
+    files = tuple(src.group(1).split()) if src else KERNEL_SOURCES
+    if not h or not kernel_source_hash(files).startswith(h.group(1)):
         return None
     for m in re.finditer(r"traffic:\s*(\S+)\s+plan=(\S+)\s+dram_bytes=([0-9.eE+]+)", text):
         if m.group(1) == kernel and (plan is None or m.group(2) == str(plan)):

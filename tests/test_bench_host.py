@@ -116,3 +116,37 @@ def test_work_model_of_2d_plans():
     assert work["sparse_2d"][0] == 8.0 * 5000 * 8
     assert work["combine_2d"][0] == 2.0 * 700 * 8
     assert bench.step_bytes(dict(info, matrix_bytes=10, adjoint_bytes=20), 8, "fp64") > 30
+
+
+def test_profile_summaries_are_current_and_name_their_kernels_sources():
+    """Every committed ncu summary names the sources its kernels are compiled
+    from (the translation unit and everything it includes among the kernel
+    sources), its hash matches them, and each `traffic:` line is found by the
+    bench's lookup."""
+    import pathlib
+    import re
+    import bench
+    csrc = pathlib.Path(ROOT) / "paper_2004_11610_gb300" / "csrc"
+
+    def closure(f, seen):
+        if f in seen or f not in bench.KERNEL_SOURCES:
+            return seen
+        seen.add(f)
+        for inc in re.findall(r'#include "([^"]+)"', (csrc / f).read_text()):
+            closure(inc, seen)
+        return seen
+
+    profiles = sorted((pathlib.Path(ROOT) / "profiles").glob("*__*.md"))
+    assert profiles
+    for path in profiles:
+        text = path.read_text()
+        files = re.search(r"^sources:\s*(.+)$", text, re.M).group(1).split()
+        tu = [f for f in files if f.endswith(".cu")]
+        assert len(tu) == 1, path.name
+        assert set(files) == closure(tu[0], set()), path.name
+        h = re.search(r"source_sha256:\s*([0-9a-f]+)", text).group(1)
+        assert bench.kernel_source_hash(tuple(files)).startswith(h), path.name
+        kernel, workload = path.stem.split("__", 1)
+        for k, plan, b in re.findall(r"traffic:\s*(\S+)\s+plan=(\S+)\s+dram_bytes=([0-9.eE+]+)", text):
+            if k == kernel:
+                assert bench.traffic_from_profiles(k, workload, plan) == float(b)
