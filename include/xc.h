@@ -181,9 +181,11 @@ int xc_plan_reserve(xc_plan_t plan, int64_t nrhs);
  * summation order is a property of the plan, so a column's result does not
  * depend on nrhs, on the stream or on batching.
  *   x_dev  device, [nrhs][ld] of the plan's I/O type (read only)
- *   y_dev  device, [nrhs][ld] (written; must not alias x_dev)
- *   nrhs   number of right-hand sides (0 is a no-op)
- *   ld     leading dimension in elements, ld >= N
+ *   y_dev  device, [nrhs][ld] (columns [0, N) of each row written, the rest
+ *          untouched); its elements up to the last used one, ((nrhs-1) ld + N)
+ *          of them, must not overlap those of x_dev (XC_ERR_ARG)
+ *   nrhs   number of right-hand sides (0 is a no-op; at most 524280)
+ *   ld     leading dimension in elements, N <= ld, nrhs * ld <= 2^40
  */
 int xc_apply(xc_plan_t plan, const void* x_dev, void* y_dev, int64_t nrhs, int64_t ld, void* stream);
 
@@ -230,7 +232,9 @@ int xc_apply_noalloc(xc_plan_t plan, const void* x_dev, void* y_dev, int64_t nrh
  * copies the input to the device, applies, copies the result back and
  * synchronises the stream.  adjoint = 0: out = A in; adjoint = 1: out = A^T in.
  * in_host / out_host: [nrhs][ld] of the plan's I/O type (pinned memory gives
- * full copy bandwidth).  Uses device staging owned by the plan.
+ * full copy bandwidth); only the first N elements of each row are read from
+ * in_host and written to out_host, the padding [N, ld) of out_host keeps its
+ * contents.  Uses device staging owned by the plan.
  */
 int xc_apply_host(xc_plan_t plan, int adjoint, const void* in_host, void* out_host,
                   int64_t nrhs, int64_t ld, void* stream);
@@ -303,14 +307,20 @@ typedef struct {
   int64_t matrix_bytes, adjoint_bytes;   /* summed over the plans */
 } xc_batch_stats;
 
-/* Group nplans plans (host array of handles; all of one precision).  The
- * batch refers to the plans, which must outlive it. */
+/* Group nplans distinct plans (host array of handles; all of one precision;
+ * a plan listed twice is XC_ERR_ARG).  The batch refers to the plans, which
+ * must outlive it. */
 int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans);
 /* Bind the I/O buffers: x_dev[i], y_dev[i] are device pointers to
  * [nrhs[i]][ld[i]] arrays of plan i's type (ld[i] >= N_i; nrhs[i] = 0 skips the
  * plan).  The forward apply reads x and writes y, the adjoint reads y and
  * writes x.  Allocates the plans' scratch and builds the task lists
- * (synchronous). */
+ * (synchronous).  All arguments are checked first: a refused bind leaves the
+ * previous binding in force.  The binding points at each plan's scratch; a
+ * later single-plan apply (or bind of another batch) that needs more scratch
+ * allocates a new buffer and the plan keeps the one the batch uses until the
+ * plan is destroyed, so the binding stays valid.  If building the task lists
+ * fails the batch is left unbound (xc_batch_apply returns XC_ERR_ARG). */
 int xc_batch_bind(xc_batch_t b, const void* const* x_dev, void* const* y_dev, const int64_t* nrhs, const int64_t* ld);
 /* One persistent launch over all bound plans (adjoint = 0: y = A x for every
  * plan; 1: x = A^T y).  Asynchronous on `stream`; allocates nothing and does

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -91,11 +92,22 @@ static void release_events(Plan* p) {
   p->event_pool.clear();
 }
 
+int ensure_scratch_kept(Plan* p, int64_t nrhs) {
+  if (nrhs <= p->scratch_nrhs || p->batch_refs == 0 || !p->scratch) return ensure_scratch(p, nrhs);
+  void* old = p->scratch;
+  p->scratch = nullptr;        // ensure_scratch then allocates without freeing
+  const int rc = ensure_scratch(p, nrhs);
+  if (p->scratch) p->retired.push_back(old);
+  else p->scratch = old;       // the growth failed: the old buffer stays in use
+  return rc;
+}
+
 static void free_plan(Plan* p) {
   if (!p) return;
   cudaDeviceSynchronize();
   release_events(p);
   for (void* d : p->allocations) cudaFree(d);
+  for (void* d : p->retired) cudaFree(d);
   delete p->d2;
   if (p->scratch) cudaFree(p->scratch);
   if (p->stage) cudaFree(p->stage);
@@ -107,9 +119,13 @@ static int validate_vectors(const Plan* p, const void* a, const void* b, int64_t
   if (nrhs < 0) return fail(XC_ERR_ARG, "nrhs < 0");
   if (nrhs == 0) return XC_OK;
   if (!a || !b) return fail(XC_ERR_ARG, "vector pointer is NULL");
-  if (a == b) return fail(XC_ERR_ARG, "input and output must not alias");
   if (ld < p->N) return fail(XC_ERR_ARG, "ld < N");
   if (nrhs > 65535LL * 8) return fail(XC_ERR_UNSUPPORTED, "nrhs above 524280");
+  if (ld > (int64_t(1) << 40) / nrhs) return fail(XC_ERR_ARG, "nrhs * ld too large");
+  // the [nrhs][ld] arrays, up to the last used element, must not overlap
+  const uintptr_t span = uintptr_t((nrhs - 1) * ld + p->N) * p->io_bytes();
+  const uintptr_t ua = reinterpret_cast<uintptr_t>(a), ub = reinterpret_cast<uintptr_t>(b);
+  if (ua < ub + span && ub < ua + span) return fail(XC_ERR_ARG, "input and output must not overlap");
   return XC_OK;
 }
 
@@ -244,13 +260,14 @@ int xc_plan_reserve(xc_plan_t plan, int64_t nrhs) {
   auto* p = reinterpret_cast<xc::Plan*>(plan);
   if (!p) return fail(XC_ERR_ARG, "plan is NULL");
   if (nrhs < 0) return fail(XC_ERR_ARG, "nrhs < 0");
-  return xc::ensure_scratch(p, nrhs);
+  return xc::ensure_scratch_kept(p, nrhs);
 }
 
 int xc_apply(xc_plan_t plan, const void* x_dev, void* y_dev, int64_t nrhs, int64_t ld, void* stream) {
   auto* p = reinterpret_cast<xc::Plan*>(plan);
   XC_TRY(xc::validate_vectors(p, x_dev, y_dev, nrhs, ld));
   if (nrhs == 0) return XC_OK;
+  XC_TRY(xc::ensure_scratch_kept(p, nrhs));
   p->last_stream = static_cast<cudaStream_t>(stream);
   return xc::launch_apply(p, x_dev, y_dev, nrhs, ld, static_cast<cudaStream_t>(stream));
 }
@@ -259,6 +276,7 @@ int xc_apply_adjoint(xc_plan_t plan, const void* y_dev, void* x_dev, int64_t nrh
   auto* p = reinterpret_cast<xc::Plan*>(plan);
   XC_TRY(xc::validate_vectors(p, y_dev, x_dev, nrhs, ld));
   if (nrhs == 0) return XC_OK;
+  XC_TRY(xc::ensure_scratch_kept(p, nrhs));
   p->last_stream = static_cast<cudaStream_t>(stream);
   return xc::launch_apply_adjoint(p, y_dev, x_dev, nrhs, ld, static_cast<cudaStream_t>(stream));
 }
@@ -293,15 +311,29 @@ int xc_apply_host(xc_plan_t plan, int adjoint, const void* in_host, void* out_ho
     p->stage = d;
     p->stage_elems = elems;
   }
+  XC_TRY(xc::ensure_scratch_kept(p, nrhs));
   auto st = static_cast<cudaStream_t>(stream);
   p->last_stream = st;
   char* din = static_cast<char*>(p->stage);
   char* dout = din + size_t(p->stage_elems) * p->io_bytes();
-  const size_t bytes = size_t(elems) * p->io_bytes();
-  XC_CUDA(cudaMemcpyAsync(din, in_host, bytes, cudaMemcpyHostToDevice, st));
+  // Only the N used elements of each row move: the caller's padding columns
+  // [N, ld) of out_host are left as they are (as xc_apply leaves them).
+  const size_t eb = p->io_bytes();
+  if (ld == p->N) {
+    const size_t bytes = size_t(elems) * eb;
+    XC_CUDA(cudaMemcpyAsync(din, in_host, bytes, cudaMemcpyHostToDevice, st));
+  } else {
+    XC_CUDA(cudaMemcpy2DAsync(din, size_t(ld) * eb, in_host, size_t(ld) * eb, size_t(p->N) * eb, size_t(nrhs),
+                              cudaMemcpyHostToDevice, st));
+  }
   if (adjoint) XC_TRY(xc::launch_apply_adjoint(p, din, dout, nrhs, ld, st));
   else XC_TRY(xc::launch_apply(p, din, dout, nrhs, ld, st));
-  XC_CUDA(cudaMemcpyAsync(out_host, dout, bytes, cudaMemcpyDeviceToHost, st));
+  if (ld == p->N) {
+    XC_CUDA(cudaMemcpyAsync(out_host, dout, size_t(elems) * eb, cudaMemcpyDeviceToHost, st));
+  } else {
+    XC_CUDA(cudaMemcpy2DAsync(out_host, size_t(ld) * eb, dout, size_t(ld) * eb, size_t(p->N) * eb, size_t(nrhs),
+                              cudaMemcpyDeviceToHost, st));
+  }
   XC_CUDA(cudaStreamSynchronize(st));
   return XC_OK;
 }

@@ -284,9 +284,12 @@ struct Batch {
   std::vector<void*> y;
   std::vector<int64_t> nrhs, ld;
   std::vector<void*> allocs;
+  bool holds_refs = false;       // counted in each plan's batch_refs (after the first bind)
   ~Batch() {
     cudaDeviceSynchronize();
     for (void* d : allocs) cudaFree(d);
+    if (holds_refs)
+      for (Plan* p : plans) --p->batch_refs;
   }
   int alloc(void** ptr, size_t bytes) {
     if (cudaMalloc(ptr, bytes == 0 ? 1 : bytes) != cudaSuccess) {
@@ -307,6 +310,7 @@ using Entry = std::pair<double, int4>;   // (cost estimate, entry)
 // (forward) and rpw_a (adjoint) right-hand sides per band item.
 int build_tasks(Batch* b, int rpw_f, int rpw_a) {
   const int np = int(b->plans.size());
+  b->rpw[0] = b->rpw[1] = 0;   // unbound until every list is in place (a failure leaves it so)
   std::vector<Entry> L[2][3];
   std::vector<unsigned> need[2] = {std::vector<unsigned>(2 * size_t(np), 0), std::vector<unsigned>(2 * size_t(np), 0)};
   for (int p = 0; p < np; ++p) {
@@ -476,6 +480,10 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans) {
       delete b;
       return fail(XC_ERR_ARG, "all plans of a batch need the same precision");
     }
+    if (std::find(b->plans.begin(), b->plans.end(), p) != b->plans.end()) {
+      delete b;   // two entries would share the plan's scratch
+      return fail(XC_ERR_ARG, "plan " + std::to_string(i) + " appears twice in the batch");
+    }
     b->precision = p->precision;
     b->plans.push_back(p);
     b->max_n = std::max(b->max_n, p->max_n);
@@ -520,17 +528,22 @@ int xc_batch_bind(xc_batch_t batch, const void* const* x_dev, void* const* y_dev
   auto* b = reinterpret_cast<xc::Batch*>(batch);
   if (!b || !x_dev || !y_dev || !nrhs || !ld) return fail(XC_ERR_ARG, "NULL argument");
   const int np = int(b->plans.size());
-  std::vector<xc::BatchPlanDev> host(np);
-  b->x.assign(x_dev, x_dev + np);
-  b->y.assign(y_dev, y_dev + np);
-  b->nrhs.assign(nrhs, nrhs + np);
-  b->ld.assign(ld, ld + np);
+  // every argument is checked before the batch changes: a refused bind
+  // leaves the previous binding in force
   for (int i = 0; i < np; ++i) {
-    xc::Plan* p = b->plans[i];
+    const xc::Plan* p = b->plans[i];
     if (nrhs[i] < 0 || nrhs[i] > (int64_t(1) << 24)) return fail(XC_ERR_ARG, "nrhs out of range");
     if (nrhs[i] > 0 && (!x_dev[i] || !y_dev[i] || x_dev[i] == y_dev[i] || ld[i] < p->N))
       return fail(XC_ERR_ARG, "bad buffers for plan " + std::to_string(i));
-    XC_TRY(xc::ensure_scratch(p, std::max<int64_t>(1, nrhs[i])));
+  }
+  for (int i = 0; i < np; ++i) XC_TRY(xc::ensure_scratch_kept(b->plans[i], std::max<int64_t>(1, nrhs[i])));
+  if (!b->holds_refs) {
+    for (xc::Plan* p : b->plans) ++p->batch_refs;
+    b->holds_refs = true;
+  }
+  std::vector<xc::BatchPlanDev> host(np);
+  for (int i = 0; i < np; ++i) {
+    xc::Plan* p = b->plans[i];
     xc::BatchPlanDev& d = host[i];
     std::memset(&d, 0, sizeof(d));
     d.blocks = static_cast<const xc::BlockDev*>(p->scratch_desc);
@@ -558,6 +571,10 @@ int xc_batch_bind(xc_batch_t batch, const void* const* x_dev, void* const* y_dev
     d.ld = ld[i];
   }
   XC_CUDA(cudaMemcpy(b->dplans, host.data(), size_t(np) * sizeof(xc::BatchPlanDev), cudaMemcpyHostToDevice));
+  b->x.assign(x_dev, x_dev + np);
+  b->y.assign(y_dev, y_dev + np);
+  b->nrhs.assign(nrhs, nrhs + np);
+  b->ld.assign(ld, ld + np);
   const int dflt = b->precision == XC_FP64 ? 2 : 8;
   std::pair<int, int> rpw{b->rpw[0] > 0 ? b->rpw[0] : dflt, b->rpw[1] > 0 ? b->rpw[1] : dflt};
   {

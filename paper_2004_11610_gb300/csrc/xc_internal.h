@@ -202,6 +202,11 @@ struct Plan {
   void* scratch_desc = nullptr;
   void* scratch = nullptr;
   int64_t scratch_nrhs = 0;
+  // batches whose binding holds a pointer to `scratch` (xc_batch_bind);
+  // while there are any, a growth keeps the old buffer in `retired` (freed
+  // with the plan) instead of freeing it under the batch
+  int batch_refs = 0;
+  std::vector<void*> retired;
   size_t pexp_off = 0;                 // XC_FP64_PAIR: byte offset of the per-RHS exponents in scratch
   void* stage = nullptr;
   int64_t stage_elems = 0;
@@ -246,6 +251,9 @@ int build_plan_device(Plan* p);
 int dense_matrix_device(const Plan* p, void* A, int64_t lda, cudaStream_t s);
 // (xc_apply.cu) execution
 int ensure_scratch(Plan* p, int64_t nrhs);
+// (xc_abi.cpp) ensure_scratch for calls made while batches may point at the
+// scratch: a buffer that has to grow is retired rather than freed
+int ensure_scratch_kept(Plan* p, int64_t nrhs);
 int launch_apply(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t s);
 int launch_apply_adjoint(Plan* p, const void* y, void* x, int64_t nrhs, int64_t ld, cudaStream_t s);
 // (xc_2d.cu) execution of the 2-D block scheme

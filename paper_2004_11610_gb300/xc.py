@@ -239,12 +239,26 @@ class Plan:
             raise ValueError(f"{name} must have shape (nrhs, N) with unit column stride")
         return t
 
+    def _pair(self, a, b, na, nb):
+        """Checks the input and output tensors of an apply (one leading
+        dimension serves both) and returns that leading dimension."""
+        self._check_tensor(a, na)
+        self._check_tensor(b, nb)
+        if b.shape != a.shape:
+            raise ValueError(f"{nb} must have the shape of {na}")
+        if a.shape[0] <= 1:
+            return self.N
+        if b.stride(0) != a.stride(0):
+            raise ValueError(f"{nb} must have the row stride of {na}")
+        return a.stride(0)
+
     def apply(self, x, out=None, stream=None):
         """y = A x for x of shape (nrhs, N) (xc_apply)."""
         import torch
         x = self._check_tensor(x if x.dim() == 2 else x[None, :], "x")
-        y = torch.empty_like(x) if out is None else self._check_tensor(out, "out")
-        _check(_lib.xc_apply(self._h, _P(x.data_ptr()), _P(y.data_ptr()), x.shape[0], x.stride(0),
+        y = torch.empty_like(x) if out is None else out
+        ld = self._pair(x, y, "x", "out")
+        _check(_lib.xc_apply(self._h, _P(x.data_ptr()), _P(y.data_ptr()), x.shape[0], ld,
                              _stream_handle(stream)), "xc_apply")
         return y
 
@@ -253,8 +267,9 @@ class Plan:
         transpose for the complex families)."""
         import torch
         y = self._check_tensor(y if y.dim() == 2 else y[None, :], "y")
-        x = torch.empty_like(y) if out is None else self._check_tensor(out, "out")
-        _check(_lib.xc_apply_adjoint(self._h, _P(y.data_ptr()), _P(x.data_ptr()), y.shape[0], y.stride(0),
+        x = torch.empty_like(y) if out is None else out
+        ld = self._pair(y, x, "y", "out")
+        _check(_lib.xc_apply_adjoint(self._h, _P(y.data_ptr()), _P(x.data_ptr()), y.shape[0], ld,
                                      _stream_handle(stream)), "xc_apply_adjoint")
         return x
 
@@ -262,20 +277,28 @@ class Plan:
         """y = A x without any device allocation (xc_apply_noalloc): the
         spectra go to the library's fixed device array instead of the plan's
         scratch.  `out` must be supplied; calls must not overlap on the GPU."""
-        x = self._check_tensor(x, "x")
-        out = self._check_tensor(out, "out")
-        _check(_lib.xc_apply_noalloc(self._h, _P(x.data_ptr()), _P(out.data_ptr()), x.shape[0], x.stride(0),
+        ld = self._pair(x, out, "x", "out")
+        _check(_lib.xc_apply_noalloc(self._h, _P(x.data_ptr()), _P(out.data_ptr()), x.shape[0], ld,
                                      _stream_handle(stream)), "xc_apply_noalloc")
         return out
 
     # -- host path
     def apply_host(self, v, adjoint: bool = False, out=None, stream=None):
         """Forward or adjoint apply on host arrays (xc_apply_host): copies in,
-        applies, copies out and synchronises."""
+        applies, copies out and synchronises.  `v` is (nrhs, ld) with ld >= N
+        (the first N columns are the vectors); `out`, if given, is a writeable
+        C-contiguous array of the same dtype and shape, whose columns beyond N
+        are left as they are."""
         v = np.ascontiguousarray(v, dtype=self.np_dtype)
         if v.ndim == 1:
             v = v[None, :]
-        res = np.empty_like(v) if out is None else out
+        if out is None:
+            res = np.empty_like(v)
+        else:
+            res = out
+            if not (isinstance(res, np.ndarray) and res.dtype == v.dtype and res.shape == v.shape
+                    and res.flags.c_contiguous and res.flags.writeable):
+                raise ValueError("out must be a writeable C-contiguous array of the input's dtype and shape")
         s = ctypes.c_void_p(0) if stream is None else _stream_handle(stream)
         _check(_lib.xc_apply_host(self._h, 1 if adjoint else 0, _P(v.ctypes.data), _P(res.ctypes.data),
                                   v.shape[0], v.shape[1], s), "xc_apply_host")
@@ -322,13 +345,13 @@ class Batch:
     def bind(self, xs, ys):
         """xs[i], ys[i]: CUDA tensors (nrhs_i, N_i) of plan i's dtype."""
         n = len(self.plans)
-        for p, a, b in zip(self.plans, xs, ys):
-            p._check_tensor(a, "x")
-            p._check_tensor(b, "y")
+        if len(xs) != n or len(ys) != n:
+            raise ValueError("one x and one y tensor per plan")
+        lds = [p._pair(a, b, "x", "y") for p, a, b in zip(self.plans, xs, ys)]
         xp = (_P * n)(*[a.data_ptr() for a in xs])
         yp = (_P * n)(*[b.data_ptr() for b in ys])
         nr = (_I64 * n)(*[a.shape[0] for a in xs])
-        ld = (_I64 * n)(*[a.stride(0) for a in xs])
+        ld = (_I64 * n)(*lds)
         _check(_lib.xc_batch_bind(self._h, xp, yp, nr, ld), "xc_batch_bind")
         self._bound = (list(xs), list(ys))
 

@@ -112,3 +112,43 @@ def test_batch_arguments_are_checked_on_the_host(xc):
     assert not h.value
     assert xc._lib.xc_batch_apply(None, 0, None) == xc.XC_ERR_ARG
     assert xc._lib.xc_batch_debug_set(None, 0, 0, 1) == xc.XC_ERR_ARG
+
+
+class _FakeCudaTensor:
+    """Just enough of a CUDA tensor for the binding's argument checks (which
+    run before anything reaches the library)."""
+
+    def __init__(self, shape, stride, dtype):
+        self.shape, self._stride, self.dtype, self.is_cuda = tuple(shape), tuple(stride), dtype, True
+
+    def dim(self):
+        return len(self.shape)
+
+    def stride(self, i):
+        return self._stride[i]
+
+    def is_complex(self):
+        return False
+
+
+def test_binding_checks_the_output_against_the_input(xc):
+    """One leading dimension serves input and output at the boundary: the
+    binding refuses an output of another shape or row stride (a shorter output
+    would be written past its end) and passes N as the leading dimension of a
+    single vector."""
+    torch = pytest.importorskip("torch")
+    plan = object.__new__(xc.Plan)
+    plan.N, plan.precision, plan.is_complex = 100, "fp64", False
+    f64 = torch.float64
+    x = _FakeCudaTensor((4, 100), (128, 1), f64)
+    assert plan._pair(x, _FakeCudaTensor((4, 100), (128, 1), f64), "x", "out") == 128
+    with pytest.raises(ValueError):
+        plan._pair(x, _FakeCudaTensor((3, 100), (128, 1), f64), "x", "out")
+    with pytest.raises(ValueError):
+        plan._pair(x, _FakeCudaTensor((4, 100), (100, 1), f64), "x", "out")
+    with pytest.raises(ValueError):
+        plan._pair(x, _FakeCudaTensor((4, 100), (1, 4), f64), "x", "out")
+    with pytest.raises(TypeError):
+        plan._pair(x, _FakeCudaTensor((4, 100), (128, 1), torch.float32), "x", "out")
+    one = _FakeCudaTensor((1, 100), (7, 1), f64)
+    assert plan._pair(one, _FakeCudaTensor((1, 100), (100, 1), f64), "x", "out") == 100

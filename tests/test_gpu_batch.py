@@ -146,3 +146,46 @@ def test_batch_rejects_mixed_precision(xc):
     finally:
         a.close()
         c.close()
+
+
+def test_batch_binding_survives_larger_single_applies_and_refused_binds(xc):
+    """A single-plan apply with more right-hand sides than the batch bound
+    grows the plan's scratch: the plan keeps the buffer the batch points at,
+    so the batch's results stay right.  A refused bind leaves the previous
+    binding in force; a plan listed twice is refused."""
+    import ctypes
+    plans, xs, ys = make_batch(xc, 6, "fp32", 5)
+    try:
+        with pytest.raises(xc.XcError) as e:
+            xc.Batch([plans[0], plans[1], plans[0]])
+        assert e.value.code == xc.XC_ERR_ARG
+        with xc.Batch(plans) as b:
+            b.bind(xs, ys)
+            b.apply(False)
+            torch.cuda.synchronize()
+            ref = [y.clone() for y in ys]
+            for i, p in enumerate(plans):        # 40 > 32 right-hand sides: every scratch grows
+                big = torch.from_numpy(inputs.normal(p.N, 40, 82, i)).to("cuda", p.torch_dtype)
+                p.apply(big)
+                p.apply_adjoint(big)
+            n = len(plans)
+            xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+            yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+            yp[2] = None                          # refused: plan 2 has no output
+            nr = (ctypes.c_int64 * n)(*[x.shape[0] for x in xs])
+            ld = (ctypes.c_int64 * n)(*[p.N for p in plans])
+            assert xc._lib.xc_batch_bind(b._h, xp, yp, nr, ld) == xc.XC_ERR_ARG
+            for y in ys:
+                y.zero_()
+            b.apply(False)
+            torch.cuda.synchronize()
+            assert b.status() == xc.XC_OK
+            for y, r in zip(ys, ref):
+                assert rel(y, r) <= 1e-12
+            b.bind(xs, ys)                        # a new bind takes the grown scratch
+            b.apply(False)
+            torch.cuda.synchronize()
+            for p, x, y in zip(plans, xs, ys):
+                assert rel(y, p.apply(x)) <= 1e-12
+    finally:
+        close_all(plans)

@@ -251,6 +251,10 @@ def test_leading_dimension_and_host_path(xc):
                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
         assert rc == 0
         torch.cuda.synchronize()
+        # output overlapping the input's rows: refused before any launch
+        rc = xc._lib.xc_apply(plan.handle, ctypes.c_void_p(big.data_ptr()), ctypes.c_void_p(big.data_ptr() + 8 * 320),
+                              5, 320, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == xc.XC_ERR_ARG
         y_ref = M.apply(ora, X)
         o = out.cpu().numpy()
         assert max_rel(o[:, :300], y_ref) <= fp64_tol(ora, 1e-10)
@@ -259,6 +263,14 @@ def test_leading_dimension_and_host_path(xc):
         assert max_rel(yh, y_ref) <= fp64_tol(ora, 1e-10)
         xh = plan.apply_host(X, adjoint=True)
         assert max_rel(xh, M.apply_adjoint(ora, X)) <= fp64_tol(ora, 1e-10)
+        # host buffers with ld = 320 > N: only the first N columns move
+        wide = np.zeros((5, 320))
+        wide[:, :300] = X
+        wout = np.full((5, 320), 7.0)
+        plan.apply_host(wide, out=wout)
+        assert max_rel(wout[:, :300], y_ref) <= fp64_tol(ora, 1e-10) and np.all(wout[:, 300:] == 7.0)
+        with pytest.raises(ValueError):
+            plan.apply_host(wide, out=np.empty((5, 300)))
 
 
 def test_dense_matrix_matches_oracle(xc):
