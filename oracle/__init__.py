@@ -24,7 +24,8 @@ method2d  The two-dimensional compression F W D W F (eq. (comp_2d)) and its
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py
 except where its docstring says "parity unpinned".  Parity unpinned: the
-compression factor of A^[1] under the 2-D block scheme (the paper's table
-gives 19.6 at N = 1024 and 1e-5; this decomposition reaches 2-4).
+compression ratio (kept elements per row) of Laguerre functions at
+Gauss-Laguerre nodes and Hermite functions at Gauss-Hermite nodes, for which
+the paper prints no numbers (reported, not pinned).
 """
 from . import special, families, method, method2d  # noqa: F401

@@ -30,7 +30,12 @@ Readings (the paper shows the decomposition only as a figure):
 - the recursion above, both remainders decomposed by the same rule;
 - the same eps1 (threshold and zeta) and eps2 for every block;
 - a rectangle is dense when a side is <= tail (default 20, the 1-D tail) or
-  when an extra count reaches the side it extends.
+  when an extra count reaches the side it extends;
+- A^[1] is zero below its diagonal (its definition in Section 5.3): a
+  rectangle that lies wholly there, and a block whose valid part does, is
+  left out -- it adds exactly zero to every output.  Its extension would
+  otherwise bring the diagonal's jump into the block and keep nearly every
+  element of a block whose valid part is zero.
 """
 from __future__ import annotations
 
@@ -141,9 +146,16 @@ def supported(family: str) -> bool:
     return family in ("laguerre", "hermite") or family in KERNELS
 
 
-def decompose(N: int, zeta: float, eps2: float, tail: int = 20):
+def zero_below_diagonal(family: str) -> bool:
+    """A^[1] vanishes for i > j (Section 5.3)."""
+    return family == "a1"
+
+
+def decompose(N: int, zeta: float, eps2: float, tail: int = 20, lower_zero: bool = False):
     """Cover the N x N index square by the valid rectangles of 2-D blocks and
-    dense rectangles (each (row, column) exactly once).  Returns (blocks as
+    dense rectangles (each (row, column) exactly once; with `lower_zero`,
+    rectangles and valid parts wholly below the diagonal are left out, so
+    entries there are covered at most once).  Returns (blocks as
     (r0, Lr, vr0, r1, c0, Lc, vc0, c1), dense rectangles as (r0, r1, c0, c1))."""
     blocks, dense = [], []
     todo = [(0, N, 0, N)]
@@ -151,6 +163,8 @@ def decompose(N: int, zeta: float, eps2: float, tail: int = 20):
         r0, r1, c0, c1 = todo.pop()
         mr, mc = r1 - r0, c1 - c0
         if mr <= 0 or mc <= 0:
+            continue
+        if lower_zero and r0 >= c1:      # every row index above every column index
             continue
         if mr <= tail or mc <= tail:
             dense.append((r0, r1, c0, c1))
@@ -163,7 +177,8 @@ def decompose(N: int, zeta: float, eps2: float, tail: int = 20):
         if sr >= mr or sc >= mc:
             dense.append((r0, r1, c0, c1))
             continue
-        blocks.append((r0, Lr, r0 + sr, r1, c0, Lc, c0 + sc, c1))
+        if not (lower_zero and r0 + sr >= c1):
+            blocks.append((r0, Lr, r0 + sr, r1, c0, Lc, c0 + sc, c1))
         todo.append((r0, r0 + sr, c0, c1))
         todo.append((r0 + sr, r1, c0, c0 + sc))
     return blocks, dense
@@ -185,7 +200,7 @@ def build(spec: Spec2D, eps: float, eps2: float = 1e-3, tail: int = 20,
         raise ValueError("the 2-D scheme extends rows downwards: Laguerre or Hermite functions")
     zeta = special.zeta_of_eps(eps if eps > 0 else (eps_window or 1e-14))
     plan = Plan2D(spec, eps, eps2, zeta)
-    blocks, dense = decompose(spec.N, zeta, eps2, tail)
+    blocks, dense = decompose(spec.N, zeta, eps2, tail, zero_below_diagonal(spec.family))
     for (r0, Lr, vr0, r1, c0, Lc, vc0, c1) in blocks:
         b = Block2D(r0, Lr, vr0, r1, c0, Lc, vc0, c1, special.kaiser_window(Lr, zeta),
                     special.kaiser_window(Lc, zeta))

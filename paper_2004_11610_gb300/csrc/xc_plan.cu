@@ -1792,8 +1792,10 @@ struct Blk2 {
 // Cover the N x N index square by the valid rectangles of 2-D blocks and
 // dense rectangles: a rectangle takes a block whose first sr rows and sc
 // columns (window below eps2) are left to two further rectangles; a side of
-// at most `tail` makes it dense.
-void decompose_2d(int64_t N, double zeta, double eps2, int64_t tail, std::vector<Blk2>* blocks,
+// at most `tail` makes it dense.  lower_zero (A^[1], zero for i > j): a
+// rectangle wholly below the diagonal, and a block whose valid part is, is
+// left out (it adds exactly zero; its extension would bring in the jump).
+void decompose_2d(int64_t N, double zeta, double eps2, int64_t tail, bool lower_zero, std::vector<Blk2>* blocks,
                   std::vector<D2Rect>* rects) {
   std::vector<std::array<int64_t, 4>> todo{{0, N, 0, N}};
   while (!todo.empty()) {
@@ -1802,6 +1804,7 @@ void decompose_2d(int64_t N, double zeta, double eps2, int64_t tail, std::vector
     const int64_t r0 = t[0], r1 = t[1], c0 = t[2], c1 = t[3];
     const int64_t mr = r1 - r0, mc = c1 - c0;
     if (mr <= 0 || mc <= 0) continue;
+    if (lower_zero && r0 >= c1) continue;
     const D2Rect whole{int(r0), int(r1), int(c0), int(c1), 0};
     if (mr <= tail || mc <= tail) {
       rects->push_back(whole);
@@ -1819,7 +1822,7 @@ void decompose_2d(int64_t N, double zeta, double eps2, int64_t tail, std::vector
       rects->push_back(whole);
       continue;
     }
-    blocks->push_back(Blk2{r0, Lr, r0 + sr, r1, c0, Lc, c0 + sc, c1});
+    if (!(lower_zero && r0 + sr >= c1)) blocks->push_back(Blk2{r0, Lr, r0 + sr, r1, c0, Lc, c0 + sc, c1});
     todo.push_back({r0, r0 + sr, c0, c1});
     todo.push_back({r0 + sr, r1, c0, c0 + sc});
   }
@@ -1869,7 +1872,7 @@ int build_plan_2d(Plan* p) {
   p->d2 = d2;
   std::vector<Blk2> blks;
   const int64_t tail = p->params.tail_max > 0 ? p->params.tail_max : 20;
-  decompose_2d(N, p->zeta, p->eps2, tail, &blks, &d2->rects_host);
+  decompose_2d(N, p->zeta, p->eps2, tail, p->family == XC_KERNEL_A1, &blks, &d2->rects_host);
   const int nb = int(blks.size());
   d2->nb = nb;
   int64_t mmax = N + 2, rmax = N;

@@ -55,7 +55,7 @@ CASES = [  # family, N, eps, spec parameters
     ("laguerre", 300, 1e-10, dict(eta=20.0)), ("laguerre", 1000, 1e-10, dict(eta=100.0)),
     ("hermite", 260, 1e-9, dict(x0=-12.0, h=0.09)), ("a1", 240, 1e-8, {}), ("a2", 250, 1e-8, {}),
     ("a2", 1024, 1e-10, {}), ("a2", 150, 0.0, {}), ("laguerre", 64, 0.0, dict(eta=5.0)),
-    ("a1", 21, 1e-8, {}),
+    ("a1", 21, 1e-8, {}), ("a1", 1024, 1e-8, {}),
 ]
 
 
@@ -133,6 +133,23 @@ def test_2d_plans_refuse_what_they_do_not_support(xc):
     with pytest.raises(xc.XcError) as e:
         xc.Plan("legendre", 100, 1e-8, nodes=np.linspace(-0.9, 0.9, 100), scheme="2d")
     assert e.value.code == xc.XC_ERR_UNSUPPORTED
+
+
+def test_a1_leaves_out_the_rectangles_below_its_diagonal(xc):
+    """A^[1] is zero below its diagonal: the plan holds exactly the oracle's
+    blocks and dense rectangles, none of them wholly below the diagonal, and
+    still gives the dense product at eps1 = 0."""
+    spec = spec_of("a1", 600)
+    with make(xc, spec, 0.0, eps2=1e-3) as plan:
+        ora = M2.build(spec, 0.0, eps2=1e-3)
+        info = plan.info()
+        assert info["blocks2d"] == len(ora.blocks) and info["dense2d"] == len(ora.dense)
+        stored = info["nnz2d"] + info["dense_elems2d"]
+        assert stored == sum(b.Lr * b.Lc for b in ora.blocks) + sum((d.r1 - d.r0) * (d.c1 - d.c0) for d in ora.dense)
+        X = inputs.normal(600, 3, 66)
+        D = M2.dense_matrix(spec)
+        assert max_rel(run(plan, X), X @ D.T) <= 1e-10
+        assert max_rel(run(plan, X, True), X @ D) <= 1e-10
 
 
 def test_bench_size_laguerre_transform(xc):

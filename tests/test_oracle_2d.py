@@ -1,7 +1,8 @@
 """Pins of the oracle's 2-D compression (eq. (comp_2d)) and its block scheme
 (Sections 4.2, 5.3): what fixes them independently of the oracle's formulas.
 
-- the decomposition covers every (row, column) of the matrix exactly once;
+- the decomposition covers every (row, column) of the matrix exactly once
+  (for A^[1], every entry on or above the diagonal; below it at most once);
 - eps1 = 0 keeps every element: the product equals the dense product up to
   rounding amplified by 1/eps2 (the identity behind eq. (comp_2d));
 - eps1 > 0: error within the eps1/eps2 bound of Section 2.2;
@@ -13,8 +14,8 @@
 - the paper's numbers: the Laguerre transform matrix at t_i = 12 i/(N-1)
   compresses "up to 3-4 %" in its main block (Section 5.3, eta = 100, 1e-10),
   where the 1-D compression keeps no fewer elements than the matrix has;
-  A^[2]'s compression factors N^2/nnz of the wavelet table (Section 5.3) are
-  met within a factor of two.
+  the compression factors N^2/nnz of A^[1] and A^[2] in the wavelet table
+  (Section 5.3) are met within a factor of two at the table's accuracy.
 """
 import math
 
@@ -44,10 +45,11 @@ SPECS = [
 
 
 @pytest.mark.parametrize("N", [21, 64, 300, 1000, 1024])
-def test_decomposition_covers_every_entry_once(N):
+@pytest.mark.parametrize("lower_zero", [False, True])
+def test_decomposition_covers_every_entry_once(N, lower_zero):
     from oracle import special as S
     zeta = S.zeta_of_eps(1e-8)
-    blocks, dense = M2.decompose(N, zeta, 1e-3)
+    blocks, dense = M2.decompose(N, zeta, 1e-3, lower_zero=lower_zero)
     cover = np.zeros((N, N), dtype=np.int32)
     for (r0, Lr, vr0, r1, c0, Lc, vc0, c1) in blocks:
         assert r0 <= vr0 < r1 <= r0 + Lr and c0 <= vc0 < c1 <= c0 + Lc
@@ -58,7 +60,13 @@ def test_decomposition_covers_every_entry_once(N):
         cover[vr0:r1, vc0:c1] += 1
     for (r0, r1, c0, c1) in dense:
         cover[r0:r1, c0:c1] += 1
-    assert np.all(cover == 1)
+    if not lower_zero:
+        assert np.all(cover == 1)
+    else:
+        upper = np.triu(np.ones((N, N), dtype=bool))
+        assert np.all(cover[upper] == 1) and np.all(cover <= 1)
+        if N >= 300:       # the left strip under the first block lies below the diagonal
+            assert cover[~upper].sum() < (~upper).sum()
 
 
 @pytest.mark.parametrize("name,spec", SPECS)
@@ -76,10 +84,8 @@ def test_error_within_the_eps1_over_eps2_bound(name, spec, eps, eps2):
     P = M2.build(spec, eps, eps2=eps2)
     D = M2.dense_matrix(spec)
     X = np.random.default_rng(2).standard_normal((4, spec.N))
-    # A^[1] jumps across its diagonal: the bound holds with a larger constant
-    c = 100.0 if spec.family == "a1" else 10.0
-    assert M.rel_l2(M2.apply(P, X), X @ D.T) <= c * eps / eps2
-    assert M.rel_l2(M2.apply_adjoint(P, X), X @ D) <= c * eps / eps2
+    assert M.rel_l2(M2.apply(P, X), X @ D.T) <= 10.0 * eps / eps2
+    assert M.rel_l2(M2.apply_adjoint(P, X), X @ D) <= 10.0 * eps / eps2
 
 
 @pytest.mark.parametrize("name,spec", SPECS)
@@ -91,7 +97,7 @@ def test_adjoint_is_the_exact_transpose(name, spec):
     assert abs(y @ fx - M2.apply_adjoint(P, y) @ x) <= 1e-12 * np.abs(y).sum() * np.abs(fx).max()
 
 
-@pytest.mark.parametrize("fam", ["laguerre", "a2"])
+@pytest.mark.parametrize("fam", ["laguerre", "a1", "a2"])
 def test_tiny_matrices_rebuilt_entrywise(fam):
     for N in (5, 21, 48):
         spec = M2.Spec2D(fam, N, 0.3, 0.7) if fam == "laguerre" else M2.Spec2D(fam, N)
@@ -154,5 +160,23 @@ def test_a2_compression_factor_near_the_wavelet_table(N, eps, eps2, paper_factor
     X = np.random.default_rng(4).standard_normal((3, N))
     err = M.rel_l2(M2.apply(P, X), X @ M2.dense_matrix(spec).T)
     assert err <= (1e-2 if eps > 1e-5 else 2e-6)
+    factor = 1.0 / M2.stored_fraction(P)
+    assert paper_factor / 2 <= factor <= paper_factor * 2
+
+
+@pytest.mark.parametrize("N,eps,eps2,paper_factor", [(64, 1e-6, 3e-2, 1.36), (128, 1e-7, 1e-2, 2.63),
+                                                     (256, 1e-7, 1e-2, 5.16), (512, 1e-7, 1e-2, 9.5),
+                                                     (1024, 1e-8, 1e-2, 19.6)])
+def test_a1_compression_factor_near_the_wavelet_table(N, eps, eps2, paper_factor):
+    """Section 5.3's table: N^2 / nnz of A^[1] at accuracy 1e-5 (1.36, 2.63,
+    5.16, 9.5, 19.6 for N = 64 .. 1024), with the rectangles below the
+    diagonal, where A^[1] is zero, left out; eps1/eps2 chosen to reach that
+    accuracy.  Met within a factor of two."""
+    spec = M2.Spec2D("a1", N)
+    P = M2.build(spec, eps, eps2=eps2)
+    X = np.random.default_rng(5).standard_normal((3, N))
+    D = M2.dense_matrix(spec)
+    assert M.rel_l2(M2.apply(P, X), X @ D.T) <= 1e-5
+    assert M.rel_l2(M2.apply_adjoint(P, X), X @ D) <= 1e-5
     factor = 1.0 / M2.stored_fraction(P)
     assert paper_factor / 2 <= factor <= paper_factor * 2
