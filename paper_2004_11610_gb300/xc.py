@@ -239,6 +239,14 @@ class Plan:
             raise ValueError(f"{name} must have shape (nrhs, N) with unit column stride")
         return t
 
+    @staticmethod
+    def _like(t):
+        """An output with the input's shape and strides (the boundary takes one
+        leading dimension for both; empty_like would make a strided input's
+        output contiguous)."""
+        import torch
+        return torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, device=t.device)
+
     def _pair(self, a, b, na, nb):
         """Checks the input and output tensors of an apply (one leading
         dimension serves both) and returns that leading dimension."""
@@ -254,9 +262,8 @@ class Plan:
 
     def apply(self, x, out=None, stream=None):
         """y = A x for x of shape (nrhs, N) (xc_apply)."""
-        import torch
         x = self._check_tensor(x if x.dim() == 2 else x[None, :], "x")
-        y = torch.empty_like(x) if out is None else out
+        y = self._like(x) if out is None else out
         ld = self._pair(x, y, "x", "out")
         _check(_lib.xc_apply(self._h, _P(x.data_ptr()), _P(y.data_ptr()), x.shape[0], ld,
                              _stream_handle(stream)), "xc_apply")
@@ -265,9 +272,8 @@ class Plan:
     def apply_adjoint(self, y, out=None, stream=None):
         """x = A^T y for y of shape (nrhs, N) (xc_apply_adjoint; the plain
         transpose for the complex families)."""
-        import torch
         y = self._check_tensor(y if y.dim() == 2 else y[None, :], "y")
-        x = torch.empty_like(y) if out is None else out
+        x = self._like(y) if out is None else out
         ld = self._pair(y, x, "y", "out")
         _check(_lib.xc_apply_adjoint(self._h, _P(y.data_ptr()), _P(x.data_ptr()), y.shape[0], ld,
                                      _stream_handle(stream)), "xc_apply_adjoint")

@@ -259,6 +259,10 @@ def test_leading_dimension_and_host_path(xc):
         o = out.cpu().numpy()
         assert max_rel(o[:, :300], y_ref) <= fp64_tol(ora, 1e-10)
         assert np.all(o[:, 300:] == 7.0)           # padding untouched
+        ys = plan.apply(big[:, :300])              # strided input: the output takes its strides
+        torch.cuda.synchronize()
+        assert ys.stride() == (320, 1)
+        assert max_rel(ys.cpu().numpy(), y_ref) <= fp64_tol(ora, 1e-10)
         yh = plan.apply_host(X)
         assert max_rel(yh, y_ref) <= fp64_tol(ora, 1e-10)
         xh = plan.apply_host(X, adjoint=True)
