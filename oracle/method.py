@@ -41,7 +41,7 @@ class OracleBlock:
     j_lo: int
     j_hi: int
     window: np.ndarray            # w_j^{zeta, L-1}, j = 0..L-1
-    maxsq: float                  # max |Ä_e|^2 over the whole block
+    maxsq: float                  # max |Ä_e|^2 over the whole block (orthonormal: of lam_n |ä|^2)
     kept: sps.csr_matrix          # thresholded Ä_e restricted to `rows`, full spectrum
     nnz_half: np.ndarray | None = None   # kept elements per row with k <= L/2
 
@@ -161,6 +161,15 @@ def build(spec, eps: float, eps2: float | None = None, precision: str = "fp64",
     The comparison is made on squared magnitudes, |ä|^2 > eps1^2 * max|ä|^2, which
     is the same test in exact arithmetic.  With eps == 0 every element is kept.
 
+    The orthonormal variant (Section 5.2) applies B = diag(sqrt(lam)) A
+    diag(1/sqrt(chi)); its rows are those of A times sqrt(lam_n), and so are
+    the rows of its compressed matrix (the window and the DFT act along the
+    rows).  The threshold is taken on those: lam_n |ä|^2 > eps1^2 max(lam |ä|^2).
+    Thresholding A's own compressed matrix instead loses the rows of small
+    polynomial values that carry most of the weight, and the accuracy of the
+    forward transform would fall with alpha and beta, which Section 5.2 says
+    it does not.
+
     `rows` restricts what is stored (the maximum still runs over all rows), so
     that sampled outputs of a full-size plan can be computed.
     """
@@ -173,18 +182,25 @@ def build(spec, eps: float, eps2: float | None = None, precision: str = "fp64",
     rows = np.arange(N) if rows is None else np.asarray(rows)
     r, c = fam_mod.scalings(spec, normalise)
     plan = OraclePlan(spec, sch, normalise, rows, r, c)
+    lam = fam_mod.quadrature_weights(spec) if normalise else None   # row weights of the threshold
+
+    def weighted(comp, sel):
+        mag = comp.real ** 2 + comp.imag ** 2
+        return mag if lam is None else lam[sel][:, None] * mag
+
     for b in sch.blocks:
         maxsq = 0.0
         for lo in range(0, N, chunk):
-            comp = compress_rows(spec, b, sch.zeta, np.arange(lo, min(N, lo + chunk)))
-            maxsq = max(maxsq, float(np.max(comp.real ** 2 + comp.imag ** 2)))
+            sel = np.arange(lo, min(N, lo + chunk))
+            comp = compress_rows(spec, b, sch.zeta, sel)
+            maxsq = max(maxsq, float(np.max(weighted(comp, sel))))
         thr = (eps * eps) * maxsq
         pieces = []
         nnz_half = []
         for lo in range(0, rows.size, chunk):
             sel = rows[lo:lo + chunk]
             comp = compress_rows(spec, b, sch.zeta, sel)
-            mag = comp.real ** 2 + comp.imag ** 2
+            mag = weighted(comp, sel)
             keep = mag > thr if eps > 0 else np.ones_like(mag, dtype=bool)
             nnz_half.append(np.count_nonzero(keep[:, : b.L // 2 + 1], axis=1))
             pieces.append(sps.csr_matrix(np.where(keep, comp, 0.0)))

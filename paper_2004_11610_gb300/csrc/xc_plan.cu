@@ -36,6 +36,9 @@ struct GenParams {
   const double* rc = nullptr;
   int64_t nrc = 0;
   int cpart = 0;        // complex families: 0 = real part cos(m theta), 1 = imaginary part sin(m theta)
+  // orthonormal variant: lambda_n, the squared row scale, which weights the
+  // threshold (null: unweighted)
+  const double* rw = nullptr;
 };
 
 __host__ __device__ __forceinline__ bool is_complex_family(int family) {
@@ -501,10 +504,11 @@ __global__ void gen_rows_kernel(GenParams g, int64_t row0, int64_t C, int64_t L,
 }
 
 // One CTA per row of the chunk: real FFT of length L = 2n of the windowed row,
-// S[row][k] = U_k / L for k = 0..n, and the block maximum of |S|^2.
+// S[row][k] = U_k / L for k = 0..n, and the block maximum of |S|^2 (times
+// rw[row] where row weights are given).
 __global__ void __launch_bounds__(256) row_fft_kernel(const double* G, int64_t C, int64_t row0, int64_t N,
                                                       BlockDev b, const cx<double>* tw, cx<double>* S,
-                                                      unsigned long long* maxsq_bits) {
+                                                      unsigned long long* maxsq_bits, const double* rw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<double>* s = reinterpret_cast<cx<double>*>(smem_raw);
   __shared__ double red[8];
@@ -517,6 +521,7 @@ __global__ void __launch_bounds__(256) row_fft_kernel(const double* G, int64_t C
   __syncthreads();
   fft_inplace<double>(s, n, b.p, b.radix, tw, threadIdx.x, blockDim.x);
   const double scale = 1.0 / double(b.L);
+  const double wt = rw ? rw[row] : 1.0;
   cx<double>* out = S + row * int64_t(n + 1);
   double local = 0.0;
   for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
@@ -526,7 +531,7 @@ __global__ void __launch_bounds__(256) row_fft_kernel(const double* G, int64_t C
     Unk = scal(scale, Unk);
     out[k] = Uk;
     out[n - k] = Unk;
-    local = fmax(local, fmax(Uk.re * Uk.re + Uk.im * Uk.im, Unk.re * Unk.re + Unk.im * Unk.im));
+    local = fmax(local, wt * fmax(Uk.re * Uk.re + Uk.im * Uk.im, Unk.re * Unk.re + Unk.im * Unk.im));
   }
   for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
@@ -546,7 +551,8 @@ __global__ void __launch_bounds__(256) row_fft_kernel(const double* G, int64_t C
 // passes.  Launched with cluster dimension (csize, 1, 1), grid = rows * csize.
 __global__ void __launch_bounds__(256) row_fft_cluster_kernel(const double* G, int64_t C, int64_t row0, int64_t N,
                                                               BlockDev b, const cx<double>* tw, cx<double>* S,
-                                                              unsigned long long* maxsq_bits, int csize) {
+                                                              unsigned long long* maxsq_bits, int csize,
+                                                              const double* rw) {
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<double>* s = reinterpret_cast<cx<double>*>(smem_raw);
@@ -571,6 +577,7 @@ __global__ void __launch_bounds__(256) row_fft_cluster_kernel(const double* G, i
   const double scale = 1.0 / double(b.L);
   double local = 0.0;
   if (live) {
+    const double wt = rw ? rw[row] : 1.0;
     cx<double>* out = S + row * int64_t(n + 1);
     for (int k = tid; k <= n / 2; k += nthreads) {
       cx<double> Uk, Unk;
@@ -579,7 +586,7 @@ __global__ void __launch_bounds__(256) row_fft_cluster_kernel(const double* G, i
       Unk = scal(scale, Unk);
       out[k] = Uk;
       out[n - k] = Unk;
-      local = fmax(local, fmax(Uk.re * Uk.re + Uk.im * Uk.im, Unk.re * Unk.re + Unk.im * Unk.im));
+      local = fmax(local, wt * fmax(Uk.re * Uk.re + Uk.im * Uk.im, Unk.re * Unk.re + Unk.im * Unk.im));
     }
   }
   for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
@@ -670,7 +677,7 @@ __host__ __device__ __forceinline__ void cf_window(int64_t row, int64_t N, int64
 // the candidate bins are computed; S is zero elsewhere.  One CTA per row.
 __global__ void __launch_bounds__(128) cheb_rows_closed_kernel(int64_t N, int64_t L, int64_t off, int n, int M,
                                                                int B, const cx<double>* xw, cx<double>* S,
-                                                               unsigned long long* maxsq_bits) {
+                                                               unsigned long long* maxsq_bits, const double* rw) {
   __shared__ cx<double> ah[2 * kCfMaxB + 2 * kCfMaxM + 1];
   __shared__ cx<double> xs[2 * kCfMaxM + 1];
   __shared__ double red[4];
@@ -709,6 +716,7 @@ __global__ void __launch_bounds__(128) cheb_rows_closed_kernel(int64_t N, int64_
   }
   __syncthreads();
   const double scale = 1.0 / (double(L) * double(L));
+  const double wt = rw ? rw[row] : 1.0;
   double local = 0.0;
   for (int64_t k = klo + threadIdx.x; k <= khi; k += blockDim.x) {
     double re = 0.0, im = 0.0;
@@ -720,7 +728,7 @@ __global__ void __launch_bounds__(128) cheb_rows_closed_kernel(int64_t N, int64_
     re *= scale;
     im *= scale;
     S[row * int64_t(n + 1) + k] = cx<double>{re, im};
-    local = fmax(local, re * re + im * im);
+    local = fmax(local, wt * (re * re + im * im));
   }
   for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
@@ -733,16 +741,21 @@ __global__ void __launch_bounds__(128) cheb_rows_closed_kernel(int64_t N, int64_
 }
 
 __device__ __forceinline__ bool kept(cx<double> v, double thr) { return v.re * v.re + v.im * v.im > thr; }
+// The real blocks' test: |v|^2, times the row weight where there are weights.
+__device__ __forceinline__ bool kept_row(cx<double> v, double thr, const double* rw, int64_t row) {
+  const double m = v.re * v.re + v.im * v.im;
+  return (rw ? rw[row] * m : m) > thr;
+}
 
 // One warp per row: first/last kept bin and the number of kept bins.
 __global__ void extents_kernel(const cx<double>* S, int64_t N, int64_t H, double thr, int* kfirst, int* klast,
-                               int* count) {
+                               int* count, const double* rw) {
   const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= N) return;
   int lo = INT_MAX, hi = -1, cnt = 0;
   for (int64_t k = lane; k < H; k += 32) {
-    if (kept(S[row * H + k], thr)) {
+    if (kept_row(S[row * H + k], thr, rw, row)) {
       lo = min(lo, int(k));
       hi = max(hi, int(k));
       ++cnt;
@@ -778,7 +791,8 @@ __device__ __forceinline__ void store_value(cx<T>* dst, cx<double> v, int pair) 
 // and k = n), everything else zero.
 template <typename T>
 __global__ void fill_forward_kernel(const cx<double>* S, int64_t N, int n, double thr, const int* k0,
-                                    const int* width, const int64_t* off, int nslices, cx<T>* val, int pair) {
+                                    const int* width, const int64_t* off, int nslices, cx<T>* val, int pair,
+                                    const double* rw) {
   const int s = blockIdx.y;
   if (s >= nslices) return;
   const int W = width[s];
@@ -791,7 +805,7 @@ __global__ void fill_forward_kernel(const cx<double>* S, int64_t N, int n, doubl
   if (row < N) {
     const int k = k0[row] + j;
     const cx<double> a = S[row * int64_t(n + 1) + k];
-    if (kept(a, thr)) v = scal((k == 0 || k == n) ? 1.0 : 2.0, a);
+    if (kept_row(a, thr, rw, row)) v = scal((k == 0 || k == n) ? 1.0 : 2.0, a);
   }
   store_value(val + off[s] + idx, v, pair);
 }
@@ -799,7 +813,8 @@ __global__ void fill_forward_kernel(const cx<double>* S, int64_t N, int n, doubl
 // Transposed band values: slice s of bins, lane -> bin 32 s + lane, row n0[bin] + j.
 template <typename T>
 __global__ void fill_adjoint_kernel(const cx<double>* S, int64_t N, int n, double thr, const int* n0,
-                                    const int* width, const int64_t* off, int tslices, cx<T>* val, int pair) {
+                                    const int* width, const int64_t* off, int tslices, cx<T>* val, int pair,
+                                    const double* rw) {
   const int s = blockIdx.y;
   if (s >= tslices) return;
   const int W = width[s];
@@ -812,7 +827,7 @@ __global__ void fill_adjoint_kernel(const cx<double>* S, int64_t N, int n, doubl
   if (k <= n) {
     const int64_t row = n0[k] + j;
     const cx<double> a = S[row * int64_t(n + 1) + k];
-    if (kept(a, thr)) v = a;
+    if (kept_row(a, thr, rw, row)) v = a;
   }
   store_value(val + off[s] + idx, v, pair);
 }
@@ -1329,7 +1344,7 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
         row_fft_kernel<<<unsigned(rows), 256, smem>>>(static_cast<double*>(Gbuf.ptr), C, row0, N, b,
                                                        static_cast<cx<double>*>(tw64.ptr),
                                                        static_cast<cx<double>*>(Sbuf.ptr),
-                                                       static_cast<unsigned long long*>(maxbuf.ptr));
+                                                       static_cast<unsigned long long*>(maxbuf.ptr), g.rw);
       } else {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(unsigned(rows * csize));
@@ -1344,7 +1359,7 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
         cfg.numAttrs = 1;
         XC_CUDA(cudaLaunchKernelEx(&cfg, row_fft_cluster_kernel, static_cast<const double*>(Gbuf.ptr), C, row0, N,
                                    b, static_cast<const cx<double>*>(tw64.ptr), static_cast<cx<double>*>(Sbuf.ptr),
-                                   static_cast<unsigned long long*>(maxbuf.ptr), csize));
+                                   static_cast<unsigned long long*>(maxbuf.ptr), csize, g.rw));
       }
       XC_CUDA(cudaGetLastError());
     }
@@ -1369,7 +1384,7 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
     XC_CUDA(cudaMemset(Sbuf.ptr, 0, s_bytes));
     cheb_rows_closed_kernel<<<unsigned(N), 128>>>(N, b.L, b.off, n, cf_M, cf_B, static_cast<cx<double>*>(xw.ptr),
                                                   static_cast<cx<double>*>(Sbuf.ptr),
-                                                  static_cast<unsigned long long*>(maxbuf.ptr));
+                                                  static_cast<unsigned long long*>(maxbuf.ptr), g.rw);
     XC_CUDA(cudaGetLastError());
     XC_CUDA(cudaDeviceSynchronize());
     return XC_OK;
@@ -1402,7 +1417,7 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
   auto extents = [&]() -> int {
     extents_kernel<<<unsigned((N * 32 + 255) / 256), 256>>>(static_cast<cx<double>*>(Sbuf.ptr), N, H, thr,
                                                             static_cast<int*>(kf.ptr), static_cast<int*>(kl.ptr),
-                                                            static_cast<int*>(cnt.ptr));
+                                                            static_cast<int*>(cnt.ptr), g.rw);
     XC_CUDA(cudaGetLastError());
     XC_CUDA(cudaMemcpy(kfirst.data(), kf.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
     XC_CUDA(cudaMemcpy(klast.data(), kl.ptr, size_t(N) * sizeof(int), cudaMemcpyDeviceToHost));
@@ -1533,12 +1548,12 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
   if (maxW > 0) {
     dim3 grid(unsigned((int64_t(maxW) * kSlice + 255) / 256), unsigned(nslices));
     fill_forward_kernel<T><<<grid, 256>>>(static_cast<cx<double>*>(Sbuf.ptr), N, n, thr, fk0_d, fw_d, foff_d,
-                                          nslices, static_cast<cx<T>*>(fval), pair);
+                                          nslices, static_cast<cx<T>*>(fval), pair, g.rw);
   }
   if (maxTW > 0) {
     dim3 grid(unsigned((int64_t(maxTW) * kSlice + 255) / 256), unsigned(tslices));
     fill_adjoint_kernel<T><<<grid, 256>>>(static_cast<cx<double>*>(Sbuf.ptr), N, n, thr, tn0_d, tw_d, toff_d,
-                                          tslices, static_cast<cx<T>*>(tval), pair);
+                                          tslices, static_cast<cx<T>*>(tval), pair, g.rw);
   }
   XC_CUDA(cudaGetLastError());
   XC_CUDA(cudaDeviceSynchronize());
@@ -1630,7 +1645,7 @@ int build_block_complex(Plan* p, const GenParams& g, const BlockShape& shp) {
                                                             static_cast<double*>(Gbuf.ptr));
         row_fft_kernel<<<unsigned(rows), 256, smem>>>(static_cast<double*>(Gbuf.ptr), C, row0, N, b,
                                                        static_cast<cx<double>*>(tw64.ptr), S,
-                                                       static_cast<unsigned long long*>(maxbuf.ptr));
+                                                       static_cast<unsigned long long*>(maxbuf.ptr), nullptr);
         XC_CUDA(cudaGetLastError());
       }
     }
@@ -1966,7 +1981,7 @@ int build_plan_2d(Plan* p) {
                     size_t(std::max(col.n, row.n)) * sizeof(cx<double>)));
     row_fft_kernel<<<unsigned(Lr), 256, size_t(col.n) * sizeof(cx<double>)>>>(
         static_cast<double*>(G.ptr), Lr, 0, Lr, col, static_cast<cx<double>*>(twc64.ptr),
-        static_cast<cx<double>*>(S1.ptr), static_cast<unsigned long long*>(dummy.ptr));
+        static_cast<cx<double>*>(S1.ptr), static_cast<unsigned long long*>(dummy.ptr), nullptr);
     XC_CUDA(cudaGetLastError());
     // along the rows: real and imaginary parts of every column bin q
     DevBuf Re, Im, A, Bm;
@@ -1980,10 +1995,10 @@ int build_plan_2d(Plan* p) {
     const size_t rsm = size_t(row.n) * sizeof(cx<double>);
     row_fft_kernel<<<unsigned(Hc), 256, rsm>>>(static_cast<double*>(Re.ptr), Hc, 0, Hc, row,
                                                 static_cast<cx<double>*>(twr64.ptr), static_cast<cx<double>*>(A.ptr),
-                                                static_cast<unsigned long long*>(dummy.ptr));
+                                                static_cast<unsigned long long*>(dummy.ptr), nullptr);
     row_fft_kernel<<<unsigned(Hc), 256, rsm>>>(static_cast<double*>(Im.ptr), Hc, 0, Hc, row,
                                                 static_cast<cx<double>*>(twr64.ptr), static_cast<cx<double>*>(Bm.ptr),
-                                                static_cast<unsigned long long*>(dummy.ptr));
+                                                static_cast<unsigned long long*>(dummy.ptr), nullptr);
     XC_CUDA(cudaGetLastError());
     std::vector<cx<double>> Ah(size_t(Hc) * size_t(Hr)), Bh(size_t(Hc) * size_t(Hr));
     XC_CUDA(cudaMemcpy(Ah.data(), A.ptr, Ah.size() * sizeof(cx<double>), cudaMemcpyDeviceToHost));
@@ -2259,8 +2274,8 @@ int build_plan_device(Plan* p) {
     g.nrc = p->nrc;
   }
   const bool fp64 = p->io64();
+  DevBuf lam;   // orthonormal variant: lambda_n, also the row weights of the blocks' thresholds
   if (p->normalise == XC_ORTHONORMAL) {
-    DevBuf lam;
     XC_TRY(alloc_tmp(&lam, size_t(N) * sizeof(double)));
     XC_TRY(plan_alloc(p, &p->rowscale, size_t(N) * p->elem_bytes()));
     XC_TRY(plan_alloc(p, &p->colscale, size_t(N) * p->elem_bytes()));
@@ -2268,6 +2283,7 @@ int build_plan_device(Plan* p) {
     scales_kernel<<<gN, 128>>>(g, static_cast<double*>(lam.ptr), p->rowscale, p->colscale, fp64 ? 1 : 0);
     XC_CUDA(cudaGetLastError());
     XC_CUDA(cudaDeviceSynchronize());
+    g.rw = static_cast<const double*>(lam.ptr);
   }
 
   const int nb = int(p->sch.blocks.size());

@@ -199,6 +199,25 @@ def test_orthonormal_and_block_scheme_variants(xc):
         assert max_rel(y, y_ref) <= fp64_tol(ora, 1e-10)
 
 
+@pytest.mark.parametrize("alpha,beta", [(3.0, 3.0), (5.0, 1.0), (-0.7, 2.0)])
+def test_orthonormal_jacobi_keeps_its_accuracy_for_large_alpha_beta(xc, alpha, beta):
+    """The orthonormal variant thresholds the row-weighted compressed matrix
+    (Section 5.2: the forward accuracy does not change with alpha and beta):
+    same kept elements as the oracle, products equal to the oracle's and
+    within the eps1/eps2 level of the dense orthonormal matrix."""
+    N, eps = 512, 1e-10
+    ora, plan = gpu_plan(xc, "jacobi", N, eps, "fp64", 1e-3, normalise=True, alpha=alpha, beta=beta)
+    with plan:
+        check_schedule(ora, plan)
+        X = inputs.uniform_pm1(N, 3, 33)
+        y, y_ref = run_both(xc, plan, ora, X)
+        assert max_rel(y, y_ref) <= fp64_tol(ora, eps)
+        xa, xa_ref = run_both(xc, plan, ora, X, adjoint=True)
+        assert max_rel(xa, xa_ref) <= fp64_tol(ora, eps)
+        Q = F.dense_matrix(ora.spec, normalise=True)
+        assert M.rel_l2(y, X @ Q.T) <= eps / 1e-3 and M.rel_l2(xa, X @ Q) <= eps / 1e-3
+
+
 @pytest.mark.parametrize("N", [2, 3, 8, 20, 21, 33])
 def test_tiny_and_dense_only_plans(xc, N):
     """N <= tail_max: no compressed block, the whole product is the dense tail."""

@@ -138,6 +138,23 @@ def test_orthonormal_round_trip():
     assert M.rel_l2(M.apply_adjoint(P, M.apply(P, x)), x) < 1e-9
 
 
+def test_orthonormal_jacobi_accuracy_does_not_change_with_alpha_beta():
+    """Section 5.2: the accuracy of the forward (and transposed) orthonormal
+    Jacobi transform stays the same as alpha or beta grow (Gauss-Jacobi nodes,
+    eps1 = 1e-10, eps2 = 1e-3): every error under eps1/eps2 and all within a
+    factor of ten of each other."""
+    N = 512
+    x = np.random.default_rng(7).uniform(0, 1, (3, N))
+    errs = []
+    for a, b in ((0.0, 0.0), (0.5, -0.5), (1.5, 0.3), (-0.7, 2.0), (3.0, 3.0), (5.0, 1.0)):
+        sp = F.make_spec("jacobi", N, alpha=a, beta=b)
+        P = M.build(sp, 1e-10, eps2=1e-3, normalise=True)
+        errs.append(M.rel_l2(M.apply(P, x), M.dense_apply(sp, x, normalise=True)))
+        errs.append(M.rel_l2(M.apply_adjoint(P, x), M.dense_apply_adjoint(sp, x, normalise=True)))
+    assert max(errs) <= 1e-10 / 1e-3
+    assert max(errs) <= 10 * min(errs)
+
+
 # ------------------------------------------------------- Appendix A closed forms
 
 def y_cos(theta, N):
