@@ -119,6 +119,24 @@ def test_chebyshev_bandwidth_section51(case):
         assert b.nnz_half.max() <= CLAIMS["rho_max"]["value"] + 1
 
 
+@pytest.mark.parametrize("case", CLAIMS["jacobi_bw"]["cases"])
+@pytest.mark.parametrize("fam,alpha,beta", [("legendre", 0.0, 0.0), ("jacobi", 0.5, -0.5)])
+def test_block_nnz_does_not_depend_on_the_block_order(case, fam, alpha, beta):
+    """Section 5.2: the compressed N x N_i submatrix of every block keeps a
+    number of elements of the order of bw N whatever N_i is.  Per block of
+    order N_i >= 4 bw (below that the half spectrum itself has fewer than 2 bw
+    bins), kept elements per row (half spectrum) lie within 15 % of the first
+    block's and between bw/3 and bw, for N = 2048 and 4096 (orders ~N down to
+    ~100)."""
+    for N in (2048, 4096):
+        sp = F.make_spec(fam, N, alpha=alpha, beta=beta)
+        P = M.build(sp, case["eps1"], eps2=case["eps2"])
+        per_row = [b.nnz_half.sum() / N for b in P.blocks if b.L >= 4 * case["bw"]]
+        assert len(per_row) >= 2
+        assert all(abs(r - per_row[0]) <= 0.15 * per_row[0] for r in per_row)
+        assert all(case["bw"] / 3 <= r <= case["bw"] for r in per_row)
+
+
 def test_forward_accuracy_tracks_eps():
     sp = _spec("chebyshev", 1000)
     x = np.random.default_rng(2).uniform(0, 1, (2, 1000))
