@@ -86,7 +86,10 @@ typedef enum {
 
 /* normalisation */
 #define XC_RAW         0   /* A[n,m] = phi_m(x_n) */
-#define XC_ORTHONORMAL 1   /* sqrt(lambda_n / chi_m) phi_m(x_n): orthogonal at Gauss nodes (Section 5.2) */
+#define XC_ORTHONORMAL 1   /* sqrt(lambda_n / chi_m) phi_m(x_n): orthogonal at Gauss nodes (Section 5.2);
+                              the threshold is taken on this matrix's compressed rows,
+                              lambda_n |a|^2 > eps1^2 max(lambda |a|^2), so the accuracy
+                              does not fall with the Jacobi alpha, beta */
 
 /* apply precision */
 #define XC_FP64             0   /* FP64 FFT, FP64 sparse product */
