@@ -4,7 +4,7 @@ block scheme (Sections 4.2 and 5.3), step by step -- test infrastructure only
 
 The matrix D[i, m] = phi_m(x_i) of a one-sided family (Laguerre or Hermite
 functions) at equispaced nodes x_i = x0 + i h.  Its rows (nodes) and columns
-(degrees) are extended "from below" and "on the right" (Section 6: the
+(degrees) are extended below the last row and to the right of the last column (Section 6: the
 functions stay defined and decay there), never before the first row or
 column.  A block is a rectangle of rows [r0, r1) and columns [c0, c1) of D:
 

@@ -186,7 +186,7 @@ def schedule(N: int, eps: float, eps2: float, two_sided: bool,
       L_i = m_i + s_i columns; its first s_i inputs are zeroed and the next
       block covers columns [0, s_i).  Blocks are added while m_i > tail_max;
       the remaining m_tail columns are multiplied directly (Section 3, last
-      step "by the direct method").  Reading: tail_max = 20 reproduces the
+      step, a direct product).  Reading: tail_max = 20 reproduces the
       number of blocks in Table 1.
     """
     ew = eps if eps > 0 else (eps_window if eps_window > 0 else 1e-14)

@@ -12,7 +12,7 @@
   nodes, Lambda(z) = Gamma(z+1/2)/Gamma(z+1) vs mpmath, A^[2] at a few entries
   by hand;
 - the paper's numbers: the Laguerre transform matrix at t_i = 12 i/(N-1)
-  compresses "up to 3-4 %" in its main block (Section 5.3, eta = 100, 1e-10),
+  keeps at most 3-4 % of its elements in its main block (Section 5.3, eta = 100, 1e-10),
   where the 1-D compression keeps no fewer elements than the matrix has;
   the compression factors N^2/nnz of A^[1] and A^[2] in the wavelet table
   (Section 5.3) are met within a factor of two at the table's accuracy.
@@ -138,7 +138,7 @@ def test_entries_against_independent_evaluations():
 
 def test_laguerre_transform_main_block_compresses_to_a_few_percent():
     """Section 5.3: eta = 100, accuracy 1e-10, N = 1000 -- the compressed
-    matrix keeps "up to 3-4 %" of the elements; the 1-D compressions of
+    matrix keeps at most 3-4 % of the elements; the 1-D compressions of
     Section 4.2 do not reduce them."""
     spec = laguerre_transform(1000, 100.0)
     P = M2.build(spec, 1e-10, eps2=1e-3)
