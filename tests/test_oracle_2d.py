@@ -29,6 +29,22 @@ from oracle import method as M
 from oracle import method2d as M2
 
 
+def wavelet_table():
+    """{N: (A1 wavelet, A1 extra, A2 wavelet 1e-2, A2 extra 1e-2, A2 extra
+    1e-6)} from tests/golden/wavelet_table.txt (Section 5.3)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "wavelet_table.txt")
+    rows = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            v = line.split()
+            rows[int(v[0])] = tuple(float(t) for t in v[1:])
+    return rows
+
+
+TABLE = wavelet_table()
+
+
 def laguerre_transform(N, eta):
     """D[i, m] = l_m(eta t_i), t_i = 12 (i + 1) / (N - 1) (the points of
     Section 5.3, i = 1..N, shifted to a 0-based index)."""
@@ -148,8 +164,8 @@ def test_laguerre_transform_main_block_compresses_to_a_few_percent():
     assert sum(b.kept.nnz for b in one_d.blocks) >= 0.9 * 1000 ** 2
 
 
-@pytest.mark.parametrize("N,eps,eps2,paper_factor", [(512, 1e-3, 1e-1, 10.3), (1024, 1e-3, 1e-1, 23.0),
-                                                     (1024, 1e-7, 1e-2, 6.5)])
+@pytest.mark.parametrize("N,eps,eps2,paper_factor", [(512, 1e-3, 1e-1, TABLE[512][3]), (1024, 1e-3, 1e-1, TABLE[1024][3]),
+                                                     (1024, 1e-7, 1e-2, TABLE[1024][4])])
 def test_a2_compression_factor_near_the_wavelet_table(N, eps, eps2, paper_factor):
     """Section 5.3's table: N^2 / nnz of A^[2] at accuracy 1e-2 (10.3 at
     N = 512, 23 at 1024) and 1e-6 (6.5 at 1024); eps1/eps2 chosen to reach
@@ -164,9 +180,9 @@ def test_a2_compression_factor_near_the_wavelet_table(N, eps, eps2, paper_factor
     assert paper_factor / 2 <= factor <= paper_factor * 2
 
 
-@pytest.mark.parametrize("N,eps,eps2,paper_factor", [(64, 1e-6, 3e-2, 1.36), (128, 1e-7, 1e-2, 2.63),
-                                                     (256, 1e-7, 1e-2, 5.16), (512, 1e-7, 1e-2, 9.5),
-                                                     (1024, 1e-8, 1e-2, 19.6)])
+@pytest.mark.parametrize("N,eps,eps2,paper_factor", [(64, 1e-6, 3e-2, TABLE[64][1]), (128, 1e-7, 1e-2, TABLE[128][1]),
+                                                     (256, 1e-7, 1e-2, TABLE[256][1]), (512, 1e-7, 1e-2, TABLE[512][1]),
+                                                     (1024, 1e-8, 1e-2, TABLE[1024][1])])
 def test_a1_compression_factor_near_the_wavelet_table(N, eps, eps2, paper_factor):
     """Section 5.3's table: N^2 / nnz of A^[1] at accuracy 1e-5 (1.36, 2.63,
     5.16, 9.5, 19.6 for N = 64 .. 1024), with the rectangles below the
