@@ -128,8 +128,13 @@ SCHEME_2D = 3
 
 
 def algorithmic_work(info, nrhs, precision, chunked=False):
-    """Per kernel: algorithmic flops and bytes of one launch.
-    A chunked forward product (plans with long bands) leaves the dense tail
+    """Per kernel: algorithmic flops and bytes of one launch.  Bytes: the
+    kept band values read once per launch (the 2-D CSR also its index words),
+    the vectors and spectra read and written once per right-hand side.  Flops
+    per right-hand side: 4 per kept element of a real plan (complex value times
+    complex spectrum, real part kept), 8 for complex plans and the 2-D CSR,
+    2.5 L log2 L per real FFT of length L (5 L log2 L complex), 2 per element
+    of a dense tail or rectangle.  A chunked forward product (plans with long bands) leaves the dense tail
     and the output to the reduction kernel; its partial sums are scratch, not
     algorithmic traffic."""
     eb = 8 if precision in ("fp64", "fp64pair") else 4
