@@ -47,7 +47,7 @@ extern "C" {
 #define XC_ERR_ALLOC       -2   /* device or host allocation failed */
 #define XC_ERR_CUDA        -3   /* a CUDA runtime call or kernel launch failed */
 #define XC_ERR_TIMEOUT     -4   /* a bounded device-side wait gave up */
-#define XC_ERR_UNSUPPORTED -5   /* valid request outside what this build implements */
+#define XC_ERR_UNSUPPORTED -5   /* valid request outside what the library implements */
 
 /* ---------------------------------------------------------------- families */
 typedef enum {
