@@ -15,7 +15,9 @@
   keeps at most 3-4 % of its elements in its main block (Section 5.3, eta = 100, 1e-10),
   where the 1-D compression keeps no fewer elements than the matrix has;
   the compression factors N^2/nnz of A^[1] and A^[2] in the wavelet table
-  (Section 5.3) are met within a factor of two at the table's accuracy.
+  (Section 5.3) are met within a factor of two at the table's accuracy;
+- planted mistakes (a DFT sign, a valid range off by one, a conjugate
+  transpose, extra counts too small, a dropped factor of A^[1]) fail a pin.
 """
 import math
 
@@ -196,3 +198,69 @@ def test_a1_compression_factor_near_the_wavelet_table(N, eps, eps2, paper_factor
     assert M.rel_l2(M2.apply_adjoint(P, X), X @ D) <= 1e-5
     factor = 1.0 / M2.stored_fraction(P)
     assert paper_factor / 2 <= factor <= paper_factor * 2
+
+
+# ------------------------------------------------------------- planted mistakes
+
+def _dense_error(P, spec, adjoint=False):
+    D = M2.dense_matrix(spec)
+    X = np.random.default_rng(11).standard_normal((2, spec.N))
+    if adjoint:
+        return M.rel_l2(M2.apply_adjoint(P, X), X @ D)
+    return M.rel_l2(M2.apply(P, X), X @ D.T)
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Each mutation of the 2-D oracle must make one of the pins above fail."""
+    from oracle import special as S
+    spec = laguerre_transform(300, 20.0)
+
+    # 1. inverse DFT along the rows of D̈ (a sign error in one dimension of
+    #    eq. (comp_2d)): the eps1 = 0 identity breaks
+    real_compress = M2.compress_block
+
+    def compress_wrong_sign(sp, b):
+        De = sp.values(b.r0, b.r0 + b.Lr, b.c0, b.c0 + b.Lc)
+        A = b.wr[:, None] * De * b.wc[None, :]
+        return np.fft.ifft(np.fft.fft(A, axis=1), axis=0) * np.sqrt(b.Lr / b.Lc)
+
+    monkeypatch.setattr(M2, "compress_block", compress_wrong_sign)
+    assert _dense_error(M2.build(spec, 0.0, eps2=1e-3), spec) > 1e-3
+    monkeypatch.setattr(M2, "compress_block", real_compress)
+    assert _dense_error(M2.build(spec, 0.0, eps2=1e-3), spec) < 1e-11
+
+    # 2. a valid range one row short (wrong index): a row loses its block's
+    #    contribution and the identity breaks
+    P = M2.build(spec, 0.0, eps2=1e-3)
+    P.blocks[0].vr0 += 1
+    assert _dense_error(P, spec) > 1e-6
+
+    # 3. conjugate transpose in the adjoint: the exact-transpose pin breaks
+    P = M2.build(spec, 1e-8, eps2=1e-3)
+    rng = np.random.default_rng(3)
+    x, y = rng.standard_normal(spec.N), rng.standard_normal(spec.N)
+    yfx = y @ M2.apply(P, x)
+    for b in P.blocks:
+        b.kept = b.kept.conj()
+    assert abs(yfx - M2.apply_adjoint(P, y) @ x) > 1e-6 * abs(yfx)
+
+    # 4. extra counts three too small: some valid rows keep a window below eps2,
+    #    which the decomposition pin checks
+    real_extra = S.extra_count
+    monkeypatch.setattr(S, "extra_count", lambda *a, **k: max(0, real_extra(*a, **k) - 3))
+    blocks, _ = M2.decompose(1000, S.zeta_of_eps(1e-8), 1e-3)
+    monkeypatch.setattr(S, "extra_count", real_extra)
+    low = min(S.kaiser_window(Lr, S.zeta_of_eps(1e-8))[vr0 - r0:r1 - r0].min()
+              for (r0, Lr, vr0, r1, c0, Lc, vc0, c1) in blocks)
+    assert low < 1e-3
+
+    # 5. A^[1] with the Lambda(j - i) factor dropped: the entries pin against
+    #    mpmath breaks
+    def a1_dropped_factor(i, j):
+        i, j = np.broadcast_arrays(np.asarray(i), np.asarray(j))
+        return np.where(i <= j, (2 / np.pi) * M2.lam(j + i), 0.0)
+
+    monkeypatch.setattr(M2, "KERNELS", dict(M2.KERNELS, a1=a1_dropped_factor))
+    A1 = M2.Spec2D("a1", 10).values(0, 10, 0, 10)
+    ref = 2 / math.pi * float(mpmath.gamma(3.5) / mpmath.gamma(4) * mpmath.gamma(7.5) / mpmath.gamma(8))
+    assert abs(A1[2, 5] - ref) > 1e-6

@@ -13,7 +13,9 @@ What fixes them independently of the oracle's own formulas:
 - the method with eps1 = 0 reproduces the dense product (the identity of
   eqs. (comp1)/(comp2)); with eps1 > 0 its error is of order eps1;
 - the adjoint is the plain transpose (bilinear identity, no conjugation);
-- at tiny N the method applied to the identity rebuilds the matrix entrywise.
+- at tiny N the method applied to the identity rebuilds the matrix entrywise;
+- planted mistakes (the sign of psi, a conjugated row factor, a conjugate
+  transpose, shifted default angles) fail a pin.
 """
 import math
 
@@ -147,3 +149,51 @@ def test_complex_method_rebuilds_tiny_matrices_entrywise(fam):
         A = M.apply(plan, np.eye(N, dtype=np.complex128)).T      # column m = A e_m
         ref = F.dense_matrix(spec)
         assert np.abs(A - ref).max() <= 1e-11 * np.abs(ref).max(), N
+
+
+# ------------------------------------------------------------- planted mistakes
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Each mutation of the complex oracle must make one of the pins above fail."""
+    eta, T, N = 50.0, 2.0, 40
+    k = 2 * np.pi * np.arange(N) / T
+
+    def power_form_error():
+        C = F.dense_matrix(F.make_spec("lagspec", N, alpha=eta, beta=T))
+        a, b = -eta / 2 - 1j * k, eta / 2 - 1j * k
+        ref = np.stack([a ** m / b ** (m + 1) for m in range(N)], axis=1)
+        return np.abs(C - ref).max() / np.abs(ref).max()
+
+    assert power_form_error() < 1e-12
+
+    # 1. psi with the wrong sign (exp(-i m psi)): the power-form pin breaks
+    real_angles = F.lagspec_angles
+    monkeypatch.setattr(F, "lagspec_angles", lambda n, e, p: -real_angles(n, e, p))
+    assert power_form_error() > 1e-3
+    monkeypatch.setattr(F, "lagspec_angles", real_angles)
+
+    # 2. the row factor conjugated, 1/(eta/2 + i k): the power-form pin breaks
+    real_factor = F.lagspec_row_factor
+    monkeypatch.setattr(F, "lagspec_row_factor", lambda n, e, p: np.conj(real_factor(n, e, p)))
+    assert power_form_error() > 1e-3
+    monkeypatch.setattr(F, "lagspec_row_factor", real_factor)
+    assert power_form_error() < 1e-12
+
+    # 3. conjugate transpose in the adjoint: the bilinear transpose pin breaks
+    spec = F.make_spec("lagspec", 150, alpha=50.0, beta=2.0)
+    plan = M.build(spec, 1e-8, eps2=1e-3)
+    rng = np.random.default_rng(9)
+    x, y = crandn(rng, spec.N), crandn(rng, spec.N)
+    lhs = np.sum(y * M.apply(plan, x))
+    for b in plan.blocks:
+        b.kept = b.kept.conj()
+    assert abs(lhs - np.sum(M.apply_adjoint(plan, y) * x)) > 1e-6 * abs(lhs)
+
+    # 4. default exp angles shifted by half an arc (2 n - N instead of
+    #    2 n + 1 - N): still orthogonal, but the first angle reaches -pi, which
+    #    the angle pin rules out
+    real_default = F.exp_default_angles
+    monkeypatch.setattr(F, "exp_default_angles", lambda n: (real_default(n)[0] - 1, n))
+    x0 = F.make_spec("exp", 64).x[0]
+    monkeypatch.setattr(F, "exp_default_angles", real_default)
+    assert not x0 > -np.pi
