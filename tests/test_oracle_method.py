@@ -137,6 +137,21 @@ def test_block_nnz_does_not_depend_on_the_block_order(case, fam, alpha, beta):
         assert all(case["bw"] / 3 <= r <= case["bw"] for r in per_row)
 
 
+@pytest.mark.parametrize("eps2", [1e-3, 1e-2])
+def test_chebyshev_extension_doubles_from_1e8_to_1e15(eps2):
+    """Section 5.1: the two-sided extension takes s ~ N/4 extra columns on each
+    side for accuracy 1e-8 and s ~ N/2 for 1e-15, twice as many.  The paper
+    does not give its eps2; for a fixed eps2 the ratio s(1e-15) / s(1e-8) is
+    within 10 % of two, for N = 512 .. 8192."""
+    c = {c_["accuracy"]: c_["s_over_N"] for c_ in CLAIMS["chebyshev_bw"]["cases"]}
+    for N in (512, 2048, 8192):
+        s = {}
+        for acc in (1e-8, 1e-15):
+            (b,) = S.schedule(N, acc, eps2, True, 0.0, 20).blocks
+            s[acc] = (b.L - N) / 2
+        assert abs(s[1e-15] / s[1e-8] - c[1e-15] / c[1e-8]) <= 0.1 * c[1e-15] / c[1e-8]
+
+
 def test_forward_accuracy_tracks_eps():
     sp = _spec("chebyshev", 1000)
     x = np.random.default_rng(2).uniform(0, 1, (2, 1000))
