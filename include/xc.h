@@ -19,7 +19,8 @@
  *     gives the text of the most recent failure on the calling thread.
  *   - Vectors are row-major [nrhs][ld] with ld >= N: right-hand side r occupies
  *     elements r*ld .. r*ld+N-1.  Their element type is the plan's I/O type:
- *     double for XC_FP64 plans, float for XC_FP32 and XC_FP32_COMPENSATED.
+ *     double for XC_FP64 and XC_FP64_PAIR plans, float for XC_FP32 and
+ *     XC_FP32_COMPENSATED.
  *     The complex families (XC_EXP, XC_LAGUERRE_SPECTRAL) take complex
  *     vectors: an element is two consecutive values (re, im) of the I/O type,
  *     and ld, N and every element count are in complex elements.
