@@ -4,7 +4,6 @@ Test infrastructure only (see the package docstring).  All arithmetic in FP64.
 """
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass, field
 
 import numpy as np
