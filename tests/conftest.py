@@ -6,8 +6,6 @@ else runs on the CPU (oracle pins, host logic, ABI symbol checks).
 import os
 import sys
 
-import pytest
-
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
