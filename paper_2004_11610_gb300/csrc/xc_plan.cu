@@ -740,8 +740,8 @@ __global__ void __launch_bounds__(128) cheb_rows_closed_kernel(int64_t N, int64_
   }
 }
 
-__device__ __forceinline__ bool kept(cx<double> v, double thr) { return v.re * v.re + v.im * v.im > thr; }
-// The real blocks' test: |v|^2, times the row weight where there are weights.
+// The real blocks' threshold test: |v|^2, times the row weight where there
+// are weights, above thr.
 __device__ __forceinline__ bool kept_row(cx<double> v, double thr, const double* rw, int64_t row) {
   const double m = v.re * v.re + v.im * v.im;
   return (rw ? rw[row] * m : m) > thr;
