@@ -565,6 +565,8 @@ def run_xc(args, rank, world, local_rank):
     dense = None
     variant = None
     if not args.no_dense:
+        # FP32 comparator at FP32 accuracy: no TF32 tensor-core rounding
+        torch.backends.cuda.matmul.allow_tf32 = False
         mats = [p.dense_matrix() for p in plans]
         torch.cuda.synchronize(dev)
         errs = []
