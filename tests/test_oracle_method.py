@@ -179,7 +179,9 @@ def test_orthonormal_jacobi_accuracy_does_not_change_with_alpha_beta():
     N = 512
     x = np.random.default_rng(7).uniform(0, 1, (3, N))
     errs = []
-    for a, b in ((0.0, 0.0), (0.5, -0.5), (1.5, 0.3), (-0.7, 2.0), (3.0, 3.0), (5.0, 1.0)):
+    # alpha, beta > -1 anywhere (Section 5.2 widens the range beyond |alpha|, |beta| < 1/2)
+    for a, b in ((0.0, 0.0), (0.5, -0.5), (1.5, 0.3), (-0.7, 2.0), (3.0, 3.0), (5.0, 1.0), (-0.9, -0.9),
+                 (-0.9, 3.0), (8.0, 8.0)):
         sp = F.make_spec("jacobi", N, alpha=a, beta=b)
         P = M.build(sp, 1e-10, eps2=1e-3, normalise=True)
         errs.append(M.rel_l2(M.apply(P, x), M.dense_apply(sp, x, normalise=True)))
