@@ -700,36 +700,46 @@ int adjoint_pair(Plan* p, const void* yv, void* xv, int64_t nrhs, int64_t ld, cu
 // host-side name as a device address; the device address is looked up once
 // per device with cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[XC_NOALLOC_SCRATCH_BYTES];
+// The work counters of the allocation-free sparse launch ({next, done}, reset
+// by the launch's last warp): its own pair, so that it never shares a pair
+// with xc_apply / xc_apply_adjoint on the same plan.  Zero at module load.
+static __device__ __align__(16) unsigned g_noalloc_counters[4];
 
 namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void* g_noalloc_ptr[kMaxDevices] = {};
+void* g_noalloc_ctr[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device (set up on the
-// first call per device).
-int noalloc_scratch(void** out) {
+// Device addresses of g_noalloc_scratch and g_noalloc_counters on the current
+// device (looked up on the first call per device).
+int noalloc_scratch(void** out, unsigned** counters) {
   int dev = 0;
   XC_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(XC_ERR_UNSUPPORTED, "device index beyond 64");
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (g_noalloc_ptr[dev] == nullptr) {
     void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || ptr == nullptr) {
+    void* ctr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&ctr, g_noalloc_counters);
+    if (e != cudaSuccess || ptr == nullptr || ctr == nullptr) {
       cudaGetLastError();
       return fail(XC_ERR_CUDA, std::string("cudaGetSymbolAddress of the no-alloc scratch failed: ") +
                                    cudaGetErrorString(e));
     }
+    g_noalloc_ctr[dev] = ctr;
     g_noalloc_ptr[dev] = ptr;
   }
   *out = g_noalloc_ptr[dev];
+  *counters = static_cast<unsigned*>(g_noalloc_ctr[dev]);
   return XC_OK;
 }
 
 template <typename T, bool COMP>
-int apply_noalloc_impl(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st, void* spec) {
+int apply_noalloc_impl(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t st, void* spec,
+                       unsigned* counters) {
   const BlockDev* bd = static_cast<const BlockDev*>(p->scratch_desc);
   if (!p->blocks.empty()) {
     const size_t smem = size_t(p->max_n) * sizeof(cx<T>);
@@ -751,7 +761,7 @@ int apply_noalloc_impl(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld
   fwd_sparse_kernel<T, RPW, COMP><<<grid, 32 * kSparseWarps, 0, st>>>(
       bd, int(p->blocks.size()), p->N, static_cast<const T*>(x), ld, static_cast<T*>(y),
       static_cast<const cx<T>*>(spec), nrhs, static_cast<const T*>(p->rowscale),
-      static_cast<const T*>(p->colscale), static_cast<const T*>(p->tail), p->m_tail, p->f_order, p->counters, 1);
+      static_cast<const T*>(p->colscale), static_cast<const T*>(p->tail), p->m_tail, p->f_order, counters, 1);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
 }
@@ -769,11 +779,12 @@ int launch_apply_noalloc(Plan* p, const void* x, void* y, int64_t nrhs, int64_t 
   if (p->precision == XC_FP64_PAIR) return fail(XC_ERR_UNSUPPORTED, "xc_apply_noalloc does not take XC_FP64_PAIR plans");
   if (p->max_csize > 1) return fail(XC_ERR_UNSUPPORTED, "xc_apply_noalloc does not take plans with cluster FFTs");
   void* spec = nullptr;
-  XC_TRY(noalloc_scratch(&spec));
+  unsigned* counters = nullptr;
+  XC_TRY(noalloc_scratch(&spec, &counters));
   switch (p->precision) {
-    case XC_FP64: return apply_noalloc_impl<double, false>(p, x, y, nrhs, ld, st, spec);
-    case XC_FP32: return apply_noalloc_impl<float, false>(p, x, y, nrhs, ld, st, spec);
-    default: return apply_noalloc_impl<float, true>(p, x, y, nrhs, ld, st, spec);
+    case XC_FP64: return apply_noalloc_impl<double, false>(p, x, y, nrhs, ld, st, spec, counters);
+    case XC_FP32: return apply_noalloc_impl<float, false>(p, x, y, nrhs, ld, st, spec, counters);
+    default: return apply_noalloc_impl<float, true>(p, x, y, nrhs, ld, st, spec, counters);
   }
 }
 
