@@ -192,6 +192,11 @@ int xc_plan_reserve(xc_plan_t plan, int64_t nrhs);
  *   ld     leading dimension in elements, N <= ld, nrhs * ld <= 2^40
  */
 int xc_apply(xc_plan_t plan, const void* x_dev, void* y_dev, int64_t nrhs, int64_t ld, void* stream);
+/* (xc_apply and xc_apply_adjoint share the plan's scratch and the work
+ * counters of its sparse kernels, which each launch's last warp resets: two
+ * calls on one plan must not overlap on the GPU, or items are skipped and
+ * outputs left unwritten.  Order them on one stream, or use one plan per
+ * stream.) */
 
 /*
  * xc_apply_adjoint -- x = A^T y (Algorithm 2 step 2 / Algorithm 4): per block,
@@ -218,14 +223,29 @@ int xc_apply_adjoint(xc_plan_t plan, const void* y_dev, void* x_dev, int64_t nrh
  * routine.  It needs (sum over blocks of L_i/2 + 1) * nrhs complex elements
  * of the plan's precision; larger requests return XC_ERR_UNSUPPORTED before
  * anything is launched (split the right-hand sides into several calls).
+ * Every row's band is summed in one pass (plans with long bands included:
+ * no chunk partials, which would need more scratch), so results equal
+ * xc_apply's to rounding, not bit for bit, on such plans.
+ *
+ * Refused with XC_ERR_UNSUPPORTED, before anything is launched:
+ *   - XC_FP64_PAIR plans;
+ *   - the complex families (XC_EXP, XC_LAGUERRE_SPECTRAL) and XC_SCHEME_2D plans;
+ *   - plans with a block whose FFT needs a thread-block cluster, i.e. whose
+ *     L/2 complex values exceed one CTA's shared memory: L > 28928 in FP64,
+ *     L > 57856 in FP32 (block method: N above about 23000 in FP64 at
+ *     eps2 = 1e-3 and about 43000 in FP32 at eps2 = 1e-1).
+ *
  *   - The first call on a device looks up that device's address of the array
  *     (once per device, with the device current); make that first call before
  *     any stream capture on the device.
- *   - All calls share the one array and it keeps the last call's contents.
- *     Every element a call reads was written earlier in the same call, so
- *     nothing needs clearing, but calls that overlap on the GPU (different
- *     streams, or different plans at the same time) race on the array: order
- *     them, e.g. on one stream.
+ *   - All calls share the one array, and one pair of work counters of the
+ *     sparse kernel beside it (also a fixed device array, reset by each
+ *     launch's last warp); the array keeps the last call's contents.  Every
+ *     element a call reads was written earlier in the same call, so nothing
+ *     needs clearing, but calls that overlap on the GPU (different streams,
+ *     or different plans at the same time) race on the array and on the
+ *     counters: order them, e.g. on one stream.  A call does not share
+ *     scratch or counters with xc_apply / xc_apply_adjoint on the same plan.
  * Arguments as for xc_apply.
  */
 #define XC_NOALLOC_SCRATCH_BYTES (16ll << 20)
@@ -309,6 +329,9 @@ typedef struct {
   int64_t tasks_forward, tasks_adjoint;
   int64_t shared_bytes;      /* dynamic shared memory of the persistent kernel */
   int64_t matrix_bytes, adjoint_bytes;   /* summed over the plans */
+  int lockstep_forward;      /* 1: plans with tight windows use lockstep band items forward (tuned) */
+  int lockstep_adjoint;      /* the same for the adjoint */
+  int lockstep_plans;        /* plans that run lockstep items in at least one direction */
 } xc_batch_stats;
 
 /* Group nplans distinct plans (host array of handles; all of one precision;
@@ -332,10 +355,24 @@ int xc_batch_bind(xc_batch_t b, const void* const* x_dev, void* const* y_dev, co
  * Launches of one batch, and of batches sharing a plan, must not overlap. */
 int xc_batch_apply(xc_batch_t b, int adjoint, void* stream);
 /* Autotuner: times the bound problem with 1, 2, 4 and 8 right-hand sides per
- * band-product task (forward + adjoint, 3 repetitions each) and keeps the
- * fastest; the choice is cached per batch shape for later binds in the
- * process.  Synchronises `stream`; the bound buffers are restored afterwards. */
+ * band-product task, with and without lockstep items for the plans that have
+ * them (forward + adjoint, 3 repetitions each), and keeps the fastest per
+ * direction; the choice is cached per batch shape for later binds in the
+ * process.  Synchronises `stream`; the bound buffers are restored afterwards.
+ *
+ * Lockstep items: a bind of an FP32 batch builds, for plans whose bands
+ * line up across the 32 rows of a slice (the union of the rows' bands, and
+ * of the bins' row runs, at most 1.25 times the stored bands: Hermite
+ * functions), window copies of both band layouts; their band products then
+ * walk one bin (row) per step for the whole warp, and their spectra are
+ * stored bin-major in scratch owned by the batch.  Plans with long bands sum
+ * them in window pieces whose grouping differs from xc_apply's, so those
+ * results equal xc_apply's to rounding, not bit for bit. */
 int xc_batch_tune(xc_batch_t b, void* stream);
+/* Set the schedule by hand instead of tuning it: right-hand sides per band
+ * item (1, 2, 4 or 8) and lockstep items on (1) or off (0), per direction.
+ * Rebuilds the task lists (synchronous); XC_ERR_ARG before a bind. */
+int xc_batch_schedule(xc_batch_t b, int rpw_forward, int rpw_adjoint, int lockstep_forward, int lockstep_adjoint);
 int xc_batch_info(xc_batch_t b, xc_batch_stats* out);
 /* Synchronise `stream` and report XC_ERR_TIMEOUT if a phase wait of an
  * earlier launch gave up (then clear it); XC_OK otherwise.  While the status
@@ -346,6 +383,37 @@ int xc_batch_status(xc_batch_t b, void* stream);
  * up after wait_limit sleeps of ~256 ns.  extra_need = 0 restores the plan. */
 int xc_batch_debug_set(xc_batch_t b, int plan, int extra_need, int64_t wait_limit);
 int xc_batch_destroy(xc_batch_t b);
+
+/* ------------------------------------------------- direct dense product
+ * The product the method replaces: y = A x with the plain matrix A (Section
+ * 1, eq. (cheb_matrix) / eq. (Jac_matrix); Section 5 compares the method with
+ * it), as a dense GEMM on the tensor cores (tcgen05) at FP32 accuracy:
+ * every FP32 value v = hi + lo with hi, lo exact TF32 numbers (hi = v rounded
+ * to TF32, lo = v - hi rounded to TF32), products accumulated as
+ * hi hi + hi lo + lo hi in FP32 ("3xTF32"; the dropped lo lo term is below
+ * 2^-22 of each product).  The benchmark times it beside the method; it is a
+ * comparator, not part of the method.
+ */
+typedef struct xc_dense* xc_dense_t;
+/* Copy A_dev (device, FP32, row-major [M][lda], lda >= K) into the
+ * comparator: its split A and the split of A^T (both K-major for the tensor
+ * cores), 16 M K bytes of device memory owned by the comparator.  A_dev is
+ * not referenced afterwards.  Synchronises `stream`. */
+int xc_dense_create(xc_dense_t* out, const float* A_dev, int64_t M, int64_t K, int64_t lda, void* stream);
+/* transpose = 0: out[r][m] = sum_k A[m][k] in[r][k]  (m < M, k < K);
+ * transpose = 1: out[r][k] = sum_m A[m][k] in[r][m].
+ * in_dev, out_dev: device FP32 [nrhs][ld], ld >= max(M, K), not overlapping
+ * (XC_ERR_ARG); only the first M (or K) entries of each output row are
+ * written.  Asynchronous on `stream`; the first call with a larger nrhs
+ * allocates the split right-hand sides (8 nrhs max(M, K) bytes, kept).  Calls
+ * on one comparator must not overlap on the GPU.  A device wait that runs out
+ * (about two seconds) is reported by xc_dense_status. */
+int xc_dense_apply(xc_dense_t dense, int transpose, const float* in_dev, float* out_dev, int64_t nrhs, int64_t ld,
+                   void* stream);
+/* Synchronise `stream`; XC_ERR_TIMEOUT (then cleared) if a wait inside an
+ * earlier xc_dense_apply gave up, XC_OK otherwise. */
+int xc_dense_status(xc_dense_t dense, void* stream);
+int xc_dense_destroy(xc_dense_t dense);
 
 /*
  * Per-kernel timing.  While enabled, every kernel the plan launches is

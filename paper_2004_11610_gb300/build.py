@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "libxc.so")
 BUILD = os.path.join(PKG, "_build")
-SOURCES = ["xc_params.cpp", "xc_abi.cpp", "xc_plan.cu", "xc_apply.cu", "xc_batch.cu", "xc_complex.cu", "xc_2d.cu"]
+SOURCES = ["xc_params.cpp", "xc_abi.cpp", "xc_plan.cu", "xc_apply.cu", "xc_batch.cu", "xc_complex.cu", "xc_2d.cu", "xc_dense.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -58,7 +58,8 @@ class xc_batch_stats(ctypes.Structure):
     _fields_ = [("nplans", ctypes.c_int), ("rhs_per_item", ctypes.c_int), ("tuned", ctypes.c_int),
                 ("rhs_per_item_adjoint", ctypes.c_int), ("tasks_forward", ctypes.c_int64), ("tasks_adjoint", ctypes.c_int64),
                 ("shared_bytes", ctypes.c_int64), ("matrix_bytes", ctypes.c_int64),
-                ("adjoint_bytes", ctypes.c_int64)]
+                ("adjoint_bytes", ctypes.c_int64), ("lockstep_forward", ctypes.c_int),
+                ("lockstep_adjoint", ctypes.c_int), ("lockstep_plans", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -86,10 +87,15 @@ _SIGS = {
                                      ctypes.POINTER(_I64)]),
     "xc_batch_apply": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "xc_batch_tune": (ctypes.c_int, [_P, _P]),
+    "xc_batch_schedule": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "xc_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(xc_batch_stats)]),
     "xc_batch_status": (ctypes.c_int, [_P, _P]),
     "xc_batch_debug_set": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _I64]),
     "xc_batch_destroy": (ctypes.c_int, [_P]),
+    "xc_dense_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, _I64, _I64, _I64, _P]),
+    "xc_dense_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _I64, _I64, _P]),
+    "xc_dense_status": (ctypes.c_int, [_P, _P]),
+    "xc_dense_destroy": (ctypes.c_int, [_P]),
     "xc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "xc_last_error_message": (ctypes.c_char_p, []),
 }
@@ -367,6 +373,16 @@ class Batch:
     def tune(self, stream=None):
         _check(_lib.xc_batch_tune(self._h, _stream_handle(stream)), "xc_batch_tune")
 
+    def schedule(self, rpw_forward: int, rpw_adjoint: int, lockstep_forward: bool, lockstep_adjoint: bool):
+        """Set the schedule by hand (xc_batch_schedule) instead of tuning it."""
+        _check(_lib.xc_batch_schedule(self._h, rpw_forward, rpw_adjoint, int(lockstep_forward),
+                                      int(lockstep_adjoint)), "xc_batch_schedule")
+
+    def set_lockstep(self, forward: bool, adjoint: bool):
+        """Lockstep items on or off per direction, keeping the right-hand sides per item."""
+        st = self.info()
+        self.schedule(st["rhs_per_item"], st["rhs_per_item_adjoint"], forward, adjoint)
+
     def info(self) -> dict:
         st = xc_batch_stats()
         _check(_lib.xc_batch_info(self._h, ctypes.byref(st)), "xc_batch_info")
@@ -382,6 +398,63 @@ class Batch:
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.xc_batch_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---------------------------------------------------------- dense comparator
+
+class Dense:
+    """The direct product y = A x with the plain FP32 matrix on the tensor
+    cores, 3xTF32 (xc_dense_*): the comparator the method is measured
+    against.  `A` is a CUDA float32 tensor (M, K); it is copied (split into
+    TF32 halves, with a transposed copy) at construction."""
+
+    def __init__(self, A, stream=None):
+        import torch
+        if not A.is_cuda or A.dtype != torch.float32 or A.dim() != 2 or A.stride(1) != 1:
+            raise TypeError("A must be a 2-D CUDA float32 tensor with unit column stride")
+        self.M, self.K = int(A.shape[0]), int(A.shape[1])
+        h = _P()
+        _check(_lib.xc_dense_create(ctypes.byref(h), _P(A.data_ptr()), self.M, self.K, A.stride(0),
+                                    _stream_handle(stream)), "xc_dense_create")
+        self._h = h
+
+    def apply(self, x, transpose: bool = False, out=None, stream=None):
+        """out[r] = A x[r] (transpose: A^T x[r]) for x of shape (nrhs, K) (or (nrhs, M))."""
+        import torch
+        n_in, n_out = (self.M, self.K) if transpose else (self.K, self.M)
+        if not x.is_cuda or x.dtype != torch.float32 or x.dim() != 2 or x.shape[1] != n_in or x.stride(1) != 1:
+            raise ValueError(f"x must be a CUDA float32 tensor of shape (nrhs, {n_in})")
+        if n_in != n_out and x.shape[0] > 1:
+            raise ValueError("rectangular comparators take one right-hand side per call")
+        ld = x.stride(0) if x.shape[0] > 1 else max(n_in, n_out)
+        if out is None:
+            out = torch.empty_strided((x.shape[0], n_out), (ld, 1), dtype=torch.float32, device=x.device)
+        elif out.shape != (x.shape[0], n_out) or out.stride(1) != 1 or (x.shape[0] > 1 and out.stride(0) != ld):
+            raise ValueError("out must match x's shape and row stride")
+        _check(_lib.xc_dense_apply(self._h, 1 if transpose else 0, _P(x.data_ptr()), _P(out.data_ptr()),
+                                   x.shape[0], ld, _stream_handle(stream)), "xc_dense_apply")
+        return out
+
+    def status(self, stream=None) -> int:
+        """XC_OK or XC_ERR_TIMEOUT (a device wait of an earlier apply gave up; cleared on read)."""
+        return int(_lib.xc_dense_status(self._h, _stream_handle(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.xc_dense_destroy(self._h)
             self._h = _P()
 
     def __del__(self):
