@@ -12,6 +12,14 @@
 //   adjoint   B: transposed band product of (plan, chunk, RPW RHS) and the
 //                dense tail of (plan, column, RHS), one warp each
 //             C: inverse FFT of (plan, block, RHS), one CTA each
+// Plans whose window (lockstep) layouts are tight -- Hermite functions, the
+// bulk of the 1000-plan workload's band values -- run their band products as
+// lockstep items instead (fwd_lock_item / fwd_lock_unit / adj_lock_item): the
+// warp's 32 rows (bins) walk the same bin (row), the forward spectra are
+// written bin-major (bin k of RHS r at k * rp + r, rp = nrhs rounded up to
+// even) into a scratch buffer owned by the batch, so that a spectrum value is
+// one broadcast load for 32 rows instead of a gather per row.  The tuner
+// decides per direction whether such plans use them.
 // Every CTA of a persistent grid works through A (CTA tasks from a device
 // counter), then its warps take B items one by one from a second counter,
 // then -- after a CTA barrier -- it works through C (CTA tasks or warp items).
@@ -31,6 +39,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -50,7 +59,8 @@ namespace {
 constexpr int kBatchThreads = 256;
 constexpr int kBatchWarps = kBatchThreads / 32;
 enum TaskKind {
-  T_FWD_FFT = 0, T_FWD_SPARSE = 1, T_ADJ_SPARSE = 2, T_ADJ_FFT = 3, T_ADJ_TAIL = 4, T_FWD_UNIT = 5, T_FWD_REDUCE = 6
+  T_FWD_FFT = 0, T_FWD_SPARSE = 1, T_ADJ_SPARSE = 2, T_ADJ_FFT = 3, T_ADJ_TAIL = 4, T_FWD_UNIT = 5, T_FWD_REDUCE = 6,
+  T_FWD_LOCK = 7, T_FWD_LUNIT = 8, T_ADJ_LOCK = 9
 };
 // control words: next entry of lists A, B, C; finished CTAs; status
 enum { C_NEXT_A = 0, C_NEXT_B = 1, C_NEXT_C = 2, C_FINISHED = 3, C_STATUS = 4, C_WORDS = 8 };
@@ -74,6 +84,15 @@ struct BatchPlanDev {
   const void* x;
   void* y;
   int64_t nrhs, ld;
+  // lockstep items (lock_f: forward, lock_a: adjoint); their spectra and
+  // partial sums live in lscratch (forward: spectra [bin][rp] of every block,
+  // then the unit partials; adjoint: the chunk partials)
+  int lock_f, lock_a, rp;
+  void* lscratch;
+  const int4* lk_units;
+  const int* lk_ubase;
+  const int2* lk_items;
+  const int* lk_cbase;
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -100,12 +119,18 @@ __device__ int wait_for(const unsigned* done, unsigned need, long long limit, un
 template <typename T>
 __device__ __forceinline__ void run_cta_task(const BatchPlanDev& P, int4 tk, cx<T>* s, int tid) {
   const T* cs = static_cast<const T*>(P.colscale);
-  if (tk.x == T_FWD_FFT)
-    fwd_fft_body<T>(P.blocks[tk.z], tk.w, static_cast<const T*>(P.x), P.ld, cs, static_cast<cx<T>*>(P.scratch),
-                    P.nrhs, s, tid, kBatchThreads);
-  else  // T_ADJ_FFT
-    adj_fft_body<T>(P.blocks[tk.z], tk.w, static_cast<const cx<T>*>(P.scratch), P.t_cbase, P.nrhs,
-                    static_cast<T*>(const_cast<void*>(P.x)), P.ld, cs, s, tid, kBatchThreads);
+  if (tk.x == T_FWD_FFT) {
+    if (P.lock_f)
+      fwd_fft_body<T>(P.blocks[tk.z], tk.w, static_cast<const T*>(P.x), P.ld, cs, static_cast<cx<T>*>(P.lscratch),
+                      P.nrhs, s, tid, kBatchThreads, nullptr, P.rp);
+    else
+      fwd_fft_body<T>(P.blocks[tk.z], tk.w, static_cast<const T*>(P.x), P.ld, cs, static_cast<cx<T>*>(P.scratch),
+                      P.nrhs, s, tid, kBatchThreads);
+  } else {  // T_ADJ_FFT
+    adj_fft_body<T>(P.blocks[tk.z], tk.w, static_cast<const cx<T>*>(P.lock_a ? P.lscratch : P.scratch),
+                    P.lock_a ? P.lk_cbase : P.t_cbase, P.nrhs, static_cast<T*>(const_cast<void*>(P.x)), P.ld, cs, s,
+                    tid, kBatchThreads);
+  }
 }
 
 // One warp item.
@@ -128,13 +153,30 @@ __device__ __forceinline__ void run_warp_item(const BatchPlanDev& P, int4 tk, in
     }
     case T_FWD_REDUCE: {
       const int64_t n = int64_t(tk.z) * 32 + lane;
+      const cx<T>* part = P.lock_f ? static_cast<const cx<T>*>(P.lscratch) + P.spec_per_rhs * P.rp
+                                   : static_cast<const cx<T>*>(P.scratch) + P.spec_per_rhs * P.nrhs;
       if (n < P.N)
         for (int64_t r = 0; r < P.nrhs; ++r)
-          fwd_reduce_row<T, COMP>(P.N, static_cast<const T*>(P.x), P.ld, static_cast<T*>(P.y),
-                                  static_cast<const cx<T>*>(P.scratch) + P.spec_per_rhs * P.nrhs, P.nrhs, P.fu_ubase,
-                                  rs, cs, static_cast<const T*>(P.tail), P.m_tail, n, r);
+          fwd_reduce_row<T, COMP>(P.N, static_cast<const T*>(P.x), P.ld, static_cast<T*>(P.y), part, P.nrhs,
+                                  P.lock_f ? P.lk_ubase : P.fu_ubase, rs, cs, static_cast<const T*>(P.tail), P.m_tail,
+                                  n, r);
       break;
     }
+    case T_FWD_LOCK:
+      fwd_lock_item<T, RPW, COMP>(P.blocks, P.nblocks, P.N, static_cast<const T*>(P.x), P.ld, static_cast<T*>(P.y),
+                                  static_cast<const cx<T>*>(P.lscratch), P.rp, P.nrhs, rs, cs,
+                                  static_cast<const T*>(P.tail), P.m_tail, tk.z, int64_t(tk.w) * RPW, lane);
+      break;
+    case T_FWD_LUNIT:
+      fwd_lock_unit<T, RPW, COMP>(P.blocks, static_cast<const cx<T>*>(P.lscratch), P.rp, P.nrhs,
+                                  static_cast<cx<T>*>(P.lscratch) + P.spec_per_rhs * P.rp, P.lk_units[tk.z], tk.z,
+                                  int64_t(tk.w) * RPW, lane);
+      break;
+    case T_ADJ_LOCK:
+      adj_lock_item<T, RPW, COMP>(P.blocks, P.nblocks, static_cast<const T*>(P.y), P.ld,
+                                  static_cast<cx<T>*>(P.lscratch), P.nrhs, rs, P.lk_cbase, P.lk_items[tk.z],
+                                  int64_t(tk.w) * RPW, lane);
+      break;
     case T_ADJ_SPARSE:
       adj_sparse_item<T, RPW, COMP>(P.blocks, P.nblocks, static_cast<const T*>(P.y), P.ld, nullptr, 0,
                                     static_cast<cx<T>*>(P.scratch), P.nrhs, rs, P.t_cbase, P.t_items[tk.z], kAdjChunk,
@@ -151,13 +193,15 @@ __device__ __forceinline__ void run_warp_item(const BatchPlanDev& P, int4 tk, in
 // increments (-1: none): index p (after the A tasks of plan p) or nplans + p
 // (after its B items).
 __device__ __forceinline__ int waits_on(int kind, int plan, int nplans) {
-  if (kind == T_FWD_SPARSE || kind == T_FWD_UNIT) return plan;
+  if (kind == T_FWD_SPARSE || kind == T_FWD_UNIT || kind == T_FWD_LOCK || kind == T_FWD_LUNIT) return plan;
   if (kind == T_FWD_REDUCE || kind == T_ADJ_FFT) return nplans + plan;
   return -1;
 }
 __device__ __forceinline__ int counts_in(int kind, int plan, int nplans) {
   if (kind == T_FWD_FFT) return plan;
-  if (kind == T_FWD_SPARSE || kind == T_FWD_UNIT || kind == T_ADJ_SPARSE || kind == T_ADJ_TAIL) return nplans + plan;
+  if (kind == T_FWD_SPARSE || kind == T_FWD_UNIT || kind == T_ADJ_SPARSE || kind == T_ADJ_TAIL ||
+      kind == T_FWD_LOCK || kind == T_FWD_LUNIT || kind == T_ADJ_LOCK)
+    return nplans + plan;
   return -1;
 }
 
@@ -277,7 +321,11 @@ struct Batch {
   std::vector<int> extra_need;   // fault injection (tests)
   long long wait_limit = 1LL << 22;   // sleeps of ~256 ns: about a second
   int rpw[2] = {0, 0};           // right-hand sides per band item, per direction (0 = not bound)
+  int lock[2] = {1, 1};          // lockstep items for the plans that have them, per direction
   bool tuned = false;
+  std::vector<BatchPlanDev> host;   // device copies of these are in dplans
+  std::vector<void*> lscratch;   // per plan: the batch's lockstep scratch (nullptr: none)
+  std::vector<int64_t> lscratch_bytes;
   size_t smem = 0;
   int64_t max_n = 0;
   std::vector<const void*> x;
@@ -307,17 +355,69 @@ namespace {
 using Entry = std::pair<double, int4>;   // (cost estimate, entry)
 
 // Work lists of both directions for the bound right-hand sides, with rpw_f
-// (forward) and rpw_a (adjoint) right-hand sides per band item.
-int build_tasks(Batch* b, int rpw_f, int rpw_a) {
+// (forward) and rpw_a (adjoint) right-hand sides per band item; lock_f /
+// lock_a: the plans that have lockstep scratch use lockstep items in that
+// direction.  Uploads the plan descriptors with the matching flags.
+int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
   const int np = int(b->plans.size());
   b->rpw[0] = b->rpw[1] = 0;   // unbound until every list is in place (a failure leaves it so)
   std::vector<Entry> L[2][3];
   std::vector<unsigned> need[2] = {std::vector<unsigned>(2 * size_t(np), 0), std::vector<unsigned>(2 * size_t(np), 0)};
   for (int p = 0; p < np; ++p) {
     const Plan* P = b->plans[p];
+    BatchPlanDev& H = b->host[p];
+    H.lock_f = lock_f && b->lscratch[p] != nullptr && P->lock_f_ok;
+    H.lock_a = lock_a && b->lscratch[p] != nullptr && P->lock_t_ok;
     const int64_t R = b->nrhs[p];
     if (R == 0) continue;
+    if (H.lock_f) {
+      for (size_t i = 0; i < P->blocks.size(); ++i) {
+        const double c = double(P->blocks[i].n) * std::log2(double(P->blocks[i].n) + 1.0);
+        for (int64_t r = 0; r < R; ++r) {
+          L[0][0].push_back({c, int4{T_FWD_FFT, p, int(i), int(r)}});
+          ++need[0][p];
+        }
+      }
+      const int64_t gf = (R + rpw_f - 1) / rpw_f;
+      if (P->fwd_chunked) {
+        for (int64_t k = 0; k < P->lk_total_units; ++k)
+          for (int64_t g = 0; g < gf; ++g) {
+            L[0][1].push_back({double(P->lk_unit_len[k]) * rpw_f, int4{T_FWD_LUNIT, p, int(k), int(g)}});
+            ++need[0][np + p];
+          }
+        for (int64_t s0 = 0; s0 < P->nslices; ++s0)
+          L[0][2].push_back({double(R) * double(P->m_tail + 4), int4{T_FWD_REDUCE, p, int(s0), 0}});
+      } else {
+        for (int64_t s0 = 0; s0 < P->nslices; ++s0) {
+          int64_t w = 0;
+          for (size_t i = 0; i < P->blocks.size(); ++i) w += P->hf_len[i][s0];
+          for (int64_t g = 0; g < gf; ++g) {
+            L[0][1].push_back({double(w + P->m_tail) * rpw_f, int4{T_FWD_LOCK, p, int(s0), int(g)}});
+            ++need[0][np + p];
+          }
+        }
+      }
+    }
+    if (H.lock_a) {
+      const int64_t ga = (R + rpw_a - 1) / rpw_a;
+      for (int64_t i = 0; i < P->lk_total_chunks; ++i)
+        for (int64_t g = 0; g < ga; ++g) {
+          L[1][1].push_back({double(P->lk_item_len[i]) * rpw_a, int4{T_ADJ_LOCK, p, int(i), int(g)}});
+          ++need[1][np + p];
+        }
+      for (int64_t m = 0; m < P->m_tail; ++m)
+        for (int64_t r = 0; r < R; ++r) {
+          L[1][1].push_back({double(P->N) / 32.0, int4{T_ADJ_TAIL, p, int(m), int(r)}});
+          ++need[1][np + p];
+        }
+      for (size_t i = 0; i < P->blocks.size(); ++i) {
+        const double c = double(P->blocks[i].n) * std::log2(double(P->blocks[i].n) + 1.0);
+        for (int64_t r = 0; r < R; ++r) L[1][2].push_back({c, int4{T_ADJ_FFT, p, int(i), int(r)}});
+      }
+    }
+    if (H.lock_f && H.lock_a) continue;
     // forward
+    if (!H.lock_f) {
     for (size_t i = 0; i < P->blocks.size(); ++i) {
       const double c = double(P->blocks[i].n) * std::log2(double(P->blocks[i].n) + 1.0);
       for (int64_t r = 0; r < R; ++r) {
@@ -341,7 +441,9 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a) {
           ++need[0][np + p];
         }
     }
+    }
     // adjoint
+    if (H.lock_a) continue;
     const int64_t ga = (R + rpw_a - 1) / rpw_a;
     for (int64_t i = 0; i < P->total_chunks; ++i)
       for (int64_t g = 0; g < ga; ++g) {
@@ -380,8 +482,11 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a) {
     }
     XC_CUDA(cudaMemcpy(b->need[d], need[d].data(), 2 * size_t(np) * sizeof(unsigned), cudaMemcpyHostToDevice));
   }
+  XC_CUDA(cudaMemcpy(b->dplans, b->host.data(), size_t(np) * sizeof(BatchPlanDev), cudaMemcpyHostToDevice));
   b->rpw[0] = rpw_f;
   b->rpw[1] = rpw_a;
+  b->lock[0] = lock_f;
+  b->lock[1] = lock_a;
   return XC_OK;
 }
 
@@ -429,9 +534,10 @@ int launch_batch(Batch* b, int dir, cudaStream_t st) {
   }
 }
 
-// Tuning cache: batch signature -> chosen right-hand sides per item (forward, adjoint).
+// Tuning cache: batch signature -> chosen (right-hand sides per item, lockstep
+// items on) per direction: {rpw_f, rpw_a, lock_f, lock_a}.
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tune_cache;
+std::map<std::string, std::array<int, 4>> g_tune_cache;
 
 std::string signature(const Batch* b) {
   std::string sig = std::to_string(b->precision) + ":" + std::to_string(b->plans.size());
@@ -490,6 +596,8 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans) {
   }
   b->smem = size_t(b->max_n) * 2 * (b->precision == XC_FP64 ? 8 : 4);
   b->extra_need.assign(nplans, 0);
+  b->lscratch.assign(nplans, nullptr);
+  b->lscratch_bytes.assign(nplans, 0);
   void* ptr = nullptr;
   int rc = b->alloc(&ptr, xc::C_WORDS * sizeof(unsigned));
   if (rc == XC_OK) {
@@ -541,7 +649,28 @@ int xc_batch_bind(xc_batch_t batch, const void* const* x_dev, void* const* y_dev
     for (xc::Plan* p : b->plans) ++p->batch_refs;
     b->holds_refs = true;
   }
-  std::vector<xc::BatchPlanDev> host(np);
+  // lockstep layouts and the batch's lockstep scratch (FP32 plans: the FP64
+  // band products are bound by the FP64 pipe, where the windows' stored
+  // zeros would only add work)
+  for (int i = 0; i < np; ++i) {
+    xc::Plan* p = b->plans[i];
+    if (b->precision == XC_FP64 || nrhs[i] == 0) continue;
+    XC_TRY(xc::ensure_lockstep(p));
+    if (!p->lock_f_ok && !p->lock_t_ok) continue;
+    const int64_t rp = (nrhs[i] + 1) / 2 * 2;
+    const int64_t fwd = p->lock_f_ok ? p->spec_per_rhs * rp + p->lk_total_units * 32 * nrhs[i] : 0;
+    const int64_t adj = p->lock_t_ok ? p->lk_total_chunks * 32 * nrhs[i] : 0;
+    const int64_t bytes = std::max<int64_t>(fwd, adj) * int64_t(sizeof(xc::cx<float>));
+    if (b->lscratch[i] == nullptr || b->lscratch_bytes[i] < bytes) {
+      void* ptr = nullptr;
+      XC_TRY(b->alloc(&ptr, size_t(bytes)));   // kept until the batch goes (a launch may still use the old one)
+      XC_CUDA(cudaMemset(ptr, 0, size_t(bytes)));   // the pad column of odd nrhs stays zero
+      b->lscratch[i] = ptr;
+      b->lscratch_bytes[i] = bytes;
+    }
+  }
+  std::vector<xc::BatchPlanDev>& host = b->host;
+  host.assign(np, xc::BatchPlanDev{});
   for (int i = 0; i < np; ++i) {
     xc::Plan* p = b->plans[i];
     xc::BatchPlanDev& d = host[i];
@@ -569,20 +698,25 @@ int xc_batch_bind(xc_batch_t batch, const void* const* x_dev, void* const* y_dev
     d.y = y_dev[i];
     d.nrhs = nrhs[i];
     d.ld = ld[i];
+    d.rp = int((nrhs[i] + 1) / 2 * 2);
+    d.lscratch = b->lscratch[i];
+    d.lk_units = p->lk_units;
+    d.lk_ubase = p->lk_ubase;
+    d.lk_items = p->lk_items;
+    d.lk_cbase = p->lk_cbase;
   }
-  XC_CUDA(cudaMemcpy(b->dplans, host.data(), size_t(np) * sizeof(xc::BatchPlanDev), cudaMemcpyHostToDevice));
   b->x.assign(x_dev, x_dev + np);
   b->y.assign(y_dev, y_dev + np);
   b->nrhs.assign(nrhs, nrhs + np);
   b->ld.assign(ld, ld + np);
   const int dflt = b->precision == XC_FP64 ? 2 : 8;
-  std::pair<int, int> rpw{b->rpw[0] > 0 ? b->rpw[0] : dflt, b->rpw[1] > 0 ? b->rpw[1] : dflt};
+  std::array<int, 4> cfg{b->rpw[0] > 0 ? b->rpw[0] : dflt, b->rpw[1] > 0 ? b->rpw[1] : dflt, b->lock[0], b->lock[1]};
   {
     std::lock_guard<std::mutex> lock(xc::g_tune_mutex);
     auto it = xc::g_tune_cache.find(xc::signature(b));
-    if (it != xc::g_tune_cache.end()) rpw = it->second;
+    if (it != xc::g_tune_cache.end()) cfg = it->second;
   }
-  return xc::build_tasks(b, rpw.first, rpw.second);
+  return xc::build_tasks(b, cfg[0], cfg[1], cfg[2], cfg[3]);
 }
 
 int xc_batch_apply(xc_batch_t batch, int adjoint, void* stream) {
@@ -627,9 +761,13 @@ int xc_batch_tune(xc_batch_t batch, void* stream) {
   cudaEvent_t ev[3];
   for (auto& e : ev) XC_CUDA(cudaEventCreate(&e));
   int best[2] = {b->rpw[0], b->rpw[1]};
+  int best_lock[2] = {b->lock[0], b->lock[1]};
   float best_ms[2] = {1e30f, 1e30f};
+  bool any_lock = false;
+  for (void* ls : b->lscratch) any_lock = any_lock || ls != nullptr;
+  for (int lk = any_lock ? 1 : 0; lk >= 0; --lk)
   for (int cand : {1, 2, 4, 8}) {
-    XC_TRY(xc::build_tasks(b, cand, cand));
+    XC_TRY(xc::build_tasks(b, cand, cand, lk, lk));
     XC_TRY(xc::launch_batch(b, 0, st));   // warm
     XC_TRY(xc::launch_batch(b, 1, st));
     float ms[2] = {0, 0};
@@ -650,6 +788,7 @@ int xc_batch_tune(xc_batch_t batch, void* stream) {
       if (ms[d] < best_ms[d]) {
         best_ms[d] = ms[d];
         best[d] = cand;
+        best_lock[d] = lk;
       }
   }
   for (auto& e : ev) cudaEventDestroy(e);
@@ -660,11 +799,21 @@ int xc_batch_tune(xc_batch_t batch, void* stream) {
     XC_CUDA(cudaMemcpyAsync(b->y[i], saved[2 * i + 1], bytes, cudaMemcpyDeviceToDevice, st));
   }
   XC_CUDA(cudaStreamSynchronize(st));
-  XC_TRY(xc::build_tasks(b, best[0], best[1]));
+  XC_TRY(xc::build_tasks(b, best[0], best[1], best_lock[0], best_lock[1]));
   b->tuned = true;
   std::lock_guard<std::mutex> lock(xc::g_tune_mutex);
-  xc::g_tune_cache[xc::signature(b)] = {best[0], best[1]};
+  xc::g_tune_cache[xc::signature(b)] = {best[0], best[1], best_lock[0], best_lock[1]};
   return XC_OK;
+}
+
+int xc_batch_schedule(xc_batch_t batch, int rpw_forward, int rpw_adjoint, int lockstep_forward,
+                      int lockstep_adjoint) {
+  auto* b = reinterpret_cast<xc::Batch*>(batch);
+  if (!b) return fail(XC_ERR_ARG, "batch is NULL");
+  if (b->rpw[0] == 0) return fail(XC_ERR_ARG, "bind the batch's buffers first");
+  for (int r : {rpw_forward, rpw_adjoint})
+    if (r != 1 && r != 2 && r != 4 && r != 8) return fail(XC_ERR_ARG, "right-hand sides per item: 1, 2, 4 or 8");
+  return xc::build_tasks(b, rpw_forward, rpw_adjoint, lockstep_forward ? 1 : 0, lockstep_adjoint ? 1 : 0);
 }
 
 int xc_batch_info(xc_batch_t batch, xc_batch_stats* out) {
@@ -677,6 +826,10 @@ int xc_batch_info(xc_batch_t batch, xc_batch_stats* out) {
   out->tuned = b->tuned ? 1 : 0;
   out->tasks_forward = b->entries(0);
   out->tasks_adjoint = b->entries(1);
+  out->lockstep_forward = b->lock[0];
+  out->lockstep_adjoint = b->lock[1];
+  for (size_t i = 0; i < b->plans.size(); ++i)
+    if (i < b->host.size() && (b->host[i].lock_f || b->host[i].lock_a)) ++out->lockstep_plans;
   out->shared_bytes = int64_t(b->smem);
   for (const xc::Plan* p : b->plans) {
     out->matrix_bytes += p->matrix_bytes;
@@ -707,7 +860,7 @@ int xc_batch_debug_set(xc_batch_t batch, int plan, int extra_need, int64_t wait_
     return fail(XC_ERR_ARG, "bad debug setting");
   b->extra_need[plan] = extra_need;
   b->wait_limit = wait_limit;
-  if (b->rpw[0] > 0) return xc::build_tasks(b, b->rpw[0], b->rpw[1]);
+  if (b->rpw[0] > 0) return xc::build_tasks(b, b->rpw[0], b->rpw[1], b->lock[0], b->lock[1]);
   return XC_OK;
 }
 

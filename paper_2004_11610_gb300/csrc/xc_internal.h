@@ -83,6 +83,21 @@ struct BlockDev {
   int t_yt;                  // 1: the adjoint product reads the transposed right-hand sides
   int64_t spec_off;          // offset (complex elements) of this block's spectrum per unit nrhs
   int t_gbase;               // index of this block's first bin slice in the plan-wide slice list
+  // Window ("lockstep") copies of the two band layouts, used by batches (null
+  // until ensure_lockstep builds them).  Forward: row slice s covers the bins
+  // [lf_lo[s], lf_lo[s] + lf_len[s]) -- the union of its 32 rows' bands --
+  // and value (s, bin k, lane) sits at lf_off[s] + (k - lf_lo[s]) * 32 + lane,
+  // zero where k is outside the lane's band; all 32 rows of a warp then step
+  // through the same bin.  Adjoint: bin slice s covers the rows [lt_lo[s],
+  // lt_lo[s] + lt_len[s]) in the same way.
+  const int* lf_lo;
+  const int* lf_len;
+  const int64_t* lf_off;
+  const void* lf_val;
+  const int* lt_lo;
+  const int* lt_len;
+  const int64_t* lt_off;
+  const void* lt_val;
 };
 
 // Rows per chunk of a transposed (bin) slice in the adjoint product: long
@@ -96,6 +111,11 @@ constexpr int64_t kAdjTargetChunks = 512;
 // Band rows per chunk of a row slice in the forward product of plans with long
 // bands; a reduction kernel adds the chunks of each slice.
 constexpr int kFwdChunk = 256;
+
+// A plan's window (lockstep) layouts are used by batches when they store at
+// most this many times the elements of the band layouts (Hermite functions:
+// about 1.05-1.2; Legendre / Jacobi / Chebyshev: 1.5-4).
+constexpr double kLockRatio = 1.25;
 
 // ---------------------------------------------------------- 2-D block scheme
 // One direction of the 2-D scheme (forward: input side = columns, output side
@@ -198,6 +218,23 @@ struct Plan {
   int* c_cbase = nullptr;              // [tslices + 1]
   int64_t c_nchunks = 0;
   int64_t matrix_bytes = 0, adjoint_bytes = 0;
+  // window ("lockstep") layouts for batches (ensure_lockstep): host copies of
+  // each block's windows, the elements they store, and the work lists over
+  // them -- forward units (block, slice, first window position, length) with
+  // the first unit of each slice, adjoint chunks (global bin slice, chunk of
+  // kAdjChunk window rows) with the first chunk of each bin slice
+  std::vector<std::vector<int>> hf_lo, hf_len, ht_lo, ht_len;
+  int64_t lock_f_elems = 0, lock_t_elems = 0;
+  bool lock_built = false;
+  bool lock_f_ok = false, lock_t_ok = false;   // the windows cost at most kLockRatio x the band layouts
+  int4* lk_units = nullptr;
+  int* lk_ubase = nullptr;
+  int64_t lk_total_units = 0;
+  std::vector<int> lk_unit_len;
+  int2* lk_items = nullptr;
+  int* lk_cbase = nullptr;
+  int64_t lk_total_chunks = 0;
+  std::vector<int> lk_item_len;
   // device copy of `blocks` (read by the kernels), scratch spectra, host-path staging
   void* scratch_desc = nullptr;
   void* scratch = nullptr;
@@ -256,6 +293,9 @@ int ensure_scratch(Plan* p, int64_t nrhs);
 int ensure_scratch_kept(Plan* p, int64_t nrhs);
 int launch_apply(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t s);
 int launch_apply_adjoint(Plan* p, const void* y, void* x, int64_t nrhs, int64_t ld, cudaStream_t s);
+// (xc_plan.cu) the window layouts of a real 1-D plan's blocks, built once;
+// uploads the updated block descriptors
+int ensure_lockstep(Plan* p);
 // (xc_2d.cu) execution of the 2-D block scheme
 size_t d2_scratch_bytes(const Plan* p, int64_t nrhs);
 int launch_apply_2d(Plan* p, const void* x, void* y, int64_t nrhs, int64_t ld, cudaStream_t s, bool adjoint);

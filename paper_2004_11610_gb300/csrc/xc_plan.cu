@@ -1531,6 +1531,46 @@ int build_block(Plan* p, int bi, const GenParams& g, const BlockShape& shp) {
   p->c_nchunks = int64_t(citems.size());
   XC_TRY(upload(p, citems, &p->c_items));
   XC_TRY(upload(p, cbase, &p->c_cbase));
+  // windows of the lockstep layouts (ensure_lockstep): per row slice the
+  // union of its rows' bands, per bin slice the union of its bins' row runs
+  {
+    auto& flo = p->hf_lo[bi];
+    auto& flen = p->hf_len[bi];
+    flo.assign(nslices, 0);
+    flen.assign(nslices, 0);
+    for (int s = 0; s < nslices; ++s) {
+      int lo = INT_MAX, hi = -1;
+      for (int l = 0; l < kSlice; ++l) {
+        const int64_t r = int64_t(s) * kSlice + l;
+        if (r < N && klast[r] >= 0) {
+          lo = std::min(lo, fk0[size_t(s) * kSlice + l]);
+          hi = std::max(hi, fk0[size_t(s) * kSlice + l] + fwidth[s]);
+        }
+      }
+      if (hi > lo) {
+        flo[s] = lo;
+        flen[s] = hi - lo;
+      }
+    }
+    auto& tlo = p->ht_lo[bi];
+    auto& tlen = p->ht_len[bi];
+    tlo.assign(tslices, 0);
+    tlen.assign(tslices, 0);
+    for (int s = 0; s < tslices; ++s) {
+      int lo = INT_MAX, hi = -1;
+      for (int l = 0; l < kSlice; ++l) {
+        const int64_t k = int64_t(s) * kSlice + l;
+        if (k < H && nhi[k] >= 0) {
+          lo = std::min(lo, tn0[size_t(s) * kSlice + l]);
+          hi = std::max(hi, tn0[size_t(s) * kSlice + l] + twidth[s]);
+        }
+      }
+      if (hi > lo) {
+        tlo[s] = lo;
+        tlen[s] = hi - lo;
+      }
+    }
+  }
   int *fk0_d, *fw_d, *tn0_d, *tw_d;
   int64_t *foff_d, *toff_d;
   XC_TRY(upload(p, fk0, &fk0_d));
@@ -2288,6 +2328,10 @@ int build_plan_device(Plan* p) {
 
   const int nb = int(p->sch.blocks.size());
   p->blocks.resize(nb);
+  p->hf_lo.assign(nb, {});
+  p->hf_len.assign(nb, {});
+  p->ht_lo.assign(nb, {});
+  p->ht_len.assign(nb, {});
   p->nnz.assign(nb, 0);
   p->stored.assign(nb, 0);
   p->maxabs.assign(nb, 0.0);
@@ -2425,6 +2469,156 @@ int build_plan_device(Plan* p) {
     p->matrix_bytes += p->m_tail * N * int64_t(p->elem_bytes());
   }
   XC_CUDA(cudaDeviceSynchronize());
+  return XC_OK;
+}
+
+// ------------------------------------------------------ lockstep layouts
+// Window copy of a band layout (forward or adjoint, the same shape): slice s
+// of the band layout holds value (j, lane) at off[s] + j * 32 + lane for the
+// lane's rows (bins) start[s * 32 + lane] + j, j < width[s]; its window copy
+// holds (w, lane) at woff[s] + w * 32 + lane for position wlo[s] + w,
+// w < wlen[s], and zero where the lane's band does not reach.  One thread
+// per window element.
+template <typename T>
+__global__ void window_copy_kernel(const cx<T>* __restrict__ val, const int* __restrict__ start,
+                                   const int* __restrict__ width, const int64_t* __restrict__ off,
+                                   const int* __restrict__ wlo, const int* __restrict__ wlen,
+                                   const int64_t* __restrict__ woff, int nslices, cx<T>* __restrict__ out) {
+  const int s = blockIdx.y;
+  if (s >= nslices) return;
+  const int64_t len = int64_t(wlen[s]) * kSlice;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x) {
+    const int w = int(e / kSlice), lane = int(e % kSlice);
+    const int j = wlo[s] + w - start[size_t(s) * kSlice + lane];
+    out[woff[s] + e] = (j >= 0 && j < width[s]) ? val[off[s] + int64_t(j) * kSlice + lane] : cx<T>{T(0), T(0)};
+  }
+}
+
+namespace {
+
+template <typename T>
+int build_lockstep(Plan* p) {
+  const int nb = int(p->blocks.size());
+  int64_t fstored = 0, tstored = 0, fwin = 0, twin = 0;
+  for (int i = 0; i < nb; ++i) {
+    fstored += p->stored[i];
+    for (int v : p->hf_len[i]) fwin += int64_t(v) * kSlice;
+    for (int v : p->ht_len[i]) twin += int64_t(v) * kSlice;
+  }
+  for (int i = 0; i < nb; ++i) {
+    const BlockDev& b = p->blocks[i];
+    std::vector<int> tw(b.tslices);
+    XC_CUDA(cudaMemcpy(tw.data(), b.t_width, tw.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int v : tw) tstored += int64_t(v) * kSlice;
+  }
+  p->lock_f_ok = fstored > 0 && double(fwin) <= kLockRatio * double(fstored);
+  p->lock_t_ok = tstored > 0 && double(twin) <= kLockRatio * double(tstored);
+  p->lock_f_elems = p->lock_f_ok ? fwin : 0;
+  p->lock_t_elems = p->lock_t_ok ? twin : 0;
+  for (int i = 0; i < nb; ++i) {
+    BlockDev& b = p->blocks[i];
+    for (int dir = 0; dir < 2; ++dir) {
+      if (!(dir == 0 ? p->lock_f_ok : p->lock_t_ok)) continue;
+      const std::vector<int>& lo = dir == 0 ? p->hf_lo[i] : p->ht_lo[i];
+      const std::vector<int>& len = dir == 0 ? p->hf_len[i] : p->ht_len[i];
+      const int ns = int(lo.size());
+      std::vector<int64_t> woff(ns, 0);
+      int64_t tot = 0;
+      int maxlen = 0;
+      for (int s = 0; s < ns; ++s) {
+        woff[s] = tot;
+        tot += int64_t(len[s]) * kSlice;
+        maxlen = std::max(maxlen, len[s]);
+      }
+      int *lo_d, *len_d;
+      int64_t* off_d;
+      void* val = nullptr;
+      XC_TRY(upload(p, lo, &lo_d));
+      XC_TRY(upload(p, len, &len_d));
+      XC_TRY(upload(p, woff, &off_d));
+      XC_TRY(plan_alloc(p, &val, size_t(std::max<int64_t>(tot, 1)) * sizeof(cx<T>)));
+      if (maxlen > 0 && ns > 0) {
+        const dim3 grid(unsigned(std::min<int64_t>((int64_t(maxlen) * kSlice + 255) / 256, 4096)), unsigned(ns));
+        if (dir == 0)
+          window_copy_kernel<T><<<grid, 256>>>(static_cast<const cx<T>*>(b.f_val), b.f_k0, b.f_width, b.f_off, lo_d,
+                                               len_d, off_d, ns, static_cast<cx<T>*>(val));
+        else
+          window_copy_kernel<T><<<grid, 256>>>(static_cast<const cx<T>*>(b.t_val), b.t_n0, b.t_width, b.t_off, lo_d,
+                                               len_d, off_d, ns, static_cast<cx<T>*>(val));
+        XC_CUDA(cudaGetLastError());
+      }
+      if (dir == 0) {
+        b.lf_lo = lo_d;
+        b.lf_len = len_d;
+        b.lf_off = off_d;
+        b.lf_val = val;
+      } else {
+        b.lt_lo = lo_d;
+        b.lt_len = len_d;
+        b.lt_off = off_d;
+        b.lt_val = val;
+      }
+    }
+  }
+  // forward units over the windows (plans with long bands): per slice, per
+  // block, window positions cut into pieces of kFwdChunk; slice-major
+  if (p->lock_f_ok && p->fwd_chunked) {
+    std::vector<int4> units;
+    std::vector<int> ubase(size_t(p->nslices) + 1, 0);
+    for (int64_t s2 = 0; s2 < p->nslices; ++s2) {
+      ubase[s2] = int(units.size());
+      for (int i = 0; i < nb; ++i) {
+        const int W = s2 < int64_t(p->hf_len[i].size()) ? p->hf_len[i][s2] : 0;
+        for (int c = 0; c * kFwdChunk < W; ++c)
+          units.push_back(int4{i, int(s2), c * kFwdChunk, std::min(kFwdChunk, W - c * kFwdChunk)});
+      }
+    }
+    ubase[p->nslices] = int(units.size());
+    p->lk_total_units = int64_t(units.size());
+    p->lk_unit_len.resize(units.size());
+    for (size_t u = 0; u < units.size(); ++u) p->lk_unit_len[u] = units[u].w;
+    XC_TRY(upload(p, units, &p->lk_units));
+    XC_TRY(upload(p, ubase, &p->lk_ubase));
+  }
+  // adjoint chunks over the windows: (global bin slice, chunk of kAdjChunk rows)
+  if (p->lock_t_ok) {
+    std::vector<int2> items;
+    std::vector<int> cbase(size_t(p->total_tslices) + 1, 0);
+    int64_t run = 0, g = 0;
+    p->lk_item_len.clear();
+    for (int i = 0; i < nb; ++i)
+      for (size_t s2 = 0; s2 < p->ht_len[i].size(); ++s2, ++g) {
+        const int W = p->ht_len[i][s2];
+        const int nch = W > 0 ? (W + kAdjChunk - 1) / kAdjChunk : 1;
+        cbase[g] = int(run);
+        for (int c = 0; c < nch; ++c) {
+          items.push_back(int2{int(g), c});
+          p->lk_item_len.push_back(std::min(kAdjChunk, std::max(0, W - c * kAdjChunk)));
+        }
+        run += nch;
+      }
+    cbase[g] = int(run);
+    p->lk_total_chunks = run;
+    XC_TRY(upload(p, items, &p->lk_items));
+    XC_TRY(upload(p, cbase, &p->lk_cbase));
+  }
+  XC_CUDA(cudaDeviceSynchronize());
+  return XC_OK;
+}
+
+}  // namespace
+
+int ensure_lockstep(Plan* p) {
+  if (p->lock_built) return XC_OK;
+  if (p->cplx || p->d2 || p->blocks.empty()) {
+    p->lock_built = true;
+    return XC_OK;
+  }
+  if (p->io64()) XC_TRY(build_lockstep<double>(p));
+  else XC_TRY(build_lockstep<float>(p));
+  if (p->scratch_desc)
+    XC_CUDA(cudaMemcpy(p->scratch_desc, p->blocks.data(), p->blocks.size() * sizeof(BlockDev), cudaMemcpyHostToDevice));
+  p->lock_built = true;
   return XC_OK;
 }
 

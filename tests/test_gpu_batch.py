@@ -1,7 +1,9 @@
 """The many-plan persistent launch (xc_batch_*): results equal the single-plan
-applies, the launch replays from a CUDA graph, the autotuner keeps results
-unchanged, and an injected missing dependency ends in XC_ERR_TIMEOUT (a
-bounded device wait) rather than a hang."""
+applies (FP64 batches bit for bit; FP32 batches to rounding, since lockstep
+items of plans with long bands group their sums by window pieces), the
+launch replays from a CUDA graph, the autotuner keeps results unchanged, and
+an injected missing dependency ends in XC_ERR_TIMEOUT (a bounded device
+wait) rather than a hang."""
 import numpy as np
 import pytest
 
@@ -48,6 +50,13 @@ def rel(a, b):
     return float((a.double() - b.double()).abs().max() / b.double().abs().max().clamp_min(1e-300))
 
 
+def tol_for(precision):
+    """Batch against single-plan applies: FP64 bit for bit; FP32 to rounding
+    (the single-plan adjoint of small plans, and the batch's lockstep items
+    of long-band plans, group their partial sums differently)."""
+    return 1e-12 if precision == "fp64" else 2e-6
+
+
 @pytest.mark.parametrize("precision,nplans", [("fp32", 24), ("fp64", 9), ("fp32c", 8)])
 def test_batch_matches_single_plan_applies(xc, precision, nplans):
     plans, xs, ys = make_batch(xc, nplans, precision, 1)
@@ -58,7 +67,7 @@ def test_batch_matches_single_plan_applies(xc, precision, nplans):
             torch.cuda.synchronize()
             assert b.status() == xc.XC_OK
             for p, x, y in zip(plans, xs, ys):
-                assert rel(y, p.apply(x)) <= 1e-12
+                assert rel(y, p.apply(x)) <= tol_for(precision)
             y_saved = [y.clone() for y in ys]
             b.apply(adjoint=True)          # reads y, writes x
             torch.cuda.synchronize()
@@ -66,7 +75,7 @@ def test_batch_matches_single_plan_applies(xc, precision, nplans):
             # single-plan adjoints of small plans cut their bands into shorter
             # chunks than the batch (more warps per right-hand side), which
             # changes the summation order: equal to rounding, not bit for bit
-            tol = 1e-12 if precision == "fp64" else 2e-6
+            tol = tol_for(precision)
             for p, x, y in zip(plans, xs, y_saved):
                 assert rel(x, p.apply_adjoint(y)) <= tol
     finally:
@@ -93,7 +102,7 @@ def test_batch_graph_capture_and_replay(xc):
                 torch.cuda.synchronize()
                 assert b.status() == xc.XC_OK
                 for p, x, y in zip(plans, xs, ys):
-                    assert rel(y, p.apply(x)) <= 1e-12
+                    assert rel(y, p.apply(x)) <= tol_for("fp32")
     finally:
         close_all(plans)
 
@@ -112,7 +121,7 @@ def test_batch_autotune_keeps_results(xc):
             b.apply(False)
             torch.cuda.synchronize()
             for p, x, y in zip(plans, xs, ys):
-                assert rel(y, p.apply(x)) <= 1e-12
+                assert rel(y, p.apply(x)) <= tol_for("fp32")
     finally:
         close_all(plans)
 
@@ -132,7 +141,7 @@ def test_batch_missing_dependency_times_out_without_hanging(xc):
             torch.cuda.synchronize()
             assert b.status() == xc.XC_OK
             for p, x, y in zip(plans, xs, ys):
-                assert rel(y, p.apply(x)) <= 1e-12
+                assert rel(y, p.apply(x)) <= tol_for("fp32")
     finally:
         close_all(plans)
 
@@ -186,6 +195,118 @@ def test_batch_binding_survives_larger_single_applies_and_refused_binds(xc):
             b.apply(False)
             torch.cuda.synchronize()
             for p, x, y in zip(plans, xs, ys):
-                assert rel(y, p.apply(x)) <= 1e-12
+                assert rel(y, p.apply(x)) <= tol_for("fp32")
+    finally:
+        close_all(plans)
+
+
+# Plans of the 1000-plan workload (inputs.batch_workload) chosen so that the
+# slice holds its largest N (Legendre, 8157), its two largest Hermite plans
+# (8039 and 7818), plans with 1 and with 32 right-hand sides, and every family.
+CONFIG4_SLICE = (452, 754, 432, 196, 85, 78, 153, 0, 1, 2)
+
+
+def test_batch_matches_the_oracle_on_a_slice_of_the_1000_plan_workload(xc):
+    """Each plan's forward and adjoint output of the persistent launches
+    (tuned, as the benchmark runs them) against the FP64 oracle: its method
+    (Algorithms 1-4 on the same nodes) and the plain dense product (forward
+    on sampled rows).  Tolerance: relative l2 <= max(10 eps, 1e-5)."""
+    from oracle import families as F
+    from oracle import method as M
+    eps = 1e-7
+    tol = max(10 * eps, 1e-5)
+    wl = inputs.batch_workload(1000)
+    plans, xs, ys, xa, specs, X, Yin = [], [], [], [], [], [], []
+    try:
+        for i in CONFIG4_SLICE:
+            fam, N, params, R = wl[i]
+            sp = F.make_spec(fam, N, params.get("alpha", 0.0), params.get("beta", 0.0))
+            specs.append(sp)
+            p = xc.Plan(fam, N, eps, precision="fp32", alpha=params.get("alpha", 0.0),
+                        beta=params.get("beta", 0.0), nodes=None if fam == "chebyshev" else sp.x)
+            plans.append(p)
+            X.append(inputs.normal(N, R, 4, i, 0))
+            Yin.append(inputs.normal(N, R, 5, i, 0))
+            xs.append(torch.from_numpy(X[-1]).to("cuda", torch.float32))
+            ys.append(torch.empty_like(xs[-1]))
+            xa.append(torch.empty_like(xs[-1]))
+        assert max(p.N for p in plans) >= 8000
+        assert sum(1 for i in CONFIG4_SLICE if wl[i][0] == "hermite") >= 2
+        assert {wl[i][3] for i in CONFIG4_SLICE} >= {1, 32}
+        with xc.Batch(plans) as fwd, xc.Batch(plans) as adj:
+            fwd.bind(xs, ys)
+            adj.bind(xa, ys)
+            fwd.tune()
+            adj.tune()
+            fwd.apply(False)
+            torch.cuda.synchronize()
+            assert fwd.status() == xc.XC_OK
+            Y = [y.double().cpu().numpy() for y in ys]
+            for y, v in zip(ys, Yin):          # independent adjoint inputs
+                y.copy_(torch.from_numpy(v).to(torch.float32))
+            adj.apply(True)
+            torch.cuda.synchronize()
+            assert adj.status() == xc.XC_OK
+            XA = [x.double().cpu().numpy() for x in xa]
+        for i, sp, y, x_in, xa_g, y_in in zip(CONFIG4_SLICE, specs, Y, X, XA, Yin):
+            ora = M.build(sp, eps, precision="fp32")
+            rows = np.unique(np.concatenate([[0, sp.N - 1], np.random.default_rng(i).integers(0, sp.N, 96)]))
+            e = {"fwd_method": M.rel_l2(y, M.apply(ora, x_in)),
+                 "fwd_dense": M.rel_l2(y[:, rows], M.dense_apply(sp, x_in, rows=rows)),
+                 "adj_method": M.rel_l2(xa_g, M.apply_adjoint(ora, y_in))}
+            print(f"batch plan {i} {sp.family} N={sp.N} R={x_in.shape[0]}: "
+                  + ", ".join(f"{k} {v:.2e}" for k, v in e.items()))
+            assert max(e.values()) <= tol, (i, e)
+    finally:
+        close_all(plans)
+
+
+@pytest.mark.parametrize("lock", [1, 0])
+def test_batch_lockstep_items_against_the_oracle(xc, lock):
+    """Hermite plans (tight windows: lockstep items) and Legendre plans (not),
+    short and long bands, odd and even right-hand-side counts, both
+    directions with lockstep items on and off, against the FP64 oracle's
+    method on the same nodes: relative l2 <= max(10 eps, 1e-5)."""
+    from oracle import families as F
+    from oracle import method as M
+    eps = 1e-7
+    cases = [("hermite", 1500, 7), ("hermite", 600, 32), ("hermite", 3100, 1), ("legendre", 900, 5),
+             ("chebyshev", 700, 4)]
+    plans, specs, xs, ys, xa, X, Yin = [], [], [], [], [], [], []
+    try:
+        for i, (fam, N, R) in enumerate(cases):
+            sp = F.make_spec(fam, N)
+            specs.append(sp)
+            plans.append(xc.Plan(fam, N, eps, precision="fp32", nodes=None if fam == "chebyshev" else sp.x))
+            X.append(inputs.normal(N, R, 40, i))
+            Yin.append(inputs.normal(N, R, 41, i))
+            xs.append(torch.from_numpy(X[-1]).to("cuda", torch.float32))
+            ys.append(torch.empty_like(xs[-1]))
+            xa.append(torch.empty_like(xs[-1]))
+        with xc.Batch(plans) as b:
+            b.bind(xs, ys)
+            # lockstep on or off for both directions (the tuner's switch)
+            b.set_lockstep(lock, lock)
+            assert b.info()["lockstep_plans"] == (3 if lock else 0)
+            b.apply(False)
+            torch.cuda.synchronize()
+            assert b.status() == xc.XC_OK
+            Y = [y.double().cpu().numpy() for y in ys]
+            for y, v in zip(ys, Yin):
+                y.copy_(torch.from_numpy(v).to(torch.float32))
+            b2 = xc.Batch(plans)
+            b2.bind(xa, ys)
+            b2.set_lockstep(lock, lock)
+            b2.apply(True)
+            torch.cuda.synchronize()
+            assert b2.status() == xc.XC_OK
+            XA = [x.double().cpu().numpy() for x in xa]
+            b2.close()
+        for sp, y, xi, xg, yi in zip(specs, Y, X, XA, Yin):
+            ora = M.build(sp, eps, precision="fp32")
+            ef = M.rel_l2(y, M.apply(ora, xi))
+            ea = M.rel_l2(xg, M.apply_adjoint(ora, yi))
+            print(f"lockstep={lock} {sp.family} N={sp.N} R={xi.shape[0]}: fwd {ef:.2e} adj {ea:.2e}")
+            assert ef <= max(10 * eps, 1e-5) and ea <= max(10 * eps, 1e-5)
     finally:
         close_all(plans)
