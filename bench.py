@@ -54,7 +54,10 @@ def parse_args():
     ap.add_argument("--nplans", type=int, default=1000, help="plans of the batch workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
-    ap.add_argument("--no-variant", action="store_true", help="skip the XC_FP64_PAIR line of FP64 workloads")
+    ap.add_argument("--no-variant", action="store_true",
+                    help="skip the precision variant (XC_FP64_PAIR of FP64 workloads, XC_FP64 of FP32 ones)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload only: skip the FP32 configurations and the 1000-plan batch")
     return ap.parse_args()
 
 
@@ -267,27 +270,21 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- cpu oracle
-def time_oracle(wl, sample_rhs, min_seconds, max_reps=1000):
-    """The FP64 oracle (as it stands) on the host: forward + adjoint apply of
-    every plan on `sample_rhs` right-hand sides, repeated for >= min_seconds.
-    Plan construction (the precompute) is not timed."""
-    plans = []
-    for i, (fam, N, params) in enumerate(wl["plans"]):
-        fwd, adj = oracle_apply_pair(fam, N, params, wl["eps"], wl["precision"])
-        plans.append((fwd, adj, inputs.draw(wl["dist"], N, sample_rhs, 90, i)))
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        for fwd, adj, X in plans:
-            adj(fwd(X))
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= min_seconds or reps >= max_reps:
-            break
-    vectors = reps * len(plans) * 2 * sample_rhs
-    return vectors / el, el, reps
+def _ref_step(args):
+    """Worker of the reference arm: one step's share (forward + adjoint of
+    every plan on its own right-hand side), started together by the barrier."""
+    _POOL_STATE["barrier"].wait(timeout=900)
+    t0 = time.perf_counter()
+    for fwd, adj, X in _POOL_STATE["plans"]:
+        adj(fwd(X))
+    return time.perf_counter() - t0
 
 
 def run_reference(args, rank, world):
+    """The FP64 oracle as it stands, timed on the host cores: one
+    single-threaded process per core, each applying forward + adjoint of every
+    plan of the workload to one right-hand side of its own per step; a step
+    ends when every process has finished its share."""
     if rank != 0:
         return
     if args.workload == "batch1000":
@@ -297,32 +294,26 @@ def run_reference(args, rank, world):
               "dist": "normal"}
     else:
         wl = inputs.WORKLOADS[args.workload]
-    plans = []
-    for i, (fam, N, params) in enumerate(wl["plans"]):
-        fwd, adj = oracle_apply_pair(fam, N, params, wl["eps"], wl["precision"])
-        plans.append((fwd, adj, inputs.draw(wl["dist"], N, 1, 91, i)))
-
-    def step():
-        for fwd, adj, X in plans:
-            adj(fwd(X))
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    el = time.perf_counter() - t0
-    vectors = args.steps * len(plans) * 2
+    n = host_cores()
+    with oracle_pool(n, wl["plans"], wl["eps"], wl["precision"], wl["dist"], 1) as pool:
+        for _ in range(args.warmup):
+            pool.map(_ref_step, [None] * n, chunksize=1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_ref_step, [None] * n, chunksize=1)
+        el = time.perf_counter() - t0
+    vectors = args.steps * len(wl["plans"]) * 2 * n
     value = vectors / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": (workload_config(args.workload, wl) if args.workload != "batch1000" else {"workload": "batch1000"})
-        | {"sample": "1 right-hand side per plan and direction per step"
+        | {"sample": f"1 right-hand side per plan, direction and process per step, {n} processes"
            + ("" if args.workload != "batch1000" else "; 4 plans of the batch with N <= 1024")},
-        "cpu_baseline": {"value": value, "unit": "vectors/s", "cores": 1, "kind": "oracle",
-                         "sample": "1 RHS per plan, forward + adjoint, numpy/scipy single-threaded"},
+        "cpu_baseline": {"value": value, "unit": "vectors/s", "cores": n, "kind": "oracle",
+                         "sample": f"1 RHS per plan and process per step, forward + adjoint, {n} single-threaded "
+                                   "numpy/scipy processes"},
         "e2e": {"value": value, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -366,21 +357,180 @@ def traffic_from_profiles(kernel, workload, plan=None):
     return None
 
 
-def measure_pair_variant(xc, torch, wl, specs, dev, steps, warmup, world, mats=None):
-    """The same FP64 workload with XC_FP64_PAIR plans (FP64 vectors and FFTs,
-    band products in FP32 pairs): vector applies per second over `steps`
-    flushed steps, and the relative l2 error against the dense product."""
-    R = wl["nrhs"]
-    plans, X, Y, XA = [], [], [], []
+def sample_rows(N, k=64, seed=0):
+    """Rows of a plan on which forward outputs are checked against the oracle."""
+    g = np.random.default_rng([N, seed])
+    return np.unique(np.concatenate([[0, N // 2, N - 1], g.integers(0, N, k)]))
+
+
+def oracle_spec(fam, N, params, nodes):
+    """The oracle's matrix at exactly the plan's nodes (Chebyshev: its exact
+    Chebyshev-Gauss angles, which the library uses as well)."""
+    from oracle import families as F
+    if fam == "chebyshev":
+        return F.make_spec("chebyshev", N)
+    return F.make_spec(fam, N, params.get("alpha", 0.0), params.get("beta", 0.0), x=nodes)
+
+
+def oracle_accuracy(torch, plans, specs, X, rhs_fwd=16, rhs_adj=4, adj_max_n=16384):
+    """Relative l2 error of each plan's forward apply (sampled rows, the first
+    rhs_fwd right-hand sides) and adjoint apply (every output, rhs_adj seeded
+    right-hand sides, plans up to adj_max_n) against the FP64 oracle's plain
+    dense product at the plan's nodes.  Part of the bench's CPU (oracle) leg."""
+    from oracle import method as M
+    out = []
+    for p, s, x in zip(plans, specs, X):
+        if p.is_complex or s["params"].get("scheme") == "2d":
+            out.append(None)
+            continue
+        sp = oracle_spec(s["family"], s["N"], s["params"], p.nodes())
+        rows = sample_rows(s["N"])
+        xs = x[:rhs_fwd]
+        y = p.apply(xs).double().cpu().numpy()[:, rows]
+        e = {"plan": f"{s['family']} N={s['N']}",
+             "forward": M.rel_l2(y, M.dense_apply(sp, xs.double().cpu().numpy(), rows=rows)),
+             "forward_sample": f"{len(rows)} rows x {xs.shape[0]} RHS"}
+        if s["N"] <= adj_max_n:
+            Yh = inputs.normal(s["N"], rhs_adj, 96, s["index"])
+            ya = p.apply_adjoint(torch.from_numpy(Yh).to(x.device, p.torch_dtype)).double().cpu().numpy()
+            e["adjoint"] = M.rel_l2(ya, M.dense_apply_adjoint(sp, Yh))
+            e["adjoint_sample"] = f"all outputs x {rhs_adj} RHS"
+        out.append(e)
+    return out
+
+
+# ------------------------------------------------------------ CPU (oracle) leg
+_POOL_STATE = {}
+
+
+def _pool_init(barrier, counter, plans_desc, eps, precision, dist, rhs):
+    """Worker start: take a worker index, build the oracle plans of the
+    sample (the precompute, not timed) with inputs of its own, warm them."""
+    with counter.get_lock():
+        w = counter.value
+        counter.value += 1
+    _POOL_STATE["barrier"] = barrier
+    plans = []
+    for i, (fam, N, params) in enumerate(plans_desc):
+        fwd, adj = oracle_apply_pair(fam, N, params, eps, precision)
+        plans.append((fwd, adj, inputs.draw(dist, N, rhs, 90, i, w)))
+    for fwd, adj, X in plans:
+        adj(fwd(X))
+    _POOL_STATE["plans"] = plans
+
+
+def _pool_run(args):
+    """Worker: after every worker has reached the barrier (so each of the n
+    tasks runs on its own worker), forward + adjoint applies of the sample
+    until `seconds` have passed; returns (vectors, seconds)."""
+    seconds, = args
+    _POOL_STATE["barrier"].wait(timeout=900)
+    plans = _POOL_STATE["plans"]
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        for fwd, adj, X in plans:
+            adj(fwd(X))
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return reps * sum(2 * X.shape[0] for _, _, X in plans), el
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_pool(n, plans_desc, eps, precision, dist, rhs):
+    """n single-threaded oracle processes (spawned, so no GPU state is
+    forked), each holding the sample's plans."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(n, initializer=_pool_init,
+                    initargs=(ctx.Barrier(n), ctx.Value("i", 0), plans_desc, eps, precision, dist, rhs))
+
+
+def time_oracle_parallel(plans_desc, eps, precision, dist, rhs, seconds, cores=None):
+    """The FP64 oracle as it stands on every host core: each process applies
+    forward + adjoint of every plan of the sample to `rhs` right-hand sides of
+    its own for `seconds`.  Returns (vectors/s summed over the processes,
+    processes, seconds)."""
+    n = cores or host_cores()
+    with oracle_pool(n, plans_desc, eps, precision, dist, rhs) as pool:
+        res = pool.map(_pool_run, [(seconds,)] * n, chunksize=1)
+    vectors = sum(v for v, _ in res)
+    el = max(e for _, e in res)
+    return vectors / el, n, el
+
+
+# ---------------------------------------------------------------- GPU path
+def measure_gemm_peaks(torch, dev):
+    """Measured FP64 and FP32 (no TF32) pipe rates: cuBLAS DGEMM and SGEMM on
+    4096^3, best of 5 after a warm-up, CUDA events -- the same kind of
+    denominator as the driver's cuBLAS bf16 peak."""
+    out = {}
+    torch.backends.cuda.matmul.allow_tf32 = False
+    n = 4096
+    for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        a = torch.randn(n, n, device=dev, dtype=dt)
+        b = torch.randn(n, n, device=dev, dtype=dt)
+        c = torch.empty(n, n, device=dev, dtype=dt)
+        for _ in range(2):
+            torch.matmul(a, b, out=c)
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+        del a, b, c
+    return out
+
+
+def make_plans(xc, torch, wl, dev, rank, precision=None, eps2=None, seed=1):
+    precision = precision or wl["precision"]
+    plans, specs, X, Y, XA = [], plan_specs(wl), [], [], []
     for s in specs:
-        p = xc.Plan(s["family"], s["N"], wl["eps"], precision="fp64pair",
-                    alpha=s["params"].get("alpha", 0.0), beta=s["params"].get("beta", 0.0))
-        p.reserve(R)
+        if eps2 is None:
+            p = make_xc_plan(xc, s["family"], s["N"], s["params"], wl["eps"], precision)
+        else:
+            p = xc.Plan(s["family"], s["N"], wl["eps"], precision=precision, eps2=eps2,
+                        alpha=s["params"].get("alpha", 0.0), beta=s["params"].get("beta", 0.0))
+        p.reserve(wl["nrhs"])
         plans.append(p)
-        x = torch.from_numpy(inputs.draw(wl["dist"], s["N"], R, 1, s["index"], 0)).to(dev, torch.float64)
+        x = torch.from_numpy(inputs.draw(wl["dist"], s["N"], wl["nrhs"], seed, s["index"], rank)).to(dev, p.torch_dtype)
         X.append(x)
         Y.append(torch.empty_like(x))
         XA.append(torch.empty_like(x))
+    return plans, specs, X, Y, XA
+
+
+def timed_steps(torch, step, steps, stream, flush):
+    """Device ms of `steps` calls of step(), L2 flushed before each, events on
+    the launching stream."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        stops[k].record(stream)
+    stops[-1].synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(starts, stops))
+
+
+def measure_variant(xc, torch, wl, dev, steps, warmup, world, precision, eps2=None, label=None):
+    """The workload's plans built in another precision (same eps; eps2 as
+    given, else that precision's default): vector applies per second over
+    `steps` flushed steps."""
+    R = wl["nrhs"]
+    plans, specs, X, Y, XA = make_plans(xc, torch, wl, dev, 0, precision=precision, eps2=eps2)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
@@ -392,54 +542,103 @@ def measure_pair_variant(xc, torch, wl, specs, dev, steps, warmup, world, mats=N
     for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
-    total = 0.0
-    for _ in range(steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step()
-        b.record(stream)
-        b.synchronize()
-        total += a.elapsed_time(b)
-    total = reduce_max(total, world, dev)
-    out = {"precision": "fp64pair (FP64 vectors, FFTs and tail; band values, spectra and band products in FP32 "
-                        "pairs with TwoProduct/TwoSum accumulation)",
-           "value": job_throughput(2 * R * len(plans), steps, total, world), "unit": "vectors/s",
-           "ms_per_step": total / steps}
-    if mats is not None:
-        errs = []
-        for p, A, x in zip(plans, mats, X):
-            y_d = x @ A.T
-            errs.append(float(torch.linalg.norm(p.apply(x) - y_d) / torch.linalg.norm(y_d)))
-            xa_d = y_d @ A
-            errs.append(float(torch.linalg.norm(p.apply_adjoint(y_d) - xa_d) / torch.linalg.norm(xa_d)))
-        out["method_rel_l2_vs_dense"] = max(errs)
-    for p in plans:
-        p.close()
+    total = reduce_max(timed_steps(torch, step, steps, stream, flush), world, dev)
+    out = {"precision": label or precision, "value": job_throughput(2 * R * len(plans), steps, total, world),
+           "unit": "vectors/s", "ms_per_step": total / steps, "eps2": plans[0].info()["eps2"]}
+    return out, plans, specs
+
+
+def dense_comparators(xc, torch, plans, X, Y, XA, dev, stream, flush, steps, prec, cplx):
+    """The direct dense product the method replaces, per plan y = A x and
+    x = A^T y, on the matrix from xc_dense_matrix: cuBLAS (torch.matmul,
+    TF32 off) in the plan's precision and, for FP32 plans, the library's own
+    tensor-core product (tcgen05, 3xTF32).  Times and the relative l2 gap
+    between the method and each comparator."""
+    torch.backends.cuda.matmul.allow_tf32 = False
+    R = X[0].shape[0]
+    vectors = 2 * R * len(plans)
+    mats = [p.dense_matrix() for p in plans]
+    torch.cuda.synchronize(dev)
+
+    def timed(step):
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize(dev)
+        return timed_steps(torch, step, steps, stream, flush) / steps
+
+    def cublas_step():
+        for A, x, y, xa in zip(mats, X, Y, XA):
+            torch.matmul(x, A.T, out=y)
+            torch.matmul(y, A, out=xa)
+
+    ms = timed(cublas_step)
+    gaps = []
+    for p, A, x in zip(plans, mats, X):
+        y_d = x @ A.T
+        gaps.append(float(torch.linalg.norm(p.apply(x) - y_d) / torch.linalg.norm(y_d)))
+        xa_d = y_d @ A
+        gaps.append(float(torch.linalg.norm(p.apply_adjoint(y_d) - xa_d) / torch.linalg.norm(xa_d)))
+    fp64 = prec in ("fp64", "fp64pair")
+    out = {"cublas": {"library": "cuBLAS via torch.matmul (TF32 off)", "ms_per_step": ms,
+                      "vectors_per_s": vectors / (ms / 1e3),
+                      "dtype": ("c128" if fp64 else "c64") if cplx else ("f64" if fp64 else "f32"),
+                      "method_rel_l2_vs_it": max(gaps)}}
+    if not fp64 and not cplx:
+        dens = [xc.Dense(A) for A in mats]
+        gaps_tc = []
+        for d, p, A, x in zip(dens, plans, mats, X):
+            y_t = d.apply(x)
+            gaps_tc.append(float(torch.linalg.norm(p.apply(x) - y_t) / torch.linalg.norm(y_t)))
+            xa_t = d.apply(y_t, transpose=True)
+            gaps_tc.append(float(torch.linalg.norm(p.apply_adjoint(y_t) - xa_t) / torch.linalg.norm(xa_t)))
+            y_c = x @ A.T
+            gaps_tc.append(float(torch.linalg.norm(y_t - y_c) / torch.linalg.norm(y_c)))   # vs cuBLAS
+        del mats
+
+        def tc_step():
+            for d, x, y, xa in zip(dens, X, Y, XA):
+                d.apply(x, out=y, stream=stream)
+                d.apply(y, transpose=True, out=xa, stream=stream)
+
+        ms_tc = timed(tc_step)
+        # per-launch time of the GEMM kernel alone (the split of the right-hand
+        # sides excluded): the forward product of the first plan
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        gemm_ms = []
+        for _ in range(5):
+            flush.zero_()
+            ev[0].record(stream)
+            dens[0].apply(X[0], out=Y[0], stream=stream)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            gemm_ms.append(ev[0].elapsed_time(ev[1]))
+        assert all(d.status() == xc.XC_OK for d in dens)
+        N0 = plans[0].N
+        out["tensor_core"] = {
+            "library": "own tcgen05 kernel (TMA, TMEM accumulators), 3xTF32 split (FP32 accuracy)",
+            "ms_per_step": ms_tc, "vectors_per_s": vectors / (ms_tc / 1e3), "dtype": "f32 (3xTF32)",
+            "method_rel_l2_vs_it": max(gaps_tc[0::3] + gaps_tc[1::3]),
+            "rel_l2_vs_cublas_sgemm": max(gaps_tc[2::3]),
+            "forward_launch_ms": min(gemm_ms),
+            "forward_tf32_mma_tflops": 3 * 2.0 * N0 * N0 * R / (min(gemm_ms) / 1e3) / 1e12}
+        for d in dens:
+            d.close()
+    else:
+        del mats
+    best = min(v["vectors_per_s"] for v in out.values())
+    out["best_vectors_per_s"] = max(v["vectors_per_s"] for v in out.values())
     return out
 
 
-def run_xc(args, rank, world, local_rank):
-    import torch
-    from paper_2004_11610_gb300 import build
-    build.build()
-    from paper_2004_11610_gb300 import xc
-
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    wl = inputs.WORKLOADS[args.workload]
+def measure_workload(xc, torch, name, dev, rank, world, steps, warmup, opts, wl=None):
+    """One named workload: timed steps, per-kernel roofline, e2e through
+    xc_apply_host, dense comparators, precision variants, and (rank 0 of a
+    single-rank run) the FP64 oracle's accuracy figures.  Returns the bench
+    line's fields."""
+    wl = wl or inputs.WORKLOADS[name]
     prec = wl["precision"]
     R = wl["nrhs"]
-    specs = plan_specs(wl)
-    plans, X, Y, XA = [], [], [], []
-    for s in specs:
-        p = make_xc_plan(xc, s["family"], s["N"], s["params"], wl["eps"], prec)
-        p.reserve(R)
-        plans.append(p)
-        x = torch.from_numpy(inputs.draw(wl["dist"], s["N"], R, 1, s["index"], rank)).to(dev, p.torch_dtype)
-        X.append(x)
-        Y.append(torch.empty_like(x))
-        XA.append(torch.empty_like(x))
+    plans, specs, X, Y, XA = make_plans(xc, torch, wl, dev, rank)
     infos = [p.info() for p in plans]
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
@@ -454,28 +653,19 @@ def run_xc(args, rank, world, local_rank):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    clocks = ClockSampler(local_rank)
-    clocks.start()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     barrier()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     launches0 = xc.xc_launch_count()
-    for k in range(args.steps):
-        flush.zero_()
-        starts[k].record(stream)
-        step()
-        stops[k].record(stream)
+    total_ms = timed_steps(torch, step, steps, stream, flush)
     barrier()
     launches = xc.xc_launch_count() - launches0
-    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
 
     # per-kernel device time, same steps again with every launch bracketed by events
     for p in plans:
         p.timing_enable(True)
         p.timing_read()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.zero_()
         step()
     torch.cuda.synchronize(dev)
@@ -483,45 +673,43 @@ def run_xc(args, rank, world, local_rank):
     for pi, (p, info) in enumerate(zip(plans, infos)):
         timing = p.timing_read()
         work = algorithmic_work(info, R, prec, chunked="fwd_reduce" in timing)
-        for name, (n, ms) in timing.items():
-            for key, table in ((name, per_kernel), ((pi, name), per_pair)):
+        for kname, (n, ms) in timing.items():
+            for key, table in ((kname, per_kernel), ((pi, kname), per_pair)):
                 e = table.setdefault(key, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
                 e["launches"] += n
                 e["ms"] += ms
-                e["flops"] += work[name][0] * n
-                e["bytes"] += work[name][1] * n
+                e["flops"] += work[kname][0] * n
+                e["bytes"] += work[kname][1] * n
         p.timing_enable(False)
-    clock_info = clocks.stop()
 
     max_ms = reduce_max(total_ms, world, dev)
-    vectors_per_step = sum(2 * R for _ in plans)
-    value = job_throughput(vectors_per_step, args.steps, max_ms, world)
-    ms_per_step = max_ms / args.steps
+    vectors_per_step = 2 * R * len(plans)
+    value = job_throughput(vectors_per_step, steps, max_ms, world)
+    ms_per_step = max_ms / steps
 
-    # roofline of the dominant kernel: the (plan, kernel) pair with the largest
-    # summed device time
-    (dom_plan, name), e = max(per_pair.items(), key=lambda kv: kv[1]["ms"])
+    # roofline of the dominant kernel: the (plan, kernel) pair with the largest summed device time
+    (dom_plan, kname), e = max(per_pair.items(), key=lambda kv: kv[1]["ms"])
     avg_ms = e["ms"] / e["launches"]
-    flops_per_launch = e["flops"] / e["launches"]
-    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
-    fp64 = prec in ("fp64", "fp64pair")   # FP64 vectors (the dense comparison runs DGEMM)
-    if prec == "fp64" or name not in ("fwd_sparse", "adj_sparse") and prec == "fp64pair":
-        peak, src = FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz"
+    achieved = e["flops"] / e["launches"] / (avg_ms / 1e3) / 1e12
+    peaks = opts["peaks"]
+    if prec == "fp64" or (prec == "fp64pair" and kname not in ("fwd_sparse", "adj_sparse")):
+        peak = peaks.get("fp64") or FP64_PEAK_TFLOPS
+        src = ("measured: cuBLAS DGEMM 4096^3, best of 5, in this run" if peaks.get("fp64")
+               else "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz")
     elif prec == "fp64pair":
         peak = PAIR_PEAK_TFLOPS
         src = ("derived: 152 SMs x 128 FP32 instr/clk x 2070 MHz / 6 FP32 instructions per algorithmic "
                "flop (one pair multiply-add = 2 flops = 12 instructions)")
     else:
-        peak, src = 152 * 128 * 2 * 2.070e9 / 1e12, "derived: 152 SMs x 128 FP32 FMA/clk x 2 flops x 2070 MHz"
-    roofline = {
-        "kernel": name, "plan": f"{specs[dom_plan]['family']} N={specs[dom_plan]['N']}",
-        "bound": "alu", "achieved": achieved, "unit": "TFLOP/s", "peak": peak, "peak_source": src,
-    }
-    roofline["frac"] = achieved / roofline["peak"]
-    tb = traffic_from_profiles(name, args.workload, dom_plan)
-    roofline["traffic"] = tb
-    roofline["algorithmic_bytes_per_launch"] = e["bytes"] / e["launches"]
-    roofline["avg_launch_ms"] = avg_ms
+        peak = peaks.get("fp32") or 152 * 128 * 2 * 2.070e9 / 1e12
+        src = ("measured: cuBLAS SGEMM (TF32 off) 4096^3, best of 5, in this run" if peaks.get("fp32")
+               else "derived: 152 SMs x 128 FP32 FMA/clk x 2 flops x 2070 MHz")
+    roofline = {"kernel": kname, "plan": f"{specs[dom_plan]['family']} N={specs[dom_plan]['N']}",
+                "bound": "alu", "achieved": achieved, "unit": "TFLOP/s", "peak": peak, "peak_source": src,
+                "frac": achieved / peak, "peak_derived": FP64_PEAK_TFLOPS if prec == "fp64" else None,
+                "traffic": traffic_from_profiles(kname, name, dom_plan),
+                "algorithmic_bytes_per_launch": e["bytes"] / e["launches"], "avg_launch_ms": avg_ms,
+                "nnz_per_row": sum(infos[dom_plan]["nnz"]) / infos[dom_plan]["N"]}
     kernel_table = {k: {"launches": v["launches"], "avg_ms": v["ms"] / v["launches"],
                         "share": v["ms"] / sum(w["ms"] for w in per_kernel.values()),
                         "tflops": v["flops"] / v["ms"] / 1e9 if v["ms"] > 0 else None}
@@ -530,122 +718,85 @@ def run_xc(args, rank, world, local_rank):
     sb = sum(step_bytes(i, R, prec) for i in infos)
     hbm_gbs = sb / (ms_per_step / 1e3) / 1e9
 
-    # end to end through the C ABI with pinned host buffers (copies timed)
-    e2e_steps = max(3, min(args.steps, 50))
-    hx = [torch.from_numpy(inputs.draw(wl["dist"], s["N"], R, 2, s["index"], rank)).to(p.torch_dtype).pin_memory()
-          for s, p in zip(specs, plans)]
-    hy = [torch.empty_like(h).pin_memory() for h in hx]
-    hz = [torch.empty_like(h).pin_memory() for h in hx]
-    import ctypes
-    st = ctypes.c_void_p(stream.cuda_stream)
+    out = {"value": value, "ms_per_step": ms_per_step, "steps": steps, "warmup": warmup,
+           "config": workload_config(name, wl) | {"parallelism": f"replicas x{world}"},
+           "roofline": roofline,
+           "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
+                   "peak_source": hbm_src, "note": "algorithmic bytes of the whole step / step time"},
+           "kernels": kernel_table, "gpu_launches": int(launches),
+           "plans": [{k: i[k] for k in ("L", "nnz", "stored", "m_tail", "zeta", "matrix_bytes")}
+                     | {"nnz_per_row": sum(i["nnz"]) / i["N"],
+                        "nnz_per_row_per_block": [round(v / i["N"], 2) for v in i["nnz"]]} for i in infos]}
 
-    def e2e_step():
-        for p, a, b, c in zip(plans, hx, hy, hz):
-            rc = xc._lib.xc_apply_host(p.handle, 0, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
-                                       R, p.N, st)
-            xc._check(rc, "xc_apply_host")
-            rc = xc._lib.xc_apply_host(p.handle, 1, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(c.data_ptr()),
-                                       R, p.N, st)
-            xc._check(rc, "xc_apply_host")
+    if opts.get("e2e", True):
+        e2e_steps = max(3, min(steps, 50))
+        hx = [torch.from_numpy(inputs.draw(wl["dist"], s["N"], R, 2, s["index"], rank)).to(p.torch_dtype).pin_memory()
+              for s, p in zip(specs, plans)]
+        hy = [torch.empty_like(h).pin_memory() for h in hx]
+        hz = [torch.empty_like(h).pin_memory() for h in hx]
+        import ctypes
+        st = ctypes.c_void_p(stream.cuda_stream)
 
-    for _ in range(2):
-        e2e_step()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    barrier()
-    e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
-    e2e_val = job_throughput(vectors_per_step, e2e_steps, 1e3 * e2e_s, world)
-    eb = 8 if prec in ("fp64", "fp64pair") else 4
-    io_bytes = sum(2 * R * s["N"] * eb * (2 if p.is_complex else 1) for s, p in zip(specs, plans))
+        def e2e_step():
+            for p, a, b, c in zip(plans, hx, hy, hz):
+                xc._check(xc._lib.xc_apply_host(p.handle, 0, ctypes.c_void_p(a.data_ptr()),
+                                                ctypes.c_void_p(b.data_ptr()), R, p.N, st), "xc_apply_host")
+                xc._check(xc._lib.xc_apply_host(p.handle, 1, ctypes.c_void_p(b.data_ptr()),
+                                                ctypes.c_void_p(c.data_ptr()), R, p.N, st), "xc_apply_host")
+
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        barrier()
+        e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
+        eb = 8 if prec in ("fp64", "fp64pair") else 4
+        io_bytes = sum(2 * R * s["N"] * eb * (2 if p.is_complex else 1) for s, p in zip(specs, plans))
+        out["e2e"] = {"value": job_throughput(vectors_per_step, e2e_steps, 1e3 * e2e_s, world), "unit": "vectors/s",
+                      "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
     cplx = any(p.is_complex for p in plans)
-
-    # dense GEMM comparison (cuBLAS through torch) at equal precision
-    dense = None
-    variant = None
-    if not args.no_dense:
-        # FP32 comparator at FP32 accuracy: no TF32 tensor-core rounding
-        torch.backends.cuda.matmul.allow_tf32 = False
-        mats = [p.dense_matrix() for p in plans]
-        torch.cuda.synchronize(dev)
-        errs = []
-        for p, A, x in zip(plans, mats, X):
-            y_m = p.apply(x)
-            y_d = x @ A.T
-            errs.append(float(torch.linalg.norm(y_m - y_d) / torch.linalg.norm(y_d)))
-            xa_m = p.apply_adjoint(y_d)
-            xa_d = y_d @ A
-            errs.append(float(torch.linalg.norm(xa_m - xa_d) / torch.linalg.norm(xa_d)))
-
-        def dense_step():
-            for A, x, y, xa in zip(mats, X, Y, XA):
-                torch.matmul(x, A.T, out=y)
-                torch.matmul(y, A, out=xa)
-
-        for _ in range(3):
-            dense_step()
-        torch.cuda.synchronize(dev)
-        ds = max(3, min(args.steps, 20))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        dms = 0.0
-        for _ in range(ds):
-            flush.zero_()
-            a.record(stream)
-            dense_step()
-            b.record(stream)
-            b.synchronize()
-            dms += a.elapsed_time(b)
-        two_d = any(sp["params"].get("scheme") == "2d" for sp in specs)
-        if prec == "fp64" and not args.no_variant and not cplx and not two_d:
-            variant = measure_pair_variant(xc, torch, wl, specs, dev, max(3, min(args.steps, 50)), 3, world, mats)
-        dense = {"vectors_per_s": vectors_per_step * ds / (dms / 1e3), "ms_per_step": dms / ds,
-                 "library": "cuBLAS via torch.matmul",
-                 "dtype": ("c128" if fp64 else "c64") if cplx else ("f64" if fp64 else "f32"),
-                 "method_rel_l2_vs_dense": max(errs),
-                 "speedup_of_method": (vectors_per_step * ds / (dms / 1e3)) and value / world /
-                 (vectors_per_step * ds / (dms / 1e3))}
-        del mats
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, el, reps = time_oracle(wl, 2, 10.0)
-        cpu = {"value": v, "unit": "vectors/s", "cores": 1, "kind": "oracle",
-               "sample": f"2 RHS per plan, forward + adjoint, {reps} repetitions in {el:.1f} s "
-                         "(numpy/scipy, single-threaded)"}
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp64pair": "f64 (band products in f32 pairs)", "fp32": "f32"}.get(
-                prec, "f32-compensated") + (" complex" if cplx else ""),
-            "data": "synthetic", "config": workload_config(args.workload, wl) | {"parallelism": f"replicas x{world}"},
-            "roofline": roofline,
-            "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
-                    "peak_source": hbm_src, "note": "algorithmic bytes of the whole step / step time"},
-            "kernels": kernel_table,
-            "dense_gemm": dense,
-            "fp64_pair_variant": variant,
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": "vectors/s", "h2d_bytes_per_step": io_bytes,
-                    "d2h_bytes_per_step": io_bytes},
-            "gpu_launches": int(launches),
-            "clocks": clock_info,
-            "plans": [{k: i[k] for k in ("L", "nnz", "stored", "m_tail", "zeta", "matrix_bytes")} for i in infos],
-        }
-        print(json.dumps(line), flush=True)
+    two_d = any(sp["params"].get("scheme") == "2d" for sp in specs)
+    if not opts.get("no_dense"):
+        ds = max(3, min(steps, 20))
+        dense = dense_comparators(xc, torch, plans, X, Y, XA, dev, stream, flush, ds, prec, cplx)
+        dense["speedup_of_method"] = (value / world) / dense["best_vectors_per_s"]
+        out["dense_gemm"] = dense
+    if opts.get("oracle") and rank == 0 and world == 1:
+        out["rel_l2_vs_fp64_oracle"] = oracle_accuracy(torch, plans, specs, X)
     for p in plans:
         p.close()
+    del X, Y, XA
+    torch.cuda.empty_cache()
+    # precision variants of the same plans
+    if not opts.get("no_variant") and not cplx and not two_d:
+        vs = max(3, min(steps, 50))
+        if prec == "fp64":
+            v, vplans, vspecs = measure_variant(xc, torch, wl, dev, vs, 3, world, "fp64pair",
+                                                label="fp64pair (FP64 vectors, FFTs and tail; band values, spectra "
+                                                      "and band products in FP32 pairs, TwoProduct/TwoSum)")
+            out["fp64_pair_variant"] = v
+        elif prec in ("fp32", "fp32c"):
+            # the same compressed matrices (same eps and eps2) applied in FP64
+            v, vplans, vspecs = measure_variant(xc, torch, wl, dev, vs, 3, world, "fp64", eps2=infos[0]["eps2"],
+                                                label="fp64 (same eps and eps2: the same compressed matrices)")
+            v["method_speedup_over_it"] = (value / world) / v["value"]
+            out["fp64_apply"] = v
+        else:
+            vplans = []
+        if opts.get("oracle") and rank == 0 and world == 1 and vplans:
+            Xv = [torch.from_numpy(inputs.draw(wl["dist"], s["N"], 16, 1, s["index"], 0)).to(dev, p.torch_dtype)
+                  for s, p in zip(vspecs, vplans)]
+            key = "fp64_pair_variant" if prec == "fp64" else "fp64_apply"
+            out[key]["rel_l2_vs_fp64_oracle"] = oracle_accuracy(torch, vplans, vspecs, Xv)
+        for p in vplans:
+            p.close()
+        torch.cuda.empty_cache()
+    return out
 
 
-# ---------------------------------------------------------------- batch path
-def run_batch(args, rank, world, local_rank):
-    """1000 plans (N log-uniform in [256, 8192], families uniform over
-    Chebyshev / Legendre / Jacobi(1/2,-1/2) / Hermite, 1..32 right-hand sides),
-    FP32, eps = 1e-7: forward + adjoint as two persistent launches replayed
-    from one CUDA graph."""
+def run_xc(args, rank, world, local_rank):
     import torch
     from paper_2004_11610_gb300 import build
     build.build()
@@ -653,7 +804,63 @@ def run_batch(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    wl = inputs.batch_workload(args.nplans)
+    wl = inputs.WORKLOADS[args.workload]
+    prec = wl["precision"]
+    cplx = any(f in ("exp", "lagspec") for f, _, _ in wl["plans"])
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    peaks = measure_gemm_peaks(torch, dev) if not args.no_dense else {}
+    opts = {"peaks": peaks, "no_dense": args.no_dense, "no_variant": args.no_variant,
+            "oracle": not args.no_cpu_baseline}
+    res = measure_workload(xc, torch, args.workload, dev, rank, world, args.steps, args.warmup, opts)
+    # the other configurations, measured in the same process (shorter runs)
+    extra = {}
+    if not args.no_extra and args.workload == "cheb_lag4096_fp64":
+        sub_steps = max(3, min(args.steps, 20))
+        for name in ("leg_jac16384_fp32c", "legendre32768_fp32"):
+            r = measure_workload(xc, torch, name, dev, rank, world, sub_steps, 3, opts | {"e2e": True})
+            extra[name] = {k: r[k] for k in ("value", "ms_per_step", "roofline", "e2e", "dense_gemm",
+                                             "rel_l2_vs_fp64_oracle", "fp64_apply", "plans") if k in r}
+            extra[name]["unit"] = "vectors/s"
+            extra[name]["config"] = r["config"]
+        b = measure_batch(xc, torch, 1000, dev, rank, world, sub_steps, 3, tune=True)
+        extra["batch1000"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "roofline", "launch_ms", "e2e",
+                                                "config", "plan_create_s", "gpu_launches")}
+    clock_info = clocks.stop()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample_rhs = 2
+        v, cores, el = time_oracle_parallel(wl["plans"], wl["eps"], prec, wl["dist"], sample_rhs, 10.0)
+        cpu = {"value": v, "unit": "vectors/s", "cores": cores, "kind": "oracle",
+               "sample": f"{sample_rhs} RHS per plan and process, forward + adjoint, {cores} single-threaded "
+                         f"processes for {el:.1f} s (numpy/scipy FP64 oracle as it stands)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": res["value"], "unit": "vectors/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp64pair": "f64 (band products in f32 pairs)", "fp32": "f32"}.get(
+                prec, "f32-compensated") + (" complex" if cplx else ""),
+            "data": "synthetic", "config": res["config"],
+            "roofline": res["roofline"], "hbm": res["hbm"], "kernels": res["kernels"],
+            "dense_gemm": res.get("dense_gemm"), "fp64_pair_variant": res.get("fp64_pair_variant"),
+            "fp64_apply": res.get("fp64_apply"), "rel_l2_vs_fp64_oracle": res.get("rel_l2_vs_fp64_oracle"),
+            "measured_peaks_tflops": peaks or None,
+            "cpu_baseline": cpu, "e2e": res.get("e2e"), "gpu_launches": res["gpu_launches"],
+            "clocks": clock_info, "plans": res["plans"], "other_configs": extra or None,
+        }
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- batch path
+def measure_batch(xc, torch, nplans, dev, rank, world, steps, warmup, tune=True):
+    """The many-plan workload (N log-uniform in [256, 8192], families uniform
+    over Chebyshev / Legendre / Jacobi(1/2,-1/2) / Hermite, 1..32 right-hand
+    sides), FP32, eps = 1e-7: forward + adjoint as two persistent launches
+    replayed from one CUDA graph.  Returns the bench line's fields."""
+    wl = inputs.batch_workload(nplans)
     t_create = time.perf_counter()
     plans, xs, ys, xa = [], [], [], []
     for i, (fam, N, params, R) in enumerate(wl):
@@ -668,8 +875,9 @@ def run_batch(args, rank, world, local_rank):
     fwd, adj = xc.Batch(plans), xc.Batch(plans)
     fwd.bind(xs, ys)          # forward: x -> y
     adj.bind(xa, ys)          # adjoint: y -> xa (keeps x)
-    fwd.tune(stream)
-    adj.tune(stream)
+    if tune:
+        fwd.tune(stream)
+        adj.tune(stream)
     infos = [p.info() for p in plans]
     R_tot = sum(x.shape[0] for x in xs)
     vectors_per_step = 2 * R_tot
@@ -679,7 +887,7 @@ def run_batch(args, rank, world, local_rank):
         fwd.apply(False, stream)
         adj.apply(True, stream)
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         step()
     torch.cuda.synchronize(dev)
     graph = torch.cuda.CUDAGraph()
@@ -694,29 +902,20 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     assert fwd.status() == xc.XC_OK and adj.status() == xc.XC_OK
 
-    clocks = ClockSampler(local_rank)
-    clocks.start()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     launches0 = xc.xc_launch_count()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
-    for k in range(args.steps):
-        flush.zero_()
-        starts[k].record(stream)
-        graph.replay()
-        stops[k].record(stream)
+    total_ms = timed_steps(torch, graph.replay, steps, stream, flush)
     torch.cuda.synchronize(dev)
     # graph replays launch the library's kernels without passing through its
     # launch counter: two persistent launches per step
-    launches = 2 * args.steps + (xc.xc_launch_count() - launches0)
-    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
+    launches = 2 * steps + (xc.xc_launch_count() - launches0)
 
     # each direction timed on its own (events around single launches)
     dir_ms = [0.0, 0.0]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    nrep = max(3, min(args.steps, 20))
+    nrep = max(3, min(steps, 20))
     for _ in range(nrep):
         flush.zero_()
         ev[0].record(stream)
@@ -729,21 +928,21 @@ def run_batch(args, rank, world, local_rank):
         ev[3].synchronize()
         dir_ms[0] += ev[0].elapsed_time(ev[1])
         dir_ms[1] += ev[2].elapsed_time(ev[3])
-    clock_info = clocks.stop()
     dir_ms = [d / nrep for d in dir_ms]
     max_ms = reduce_max(total_ms, world, dev)
-    value = job_throughput(vectors_per_step, args.steps, max_ms, world)
-    ms_per_step = max_ms / args.steps
+    value = job_throughput(vectors_per_step, steps, max_ms, world)
+    ms_per_step = max_ms / steps
 
-    # algorithmic bytes of one launch per direction (matrices once, vectors, spectra)
+    # algorithmic bytes of one launch per direction: every plan's stored band
+    # values once, its vectors in and out, its spectra (forward) or chunk
+    # partials (adjoint) written and read once
     eb = 4
     fwd_bytes = adj_bytes = 0
     for info, x in zip(infos, xs):
         R = x.shape[0]
         H = sum(L // 2 + 1 for L in info["L"])
-        chunks_bins = H  # partials ~ bins when each bin slice is one chunk
         fwd_bytes += info["matrix_bytes"] + R * (2 * info["N"] * eb + 2 * H * 2 * eb)
-        adj_bytes += info["adjoint_bytes"] + R * (2 * info["N"] * eb + 2 * chunks_bins * 2 * eb)
+        adj_bytes += info["adjoint_bytes"] + R * (2 * info["N"] * eb + 2 * H * 2 * eb)
     hbm_peak, hbm_src = measured_peaks()
     dom = 0 if dir_ms[0] >= dir_ms[1] else 1
     achieved = (fwd_bytes, adj_bytes)[dom] / (dir_ms[dom] / 1e3) / 1e9
@@ -751,7 +950,11 @@ def run_batch(args, rank, world, local_rank):
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "peak_source": hbm_src,
                 "traffic": traffic_from_profiles("batch_kernel", "batch1000", ("forward", "adjoint")[dom]),
-                "algorithmic_bytes_per_launch": (fwd_bytes, adj_bytes)[dom], "avg_launch_ms": dir_ms[dom]}
+                "algorithmic_bytes_per_launch": (fwd_bytes, adj_bytes)[dom], "avg_launch_ms": dir_ms[dom],
+                "other_direction": {"kernel": ("batch_kernel (forward)", "batch_kernel (adjoint)")[1 - dom],
+                                    "achieved": (fwd_bytes, adj_bytes)[1 - dom] / (dir_ms[1 - dom] / 1e3) / 1e9,
+                                    "avg_launch_ms": dir_ms[1 - dom]}}
+    roofline["other_direction"]["frac"] = roofline["other_direction"]["achieved"] / hbm_peak
 
     # end to end: pinned host inputs copied in, both launches, results copied out
     hx = [x.cpu().pin_memory() for x in xs]
@@ -769,60 +972,65 @@ def run_batch(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
 
     e2e_step()
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_steps = max(3, min(steps, 20))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
     io_in = sum(x.numel() * 4 for x in xs)
-    io_out = 2 * io_in
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import families as F
-        from oracle import method as M
-        sample = [w for w in wl if w[1] <= 1024][:6]
-        oplans = []
-        for j, (fam, N, params, R) in enumerate(sample):
-            sp = F.make_spec(fam, N, params.get("alpha", 0.0), params.get("beta", 0.0))
-            oplans.append((M.build(sp, 1e-7, precision="fp32"), inputs.normal(N, R, 94, j)))
-        reps, t0 = 0, time.perf_counter()
-        while time.perf_counter() - t0 < 10.0:
-            for P, X in oplans:
-                M.apply_adjoint(P, M.apply(P, X))
-            reps += 1
-        el = time.perf_counter() - t0
-        nv = reps * sum(2 * X.shape[0] for _, X in oplans)
-        cpu = {"value": nv / el, "unit": "vectors/s", "cores": 1, "kind": "oracle",
-               "sample": f"{len(oplans)} plans of the batch with N <= 1024 ({sum(X.shape[0] for _, X in oplans)} RHS), "
-                         f"forward + adjoint, {reps} repetitions in {el:.1f} s (FP64 oracle, single-threaded)"}
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch1000", "plans": len(plans), "rhs_total": R_tot, "eps": 1e-7,
-                       "precision": "fp32", "step": "forward + adjoint of every plan, one CUDA-graph replay "
-                       "of two persistent launches", "l2": "flushed before every timed step (256 MiB write)",
-                       "parallelism": f"replicas x{world}",
-                       "tuned_rhs_per_item": [fwd.info()["rhs_per_item"], adj.info()["rhs_per_item_adjoint"]]},
-            "roofline": roofline,
-            "launch_ms": {"forward": dir_ms[0], "adjoint": dir_ms[1]},
-            "cpu_baseline": cpu,
-            "e2e": {"value": vectors_per_step * e2e_steps / e2e_s, "unit": "vectors/s",
-                    "h2d_bytes_per_step": io_in, "d2h_bytes_per_step": io_out},
-            "gpu_launches": int(launches),
-            "clocks": clock_info,
-            "plan_create_s": t_create,
-            "matrix_bytes": sum(i["matrix_bytes"] for i in infos),
-            "adjoint_bytes": sum(i["adjoint_bytes"] for i in infos),
-        }
-        print(json.dumps(line), flush=True)
+    out = {
+        "value": value, "unit": "vectors/s", "ms_per_step": ms_per_step, "roofline": roofline,
+        "launch_ms": {"forward": dir_ms[0], "adjoint": dir_ms[1]},
+        "e2e": {"value": job_throughput(vectors_per_step, e2e_steps, 1e3 * e2e_s, world), "unit": "vectors/s",
+                "h2d_bytes_per_step": io_in, "d2h_bytes_per_step": 2 * io_in},
+        "gpu_launches": int(launches), "plan_create_s": t_create,
+        "config": {"workload": "batch1000", "plans": len(plans), "rhs_total": R_tot, "eps": 1e-7,
+                   "precision": "fp32", "step": "forward + adjoint of every plan, one CUDA-graph replay "
+                   "of two persistent launches", "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world}",
+                   "tuned_rhs_per_item": [fwd.info()["rhs_per_item"], adj.info()["rhs_per_item_adjoint"]]},
+        "matrix_bytes": sum(i["matrix_bytes"] for i in infos),
+        "adjoint_bytes": sum(i["adjoint_bytes"] for i in infos),
+    }
+    del graph
     fwd.close()
     adj.close()
     for p in plans:
         p.close()
+    del xs, ys, xa
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(args, rank, world, local_rank):
+    import torch
+    from paper_2004_11610_gb300 import build
+    build.build()
+    from paper_2004_11610_gb300 import xc
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    b = measure_batch(xc, torch, args.nplans, dev, rank, world, args.steps, args.warmup)
+    clock_info = clocks.stop()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = [w for w in inputs.batch_workload(args.nplans) if w[1] <= 1024][:6]
+        v, cores, el = time_oracle_parallel([(f, N, p) for f, N, p, _ in sample], 1e-7, "fp32", "normal", 2, 10.0)
+        cpu = {"value": v, "unit": "vectors/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(sample)} plans of the batch with N <= 1024, 2 RHS each per process, forward + "
+                         f"adjoint, {cores} single-threaded processes for {el:.1f} s (FP64 oracle)"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": b["value"], "unit": "vectors/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": b["config"],
+            "roofline": b["roofline"], "launch_ms": b["launch_ms"], "cpu_baseline": cpu, "e2e": b["e2e"],
+            "gpu_launches": b["gpu_launches"], "clocks": clock_info, "plan_create_s": b["plan_create_s"],
+            "matrix_bytes": b["matrix_bytes"], "adjoint_bytes": b["adjoint_bytes"],
+        }
+        print(json.dumps(line), flush=True)
 
 
 def main():
