@@ -320,7 +320,8 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU path
-KERNEL_SOURCES = ("xc_items.cuh", "xc_apply.cu", "xc_batch.cu", "xc_fft.cuh", "xc_complex.cu", "xc_2d.cu")
+KERNEL_SOURCES = ("xc_items.cuh", "xc_apply.cu", "xc_batch.cu", "xc_fft.cuh", "xc_complex.cu", "xc_2d.cu",
+                  "xc_lock.cuh", "xc_dense.cu")
 
 
 def kernel_source_hash(files=KERNEL_SOURCES):

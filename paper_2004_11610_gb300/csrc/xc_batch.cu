@@ -17,9 +17,10 @@
 // lockstep items instead (fwd_lock_item / fwd_lock_unit / adj_lock_item): the
 // warp's 32 rows (bins) walk the same bin (row), the forward spectra are
 // written bin-major (bin k of RHS r at k * rp + r, rp = nrhs rounded up to
-// even) into a scratch buffer owned by the batch, so that a spectrum value is
-// one broadcast load for 32 rows instead of a gather per row.  The tuner
-// decides per direction whether such plans use them.
+// 8) into a scratch buffer owned by the batch, and each lane owns a block of
+// RL rows (bins) x 8 right-hand sides, so that every band and spectrum value
+// it loads feeds several multiply-adds.  The tuner decides per direction
+// whether such plans use them.
 // Every CTA of a persistent grid works through A (CTA tasks from a device
 // counter), then its warps take B items one by one from a second counter,
 // then -- after a CTA barrier -- it works through C (CTA tasks or warp items).
@@ -40,6 +41,7 @@
 
 #include <algorithm>
 #include <array>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -51,6 +53,7 @@
 #include "xc_fft.cuh"
 #include "xc_internal.h"
 #include "xc_items.cuh"
+#include "xc_lock.cuh"
 
 namespace xc {
 
@@ -87,7 +90,7 @@ struct BatchPlanDev {
   // lockstep items (lock_f: forward, lock_a: adjoint); their spectra and
   // partial sums live in lscratch (forward: spectra [bin][rp] of every block,
   // then the unit partials; adjoint: the chunk partials)
-  int lock_f, lock_a, rp;
+  int lock_f, lock_a, rp, rl;   // rp: bin-major spectrum row (nrhs rounded up to 8); rl: rows per lane
   void* lscratch;
   const int4* lk_units;
   const int* lk_ubase;
@@ -133,9 +136,64 @@ __device__ __forceinline__ void run_cta_task(const BatchPlanDev& P, int4 tk, cx<
   }
 }
 
+// Lockstep forward items of a plan: RL = P.rl rows per lane (1, 2 or 4;
+// 8 RL right-hand sides per item).
+template <typename T, bool COMP>
+__device__ __noinline__ void run_lock_item(const BatchPlanDev& P, int4 tk, int lane, unsigned char* ring) {
+  const T* rs = static_cast<const T*>(P.rowscale);
+  const T* cs = static_cast<const T*>(P.colscale);
+  const cx<T>* sp = static_cast<const cx<T>*>(P.lscratch);
+  auto go = [&](auto rl) {
+    constexpr int RL = decltype(rl)::value;
+    fwd_lock_item<T, RL, COMP>(P.blocks, P.nblocks, P.N, static_cast<const T*>(P.x), P.ld, static_cast<T*>(P.y), sp,
+                               P.rp, P.nrhs, rs, cs, static_cast<const T*>(P.tail), P.m_tail, tk.z,
+                               int64_t(tk.w) * lock_rhs<RL>(), lane, ring);
+  };
+  if constexpr (!COMP) {
+    if (P.rl == 4) {
+      go(std::integral_constant<int, 4>{});
+      return;
+    }
+  }
+  if (P.rl == 2) go(std::integral_constant<int, 2>{});
+  else go(std::integral_constant<int, 1>{});
+}
+
+template <typename T, bool COMP>
+__device__ __noinline__ void run_lock_unit(const BatchPlanDev& P, int4 tk, int lane, unsigned char* ring) {
+  const cx<T>* sp = static_cast<const cx<T>*>(P.lscratch);
+  cx<T>* part = static_cast<cx<T>*>(P.lscratch) + P.spec_per_rhs * P.rp;
+  auto go = [&](auto rl) {
+    constexpr int RL = decltype(rl)::value;
+    fwd_lock_unit<T, RL, COMP>(P.blocks, sp, P.rp, P.nrhs, part, P.lk_units[tk.z], tk.z,
+                               int64_t(tk.w) * lock_rhs<RL>(), lane, ring);
+  };
+  if constexpr (!COMP) {
+    if (P.rl == 4) {
+      go(std::integral_constant<int, 4>{});
+      return;
+    }
+  }
+  if (P.rl == 2) go(std::integral_constant<int, 2>{});
+  else go(std::integral_constant<int, 1>{});
+}
+
+// Lockstep adjoint items: RL bins per lane, so that the real and imaginary
+// sums of RL bins x 8 RHS stay in registers: 2, and 1 with compensation (4
+// bins per lane in the kernels with 128 registers per thread ran no faster).
+template <int RPW, bool COMP>
+__host__ __device__ constexpr int adj_lock_rl() { return COMP ? 1 : 2; }
+
+template <typename T, bool COMP, int RL>
+__device__ __noinline__ void run_lock_adj(const BatchPlanDev& P, int4 tk, int lane, unsigned char* ring) {
+  adj_lock_item<T, RL, COMP>(P.blocks, P.nblocks, static_cast<const T*>(P.y), P.ld,
+                             static_cast<cx<T>*>(P.lscratch), P.nrhs, static_cast<const T*>(P.rowscale), P.lk_cbase,
+                             P.lk_items[tk.z], int64_t(tk.w) * lock_rhs<RL>(), lane, ring);
+}
+
 // One warp item.
 template <typename T, int RPW, bool COMP>
-__device__ __forceinline__ void run_warp_item(const BatchPlanDev& P, int4 tk, int lane) {
+__device__ __forceinline__ void run_warp_item(const BatchPlanDev& P, int4 tk, int lane, unsigned char* ring) {
   const T* rs = static_cast<const T*>(P.rowscale);
   const T* cs = static_cast<const T*>(P.colscale);
   switch (tk.x) {
@@ -162,20 +220,15 @@ __device__ __forceinline__ void run_warp_item(const BatchPlanDev& P, int4 tk, in
                                   n, r);
       break;
     }
+    // lockstep items exist for FP32 batches only
     case T_FWD_LOCK:
-      fwd_lock_item<T, RPW, COMP>(P.blocks, P.nblocks, P.N, static_cast<const T*>(P.x), P.ld, static_cast<T*>(P.y),
-                                  static_cast<const cx<T>*>(P.lscratch), P.rp, P.nrhs, rs, cs,
-                                  static_cast<const T*>(P.tail), P.m_tail, tk.z, int64_t(tk.w) * RPW, lane);
+      if constexpr (sizeof(T) == 4) run_lock_item<T, COMP>(P, tk, lane, ring);
       break;
     case T_FWD_LUNIT:
-      fwd_lock_unit<T, RPW, COMP>(P.blocks, static_cast<const cx<T>*>(P.lscratch), P.rp, P.nrhs,
-                                  static_cast<cx<T>*>(P.lscratch) + P.spec_per_rhs * P.rp, P.lk_units[tk.z], tk.z,
-                                  int64_t(tk.w) * RPW, lane);
+      if constexpr (sizeof(T) == 4) run_lock_unit<T, COMP>(P, tk, lane, ring);
       break;
     case T_ADJ_LOCK:
-      adj_lock_item<T, RPW, COMP>(P.blocks, P.nblocks, static_cast<const T*>(P.y), P.ld,
-                                  static_cast<cx<T>*>(P.lscratch), P.nrhs, rs, P.lk_cbase, P.lk_items[tk.z],
-                                  int64_t(tk.w) * RPW, lane);
+      if constexpr (sizeof(T) == 4) run_lock_adj<T, COMP, adj_lock_rl<RPW, COMP>()>(P, tk, lane, ring);
       break;
     case T_ADJ_SPARSE:
       adj_sparse_item<T, RPW, COMP>(P.blocks, P.nblocks, static_cast<const T*>(P.y), P.ld, nullptr, 0,
@@ -239,7 +292,7 @@ __device__ void cta_list(const BatchPlanDev* __restrict__ plans, const int4* __r
 template <typename T, int RPW, bool COMP>
 __device__ void warp_list(const BatchPlanDev* __restrict__ plans, const int4* __restrict__ list, int64_t n,
                           unsigned* next, const unsigned* __restrict__ need, unsigned* done, int nplans,
-                          long long wait_limit, unsigned* status) {
+                          long long wait_limit, unsigned* status, unsigned char* ring) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     unsigned t = 0;
@@ -253,7 +306,7 @@ __device__ void warp_list(const BatchPlanDev* __restrict__ plans, const int4* __
       ok = w >= 0 ? wait_for(&done[w], need[w], wait_limit, status) : (*(volatile unsigned*)status == 0u);
     }
     ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (ok) run_warp_item<T, RPW, COMP>(plans[tk.y], tk, lane);
+    if (ok) run_warp_item<T, RPW, COMP>(plans[tk.y], tk, lane, ring);
     const int c = counts_in(tk.x, tk.y, nplans);
     if (c >= 0) {
       __syncwarp();                           // every lane's results are written
@@ -272,7 +325,7 @@ __global__ void __launch_bounds__(kBatchThreads, RPW * sizeof(T) >= 32 ? 2 : 3)
     batch_kernel(const BatchPlanDev* __restrict__ plans, const int4* __restrict__ listA, int64_t nA,
                  const int4* __restrict__ listB, int64_t nB, const int4* __restrict__ listC, int64_t nC,
                  int c_by_warps, unsigned* ctrl, const unsigned* __restrict__ need, unsigned* done, int nplans,
-                 long long wait_limit) {
+                 long long wait_limit, int smem_ring) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   __shared__ unsigned s_task;
@@ -281,10 +334,12 @@ __global__ void __launch_bounds__(kBatchThreads, RPW * sizeof(T) >= 32 ? 2 : 3)
   const int tid = threadIdx.x;
   unsigned* status = &ctrl[C_STATUS];
   cta_list<T>(plans, listA, nA, &ctrl[C_NEXT_A], need, done, nplans, wait_limit, status, s, &s_task, &s_ok);
-  warp_list<T, RPW, COMP>(plans, listB, nB, &ctrl[C_NEXT_B], need, done, nplans, wait_limit, status);
+  // the band phase: each warp's staging ring in the FFT buffer, idle until phase C
+  unsigned char* ring = smem_ring ? smem_raw + (tid >> 5) * kRingBytes : nullptr;
+  warp_list<T, RPW, COMP>(plans, listB, nB, &ctrl[C_NEXT_B], need, done, nplans, wait_limit, status, ring);
   __syncthreads();
   if (c_by_warps)
-    warp_list<T, RPW, COMP>(plans, listC, nC, &ctrl[C_NEXT_C], need, done, nplans, wait_limit, status);
+    warp_list<T, RPW, COMP>(plans, listC, nC, &ctrl[C_NEXT_C], need, done, nplans, wait_limit, status, nullptr);
   else
     cta_list<T>(plans, listC, nC, &ctrl[C_NEXT_C], need, done, nplans, wait_limit, status, s, &s_task, &s_ok);
   __syncthreads();
@@ -322,6 +377,7 @@ struct Batch {
   long long wait_limit = 1LL << 22;   // sleeps of ~256 ns: about a second
   int rpw[2] = {0, 0};           // right-hand sides per band item, per direction (0 = not bound)
   int lock[2] = {1, 1};          // lockstep items for the plans that have them, per direction
+  bool ring = false;             // the kernel's shared memory holds the warps' staging rings
   bool tuned = false;
   std::vector<BatchPlanDev> host;   // device copies of these are in dplans
   std::vector<void*> lscratch;   // per plan: the batch's lockstep scratch (nullptr: none)
@@ -378,11 +434,13 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
           ++need[0][p];
         }
       }
-      const int64_t gf = (R + rpw_f - 1) / rpw_f;
+      // a lockstep item covers 8 RL right-hand sides (RL rows per lane)
+      const int64_t lr = 8 * int64_t(H.rl);
+      const int64_t gf = (R + lr - 1) / lr;
       if (P->fwd_chunked) {
         for (int64_t k = 0; k < P->lk_total_units; ++k)
           for (int64_t g = 0; g < gf; ++g) {
-            L[0][1].push_back({double(P->lk_unit_len[k]) * rpw_f, int4{T_FWD_LUNIT, p, int(k), int(g)}});
+            L[0][1].push_back({double(P->lk_unit_len[k]) * double(lr), int4{T_FWD_LUNIT, p, int(k), int(g)}});
             ++need[0][np + p];
           }
         for (int64_t s0 = 0; s0 < P->nslices; ++s0)
@@ -392,17 +450,19 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
           int64_t w = 0;
           for (size_t i = 0; i < P->blocks.size(); ++i) w += P->hf_len[i][s0];
           for (int64_t g = 0; g < gf; ++g) {
-            L[0][1].push_back({double(w + P->m_tail) * rpw_f, int4{T_FWD_LOCK, p, int(s0), int(g)}});
+            L[0][1].push_back({double(w + P->m_tail) * double(lr), int4{T_FWD_LOCK, p, int(s0), int(g)}});
             ++need[0][np + p];
           }
         }
       }
     }
     if (H.lock_a) {
-      const int64_t ga = (R + rpw_a - 1) / rpw_a;
+      // adjoint lockstep items: RL bins x 8 RHS per lane, 8 RL right-hand sides per item
+      const int64_t la = b->precision == XC_FP32_COMPENSATED ? 8 : 16;
+      const int64_t ga = (R + la - 1) / la;
       for (int64_t i = 0; i < P->lk_total_chunks; ++i)
         for (int64_t g = 0; g < ga; ++g) {
-          L[1][1].push_back({double(P->lk_item_len[i]) * rpw_a, int4{T_ADJ_LOCK, p, int(i), int(g)}});
+          L[1][1].push_back({double(P->lk_item_len[i]) * double(la), int4{T_ADJ_LOCK, p, int(i), int(g)}});
           ++need[1][np + p];
         }
       for (int64_t m = 0; m < P->m_tail; ++m)
@@ -510,7 +570,7 @@ int launch_batch_rpw(Batch* b, int dir, cudaStream_t st) {
   fn<<<unsigned(grid), kBatchThreads, b->smem, st>>>(b->dplans, b->list[dir][0], b->nlist[dir][0], b->list[dir][1],
                                                       b->nlist[dir][1], b->list[dir][2], b->nlist[dir][2],
                                                       dir == 0 ? 1 : 0, b->ctrl, b->need[dir], b->done,
-                                                      int(b->plans.size()), b->wait_limit);
+                                                      int(b->plans.size()), b->wait_limit, b->ring ? 1 : 0);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
 }
@@ -595,6 +655,9 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans) {
     b->max_n = std::max(b->max_n, p->max_n);
   }
   b->smem = size_t(b->max_n) * 2 * (b->precision == XC_FP64 ? 8 : 4);
+  // FP32 batches: room for every warp's staging ring of the lockstep items
+  b->ring = b->precision != XC_FP64;
+  if (b->ring) b->smem = std::max(b->smem, size_t(xc::kBatchWarps) * size_t(xc::kRingBytes));
   b->extra_need.assign(nplans, 0);
   b->lscratch.assign(nplans, nullptr);
   b->lscratch_bytes.assign(nplans, 0);
@@ -657,7 +720,7 @@ int xc_batch_bind(xc_batch_t batch, const void* const* x_dev, void* const* y_dev
     if (b->precision == XC_FP64 || nrhs[i] == 0) continue;
     XC_TRY(xc::ensure_lockstep(p));
     if (!p->lock_f_ok && !p->lock_t_ok) continue;
-    const int64_t rp = (nrhs[i] + 1) / 2 * 2;
+    const int64_t rp = (nrhs[i] + 7) / 8 * 8;
     const int64_t fwd = p->lock_f_ok ? p->spec_per_rhs * rp + p->lk_total_units * 32 * nrhs[i] : 0;
     const int64_t adj = p->lock_t_ok ? p->lk_total_chunks * 32 * nrhs[i] : 0;
     const int64_t bytes = std::max<int64_t>(fwd, adj) * int64_t(sizeof(xc::cx<float>));
@@ -698,7 +761,10 @@ int xc_batch_bind(xc_batch_t batch, const void* const* x_dev, void* const* y_dev
     d.y = y_dev[i];
     d.nrhs = nrhs[i];
     d.ld = ld[i];
-    d.rp = int((nrhs[i] + 1) / 2 * 2);
+    d.rp = int((nrhs[i] + 7) / 8 * 8);
+    // rows per lane: 8 RL right-hand sides per item (FP32 up to 4; two with
+    // compensation, whose accumulators take twice the registers)
+    d.rl = nrhs[i] > 16 && b->precision == XC_FP32 ? 4 : nrhs[i] > 8 ? 2 : 1;
     d.lscratch = b->lscratch[i];
     d.lk_units = p->lk_units;
     d.lk_ubase = p->lk_ubase;

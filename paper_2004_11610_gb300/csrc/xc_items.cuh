@@ -329,144 +329,6 @@ __device__ __forceinline__ void fwd_reduce_row(int64_t N, const T* __restrict__ 
   y[r * ld + n] = acc.value() * (rowscale ? rowscale[n] : T(1));
 }
 
-// ------------------------------------------- lockstep (window) band items
-// The batch's items for plans whose window layouts are tight (see BlockDev):
-// the 32 lanes of a warp walk the same bin (forward) or row (adjoint) of the
-// window, so that the right-hand-side values of that bin or row are the same
-// for every lane -- one broadcast load per value serves the 32 rows (bins)
-// instead of one gather per lane.  Lanes whose band does not reach the bin
-// read a stored zero, which leaves their sums unchanged.
-
-// RPW spectrum values F[q], q < nq (warp-uniform address, bin-major, 16-byte
-// aligned for pairs), into (re, im) accumulators with the lane's value c.
-template <typename T, int RPW, bool COMP>
-__device__ __forceinline__ void lock_step_fwd(const cx<T>& c, const cx<T>* __restrict__ f, int nq,
-                                              Acc<T, COMP> (&acc)[RPW]) {
-  if constexpr (sizeof(T) == 4 && RPW % 2 == 0) {
-#pragma unroll
-    for (int q = 0; q < RPW; q += 2) {
-      if (q < nq) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(f + q));
-        acc[q].add(c.re, t.x);
-        acc[q].add(c.im, t.y);
-        acc[q + 1].add(c.re, t.z);
-        acc[q + 1].add(c.im, t.w);
-      }
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < RPW; ++q) {
-      if (q < nq) {
-        const cx<T> fq = f[q];
-        acc[q].add(c.re, fq.re);
-        acc[q].add(c.im, fq.im);
-      }
-    }
-  }
-}
-
-// Window positions [w0, w1) of forward slice `slice` of block b for the RPW
-// right-hand sides from r0: F points at the block's bin-major spectra.
-template <typename T, int RPW, bool COMP>
-__device__ __forceinline__ void lock_band_fwd(const BlockDev& b, int64_t slice, int lane,
-                                              const cx<T>* __restrict__ F, int rp, int64_t r0, int w0, int w1, int nq,
-                                              Acc<T, COMP> (&acc)[RPW]) {
-  const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.lf_val) + b.lf_off[slice] + lane;
-  const cx<T>* __restrict__ f = F + b.spec_off * rp + int64_t(b.lf_lo[slice]) * rp + r0;
-#pragma unroll 4
-  for (int w = w0; w < w1; ++w) lock_step_fwd<T, RPW, COMP>(val[w * 32], f + int64_t(w) * rp, nq, acc);
-}
-
-// Forward item (row slice, RPW right-hand sides from r_begin) of a plan
-// without chunked bands: every block's window, then the dense tail; writes y.
-// Each row's nonzero terms come in the order of fwd_sparse_item (ascending
-// bins), the stored zeros add nothing, so the sums are those of xc_apply.
-template <typename T, int RPW, bool COMP>
-__device__ void fwd_lock_item(const BlockDev* __restrict__ blocks, int nblocks, int64_t N, const T* __restrict__ x,
-                              int64_t ld, T* __restrict__ y, const cx<T>* __restrict__ spec, int rp, int64_t nrhs,
-                              const T* __restrict__ rowscale, const T* __restrict__ colscale,
-                              const T* __restrict__ tail, int64_t m_tail, int64_t slice, int64_t r_begin, int lane) {
-  const int64_t n = slice * 32 + lane;
-  const int64_t r0 = r_begin;
-  if (r0 >= nrhs) return;
-  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
-  Acc<T, COMP> acc[RPW];
-  for (int i = 0; i < nblocks; ++i) {
-    const BlockDev& b = blocks[i];
-    lock_band_fwd<T, RPW, COMP>(b, slice, lane, spec, rp, r0, 0, b.lf_len[slice], nq, acc);
-  }
-  if (n < N) {
-    for (int64_t m = 0; m < m_tail; ++m) {
-      const T tv = tail[m * N + n];
-      const T cs = colscale ? colscale[m] : T(1);
-#pragma unroll
-      for (int q = 0; q < RPW; ++q)
-        if (q < nq) acc[q].add(tv, x[(r0 + q) * ld + m] * cs);
-    }
-    const T rs = rowscale ? rowscale[n] : T(1);
-#pragma unroll
-    for (int q = 0; q < RPW; ++q)
-      if (q < nq) y[(r0 + q) * ld + n] = acc[q].value() * rs;
-  }
-}
-
-// Forward unit (block, slice, window positions [unit.z, unit.z + unit.w)) of
-// a plan with chunked bands: partial sums to part[u][rhs][lane], as
-// fwd_unit_item.
-template <typename T, int RPW, bool COMP>
-__device__ void fwd_lock_unit(const BlockDev* __restrict__ blocks, const cx<T>* __restrict__ spec, int rp,
-                              int64_t nrhs, cx<T>* __restrict__ part, int4 unit, int64_t u, int64_t r_begin, int lane) {
-  const int64_t r0 = r_begin;
-  if (r0 >= nrhs) return;
-  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
-  Acc<T, COMP> acc[RPW];
-  lock_band_fwd<T, RPW, COMP>(blocks[unit.x], unit.y, lane, spec, rp, r0, unit.z, unit.z + unit.w, nq, acc);
-  cx<T>* out = part + (u * nrhs + r0) * 32 + lane;
-#pragma unroll
-  for (int q = 0; q < RPW; ++q)
-    if (q < nq) out[q * 32] = cx<T>{acc[q].s, acc[q].c};
-}
-
-// Adjoint item (global bin slice it.x, chunk it.y of kAdjChunk window rows):
-// lane = bin; the rows' values of y are broadcast loads.  Partial sums to
-// part[(cbase[it.x] + it.y)][rhs][lane], as adj_sparse_item.
-template <typename T, int RPW, bool COMP>
-__device__ void adj_lock_item(const BlockDev* __restrict__ blocks, int nblocks, const T* __restrict__ y, int64_t ld,
-                              cx<T>* __restrict__ part, int64_t nrhs, const T* __restrict__ rowscale,
-                              const int* __restrict__ cbase, int2 it, int64_t r_begin, int lane) {
-  int i = 0;
-  while (i < nblocks - 1 && it.x >= blocks[i].t_gbase + blocks[i].tslices) ++i;
-  const BlockDev& b = blocks[i];
-  const int gl = it.x - b.t_gbase;
-  const int len = b.lt_len[gl];
-  const int w0 = it.y * kAdjChunk;
-  const int w1 = min(len, w0 + kAdjChunk);
-  const int64_t lo = b.lt_lo[gl];
-  const cx<T>* __restrict__ val = static_cast<const cx<T>*>(b.lt_val) + b.lt_off[gl] + lane;
-  const int64_t r0 = r_begin;
-  if (r0 >= nrhs) return;
-  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
-  Acc<T, COMP> re[RPW], im[RPW];
-#pragma unroll 4
-  for (int w = w0; w < w1; ++w) {
-    const cx<T> c = val[w * 32];
-    const int64_t row = lo + w;
-    const T rs = rowscale ? rowscale[row] : T(1);
-#pragma unroll
-    for (int q = 0; q < RPW; ++q) {
-      if (q < nq) {
-        const T v = __ldg(y + (r0 + q) * ld + row) * rs;
-        re[q].add(c.re, v);
-        im[q].add(c.im, v);
-      }
-    }
-  }
-  cx<T>* out = part + ((cbase[it.x] + it.y) * nrhs + r0) * 32 + lane;
-#pragma unroll
-  for (int q = 0; q < RPW; ++q)
-    if (q < nq) out[q * 32] = cx<T>{re[q].value(), im[q].value()};
-}
-
 // ------------------------------------------------------- adjoint sparse
 // RPW consecutive values from p, which is aligned to RPW * sizeof(T) bytes
 // (vector loads of up to 16 bytes).

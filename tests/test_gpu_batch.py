@@ -261,17 +261,19 @@ def test_batch_matches_the_oracle_on_a_slice_of_the_1000_plan_workload(xc):
         close_all(plans)
 
 
-@pytest.mark.parametrize("lock", [1, 0])
-def test_batch_lockstep_items_against_the_oracle(xc, lock):
+@pytest.mark.parametrize("lock,rpw", [(1, 8), (1, 4), (0, 4)])
+def test_batch_lockstep_items_against_the_oracle(xc, lock, rpw):
     """Hermite plans (tight windows: lockstep items) and Legendre plans (not),
-    short and long bands, odd and even right-hand-side counts, both
-    directions with lockstep items on and off, against the FP64 oracle's
-    method on the same nodes: relative l2 <= max(10 eps, 1e-5)."""
+    short and long bands, 1 to 32 right-hand sides (1, 2 and 4 rows per lane
+    in the lockstep forward items), both directions with lockstep items on
+    and off, in the kernels built for 4 and for 8 right-hand sides per
+    classic item (80 and 128 registers per thread), against the FP64
+    oracle's method on the same nodes: relative l2 <= max(10 eps, 1e-5)."""
     from oracle import families as F
     from oracle import method as M
     eps = 1e-7
-    cases = [("hermite", 1500, 7), ("hermite", 600, 32), ("hermite", 3100, 1), ("legendre", 900, 5),
-             ("chebyshev", 700, 4)]
+    cases = [("hermite", 1500, 7), ("hermite", 600, 32), ("hermite", 3100, 1), ("hermite", 2200, 13),
+             ("hermite", 900, 20), ("legendre", 900, 5), ("chebyshev", 700, 4)]
     plans, specs, xs, ys, xa, X, Yin = [], [], [], [], [], [], []
     try:
         for i, (fam, N, R) in enumerate(cases):
@@ -286,8 +288,8 @@ def test_batch_lockstep_items_against_the_oracle(xc, lock):
         with xc.Batch(plans) as b:
             b.bind(xs, ys)
             # lockstep on or off for both directions (the tuner's switch)
-            b.set_lockstep(lock, lock)
-            assert b.info()["lockstep_plans"] == (3 if lock else 0)
+            b.schedule(rpw, rpw, lock, lock)
+            assert b.info()["lockstep_plans"] == (5 if lock else 0)
             b.apply(False)
             torch.cuda.synchronize()
             assert b.status() == xc.XC_OK
@@ -296,7 +298,7 @@ def test_batch_lockstep_items_against_the_oracle(xc, lock):
                 y.copy_(torch.from_numpy(v).to(torch.float32))
             b2 = xc.Batch(plans)
             b2.bind(xa, ys)
-            b2.set_lockstep(lock, lock)
+            b2.schedule(rpw, rpw, lock, lock)
             b2.apply(True)
             torch.cuda.synchronize()
             assert b2.status() == xc.XC_OK
