@@ -136,6 +136,35 @@ __device__ __forceinline__ void run_cta_task(const BatchPlanDev& P, int4 tk, cx<
   }
 }
 
+// Batch tail item: columns [m0, m0 + kTailCols) of x (those below m_tail)
+// for right-hand side r, x_m = colscale_m sum_n tail[m][n] rowscale_n y_n;
+// the lanes stride over the rows with one sum per column (in the order of
+// adj_tail_warp), then a warp reduction per column.  Eight columns per item
+// keep the batch's list short (one item per column and RHS made the
+// bookkeeping of the adjoint launch cost as much as a third of it).
+constexpr int kTailCols = 8;
+
+template <typename T, bool COMP>
+__device__ void adj_tail_cols(int64_t N, int64_t m_tail, int64_t m0, int64_t r, const T* __restrict__ tail,
+                              const T* __restrict__ y, int64_t ld, T* __restrict__ x, const T* __restrict__ rowscale,
+                              const T* __restrict__ colscale, int lane) {
+  const int nc = int(m_tail - m0 < kTailCols ? m_tail - m0 : kTailCols);
+  Acc<T, COMP> acc[kTailCols];
+  for (int64_t n = lane; n < N; n += 32) {
+    const T yv = y[r * ld + n] * (rowscale ? rowscale[n] : T(1));
+#pragma unroll
+    for (int c = 0; c < kTailCols; ++c)
+      if (c < nc) acc[c].add(tail[(m0 + c) * N + n], yv);
+  }
+#pragma unroll
+  for (int c = 0; c < kTailCols; ++c) {
+    if (c >= nc) break;
+    T v = acc[c].value();
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) x[r * ld + m0 + c] = v * (colscale ? colscale[m0 + c] : T(1));
+  }
+}
+
 // Lockstep forward items of a plan: RL = P.rl rows per lane (1, 2 or 4;
 // 8 RL right-hand sides per item).
 template <typename T, bool COMP>
@@ -235,9 +264,9 @@ __device__ __forceinline__ void run_warp_item(const BatchPlanDev& P, int4 tk, in
                                     static_cast<cx<T>*>(P.scratch), P.nrhs, rs, P.t_cbase, P.t_items[tk.z], kAdjChunk,
                                     int64_t(tk.w) * RPW, lane);
       break;
-    default:  // T_ADJ_TAIL: column tk.z, RHS tk.w
-      adj_tail_warp<T, COMP>(P.N, tk.z, tk.w, static_cast<const T*>(P.tail), static_cast<const T*>(P.y), P.ld,
-                             static_cast<T*>(const_cast<void*>(P.x)), rs, cs, lane);
+    default:  // T_ADJ_TAIL: columns [tk.z, tk.z + kTailCols), RHS tk.w
+      adj_tail_cols<T, COMP>(P.N, P.m_tail, tk.z, tk.w, static_cast<const T*>(P.tail), static_cast<const T*>(P.y),
+                             P.ld, static_cast<T*>(const_cast<void*>(P.x)), rs, cs, lane);
       break;
   }
 }
@@ -288,33 +317,52 @@ __device__ void cta_list(const BatchPlanDev* __restrict__ plans, const int4* __r
   }
 }
 
-// A list worked through by single warps.
+// A list worked through by single warps, one entry per atomic on the list
+// counter.  (Taking four consecutive entries per atomic, with the completions
+// of a plan's entries added at once, made the 1000-plan batch slower: the
+// right-hand-side groups of one band chunk, which sit next to each other in
+// the list, then run one after another on one warp instead of side by side
+// on four, and the list's end balances worse.)
 template <typename T, int RPW, bool COMP>
 __device__ void warp_list(const BatchPlanDev* __restrict__ plans, const int4* __restrict__ list, int64_t n,
                           unsigned* next, const unsigned* __restrict__ need, unsigned* done, int nplans,
                           long long wait_limit, unsigned* status, unsigned char* ring) {
   const int lane = threadIdx.x & 31;
-  for (;;) {
-    unsigned t = 0;
-    if (lane == 0) t = atomicAdd(next, 1u);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    if (int64_t(t) >= n) break;
-    const int4 tk = list[t];
-    int ok = 0;
-    if (lane == 0) {
-      const int w = waits_on(tk.x, tk.y, nplans);
-      ok = w >= 0 ? wait_for(&done[w], need[w], wait_limit, status) : (*(volatile unsigned*)status == 0u);
-    }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (ok) run_warp_item<T, RPW, COMP>(plans[tk.y], tk, lane, ring);
-    const int c = counts_in(tk.x, tk.y, nplans);
-    if (c >= 0) {
+  int pend_c = -1;
+  unsigned pend = 0;
+  auto flush = [&]() {
+    if (pend_c >= 0 && pend > 0) {
       __syncwarp();                           // every lane's results are written
       if (lane == 0) {
         __threadfence();
-        atomicAdd(&done[c], 1u);
+        atomicAdd(&done[pend_c], pend);
       }
     }
+    pend = 0;
+  };
+  for (;;) {
+    unsigned t0 = 0;
+    if (lane == 0) t0 = atomicAdd(next, 1u);
+    t0 = __shfl_sync(0xffffffffu, t0, 0);
+    if (int64_t(t0) >= n) break;
+    {
+      const int64_t t = t0;
+      const int4 tk = list[t];
+      int ok = 0;
+      if (lane == 0) {
+        const int w = waits_on(tk.x, tk.y, nplans);
+        ok = w >= 0 ? wait_for(&done[w], need[w], wait_limit, status) : (*(volatile unsigned*)status == 0u);
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (ok) run_warp_item<T, RPW, COMP>(plans[tk.y], tk, lane, ring);
+      const int c = counts_in(tk.x, tk.y, nplans);
+      if (c != pend_c) {
+        flush();
+        pend_c = c;
+      }
+      if (c >= 0) ++pend;
+    }
+    flush();
   }
 }
 
@@ -465,9 +513,10 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
           L[1][1].push_back({double(P->lk_item_len[i]) * double(la), int4{T_ADJ_LOCK, p, int(i), int(g)}});
           ++need[1][np + p];
         }
-      for (int64_t m = 0; m < P->m_tail; ++m)
+      for (int64_t m = 0; m < P->m_tail; m += kTailCols)
         for (int64_t r = 0; r < R; ++r) {
-          L[1][1].push_back({double(P->N) / 32.0, int4{T_ADJ_TAIL, p, int(m), int(r)}});
+          L[1][1].push_back({double(P->N) / 32.0 * double(std::min<int64_t>(kTailCols, P->m_tail - m)),
+                             int4{T_ADJ_TAIL, p, int(m), int(r)}});
           ++need[1][np + p];
         }
       for (size_t i = 0; i < P->blocks.size(); ++i) {
@@ -510,9 +559,10 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
         L[1][1].push_back({double(P->item_len[i]) * rpw_a, int4{T_ADJ_SPARSE, p, int(i), int(g)}});
         ++need[1][np + p];
       }
-    for (int64_t m = 0; m < P->m_tail; ++m)
+    for (int64_t m = 0; m < P->m_tail; m += kTailCols)
       for (int64_t r = 0; r < R; ++r) {
-        L[1][1].push_back({double(P->N) / 32.0, int4{T_ADJ_TAIL, p, int(m), int(r)}});
+        L[1][1].push_back({double(P->N) / 32.0 * double(std::min<int64_t>(kTailCols, P->m_tail - m)),
+                           int4{T_ADJ_TAIL, p, int(m), int(r)}});
         ++need[1][np + p];
       }
     for (size_t i = 0; i < P->blocks.size(); ++i) {
