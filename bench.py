@@ -631,6 +631,29 @@ def dense_comparators(xc, torch, plans, X, Y, XA, dev, stream, flush, steps, pre
     return out
 
 
+def cufft_ms(torch, lengths, nrhs, dtype, dev, flush, stream, reps=5):
+    """cuFFT (torch.fft.rfft) on nrhs real vectors of each block length, the
+    transforms the forward FFT stage computes: summed over the blocks, best of
+    `reps` with L2 flushed, CUDA events on `stream`."""
+    total = 0.0
+    for L in lengths:
+        x = torch.randn(nrhs, L, dtype=dtype, device=dev)
+        for _ in range(2):
+            torch.fft.rfft(x)
+        best = 1e30
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            torch.fft.rfft(x)
+            b.record(stream)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b))
+        total += best
+        del x
+    return total
+
+
 def measure_workload(xc, torch, name, dev, rank, world, steps, warmup, opts, wl=None):
     """One named workload: timed steps, per-kernel roofline, e2e through
     xc_apply_host, dense comparators, precision variants, and (rank 0 of a
@@ -719,12 +742,26 @@ def measure_workload(xc, torch, name, dev, rank, world, steps, warmup, opts, wl=
     sb = sum(step_bytes(i, R, prec) for i in infos)
     hbm_gbs = sb / (ms_per_step / 1e3) / 1e9
 
+    # the FFT stage against cuFFT, a timed cross-check only: the library's
+    # forward FFT launch (extension, window division, real FFT, half
+    # spectrum out, every block) against torch.fft.rfft of the same lengths
+    fft_cmp = []
+    for pi, (p, info) in enumerate(zip(plans, infos)):
+        ours = per_pair.get((pi, "fwd_fft"))
+        if p.is_complex or info.get("scheme") == SCHEME_2D or not ours or not info["L"]:
+            continue
+        ours_ms = ours["ms"] / ours["launches"]
+        ms = cufft_ms(torch, info["L"], R, torch.float64 if prec in ("fp64", "fp64pair") else torch.float32, dev,
+                      flush, stream)
+        fft_cmp.append({"plan": f"{specs[pi]['family']} N={specs[pi]['N']}", "blocks_L": info["L"],
+                        "own_fwd_fft_ms": ours_ms, "cufft_rfft_ms": ms, "cufft_over_own": ms / ours_ms})
+
     out = {"value": value, "ms_per_step": ms_per_step, "steps": steps, "warmup": warmup,
            "config": workload_config(name, wl) | {"parallelism": f"replicas x{world}"},
            "roofline": roofline,
            "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak,
                    "peak_source": hbm_src, "note": "algorithmic bytes of the whole step / step time"},
-           "kernels": kernel_table, "gpu_launches": int(launches),
+           "kernels": kernel_table, "gpu_launches": int(launches), "fft_vs_cufft": fft_cmp,
            "plans": [{k: i[k] for k in ("L", "nnz", "stored", "m_tail", "zeta", "matrix_bytes")}
                      | {"nnz_per_row": sum(i["nnz"]) / i["N"],
                         "nnz_per_row_per_block": [round(v / i["N"], 2) for v in i["nnz"]]} for i in infos]}
@@ -821,7 +858,8 @@ def run_xc(args, rank, world, local_rank):
         for name in ("leg_jac16384_fp32c", "legendre32768_fp32"):
             r = measure_workload(xc, torch, name, dev, rank, world, sub_steps, 3, opts | {"e2e": True})
             extra[name] = {k: r[k] for k in ("value", "ms_per_step", "roofline", "e2e", "dense_gemm",
-                                             "rel_l2_vs_fp64_oracle", "fp64_apply", "plans") if k in r}
+                                             "rel_l2_vs_fp64_oracle", "fp64_apply", "plans", "fft_vs_cufft")
+                           if k in r}
             extra[name]["unit"] = "vectors/s"
             extra[name]["config"] = r["config"]
         b = measure_batch(xc, torch, 1000, dev, rank, world, sub_steps, 3, tune=True)
@@ -846,6 +884,7 @@ def run_xc(args, rank, world, local_rank):
                 prec, "f32-compensated") + (" complex" if cplx else ""),
             "data": "synthetic", "config": res["config"],
             "roofline": res["roofline"], "hbm": res["hbm"], "kernels": res["kernels"],
+            "fft_vs_cufft": res.get("fft_vs_cufft"),
             "dense_gemm": res.get("dense_gemm"), "fp64_pair_variant": res.get("fp64_pair_variant"),
             "fp64_apply": res.get("fp64_apply"), "rel_l2_vs_fp64_oracle": res.get("rel_l2_vs_fp64_oracle"),
             "measured_peaks_tflops": peaks or None,
