@@ -1028,7 +1028,10 @@ def measure_batch(xc, torch, nplans, dev, rank, world, steps, warmup, tune=True)
                    "precision": "fp32", "step": "forward + adjoint of every plan, one CUDA-graph replay "
                    "of two persistent launches", "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}",
-                   "tuned_rhs_per_item": [fwd.info()["rhs_per_item"], adj.info()["rhs_per_item_adjoint"]]},
+                   "tuned_rhs_per_item": [fwd.info()["rhs_per_item"], adj.info()["rhs_per_item_adjoint"]],
+                   "tuned_lockstep": [fwd.info()["lockstep_forward"], adj.info()["lockstep_adjoint"]],
+                   "tune_ms": {"forward": _tune_table(fwd.info()["tune_ms_forward"]),
+                               "adjoint": _tune_table(adj.info()["tune_ms_adjoint"])}},
         "matrix_bytes": sum(i["matrix_bytes"] for i in infos),
         "adjoint_bytes": sum(i["adjoint_bytes"] for i in infos),
     }
@@ -1040,6 +1043,11 @@ def measure_batch(xc, torch, nplans, dev, rank, world, steps, warmup, tune=True)
     del xs, ys, xa
     torch.cuda.empty_cache()
     return out
+
+
+def _tune_table(ms):
+    """The tuner's summed timings keyed "lockstep<l>_rpw<r>" (tried candidates only)."""
+    return {f"lockstep{k // 4}_rpw{1 << (k % 4)}": round(v, 4) for k, v in enumerate(ms) if v >= 0}
 
 
 def run_batch(args, rank, world, local_rank):

@@ -332,6 +332,9 @@ typedef struct {
   int lockstep_forward;      /* 1: plans with tight windows use lockstep band items forward (tuned) */
   int lockstep_adjoint;      /* the same for the adjoint */
   int lockstep_plans;        /* plans that run lockstep items in at least one direction */
+  /* the tuner's timings (ms, summed over 3 launches) per candidate schedule,
+   * entry 4 * lockstep + log2(right-hand sides per item); -1 where not tried */
+  float tune_ms_forward[8], tune_ms_adjoint[8];
 } xc_batch_stats;
 
 /* Group nplans distinct plans (host array of handles; all of one precision;

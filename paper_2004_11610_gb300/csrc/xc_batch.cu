@@ -209,7 +209,8 @@ __device__ __noinline__ void run_lock_unit(const BatchPlanDev& P, int4 tk, int l
 
 // Lockstep adjoint items: RL bins per lane, so that the real and imaginary
 // sums of RL bins x 8 RHS stay in registers: 2, and 1 with compensation (4
-// bins per lane in the kernels with 128 registers per thread ran no faster).
+// bins x 8 and 2 bins x 16 right-hand sides per lane, in the kernels with
+// 128 registers per thread, ran no faster).
 template <int RPW, bool COMP>
 __host__ __device__ constexpr int adj_lock_rl() { return COMP ? 1 : 2; }
 
@@ -425,6 +426,7 @@ struct Batch {
   long long wait_limit = 1LL << 22;   // sleeps of ~256 ns: about a second
   int rpw[2] = {0, 0};           // right-hand sides per band item, per direction (0 = not bound)
   int lock[2] = {1, 1};          // lockstep items for the plans that have them, per direction
+  float tune_ms[2][8] = {{-1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1, -1, -1}};
   bool ring = false;             // the kernel's shared memory holds the warps' staging rings
   bool tuned = false;
   std::vector<BatchPlanDev> host;   // device copies of these are in dplans
@@ -900,6 +902,8 @@ int xc_batch_tune(xc_batch_t batch, void* stream) {
       ms[0] += f;
       ms[1] += a;
     }
+    const int slot = 4 * lk + (cand == 1 ? 0 : cand == 2 ? 1 : cand == 4 ? 2 : 3);
+    for (int d = 0; d < 2; ++d) b->tune_ms[d][slot] = ms[d];
     for (int d = 0; d < 2; ++d)
       if (ms[d] < best_ms[d]) {
         best_ms[d] = ms[d];
@@ -944,6 +948,10 @@ int xc_batch_info(xc_batch_t batch, xc_batch_stats* out) {
   out->tasks_adjoint = b->entries(1);
   out->lockstep_forward = b->lock[0];
   out->lockstep_adjoint = b->lock[1];
+  for (int k = 0; k < 8; ++k) {
+    out->tune_ms_forward[k] = b->tune_ms[0][k];
+    out->tune_ms_adjoint[k] = b->tune_ms[1][k];
+  }
   for (size_t i = 0; i < b->plans.size(); ++i)
     if (i < b->host.size() && (b->host[i].lock_f || b->host[i].lock_a)) ++out->lockstep_plans;
   out->shared_bytes = int64_t(b->smem);

@@ -97,9 +97,14 @@ __device__ __forceinline__ void lock_band_fwd_ring(const BlockDev& b, int64_t sl
                                                    int w1, unsigned char* ring, Acc<float, COMP> (&acc)[RL][8]) {
   constexpr int NF = RL * 4;   // lanes copying the 8 RL spectrum values (16 bytes each)
   // lane l < 16 copies bytes [16 l, 16 l + 16) of the position's band values,
-  // lane 16 + m the m-th 16 bytes of its spectrum values: one source pointer
-  // and one stride per lane, destination slot + 16 l
-  const bool copier = lane < 16 + NF;
+  // lane 16 + m the m-th 16 bytes of its spectrum values (right-hand sides
+  // r0 + 2m and r0 + 2m + 1): one source pointer and one stride per lane,
+  // destination slot + 16 l.  Spectrum rows hold rp values: the lanes past
+  // them copy nothing (an item of 8 RL right-hand sides can reach past rp,
+  // and past the last bin's row that would read beyond the spectra), and
+  // the slots they leave stale feed only sums of right-hand sides >= rp,
+  // which are never written.
+  const bool copier = lane < 16 || (lane < 16 + NF && r0 + 2 * (lane - 16) < rp);
   const unsigned char* src =
       lane < 16 ? reinterpret_cast<const unsigned char*>(static_cast<const cx<float>*>(b.lf_val) + b.lf_off[slice]) +
                       lane * 16

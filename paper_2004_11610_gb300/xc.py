@@ -59,7 +59,8 @@ class xc_batch_stats(ctypes.Structure):
                 ("rhs_per_item_adjoint", ctypes.c_int), ("tasks_forward", ctypes.c_int64), ("tasks_adjoint", ctypes.c_int64),
                 ("shared_bytes", ctypes.c_int64), ("matrix_bytes", ctypes.c_int64),
                 ("adjoint_bytes", ctypes.c_int64), ("lockstep_forward", ctypes.c_int),
-                ("lockstep_adjoint", ctypes.c_int), ("lockstep_plans", ctypes.c_int)]
+                ("lockstep_adjoint", ctypes.c_int), ("lockstep_plans", ctypes.c_int), ("tune_ms_forward", ctypes.c_float * 8),
+                ("tune_ms_adjoint", ctypes.c_float * 8)]
 
 
 _P = ctypes.c_void_p
@@ -386,7 +387,8 @@ class Batch:
     def info(self) -> dict:
         st = xc_batch_stats()
         _check(_lib.xc_batch_info(self._h, ctypes.byref(st)), "xc_batch_info")
-        return {k: getattr(st, k) for k, _ in xc_batch_stats._fields_}
+        return {k: list(v) if isinstance(v, ctypes.Array) else v
+                for k, v in ((k, getattr(st, k)) for k, _ in xc_batch_stats._fields_)}
 
     def status(self, stream=None) -> int:
         """XC_OK or XC_ERR_TIMEOUT (cleared on read)."""

@@ -63,10 +63,11 @@ def test_dense_tensor_core_product_matches_the_oracle(xc, fam, N, nrhs):
     assert ea <= 4e-6 + rel(sg_a, ref_a)
 
 
-@pytest.mark.parametrize("N,nrhs", [(16384, 256), (32768, 128)])
+@pytest.mark.parametrize("N,nrhs", [(16384, 256), (32768, 128), (8192, 256)])
 def test_dense_tensor_core_product_at_the_benchmark_sizes(xc, N, nrhs):
     """Legendre at N = 16384 with 256 right-hand sides and N = 32768 with 128
-    (the launch shapes the benchmark times), against the oracle's dense
+    (the launch shapes the benchmark times), and N = 8192 with 256 (the
+    profiled case: 1.3 GB on the device), against the oracle's dense
     product on sampled rows (forward) and sampled right-hand sides (transpose,
     on every output)."""
     sp = F.make_spec("legendre", N)
