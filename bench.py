@@ -321,7 +321,7 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- GPU path
 KERNEL_SOURCES = ("xc_items.cuh", "xc_apply.cu", "xc_batch.cu", "xc_fft.cuh", "xc_complex.cu", "xc_2d.cu",
-                  "xc_lock.cuh", "xc_dense.cu")
+                  "xc_lock.cuh", "xc_dense.cu", "xc_tc.cuh", "xc_window.cuh")
 
 
 def kernel_source_hash(files=KERNEL_SOURCES):

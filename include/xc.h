@@ -329,12 +329,14 @@ typedef struct {
   int64_t tasks_forward, tasks_adjoint;
   int64_t shared_bytes;      /* dynamic shared memory of the persistent kernel */
   int64_t matrix_bytes, adjoint_bytes;   /* summed over the plans */
-  int lockstep_forward;      /* 1: plans with tight windows use lockstep band items forward (tuned) */
+  int lockstep_forward;      /* 1: plans with tight windows use lockstep band items forward; 2: tensor
+                                windows where plans have them (tuned) */
   int lockstep_adjoint;      /* the same for the adjoint */
   int lockstep_plans;        /* plans that run lockstep items in at least one direction */
   /* the tuner's timings (ms, summed over 3 launches) per candidate schedule,
    * entry 4 * lockstep + log2(right-hand sides per item); -1 where not tried */
-  float tune_ms_forward[8], tune_ms_adjoint[8];
+  float tune_ms_forward[12], tune_ms_adjoint[12];
+  int tensor_plans;          /* plans whose forward band products run on the tensor cores */
 } xc_batch_stats;
 
 /* Group nplans distinct plans (host array of handles; all of one precision;
@@ -353,15 +355,18 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans);
  * fails the batch is left unbound (xc_batch_apply returns XC_ERR_ARG). */
 int xc_batch_bind(xc_batch_t b, const void* const* x_dev, void* const* y_dev, const int64_t* nrhs, const int64_t* ld);
 /* One persistent launch over all bound plans (adjoint = 0: y = A x for every
- * plan; 1: x = A^T y).  Asynchronous on `stream`; allocates nothing and does
- * not synchronise, so it can be captured in a CUDA graph and replayed.
- * Launches of one batch, and of batches sharing a plan, must not overlap. */
+ * plan; 1: x = A^T y), and, forward, up to three tensor-core launches for
+ * the plans whose band products run on tensor windows (below).
+ * Asynchronous on `stream`; allocates nothing and does not synchronise, so
+ * it can be captured in a CUDA graph and replayed.  Launches of one batch,
+ * and of batches sharing a plan, must not overlap. */
 int xc_batch_apply(xc_batch_t b, int adjoint, void* stream);
 /* Autotuner: times the bound problem with 1, 2, 4 and 8 right-hand sides per
- * band-product task, with and without lockstep items for the plans that have
- * them (forward + adjoint, 3 repetitions each), and keeps the fastest per
- * direction; the choice is cached per batch shape for later binds in the
- * process.  Synchronises `stream`; the bound buffers are restored afterwards.
+ * band-product task, with tensor windows forward (where plans have them),
+ * with lockstep items and with neither (forward + adjoint, 3 repetitions
+ * each), and keeps the fastest per direction; the choice is cached per batch
+ * shape for later binds in the process.  Synchronises `stream`; the bound
+ * buffers are restored afterwards.
  *
  * Lockstep items: a bind of an FP32 batch builds, for plans whose bands
  * line up across the 32 rows of a slice (the union of the rows' bands, and
@@ -370,10 +375,21 @@ int xc_batch_apply(xc_batch_t b, int adjoint, void* stream);
  * walk one bin (row) per step for the whole warp, and their spectra are
  * stored bin-major in scratch owned by the batch.  Plans with long bands sum
  * them in window pieces whose grouping differs from xc_apply's, so those
- * results equal xc_apply's to rounding, not bit for bit. */
+ * results equal xc_apply's to rounding, not bit for bit.
+ *
+ * Tensor windows: a bind of an XC_FP32 batch also builds, for plans whose
+ * bands over groups of 128 rows cost at most 1.5 times their stored bands,
+ * 128-row x 16-bin tiles of the forward band layout; with lockstep 2 the
+ * forward band products of those plans with at most 64 right-hand sides
+ * run as dense 3xTF32 tensor-core products over the tiles (tcgen05, FP32
+ * accuracy, xc_window.cuh), after the persistent launch has made their
+ * spectra.  Their results equal xc_apply's to FP32 rounding. */
 int xc_batch_tune(xc_batch_t b, void* stream);
 /* Set the schedule by hand instead of tuning it: right-hand sides per band
- * item (1, 2, 4 or 8) and lockstep items on (1) or off (0), per direction.
+ * item (1, 2, 4 or 8) and lockstep items on (1) or off (0), per direction;
+ * lockstep_forward = 2 runs the forward band products of the plans with
+ * tensor windows on the tensor cores (lockstep items for the other plans
+ * that have them).
  * Rebuilds the task lists (synchronous); XC_ERR_ARG before a bind. */
 int xc_batch_schedule(xc_batch_t b, int rpw_forward, int rpw_adjoint, int lockstep_forward, int lockstep_adjoint);
 int xc_batch_info(xc_batch_t b, xc_batch_stats* out);

@@ -54,6 +54,7 @@
 #include "xc_internal.h"
 #include "xc_items.cuh"
 #include "xc_lock.cuh"
+#include "xc_window.cuh"
 
 namespace xc {
 
@@ -63,7 +64,7 @@ constexpr int kBatchThreads = 256;
 constexpr int kBatchWarps = kBatchThreads / 32;
 enum TaskKind {
   T_FWD_FFT = 0, T_FWD_SPARSE = 1, T_ADJ_SPARSE = 2, T_ADJ_FFT = 3, T_ADJ_TAIL = 4, T_FWD_UNIT = 5, T_FWD_REDUCE = 6,
-  T_FWD_LOCK = 7, T_FWD_LUNIT = 8, T_ADJ_LOCK = 9
+  T_FWD_LOCK = 7, T_FWD_LUNIT = 8, T_ADJ_LOCK = 9, T_FWD_TAIL = 10
 };
 // control words: next entry of lists A, B, C; finished CTAs; status
 enum { C_NEXT_A = 0, C_NEXT_B = 1, C_NEXT_C = 2, C_FINISHED = 3, C_STATUS = 4, C_WORDS = 8 };
@@ -165,6 +166,30 @@ __device__ void adj_tail_cols(int64_t N, int64_t m_tail, int64_t m0, int64_t r, 
   }
 }
 
+// Forward dense-tail item of a plan whose band products run in the window
+// launches (xc_window.cuh): rows 32 slice + lane, right-hand sides [r0, r0 +
+// RPW); y[r][n] = sum_m tail[m][n] colscale_m x[r][m], unscaled -- the window
+// epilogue adds the band sums and applies the row scale.
+template <typename T, int RPW, bool COMP>
+__device__ void fwd_tail_item(int64_t N, int64_t m_tail, const T* __restrict__ tail, const T* __restrict__ x,
+                              int64_t ld, T* __restrict__ y, const T* __restrict__ colscale, int64_t nrhs,
+                              int64_t slice, int64_t r0, int lane) {
+  const int64_t n = slice * 32 + lane;
+  if (n >= N || r0 >= nrhs) return;
+  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
+  Acc<T, COMP> acc[RPW];
+  for (int64_t m = 0; m < m_tail; ++m) {
+    const T tv = tail[m * N + n];
+    const T cs = colscale ? colscale[m] : T(1);
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+      if (q < nq) acc[q].add(tv, x[(r0 + q) * ld + m] * cs);
+  }
+#pragma unroll
+  for (int q = 0; q < RPW; ++q)
+    if (q < nq) y[(r0 + q) * ld + n] = acc[q].value();
+}
+
 // Lockstep forward items of a plan: RL = P.rl rows per lane (1, 2 or 4;
 // 8 RL right-hand sides per item).
 template <typename T, bool COMP>
@@ -259,6 +284,10 @@ __device__ __forceinline__ void run_warp_item(const BatchPlanDev& P, int4 tk, in
       break;
     case T_ADJ_LOCK:
       if constexpr (sizeof(T) == 4) run_lock_adj<T, COMP, adj_lock_rl<RPW, COMP>()>(P, tk, lane, ring);
+      break;
+    case T_FWD_TAIL:
+      fwd_tail_item<T, RPW, COMP>(P.N, P.m_tail, static_cast<const T*>(P.tail), static_cast<const T*>(P.x), P.ld,
+                                  static_cast<T*>(P.y), cs, P.nrhs, tk.z, int64_t(tk.w) * RPW, lane);
       break;
     case T_ADJ_SPARSE:
       adj_sparse_item<T, RPW, COMP>(P.blocks, P.nblocks, static_cast<const T*>(P.y), P.ld, nullptr, 0,
@@ -426,7 +455,15 @@ struct Batch {
   long long wait_limit = 1LL << 22;   // sleeps of ~256 ns: about a second
   int rpw[2] = {0, 0};           // right-hand sides per band item, per direction (0 = not bound)
   int lock[2] = {1, 1};          // lockstep items for the plans that have them, per direction
-  float tune_ms[2][8] = {{-1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1, -1, -1}};
+  float tune_ms[2][12];           // the tuner's timings, entry 4 * lockstep + log2(rpw); -1: not tried
+  // forward tensor-window launches (xc_window.cuh), one per class of
+  // spectrum row length rp <= 16, 32, 64: the plans' descriptors and the
+  // tasks (plan, row group) of each class
+  WinPlan* dwin = nullptr;
+  std::vector<WinPlan> hwin;
+  int2* wlist[3] = {nullptr, nullptr, nullptr};
+  int64_t nw[3] = {0, 0, 0}, wcap[3] = {0, 0, 0};
+  int tens_plans = 0;
   bool ring = false;             // the kernel's shared memory holds the warps' staging rings
   bool tuned = false;
   std::vector<BatchPlanDev> host;   // device copies of these are in dplans
@@ -460,23 +497,70 @@ namespace {
 
 using Entry = std::pair<double, int4>;   // (cost estimate, entry)
 
+// Whether plan p of the batch runs its forward band product on the tensor
+// cores (xc_window.cuh) when the schedule asks for it: an XC_FP32 plan with
+// tensor windows, lockstep scratch and at most 64 right-hand sides.
+bool tensor_capable(const Batch* b, int p) {
+  const Plan* P = b->plans[p];
+  return b->precision == XC_FP32 && P->tens_ok && b->lscratch[p] != nullptr && b->nrhs[p] > 0 && b->nrhs[p] <= 64;
+}
+
 // Work lists of both directions for the bound right-hand sides, with rpw_f
 // (forward) and rpw_a (adjoint) right-hand sides per band item; lock_f /
 // lock_a: the plans that have lockstep scratch use lockstep items in that
-// direction.  Uploads the plan descriptors with the matching flags.
+// direction, and with lock_f = 2 the plans with tensor windows run their
+// forward band products in the window launches (tasks = row groups, one
+// list per class of spectrum row length).  Uploads the plan descriptors
+// with the matching flags.
 int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
   const int np = int(b->plans.size());
   b->rpw[0] = b->rpw[1] = 0;   // unbound until every list is in place (a failure leaves it so)
   std::vector<Entry> L[2][3];
+  std::vector<std::pair<double, int2>> W[3];
   std::vector<unsigned> need[2] = {std::vector<unsigned>(2 * size_t(np), 0), std::vector<unsigned>(2 * size_t(np), 0)};
+  b->hwin.assign(np, WinPlan{});
+  b->tens_plans = 0;
   for (int p = 0; p < np; ++p) {
     const Plan* P = b->plans[p];
     BatchPlanDev& H = b->host[p];
-    H.lock_f = lock_f && b->lscratch[p] != nullptr && P->lock_f_ok;
+    const bool tens = lock_f == 2 && tensor_capable(b, p);
+    // tensor plans keep the lockstep (bin-major) spectra of their FFTs
+    H.lock_f = tens || (lock_f && b->lscratch[p] != nullptr && P->lock_f_ok);
     H.lock_a = lock_a && b->lscratch[p] != nullptr && P->lock_t_ok;
     const int64_t R = b->nrhs[p];
     if (R == 0) continue;
-    if (H.lock_f) {
+    if (tens) {
+      for (size_t i = 0; i < P->blocks.size(); ++i) {
+        const double c = double(P->blocks[i].n) * std::log2(double(P->blocks[i].n) + 1.0);
+        for (int64_t r = 0; r < R; ++r) {
+          L[0][0].push_back({c, int4{T_FWD_FFT, p, int(i), int(r)}});
+          ++need[0][p];
+        }
+      }
+      // the dense tail's sums go to y first (warp items of the persistent launch)
+      if (P->m_tail > 0)
+        for (int64_t s0 = 0; s0 < P->nslices; ++s0)
+          for (int64_t g = 0; g < (R + rpw_f - 1) / rpw_f; ++g)
+            L[0][1].push_back({double(P->m_tail) * rpw_f, int4{T_FWD_TAIL, p, int(s0), int(g)}});
+      const int cls = H.rp <= 16 ? 0 : H.rp <= 32 ? 1 : 2;
+      for (int64_t g = 0; g < P->tens_groups; ++g) {
+        int tiles = 0;
+        for (size_t i = 0; i < P->blocks.size(); ++i) tiles += P->tw_nkb_h[i][g];
+        W[cls].push_back({double(tiles), int2{p, int(g)}});
+      }
+      WinPlan& w = b->hwin[p];
+      w.blocks = static_cast<const BlockDev*>(P->scratch_desc);
+      w.nblocks = int(P->blocks.size());
+      w.rp = H.rp;
+      w.N = P->N;
+      w.nrhs = R;
+      w.ld = b->ld[p];
+      w.y = static_cast<float*>(b->y[p]);
+      w.spec = static_cast<const cx<float>*>(b->lscratch[p]);
+      w.tail_in_y = P->m_tail > 0 ? 1 : 0;
+      w.rowscale = static_cast<const float*>(P->rowscale);
+      ++b->tens_plans;
+    } else if (H.lock_f) {
       for (size_t i = 0; i < P->blocks.size(); ++i) {
         const double c = double(P->blocks[i].n) * std::log2(double(P->blocks[i].n) + 1.0);
         for (int64_t r = 0; r < R; ++r) {
@@ -527,7 +611,7 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
       }
     }
     if (H.lock_f && H.lock_a) continue;
-    // forward
+    // forward (row-per-lane items)
     if (!H.lock_f) {
     for (size_t i = 0; i < P->blocks.size(); ++i) {
       const double c = double(P->blocks[i].n) * std::log2(double(P->blocks[i].n) + 1.0);
@@ -594,6 +678,29 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
     }
     XC_CUDA(cudaMemcpy(b->need[d], need[d].data(), 2 * size_t(np) * sizeof(unsigned), cudaMemcpyHostToDevice));
   }
+  for (int c = 0; c < 3; ++c) {
+    auto& v = W[c];
+    std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& e) { return a.first > e.first; });
+    std::vector<int2> flat(v.size());
+    for (size_t k = 0; k < v.size(); ++k) flat[k] = v[k].second;
+    if (int64_t(flat.size()) > b->wcap[c] || b->wlist[c] == nullptr) {
+      void* ptr = nullptr;
+      XC_TRY(b->alloc(&ptr, std::max<size_t>(1, flat.size()) * sizeof(int2)));
+      b->wlist[c] = static_cast<int2*>(ptr);
+      b->wcap[c] = int64_t(std::max<size_t>(1, flat.size()));
+    }
+    b->nw[c] = int64_t(flat.size());
+    if (!flat.empty())
+      XC_CUDA(cudaMemcpy(b->wlist[c], flat.data(), flat.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  }
+  if (b->tens_plans > 0) {
+    if (b->dwin == nullptr) {
+      void* ptr = nullptr;
+      XC_TRY(b->alloc(&ptr, size_t(np) * sizeof(WinPlan)));
+      b->dwin = static_cast<WinPlan*>(ptr);
+    }
+    XC_CUDA(cudaMemcpy(b->dwin, b->hwin.data(), size_t(np) * sizeof(WinPlan), cudaMemcpyHostToDevice));
+  }
   XC_CUDA(cudaMemcpy(b->dplans, b->host.data(), size_t(np) * sizeof(BatchPlanDev), cudaMemcpyHostToDevice));
   b->rpw[0] = rpw_f;
   b->rpw[1] = rpw_a;
@@ -637,13 +744,37 @@ int launch_batch_t(Batch* b, int dir, cudaStream_t st) {
   }
 }
 
+template <int NP>
+int launch_window(Batch* b, int cls, cudaStream_t st) {
+  using C = WinCfg<NP>;
+  auto fn = window_fwd_kernel<NP>;
+  XC_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               C::SMEM));
+  int dev = 0, sms = 0;
+  XC_CUDA(cudaGetDevice(&dev));
+  XC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t grid = std::min<int64_t>(sms, b->nw[cls]);
+  count_launch();
+  fn<<<unsigned(grid), kWinThreads, C::SMEM, st>>>(b->dwin, b->wlist[cls], int(b->nw[cls]), &b->ctrl[C_STATUS]);
+  XC_CUDA(cudaGetLastError());
+  return XC_OK;
+}
+
 int launch_batch(Batch* b, int dir, cudaStream_t st) {
-  if (b->entries(dir) == 0) return XC_OK;
-  switch (b->precision) {
-    case XC_FP64: return launch_batch_t<double, false>(b, dir, st);
-    case XC_FP32: return launch_batch_t<float, false>(b, dir, st);
-    default: return launch_batch_t<float, true>(b, dir, st);
+  if (b->entries(dir) > 0) {
+    switch (b->precision) {
+      case XC_FP64: XC_TRY((launch_batch_t<double, false>(b, dir, st))); break;
+      case XC_FP32: XC_TRY((launch_batch_t<float, false>(b, dir, st))); break;
+      default: XC_TRY((launch_batch_t<float, true>(b, dir, st))); break;
+    }
   }
+  // forward band products of the tensor plans, after their FFTs
+  if (dir == 0 && b->tens_plans > 0) {
+    if (b->nw[0] > 0) XC_TRY(launch_window<16>(b, 0, st));
+    if (b->nw[1] > 0) XC_TRY(launch_window<32>(b, 1, st));
+    if (b->nw[2] > 0) XC_TRY(launch_window<64>(b, 2, st));
+  }
+  return XC_OK;
 }
 
 // Tuning cache: batch signature -> chosen (right-hand sides per item, lockstep
@@ -710,6 +841,7 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans) {
   // FP32 batches: room for every warp's staging ring of the lockstep items
   b->ring = b->precision != XC_FP64;
   if (b->ring) b->smem = std::max(b->smem, size_t(xc::kBatchWarps) * size_t(xc::kRingBytes));
+  std::fill(&b->tune_ms[0][0], &b->tune_ms[0][0] + 2 * 12, -1.f);
   b->extra_need.assign(nplans, 0);
   b->lscratch.assign(nplans, nullptr);
   b->lscratch_bytes.assign(nplans, 0);
@@ -771,9 +903,14 @@ int xc_batch_bind(xc_batch_t batch, const void* const* x_dev, void* const* y_dev
     xc::Plan* p = b->plans[i];
     if (b->precision == XC_FP64 || nrhs[i] == 0) continue;
     XC_TRY(xc::ensure_lockstep(p));
-    if (!p->lock_f_ok && !p->lock_t_ok) continue;
+    if (!p->lock_f_ok && !p->lock_t_ok && !p->tens_ok) continue;
     const int64_t rp = (nrhs[i] + 7) / 8 * 8;
-    const int64_t fwd = p->lock_f_ok ? p->spec_per_rhs * rp + p->lk_total_units * 32 * nrhs[i] : 0;
+    // forward: bin-major spectra, the lockstep unit partials, and 16 bins
+    // of zeros past the spectra (a tensor window's last tile may reach 15
+    // bins past its block's spectrum)
+    const int64_t fwd = p->lock_f_ok || p->tens_ok
+                            ? p->spec_per_rhs * rp + p->lk_total_units * 32 * nrhs[i] + xc::kWinBins * rp
+                            : 0;
     const int64_t adj = p->lock_t_ok ? p->lk_total_chunks * 32 * nrhs[i] : 0;
     const int64_t bytes = std::max<int64_t>(fwd, adj) * int64_t(sizeof(xc::cx<float>));
     if (b->lscratch[i] == nullptr || b->lscratch_bytes[i] < bytes) {
@@ -881,9 +1018,13 @@ int xc_batch_tune(xc_batch_t batch, void* stream) {
   int best[2] = {b->rpw[0], b->rpw[1]};
   int best_lock[2] = {b->lock[0], b->lock[1]};
   float best_ms[2] = {1e30f, 1e30f};
-  bool any_lock = false;
-  for (void* ls : b->lscratch) any_lock = any_lock || ls != nullptr;
-  for (int lk = any_lock ? 1 : 0; lk >= 0; --lk)
+  bool any_lock = false, any_tens = false;
+  for (size_t p = 0; p < b->plans.size(); ++p) {
+    any_lock = any_lock || b->lscratch[p] != nullptr;
+    any_tens = any_tens || xc::tensor_capable(b, int(p));
+  }
+  // lockstep 2: tensor windows forward (lockstep items in the adjoint)
+  for (int lk = any_tens ? 2 : any_lock ? 1 : 0; lk >= 0; --lk)
   for (int cand : {1, 2, 4, 8}) {
     XC_TRY(xc::build_tasks(b, cand, cand, lk, lk));
     XC_TRY(xc::launch_batch(b, 0, st));   // warm
@@ -933,7 +1074,8 @@ int xc_batch_schedule(xc_batch_t batch, int rpw_forward, int rpw_adjoint, int lo
   if (b->rpw[0] == 0) return fail(XC_ERR_ARG, "bind the batch's buffers first");
   for (int r : {rpw_forward, rpw_adjoint})
     if (r != 1 && r != 2 && r != 4 && r != 8) return fail(XC_ERR_ARG, "right-hand sides per item: 1, 2, 4 or 8");
-  return xc::build_tasks(b, rpw_forward, rpw_adjoint, lockstep_forward ? 1 : 0, lockstep_adjoint ? 1 : 0);
+  return xc::build_tasks(b, rpw_forward, rpw_adjoint, lockstep_forward == 2 ? 2 : lockstep_forward ? 1 : 0,
+                         lockstep_adjoint ? 1 : 0);
 }
 
 int xc_batch_info(xc_batch_t batch, xc_batch_stats* out) {
@@ -948,10 +1090,11 @@ int xc_batch_info(xc_batch_t batch, xc_batch_stats* out) {
   out->tasks_adjoint = b->entries(1);
   out->lockstep_forward = b->lock[0];
   out->lockstep_adjoint = b->lock[1];
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < 12; ++k) {
     out->tune_ms_forward[k] = b->tune_ms[0][k];
     out->tune_ms_adjoint[k] = b->tune_ms[1][k];
   }
+  out->tensor_plans = b->tens_plans;
   for (size_t i = 0; i < b->plans.size(); ++i)
     if (i < b->host.size() && (b->host[i].lock_f || b->host[i].lock_a)) ++out->lockstep_plans;
   out->shared_bytes = int64_t(b->smem);

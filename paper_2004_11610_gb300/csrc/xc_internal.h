@@ -98,6 +98,17 @@ struct BlockDev {
   const int* lt_len;
   const int64_t* lt_off;
   const void* lt_val;
+  // Tensor windows (FP32 plans, batches; null until ensure_lockstep builds
+  // them): group g of 128 rows covers the bins [tw_lo[g], tw_lo[g] + 16
+  // tw_nkb[g]) in tw_nkb[g] tiles of 128 rows x 16 bins from tile tw_off[g]
+  // of tw_val; a tile is 128 rows of 32 FP32 values (real and imaginary
+  // parts of 16 bins, zero outside the row's stored band), the 16-byte chunk
+  // c of row r stored at chunk c ^ (r & 7) (the 128-byte swizzled K-major
+  // layout of the tensor core's operands; xc_window.cuh).
+  const int* tw_lo;
+  const int* tw_nkb;
+  const int64_t* tw_off;
+  const float* tw_val;
 };
 
 // Rows per chunk of a transposed (bin) slice in the adjoint product: long
@@ -116,6 +127,10 @@ constexpr int kFwdChunk = 256;
 // most this many times the elements of the band layouts (Hermite functions:
 // about 1.05-1.2; Legendre / Jacobi / Chebyshev: 1.5-4).
 constexpr double kLockRatio = 1.25;
+
+// The tensor windows (128 rows) of an FP32 plan are built when they store at
+// most this many times the elements of its band layout.
+constexpr double kTensorRatio = 1.5;
 
 // ---------------------------------------------------------- 2-D block scheme
 // One direction of the 2-D scheme (forward: input side = columns, output side
@@ -227,6 +242,12 @@ struct Plan {
   int64_t lock_f_elems = 0, lock_t_elems = 0;
   bool lock_built = false;
   bool lock_f_ok = false, lock_t_ok = false;   // the windows cost at most kLockRatio x the band layouts
+  // tensor windows (forward, XC_FP32 plans): built when they cost at most
+  // kTensorRatio x the band layout; per block the tiles of each row group
+  bool tens_ok = false;
+  int64_t tens_elems = 0;
+  int64_t tens_groups = 0;
+  std::vector<std::vector<int>> tw_nkb_h;   // [block][group]
   int4* lk_units = nullptr;
   int* lk_ubase = nullptr;
   int64_t lk_total_units = 0;

@@ -2494,6 +2494,41 @@ __global__ void window_copy_kernel(const cx<T>* __restrict__ val, const int* __r
   }
 }
 
+// Tensor-window tiles of one block (forward, FP32 plans; the layout of
+// BlockDev::tw_*): blockIdx.y = row group g; element e = (tile kb, row r,
+// 16-byte chunk c) of the group's tiles, chunk c = bins lo + 16 kb + 2c and
+// + 1 of row 128 g + r (real, imaginary parts), stored at chunk c ^ (r & 7)
+// of the tile row; zero outside the row's stored band and for rows >= N.
+__global__ void tensor_tile_kernel(const cx<float>* __restrict__ fval, const int* __restrict__ fk0,
+                                   const int* __restrict__ fwidth, const int64_t* __restrict__ foff, int64_t N,
+                                   const int* __restrict__ glo, const int* __restrict__ gnkb,
+                                   const int64_t* __restrict__ goff, float* __restrict__ out) {
+  const int g = blockIdx.y;
+  const int64_t total = int64_t(gnkb[g]) * 1024;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int kb = int(e >> 10), r = int(e >> 3) & 127, c = int(e & 7);
+    const int64_t row = int64_t(g) * 128 + r;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row < N) {
+      const int64_t s = row >> 5;
+      const int w = fwidth[s];
+      const int j = glo[g] + 16 * kb + 2 * c - fk0[row];
+      const cx<float>* base = fval + foff[s] + (row & 31);
+      if (j >= 0 && j < w) {
+        const cx<float> a = base[int64_t(j) * 32];
+        v.x = a.re;
+        v.y = a.im;
+      }
+      if (j + 1 >= 0 && j + 1 < w) {
+        const cx<float> a = base[int64_t(j + 1) * 32];
+        v.z = a.re;
+        v.w = a.im;
+      }
+    }
+    reinterpret_cast<float4*>(out + (goff[g] + kb) * 4096 + int64_t(r) * 32)[c ^ (r & 7)] = v;
+  }
+}
+
 namespace {
 
 template <typename T>
@@ -2601,6 +2636,64 @@ int build_lockstep(Plan* p) {
     p->lk_total_chunks = run;
     XC_TRY(upload(p, items, &p->lk_items));
     XC_TRY(upload(p, cbase, &p->lk_cbase));
+  }
+  // tensor windows (forward, XC_FP32 plans): row group g = slices 4g .. 4g+3,
+  // window = the union of their slice windows, rounded up to whole tiles
+  if constexpr (sizeof(T) == 4) {
+    if (p->precision == XC_FP32 && fstored > 0) {
+      const int64_t groups = (p->N + 127) / 128;
+      std::vector<std::vector<int>> glo(nb, std::vector<int>(groups, 0)), gnkb(nb, std::vector<int>(groups, 0));
+      int64_t tiles = 0;
+      for (int i = 0; i < nb; ++i)
+        for (int64_t g = 0; g < groups; ++g) {
+          int lo = INT_MAX, hi = -1;
+          for (int64_t s = 4 * g; s < std::min<int64_t>(4 * g + 4, int64_t(p->hf_len[i].size())); ++s)
+            if (p->hf_len[i][s] > 0) {
+              lo = std::min(lo, p->hf_lo[i][s]);
+              hi = std::max(hi, p->hf_lo[i][s] + p->hf_len[i][s]);
+            }
+          if (hi > lo) {
+            glo[i][g] = lo;
+            gnkb[i][g] = (hi - lo + 15) / 16;
+            tiles += gnkb[i][g];
+          }
+        }
+      const int64_t elems = tiles * 128 * 16;
+      p->tens_ok = double(elems) <= kTensorRatio * double(fstored);
+      p->tens_elems = p->tens_ok ? elems : 0;
+      p->tens_groups = p->tens_ok ? groups : 0;
+      if (p->tens_ok) {
+        p->tw_nkb_h = gnkb;
+        void* val = nullptr;
+        XC_TRY(plan_alloc(p, &val, size_t(std::max<int64_t>(tiles, 1)) * 4096 * sizeof(float)));
+        int64_t t0 = 0;
+        for (int i = 0; i < nb; ++i) {
+          BlockDev& b = p->blocks[i];
+          std::vector<int64_t> goff(groups, 0);
+          int maxk = 0;
+          for (int64_t g = 0; g < groups; ++g) {
+            goff[g] = t0;
+            t0 += gnkb[i][g];
+            maxk = std::max(maxk, gnkb[i][g]);
+          }
+          int *lo_d, *nkb_d;
+          int64_t* off_d;
+          XC_TRY(upload(p, glo[i], &lo_d));
+          XC_TRY(upload(p, gnkb[i], &nkb_d));
+          XC_TRY(upload(p, goff, &off_d));
+          if (maxk > 0) {
+            const dim3 grid(unsigned(std::min<int64_t>((int64_t(maxk) * 1024 + 255) / 256, 4096)), unsigned(groups));
+            tensor_tile_kernel<<<grid, 256>>>(static_cast<const cx<float>*>(b.f_val), b.f_k0, b.f_width, b.f_off,
+                                              p->N, lo_d, nkb_d, off_d, static_cast<float*>(val));
+            XC_CUDA(cudaGetLastError());
+          }
+          b.tw_lo = lo_d;
+          b.tw_nkb = nkb_d;
+          b.tw_off = off_d;
+          b.tw_val = static_cast<const float*>(val);
+        }
+      }
+    }
   }
   XC_CUDA(cudaDeviceSynchronize());
   return XC_OK;

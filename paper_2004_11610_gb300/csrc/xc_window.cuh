@@ -1,0 +1,343 @@
+// Forward band products of FP32 plans with dense windows on the tensor cores
+// (the many-plan batch, xc_batch.cu).
+//
+// Plans whose bands are wide and move slowly from row to row (Hermite
+// functions: over a thousand stored bins per row) store, besides their band
+// layouts, tensor windows: per group of 128 rows and block, the union of the
+// rows' stored bins [lo, lo + 16 nkb), as nkb tiles of 128 rows x 16 bins
+// (BlockDev::tw_*).  Over one window the band product of Algorithm 1 (step
+// 3: y_n = sum_k Re(A_nk conj-folded . F_k)) is a dense contraction,
+//   y[n][r] = sum_k  A[n][2k] F[k][r].re + A[n][2k+1] F[k][r].im,
+// with K = 32 FP32 values per tile (16 bins, real and imaginary parts
+// interleaved) and the spectra F in the bin-major layout of the lockstep
+// items (bin k of RHS r at spec + (spec_off + k) rp + r).  Zeros stored
+// outside a row's band leave its sum unchanged.
+//
+// Precision: 3xTF32 as in the dense comparator (xc_dense.cu): A = A_hi + A_lo
+// and F = F_hi + F_lo split exactly into TF32 numbers, the product summed as
+// A_hi F_hi + A_lo F_hi + A_hi F_lo; each tile's products start a fresh
+// tensor-memory accumulator (the tensor core truncates when it adds), which
+// the epilogue adds to FP32 registers with round-to-nearest additions.  The
+// split is made in shared memory, so the band tiles cross HBM once, as FP32.
+//
+// Kernel: persistent, one CTA per SM, tasks (plan, row group) taken in
+// a fixed order (task blockIdx.x + i gridDim.x), each task the tiles of all
+// blocks of its row group.  448 threads:
+//   warp 0     producer: per tile one bulk copy of the 16 KB band tile and
+//              one of the 16 bins x rp spectrum values (contiguous in the
+//              bin-major layout) into a ring of STAGES stages
+//   warp 1     allocates tensor memory (two accumulator buffers of 2 NP
+//              columns); one thread issues, per K step of 8,
+//              tcgen05.mma kind::tf32 M = 128, N = 2 NP: A_hi x [F_hi; F_lo]
+//              and N = NP: A_lo x F_hi into the same first NP columns
+//   warps 2-9  converters: thread t splits half t / 128 of band row t % 128
+//              of the tile in place (hi) and into the lo tile, and writes
+//              F_hi / F_lo as K-major 128-byte swizzled rows of the
+//              right-hand sides (zero past rp), then releases the stage to
+//              the MMA thread (two converter warps per scheduler: the split
+//              is bound by shared-memory latency, not by its arithmetic)
+//   warps 10-13 epilogue: warp w owns tensor-memory lanes 32 (w % 4) .. + 31
+//              = rows of the group; per tile it loads the 2 NP columns and
+//              adds hi and lo parts to its NP sums; after a task's last tile
+//              it adds the dense tail's sum, which the persistent launch has
+//              left in y (plans with a tail), scales by rowscale_n and
+//              stores y[r][n]
+// Every mbarrier wait is bounded; a wait that runs out sets the batch's
+// status word (XC_ERR_TIMEOUT for xc_batch_status), waits (bounded) for the
+// copies and products in flight, frees the tensor memory and returns.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "xc_internal.h"
+#include "xc_tc.cuh"
+
+namespace xc {
+
+// Rows of a tensor window group (= UMMA M) and bins per tile (16 bins = 32
+// FP32 values = one 128-byte swizzle row).
+constexpr int kWinRows = 128;
+constexpr int kWinBins = 16;
+constexpr int kWinTileFloats = kWinRows * 2 * kWinBins;   // 4096
+
+// One plan of a window launch (device copy per plan of the batch).
+struct WinPlan {
+  const BlockDev* blocks;
+  int nblocks;
+  int rp;                       // spectrum row length (nrhs rounded up to 8), <= NP of the launch
+  int64_t N, nrhs, ld;
+  float* y;                     // [nrhs][ld]; holds the dense tail's sum (unscaled) when tail_in_y
+  const cx<float>* spec;        // bin-major spectra of all blocks
+  int tail_in_y;
+  const float* rowscale;
+};
+
+template <int NP>
+struct WinCfg {
+  static constexpr int A_BYTES = kWinTileFloats * 4;   // 16 KB: band tile (hi in place) and its lo tile
+  static constexpr int BT_BYTES = 2 * NP * 128;        // F_hi rows then F_lo rows, K-major
+  static constexpr int BR_BYTES = kWinBins * NP * 8;   // raw spectra: 16 bins x up to NP complex values
+  static constexpr int STAGE = 2 * A_BYTES + BT_BYTES + BR_BYTES;
+  static constexpr int STAGES = (200 * 1024) / STAGE < 4 ? (200 * 1024) / STAGE : 4;
+  static constexpr int SMEM = STAGES * STAGE + 1024 /* alignment */ + 256 /* barriers */;
+  static constexpr int TMEM_COLS = 4 * NP < 32 ? 32 : 4 * NP;   // two buffers of 2 NP columns
+  static_assert(NP % 16 == 0 && 2 * NP <= 256, "UMMA N for M = 128");
+  static_assert(STAGES >= 2 && STAGE % 1024 == 0, "1024-byte aligned stages, two at least");
+};
+
+constexpr int kWinConvThreads = 256;
+constexpr int kWinThreads = 64 + kWinConvThreads + 128;
+
+template <int NP>
+__global__ void __launch_bounds__(kWinThreads, 1)
+    window_fwd_kernel(const WinPlan* __restrict__ plans, const int2* __restrict__ tasks, int ntasks,
+                      unsigned* status) {
+  using namespace tc;
+  using C = WinCfg<NP>;
+  constexpr int S = C::STAGES;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  // barriers: full[S], conv[S], empty[S], tfull[2], tempty[2]; then the tensor-memory address
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * C::STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 4);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t tile0 = smem_u32(smem);
+  auto a_t = [&](int s) { return tile0 + uint32_t(s * C::STAGE); };                         // band hi (in place)
+  auto a_lo = [&](int s) { return tile0 + uint32_t(s * C::STAGE + C::A_BYTES); };
+  auto b_t = [&](int s) { return tile0 + uint32_t(s * C::STAGE + 2 * C::A_BYTES); };         // F_hi; F_lo
+  auto b_raw = [&](int s) { return tile0 + uint32_t(s * C::STAGE + 2 * C::A_BYTES + C::BT_BYTES); };
+  auto full = [&](int s) { return smem_u32(&bars[s]); };
+  auto conv = [&](int s) { return smem_u32(&bars[S + s]); };
+  auto empty = [&](int s) { return smem_u32(&bars[2 * S + s]); };
+  auto tfull = [&](int b) { return smem_u32(&bars[3 * S + b]); };
+  auto tempty = [&](int b) { return smem_u32(&bars[3 * S + 2 + b]); };
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(conv(s), kWinConvThreads);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull(b), 1);
+      mbar_init(tempty(b), 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), uint32_t(C::TMEM_COLS));
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int* abort = &s_abort;
+  int zero_flag = 0;
+  volatile int* no_abort = &zero_flag;
+  auto give_up = [&]() {
+    s_abort = 1;
+    atomicCAS(status, 0u, 1u);
+  };
+  // tiles of a task: all blocks' tiles of its row group
+  auto task_tiles = [&](const WinPlan& P, int g) {
+    int n = 0;
+    for (int bi = 0; bi < P.nblocks; ++bi) n += P.blocks[bi].tw_nkb[g];
+    return n;
+  };
+
+  if (warp == 0) {
+    // ---------------------------------------------------------- producer
+    if (lane == 0) {
+      int kbi = 0;   // tiles issued by this CTA
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
+        const int2 tk = tasks[t];
+        const WinPlan& P = plans[tk.x];
+        const uint32_t braw_bytes = uint32_t(kWinBins * P.rp * 8);
+        for (int bi = 0; bi < P.nblocks && ok; ++bi) {
+          const BlockDev& b = P.blocks[bi];
+          const int nkb = b.tw_nkb[tk.y];
+          const int64_t lo = b.tw_lo[tk.y];
+          const float* a_src = b.tw_val + b.tw_off[tk.y] * kWinTileFloats;
+          for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kbi % S;
+            if (!mbar_wait(empty(s), (uint32_t(kbi / S) & 1u) ^ 1u, abort)) {
+              if (!*abort) give_up();
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(full(s), uint32_t(C::A_BYTES) + braw_bytes);
+            bulk_load(a_t(s), a_src + int64_t(kb) * kWinTileFloats, uint32_t(C::A_BYTES), full(s));
+            bulk_load(b_raw(s), P.spec + (b.spec_off + lo + int64_t(kb) * kWinBins) * P.rp, braw_bytes, full(s));
+            ++kbi;
+          }
+        }
+      }
+      // copies still in flight land before the CTA leaves
+      for (int k = kbi > S ? kbi - S : 0; k < kbi; ++k)
+        if (!mbar_wait(full(k % S), uint32_t(k / S) & 1u, no_abort) && !*abort) give_up();
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc2 = tf32_idesc(kWinRows, 2 * NP);   // A_hi x [F_hi; F_lo]
+      constexpr uint32_t idesc1 = tf32_idesc(kWinRows, NP);       // A_lo x F_hi
+      int kbi = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
+        const int2 tk = tasks[t];
+        const int nk = task_tiles(plans[tk.x], tk.y);
+        for (int k = 0; k < nk; ++k) {
+          const int s = kbi % S, buf = kbi & 1;
+          if (!mbar_wait(tempty(buf), (uint32_t(kbi >> 1) & 1u) ^ 1u, abort) ||
+              !mbar_wait(conv(s), uint32_t(kbi / S) & 1u, abort)) {
+            if (!*abort) give_up();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem + uint32_t(buf * 2 * NP);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t off = uint32_t(kk * 32);   // K step of 8 FP32 values inside the swizzled row
+            umma_tf32(d, sw128_desc(a_t(s) + off), sw128_desc(b_t(s) + off), idesc2, kk != 0 ? 1u : 0u);
+            umma_tf32(d, sw128_desc(a_lo(s) + off), sw128_desc(b_t(s) + off), idesc1, 1u);
+          }
+          umma_commit(empty(s));
+          umma_commit(tfull(buf));
+          ++kbi;
+        }
+      }
+      // no product may still run when the tensor memory is freed
+      for (int k = kbi > 2 ? kbi - 2 : 0; k < kbi; ++k)
+        if (!mbar_wait(tfull(k & 1), uint32_t(k >> 1) & 1u, no_abort) && !*abort) give_up();
+    }
+  } else if (warp < 2 + kWinConvThreads / 32) {
+    // ---------------------------------------------------------- converters
+    const int ct = threadIdx.x - 64;
+    const int row = ct & 127, half = ct >> 7;   // band row of the tile, chunks [4 half, 4 half + 4)
+    int kbi = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
+      const int2 tk = tasks[t];
+      const WinPlan& P = plans[tk.x];
+      const int nk = task_tiles(P, tk.y);
+      const int rp = P.rp;
+      for (int k = 0; k < nk; ++k) {
+        const int s = kbi % S;
+        if (!mbar_wait(full(s), uint32_t(kbi / S) & 1u, abort)) {
+          if (!*abort) give_up();
+          ok = false;
+          break;
+        }
+        // band row: hi in place, lo to the lo tile (same swizzled positions);
+        // the chunk order rotates with the row so that a warp's accesses
+        // spread over all banks
+        float4* ar = reinterpret_cast<float4*>(smem + (a_t(s) - tile0) + row * 128);
+        float4* lr = reinterpret_cast<float4*>(smem + (a_lo(s) - tile0) + row * 128);
+#pragma unroll
+        for (int c0 = 0; c0 < 4; ++c0) {
+          const int c = (4 * half + c0) ^ (row & 7);
+          const float4 v = ar[c];
+          float4 h, l;
+          split_tf32(v.x, &h.x, &l.x);
+          split_tf32(v.y, &h.y, &l.y);
+          split_tf32(v.z, &h.z, &l.z);
+          split_tf32(v.w, &h.w, &l.w);
+          ar[c] = h;
+          lr[c] = l;
+        }
+        // spectra: K-major rows n of [F_hi; F_lo], chunk c = bins 2c, 2c+1
+        const float2* raw = reinterpret_cast<const float2*>(smem + (b_raw(s) - tile0));
+        unsigned char* bt = smem + (b_t(s) - tile0);
+        for (int i = ct; i < NP * 8; i += kWinConvThreads) {
+          const int n = i >> 3, c = i & 7;
+          float2 f0 = make_float2(0.f, 0.f), f1 = make_float2(0.f, 0.f);
+          if (n < rp) {
+            f0 = raw[(2 * c) * rp + n];
+            f1 = raw[(2 * c + 1) * rp + n];
+          }
+          float4 h, l;
+          split_tf32(f0.x, &h.x, &l.x);
+          split_tf32(f0.y, &h.y, &l.y);
+          split_tf32(f1.x, &h.z, &l.z);
+          split_tf32(f1.y, &h.w, &l.w);
+          const int sw = (c ^ (n & 7)) * 16;
+          *reinterpret_cast<float4*>(bt + n * 128 + sw) = h;
+          *reinterpret_cast<float4*>(bt + (NP + n) * 128 + sw) = l;
+        }
+        fence_async_smem();   // the tensor core reads these tiles through the async proxy
+        mbar_arrive(conv(s));
+        ++kbi;
+      }
+    }
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const int q = warp & 3;   // tensor-memory lanes [32 q, 32 q + 32) = rows of the group (warps 10-13: 2, 3, 0, 1)
+    int kbi = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
+      const int2 tk = tasks[t];
+      const WinPlan& P = plans[tk.x];
+      const int nk = task_tiles(P, tk.y);
+      float acc[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) acc[j] = 0.f;
+      for (int k = 0; k < nk; ++k) {
+        const int buf = kbi & 1;
+        int ready = 0;   // one lane waits, the warp follows (tcgen05.ld is warp-collective)
+        if (lane == 0) {
+          ready = mbar_wait(tfull(buf), uint32_t(kbi >> 1) & 1u, abort) ? 1 : 0;
+          if (!ready && !*abort) give_up();
+        }
+        ready = __shfl_sync(0xffffffffu, ready, 0);
+        if (!ready) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t base = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * 2 * NP);
+#pragma unroll
+        for (int c0 = 0; c0 < NP; c0 += 16) {
+          float vh[16], vl[16];
+          tmem_ld16(base + uint32_t(c0), vh);        // A_hi F_hi + A_lo F_hi
+          tmem_ld16(base + uint32_t(NP + c0), vl);   // A_hi F_lo
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[c0 + j] += vh[j] + vl[j];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty(buf));
+        ++kbi;
+      }
+      if (!ok) break;
+      const int64_t n = int64_t(tk.y) * kWinRows + q * 32 + lane;
+      if (n < P.N) {
+        const int nq = int(P.nrhs < NP ? P.nrhs : NP);
+        float* yn = P.y + n;
+        if (P.tail_in_y) {
+#pragma unroll
+          for (int j = 0; j < NP; ++j)
+            if (j < nq) acc[j] += yn[j * P.ld];
+        }
+        const float rs = P.rowscale ? P.rowscale[n] : 1.f;
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+          if (j < nq) yn[j * P.ld] = acc[j] * rs;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, uint32_t(C::TMEM_COLS));
+  }
+}
+
+}  // namespace xc

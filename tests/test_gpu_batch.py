@@ -265,8 +265,8 @@ def test_batch_matches_the_oracle_on_a_slice_of_the_1000_plan_workload(xc):
 def test_batch_lockstep_items_against_the_oracle(xc, lock, rpw):
     """Hermite plans (tight windows: lockstep items) and Legendre plans (not),
     short and long bands, 1 to 40 right-hand sides (1, 2 and 4 rows per lane
-    in the lockstep forward items, 8 and 16 right-hand sides per lane in the
-    adjoint ones, a ragged second group of 32), both directions with lockstep items on
+    in the lockstep forward items, a ragged second group of 32 right-hand
+    sides), both directions with lockstep items on
     and off, in the kernels built for 4 and for 8 right-hand sides per
     classic item (80 and 128 registers per thread), against the FP64
     oracle's method on the same nodes: relative l2 <= max(10 eps, 1e-5)."""
@@ -311,5 +311,56 @@ def test_batch_lockstep_items_against_the_oracle(xc, lock, rpw):
             ea = M.rel_l2(xg, M.apply_adjoint(ora, yi))
             print(f"lockstep={lock} {sp.family} N={sp.N} R={xi.shape[0]}: fwd {ef:.2e} adj {ea:.2e}")
             assert ef <= max(10 * eps, 1e-5) and ea <= max(10 * eps, 1e-5)
+    finally:
+        close_all(plans)
+
+
+@pytest.mark.parametrize("rpw", [4, 8])
+def test_batch_tensor_windows_against_the_oracle(xc, rpw):
+    """Forward band products on the tensor cores (schedule lockstep 2):
+    Hermite plans with ragged row groups (N not a multiple of 128), 1 to 64
+    right-hand sides (the three launch classes rp <= 16, 32, 64, with rp
+    above nrhs), against the FP64 oracle's method on the same nodes
+    (relative l2 <= max(10 eps, 1e-5)) and against the batch's lockstep
+    items on the same inputs (FP32 rounding); a Legendre plan in the same
+    batch keeps its row-per-lane items."""
+    from oracle import families as F
+    from oracle import method as M
+    eps = 1e-7
+    cases = [("hermite", 300, 1), ("hermite", 1000, 9), ("hermite", 2500, 16), ("hermite", 777, 17),
+             ("hermite", 4100, 24), ("hermite", 1300, 33), ("hermite", 2000, 64), ("legendre", 900, 5)]
+    plans, specs, xs, ys, X = [], [], [], [], []
+    try:
+        for i, (fam, N, R) in enumerate(cases):
+            sp = F.make_spec(fam, N)
+            specs.append(sp)
+            plans.append(xc.Plan(fam, N, eps, precision="fp32", nodes=sp.x))
+            X.append(inputs.normal(N, R, 42, i))
+            xs.append(torch.from_numpy(X[-1]).to("cuda", torch.float32))
+            ys.append(torch.empty_like(xs[-1]))
+        with xc.Batch(plans) as b:
+            b.bind(xs, ys)
+            b.schedule(rpw, rpw, 1, 1)
+            b.apply(False)
+            torch.cuda.synchronize()
+            assert b.status() == xc.XC_OK
+            Y_lock = [y.double().cpu().numpy() for y in ys]
+            b.schedule(rpw, rpw, 2, 1)
+            info = b.info()
+            print(f"tensor plans {info['tensor_plans']} of {len(cases)}, lockstep plans {info['lockstep_plans']}")
+            assert info["tensor_plans"] >= 5 and info["lockstep_forward"] == 2
+            for y in ys:
+                y.fill_(float("nan"))
+            b.apply(False)
+            torch.cuda.synchronize()
+            assert b.status() == xc.XC_OK
+            Y = [y.double().cpu().numpy() for y in ys]
+        for sp, y, yl, xi in zip(specs, Y, Y_lock, X):
+            ora = M.build(sp, eps, precision="fp32")
+            ef = M.rel_l2(y, M.apply(ora, xi))
+            el = M.rel_l2(y, yl)
+            print(f"tensor windows {sp.family} N={sp.N} R={xi.shape[0]}: vs oracle {ef:.2e}, vs lockstep {el:.2e}")
+            assert np.isfinite(y).all()
+            assert ef <= max(10 * eps, 1e-5) and el <= 2e-6
     finally:
         close_all(plans)
