@@ -64,7 +64,7 @@ constexpr int kBatchThreads = 256;
 constexpr int kBatchWarps = kBatchThreads / 32;
 enum TaskKind {
   T_FWD_FFT = 0, T_FWD_SPARSE = 1, T_ADJ_SPARSE = 2, T_ADJ_FFT = 3, T_ADJ_TAIL = 4, T_FWD_UNIT = 5, T_FWD_REDUCE = 6,
-  T_FWD_LOCK = 7, T_FWD_LUNIT = 8, T_ADJ_LOCK = 9, T_FWD_TAIL = 10
+  T_FWD_LOCK = 7, T_FWD_LUNIT = 8, T_ADJ_LOCK = 9
 };
 // control words: next entry of lists A, B, C; finished CTAs; status
 enum { C_NEXT_A = 0, C_NEXT_B = 1, C_NEXT_C = 2, C_FINISHED = 3, C_STATUS = 4, C_WORDS = 8 };
@@ -166,28 +166,40 @@ __device__ void adj_tail_cols(int64_t N, int64_t m_tail, int64_t m0, int64_t r, 
   }
 }
 
-// Forward dense-tail item of a plan whose band products run in the window
-// launches (xc_window.cuh): rows 32 slice + lane, right-hand sides [r0, r0 +
-// RPW); y[r][n] = sum_m tail[m][n] colscale_m x[r][m], unscaled -- the window
-// epilogue adds the band sums and applies the row scale.
-template <typename T, int RPW, bool COMP>
-__device__ void fwd_tail_item(int64_t N, int64_t m_tail, const T* __restrict__ tail, const T* __restrict__ x,
-                              int64_t ld, T* __restrict__ y, const T* __restrict__ colscale, int64_t nrhs,
-                              int64_t slice, int64_t r0, int lane) {
-  const int64_t n = slice * 32 + lane;
-  if (n >= N || r0 >= nrhs) return;
-  const int nq = int(nrhs - r0 < RPW ? nrhs - r0 : RPW);
-  Acc<T, COMP> acc[RPW];
-  for (int64_t m = 0; m < m_tail; ++m) {
-    const T tv = tail[m * N + n];
-    const T cs = colscale ? colscale[m] : T(1);
+// Forward dense tails of the plans whose band products run in the window
+// launches (xc_window.cuh): one warp per entry (plan, row slice), lane = row
+// 32 slice + lane, all right-hand sides in groups of 8; y[r][n] = sum_m
+// tail[m][n] colscale_m x[r][m], unscaled -- the window epilogue adds the
+// band sums and applies the row scale.  A launch of its own: as an item of
+// the persistent kernel it cost that kernel's 80-register instantiations a
+// quarter of their speed.
+__global__ void __launch_bounds__(256) fwd_tail_kernel(const BatchPlanDev* __restrict__ plans,
+                                                       const int2* __restrict__ entries, int64_t n) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t e = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; e < n;
+       e += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    const int2 en = entries[e];
+    const BatchPlanDev& P = plans[en.x];
+    const int64_t row = int64_t(en.y) * 32 + lane;
+    if (row >= P.N) continue;
+    const float* tail = static_cast<const float*>(P.tail);
+    const float* x = static_cast<const float*>(P.x);
+    const float* cs = static_cast<const float*>(P.colscale);
+    float* y = static_cast<float*>(P.y);
+    for (int64_t r0 = 0; r0 < P.nrhs; r0 += 8) {
+      const int nq = int(P.nrhs - r0 < 8 ? P.nrhs - r0 : 8);
+      float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int64_t m = 0; m < P.m_tail; ++m) {
+        const float tv = tail[m * P.N + row] * (cs ? cs[m] : 1.f);
 #pragma unroll
-    for (int q = 0; q < RPW; ++q)
-      if (q < nq) acc[q].add(tv, x[(r0 + q) * ld + m] * cs);
+        for (int q = 0; q < 8; ++q)
+          if (q < nq) acc[q] = fmaf(tv, x[(r0 + q) * P.ld + m], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < nq) y[(r0 + q) * P.ld + row] = acc[q];
+    }
   }
-#pragma unroll
-  for (int q = 0; q < RPW; ++q)
-    if (q < nq) y[(r0 + q) * ld + n] = acc[q].value();
 }
 
 // Lockstep forward items of a plan: RL = P.rl rows per lane (1, 2 or 4;
@@ -284,10 +296,6 @@ __device__ __forceinline__ void run_warp_item(const BatchPlanDev& P, int4 tk, in
       break;
     case T_ADJ_LOCK:
       if constexpr (sizeof(T) == 4) run_lock_adj<T, COMP, adj_lock_rl<RPW, COMP>()>(P, tk, lane, ring);
-      break;
-    case T_FWD_TAIL:
-      fwd_tail_item<T, RPW, COMP>(P.N, P.m_tail, static_cast<const T*>(P.tail), static_cast<const T*>(P.x), P.ld,
-                                  static_cast<T*>(P.y), cs, P.nrhs, tk.z, int64_t(tk.w) * RPW, lane);
       break;
     case T_ADJ_SPARSE:
       adj_sparse_item<T, RPW, COMP>(P.blocks, P.nblocks, static_cast<const T*>(P.y), P.ld, nullptr, 0,
@@ -463,6 +471,8 @@ struct Batch {
   std::vector<WinPlan> hwin;
   int2* wlist[3] = {nullptr, nullptr, nullptr};
   int64_t nw[3] = {0, 0, 0}, wcap[3] = {0, 0, 0};
+  int2* tlist = nullptr;         // (plan, row slice) entries of fwd_tail_kernel
+  int64_t ntail = 0, tcap = 0;
   int tens_plans = 0;
   bool ring = false;             // the kernel's shared memory holds the warps' staging rings
   bool tuned = false;
@@ -517,6 +527,7 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
   b->rpw[0] = b->rpw[1] = 0;   // unbound until every list is in place (a failure leaves it so)
   std::vector<Entry> L[2][3];
   std::vector<std::pair<double, int2>> W[3];
+  std::vector<int2> tails;
   std::vector<unsigned> need[2] = {std::vector<unsigned>(2 * size_t(np), 0), std::vector<unsigned>(2 * size_t(np), 0)};
   b->hwin.assign(np, WinPlan{});
   b->tens_plans = 0;
@@ -537,11 +548,9 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
           ++need[0][p];
         }
       }
-      // the dense tail's sums go to y first (warp items of the persistent launch)
+      // the dense tail's sums go to y first (fwd_tail_kernel)
       if (P->m_tail > 0)
-        for (int64_t s0 = 0; s0 < P->nslices; ++s0)
-          for (int64_t g = 0; g < (R + rpw_f - 1) / rpw_f; ++g)
-            L[0][1].push_back({double(P->m_tail) * rpw_f, int4{T_FWD_TAIL, p, int(s0), int(g)}});
+        for (int64_t s0 = 0; s0 < P->nslices; ++s0) tails.push_back(int2{p, int(s0)});
       const int cls = H.rp <= 16 ? 0 : H.rp <= 32 ? 1 : 2;
       for (int64_t g = 0; g < P->tens_groups; ++g) {
         int tiles = 0;
@@ -549,7 +558,7 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
         W[cls].push_back({double(tiles), int2{p, int(g)}});
       }
       WinPlan& w = b->hwin[p];
-      w.blocks = static_cast<const BlockDev*>(P->scratch_desc);
+      w.blocks = P->win_blocks;
       w.nblocks = int(P->blocks.size());
       w.rp = H.rp;
       w.N = P->N;
@@ -693,6 +702,15 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
     if (!flat.empty())
       XC_CUDA(cudaMemcpy(b->wlist[c], flat.data(), flat.size() * sizeof(int2), cudaMemcpyHostToDevice));
   }
+  if (int64_t(tails.size()) > b->tcap || b->tlist == nullptr) {
+    void* ptr = nullptr;
+    XC_TRY(b->alloc(&ptr, std::max<size_t>(1, tails.size()) * sizeof(int2)));
+    b->tlist = static_cast<int2*>(ptr);
+    b->tcap = int64_t(std::max<size_t>(1, tails.size()));
+  }
+  b->ntail = int64_t(tails.size());
+  if (!tails.empty())
+    XC_CUDA(cudaMemcpy(b->tlist, tails.data(), tails.size() * sizeof(int2), cudaMemcpyHostToDevice));
   if (b->tens_plans > 0) {
     if (b->dwin == nullptr) {
       void* ptr = nullptr;
@@ -748,14 +766,15 @@ template <int NP>
 int launch_window(Batch* b, int cls, cudaStream_t st) {
   using C = WinCfg<NP>;
   auto fn = window_fwd_kernel<NP>;
-  XC_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               C::SMEM));
+  // one CTA per SM: each allocates all of the SM's tensor memory
+  const int smem = std::max(C::SMEM, 116 * 1024);
+  XC_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int dev = 0, sms = 0;
   XC_CUDA(cudaGetDevice(&dev));
   XC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t grid = std::min<int64_t>(sms, b->nw[cls]);
   count_launch();
-  fn<<<unsigned(grid), kWinThreads, C::SMEM, st>>>(b->dwin, b->wlist[cls], int(b->nw[cls]), &b->ctrl[C_STATUS]);
+  fn<<<unsigned(grid), kWinThreads, smem, st>>>(b->dwin, b->wlist[cls], int(b->nw[cls]), &b->ctrl[C_STATUS]);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
 }
@@ -768,8 +787,15 @@ int launch_batch(Batch* b, int dir, cudaStream_t st) {
       default: XC_TRY((launch_batch_t<float, true>(b, dir, st))); break;
     }
   }
-  // forward band products of the tensor plans, after their FFTs
+  // forward band products of the tensor plans, after their FFTs (and their
+  // dense tails, which the window epilogue adds)
   if (dir == 0 && b->tens_plans > 0) {
+    if (b->ntail > 0) {
+      count_launch();
+      fwd_tail_kernel<<<unsigned(std::min<int64_t>((b->ntail + 7) / 8, 4096)), 256, 0, st>>>(b->dplans, b->tlist,
+                                                                                          b->ntail);
+      XC_CUDA(cudaGetLastError());
+    }
     if (b->nw[0] > 0) XC_TRY(launch_window<16>(b, 0, st));
     if (b->nw[1] > 0) XC_TRY(launch_window<32>(b, 1, st));
     if (b->nw[2] > 0) XC_TRY(launch_window<64>(b, 2, st));

@@ -98,17 +98,21 @@ struct BlockDev {
   const int* lt_len;
   const int64_t* lt_off;
   const void* lt_val;
-  // Tensor windows (FP32 plans, batches; null until ensure_lockstep builds
-  // them): group g of 128 rows covers the bins [tw_lo[g], tw_lo[g] + 16
-  // tw_nkb[g]) in tw_nkb[g] tiles of 128 rows x 16 bins from tile tw_off[g]
-  // of tw_val; a tile is 128 rows of 32 FP32 values (real and imaginary
-  // parts of 16 bins, zero outside the row's stored band), the 16-byte chunk
-  // c of row r stored at chunk c ^ (r & 7) (the 128-byte swizzled K-major
-  // layout of the tensor core's operands; xc_window.cuh).
-  const int* tw_lo;
-  const int* tw_nkb;
-  const int64_t* tw_off;
-  const float* tw_val;
+};
+
+// Tensor windows of one block (FP32 plans, batches; built by ensure_lockstep,
+// kept apart from BlockDev, which every band item reads): group g of 128 rows
+// covers the bins [lo[g], lo[g] + 16 nkb[g]) in nkb[g] tiles of 128 rows x 16
+// bins from tile off[g] of val; a tile is 128 rows of 32 FP32 values (real
+// and imaginary parts of 16 bins, zero outside the row's stored band), the
+// 16-byte chunk c of row r stored at chunk c ^ (r & 7) (the 128-byte
+// swizzled K-major layout of the tensor core's operands; xc_window.cuh).
+struct WinBlock {
+  const int* lo;
+  const int* nkb;
+  const int64_t* off;
+  const float* val;
+  int64_t spec_off;          // = BlockDev::spec_off
 };
 
 // Rows per chunk of a transposed (bin) slice in the adjoint product: long
@@ -248,6 +252,7 @@ struct Plan {
   int64_t tens_elems = 0;
   int64_t tens_groups = 0;
   std::vector<std::vector<int>> tw_nkb_h;   // [block][group]
+  WinBlock* win_blocks = nullptr;           // device copy, one per block
   int4* lk_units = nullptr;
   int* lk_ubase = nullptr;
   int64_t lk_total_units = 0;

@@ -2664,6 +2664,7 @@ int build_lockstep(Plan* p) {
       p->tens_groups = p->tens_ok ? groups : 0;
       if (p->tens_ok) {
         p->tw_nkb_h = gnkb;
+        std::vector<WinBlock> wb(nb);
         void* val = nullptr;
         XC_TRY(plan_alloc(p, &val, size_t(std::max<int64_t>(tiles, 1)) * 4096 * sizeof(float)));
         int64_t t0 = 0;
@@ -2687,11 +2688,9 @@ int build_lockstep(Plan* p) {
                                               p->N, lo_d, nkb_d, off_d, static_cast<float*>(val));
             XC_CUDA(cudaGetLastError());
           }
-          b.tw_lo = lo_d;
-          b.tw_nkb = nkb_d;
-          b.tw_off = off_d;
-          b.tw_val = static_cast<const float*>(val);
+          wb[i] = WinBlock{lo_d, nkb_d, off_d, static_cast<const float*>(val), b.spec_off};
         }
+        XC_TRY(upload(p, wb, &p->win_blocks));
       }
     }
   }

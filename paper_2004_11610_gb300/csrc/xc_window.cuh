@@ -5,7 +5,7 @@
 // functions: over a thousand stored bins per row) store, besides their band
 // layouts, tensor windows: per group of 128 rows and block, the union of the
 // rows' stored bins [lo, lo + 16 nkb), as nkb tiles of 128 rows x 16 bins
-// (BlockDev::tw_*).  Over one window the band product of Algorithm 1 (step
+// (WinBlock).  Over one window the band product of Algorithm 1 (step
 // 3: y_n = sum_k Re(A_nk conj-folded . F_k)) is a dense contraction,
 //   y[n][r] = sum_k  A[n][2k] F[k][r].re + A[n][2k+1] F[k][r].im,
 // with K = 32 FP32 values per tile (16 bins, real and imaginary parts
@@ -18,7 +18,10 @@
 // A_hi F_hi + A_lo F_hi + A_hi F_lo; each tile's products start a fresh
 // tensor-memory accumulator (the tensor core truncates when it adds), which
 // the epilogue adds to FP32 registers with round-to-nearest additions.  The
-// split is made in shared memory, so the band tiles cross HBM once, as FP32.
+// split is made on the SM, so the band tiles cross HBM once, as FP32: the
+// band operand goes to tensor memory (read there by the MMAs, which would
+// otherwise fetch the 128 x 8 operand from shared memory for every narrow
+// product), the spectra to shared memory.
 //
 // Kernel: persistent, one CTA per SM, tasks (plan, row group) taken in
 // a fixed order (task blockIdx.x + i gridDim.x), each task the tiles of all
@@ -26,19 +29,24 @@
 //   warp 0     producer: per tile one bulk copy of the 16 KB band tile and
 //              one of the 16 bins x rp spectrum values (contiguous in the
 //              bin-major layout) into a ring of STAGES stages
-//   warp 1     allocates tensor memory (two accumulator buffers of 2 NP
-//              columns); one thread issues, per K step of 8,
-//              tcgen05.mma kind::tf32 M = 128, N = 2 NP: A_hi x [F_hi; F_lo]
-//              and N = NP: A_lo x F_hi into the same first NP columns
-//   warps 2-9  converters: thread t splits half t / 128 of band row t % 128
-//              of the tile in place (hi) and into the lo tile, and writes
-//              F_hi / F_lo as K-major 128-byte swizzled rows of the
-//              right-hand sides (zero past rp), then releases the stage to
-//              the MMA thread (two converter warps per scheduler: the split
-//              is bound by shared-memory latency, not by its arithmetic)
+//   warp 1     allocates all 512 tensor-memory columns: per stage 32
+//              columns of A_hi and 32 of A_lo (lane = band row), and two
+//              accumulator buffers of 3 NP columns; one thread issues, per K
+//              step of 8, tcgen05.mma kind::tf32 with A in tensor memory,
+//              M = 128, N = 2 NP: A_hi x [F_hi; F_lo] into columns [0, 2 NP)
+//              and N = NP: A_lo x F_hi into [2 NP, 3 NP) -- two independent
+//              accumulation chains: one chain of these narrow products is
+//              bound by the latency from one accumulation to the next
+//   warps 2-9  converters: warp w, lane l splits half (w - 2) / 4 of band
+//              row 32 (w % 4) + l (its tensor-memory lane) and stores hi and
+//              lo to the stage's tensor-memory columns, and the threads
+//              together write F_hi / F_lo as K-major 128-byte swizzled rows
+//              of the right-hand sides (zero past rp) to shared memory, then
+//              release the stage to the MMA thread (two converter warps per
+//              scheduler: the split is bound by latency, not arithmetic)
 //   warps 10-13 epilogue: warp w owns tensor-memory lanes 32 (w % 4) .. + 31
-//              = rows of the group; per tile it loads the 2 NP columns and
-//              adds hi and lo parts to its NP sums; after a task's last tile
+//              = rows of the group; per tile it loads the 3 NP columns and
+//              adds the three parts to its NP sums; after a task's last tile
 //              it adds the dense tail's sum, which the persistent launch has
 //              left in y (plans with a tail), scales by rowscale_n and
 //              stores y[r][n]
@@ -64,7 +72,7 @@ constexpr int kWinTileFloats = kWinRows * 2 * kWinBins;   // 4096
 
 // One plan of a window launch (device copy per plan of the batch).
 struct WinPlan {
-  const BlockDev* blocks;
+  const WinBlock* blocks;
   int nblocks;
   int rp;                       // spectrum row length (nrhs rounded up to 8), <= NP of the launch
   int64_t N, nrhs, ld;
@@ -76,19 +84,26 @@ struct WinPlan {
 
 template <int NP>
 struct WinCfg {
-  static constexpr int A_BYTES = kWinTileFloats * 4;   // 16 KB: band tile (hi in place) and its lo tile
+  static constexpr int A_BYTES = kWinTileFloats * 4;   // 16 KB: the band tile as copied
   static constexpr int BT_BYTES = 2 * NP * 128;        // F_hi rows then F_lo rows, K-major
   static constexpr int BR_BYTES = kWinBins * NP * 8;   // raw spectra: 16 bins x up to NP complex values
-  static constexpr int STAGE = 2 * A_BYTES + BT_BYTES + BR_BYTES;
-  static constexpr int STAGES = (200 * 1024) / STAGE < 4 ? (200 * 1024) / STAGE : 4;
+  static constexpr int STAGE = A_BYTES + BT_BYTES + BR_BYTES;
+  // stages of the shared-memory ring = stages of the band operand in tensor
+  // memory (a deeper ring, with the band stages released separately, ran
+  // slower)
+  static constexpr int STAGES = NP <= 32 ? 4 : 2;
   static constexpr int SMEM = STAGES * STAGE + 1024 /* alignment */ + 256 /* barriers */;
-  static constexpr int TMEM_COLS = 4 * NP < 32 ? 32 : 4 * NP;   // two buffers of 2 NP columns
+  static constexpr int TMEM_COLS = 512;
+  static constexpr int A_COLS = 64;                    // per stage: A_hi [0, 32), A_lo [32, 64)
+  static constexpr int D_COL = STAGES * A_COLS;        // accumulators [D_COL + 3 NP buf, + 3 NP)
   static_assert(NP % 16 == 0 && 2 * NP <= 256, "UMMA N for M = 128");
-  static_assert(STAGES >= 2 && STAGE % 1024 == 0, "1024-byte aligned stages, two at least");
+  static_assert(D_COL + 6 * NP <= TMEM_COLS, "tensor memory");
+  static_assert(STAGE % 1024 == 0, "1024-byte aligned stages");
+  static_assert((3 * STAGES + 4) * 8 + 4 <= 256, "barrier space");
 };
 
 constexpr int kWinConvThreads = 256;
-constexpr int kWinThreads = 64 + kWinConvThreads + 128;
+constexpr int kWinThreads = 64 + kWinConvThreads + 128 + 32;   // + the second MMA issuer (last warp)
 
 template <int NP>
 __global__ void __launch_bounds__(kWinThreads, 1)
@@ -97,8 +112,12 @@ __global__ void __launch_bounds__(kWinThreads, 1)
   using namespace tc;
   using C = WinCfg<NP>;
   constexpr int S = C::STAGES;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+  // (a name of its own: extern shared arrays of one name are one symbol in a
+  // translation unit, and a 1024-byte alignment here would add 1 KB of static
+  // shared memory to the batch kernel -- enough, at three CTAs per SM, to
+  // take a step of the shared-memory carveout from its L1)
+  extern __shared__ __align__(16) unsigned char win_smem[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(win_smem) + 1023) &
                                                          ~static_cast<uintptr_t>(1023));
   // barriers: full[S], conv[S], empty[S], tfull[2], tempty[2]; then the tensor-memory address
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * C::STAGE);
@@ -107,10 +126,9 @@ __global__ void __launch_bounds__(kWinThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tile0 = smem_u32(smem);
-  auto a_t = [&](int s) { return tile0 + uint32_t(s * C::STAGE); };                         // band hi (in place)
-  auto a_lo = [&](int s) { return tile0 + uint32_t(s * C::STAGE + C::A_BYTES); };
-  auto b_t = [&](int s) { return tile0 + uint32_t(s * C::STAGE + 2 * C::A_BYTES); };         // F_hi; F_lo
-  auto b_raw = [&](int s) { return tile0 + uint32_t(s * C::STAGE + 2 * C::A_BYTES + C::BT_BYTES); };
+  auto a_t = [&](int s) { return tile0 + uint32_t(s * C::STAGE); };                         // band tile
+  auto b_t = [&](int s) { return tile0 + uint32_t(s * C::STAGE + C::A_BYTES); };             // F_hi; F_lo
+  auto b_raw = [&](int s) { return tile0 + uint32_t(s * C::STAGE + C::A_BYTES + C::BT_BYTES); };
   auto full = [&](int s) { return smem_u32(&bars[s]); };
   auto conv = [&](int s) { return smem_u32(&bars[S + s]); };
   auto empty = [&](int s) { return smem_u32(&bars[2 * S + s]); };
@@ -122,10 +140,10 @@ __global__ void __launch_bounds__(kWinThreads, 1)
     for (int s = 0; s < S; ++s) {
       mbar_init(full(s), 1);
       mbar_init(conv(s), kWinConvThreads);
-      mbar_init(empty(s), 1);
+      mbar_init(empty(s), 2);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(tfull(b), 1);
+      mbar_init(tfull(b), 2);
       mbar_init(tempty(b), 4);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -146,7 +164,7 @@ __global__ void __launch_bounds__(kWinThreads, 1)
   // tiles of a task: all blocks' tiles of its row group
   auto task_tiles = [&](const WinPlan& P, int g) {
     int n = 0;
-    for (int bi = 0; bi < P.nblocks; ++bi) n += P.blocks[bi].tw_nkb[g];
+    for (int bi = 0; bi < P.nblocks; ++bi) n += P.blocks[bi].nkb[g];
     return n;
   };
 
@@ -160,10 +178,10 @@ __global__ void __launch_bounds__(kWinThreads, 1)
         const WinPlan& P = plans[tk.x];
         const uint32_t braw_bytes = uint32_t(kWinBins * P.rp * 8);
         for (int bi = 0; bi < P.nblocks && ok; ++bi) {
-          const BlockDev& b = P.blocks[bi];
-          const int nkb = b.tw_nkb[tk.y];
-          const int64_t lo = b.tw_lo[tk.y];
-          const float* a_src = b.tw_val + b.tw_off[tk.y] * kWinTileFloats;
+          const WinBlock& b = P.blocks[bi];
+          const int nkb = b.nkb[tk.y];
+          const int64_t lo = b.lo[tk.y];
+          const float* a_src = b.val + b.off[tk.y] * kWinTileFloats;
           for (int kb = 0; kb < nkb; ++kb) {
             const int s = kbi % S;
             if (!mbar_wait(empty(s), (uint32_t(kbi / S) & 1u) ^ 1u, abort)) {
@@ -182,8 +200,12 @@ __global__ void __launch_bounds__(kWinThreads, 1)
       for (int k = kbi > S ? kbi - S : 0; k < kbi; ++k)
         if (!mbar_wait(full(k % S), uint32_t(k / S) & 1u, no_abort) && !*abort) give_up();
     }
-  } else if (warp == 1) {
-    // ---------------------------------------------------------- MMA issuer
+  } else if (warp == 1 || warp == kWinThreads / 32 - 1) {
+    // ---------------------------------------------------------- MMA issuers
+    // warp 1: A_hi x [F_hi; F_lo] into columns [0, 2 NP); the last warp:
+    // A_lo x F_hi into [2 NP, 3 NP) -- two issuing threads, each committing
+    // to the stage and buffer barriers (which count two arrivals)
+    const bool second = warp != 1;
     if (lane == 0) {
       constexpr uint32_t idesc2 = tf32_idesc(kWinRows, 2 * NP);   // A_hi x [F_hi; F_lo]
       constexpr uint32_t idesc1 = tf32_idesc(kWinRows, NP);       // A_lo x F_hi
@@ -201,12 +223,18 @@ __global__ void __launch_bounds__(kWinThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t d = tmem + uint32_t(buf * 2 * NP);
+          const uint32_t d = tmem + uint32_t(C::D_COL + buf * 3 * NP);
+          const uint32_t a = tmem + uint32_t(s * C::A_COLS);
+          if (!second) {
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t off = uint32_t(kk * 32);   // K step of 8 FP32 values inside the swizzled row
-            umma_tf32(d, sw128_desc(a_t(s) + off), sw128_desc(b_t(s) + off), idesc2, kk != 0 ? 1u : 0u);
-            umma_tf32(d, sw128_desc(a_lo(s) + off), sw128_desc(b_t(s) + off), idesc1, 1u);
+            for (int kk = 0; kk < 4; ++kk)   // K step of 8 FP32 values = 32 bytes inside the swizzled row
+              umma_tf32_ts(d, a + uint32_t(kk * 8), sw128_desc(b_t(s) + uint32_t(kk * 32)), idesc2,
+                           kk != 0 ? 1u : 0u);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              umma_tf32_ts(d + uint32_t(2 * NP), a + uint32_t(32 + kk * 8), sw128_desc(b_t(s) + uint32_t(kk * 32)),
+                           idesc1, kk != 0 ? 1u : 0u);
           }
           umma_commit(empty(s));
           umma_commit(tfull(buf));
@@ -220,7 +248,9 @@ __global__ void __launch_bounds__(kWinThreads, 1)
   } else if (warp < 2 + kWinConvThreads / 32) {
     // ---------------------------------------------------------- converters
     const int ct = threadIdx.x - 64;
-    const int row = ct & 127, half = ct >> 7;   // band row of the tile, chunks [4 half, 4 half + 4)
+    // band row = this thread's tensor-memory lane; K columns [16 half, 16 half + 16)
+    const int row = 32 * (warp & 3) + lane, half = (warp - 2) >> 2;
+    const uint32_t a_lane = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(16 * half);
     int kbi = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
@@ -230,28 +260,33 @@ __global__ void __launch_bounds__(kWinThreads, 1)
       const int rp = P.rp;
       for (int k = 0; k < nk; ++k) {
         const int s = kbi % S;
-        if (!mbar_wait(full(s), uint32_t(kbi / S) & 1u, abort)) {
-          if (!*abort) give_up();
+        // one lane waits, the warp follows (the tensor-memory stores are warp-collective)
+        int ready = 0;
+        if (lane == 0) {
+          ready = mbar_wait(full(s), uint32_t(kbi / S) & 1u, abort) ? 1 : 0;
+          if (!ready && !*abort) give_up();
+        }
+        if (!__shfl_sync(0xffffffffu, ready, 0)) {
           ok = false;
           break;
         }
-        // band row: hi in place, lo to the lo tile (same swizzled positions);
-        // the chunk order rotates with the row so that a warp's accesses
-        // spread over all banks
-        float4* ar = reinterpret_cast<float4*>(smem + (a_t(s) - tile0) + row * 128);
-        float4* lr = reinterpret_cast<float4*>(smem + (a_lo(s) - tile0) + row * 128);
+        // band row, K values 16 half .. + 15 (chunk c of the copied tile row
+        // at position c ^ (row & 7)), split into the stage's tensor memory
+        const float4* ar = reinterpret_cast<const float4*>(smem + (a_t(s) - tile0) + row * 128);
+        float hv[16], lv[16];
 #pragma unroll
         for (int c0 = 0; c0 < 4; ++c0) {
-          const int c = (4 * half + c0) ^ (row & 7);
-          const float4 v = ar[c];
-          float4 h, l;
-          split_tf32(v.x, &h.x, &l.x);
-          split_tf32(v.y, &h.y, &l.y);
-          split_tf32(v.z, &h.z, &l.z);
-          split_tf32(v.w, &h.w, &l.w);
-          ar[c] = h;
-          lr[c] = l;
+          const float4 v = ar[(4 * half + c0) ^ (row & 7)];
+          split_tf32(v.x, &hv[4 * c0], &lv[4 * c0]);
+          split_tf32(v.y, &hv[4 * c0 + 1], &lv[4 * c0 + 1]);
+          split_tf32(v.z, &hv[4 * c0 + 2], &lv[4 * c0 + 2]);
+          split_tf32(v.w, &hv[4 * c0 + 3], &lv[4 * c0 + 3]);
         }
+        // (the stage's previous products are done: the producer waited for
+        // them before copying this tile)
+        tc_fence_after();
+        tmem_st16(a_lane + uint32_t(s * C::A_COLS), hv);
+        tmem_st16(a_lane + uint32_t(s * C::A_COLS + 32), lv);
         // spectra: K-major rows n of [F_hi; F_lo], chunk c = bins 2c, 2c+1
         const float2* raw = reinterpret_cast<const float2*>(smem + (b_raw(s) - tile0));
         unsigned char* bt = smem + (b_t(s) - tile0);
@@ -271,7 +306,10 @@ __global__ void __launch_bounds__(kWinThreads, 1)
           *reinterpret_cast<float4*>(bt + n * 128 + sw) = h;
           *reinterpret_cast<float4*>(bt + (NP + n) * 128 + sw) = l;
         }
-        fence_async_smem();   // the tensor core reads these tiles through the async proxy
+        __syncwarp();
+        tmem_wait_st();       // the band values are in tensor memory
+        tc_fence_before();
+        fence_async_smem();   // the tensor core reads the spectrum tiles through the async proxy
         mbar_arrive(conv(s));
         ++kbi;
       }
@@ -301,14 +339,15 @@ __global__ void __launch_bounds__(kWinThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t base = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * 2 * NP);
+        const uint32_t base = tmem + (uint32_t(q * 32) << 16) + uint32_t(C::D_COL + buf * 3 * NP);
 #pragma unroll
         for (int c0 = 0; c0 < NP; c0 += 16) {
-          float vh[16], vl[16];
-          tmem_ld16(base + uint32_t(c0), vh);        // A_hi F_hi + A_lo F_hi
-          tmem_ld16(base + uint32_t(NP + c0), vl);   // A_hi F_lo
+          float vh[16], vl[16], vm[16];
+          tmem_ld16(base + uint32_t(c0), vh);            // A_hi F_hi
+          tmem_ld16(base + uint32_t(NP + c0), vl);       // A_hi F_lo
+          tmem_ld16(base + uint32_t(2 * NP + c0), vm);   // A_lo F_hi
 #pragma unroll
-          for (int j = 0; j < 16; ++j) acc[c0 + j] += vh[j] + vl[j];
+          for (int j = 0; j < 16; ++j) acc[c0 + j] += vh[j] + (vl[j] + vm[j]);
         }
         tc_fence_before();
         __syncwarp();
