@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--impl", choices=("xc", "reference"), default="xc")
     ap.add_argument("--workload", default="cheb_lag4096_fp64", choices=sorted(inputs.WORKLOADS) + ["batch1000"])
     ap.add_argument("--nplans", type=int, default=1000, help="plans of the batch workload")
+    ap.add_argument("--batch-schedule", default="",
+                    help="rpw_f,rpw_a,lockstep_f,lockstep_a: a fixed batch schedule instead of the tuner (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-variant", action="store_true",
@@ -895,11 +897,14 @@ def run_xc(args, rank, world, local_rank):
 
 
 # ---------------------------------------------------------------- batch path
-def measure_batch(xc, torch, nplans, dev, rank, world, steps, warmup, tune=True):
+def measure_batch(xc, torch, nplans, dev, rank, world, steps, warmup, tune=True, schedule=None):
     """The many-plan workload (N log-uniform in [256, 8192], families uniform
     over Chebyshev / Legendre / Jacobi(1/2,-1/2) / Hermite, 1..32 right-hand
     sides), FP32, eps = 1e-7: forward + adjoint as two persistent launches
-    replayed from one CUDA graph.  Returns the bench line's fields."""
+    (and, forward, the tensor-core window launches) replayed from one CUDA
+    graph.  `schedule` (rpw_f, rpw_a, lockstep_f, lockstep_a) replaces the
+    tuner's choice (fixed launch counts, for profiling).  Returns the bench
+    line's fields."""
     wl = inputs.batch_workload(nplans)
     t_create = time.perf_counter()
     plans, xs, ys, xa = [], [], [], []
@@ -915,7 +920,10 @@ def measure_batch(xc, torch, nplans, dev, rank, world, steps, warmup, tune=True)
     fwd, adj = xc.Batch(plans), xc.Batch(plans)
     fwd.bind(xs, ys)          # forward: x -> y
     adj.bind(xa, ys)          # adjoint: y -> xa (keeps x)
-    if tune:
+    if schedule is not None:
+        fwd.schedule(*schedule)
+        adj.schedule(*schedule)
+    elif tune:
         fwd.tune(stream)
         adj.tune(stream)
     infos = [p.info() for p in plans]
@@ -1060,7 +1068,8 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     clocks = ClockSampler(local_rank)
     clocks.start()
-    b = measure_batch(xc, torch, args.nplans, dev, rank, world, args.steps, args.warmup)
+    sched = tuple(int(v) for v in args.batch_schedule.split(",")) if args.batch_schedule else None
+    b = measure_batch(xc, torch, args.nplans, dev, rank, world, args.steps, args.warmup, schedule=sched)
     clock_info = clocks.stop()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
