@@ -1001,7 +1001,9 @@ def measure_batch(xc, torch, nplans, dev, rank, world, steps, warmup, tune=True,
                 "algorithmic_bytes_per_launch": (fwd_bytes, adj_bytes)[dom], "avg_launch_ms": dir_ms[dom],
                 "other_direction": {"kernel": ("batch_kernel (forward)", "batch_kernel (adjoint)")[1 - dom],
                                     "achieved": (fwd_bytes, adj_bytes)[1 - dom] / (dir_ms[1 - dom] / 1e3) / 1e9,
-                                    "avg_launch_ms": dir_ms[1 - dom]}}
+                                    "avg_launch_ms": dir_ms[1 - dom],
+                                    "traffic": traffic_from_profiles("batch_kernel", "batch1000",
+                                                                     ("forward", "adjoint")[1 - dom])}}
     roofline["other_direction"]["frac"] = roofline["other_direction"]["achieved"] / hbm_peak
 
     # end to end: pinned host inputs copied in, both launches, results copied out
