@@ -337,6 +337,7 @@ typedef struct {
    * entry 4 * lockstep + log2(right-hand sides per item); -1 where not tried */
   float tune_ms_forward[12], tune_ms_adjoint[12];
   int tensor_plans;          /* plans whose forward band products run on the tensor cores */
+  int tensor_plans_adjoint;  /* the same for the adjoint band products */
 } xc_batch_stats;
 
 /* Group nplans distinct plans (host array of handles; all of one precision;
@@ -378,18 +379,19 @@ int xc_batch_apply(xc_batch_t b, int adjoint, void* stream);
  * results equal xc_apply's to rounding, not bit for bit.
  *
  * Tensor windows: a bind of an XC_FP32 batch also builds, for plans whose
- * bands over groups of 128 rows cost at most 1.5 times their stored bands,
- * 128-row x 16-bin tiles of the forward band layout; with lockstep 2 the
- * forward band products of those plans with at most 64 right-hand sides
- * run as dense 3xTF32 tensor-core products over the tiles (tcgen05, FP32
- * accuracy, xc_window.cuh), after the persistent launch has made their
- * spectra.  Their results equal xc_apply's to FP32 rounding. */
+ * bands over groups of 128 rows (adjoint: the rows of groups of 64 bins)
+ * cost at most 1.5 times their stored bands, 16 KB tiles of the band
+ * layouts; with lockstep 2 the band products of those plans with at most 64
+ * right-hand sides run as dense 3xTF32 tensor-core products over the tiles
+ * (tcgen05, FP32 accuracy, xc_window.cuh): forward after the persistent
+ * launch has made their spectra, adjoint before it, which then runs their
+ * inverse FFTs.  Their results equal xc_apply's to FP32 rounding. */
 int xc_batch_tune(xc_batch_t b, void* stream);
 /* Set the schedule by hand instead of tuning it: right-hand sides per band
  * item (1, 2, 4 or 8) and lockstep items on (1) or off (0), per direction;
- * lockstep_forward = 2 runs the forward band products of the plans with
- * tensor windows on the tensor cores (lockstep items for the other plans
- * that have them).
+ * lockstep 2 runs the band products of the plans with tensor windows on the
+ * tensor cores in that direction (lockstep items for the other plans that
+ * have them).
  * Rebuilds the task lists (synchronous); XC_ERR_ARG before a bind. */
 int xc_batch_schedule(xc_batch_t b, int rpw_forward, int rpw_adjoint, int lockstep_forward, int lockstep_adjoint);
 int xc_batch_info(xc_batch_t b, xc_batch_stats* out);

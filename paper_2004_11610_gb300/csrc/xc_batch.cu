@@ -202,6 +202,25 @@ __global__ void __launch_bounds__(256) fwd_tail_kernel(const BatchPlanDev* __res
   }
 }
 
+// Row-scaled right-hand sides of the plans whose adjoint band products run in
+// the window launches, stored row-major for them: yt[n][r] = y[r][n]
+// rowscale_n, one warp per entry (plan, row slice), lane = row.  The pad
+// columns r >= nrhs and the pad rows past N stay zero from the allocation.
+__global__ void __launch_bounds__(256) adj_yt_kernel(const WinPlan* __restrict__ plans,
+                                                     const int2* __restrict__ entries, int64_t n) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t e = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; e < n;
+       e += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    const int2 en = entries[e];
+    const WinPlan& P = plans[en.x];
+    const int64_t row = int64_t(en.y) * 32 + lane;
+    if (row >= P.N) continue;
+    const float rs = P.rowscale ? P.rowscale[row] : 1.f;
+    float* out = P.yt + row * P.rp;
+    for (int64_t r = 0; r < P.nrhs; ++r) out[r] = P.y[r * P.ld + row] * rs;
+  }
+}
+
 // Lockstep forward items of a plan: RL = P.rl rows per lane (1, 2 or 4;
 // 8 RL right-hand sides per item).
 template <typename T, bool COMP>
@@ -467,13 +486,19 @@ struct Batch {
   // forward tensor-window launches (xc_window.cuh), one per class of
   // spectrum row length rp <= 16, 32, 64: the plans' descriptors and the
   // tasks (plan, row group) of each class
-  WinPlan* dwin = nullptr;
-  std::vector<WinPlan> hwin;
-  int2* wlist[3] = {nullptr, nullptr, nullptr};
-  int64_t nw[3] = {0, 0, 0}, wcap[3] = {0, 0, 0};
+  // (per direction: the window launches of the forward band products and of
+  // the adjoint's)
+  WinPlan* dwin[2] = {nullptr, nullptr};
+  std::vector<WinPlan> hwin[2];
+  int4* wlist[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  int64_t nw[2][3] = {{0, 0, 0}, {0, 0, 0}}, wcap[2][3] = {{0, 0, 0}, {0, 0, 0}};
   int2* tlist = nullptr;         // (plan, row slice) entries of fwd_tail_kernel
   int64_t ntail = 0, tcap = 0;
-  int tens_plans = 0;
+  int2* ylist = nullptr;         // (plan, row slice) entries of adj_yt_kernel
+  int64_t nyt = 0, ycap = 0;
+  std::vector<void*> ytbuf;      // per plan: the adjoint windows' row-scaled right-hand sides (nullptr: none)
+  std::vector<int64_t> ytbuf_bytes;
+  int tens_plans[2] = {0, 0};
   bool ring = false;             // the kernel's shared memory holds the warps' staging rings
   bool tuned = false;
   std::vector<BatchPlanDev> host;   // device copies of these are in dplans
@@ -514,6 +539,12 @@ bool tensor_capable(const Batch* b, int p) {
   const Plan* P = b->plans[p];
   return b->precision == XC_FP32 && P->tens_ok && b->lscratch[p] != nullptr && b->nrhs[p] > 0 && b->nrhs[p] <= 64;
 }
+// The same for the adjoint band product (transposed tensor windows).
+bool tensor_t_capable(const Batch* b, int p) {
+  const Plan* P = b->plans[p];
+  return b->precision == XC_FP32 && P->tens_t_ok && b->lscratch[p] != nullptr && b->ytbuf[p] != nullptr &&
+         b->nrhs[p] > 0 && b->nrhs[p] <= 64;
+}
 
 // Work lists of both directions for the bound right-hand sides, with rpw_f
 // (forward) and rpw_a (adjoint) right-hand sides per band item; lock_f /
@@ -526,18 +557,24 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
   const int np = int(b->plans.size());
   b->rpw[0] = b->rpw[1] = 0;   // unbound until every list is in place (a failure leaves it so)
   std::vector<Entry> L[2][3];
-  std::vector<std::pair<double, int2>> W[3];
-  std::vector<int2> tails;
+  std::vector<std::pair<double, int4>> W[2][3];
+  std::vector<int2> tails, yts;
   std::vector<unsigned> need[2] = {std::vector<unsigned>(2 * size_t(np), 0), std::vector<unsigned>(2 * size_t(np), 0)};
-  b->hwin.assign(np, WinPlan{});
-  b->tens_plans = 0;
+  for (int d = 0; d < 2; ++d) {
+    b->hwin[d].assign(np, WinPlan{});
+    b->tens_plans[d] = 0;
+  }
   for (int p = 0; p < np; ++p) {
     const Plan* P = b->plans[p];
     BatchPlanDev& H = b->host[p];
     const bool tens = lock_f == 2 && tensor_capable(b, p);
     // tensor plans keep the lockstep (bin-major) spectra of their FFTs
     H.lock_f = tens || (lock_f && b->lscratch[p] != nullptr && P->lock_f_ok);
-    H.lock_a = lock_a && b->lscratch[p] != nullptr && P->lock_t_ok;
+    const bool tens_a = lock_a == 2 && tensor_t_capable(b, p);
+    // tensor adjoint plans write one chunk partial per bin slice, which the
+    // inverse FFTs read as they read the lockstep items' partials
+    H.lock_a = tens_a || (lock_a && b->lscratch[p] != nullptr && P->lock_t_ok);
+    H.lk_cbase = tens_a ? P->tw_tcbase : P->lk_cbase;
     const int64_t R = b->nrhs[p];
     if (R == 0) continue;
     if (tens) {
@@ -555,9 +592,9 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
       for (int64_t g = 0; g < P->tens_groups; ++g) {
         int tiles = 0;
         for (size_t i = 0; i < P->blocks.size(); ++i) tiles += P->tw_nkb_h[i][g];
-        W[cls].push_back({double(tiles), int2{p, int(g)}});
+        W[0][cls].push_back({double(tiles), int4{p, 0, int(g), 0}});
       }
-      WinPlan& w = b->hwin[p];
+      WinPlan& w = b->hwin[0][p];
       w.blocks = P->win_blocks;
       w.nblocks = int(P->blocks.size());
       w.rp = H.rp;
@@ -568,7 +605,7 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
       w.spec = static_cast<const cx<float>*>(b->lscratch[p]);
       w.tail_in_y = P->m_tail > 0 ? 1 : 0;
       w.rowscale = static_cast<const float*>(P->rowscale);
-      ++b->tens_plans;
+      ++b->tens_plans[0];
     } else if (H.lock_f) {
       for (size_t i = 0; i < P->blocks.size(); ++i) {
         const double c = double(P->blocks[i].n) * std::log2(double(P->blocks[i].n) + 1.0);
@@ -599,7 +636,37 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
         }
       }
     }
-    if (H.lock_a) {
+    if (tens_a) {
+      // adjoint on the tensor cores: yt, then every bin group's window
+      // product (groups without tiles write zeros), the tails and inverse FFTs
+      for (int64_t s0 = 0; s0 < P->nslices; ++s0) yts.push_back(int2{p, int(s0)});
+      const int cls = H.rp <= 16 ? 0 : H.rp <= 32 ? 1 : 2;
+      for (size_t i = 0; i < P->blocks.size(); ++i)
+        for (size_t g = 0; g < P->tw_t_nkb_h[i].size(); ++g)
+          W[1][cls].push_back({double(P->tw_t_nkb_h[i][g]) + 0.5, int4{p, int(i), int(g), 0}});
+      for (int64_t m = 0; m < P->m_tail; m += kTailCols)
+        for (int64_t r = 0; r < R; ++r) {
+          L[1][1].push_back({double(P->N) / 32.0 * double(std::min<int64_t>(kTailCols, P->m_tail - m)),
+                             int4{T_ADJ_TAIL, p, int(m), int(r)}});
+          ++need[1][np + p];
+        }
+      for (size_t i = 0; i < P->blocks.size(); ++i) {
+        const double c = double(P->blocks[i].n) * std::log2(double(P->blocks[i].n) + 1.0);
+        for (int64_t r = 0; r < R; ++r) L[1][2].push_back({c, int4{T_ADJ_FFT, p, int(i), int(r)}});
+      }
+      WinPlan& w = b->hwin[1][p];
+      w.blocks = P->win_blocks_t;
+      w.nblocks = int(P->blocks.size());
+      w.rp = H.rp;
+      w.N = P->N;
+      w.nrhs = R;
+      w.ld = b->ld[p];
+      w.y = static_cast<float*>(b->y[p]);
+      w.rowscale = static_cast<const float*>(P->rowscale);
+      w.yt = static_cast<float*>(b->ytbuf[p]);
+      w.part = static_cast<cx<float>*>(b->lscratch[p]);
+      ++b->tens_plans[1];
+    } else if (H.lock_a) {
       // adjoint lockstep items: RL bins x 8 RHS per lane, 8 RL right-hand sides per item
       const int64_t la = b->precision == XC_FP32_COMPENSATED ? 8 : 16;
       const int64_t ga = (R + la - 1) / la;
@@ -687,21 +754,31 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
     }
     XC_CUDA(cudaMemcpy(b->need[d], need[d].data(), 2 * size_t(np) * sizeof(unsigned), cudaMemcpyHostToDevice));
   }
-  for (int c = 0; c < 3; ++c) {
-    auto& v = W[c];
-    std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& e) { return a.first > e.first; });
-    std::vector<int2> flat(v.size());
-    for (size_t k = 0; k < v.size(); ++k) flat[k] = v[k].second;
-    if (int64_t(flat.size()) > b->wcap[c] || b->wlist[c] == nullptr) {
-      void* ptr = nullptr;
-      XC_TRY(b->alloc(&ptr, std::max<size_t>(1, flat.size()) * sizeof(int2)));
-      b->wlist[c] = static_cast<int2*>(ptr);
-      b->wcap[c] = int64_t(std::max<size_t>(1, flat.size()));
+  for (int d = 0; d < 2; ++d)
+    for (int c = 0; c < 3; ++c) {
+      auto& v = W[d][c];
+      std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& e) { return a.first > e.first; });
+      std::vector<int4> flat(v.size());
+      for (size_t k = 0; k < v.size(); ++k) flat[k] = v[k].second;
+      if (int64_t(flat.size()) > b->wcap[d][c] || b->wlist[d][c] == nullptr) {
+        void* ptr = nullptr;
+        XC_TRY(b->alloc(&ptr, std::max<size_t>(1, flat.size()) * sizeof(int4)));
+        b->wlist[d][c] = static_cast<int4*>(ptr);
+        b->wcap[d][c] = int64_t(std::max<size_t>(1, flat.size()));
+      }
+      b->nw[d][c] = int64_t(flat.size());
+      if (!flat.empty())
+        XC_CUDA(cudaMemcpy(b->wlist[d][c], flat.data(), flat.size() * sizeof(int4), cudaMemcpyHostToDevice));
     }
-    b->nw[c] = int64_t(flat.size());
-    if (!flat.empty())
-      XC_CUDA(cudaMemcpy(b->wlist[c], flat.data(), flat.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  if (int64_t(yts.size()) > b->ycap || b->ylist == nullptr) {
+    void* ptr = nullptr;
+    XC_TRY(b->alloc(&ptr, std::max<size_t>(1, yts.size()) * sizeof(int2)));
+    b->ylist = static_cast<int2*>(ptr);
+    b->ycap = int64_t(std::max<size_t>(1, yts.size()));
   }
+  b->nyt = int64_t(yts.size());
+  if (!yts.empty())
+    XC_CUDA(cudaMemcpy(b->ylist, yts.data(), yts.size() * sizeof(int2), cudaMemcpyHostToDevice));
   if (int64_t(tails.size()) > b->tcap || b->tlist == nullptr) {
     void* ptr = nullptr;
     XC_TRY(b->alloc(&ptr, std::max<size_t>(1, tails.size()) * sizeof(int2)));
@@ -711,14 +788,15 @@ int build_tasks(Batch* b, int rpw_f, int rpw_a, int lock_f, int lock_a) {
   b->ntail = int64_t(tails.size());
   if (!tails.empty())
     XC_CUDA(cudaMemcpy(b->tlist, tails.data(), tails.size() * sizeof(int2), cudaMemcpyHostToDevice));
-  if (b->tens_plans > 0) {
-    if (b->dwin == nullptr) {
-      void* ptr = nullptr;
-      XC_TRY(b->alloc(&ptr, size_t(np) * sizeof(WinPlan)));
-      b->dwin = static_cast<WinPlan*>(ptr);
+  for (int d = 0; d < 2; ++d)
+    if (b->tens_plans[d] > 0) {
+      if (b->dwin[d] == nullptr) {
+        void* ptr = nullptr;
+        XC_TRY(b->alloc(&ptr, size_t(np) * sizeof(WinPlan)));
+        b->dwin[d] = static_cast<WinPlan*>(ptr);
+      }
+      XC_CUDA(cudaMemcpy(b->dwin[d], b->hwin[d].data(), size_t(np) * sizeof(WinPlan), cudaMemcpyHostToDevice));
     }
-    XC_CUDA(cudaMemcpy(b->dwin, b->hwin.data(), size_t(np) * sizeof(WinPlan), cudaMemcpyHostToDevice));
-  }
   XC_CUDA(cudaMemcpy(b->dplans, b->host.data(), size_t(np) * sizeof(BatchPlanDev), cudaMemcpyHostToDevice));
   b->rpw[0] = rpw_f;
   b->rpw[1] = rpw_a;
@@ -762,24 +840,47 @@ int launch_batch_t(Batch* b, int dir, cudaStream_t st) {
   }
 }
 
-template <int NP>
+template <int NP, bool ADJ>
 int launch_window(Batch* b, int cls, cudaStream_t st) {
   using C = WinCfg<NP>;
-  auto fn = window_fwd_kernel<NP>;
+  auto fn = window_kernel<NP, ADJ>;
+  const int d = ADJ ? 1 : 0;
   // one CTA per SM: each allocates all of the SM's tensor memory
   const int smem = std::max(C::SMEM, 116 * 1024);
   XC_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int dev = 0, sms = 0;
   XC_CUDA(cudaGetDevice(&dev));
   XC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t grid = std::min<int64_t>(sms, b->nw[cls]);
+  const int64_t grid = std::min<int64_t>(sms, b->nw[d][cls]);
   count_launch();
-  fn<<<unsigned(grid), kWinThreads, smem, st>>>(b->dwin, b->wlist[cls], int(b->nw[cls]), &b->ctrl[C_STATUS]);
+  fn<<<unsigned(grid), kWinThreads, smem, st>>>(b->dwin[d], b->wlist[d][cls], int(b->nw[d][cls]),
+                                                &b->ctrl[C_STATUS]);
   XC_CUDA(cudaGetLastError());
   return XC_OK;
 }
 
+template <bool ADJ>
+int launch_windows(Batch* b, cudaStream_t st) {
+  const int d = ADJ ? 1 : 0;
+  if (b->nw[d][0] > 0) XC_TRY((launch_window<16, ADJ>(b, 0, st)));
+  if (b->nw[d][1] > 0) XC_TRY((launch_window<32, ADJ>(b, 1, st)));
+  if (b->nw[d][2] > 0) XC_TRY((launch_window<64, ADJ>(b, 2, st)));
+  return XC_OK;
+}
+
 int launch_batch(Batch* b, int dir, cudaStream_t st) {
+  // adjoint band products of the tensor plans first: their row-scaled
+  // right-hand sides, then the window products, whose partials the inverse
+  // FFTs of the persistent launch read
+  if (dir == 1 && b->tens_plans[1] > 0) {
+    if (b->nyt > 0) {
+      count_launch();
+      adj_yt_kernel<<<unsigned(std::min<int64_t>((b->nyt + 7) / 8, 4096)), 256, 0, st>>>(b->dwin[1], b->ylist,
+                                                                                      b->nyt);
+      XC_CUDA(cudaGetLastError());
+    }
+    XC_TRY(launch_windows<true>(b, st));
+  }
   if (b->entries(dir) > 0) {
     switch (b->precision) {
       case XC_FP64: XC_TRY((launch_batch_t<double, false>(b, dir, st))); break;
@@ -789,16 +890,14 @@ int launch_batch(Batch* b, int dir, cudaStream_t st) {
   }
   // forward band products of the tensor plans, after their FFTs (and their
   // dense tails, which the window epilogue adds)
-  if (dir == 0 && b->tens_plans > 0) {
+  if (dir == 0 && b->tens_plans[0] > 0) {
     if (b->ntail > 0) {
       count_launch();
       fwd_tail_kernel<<<unsigned(std::min<int64_t>((b->ntail + 7) / 8, 4096)), 256, 0, st>>>(b->dplans, b->tlist,
                                                                                           b->ntail);
       XC_CUDA(cudaGetLastError());
     }
-    if (b->nw[0] > 0) XC_TRY(launch_window<16>(b, 0, st));
-    if (b->nw[1] > 0) XC_TRY(launch_window<32>(b, 1, st));
-    if (b->nw[2] > 0) XC_TRY(launch_window<64>(b, 2, st));
+    XC_TRY(launch_windows<false>(b, st));
   }
   return XC_OK;
 }
@@ -870,6 +969,8 @@ int xc_batch_create(xc_batch_t* out, const xc_plan_t* plans, int nplans) {
   std::fill(&b->tune_ms[0][0], &b->tune_ms[0][0] + 2 * 12, -1.f);
   b->extra_need.assign(nplans, 0);
   b->lscratch.assign(nplans, nullptr);
+  b->ytbuf.assign(nplans, nullptr);
+  b->ytbuf_bytes.assign(nplans, 0);
   b->lscratch_bytes.assign(nplans, 0);
   void* ptr = nullptr;
   int rc = b->alloc(&ptr, xc::C_WORDS * sizeof(unsigned));
@@ -929,7 +1030,7 @@ int xc_batch_bind(xc_batch_t batch, const void* const* x_dev, void* const* y_dev
     xc::Plan* p = b->plans[i];
     if (b->precision == XC_FP64 || nrhs[i] == 0) continue;
     XC_TRY(xc::ensure_lockstep(p));
-    if (!p->lock_f_ok && !p->lock_t_ok && !p->tens_ok) continue;
+    if (!p->lock_f_ok && !p->lock_t_ok && !p->tens_ok && !p->tens_t_ok) continue;
     const int64_t rp = (nrhs[i] + 7) / 8 * 8;
     // forward: bin-major spectra, the lockstep unit partials, and 16 bins
     // of zeros past the spectra (a tensor window's last tile may reach 15
@@ -937,7 +1038,10 @@ int xc_batch_bind(xc_batch_t batch, const void* const* x_dev, void* const* y_dev
     const int64_t fwd = p->lock_f_ok || p->tens_ok
                             ? p->spec_per_rhs * rp + p->lk_total_units * 32 * nrhs[i] + xc::kWinBins * rp
                             : 0;
-    const int64_t adj = p->lock_t_ok ? p->lk_total_chunks * 32 * nrhs[i] : 0;
+    // adjoint: the chunk partials (lockstep chunks, or one per bin slice)
+    const int64_t adj = p->lock_t_ok || p->tens_t_ok
+                            ? std::max<int64_t>(p->lk_total_chunks, p->total_tslices) * 32 * nrhs[i]
+                            : 0;
     const int64_t bytes = std::max<int64_t>(fwd, adj) * int64_t(sizeof(xc::cx<float>));
     if (b->lscratch[i] == nullptr || b->lscratch_bytes[i] < bytes) {
       void* ptr = nullptr;
@@ -945,6 +1049,18 @@ int xc_batch_bind(xc_batch_t batch, const void* const* x_dev, void* const* y_dev
       XC_CUDA(cudaMemset(ptr, 0, size_t(bytes)));   // the pad column of odd nrhs stays zero
       b->lscratch[i] = ptr;
       b->lscratch_bytes[i] = bytes;
+    }
+    if (p->tens_t_ok && nrhs[i] <= 64) {
+      // row-scaled right-hand sides of the adjoint windows, [N + 32][rp]: a
+      // window's last tile may reach 31 rows past N (zeros)
+      const int64_t ybytes = (p->N + 32) * rp * int64_t(sizeof(float));
+      if (b->ytbuf[i] == nullptr || b->ytbuf_bytes[i] < ybytes) {
+        void* ptr = nullptr;
+        XC_TRY(b->alloc(&ptr, size_t(ybytes)));
+        XC_CUDA(cudaMemset(ptr, 0, size_t(ybytes)));
+        b->ytbuf[i] = ptr;
+        b->ytbuf_bytes[i] = ybytes;
+      }
     }
   }
   std::vector<xc::BatchPlanDev>& host = b->host;
@@ -1047,7 +1163,7 @@ int xc_batch_tune(xc_batch_t batch, void* stream) {
   bool any_lock = false, any_tens = false;
   for (size_t p = 0; p < b->plans.size(); ++p) {
     any_lock = any_lock || b->lscratch[p] != nullptr;
-    any_tens = any_tens || xc::tensor_capable(b, int(p));
+    any_tens = any_tens || xc::tensor_capable(b, int(p)) || xc::tensor_t_capable(b, int(p));
   }
   // lockstep 2: tensor windows forward (lockstep items in the adjoint)
   for (int lk = any_tens ? 2 : any_lock ? 1 : 0; lk >= 0; --lk)
@@ -1101,7 +1217,7 @@ int xc_batch_schedule(xc_batch_t batch, int rpw_forward, int rpw_adjoint, int lo
   for (int r : {rpw_forward, rpw_adjoint})
     if (r != 1 && r != 2 && r != 4 && r != 8) return fail(XC_ERR_ARG, "right-hand sides per item: 1, 2, 4 or 8");
   return xc::build_tasks(b, rpw_forward, rpw_adjoint, lockstep_forward == 2 ? 2 : lockstep_forward ? 1 : 0,
-                         lockstep_adjoint ? 1 : 0);
+                         lockstep_adjoint == 2 ? 2 : lockstep_adjoint ? 1 : 0);
 }
 
 int xc_batch_info(xc_batch_t batch, xc_batch_stats* out) {
@@ -1120,7 +1236,8 @@ int xc_batch_info(xc_batch_t batch, xc_batch_stats* out) {
     out->tune_ms_forward[k] = b->tune_ms[0][k];
     out->tune_ms_adjoint[k] = b->tune_ms[1][k];
   }
-  out->tensor_plans = b->tens_plans;
+  out->tensor_plans = b->tens_plans[0];
+  out->tensor_plans_adjoint = b->tens_plans[1];
   for (size_t i = 0; i < b->plans.size(); ++i)
     if (i < b->host.size() && (b->host[i].lock_f || b->host[i].lock_a)) ++out->lockstep_plans;
   out->shared_bytes = int64_t(b->smem);

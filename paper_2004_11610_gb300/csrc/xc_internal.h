@@ -107,12 +107,18 @@ struct BlockDev {
 // and imaginary parts of 16 bins, zero outside the row's stored band), the
 // 16-byte chunk c of row r stored at chunk c ^ (r & 7) (the 128-byte
 // swizzled K-major layout of the tensor core's operands; xc_window.cuh).
+//
+// Adjoint windows (the transposed layout): group g of 64 bins (bin slices 2g,
+// 2g + 1) covers the rows [lo[g], lo[g] + 32 nkb[g]) in tiles of 128 rows x
+// 32 FP32 values: row m holds the real (m < 64) or imaginary part of bin
+// 64 g + (m & 63)'s values at 32 consecutive rows of y, swizzled the same way.
 struct WinBlock {
   const int* lo;
   const int* nkb;
   const int64_t* off;
   const float* val;
   int64_t spec_off;          // = BlockDev::spec_off
+  int gbase, tslices;        // = BlockDev::t_gbase, tslices (adjoint)
 };
 
 // Rows per chunk of a transposed (bin) slice in the adjoint product: long
@@ -253,6 +259,13 @@ struct Plan {
   int64_t tens_groups = 0;
   std::vector<std::vector<int>> tw_nkb_h;   // [block][group]
   WinBlock* win_blocks = nullptr;           // device copy, one per block
+  // the same for the adjoint (groups of 64 bins per block), and the chunk
+  // base of its partials (one chunk per bin slice: 0, 1, ..., total_tslices)
+  bool tens_t_ok = false;
+  int64_t tens_t_elems = 0;
+  std::vector<std::vector<int>> tw_t_nkb_h;   // [block][group]
+  WinBlock* win_blocks_t = nullptr;
+  int* tw_tcbase = nullptr;
   int4* lk_units = nullptr;
   int* lk_ubase = nullptr;
   int64_t lk_total_units = 0;

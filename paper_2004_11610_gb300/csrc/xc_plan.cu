@@ -2529,6 +2529,38 @@ __global__ void tensor_tile_kernel(const cx<float>* __restrict__ fval, const int
   }
 }
 
+// Adjoint tensor-window tiles of one block (the layout of WinBlock, adjoint):
+// blockIdx.y = bin group g; element e = (tile kb, row m, 16-byte chunk c) of
+// the group's tiles, chunk c = rows lo + 32 kb + 4c .. + 3 of component m >> 6
+// of bin 64 g + (m & 63), stored at chunk c ^ (m & 7); zero outside the bin's
+// stored run of rows and for bins >= H.
+__global__ void tensor_tile_t_kernel(const cx<float>* __restrict__ tval, const int* __restrict__ tn0,
+                                     const int* __restrict__ twidth, const int64_t* __restrict__ toff, int H,
+                                     const int* __restrict__ glo, const int* __restrict__ gnkb,
+                                     const int64_t* __restrict__ goff, float* __restrict__ out) {
+  const int g = blockIdx.y;
+  const int64_t total = int64_t(gnkb[g]) * 1024;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int kb = int(e >> 10), m = int(e >> 3) & 127, c = int(e & 7);
+    const int k = 64 * g + (m & 63);
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (k < H) {
+      const int s = k >> 5;
+      const int w = twidth[s];
+      const cx<float>* base = tval + toff[s] + (k & 31);
+      const int j0 = glo[g] + 32 * kb + 4 * c - tn0[k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (j0 + i >= 0 && j0 + i < w) {
+          const cx<float> a = base[int64_t(j0 + i) * 32];
+          v[i] = (m >> 6) ? a.im : a.re;
+        }
+    }
+    reinterpret_cast<float4*>(out + (goff[g] + kb) * 4096 + int64_t(m) * 32)[c ^ (m & 7)] =
+        make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
 namespace {
 
 template <typename T>
@@ -2688,9 +2720,71 @@ int build_lockstep(Plan* p) {
                                               p->N, lo_d, nkb_d, off_d, static_cast<float*>(val));
             XC_CUDA(cudaGetLastError());
           }
-          wb[i] = WinBlock{lo_d, nkb_d, off_d, static_cast<const float*>(val), b.spec_off};
+          wb[i] = WinBlock{lo_d, nkb_d, off_d, static_cast<const float*>(val), b.spec_off, b.t_gbase, b.tslices};
         }
         XC_TRY(upload(p, wb, &p->win_blocks));
+      }
+    }
+    // adjoint: bin group g of a block = bin slices 2g, 2g + 1, window = the
+    // union of their row runs, rounded up to whole tiles of 32 rows
+    if (p->precision == XC_FP32 && tstored > 0) {
+      std::vector<std::vector<int>> glo(nb), gnkb(nb);
+      int64_t tiles = 0;
+      for (int i = 0; i < nb; ++i) {
+        const int64_t ts = int64_t(p->ht_len[i].size());
+        const int64_t groups = (ts + 1) / 2;
+        glo[i].assign(groups, 0);
+        gnkb[i].assign(groups, 0);
+        for (int64_t g = 0; g < groups; ++g) {
+          int lo = INT_MAX, hi = -1;
+          for (int64_t s = 2 * g; s < std::min<int64_t>(2 * g + 2, ts); ++s)
+            if (p->ht_len[i][s] > 0) {
+              lo = std::min(lo, p->ht_lo[i][s]);
+              hi = std::max(hi, p->ht_lo[i][s] + p->ht_len[i][s]);
+            }
+          if (hi > lo) {
+            glo[i][g] = lo;
+            gnkb[i][g] = (hi - lo + 31) / 32;
+            tiles += gnkb[i][g];
+          }
+        }
+      }
+      const int64_t elems = tiles * 64 * 32;   // complex values per tile: 64 bins x 32 rows
+      p->tens_t_ok = double(elems) <= kTensorRatio * double(tstored);
+      p->tens_t_elems = p->tens_t_ok ? elems : 0;
+      if (p->tens_t_ok) {
+        p->tw_t_nkb_h = gnkb;
+        std::vector<WinBlock> wb(nb);
+        void* val = nullptr;
+        XC_TRY(plan_alloc(p, &val, size_t(std::max<int64_t>(tiles, 1)) * 4096 * sizeof(float)));
+        int64_t t0 = 0;
+        for (int i = 0; i < nb; ++i) {
+          const BlockDev& b = p->blocks[i];
+          const int64_t groups = int64_t(glo[i].size());
+          std::vector<int64_t> goff(std::max<int64_t>(groups, 1), 0);
+          int maxk = 0;
+          for (int64_t g = 0; g < groups; ++g) {
+            goff[g] = t0;
+            t0 += gnkb[i][g];
+            maxk = std::max(maxk, gnkb[i][g]);
+          }
+          int *lo_d, *nkb_d;
+          int64_t* off_d;
+          XC_TRY(upload(p, glo[i], &lo_d));
+          XC_TRY(upload(p, gnkb[i], &nkb_d));
+          XC_TRY(upload(p, goff, &off_d));
+          if (maxk > 0) {
+            const dim3 grid(unsigned(std::min<int64_t>((int64_t(maxk) * 1024 + 255) / 256, 4096)), unsigned(groups));
+            tensor_tile_t_kernel<<<grid, 256>>>(static_cast<const cx<float>*>(b.t_val), b.t_n0, b.t_width, b.t_off,
+                                                b.H, lo_d, nkb_d, off_d, static_cast<float*>(val));
+            XC_CUDA(cudaGetLastError());
+          }
+          wb[i] = WinBlock{lo_d, nkb_d, off_d, static_cast<const float*>(val), 0, b.t_gbase, b.tslices};
+        }
+        XC_TRY(upload(p, wb, &p->win_blocks_t));
+        std::vector<int> cb(size_t(p->total_tslices) + 1);
+        for (size_t i = 0; i < cb.size(); ++i) cb[i] = int(i);
+        XC_TRY(upload(p, cb, &p->tw_tcbase));
       }
     }
   }

@@ -53,6 +53,17 @@
 // Every mbarrier wait is bounded; a wait that runs out sets the batch's
 // status word (XC_ERR_TIMEOUT for xc_batch_status), waits (bounded) for the
 // copies and products in flight, frees the tensor memory and returns.
+//
+// The adjoint (ADJ = true; Algorithm 2, step 1: U_k = sum_n A_nk y_n of the
+// stored bands, before the inverse FFT) runs the same pipeline on the
+// transposed windows: a task is (plan, block, group of 64 bins), a tile is
+// M = 128 rows = the real parts of the 64 bins' values, then their imaginary
+// parts, over K = 32 rows of y; the right-hand sides come from yt, the
+// row-scaled right-hand sides stored row-major ([row][rp], written by a small
+// launch before), so a tile's 32 rows x rp values are again one bulk copy.
+// The epilogue writes each bin's sums as the one chunk partial of its bin
+// slice ([slice][rhs][32] complex), which the inverse-FFT tasks of the
+// persistent launch add up as they do the lockstep items' partials.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -74,12 +85,15 @@ constexpr int kWinTileFloats = kWinRows * 2 * kWinBins;   // 4096
 struct WinPlan {
   const WinBlock* blocks;
   int nblocks;
-  int rp;                       // spectrum row length (nrhs rounded up to 8), <= NP of the launch
+  int rp;                       // spectrum (yt) row length (nrhs rounded up to 8), <= NP of the launch
   int64_t N, nrhs, ld;
-  float* y;                     // [nrhs][ld]; holds the dense tail's sum (unscaled) when tail_in_y
-  const cx<float>* spec;        // bin-major spectra of all blocks
+  float* y;                     // forward: [nrhs][ld] output, holding the dense tail's sum (unscaled)
+                                // when tail_in_y; adjoint: the [nrhs][ld] input
+  const cx<float>* spec;        // forward: bin-major spectra of all blocks
   int tail_in_y;
   const float* rowscale;
+  float* yt;                    // adjoint: [N + 32][rp] row-scaled right-hand sides (pad rows zero)
+  cx<float>* part;              // adjoint: chunk partials [slice][nrhs][32], one chunk per bin slice
 };
 
 template <int NP>
@@ -105,10 +119,9 @@ struct WinCfg {
 constexpr int kWinConvThreads = 256;
 constexpr int kWinThreads = 64 + kWinConvThreads + 128 + 32;   // + the second MMA issuer (last warp)
 
-template <int NP>
+template <int NP, bool ADJ>
 __global__ void __launch_bounds__(kWinThreads, 1)
-    window_fwd_kernel(const WinPlan* __restrict__ plans, const int2* __restrict__ tasks, int ntasks,
-                      unsigned* status) {
+    window_kernel(const WinPlan* __restrict__ plans, const int4* __restrict__ tasks, int ntasks, unsigned* status) {
   using namespace tc;
   using C = WinCfg<NP>;
   constexpr int S = C::STAGES;
@@ -161,10 +174,12 @@ __global__ void __launch_bounds__(kWinThreads, 1)
     s_abort = 1;
     atomicCAS(status, 0u, 1u);
   };
-  // tiles of a task: all blocks' tiles of its row group
-  auto task_tiles = [&](const WinPlan& P, int g) {
+  // tiles of a task: forward all blocks' tiles of its row group, adjoint
+  // the tiles of its block's bin group
+  auto task_tiles = [&](const WinPlan& P, int4 tk) {
+    if constexpr (ADJ) return P.blocks[tk.y].nkb[tk.z];
     int n = 0;
-    for (int bi = 0; bi < P.nblocks; ++bi) n += P.blocks[bi].nkb[g];
+    for (int bi = 0; bi < P.nblocks; ++bi) n += P.blocks[bi].nkb[tk.z];
     return n;
   };
 
@@ -174,14 +189,14 @@ __global__ void __launch_bounds__(kWinThreads, 1)
       int kbi = 0;   // tiles issued by this CTA
       bool ok = true;
       for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
-        const int2 tk = tasks[t];
+        const int4 tk = tasks[t];
         const WinPlan& P = plans[tk.x];
-        const uint32_t braw_bytes = uint32_t(kWinBins * P.rp * 8);
-        for (int bi = 0; bi < P.nblocks && ok; ++bi) {
+        const uint32_t braw_bytes = uint32_t(kWinBins * P.rp * 8);   // = 32 rows x rp values of yt
+        for (int bi = ADJ ? tk.y : 0; bi < (ADJ ? tk.y + 1 : P.nblocks) && ok; ++bi) {
           const WinBlock& b = P.blocks[bi];
-          const int nkb = b.nkb[tk.y];
-          const int64_t lo = b.lo[tk.y];
-          const float* a_src = b.val + b.off[tk.y] * kWinTileFloats;
+          const int nkb = b.nkb[tk.z];
+          const int64_t lo = b.lo[tk.z];
+          const float* a_src = b.val + b.off[tk.z] * kWinTileFloats;
           for (int kb = 0; kb < nkb; ++kb) {
             const int s = kbi % S;
             if (!mbar_wait(empty(s), (uint32_t(kbi / S) & 1u) ^ 1u, abort)) {
@@ -191,7 +206,10 @@ __global__ void __launch_bounds__(kWinThreads, 1)
             }
             mbar_expect_tx(full(s), uint32_t(C::A_BYTES) + braw_bytes);
             bulk_load(a_t(s), a_src + int64_t(kb) * kWinTileFloats, uint32_t(C::A_BYTES), full(s));
-            bulk_load(b_raw(s), P.spec + (b.spec_off + lo + int64_t(kb) * kWinBins) * P.rp, braw_bytes, full(s));
+            if constexpr (ADJ)
+              bulk_load(b_raw(s), P.yt + (lo + int64_t(kb) * 2 * kWinBins) * P.rp, braw_bytes, full(s));
+            else
+              bulk_load(b_raw(s), P.spec + (b.spec_off + lo + int64_t(kb) * kWinBins) * P.rp, braw_bytes, full(s));
             ++kbi;
           }
         }
@@ -212,8 +230,8 @@ __global__ void __launch_bounds__(kWinThreads, 1)
       int kbi = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
-        const int2 tk = tasks[t];
-        const int nk = task_tiles(plans[tk.x], tk.y);
+        const int4 tk = tasks[t];
+        const int nk = task_tiles(plans[tk.x], tk);
         for (int k = 0; k < nk; ++k) {
           const int s = kbi % S, buf = kbi & 1;
           if (!mbar_wait(tempty(buf), (uint32_t(kbi >> 1) & 1u) ^ 1u, abort) ||
@@ -254,9 +272,9 @@ __global__ void __launch_bounds__(kWinThreads, 1)
     int kbi = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
-      const int2 tk = tasks[t];
+      const int4 tk = tasks[t];
       const WinPlan& P = plans[tk.x];
-      const int nk = task_tiles(P, tk.y);
+      const int nk = task_tiles(P, tk);
       const int rp = P.rp;
       for (int k = 0; k < nk; ++k) {
         const int s = kbi % S;
@@ -287,21 +305,30 @@ __global__ void __launch_bounds__(kWinThreads, 1)
         tc_fence_after();
         tmem_st16(a_lane + uint32_t(s * C::A_COLS), hv);
         tmem_st16(a_lane + uint32_t(s * C::A_COLS + 32), lv);
-        // spectra: K-major rows n of [F_hi; F_lo], chunk c = bins 2c, 2c+1
-        const float2* raw = reinterpret_cast<const float2*>(smem + (b_raw(s) - tile0));
+        // right-hand sides: K-major rows n of [F_hi; F_lo]; chunk c = bins 2c,
+        // 2c+1 (forward spectra, complex) or rows 4c .. 4c+3 (adjoint yt)
+        const float* raw = reinterpret_cast<const float*>(smem + (b_raw(s) - tile0));
         unsigned char* bt = smem + (b_t(s) - tile0);
         for (int i = ct; i < NP * 8; i += kWinConvThreads) {
           const int n = i >> 3, c = i & 7;
-          float2 f0 = make_float2(0.f, 0.f), f1 = make_float2(0.f, 0.f);
+          float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
           if (n < rp) {
-            f0 = raw[(2 * c) * rp + n];
-            f1 = raw[(2 * c + 1) * rp + n];
+            if constexpr (ADJ) {
+              f.x = raw[(4 * c) * rp + n];
+              f.y = raw[(4 * c + 1) * rp + n];
+              f.z = raw[(4 * c + 2) * rp + n];
+              f.w = raw[(4 * c + 3) * rp + n];
+            } else {
+              const float2 f0 = reinterpret_cast<const float2*>(raw)[(2 * c) * rp + n];
+              const float2 f1 = reinterpret_cast<const float2*>(raw)[(2 * c + 1) * rp + n];
+              f = make_float4(f0.x, f0.y, f1.x, f1.y);
+            }
           }
           float4 h, l;
-          split_tf32(f0.x, &h.x, &l.x);
-          split_tf32(f0.y, &h.y, &l.y);
-          split_tf32(f1.x, &h.z, &l.z);
-          split_tf32(f1.y, &h.w, &l.w);
+          split_tf32(f.x, &h.x, &l.x);
+          split_tf32(f.y, &h.y, &l.y);
+          split_tf32(f.z, &h.z, &l.z);
+          split_tf32(f.w, &h.w, &l.w);
           const int sw = (c ^ (n & 7)) * 16;
           *reinterpret_cast<float4*>(bt + n * 128 + sw) = h;
           *reinterpret_cast<float4*>(bt + (NP + n) * 128 + sw) = l;
@@ -320,9 +347,9 @@ __global__ void __launch_bounds__(kWinThreads, 1)
     int kbi = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
-      const int2 tk = tasks[t];
+      const int4 tk = tasks[t];
       const WinPlan& P = plans[tk.x];
-      const int nk = task_tiles(P, tk.y);
+      const int nk = task_tiles(P, tk);
       float acc[NP];
 #pragma unroll
       for (int j = 0; j < NP; ++j) acc[j] = 0.f;
@@ -355,7 +382,23 @@ __global__ void __launch_bounds__(kWinThreads, 1)
         ++kbi;
       }
       if (!ok) break;
-      const int64_t n = int64_t(tk.y) * kWinRows + q * 32 + lane;
+      if constexpr (ADJ) {
+        // lane m = 32 q + lane: bin 64 g + (m & 63) of the block, real part
+        // (m < 64) or imaginary part; its bin slice's one chunk partial
+        const WinBlock& b = P.blocks[tk.y];
+        const int m = q * 32 + lane, bl = m & 63;
+        const int sl = 2 * tk.z + (bl >> 5);
+        if (sl < b.tslices) {
+          float* out = reinterpret_cast<float*>(P.part + (int64_t(b.gbase) + sl) * P.nrhs * 32) +
+                       2 * (bl & 31) + (m >> 6);
+          const int nq = int(P.nrhs < NP ? P.nrhs : NP);
+#pragma unroll
+          for (int j = 0; j < NP; ++j)
+            if (j < nq) out[int64_t(j) * 64] = acc[j];
+        }
+        continue;
+      }
+      const int64_t n = int64_t(tk.z) * kWinRows + q * 32 + lane;
       if (n < P.N) {
         const int nq = int(P.nrhs < NP ? P.nrhs : NP);
         float* yn = P.y + n;

@@ -60,7 +60,8 @@ class xc_batch_stats(ctypes.Structure):
                 ("shared_bytes", ctypes.c_int64), ("matrix_bytes", ctypes.c_int64),
                 ("adjoint_bytes", ctypes.c_int64), ("lockstep_forward", ctypes.c_int),
                 ("lockstep_adjoint", ctypes.c_int), ("lockstep_plans", ctypes.c_int), ("tune_ms_forward", ctypes.c_float * 12),
-                ("tune_ms_adjoint", ctypes.c_float * 12), ("tensor_plans", ctypes.c_int)]
+                ("tune_ms_adjoint", ctypes.c_float * 12), ("tensor_plans", ctypes.c_int),
+                ("tensor_plans_adjoint", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -317,27 +317,29 @@ def test_batch_lockstep_items_against_the_oracle(xc, lock, rpw):
 
 @pytest.mark.parametrize("rpw", [4, 8])
 def test_batch_tensor_windows_against_the_oracle(xc, rpw):
-    """Forward band products on the tensor cores (schedule lockstep 2):
-    Hermite plans with ragged row groups (N not a multiple of 128), 1 to 64
-    right-hand sides (the three launch classes rp <= 16, 32, 64, with rp
-    above nrhs), against the FP64 oracle's method on the same nodes
-    (relative l2 <= max(10 eps, 1e-5)) and against the batch's lockstep
-    items on the same inputs (FP32 rounding); a Legendre plan in the same
-    batch keeps its row-per-lane items."""
+    """Band products on the tensor cores (schedule lockstep 2), forward and
+    adjoint: Hermite plans with ragged row and bin groups (N not a multiple
+    of 128), 1 to 64 right-hand sides (the three launch classes rp <= 16, 32,
+    64, with rp above nrhs), against the FP64 oracle's method on the same
+    nodes (relative l2 <= max(10 eps, 1e-5)) and against the batch's
+    lockstep items on the same inputs (FP32 rounding); a Legendre plan in
+    the same batch keeps its row-per-lane items."""
     from oracle import families as F
     from oracle import method as M
     eps = 1e-7
     cases = [("hermite", 300, 1), ("hermite", 1000, 9), ("hermite", 2500, 16), ("hermite", 777, 17),
              ("hermite", 4100, 24), ("hermite", 1300, 33), ("hermite", 2000, 64), ("legendre", 900, 5)]
-    plans, specs, xs, ys, X = [], [], [], [], []
+    plans, specs, xs, ys, X, xa, Yin = [], [], [], [], [], [], []
     try:
         for i, (fam, N, R) in enumerate(cases):
             sp = F.make_spec(fam, N)
             specs.append(sp)
             plans.append(xc.Plan(fam, N, eps, precision="fp32", nodes=sp.x))
             X.append(inputs.normal(N, R, 42, i))
+            Yin.append(inputs.normal(N, R, 43, i))
             xs.append(torch.from_numpy(X[-1]).to("cuda", torch.float32))
             ys.append(torch.empty_like(xs[-1]))
+            xa.append(torch.empty_like(xs[-1]))
         with xc.Batch(plans) as b:
             b.bind(xs, ys)
             b.schedule(rpw, rpw, 1, 1)
@@ -355,12 +357,35 @@ def test_batch_tensor_windows_against_the_oracle(xc, rpw):
             torch.cuda.synchronize()
             assert b.status() == xc.XC_OK
             Y = [y.double().cpu().numpy() for y in ys]
-        for sp, y, yl, xi in zip(specs, Y, Y_lock, X):
+        for y, v in zip(ys, Yin):
+            y.copy_(torch.from_numpy(v).to(torch.float32))
+        with xc.Batch(plans) as b2:
+            b2.bind(xa, ys)
+            b2.schedule(rpw, rpw, 1, 1)
+            b2.apply(True)
+            torch.cuda.synchronize()
+            assert b2.status() == xc.XC_OK
+            XA_lock = [x.double().cpu().numpy() for x in xa]
+            b2.schedule(rpw, rpw, 2, 2)
+            info = b2.info()
+            print(f"adjoint tensor plans {info['tensor_plans_adjoint']} of {len(cases)}")
+            assert info["tensor_plans_adjoint"] >= 5 and info["lockstep_adjoint"] == 2
+            for x in xa:
+                x.fill_(float("nan"))
+            b2.apply(True)
+            torch.cuda.synchronize()
+            assert b2.status() == xc.XC_OK
+            XA = [x.double().cpu().numpy() for x in xa]
+        for sp, y, yl, xi, xg, xl, yi in zip(specs, Y, Y_lock, X, XA, XA_lock, Yin):
             ora = M.build(sp, eps, precision="fp32")
             ef = M.rel_l2(y, M.apply(ora, xi))
             el = M.rel_l2(y, yl)
-            print(f"tensor windows {sp.family} N={sp.N} R={xi.shape[0]}: vs oracle {ef:.2e}, vs lockstep {el:.2e}")
-            assert np.isfinite(y).all()
+            ea = M.rel_l2(xg, M.apply_adjoint(ora, yi))
+            eal = M.rel_l2(xg, xl)
+            print(f"tensor windows {sp.family} N={sp.N} R={xi.shape[0]}: fwd vs oracle {ef:.2e}, vs lockstep "
+                  f"{el:.2e}; adj vs oracle {ea:.2e}, vs lockstep {eal:.2e}")
+            assert np.isfinite(y).all() and np.isfinite(xg).all()
             assert ef <= max(10 * eps, 1e-5) and el <= 2e-6
+            assert ea <= max(10 * eps, 1e-5) and eal <= 2e-6
     finally:
         close_all(plans)
