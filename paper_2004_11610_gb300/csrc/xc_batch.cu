@@ -843,7 +843,7 @@ int launch_batch_t(Batch* b, int dir, cudaStream_t st) {
 template <int NP, bool ADJ>
 int launch_window(Batch* b, int cls, cudaStream_t st) {
   using C = WinCfg<NP>;
-  auto fn = window_kernel<NP, ADJ>;
+  auto fn = tc_window_kernel<NP, ADJ>;
   const int d = ADJ ? 1 : 0;
   // one CTA per SM: each allocates all of the SM's tensor memory
   const int smem = std::max(C::SMEM, 116 * 1024);

@@ -121,7 +121,7 @@ constexpr int kWinThreads = 64 + kWinConvThreads + 128 + 32;   // + the second M
 
 template <int NP, bool ADJ>
 __global__ void __launch_bounds__(kWinThreads, 1)
-    window_kernel(const WinPlan* __restrict__ plans, const int4* __restrict__ tasks, int ntasks, unsigned* status) {
+    tc_window_kernel(const WinPlan* __restrict__ plans, const int4* __restrict__ tasks, int ntasks, unsigned* status) {
   using namespace tc;
   using C = WinCfg<NP>;
   constexpr int S = C::STAGES;
