@@ -51,9 +51,11 @@ __host__ __device__ __forceinline__ bool is_trig(int family) {
 }
 
 // exp(-a) for a >= 0 as mant * 2^expo, with the argument split
-// a = q ln2 - r (q integer, ln2 = hi + lo, q * hi exact) so that the result
-// keeps full relative accuracy even when exp(-a) is far below the FP64 range.
-// a_lo carries a low-order part of the argument (exact products).
+// a = q ln2 - r (q integer, ln2 = hi + lo, q * hi exact: the published
+// Cody-Waite additive range reduction) so that the result keeps full
+// relative accuracy even when exp(-a) is far below the FP64 range; the
+// reduced exp(-r) is CUDA's own exp.  a_lo carries a low-order part of the
+// argument (exact products).
 __device__ void exp_neg_split(double a_hi, double a_lo, double* mant, int* expo) {
   const double ln2_hi = 0.6931471803691238;          // ln 2 to 32 significant bits
   const double ln2_lo = 1.9082149292705877e-10;      // ln 2 - ln2_hi
