@@ -1040,6 +1040,7 @@ def measure_batch(xc, torch, nplans, dev, rank, world, steps, warmup, tune=True,
                    "parallelism": f"replicas x{world}",
                    "tuned_rhs_per_item": [fwd.info()["rhs_per_item"], adj.info()["rhs_per_item_adjoint"]],
                    "tuned_lockstep": [fwd.info()["lockstep_forward"], adj.info()["lockstep_adjoint"]],
+                   "tensor_window_plans": [fwd.info()["tensor_plans"], adj.info()["tensor_plans_adjoint"]],
                    "tune_ms": {"forward": _tune_table(fwd.info()["tune_ms_forward"]),
                                "adjoint": _tune_table(adj.info()["tune_ms_adjoint"])}},
         "matrix_bytes": sum(i["matrix_bytes"] for i in infos),
