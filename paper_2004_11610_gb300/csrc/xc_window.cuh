@@ -25,24 +25,27 @@
 //
 // Kernel: persistent, one CTA per SM, tasks (plan, row group) taken in
 // a fixed order (task blockIdx.x + i gridDim.x), each task the tiles of all
-// blocks of its row group.  448 threads:
+// blocks of its row group.  480 threads:
 //   warp 0     producer: per tile one bulk copy of the 16 KB band tile and
 //              one of the 16 bins x rp spectrum values (contiguous in the
 //              bin-major layout) into a ring of STAGES stages
 //   warp 1     allocates all 512 tensor-memory columns: per stage 32
 //              columns of A_hi and 32 of A_lo (lane = band row), and two
-//              accumulator buffers of 3 NP columns; one thread issues, per K
-//              step of 8, tcgen05.mma kind::tf32 with A in tensor memory,
-//              M = 128, N = 2 NP: A_hi x [F_hi; F_lo] into columns [0, 2 NP)
-//              and N = NP: A_lo x F_hi into [2 NP, 3 NP) -- two independent
-//              accumulation chains: one chain of these narrow products is
-//              bound by the latency from one accumulation to the next
+//              accumulator buffers of 3 NP columns; its first thread
+//              issues, per K step of 8, tcgen05.mma kind::tf32 with A in
+//              tensor memory, M = 128, N = 2 NP: A_hi x [F_hi; F_lo] into
+//              columns [0, 2 NP)
+//   warp 14    the second issuer: N = NP, A_lo x F_hi into [2 NP, 3 NP) --
+//              two threads issuing into separate accumulators, since one
+//              thread issuing these narrow products back to back left the
+//              tensor pipe idle about two thirds of the time; both commit
+//              to the stage and buffer barriers, which count two arrivals
 //   warps 2-9  converters: warp w, lane l splits half (w - 2) / 4 of band
 //              row 32 (w % 4) + l (its tensor-memory lane) and stores hi and
 //              lo to the stage's tensor-memory columns, and the threads
 //              together write F_hi / F_lo as K-major 128-byte swizzled rows
 //              of the right-hand sides (zero past rp) to shared memory, then
-//              release the stage to the MMA thread (two converter warps per
+//              release the stage to the MMA threads (two converter warps per
 //              scheduler: the split is bound by latency, not arithmetic)
 //   warps 10-13 epilogue: warp w owns tensor-memory lanes 32 (w % 4) .. + 31
 //              = rows of the group; per tile it loads the 3 NP columns and
