@@ -21,6 +21,15 @@
 // RL rows (bins) x 8 right-hand sides, so that every band and spectrum value
 // it loads feeds several multiply-adds.  The tuner decides per direction
 // whether such plans use them.
+// FP32 plans whose bands are nearly dense over 128 rows (64 bins) also have
+// tensor windows; with lockstep 2 their band products leave the persistent
+// launch for tensor-core launches of their own (xc_window.cuh): forward, the
+// persistent launch makes their spectra (bin-major), fwd_tail_kernel puts
+// their dense tails' sums in y, and tc_window_kernel<NP, false> adds the band
+// sums; adjoint, adj_yt_kernel writes their row-scaled right-hand sides
+// row-major, tc_window_kernel<NP, true> writes one chunk partial per bin
+// slice, and the persistent launch that follows runs their tails and inverse
+// FFTs.
 // Every CTA of a persistent grid works through A (CTA tasks from a device
 // counter), then its warps take B items one by one from a second counter,
 // then -- after a CTA barrier -- it works through C (CTA tasks or warp items).
