@@ -154,3 +154,16 @@ def test_profile_summaries_are_current_and_name_their_kernels_sources():
         for k, plan, b in re.findall(r"traffic:\s*(\S+)\s+plan=(\S+)\s+dram_bytes=([0-9.eE+]+)", text):
             if k == kernel:
                 assert bench.traffic_from_profiles(k, workload, plan) == (None if stale else float(b))
+
+
+def test_tune_table_names_every_tried_schedule():
+    """The batch tuner's timings (entry 4 * lockstep + log2(rhs per item),
+    lockstep 0/1/2 = row per lane / lockstep items / tensor windows) become
+    named bench fields; untried candidates (-1) are left out."""
+    import bench
+    ms = [float(k) for k in range(12)]
+    ms[5] = -1.0
+    t = bench._tune_table(ms)
+    assert len(t) == 11 and "lockstep1_rpw2" not in t
+    assert t["lockstep0_rpw1"] == 0.0 and t["lockstep0_rpw8"] == 3.0
+    assert t["lockstep2_rpw1"] == 8.0 and t["lockstep2_rpw8"] == 11.0
